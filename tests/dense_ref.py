@@ -1,0 +1,106 @@
+"""Independent dense-matrix construction of the Wilson-Dirac operator (test pin).
+
+Written separately from the oracle (no shared code): the gamma matrices are
+spelled out entry by entry, links come from the explicit 2x2 form of a
+quaternion and the adjoint links from the quaternion rotation matrix, and the
+operator is assembled as a (4 nc V)^2 matrix from permutation matrices.  Used
+on lattices up to 4^4 to brute-force the oracle's matrix-free routines.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+# Chiral basis, written out: g0 = [[0,1],[1,0]], gk = [[0,-i s_k],[i s_k,0]].
+_i = 1j
+GAMMA = [
+    np.array([[0, 0, 1, 0],
+              [0, 0, 0, 1],
+              [1, 0, 0, 0],
+              [0, 1, 0, 0]], dtype=complex),
+    np.array([[0, 0, 0, -_i],
+              [0, 0, -_i, 0],
+              [0, _i, 0, 0],
+              [_i, 0, 0, 0]], dtype=complex),
+    np.array([[0, 0, 0, -1],
+              [0, 0, 1, 0],
+              [0, 1, 0, 0],
+              [-1, 0, 0, 0]], dtype=complex),
+    np.array([[0, 0, -_i, 0],
+              [0, 0, 0, _i],
+              [_i, 0, 0, 0],
+              [0, -_i, 0, 0]], dtype=complex),
+]
+GAMMA5 = np.diag([-1, -1, 1, 1]).astype(complex)
+
+
+def su2(q) -> np.ndarray:
+    """Explicit 2x2 matrix of a0 + i(a1 s1 + a2 s2 + a3 s3)."""
+    a0, a1, a2, a3 = q
+    return np.array([[a0 + 1j * a3, a2 + 1j * a1],
+                     [-a2 + 1j * a1, a0 - 1j * a3]])
+
+
+def rotation(q) -> np.ndarray:
+    """Adjoint link as the 3x3 rotation of the unit quaternion q:
+    R = (a0^2 - |a|^2) 1 + 2 a a^T + 2 a0 [a]_x^T, where [a]_x^T has entries eps_{b c k} a_k.
+    """
+    a0 = q[0]
+    a = np.asarray(q[1:], dtype=float)
+    cross = np.array([[0.0, a[2], -a[1]],
+                      [-a[2], 0.0, a[0]],
+                      [a[1], -a[0], 0.0]])
+    return (a0 * a0 - a @ a) * np.eye(3) + 2.0 * np.outer(a, a) + 2.0 * a0 * cross
+
+
+def site_index(dims):
+    return np.arange(int(np.prod(dims))).reshape(dims)
+
+
+def link_matrices(dims, q, nc):
+    V = int(np.prod(dims))
+    out = np.zeros((4, V, nc, nc), dtype=complex)
+    for mu in range(4):
+        for x in range(V):
+            out[mu, x] = su2(q[mu, x]) if nc == 2 else rotation(q[mu, x])
+    return out
+
+
+def hopping_dense(dims, q, nc) -> np.ndarray:
+    """Dense H with (H psi)(x) = sum_mu (1-g) U_mu(x) psi(x+mu) + (1+g) U_mu(x-mu)^+ psi(x-mu).
+
+    Index order (site, spin, colour).  On an extent-2 direction the forward and
+    backward neighbours coincide and the two blocks add.
+    """
+    V = int(np.prod(dims))
+    idx = site_index(dims)
+    U = link_matrices(dims, q, nc)
+    n = V * 4 * nc
+    H = np.zeros((V, 4, nc, V, 4, nc), dtype=complex)
+    one = np.eye(4)
+    for mu in range(4):
+        fwd = np.roll(idx, -1, axis=mu).reshape(-1)  # fwd[x] = x + mu
+        bwd = np.roll(idx, 1, axis=mu).reshape(-1)   # bwd[x] = x - mu
+        pm = one - GAMMA[mu]
+        pp = one + GAMMA[mu]
+        for x in range(V):
+            H[x, :, :, fwd[x], :, :] += np.einsum("st,cd->sctd", pm, U[mu, x])
+            H[x, :, :, bwd[x], :, :] += np.einsum("st,cd->sctd", pp, U[mu, bwd[x]].conj().T)
+    return H.reshape(n, n)
+
+
+def dirac_dense(dims, q, nc, m0) -> np.ndarray:
+    n = int(np.prod(dims)) * 4 * nc
+    return (4.0 + m0) * np.eye(n) - 0.5 * hopping_dense(dims, q, nc)
+
+
+def parity_of_sites(dims) -> np.ndarray:
+    return (np.indices(dims).sum(axis=0) & 1).reshape(-1)
+
+
+def eo_blocks(dims, nc, M):
+    """Split a (site, spin, colour) matrix into even/odd blocks."""
+    par = np.repeat(parity_of_sites(dims), 4 * nc)
+    e = np.where(par == 0)[0]
+    o = np.where(par == 1)[0]
+    return M[np.ix_(e, e)], M[np.ix_(e, o)], M[np.ix_(o, e)], M[np.ix_(o, o)], e, o
