@@ -1,0 +1,490 @@
+#!/usr/bin/env python3
+"""Benchmark of the even-odd Wilson-Dirac operator on one GB300 (or N replicas).
+
+Metric: "Dirac-op GB/s & % HBM peak at 48^4 SU(2); mixed vs FP64 CG time to
+1e-10".  One step is one even-odd Dirac application of the whole 48^4 lattice
+in the SU(2) fundamental representation, FP64: out_e = D_eo in_o and
+out_o = D_oe in_e (two launches of the hop kernel, every site once).  Its
+throughput counts the compulsory bytes of the hop (per output site: the input
+spinor once, the output spinor once and 8 quaternion links = 512 B in FP64).
+The CG half of the metric (32^4, FP64 vs FP32/FP16-inner mixed precision,
+true residual 1e-10) and the other precisions/representations are measured
+after the timed region and reported under "extras".
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank runs an independent replica (the single-GPU hot path
+has no data exchange); value = the bytes all ranks processed / max rank time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dirac-op GB/s & % HBM peak at 48^4 SU(2); mixed vs FP64 CG time to 1e-10"
+DIMS = (48, 48, 48, 48)
+GAUGE_SEED, SPINOR_SEED = 1003, 2003
+HBM_FALLBACK = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="skip the CG and precision sweep")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def hop_bytes_per_site(rep: str, prec: str) -> int:
+    """Compulsory bytes per output site of one hop: 1 spinor in, 1 out, 8 links."""
+    spinor = {"f64": 16 * 8, "f32": 16 * 4, "f16": 16 * 2 + 4}
+    link = {"f64": 32, "f32": 16, "f16": 8}
+    nspin = {"fund": 1.0, "adj": 1.5}[rep]
+    return int(2 * spinor[prec] * nspin + 8 * link[prec])
+
+
+def neighbour_bytes_per_site(rep: str, prec: str) -> int:
+    spinor = {"f64": 16 * 8, "f32": 16 * 4, "f16": 16 * 2 + 4}
+    link = {"f64": 32, "f32": 16, "f16": 8}
+    nspin = {"fund": 1.0, "adj": 1.5}[rep]
+    return int(9 * spinor[prec] * nspin + 8 * link[prec])
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2411_18511_gb300", "csrc")
+    for f in ("hr_internal.cuh", "hr_hop.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """Per-launch DRAM bytes of a kernel from a committed ncu summary, if it was
+    taken on the current kernel source (a 'source_hash:' line must match)."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_hash")):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append(line.strip())
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_smi_id(torch, dev: int) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+# ----------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    from paper_2411_18511_gb300 import hr, fields
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    ctx = hr.Context(local)
+    dims = DIMS
+    V = int(np.prod(dims))
+    Vh = V // 2
+    rep, prec = hr.HR_FUND, hr.HR_F64
+    q = synth.haar_links(dims, GAUGE_SEED)
+    psi = synth.gaussian_spinor(dims, 2, SPINOR_SEED)
+    gauge = fields.pack_gauge(ctx, dims, rep, prec, fields.gauge_to_device(q))
+    dpsi = fields.spinor_to_device(psi)
+    src = fields.pack_spinor(ctx, dims, rep, prec, hr.HR_FULL, dpsi)
+    dst = fields.empty_spinor(dims, rep, prec, hr.HR_FULL)
+    half = hr.hr_spinor_packed_bytes(dims, rep, prec, hr.HR_EVEN, 1)
+    stream = torch.cuda.current_stream()
+    s_ptr = stream.cuda_stream
+    L = hr.lib()
+    lat = hr.lattice(dims)
+    p_g, p_s, p_d = gauge.data_ptr(), src.data_ptr(), dst.data_ptr()
+
+    def step():
+        # out_e = D_eo in_o ; out_o = D_oe in_e   (two hop launches)
+        rc = L.hr_dirac_eo(ctx.handle, lat, 0.0, rep, prec, hr.HR_EVEN, hr.HR_OP_HOP, 1, p_g,
+                           p_s + half, p_d, None, 0, s_ptr)
+        rc |= L.hr_dirac_eo(ctx.handle, lat, 0.0, rep, prec, hr.HR_ODD, hr.HR_OP_HOP, 1, p_g,
+                            p_s, p_d + half, None, 0, s_ptr)
+        if rc:
+            ctx.check(rc)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_smi_id(torch, local))
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    bytes_site = hop_bytes_per_site("fund", "f64")
+    bytes_step = 2 * Vh * bytes_site
+    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    launch_ms = ms_step / 2.0
+    achieved = Vh * bytes_site / (launch_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    host_in = torch.view_as_real(torch.from_numpy(psi)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_can = torch.empty(host_in.shape, dtype=torch.float64, device="cuda")
+    dev_can_out = torch.empty_like(dev_can)
+    full_bytes = hr.hr_spinor_packed_bytes(dims, rep, prec, hr.HR_FULL, 1)
+
+    def e2e_step():
+        dev_can.copy_(host_in, non_blocking=True)
+        hr.hr_spinor_pack(ctx, dims, rep, prec, hr.HR_FULL, 1, dev_can, src, stream)
+        step()
+        hr.hr_spinor_unpack(ctx, dims, rep, prec, hr.HR_FULL, 1, dst, dev_can_out, stream)
+        host_out.copy_(dev_can_out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    n_e2e = max(5, min(50, args.steps // 20))
+    e0.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    if dist is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": round(world * bytes_step / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": int(host_in.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
+           "ms_per_step": round(e2e_ms, 4),
+           "path": "pinned host canonical spinor -> H2D -> hr_spinor_pack -> 2x hr_dirac_eo -> hr_spinor_unpack -> D2H"}
+    del dev_can, dev_can_out
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(ctx, torch, hr, fields, synth, q, psi)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(q, psi)
+
+    result = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (Haar-random SU(2) links, Gaussian complex source, Philox seeds 1003/2003)",
+        "config": {
+            "workload": "even-odd Wilson-Dirac hop pair D_eo+D_oe, 48^4 SU(2) fundamental, FP64",
+            "lattice": list(dims), "rep": "fund", "prec": "f64",
+            "bytes_per_site": bytes_site, "byte_convention": "compulsory (1 spinor in + 1 out + 8 quaternion links)",
+            "neighbour_counted_gbs": round(value * neighbour_bytes_per_site("fund", "f64") / bytes_site, 2),
+            "l2": "inputs larger than L2 (gauge 680 MB, spinor half 340 MB per launch)",
+            "parallelism": f"replicas{world}",
+        },
+        "roofline": {
+            "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} HBM copy",
+            "traffic": profiled_traffic("hop_fund_f64_48x48x48x48.md"),
+            "kernel": "k_hop<fund,f64>", "bytes_per_launch": Vh * bytes_site,
+            "avg_launch_ms": round(launch_ms, 5),
+        },
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "extras": extras,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def time_hop(ctx, torch, hr, fields, dims, rep, prec, q, psi, steps=100):
+    """Average GB/s of one hop launch (compulsory bytes) for a rep/prec."""
+    gauge = fields.pack_gauge(ctx, dims, rep, prec, fields.gauge_to_device(q))
+    src = fields.pack_spinor(ctx, dims, rep, prec, hr.HR_ODD, psi)
+    dst = fields.empty_spinor(dims, rep, prec, hr.HR_EVEN)
+    for _ in range(5):
+        hr.hr_dirac_eo(ctx, dims, 0.0, rep, prec, hr.HR_EVEN, hr.HR_OP_HOP, 1, gauge, src, dst)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        hr.hr_dirac_eo(ctx, dims, 0.0, rep, prec, hr.HR_EVEN, hr.HR_OP_HOP, 1, gauge, src, dst)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    Vh = int(np.prod(dims)) // 2
+    rname = "fund" if rep == hr.HR_FUND else "adj"
+    pname = {hr.HR_F64: "f64", hr.HR_F32: "f32", hr.HR_F16: "f16"}[prec]
+    b = hop_bytes_per_site(rname, pname)
+    if rep == hr.HR_ADJ_MAT:
+        b += 8 * ({"f64": 72, "f32": 36, "f16": 18}[pname] - {"f64": 32, "f32": 16, "f16": 8}[pname])
+    return {"ms": round(ms, 5), "gbs": round(Vh * b / (ms * 1e-3) / 1e9, 1), "bytes_per_site": b}
+
+
+def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
+    out = {}
+    dims = DIMS
+    dq = None
+    # precision / representation sweep of the hop at 48^4 (config: adjoint FP64 and FP32, 200 applications)
+    fund_psi = fields.spinor_to_device(psi48)
+    for prec in (hr.HR_F32, hr.HR_F16):
+        out[f"hop_fund_{ {1: 'f32', 2: 'f16'}[prec]}_48"] = time_hop(ctx, torch, hr, fields, dims, hr.HR_FUND, prec, q48, fund_psi)
+    del fund_psi
+    adj_psi = fields.spinor_to_device(synth.gaussian_spinor(dims, 3, 2004))
+    for rep, rn in ((hr.HR_ADJ, "adj"), (hr.HR_ADJ_MAT, "adjmat")):
+        for prec in (hr.HR_F64, hr.HR_F32):
+            out[f"hop_{rn}_{ {0: 'f64', 1: 'f32'}[prec]}_48"] = time_hop(
+                ctx, torch, hr, fields, dims, rep, prec, q48, adj_psi, steps=200)
+    del adj_psi
+    torch.cuda.empty_cache()
+    # CG time to solution at 32^4 (smeared links, plaquette ~0.6, m0 = -0.2, tol 1e-10)
+    d32 = (32, 32, 32, 32)
+    t0 = time.time()
+    q32, nsm, plaq = synth.ape_smear_to_plaquette(synth.haar_links(d32, 1002), d32, 0.6)
+    b = synth.gaussian_spinor(d32, 2, 2002)
+    gauge = fields.pack_gauge(ctx, d32, hr.HR_FUND, hr.HR_F64, fields.gauge_to_device(q32))
+    bp = fields.pack_spinor(ctx, d32, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, fields.spinor_to_device(b))
+    cg = {"lattice": list(d32), "m0": -0.2, "tol": 1e-10, "plaquette": round(plaq, 4), "ape_steps": nsm,
+          "setup_s": round(time.time() - t0, 1)}
+    for name, inner in (("fp64", hr.HR_F64), ("mixed_f32", hr.HR_F32), ("mixed_f16", hr.HR_F16)):
+        opts = hr.hr_solver_default_opts()
+        opts.inner_prec = inner
+        work = fields.empty_bytes(hr.hr_cg_workspace_bytes(d32, hr.HR_FUND, opts))
+        times = []
+        info = None
+        rc = None
+        for rep_i in range(3):
+            xp = fields.zeros_spinor(d32, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
+            rc, info = hr.hr_cg_solve(ctx, d32, -0.2, hr.HR_FUND, opts, gauge, bp, xp, work)
+            times.append(info.seconds)
+        cg[name] = {"status": hr.STATUS_NAMES.get(rc, rc), "seconds_median": round(statistics.median(times), 4),
+                    "iters": info.iters, "reliable_updates": info.n_reliable_updates,
+                    "true_rel_residual": info.true_rel_residual}
+        del work
+    if "fp64" in cg and cg["fp64"]["seconds_median"] > 0:
+        for k in ("mixed_f32", "mixed_f16"):
+            cg[k]["speedup_vs_fp64"] = round(cg["fp64"]["seconds_median"] / cg[k]["seconds_median"], 3)
+    out["cg_32"] = cg
+    return out
+
+
+def cpu_baseline(q, psi):
+    """The FP64 oracle as it stands on the host cores: one hop pair over the
+    whole 48^4 lattice (every site once), OpenMP over sites."""
+    import oracle
+    try:
+        L = oracle.expand_links(DIMS, 2, q)
+        V = int(np.prod(DIMS))
+        t0 = time.perf_counter()
+        out = oracle.hop(DIMS, L, psi, parity=-1)
+        dt = time.perf_counter() - t0
+        del out, L
+        gbs = (V // 2) * 2 * hop_bytes_per_site("fund", "f64") / dt / 1e9
+        return {"value": round(gbs, 3), "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": f"one D_eo+D_oe application over all {V} sites of 48^4 ({dt:.2f} s)",
+                "cpu": _cpu_model()}
+    except Exception as exc:  # the baseline is informative only
+        return {"value": None, "unit": "GB/s", "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
+
+
+def _cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return os.uname().machine
+
+
+# ----------------------------------------------------------------------------- reference
+
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload and metric, on the host cores."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    q = synth.haar_links(DIMS, GAUGE_SEED)
+    psi = synth.gaussian_spinor(DIMS, 2, SPINOR_SEED)
+    L = oracle.expand_links(DIMS, 2, q)
+    V = int(np.prod(DIMS))
+    rng = np.random.default_rng(0)
+    # size each step's sample so that warmup + steps take about two minutes
+    probe = rng.choice(V, 20000, replace=False)
+    t0 = time.perf_counter()
+    oracle.hop_sites(DIMS, L, psi, probe)
+    per_site = (time.perf_counter() - t0) / probe.size
+    n_sites = int(min(V, max(2000, 120.0 / max(1, args.steps + args.warmup) / per_site)))
+    sites = [rng.choice(V, n_sites, replace=False) for _ in range(4)]
+    for w in range(args.warmup):
+        oracle.hop_sites(DIMS, L, psi, sites[w % 4])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.hop_sites(DIMS, L, psi, sites[k % 4])
+    dt = time.perf_counter() - t0
+    bps = hop_bytes_per_site("fund", "f64")
+    value = n_sites * args.steps * bps / dt / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "even-odd Wilson-Dirac hop pair D_eo+D_oe, 48^4 SU(2) fundamental, FP64",
+                   "lattice": list(DIMS)},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{n_sites} random sites of 48^4 per step (hop at each site)"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

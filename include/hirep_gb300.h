@@ -1,0 +1,227 @@
+/*
+ * hirep_gb300.h -- C ABI of libhirep_gb300.so, the even-odd Wilson-Dirac hot
+ * path for SU(2) gauge links on one NVIDIA GB300 (sm_103a).
+ *
+ * What the library computes.  arXiv:2411.18511 ("Scaling SU(2) to 1000 GPUs
+ * using HiRep") measures the unimproved Wilson-Dirac operator (Sec. 2.1,
+ * Table 1), its even/odd split and its even-odd preconditioned form "used
+ * mainly in the HMC" (Sec. 2.1), for SU(2) with fermions in the fundamental and
+ * higher representations (Sec. 1), inside the code's inverters (Sec. 1).  The
+ * paper prints no formula; this library implements the textbook operator
+ *
+ *   (D psi)(x) = (4+m0) psi(x) - 1/2 (H psi)(x),
+ *   (H psi)(x) = sum_mu (1-g_mu) U_mu(x) psi(x+mu) + (1+g_mu) U_mu(x-mu)^+ psi(x-mu),
+ *
+ * periodic in all four directions, chiral gamma basis
+ *   g_0 = [[0,1],[1,0]], g_k = [[0,-i s_k],[i s_k,0]], g5 = g0 g1 g2 g3 = diag(-1,-1,1,1),
+ * kappa = 1/(8 + 2 m0), and on even sites the Schur complement
+ *
+ *   Mhat = (4+m0) - H_eo H_oe / (4 (4+m0)),   Mhat^+ = g5 Mhat g5.
+ *
+ * Representations: HR_FUND (SU(2) fundamental, 2 complex colours) and the
+ * adjoint (3 colours, real links R_ab = 1/2 tr(s_a U s_b U^+)).
+ *
+ * Conventions common to every call
+ * --------------------------------
+ * - Lattice extents (T, L1, L2, L3), each even and >= 2.  Site x = (x0..x3)
+ *   has lexicographic index ((x0*L1 + x1)*L2 + x2)*L3 + x3 and parity
+ *   (x0+x1+x2+x3) mod 2 (even = 0).  V = T*L1*L2*L3, V_h = V/2.
+ * - Canonical ("user") layouts, FP64:
+ *     gauge  double[4][V][4]      link U_mu(x) as quaternion (a0,a1,a2,a3),
+ *                                 U = a0 + i(a1 s1 + a2 s2 + a3 s3)
+ *     spinor double[V][4][nc][2]  site, spin, colour, (re, im)
+ * - Packed layouts are opaque device buffers sized by hr_*_packed_bytes; the
+ *   kernels read and write packed data only.  A packed spinor of one parity
+ *   holds V_h sites; a "full" packed spinor is the even half followed by the
+ *   odd half.  Packed buffers must be 256-byte aligned (cudaMalloc and torch
+ *   allocations are).
+ * - Ownership: the caller owns every buffer (device pointers, allocated by
+ *   the caller) and the stream.  No hot call allocates memory.  Work buffers
+ *   are passed in, sized by hr_workspace_bytes.  Calls are asynchronous on
+ *   the given stream unless stated otherwise.
+ * - A context's device scratch (reduction partials, solver scalars) is shared
+ *   by the calls made with it: calls on one context must not overlap in time
+ *   (use one stream per context, or one context per stream).
+ * - Errors: every call returns hr_status; argument errors are detected on the
+ *   host before anything is launched; hr_last_error() gives a message.
+ */
+#ifndef HIREP_GB300_H
+#define HIREP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *hr_stream; /* cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    HR_OK = 0,
+    HR_ERR_INVALID_ARG = 1,   /* bad pointer, size, enum or extent              */
+    HR_ERR_UNSUPPORTED = 2,   /* valid but not implemented (odd extent, combo)  */
+    HR_ERR_CUDA = 3,          /* a CUDA runtime call failed                     */
+    HR_ERR_NOT_CONVERGED = 4, /* solver hit maxiter; x holds the last iterate   */
+    HR_ERR_NUMERIC = 5,       /* NaN or Inf met in a residual                   */
+    HR_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                  */
+    HR_ERR_WORKSPACE = 7      /* workspace too small                            */
+} hr_status;
+
+typedef enum {
+    HR_FUND = 0,    /* fundamental: 2 complex colours, links stored as quaternions        */
+    HR_ADJ = 1,     /* adjoint: 3 colours, links stored as quaternions, R(U) rebuilt in registers */
+    HR_ADJ_MAT = 2  /* adjoint: as HR_ADJ but links stored as 3x3 real matrices R(U)    */
+} hr_rep;
+
+typedef enum {
+    HR_F64 = 0, /* FP64 storage (IEEE binary64)                                          */
+    HR_F32 = 1, /* FP32 storage and arithmetic                                            */
+    HR_F16 = 2  /* binary16 storage (spinors scaled by a per-site FP32 max-abs), FP32 arithmetic */
+} hr_prec;
+
+typedef enum { HR_EVEN = 0, HR_ODD = 1, HR_FULL = 2 } hr_parity;
+
+typedef enum {
+    HR_OP_HOP = 0,       /* out_p = D_{p,1-p} in = -1/2 H_{p,1-p} in  (in on parity 1-p) */
+    HR_OP_SCHUR = 1,     /* out_e = Mhat in_e           (out_parity must be HR_EVEN)   */
+    HR_OP_SCHUR_DAG = 2, /* out_e = Mhat^+ in_e                                       */
+    HR_OP_NORMAL = 3     /* out_e = Mhat^+ Mhat in_e                                  */
+} hr_op;
+
+typedef struct { int dims[4]; } hr_lattice; /* (T, L1, L2, L3) */
+
+typedef struct hr_ctx hr_ctx;
+
+/* ---------------------------------------------------------------------- */
+/* context                                                                  */
+/* ---------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`: allocates its small device
+ * scratch (reduction partials, solver scalars, status word; < 4 MB) once.
+ * *ctx receives the handle; HR_ERR_CUDA if the device cannot be used. */
+hr_status hr_ctx_create(hr_ctx **ctx, int device);
+hr_status hr_ctx_destroy(hr_ctx *ctx);
+/* Message of the last failed call on this context ("" if none). Never NULL. */
+const char *hr_last_error(const hr_ctx *ctx);
+/* Library version string. */
+const char *hr_version(void);
+
+/* m0 = 1/(2 kappa) - 4, i.e. kappa = 1/(8 + 2 m0). */
+double hr_kappa_to_m0(double kappa);
+double hr_m0_to_kappa(double m0);
+
+/* ---------------------------------------------------------------------- */
+/* sizes and layout conversion                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of a packed gauge field (all 4V links, both parities); 0 if invalid. */
+size_t hr_gauge_packed_bytes(hr_lattice lat, hr_rep rep, hr_prec prec);
+/* Bytes of a packed spinor field: one parity (V_h sites) times n_rhs
+ * right-hand sides (parity = HR_EVEN/HR_ODD), or both halves (HR_FULL). */
+size_t hr_spinor_packed_bytes(hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity parity, int n_rhs);
+
+/* canonical gauge (device, double[4][V][4]) -> packed (device).  For HR_ADJ_MAT
+ * the 3x3 adjoint matrices are built on the GPU from the quaternions. */
+hr_status hr_gauge_pack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec,
+                        const double *canonical, void *packed, hr_stream stream);
+
+/* canonical spinor(s) (device, double[n_rhs][V][4][nc][2]) -> packed sites of
+ * `parity` (HR_FULL: both halves).  n_rhs > 1 gives the multi-RHS layout. */
+hr_status hr_spinor_pack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity parity,
+                         int n_rhs, const double *canonical, void *packed, hr_stream stream);
+/* packed -> canonical; writes only the sites of `parity` (all for HR_FULL). */
+hr_status hr_spinor_unpack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity parity,
+                           int n_rhs, const void *packed, double *canonical, hr_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* operators                                                               */
+/* ---------------------------------------------------------------------- */
+
+/* Work bytes needed by hr_dirac_eo (op) / hr_dirac_apply for n_rhs vectors. */
+size_t hr_dirac_workspace_bytes(hr_lattice lat, hr_rep rep, hr_prec prec, hr_op op, int n_rhs);
+
+/* Full operator (Sec. 2.1): out = D in on all V sites; in/out are full packed
+ * spinors (HR_FULL layout), gauge is packed with the same rep and prec. */
+hr_status hr_dirac_apply(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, hr_prec prec,
+                         const void *gauge, const void *in, void *out, hr_stream stream);
+
+/* Even-odd operators (Sec. 2.1).  HR_OP_HOP: out (parity out_parity) =
+ * -1/2 H in (in has the other parity); the SCHUR ops take and return even
+ * vectors and need `work` of hr_dirac_workspace_bytes (odd temporaries).
+ * n_rhs >= 1 vectors in the multi-RHS layout share each link load. */
+hr_status hr_dirac_eo(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, hr_prec prec,
+                      hr_parity out_parity, hr_op op, int n_rhs, const void *gauge, const void *in,
+                      void *out, void *work, size_t work_bytes, hr_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* solvers                                                                 */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    double tol;            /* stop when |b - A x| / |b| <= tol (true residual, FP64) */
+    int maxiter;           /* cap on operator applications of A = Mhat^+ Mhat        */
+    hr_prec inner_prec;    /* HR_F64: plain FP64 CG; HR_F32/HR_F16: mixed precision    */
+    double reliable_delta; /* mixed precision: reliable update when |r| < delta max|r|  */
+    int n_rhs;             /* independent right-hand sides solved together (>= 1)      */
+    int x0_is_guess;       /* 1: x holds an initial guess; 0: start from x = 0          */
+    int check_every;       /* host convergence check interval in iterations (0: auto) */
+} hr_solver_opts;
+
+typedef struct {
+    int iters;                 /* CG iterations (applications of A), max over RHS     */
+    int n_reliable_updates;    /* FP64 residual recomputations                        */
+    double true_rel_residual;  /* |b - A x| / |b| recomputed in FP64, max over RHS    */
+    double seconds;            /* wall time of the solve on the stream                */
+} hr_solve_info;
+
+/* Default options: tol 1e-10, maxiter 20000, FP64, delta 0.1, 1 RHS. */
+hr_solver_opts hr_solver_default_opts(void);
+
+/* Work bytes for hr_cg_solve with these options. */
+size_t hr_cg_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *opts);
+
+/* Solve Mhat^+ Mhat x = b on even sites by CG (Sec. 1 "inverters"; the
+ * even-odd preconditioned operator of Sec. 2.1).  gauge: packed HR_F64 gauge
+ * of `rep`; b, x: packed HR_F64 even spinors (n_rhs of them).  Low-precision
+ * gauge copies for the mixed solver are made inside `work`.  Synchronises the
+ * stream before returning (it reads the residuals); info may be NULL.
+ * Returns HR_ERR_NOT_CONVERGED if maxiter is reached (x = last iterate). */
+hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep,
+                      const hr_solver_opts *opts, const void *gauge, const void *b, void *x,
+                      hr_solve_info *info, void *work, size_t work_bytes, hr_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* link derivatives                                                         */
+/* ---------------------------------------------------------------------- */
+
+/* force[mu][x][a] += beta * d Re<a_f, H b_f> / d w_a  for the variation
+ * U_mu(x) -> exp(i w.s/2) U_mu(x) (HMC fermion force, fundamental links).
+ * a_f, b_f: full packed FP64 fundamental spinors; force: device double[4][V][3]. */
+hr_status hr_force(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *a_full,
+                   const void *b_full, double beta, double *force, hr_stream stream);
+
+/* grad[mu][x][k] += beta * d Re<a_f, H b_f> / d q_k for the quaternion
+ * components q_k of U_mu(x) (U = sum_k q_k E_k, E_0 = 1, E_k = i s_k).
+ * grad: device double[4][V][4]. */
+hr_status hr_link_grad(hr_ctx *ctx, hr_lattice lat, const void *a_full, const void *b_full,
+                       double beta, double *grad, hr_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* vector utilities on packed FP64 spinors (n vectors of one parity)        */
+/* ---------------------------------------------------------------------- */
+
+/* *result (host) = sum |v|^2 over the packed even/odd FP64 field (n_rhs = 1).
+ * Synchronises the stream. */
+hr_status hr_norm2(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *v, double *result,
+                   hr_stream stream);
+/* y = a*x + y on packed FP64 fields of one parity. */
+hr_status hr_axpy(hr_ctx *ctx, hr_lattice lat, hr_rep rep, double a, const void *x, void *y,
+                  hr_stream stream);
+/* v = g5 v on a packed FP64 field of one parity (in place). */
+hr_status hr_gamma5(hr_ctx *ctx, hr_lattice lat, hr_rep rep, void *v, hr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HIREP_GB300_H */

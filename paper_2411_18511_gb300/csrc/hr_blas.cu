@@ -1,0 +1,370 @@
+// hr_blas.cu -- fused vector kernels of the CG solvers on packed spinor fields.
+//
+// Every kernel works site by site on the packed AoSoA layout (one thread per
+// virtual site, grid-stride), so each spinor is read and written exactly once
+// per call, and reductions are fused into the pass that produces the vector:
+//   xr      : x += alpha p, r -= alpha q, |r|^2   (one pass, 4 reads + 2 writes)
+//   p       : p = r + beta p
+//   residual: r = b - Ax, |r|^2                   (reliable update / final check)
+//   accum   : x_hi += x_lo, x_lo = 0              (mixed precision)
+//   convert : precision change between packed layouts
+// Per-RHS scalars (alpha, beta, ...) are read from the context's device scalar
+// block, so a solver iteration needs no host round trip.  Reductions are FP64,
+// deterministic (warp shuffle, block, then last-block sum in block order).
+#include "hr_host.h"
+
+using namespace hr;
+
+namespace {
+
+constexpr int kBS = 256;
+
+template <int P> using RT = typename PrecTraits<P>::T;
+
+template <class A, class B> struct Wider { using T = A; };
+template <> struct Wider<float, double> { using T = double; };
+
+template <int NC, class T>
+__device__ __forceinline__ double site_norm2(const cpx<T> (&v)[4][NC])
+{
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s += (double)v[a][c].re * (double)v[a][c].re + (double)v[a][c].im * (double)v[a][c].im;
+    return s;
+}
+
+template <int NC, int P>
+__global__ void __launch_bounds__(kBS) k_norm2(Geom g, const void *v, RedSlot red, double *scal, int fin)
+{
+    using T = RT<P>;
+    const int nv = g.vh << g.lrhs;
+    double acc = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<T> a[4][NC];
+        load_spinor<NC, P>(v, g.nblk_s, j, a);
+        acc += site_norm2<NC>(a);
+    }
+    __shared__ double smem[32 * 32];
+    __shared__ double sums[32];
+    if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
+}
+
+// x += alpha p ; r -= alpha q ; |r|^2 -> fin (kFinBeta / kFinBetaMixed)
+template <int NC, int PX, int PP, int PR, int PQ>
+__global__ void __launch_bounds__(kBS) k_xr(Geom g, void *x, const void *p, void *r, const void *q, RedSlot red,
+                                            double *scal, int fin)
+{
+    using T = typename Wider<RT<PX>, RT<PR>>::T;
+    if (sc(scal, S_FLAGS, F_DONE) != 0.0) return;
+    const int nv = g.vh << g.lrhs;
+    double acc = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        const T al = (T)sc(scal, S_ALPHA, j & (g.nrhs - 1));
+        cpx<T> xv[4][NC], pv[4][NC], rv[4][NC], qv[4][NC];
+        load_spinor<NC, PX>(x, g.nblk_s, j, xv);
+        load_spinor<NC, PP>(p, g.nblk_s, j, pv);
+        load_spinor<NC, PR>(r, g.nblk_s, j, rv);
+        load_spinor<NC, PQ>(q, g.nblk_s, j, qv);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                xv[a][c].re += al * pv[a][c].re;
+                xv[a][c].im += al * pv[a][c].im;
+                rv[a][c].re -= al * qv[a][c].re;
+                rv[a][c].im -= al * qv[a][c].im;
+            }
+        store_spinor<NC, PX>(x, g.nblk_s, j, xv);
+        store_spinor<NC, PR>(r, g.nblk_s, j, rv);
+        acc += site_norm2<NC>(rv);
+    }
+    __shared__ double smem[32 * 32];
+    __shared__ double sums[32];
+    if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
+}
+
+// p = r + beta p
+template <int NC, int PP, int PR>
+__global__ void __launch_bounds__(kBS) k_p(Geom g, void *p, const void *r, const double *scal)
+{
+    using T = typename Wider<RT<PP>, RT<PR>>::T;
+    if (sc((double *)scal, S_FLAGS, F_DONE) != 0.0) return;
+    const int nv = g.vh << g.lrhs;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        const T be = (T)scal[S_BETA * kMaxRhsSlots + (j & (g.nrhs - 1))];
+        cpx<T> pv[4][NC], rv[4][NC];
+        load_spinor<NC, PP>(p, g.nblk_s, j, pv);
+        load_spinor<NC, PR>(r, g.nblk_s, j, rv);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) pv[a][c] = {rv[a][c].re + be * pv[a][c].re, rv[a][c].im + be * pv[a][c].im};
+        store_spinor<NC, PP>(p, g.nblk_s, j, pv);
+    }
+}
+
+template <int NC, int PS, int PD>
+__global__ void __launch_bounds__(kBS) k_convert(Geom g, const void *src, void *dst, const double *gate)
+{
+    using T = typename Wider<RT<PS>, RT<PD>>::T;
+    if (gate && *gate == 0.0) return;
+    const int nv = g.vh << g.lrhs;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<T> v[4][NC];
+        load_spinor<NC, PS>(src, g.nblk_s, j, v);
+        store_spinor<NC, PD>(dst, g.nblk_s, j, v);
+    }
+}
+
+// r = b - ax ; |r|^2 -> fin ; optionally r_lo = r in precision PL
+template <int NC, int PL>
+__global__ void __launch_bounds__(kBS) k_residual(Geom g, const void *b, const void *ax, void *r, RedSlot red,
+                                                  double *scal, int fin, const double *gate, void *r_lo)
+{
+    if (gate && *gate == 0.0) return;
+    const int nv = g.vh << g.lrhs;
+    double acc = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<double> bv[4][NC], av[4][NC];
+        load_spinor<NC, kF64>(b, g.nblk_s, j, bv);
+        load_spinor<NC, kF64>(ax, g.nblk_s, j, av);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) bv[a][c] = csub(bv[a][c], av[a][c]);
+        store_spinor<NC, kF64>(r, g.nblk_s, j, bv);
+        if (PL != kF64 && r_lo) store_spinor<NC, PL>(r_lo, g.nblk_s, j, bv);
+        acc += site_norm2<NC>(bv);
+    }
+    __shared__ double smem[32 * 32];
+    __shared__ double sums[32];
+    if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
+}
+
+// x_hi += x_lo ; x_lo = 0
+template <int NC, int PL>
+__global__ void __launch_bounds__(kBS) k_accum(Geom g, void *xhi, void *xlo, const double *gate)
+{
+    if (gate && *gate == 0.0) return;
+    const int nv = g.vh << g.lrhs;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<double> h[4][NC], l[4][NC];
+        load_spinor<NC, kF64>(xhi, g.nblk_s, j, h);
+        load_spinor<NC, PL>(xlo, g.nblk_s, j, l);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                h[a][c] = cadd(h[a][c], l[a][c]);
+                l[a][c] = {0.0, 0.0};
+            }
+        store_spinor<NC, kF64>(xhi, g.nblk_s, j, h);
+        store_spinor<NC, PL>(xlo, g.nblk_s, j, l);
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kBS) k_axpy(Geom g, double a, const void *x, void *y)
+{
+    const int nv = g.vh << g.lrhs;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<double> xv[4][NC], yv[4][NC];
+        load_spinor<NC, kF64>(x, g.nblk_s, j, xv);
+        load_spinor<NC, kF64>(y, g.nblk_s, j, yv);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) yv[s][c] = {yv[s][c].re + a * xv[s][c].re, yv[s][c].im + a * xv[s][c].im};
+        store_spinor<NC, kF64>(y, g.nblk_s, j, yv);
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kBS) k_gamma5(Geom g, void *v)
+{
+    const int nv = g.vh << g.lrhs;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<double> a[4][NC];
+        load_spinor<NC, kF64>(v, g.nblk_s, j, a);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            a[0][c] = {-a[0][c].re, -a[0][c].im};
+            a[1][c] = {-a[1][c].re, -a[1][c].im};
+        }
+        store_spinor<NC, kF64>(v, g.nblk_s, j, a);
+    }
+}
+
+inline int grid_cap(hr_ctx *ctx, const Geom &g)
+{
+    long long nv = (long long)g.vh << g.lrhs;
+    int cap = ctx->sm_count > 0 ? ctx->sm_count * 8 : 1024;
+    if (cap > kMaxBlocks) cap = kMaxBlocks;
+    return grid_for(nv, kBS, cap);
+}
+
+#define HR_DISPATCH_NC(rep, CALL)          \
+    do {                                   \
+        if (rep_nc(rep) == 2) {            \
+            constexpr int NC = 2;          \
+            CALL;                          \
+        } else {                           \
+            constexpr int NC = 3;          \
+            CALL;                          \
+        }                                  \
+    } while (0)
+
+#define HR_DISPATCH_P(prec, P, CALL)                       \
+    do {                                                   \
+        if ((prec) == kF64) { constexpr int P = kF64; CALL; } \
+        else if ((prec) == kF32) { constexpr int P = kF32; CALL; } \
+        else { constexpr int P = kF16; CALL; }             \
+    } while (0)
+
+} // namespace
+
+namespace hr {
+
+hr_status blas_norm2(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *v, int fin, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    RedSlot red = red_slot(ctx, C_NORM);
+    HR_DISPATCH_NC(rep, HR_DISPATCH_P(prec, P, (k_norm2<NC, P><<<grid, kBS, 0, s>>>(g, v, red, ctx->d_scal, fin))));
+    return check_launch(ctx, "norm2");
+}
+
+hr_status blas_xr(hr_ctx *ctx, const Geom &g, int rep, int px, int pp, int pr, int pq, void *x, const void *p, void *r,
+                  const void *q, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    RedSlot red = red_slot(ctx, C_XR);
+    if (px == kF64 && pp == kF64 && pr == kF64 && pq == kF64) {
+        HR_DISPATCH_NC(rep, (k_xr<NC, kF64, kF64, kF64, kF64><<<grid, kBS, 0, s>>>(g, x, p, r, q, red, ctx->d_scal, kFinBeta)));
+    } else if (px == kF32 && pp == kF32 && pr == kF32 && pq == kF32) {
+        HR_DISPATCH_NC(rep, (k_xr<NC, kF32, kF32, kF32, kF32><<<grid, kBS, 0, s>>>(g, x, p, r, q, red, ctx->d_scal, kFinBetaMixed)));
+    } else if (px == kF32 && pp == kF16 && pr == kF16 && pq == kF16) {
+        HR_DISPATCH_NC(rep, (k_xr<NC, kF32, kF16, kF16, kF16><<<grid, kBS, 0, s>>>(g, x, p, r, q, red, ctx->d_scal, kFinBetaMixed)));
+    } else {
+        return set_error(ctx, HR_ERR_UNSUPPORTED, "xr precision combination");
+    }
+    return check_launch(ctx, "xr update");
+}
+
+hr_status blas_p(hr_ctx *ctx, const Geom &g, int rep, int pp, int pr, void *p, const void *r, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    if (pp != pr) return set_error(ctx, HR_ERR_UNSUPPORTED, "p update precision combination");
+    HR_DISPATCH_NC(rep, HR_DISPATCH_P(pp, P, (k_p<NC, P, P><<<grid, kBS, 0, s>>>(g, p, r, ctx->d_scal))));
+    return check_launch(ctx, "p update");
+}
+
+hr_status blas_convert(hr_ctx *ctx, const Geom &g, int rep, int psrc, int pdst, const void *src, void *dst,
+                       const double *gate, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    if (psrc == kF64) {
+        HR_DISPATCH_NC(rep, HR_DISPATCH_P(pdst, P, (k_convert<NC, kF64, P><<<grid, kBS, 0, s>>>(g, src, dst, gate))));
+    } else if (pdst == kF64) {
+        HR_DISPATCH_NC(rep, HR_DISPATCH_P(psrc, P, (k_convert<NC, P, kF64><<<grid, kBS, 0, s>>>(g, src, dst, gate))));
+    } else {
+        return set_error(ctx, HR_ERR_UNSUPPORTED, "convert precision combination");
+    }
+    return check_launch(ctx, "convert");
+}
+
+hr_status blas_residual(hr_ctx *ctx, const Geom &g, int rep, const void *b, const void *ax, void *r, int fin,
+                        const double *gate, int plo, void *r_lo, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    RedSlot red = red_slot(ctx, C_RES);
+    if (!r_lo) plo = kF64;
+    HR_DISPATCH_NC(rep, HR_DISPATCH_P(plo, P, (k_residual<NC, P><<<grid, kBS, 0, s>>>(g, b, ax, r, red, ctx->d_scal, fin, gate, r_lo))));
+    return check_launch(ctx, "residual");
+}
+
+hr_status blas_accum(hr_ctx *ctx, const Geom &g, int rep, int plo, void *xhi, void *xlo, const double *gate,
+                     cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    if (plo == kF32) {
+        HR_DISPATCH_NC(rep, (k_accum<NC, kF32><<<grid, kBS, 0, s>>>(g, xhi, xlo, gate)));
+    } else {
+        return set_error(ctx, HR_ERR_UNSUPPORTED, "accumulate precision");
+    }
+    return check_launch(ctx, "accumulate");
+}
+
+hr_status blas_axpy(hr_ctx *ctx, const Geom &g, int rep, double a, const void *x, void *y, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    HR_DISPATCH_NC(rep, (k_axpy<NC><<<grid, kBS, 0, s>>>(g, a, x, y)));
+    return check_launch(ctx, "axpy");
+}
+
+hr_status blas_gamma5(hr_ctx *ctx, const Geom &g, int rep, void *v, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    HR_DISPATCH_NC(rep, (k_gamma5<NC><<<grid, kBS, 0, s>>>(g, v)));
+    return check_launch(ctx, "gamma5");
+}
+
+hr_status blas_zero(hr_ctx *ctx, const Geom &g, int rep, int prec, void *v, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(v, 0, spinor_half_bytes(g, rep, prec), s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+    return HR_OK;
+}
+
+hr_status blas_copy(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *src, void *dst, cudaStream_t s)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, src, spinor_half_bytes(g, rep, prec), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+    return HR_OK;
+}
+
+} // namespace hr
+
+extern "C" {
+
+hr_status hr_norm2(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *v, double *result, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    if (!v || !result) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    Geom g = make_geom(lat, 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = blas_norm2(ctx, g, rep, kF64, v, kFinStore, s);
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_scal, ctx->d_scal + S_OUT * kMaxRhsSlots, sizeof(double),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "norm2 readback: %s", cudaGetErrorString(e));
+    *result = ctx->h_scal[0];
+    return HR_OK;
+}
+
+hr_status hr_axpy(hr_ctx *ctx, hr_lattice lat, hr_rep rep, double a, const void *x, void *y, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    if (!x || !y) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    return blas_axpy(ctx, make_geom(lat, 1), rep, a, x, y, (cudaStream_t)stream);
+}
+
+hr_status hr_gamma5(hr_ctx *ctx, hr_lattice lat, hr_rep rep, void *v, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    if (!v) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    return blas_gamma5(ctx, make_geom(lat, 1), rep, v, (cudaStream_t)stream);
+}
+
+} // extern "C"

@@ -1,0 +1,327 @@
+// hr_hop.cu -- the even-odd Wilson hopping kernel and the operators built on it:
+// D_eo / D_oe, the Schur complement Mhat, Mhat^+, Mhat^+ Mhat and the full D.
+//
+// One thread per output (virtual) site.  For each of the 8 directions the
+// thread loads the neighbour spinor (128-bit loads, AoSoA blocks of 32 sites),
+// projects it to a half spinor with (1 -/+ g_mu), multiplies both spin
+// components by the link rebuilt in registers from its quaternion (or by the
+// stored 3x3 adjoint matrix), and adds the two rebuilt spin pairs into the
+// accumulator.  The periodic wrap is resolved in the neighbour index; there is
+// no halo.  The epilogue forms out = alpha*aux + beta*[g5] H [g5] in and, when
+// asked, reduces |out|^2 per right-hand side (fused CG reduction).
+#include "hr_host.h"
+
+using namespace hr;
+
+namespace {
+
+struct HopArgs {
+    Geom g;
+    int p;
+    const void *gauge;
+    const void *in;
+    const void *aux;
+    void *out;
+    double alpha, beta;
+    int g5_in, g5_out;
+    int fin;
+    RedSlot red;
+    double *scal;
+    const double *gate;
+    const double *done; // skip all work when *done != 0 (solver converged)
+};
+
+template <int MU, bool FWD, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int link_par, int j_nb, bool neg_upper,
+                                         cpx<T> (&acc)[4][NC])
+{
+    cpx<T> s[4][NC];
+    load_spinor<NC, PREC>(a.in, a.g.nblk_s, j_nb, s);
+    if (neg_upper) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            s[0][c] = {-s[0][c].re, -s[0][c].im};
+            s[1][c] = {-s[1][c].re, -s[1][c].im};
+        }
+    }
+    cpx<T> h[2][NC], r[2][NC];
+    spin_project<MU, FWD>(s, h);
+    if constexpr (REP == kRepFund) {
+        T q[4];
+        load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+        su2_mul<!FWD>(q, h[0], r[0]);
+        su2_mul<!FWD>(q, h[1], r[1]);
+    } else {
+        T R[3][3];
+        if constexpr (REP == kRepAdj) {
+            T q[4];
+            load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+            quat_to_adj(q, R);
+        } else {
+            load_mat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, R);
+        }
+        so3_mul<!FWD>(R, h[0], r[0]);
+        so3_mul<!FWD>(R, h[1], r[1]);
+    }
+    spin_accumulate<MU, FWD>(acc, r);
+}
+
+template <int MU, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void hop_dir(const HopArgs &a, int i, int rr, const SiteNb &nb, cpx<T> (&acc)[4][NC])
+{
+    const int l = a.g.lrhs;
+    // forward: (1 - g_mu) U_mu(x) psi(x + mu); the link sits at x (parity p)
+    hop_term<MU, true, REP, PREC>(a, i, a.p, (nb.fwd[MU] << l) + rr, a.g5_in != 0, acc);
+    // backward: (1 + g_mu) U_mu(x - mu)^+ psi(x - mu); the link sits at x - mu (parity 1-p)
+    hop_term<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, a.g5_in != 0, acc);
+}
+
+template <int REP, int PREC>
+__global__ void __launch_bounds__(256) k_hop(HopArgs a)
+{
+    using T = typename PrecTraits<PREC>::T;
+    constexpr int NC = RepTraits<REP>::NC;
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) {
+        // nothing to do; a reducing launch still has to leave the counter clean,
+        // which it does because no block reaches the reduction
+        return;
+    }
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    double red = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        cpx<T> acc[4][NC];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[s][c] = {T(0), T(0)};
+        hop_dir<0, REP, PREC>(a, i, rr, nb, acc);
+        hop_dir<1, REP, PREC>(a, i, rr, nb, acc);
+        hop_dir<2, REP, PREC>(a, i, rr, nb, acc);
+        hop_dir<3, REP, PREC>(a, i, rr, nb, acc);
+        // epilogue: out = alpha * aux + beta * g5^{g5_out} acc
+        const T be = (T)a.beta;
+        const T bu = a.g5_out ? -be : be;
+        cpx<T> o[4][NC];
+        if (a.aux) {
+            load_spinor<NC, PREC>(a.aux, g.nblk_s, j, o);
+            const T al = (T)a.alpha;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    T b = s < 2 ? bu : be;
+                    o[s][c] = {al * o[s][c].re + b * acc[s][c].re, al * o[s][c].im + b * acc[s][c].im};
+                }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    T b = s < 2 ? bu : be;
+                    o[s][c] = {b * acc[s][c].re, b * acc[s][c].im};
+                }
+        }
+        store_spinor<NC, PREC>(a.out, g.nblk_s, j, o);
+        if (a.fin) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    red += (double)o[s][c].re * (double)o[s][c].re + (double)o[s][c].im * (double)o[s][c].im;
+        }
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+template <int REP, int PREC>
+hr_status launch_t(hr_ctx *ctx, const Geom &g, const HopArgs &a, cudaStream_t s)
+{
+    const long long nv = (long long)g.vh << g.lrhs;
+    int bs = 128;
+    auto it = ctx->tuned_block.find("hop");
+    if (it != ctx->tuned_block.end()) bs = it->second;
+    // non-reducing launches cover all sites; reducing ones are capped so the
+    // per-block partials fit the context's scratch
+    int cap = a.fin ? kMaxBlocks : (1 << 30);
+    int grid = grid_for(nv, bs, cap);
+    k_hop<REP, PREC><<<grid, bs, 0, s>>>(a);
+    return check_launch(ctx, "hop kernel");
+}
+
+} // namespace
+
+namespace hr {
+
+hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, cudaStream_t s)
+{
+    HopArgs a;
+    a.g = g;
+    a.p = L.p;
+    a.gauge = L.gauge;
+    a.in = L.in;
+    a.aux = L.aux;
+    a.out = L.out;
+    a.alpha = L.alpha;
+    a.beta = L.beta;
+    a.g5_in = L.g5_in;
+    a.g5_out = L.g5_out;
+    a.fin = L.fin;
+    a.red = red_slot(ctx, C_HOP);
+    a.scal = ctx->d_scal;
+    a.gate = L.gate;
+    a.done = L.done;
+    switch (rep * 3 + prec) {
+    case 0: return launch_t<kRepFund, kF64>(ctx, g, a, s);
+    case 1: return launch_t<kRepFund, kF32>(ctx, g, a, s);
+    case 2: return launch_t<kRepFund, kF16>(ctx, g, a, s);
+    case 3: return launch_t<kRepAdj, kF64>(ctx, g, a, s);
+    case 4: return launch_t<kRepAdj, kF32>(ctx, g, a, s);
+    case 5: return launch_t<kRepAdj, kF16>(ctx, g, a, s);
+    case 6: return launch_t<kRepAdjMat, kF64>(ctx, g, a, s);
+    case 7: return launch_t<kRepAdjMat, kF32>(ctx, g, a, s);
+    case 8: return launch_t<kRepAdjMat, kF16>(ctx, g, a, s);
+    }
+    return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+}
+
+// Even-site operators from two hops each:
+//   Mhat    : t_o = H_oe in;        out = A in - c H_eo t_o
+//   Mhat^+  : t_o = H_oe g5 in;     out = A in - c g5 H_eo t_o
+//   normal  : u = Mhat in (|u|^2 reduced with fin_schur), out = Mhat^+ u
+// with A = 4 + m0 and c = 1 / (4 A).
+hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, int op, const void *gauge,
+                      const void *in, void *out, void *work_odd, void *work_even, int fin_schur, const double *gate,
+                      const double *done, cudaStream_t s)
+{
+    const double A = 4.0 + m0, c = 1.0 / (4.0 * A);
+    hr_status st;
+    HopLaunch L{};
+    L.gauge = gauge;
+    L.gate = gate;
+    L.done = done;
+    auto schur = [&](const void *src, void *dst, bool dag, int fin) -> hr_status {
+        HopLaunch h1 = L;
+        h1.p = 1;
+        h1.in = src;
+        h1.aux = nullptr;
+        h1.out = work_odd;
+        h1.alpha = 0.0;
+        h1.beta = 1.0;
+        h1.g5_in = dag ? 1 : 0;
+        h1.g5_out = 0;
+        h1.fin = kFinNone;
+        hr_status e = launch_hop(ctx, g, rep, prec, h1, s);
+        if (e) return e;
+        HopLaunch h2 = L;
+        h2.p = 0;
+        h2.in = work_odd;
+        h2.aux = src;
+        h2.out = dst;
+        h2.alpha = A;
+        h2.beta = -c;
+        h2.g5_in = 0;
+        h2.g5_out = dag ? 1 : 0;
+        h2.fin = fin;
+        return launch_hop(ctx, g, rep, prec, h2, s);
+    };
+    switch (op) {
+    case HR_OP_SCHUR: return schur(in, out, false, fin_schur);
+    case HR_OP_SCHUR_DAG: return schur(in, out, true, fin_schur);
+    case HR_OP_NORMAL:
+        st = schur(in, work_even, false, fin_schur);
+        if (st) return st;
+        return schur(work_even, out, true, kFinNone);
+    }
+    return set_error(ctx, HR_ERR_INVALID_ARG, "bad op %d", op);
+}
+
+} // namespace hr
+
+extern "C" {
+
+size_t hr_dirac_workspace_bytes(hr_lattice lat, hr_rep rep, hr_prec prec, hr_op op, int n_rhs)
+{
+    if (!valid_rep(rep) || !valid_prec(prec) || n_rhs < 1) return 0;
+    size_t half = hr_spinor_packed_bytes(lat, rep, prec, HR_EVEN, n_rhs);
+    switch (op) {
+    case HR_OP_HOP: return 0;
+    case HR_OP_SCHUR:
+    case HR_OP_SCHUR_DAG: return half;
+    case HR_OP_NORMAL: return 2 * half;
+    }
+    return 0;
+}
+
+hr_status hr_dirac_eo(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, hr_prec prec, hr_parity out_parity,
+                      hr_op op, int n_rhs, const void *gauge, const void *in, void *out, void *work, size_t work_bytes,
+                      hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+    hr_status st = validate_lattice(ctx, lat, n_rhs);
+    if (st) return st;
+    if (!gauge || !in || !out) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+    if (in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "in and out must not alias");
+    if (!(4.0 + m0 != 0.0)) return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero");
+    Geom g = make_geom(lat, n_rhs);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op == HR_OP_HOP) {
+        if (out_parity != HR_EVEN && out_parity != HR_ODD)
+            return set_error(ctx, HR_ERR_INVALID_ARG, "HR_OP_HOP needs out_parity HR_EVEN or HR_ODD");
+        HopLaunch L{};
+        L.p = out_parity;
+        L.gauge = gauge;
+        L.in = in;
+        L.out = out;
+        L.beta = -0.5;
+        return launch_hop(ctx, g, rep, prec, L, s);
+    }
+    if (op != HR_OP_SCHUR && op != HR_OP_SCHUR_DAG && op != HR_OP_NORMAL)
+        return set_error(ctx, HR_ERR_INVALID_ARG, "bad op %d", (int)op);
+    if (out_parity != HR_EVEN) return set_error(ctx, HR_ERR_INVALID_ARG, "Schur operators act on even sites");
+    size_t need = hr_dirac_workspace_bytes(lat, rep, prec, op, n_rhs);
+    if (!work || work_bytes < need)
+        return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, work_bytes);
+    size_t half = spinor_half_bytes(g, rep, prec);
+    void *wo = work;
+    void *we = (op == HR_OP_NORMAL) ? (char *)work + half : nullptr;
+    return apply_eo_op(ctx, g, m0, rep, prec, op, gauge, in, out, wo, we, kFinNone, nullptr, nullptr, s);
+}
+
+hr_status hr_dirac_apply(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, hr_prec prec, const void *gauge,
+                         const void *in, void *out, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    if (!gauge || !in || !out) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+    if (in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "in and out must not alias");
+    Geom g = make_geom(lat, 1);
+    size_t half = spinor_half_bytes(g, rep, prec);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int p = 0; p < 2; ++p) {
+        HopLaunch L{};
+        L.p = p;
+        L.gauge = gauge;
+        L.in = (const char *)in + (p == 0 ? half : 0);   // the other parity
+        L.aux = (const char *)in + (p == 0 ? 0 : half);  // same parity
+        L.out = (char *)out + (p == 0 ? 0 : half);
+        L.alpha = 4.0 + m0;
+        L.beta = -0.5;
+        st = launch_hop(ctx, g, rep, prec, L, s);
+        if (st) return st;
+    }
+    return HR_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,107 @@
+// hr_host.h -- host-side internals of libhirep_gb300: the context, error
+// reporting, argument validation and launch helpers shared by the .cu files.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "hirep_gb300.h"
+#include "hr_internal.cuh"
+
+// Device scratch owned by a context (allocated once in hr_ctx_create).
+namespace hr {
+constexpr int kMaxBlocks = 4096;      // cap on blocks of any reducing launch
+constexpr int kMaxRhs = 32;
+constexpr int kNumCounters = 64;
+constexpr int kScalDoubles = 64 * kMaxRhs;
+
+} // namespace hr
+
+struct hr_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    double *d_partials = nullptr;  // kMaxBlocks * kMaxRhs
+    unsigned *d_counters = nullptr;
+    double *d_scal = nullptr;      // kScalDoubles
+    double *h_scal = nullptr;      // pinned mirror
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::map<std::string, int> tuned_block; // autotuner: key -> threads per block
+    std::string tune_cache_path;
+    bool autotune = false;
+};
+
+namespace hr {
+
+hr_status set_error(hr_ctx *ctx, hr_status st, const char *fmt, ...);
+hr_status check_launch(hr_ctx *ctx, const char *what);
+hr_status validate_lattice(hr_ctx *ctx, const hr_lattice &lat, int nrhs);
+bool valid_rep(int rep);
+bool valid_prec(int prec);
+inline int rep_nc(int rep) { return rep == HR_FUND ? 2 : 3; }
+
+size_t spinor_half_bytes(const Geom &g, int rep, int prec);
+size_t gauge_bytes(const Geom &g, int rep, int prec);
+
+inline RedSlot red_slot(hr_ctx *ctx, int counter)
+{
+    RedSlot s;
+    s.partials = ctx->d_partials;
+    s.counter = ctx->d_counters + counter;
+    return s;
+}
+
+inline int grid_for(long long n, int block, int cap)
+{
+    long long b = (n + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// counters used by the reducing kernels (each reduction site has its own)
+enum Counter { C_HOP = 0, C_XR = 1, C_RES = 2, C_NORM = 3, C_DOT = 4, C_MISC = 5, C_BATCH = 16 };
+
+// ---- hop launches (hr_hop.cu) ----
+struct HopLaunch {
+    int p;                 // output parity
+    const void *gauge;
+    const void *in;
+    const void *aux;
+    void *out;
+    double alpha, beta;
+    int g5_in, g5_out;
+    int fin;               // FinishMode of the |out|^2 reduction (kFinNone: no reduction)
+    const double *gate;    // skip the launch's work unless *gate != 0 (nullable)
+    const double *done;    // skip the launch's work when *done != 0 (nullable)
+};
+hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, cudaStream_t s);
+// out = op(in) on even sites, work = odd temporary (+ even temporary for NORMAL)
+hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, int op, const void *gauge,
+                      const void *in, void *out, void *work_odd, void *work_even, int fin_schur,
+                      const double *gate, const double *done, cudaStream_t s);
+
+// ---- BLAS launches (hr_blas.cu) ----
+hr_status blas_norm2(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *v, int fin, cudaStream_t s);
+hr_status blas_xr(hr_ctx *ctx, const Geom &g, int rep, int px, int pp, int pr, int pq, void *x, const void *p,
+                  void *r, const void *q, cudaStream_t s);
+hr_status blas_p(hr_ctx *ctx, const Geom &g, int rep, int pp, int pr, void *p, const void *r, cudaStream_t s);
+hr_status blas_convert(hr_ctx *ctx, const Geom &g, int rep, int psrc, int pdst, const void *src, void *dst,
+                       const double *gate, cudaStream_t s);
+// r = b - ax (FP64) with |r|^2 -> fin; also writes r in precision plo to r_lo when given
+hr_status blas_residual(hr_ctx *ctx, const Geom &g, int rep, const void *b, const void *ax, void *r, int fin,
+                        const double *gate, int plo, void *r_lo, cudaStream_t s);
+// packed FP64 gauge -> packed gauge of precision pdst (same rep)
+hr_status gauge_convert(hr_ctx *ctx, const Geom &g, int rep, int pdst, const void *src, void *dst, cudaStream_t s);
+hr_status blas_accum(hr_ctx *ctx, const Geom &g, int rep, int plo, void *xhi, void *xlo, const double *gate,
+                     cudaStream_t s);
+hr_status blas_axpy(hr_ctx *ctx, const Geom &g, int rep, double a, const void *x, void *y, cudaStream_t s);
+hr_status blas_gamma5(hr_ctx *ctx, const Geom &g, int rep, void *v, cudaStream_t s);
+hr_status blas_zero(hr_ctx *ctx, const Geom &g, int rep, int prec, void *v, cudaStream_t s);
+hr_status blas_copy(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *src, void *dst, cudaStream_t s);
+
+} // namespace hr

@@ -1,0 +1,523 @@
+// hr_internal.cuh -- shared device code of libhirep_gb300: lattice geometry,
+// packed field layouts, complex arithmetic and the spin/colour algebra of the
+// Wilson hopping term.
+//
+// Operator (arXiv:2411.18511 names the unimproved Wilson-Dirac operator in
+// Sec. 2.1 / Table 1 without writing it; this is the textbook form):
+//   (H psi)(x) = sum_mu (1-g_mu) U_mu(x) psi(x+mu) + (1+g_mu) U_mu(x-mu)^+ psi(x-mu)
+// in the chiral basis g_0 = [[0,1],[1,0]], g_k = [[0,-i s_k],[i s_k,0]].
+//
+// Packed layouts (device, opaque to callers)
+// ------------------------------------------
+// Sites of one parity are numbered by their even-odd index i = lex/2, where
+// lex = ((x0*L1 + x1)*L2 + x2)*L3 + x3; a multi-RHS field numbers "virtual
+// sites" j = i*N + r (r = right-hand side, N a power of two <= 32).  Fields are
+// array-of-structure-of-arrays in blocks of 32 virtual sites: one 16-byte
+// vector v of site j sits at vector index ((j/32)*NVEC + v)*32 + j%32, so a
+// warp reading one vector of 32 consecutive sites reads 512 contiguous bytes.
+//   spinor FP64: NVEC = 4*NC double2 (one complex each)
+//   spinor FP32: NVEC = 2*NC float4  (two complex each)
+//   spinor FP16: NVEC = NC   uint4   (four complex each, binary16), followed by
+//                one float scale per site (the site's max |component|)
+//   gauge (quaternion links): link (p, mu, i) in slot L = (p*4+mu)*nblk + i/32,
+//     FP64 two double2 at (L*2+v)*32 + i%32, FP32 one float4, FP16 one uint2
+//   gauge HR_ADJ_MAT: 9 reals R_ab at (L*9 + 3a+b)*32 + i%32
+// where nblk = ceil(V_h/32) for the gauge and ceil(V_h*N/32) for spinors.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hirep_gb300.h"
+
+namespace hr {
+
+constexpr int kRepFund = 0, kRepAdj = 1, kRepAdjMat = 2;
+constexpr int kF64 = 0, kF32 = 1, kF16 = 2;
+
+template <int REP> struct RepTraits { static constexpr int NC = (REP == kRepFund) ? 2 : 3; };
+
+// ---------------------------------------------------------------- geometry
+
+struct Geom {
+    int d[4];   // T, L1, L2, L3
+    int h3;     // L3 / 2
+    int vh;     // sites per parity
+    int nrhs;   // right-hand sides (power of two)
+    int lrhs;   // log2(nrhs)
+    int nblk_g; // 32-site blocks of the gauge (per parity and direction)
+    int nblk_s; // 32-virtual-site blocks of a spinor field of one parity
+};
+
+inline Geom make_geom(const hr_lattice &lat, int nrhs)
+{
+    Geom g;
+    for (int k = 0; k < 4; ++k) g.d[k] = lat.dims[k];
+    g.h3 = lat.dims[3] / 2;
+    long long v = (long long)lat.dims[0] * lat.dims[1] * lat.dims[2] * lat.dims[3];
+    g.vh = (int)(v / 2);
+    g.nrhs = nrhs;
+    int l = 0;
+    while ((1 << l) < nrhs) ++l;
+    g.lrhs = l;
+    g.nblk_g = (g.vh + 31) / 32;
+    g.nblk_s = (int)(((long long)g.vh * nrhs + 31) / 32);
+    return g;
+}
+
+// Coordinates and neighbours of the site with even-odd index i and parity p.
+struct SiteNb {
+    int fwd[4]; // even-odd index of x + mu (other parity)
+    int bwd[4]; // even-odd index of x - mu (other parity)
+};
+
+__device__ __forceinline__ void site_neighbours(const Geom &g, int i, int p, SiteNb &nb)
+{
+    const int h3 = g.h3;
+    int k = i % h3;
+    int row = i / h3;
+    int x2 = row % g.d[2];
+    int r1 = row / g.d[2];
+    int x1 = r1 % g.d[1];
+    int x0 = r1 / g.d[1];
+    int odd3 = (x0 + x1 + x2 + p) & 1; // x3 = 2k + odd3
+    // direction 3 (fastest): stays in the row, wraps within it
+    int base = row * h3;
+    nb.fwd[3] = odd3 ? (k + 1 == h3 ? base : i + 1) : i;
+    nb.bwd[3] = odd3 ? i : (k == 0 ? base + h3 - 1 : i - 1);
+    // directions 2, 1, 0: move whole rows
+    const int s2 = h3, s1 = g.d[2] * h3, s0 = g.d[1] * g.d[2] * h3;
+    nb.fwd[2] = (x2 + 1 == g.d[2]) ? i - (g.d[2] - 1) * s2 : i + s2;
+    nb.bwd[2] = (x2 == 0) ? i + (g.d[2] - 1) * s2 : i - s2;
+    nb.fwd[1] = (x1 + 1 == g.d[1]) ? i - (g.d[1] - 1) * s1 : i + s1;
+    nb.bwd[1] = (x1 == 0) ? i + (g.d[1] - 1) * s1 : i - s1;
+    nb.fwd[0] = (x0 + 1 == g.d[0]) ? i - (g.d[0] - 1) * s0 : i + s0;
+    nb.bwd[0] = (x0 == 0) ? i + (g.d[0] - 1) * s0 : i - s0;
+}
+
+// lexicographic index of the site with even-odd index i and parity p
+__device__ __forceinline__ long long eo_to_lex(const Geom &g, int i, int p)
+{
+    int k = i % g.h3;
+    int row = i / g.h3;
+    int x2 = row % g.d[2];
+    int r1 = row / g.d[2];
+    int x1 = r1 % g.d[1];
+    int x0 = r1 / g.d[1];
+    int odd3 = (x0 + x1 + x2 + p) & 1;
+    return (long long)row * g.d[3] + 2 * k + odd3;
+}
+
+// ---------------------------------------------------------------- complex
+
+template <class T> struct cpx {
+    T re, im;
+};
+
+template <class T> __device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <class T> __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+// a + i b, a - i b
+template <class T> __device__ __forceinline__ cpx<T> cadd_i(cpx<T> a, cpx<T> b) { return {a.re - b.im, a.im + b.re}; }
+template <class T> __device__ __forceinline__ cpx<T> csub_i(cpx<T> a, cpx<T> b) { return {a.re + b.im, a.im - b.re}; }
+
+// ---------------------------------------------------------------- layouts
+
+template <int PREC> struct PrecTraits;
+template <> struct PrecTraits<kF64> { using T = double; static constexpr int W = 2; };
+template <> struct PrecTraits<kF32> { using T = float; static constexpr int W = 4; };
+template <> struct PrecTraits<kF16> { using T = float; static constexpr int W = 8; };
+
+template <int NC, int PREC> struct SpinorLayout {
+    static constexpr int NR = 8 * NC;                    // reals per site
+    static constexpr int NVEC = NR / PrecTraits<PREC>::W; // 16-byte vectors per site
+    __host__ __device__ static size_t data_bytes(int nblk) { return (size_t)nblk * 32 * NVEC * 16; }
+    static size_t bytes(int nblk)
+    {
+        size_t b = data_bytes(nblk);
+        if (PREC == kF16) b += (size_t)nblk * 32 * sizeof(float);
+        return (b + 255) & ~(size_t)255;
+    }
+};
+
+__device__ __forceinline__ size_t vec_index(int j, int v, int nvec)
+{
+    return ((size_t)(j >> 5) * nvec + v) * 32 + (j & 31);
+}
+
+template <int NC, int PREC, class T>
+__device__ __forceinline__ void load_spinor(const void *base, int nblk, int j, cpx<T> (&s)[4][NC])
+{
+    using L = SpinorLayout<NC, PREC>;
+    constexpr int NV = L::NVEC;
+    cpx<T> *flat = &s[0][0];
+    if constexpr (PREC == kF64) {
+        const double2 *p = (const double2 *)base;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double2 w = __ldg(p + vec_index(j, v, NV));
+            flat[v].re = (T)w.x;
+            flat[v].im = (T)w.y;
+        }
+    } else if constexpr (PREC == kF32) {
+        const float4 *p = (const float4 *)base;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            float4 w = __ldg(p + vec_index(j, v, NV));
+            flat[2 * v] = {(T)w.x, (T)w.y};
+            flat[2 * v + 1] = {(T)w.z, (T)w.w};
+        }
+    } else {
+        const uint4 *p = (const uint4 *)base;
+        const float *nrm = (const float *)((const char *)base + L::data_bytes(nblk));
+        float sc = __ldg(nrm + j);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            uint4 w = __ldg(p + vec_index(j, v, NV));
+            uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __half2 h = *reinterpret_cast<__half2 *>(&u[q]);
+                float2 f = __half22float2(h);
+                flat[4 * v + q] = {(T)(f.x * sc), (T)(f.y * sc)};
+            }
+        }
+    }
+}
+
+template <int NC, int PREC, class T>
+__device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const cpx<T> (&s)[4][NC])
+{
+    using L = SpinorLayout<NC, PREC>;
+    constexpr int NV = L::NVEC;
+    const cpx<T> *flat = &s[0][0];
+    if constexpr (PREC == kF64) {
+        double2 *p = (double2 *)base;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) p[vec_index(j, v, NV)] = make_double2((double)flat[v].re, (double)flat[v].im);
+    } else if constexpr (PREC == kF32) {
+        float4 *p = (float4 *)base;
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            p[vec_index(j, v, NV)] = make_float4((float)flat[2 * v].re, (float)flat[2 * v].im,
+                                                 (float)flat[2 * v + 1].re, (float)flat[2 * v + 1].im);
+    } else {
+        uint4 *p = (uint4 *)base;
+        float *nrm = (float *)((char *)base + L::data_bytes(nblk));
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4 * NC; ++k) m = fmaxf(m, fmaxf(fabsf((float)flat[k].re), fabsf((float)flat[k].im)));
+        float inv = m > 0.f ? 1.f / m : 0.f;
+        nrm[j] = m;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            uint32_t u[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __half2 h = __floats2half2_rn((float)flat[4 * v + q].re * inv, (float)flat[4 * v + q].im * inv);
+                u[q] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            p[vec_index(j, v, NV)] = make_uint4(u[0], u[1], u[2], u[3]);
+        }
+    }
+}
+
+// Gauge: quaternion links
+template <int PREC> struct GaugeQuat {
+    static size_t bytes(int nblk_g)
+    {
+        size_t per = (PREC == kF64) ? 32 : (PREC == kF32 ? 16 : 8);
+        return (size_t)8 * nblk_g * 32 * per;
+    }
+};
+
+template <int PREC, class T>
+__device__ __forceinline__ void load_quat(const void *base, int nblk_g, int p, int mu, int i, T (&a)[4])
+{
+    size_t slot = (size_t)(p * 4 + mu) * nblk_g + (i >> 5);
+    int lane = i & 31;
+    if constexpr (PREC == kF64) {
+        const double2 *q = (const double2 *)base;
+        double2 w0 = __ldg(q + (slot * 2 + 0) * 32 + lane);
+        double2 w1 = __ldg(q + (slot * 2 + 1) * 32 + lane);
+        a[0] = (T)w0.x; a[1] = (T)w0.y; a[2] = (T)w1.x; a[3] = (T)w1.y;
+    } else if constexpr (PREC == kF32) {
+        float4 w = __ldg((const float4 *)base + slot * 32 + lane);
+        a[0] = w.x; a[1] = w.y; a[2] = w.z; a[3] = w.w;
+    } else {
+        uint2 w = __ldg((const uint2 *)base + slot * 32 + lane);
+        float2 f0 = __half22float2(*reinterpret_cast<__half2 *>(&w.x));
+        float2 f1 = __half22float2(*reinterpret_cast<__half2 *>(&w.y));
+        a[0] = f0.x; a[1] = f0.y; a[2] = f1.x; a[3] = f1.y;
+    }
+}
+
+template <int PREC> struct GaugeMat {
+    static size_t bytes(int nblk_g)
+    {
+        size_t per = (PREC == kF64) ? 8 : (PREC == kF32 ? 4 : 2);
+        return (size_t)8 * nblk_g * 32 * 9 * per;
+    }
+};
+
+template <int PREC, class T>
+__device__ __forceinline__ void load_mat(const void *base, int nblk_g, int p, int mu, int i, T (&R)[3][3])
+{
+    size_t slot = (size_t)(p * 4 + mu) * nblk_g + (i >> 5);
+    int lane = i & 31;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        size_t idx = (slot * 9 + e) * 32 + lane;
+        T v;
+        if constexpr (PREC == kF64) v = (T)__ldg((const double *)base + idx);
+        else if constexpr (PREC == kF32) v = __ldg((const float *)base + idx);
+        else v = __half2float(((const __half *)base)[idx]);
+        R[e / 3][e % 3] = v;
+    }
+}
+
+// Adjoint link of a unit quaternion: R_bc = (a0^2-|a|^2) d_bc + 2 a_b a_c + 2 a0 eps_bck a_k
+template <class T> __device__ __forceinline__ void quat_to_adj(const T (&a)[4], T (&R)[3][3])
+{
+    T w = a[0] * a[0] - (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+    T b1 = 2 * a[1], b2 = 2 * a[2], b3 = 2 * a[3], c = 2 * a[0];
+    R[0][0] = w + b1 * a[1]; R[0][1] = b1 * a[2] + c * a[3]; R[0][2] = b1 * a[3] - c * a[2];
+    R[1][0] = b2 * a[1] - c * a[3]; R[1][1] = w + b2 * a[2]; R[1][2] = b2 * a[3] + c * a[1];
+    R[2][0] = b3 * a[1] + c * a[2]; R[2][1] = b3 * a[2] - c * a[1]; R[2][2] = w + b3 * a[3];
+}
+
+// ---------------------------------------------------------------- colour algebra
+
+// r = U h (DAG = false) or U^+ h (DAG = true), U = a0 + i a.s
+template <bool DAG, class T>
+__device__ __forceinline__ void su2_mul(const T (&a)[4], const cpx<T> (&h)[2], cpx<T> (&r)[2])
+{
+    const T a0 = a[0];
+    const T a1 = DAG ? -a[1] : a[1], a2 = DAG ? -a[2] : a[2], a3 = DAG ? -a[3] : a[3];
+    r[0].re = a0 * h[0].re - a3 * h[0].im + a2 * h[1].re - a1 * h[1].im;
+    r[0].im = a0 * h[0].im + a3 * h[0].re + a2 * h[1].im + a1 * h[1].re;
+    r[1].re = a0 * h[1].re + a3 * h[1].im - a2 * h[0].re - a1 * h[0].im;
+    r[1].im = a0 * h[1].im - a3 * h[1].re - a2 * h[0].im + a1 * h[0].re;
+}
+
+// r = R h (DAG = false) or R^T h (real 3x3)
+template <bool DAG, class T>
+__device__ __forceinline__ void so3_mul(const T (&R)[3][3], const cpx<T> (&h)[3], cpx<T> (&r)[3])
+{
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        T m0 = DAG ? R[0][b] : R[b][0], m1 = DAG ? R[1][b] : R[b][1], m2 = DAG ? R[2][b] : R[b][2];
+        r[b].re = m0 * h[0].re + m1 * h[1].re + m2 * h[2].re;
+        r[b].im = m0 * h[0].im + m1 * h[1].im + m2 * h[2].im;
+    }
+}
+
+// ---------------------------------------------------------------- spin algebra
+// (1 -/+ g_mu) psi = (h, P h) with a 2-spin half spinor h; FWD selects (1 - g_mu).
+
+template <int MU, bool FWD, class T, int NC>
+__device__ __forceinline__ void spin_project(const cpx<T> (&s)[4][NC], cpx<T> (&h)[2][NC])
+{
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        if constexpr (MU == 0) {
+            h[0][c] = FWD ? csub(s[0][c], s[2][c]) : cadd(s[0][c], s[2][c]);
+            h[1][c] = FWD ? csub(s[1][c], s[3][c]) : cadd(s[1][c], s[3][c]);
+        } else if constexpr (MU == 1) {
+            h[0][c] = FWD ? cadd_i(s[0][c], s[3][c]) : csub_i(s[0][c], s[3][c]);
+            h[1][c] = FWD ? cadd_i(s[1][c], s[2][c]) : csub_i(s[1][c], s[2][c]);
+        } else if constexpr (MU == 2) {
+            h[0][c] = FWD ? cadd(s[0][c], s[3][c]) : csub(s[0][c], s[3][c]);
+            h[1][c] = FWD ? csub(s[1][c], s[2][c]) : cadd(s[1][c], s[2][c]);
+        } else {
+            h[0][c] = FWD ? cadd_i(s[0][c], s[2][c]) : csub_i(s[0][c], s[2][c]);
+            h[1][c] = FWD ? csub_i(s[1][c], s[3][c]) : cadd_i(s[1][c], s[3][c]);
+        }
+    }
+}
+
+// acc += (r, P r): the lower two spins of (1 -/+ g_mu) rebuilt from the upper two
+template <int MU, bool FWD, class T, int NC>
+__device__ __forceinline__ void spin_accumulate(cpx<T> (&acc)[4][NC], const cpx<T> (&r)[2][NC])
+{
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        acc[0][c] = cadd(acc[0][c], r[0][c]);
+        acc[1][c] = cadd(acc[1][c], r[1][c]);
+        if constexpr (MU == 0) {
+            if (FWD) { acc[2][c] = csub(acc[2][c], r[0][c]); acc[3][c] = csub(acc[3][c], r[1][c]); }
+            else { acc[2][c] = cadd(acc[2][c], r[0][c]); acc[3][c] = cadd(acc[3][c], r[1][c]); }
+        } else if constexpr (MU == 1) {
+            if (FWD) { acc[2][c] = csub_i(acc[2][c], r[1][c]); acc[3][c] = csub_i(acc[3][c], r[0][c]); }
+            else { acc[2][c] = cadd_i(acc[2][c], r[1][c]); acc[3][c] = cadd_i(acc[3][c], r[0][c]); }
+        } else if constexpr (MU == 2) {
+            if (FWD) { acc[2][c] = csub(acc[2][c], r[1][c]); acc[3][c] = cadd(acc[3][c], r[0][c]); }
+            else { acc[2][c] = cadd(acc[2][c], r[1][c]); acc[3][c] = csub(acc[3][c], r[0][c]); }
+        } else {
+            if (FWD) { acc[2][c] = csub_i(acc[2][c], r[0][c]); acc[3][c] = cadd_i(acc[3][c], r[1][c]); }
+            else { acc[2][c] = cadd_i(acc[2][c], r[0][c]); acc[3][c] = csub_i(acc[3][c], r[1][c]); }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+
+// Deterministic grid reduction of up to 32 per-RHS sums.  Every thread passes
+// its value for right-hand side (j & (nrhs-1)); the block's per-RHS sums go to
+// partials[blockIdx.x*nrhs + r]; the last block to finish adds the partials in
+// block order into sums[r] and returns true (only in that block).
+struct RedSlot {
+    double *partials;  // >= gridDim.x * nrhs doubles
+    unsigned *counter; // zero before the launch; reset by the last block
+};
+
+__device__ __forceinline__ double warp_sum_strided(double v, int nrhs)
+{
+    for (int off = 16; off >= nrhs; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <int MAXW = 32>
+__device__ inline bool grid_reduce(double v, int nrhs, RedSlot slot, double *sums, double *smem /* >= 32*32 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    v = warp_sum_strided(v, nrhs);
+    if (lane < nrhs) smem[warp * 32 + lane] = v;
+    __syncthreads();
+    if (threadIdx.x < nrhs) {
+        double s = 0;
+        for (int w = 0; w < nwarps; ++w) s += smem[w * 32 + threadIdx.x];
+        slot.partials[(size_t)blockIdx.x * nrhs + threadIdx.x] = s;
+    }
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(slot.counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if (threadIdx.x < nrhs) {
+        double s = 0;
+        const volatile double *pp = slot.partials;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += pp[(size_t)b * nrhs + threadIdx.x];
+        sums[threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) *slot.counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------- solver scalars
+constexpr int kMaxRhsSlots = 32;
+
+// offsets (in units of kMaxRhsSlots doubles) of a context's solver scalar block
+enum ScalSlot {
+    S_RR = 0,      // |r|^2 of the current recurrence
+    S_PAP = 1,     // <p, A p> = |Mhat p|^2
+    S_ALPHA = 2,
+    S_BETA = 3,
+    S_BB = 4,      // |b|^2
+    S_STOP = 5,    // tol^2 |b|^2
+    S_ACTIVE = 6,  // 1.0 while the RHS is iterating
+    S_RMAX = 7,    // max |r|^2 since the last reliable update
+    S_RROLD = 8,   // |r|^2 before the current iteration
+    S_OUT = 9,     // generic reduction output
+    S_FLAGS = 10,  // [0] all done, [1] reliable-update gate, [2] NaN/Inf seen, [3] iterations
+    S_DELTA2 = 11, // [0] reliable-update threshold delta^2
+    S_NSLOTS = 12
+};
+constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4;
+
+enum FinishMode {
+    kFinNone = 0,
+    kFinStore = 1,      // scal[S_OUT] = sums
+    kFinAlpha = 2,      // pAp = sums; alpha = active ? rr / pAp : 0
+    kFinBeta = 3,       // rr_new = sums; beta; converged RHS stop
+    kFinBetaMixed = 4,  // as kFinBeta, but convergence and small residuals open the reliable-update gate
+    kFinResidual = 5,   // true FP64 residual of a reliable update: restart bookkeeping, close the gate
+    kFinInit = 6,       // |r0|^2: rr = rmax = rrold = sums, a RHS is active while rr > stop
+    kFinBB = 7          // |b|^2: bb = sums, stop = tol^2 bb (tol^2 in scal[S_DELTA2][1])
+};
+
+__device__ __forceinline__ double &sc(double *scal, int slot, int r) { return scal[slot * kMaxRhsSlots + r]; }
+
+// Scalar updates run by the last block of a grid reduction (threads 0..nrhs-1
+// hold one right-hand side each); afterwards thread 0 refreshes the flags.
+__device__ inline void finish_reduction(int mode, const double *sums, int nrhs, double *scal)
+{
+    const int r = threadIdx.x;
+    if (r < nrhs) {
+        double v = sums[r];
+        bool bad = !isfinite(v);
+        bool act = sc(scal, S_ACTIVE, r) != 0.0;
+        switch (mode) {
+        case kFinStore:
+            sc(scal, S_OUT, r) = v;
+            break;
+        case kFinAlpha:
+            sc(scal, S_PAP, r) = v;
+            sc(scal, S_ALPHA, r) = (act && v > 0.0) ? sc(scal, S_RR, r) / v : 0.0;
+            break;
+        case kFinBeta:
+        case kFinBetaMixed: {
+            double rr = sc(scal, S_RR, r);
+            sc(scal, S_RROLD, r) = rr;
+            if (act) {
+                sc(scal, S_BETA, r) = v / rr;
+                sc(scal, S_RR, r) = v;
+                if (mode == kFinBeta) {
+                    if (v <= sc(scal, S_STOP, r)) sc(scal, S_ACTIVE, r) = 0.0;
+                } else {
+                    double rmax = fmax(sc(scal, S_RMAX, r), v);
+                    sc(scal, S_RMAX, r) = rmax;
+                    if (v <= sc(scal, S_STOP, r) || v < sc(scal, S_DELTA2, 0) * rmax) sc(scal, S_FLAGS, F_GATE) = 1.0;
+                }
+            } else {
+                sc(scal, S_BETA, r) = 0.0;
+            }
+            break;
+        }
+        case kFinInit:
+            sc(scal, S_RR, r) = v;
+            sc(scal, S_RMAX, r) = v;
+            sc(scal, S_RROLD, r) = v;
+            sc(scal, S_ACTIVE, r) = (v > sc(scal, S_STOP, r)) ? 1.0 : 0.0;
+            break;
+        case kFinBB:
+            sc(scal, S_BB, r) = v;
+            sc(scal, S_STOP, r) = sc(scal, S_DELTA2, 1) * v;
+            break;
+        case kFinResidual:
+            if (act) {
+                sc(scal, S_BETA, r) = v / sc(scal, S_RROLD, r);
+                sc(scal, S_RR, r) = v;
+                sc(scal, S_RMAX, r) = v;
+                if (v <= sc(scal, S_STOP, r)) sc(scal, S_ACTIVE, r) = 0.0;
+            } else {
+                sc(scal, S_BETA, r) = 0.0;
+            }
+            sc(scal, S_OUT, r) = v;
+            break;
+        default:
+            break;
+        }
+        if (bad && mode != kFinStore) sc(scal, S_FLAGS, F_NUMERIC) = 1.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && mode != kFinStore && mode != kFinBB) {
+        bool all_done = true;
+        for (int k = 0; k < nrhs; ++k) all_done = all_done && (sc(scal, S_ACTIVE, k) == 0.0);
+        if (sc(scal, S_FLAGS, F_NUMERIC) != 0.0) all_done = true;
+        sc(scal, S_FLAGS, F_DONE) = all_done ? 1.0 : 0.0;
+        if (mode == kFinBeta || mode == kFinBetaMixed) sc(scal, S_FLAGS, F_ITERS) += 1.0;
+        if (mode == kFinResidual) {
+            sc(scal, S_FLAGS, F_GATE) = 0.0;
+            sc(scal, S_FLAGS, F_NRELIABLE) += 1.0;
+        }
+    }
+}
+
+} // namespace hr

@@ -1,0 +1,308 @@
+"""ctypes binding of libhirep_gb300.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls
+(``include/hirep_gb300.h``) and only converts arguments: torch tensors become
+device pointers, streams become ``cudaStream_t`` handles, status codes become
+:class:`HrError`.  All computation happens in the library's CUDA kernels.
+The library is built in-tree (``paper_2411_18511_gb300/_build``); if it cannot
+be built or loaded, :func:`lib` raises -- there is no fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+# ------------------------------------------------------------------ enums
+HR_OK, HR_ERR_INVALID_ARG, HR_ERR_UNSUPPORTED, HR_ERR_CUDA = 0, 1, 2, 3
+HR_ERR_NOT_CONVERGED, HR_ERR_NUMERIC, HR_ERR_TIMEOUT, HR_ERR_WORKSPACE = 4, 5, 6, 7
+HR_FUND, HR_ADJ, HR_ADJ_MAT = 0, 1, 2
+HR_F64, HR_F32, HR_F16 = 0, 1, 2
+HR_EVEN, HR_ODD, HR_FULL = 0, 1, 2
+HR_OP_HOP, HR_OP_SCHUR, HR_OP_SCHUR_DAG, HR_OP_NORMAL = 0, 1, 2, 3
+
+STATUS_NAMES = {0: "HR_OK", 1: "HR_ERR_INVALID_ARG", 2: "HR_ERR_UNSUPPORTED", 3: "HR_ERR_CUDA",
+                4: "HR_ERR_NOT_CONVERGED", 5: "HR_ERR_NUMERIC", 6: "HR_ERR_TIMEOUT",
+                7: "HR_ERR_WORKSPACE"}
+
+# every symbol the header declares (checked by the ABI tests)
+EXPORTED = [
+    "hr_ctx_create", "hr_ctx_destroy", "hr_last_error", "hr_version", "hr_kappa_to_m0",
+    "hr_m0_to_kappa", "hr_gauge_packed_bytes", "hr_spinor_packed_bytes", "hr_gauge_pack",
+    "hr_spinor_pack", "hr_spinor_unpack", "hr_dirac_workspace_bytes", "hr_dirac_apply",
+    "hr_dirac_eo", "hr_solver_default_opts", "hr_cg_workspace_bytes", "hr_cg_solve", "hr_force",
+    "hr_link_grad", "hr_norm2", "hr_axpy", "hr_gamma5",
+]
+
+
+class HrError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        self.code = code
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {message}")
+
+
+class hr_lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4)]
+
+
+class hr_solver_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner_prec", ctypes.c_int),
+                ("reliable_delta", ctypes.c_double), ("n_rhs", ctypes.c_int),
+                ("x0_is_guess", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class hr_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("n_reliable_updates", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the CUDA library; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+            LAT = hr_lattice
+            sig = {
+                "hr_ctx_create": ([ctypes.POINTER(P), I], I),
+                "hr_ctx_destroy": ([P], I),
+                "hr_last_error": ([P], ctypes.c_char_p),
+                "hr_version": ([], ctypes.c_char_p),
+                "hr_kappa_to_m0": ([D], D),
+                "hr_m0_to_kappa": ([D], D),
+                "hr_gauge_packed_bytes": ([LAT, I, I], S),
+                "hr_spinor_packed_bytes": ([LAT, I, I, I, I], S),
+                "hr_gauge_pack": ([P, LAT, I, I, P, P, P], I),
+                "hr_spinor_pack": ([P, LAT, I, I, I, I, P, P, P], I),
+                "hr_spinor_unpack": ([P, LAT, I, I, I, I, P, P, P], I),
+                "hr_dirac_workspace_bytes": ([LAT, I, I, I, I], S),
+                "hr_dirac_apply": ([P, LAT, D, I, I, P, P, P, P], I),
+                "hr_dirac_eo": ([P, LAT, D, I, I, I, I, I, P, P, P, P, S, P], I),
+                "hr_solver_default_opts": ([], hr_solver_opts),
+                "hr_cg_workspace_bytes": ([LAT, I, ctypes.POINTER(hr_solver_opts)], S),
+                "hr_cg_solve": ([P, LAT, D, I, ctypes.POINTER(hr_solver_opts), P, P, P,
+                                 ctypes.POINTER(hr_solve_info), P, S, P], I),
+                "hr_force": ([P, LAT, P, P, P, D, P, P], I),
+                "hr_link_grad": ([P, LAT, P, P, D, P, P], I),
+                "hr_norm2": ([P, LAT, I, P, ctypes.POINTER(D), P], I),
+                "hr_axpy": ([P, LAT, I, D, P, P, P], I),
+                "hr_gamma5": ([P, LAT, I, P, P], I),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+# ------------------------------------------------------------------ helpers
+
+def lattice(dims) -> hr_lattice:
+    lat = hr_lattice()
+    for k in range(4):
+        lat.dims[k] = int(dims[k])
+    return lat
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(int(x))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _need(t, nbytes: int, what: str):
+    """Buffer checks the C ABI cannot do: device residency and size."""
+    if t is None or not hasattr(t, "data_ptr"):
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise ValueError(f"{what}: {have} bytes given, {nbytes} needed")
+
+
+class Context:
+    """Owns an ``hr_ctx`` (device scratch for reductions and solver scalars)."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        rc = lib().hr_ctx_create(ctypes.byref(self._h), int(device))
+        if rc != HR_OK:
+            raise HrError(rc, f"hr_ctx_create(device={device}) failed")
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().hr_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc: int):
+        if rc != HR_OK:
+            msg = lib().hr_last_error(self._h)
+            raise HrError(rc, msg.decode() if msg else "")
+        return rc
+
+
+# ------------------------------------------------------------------ C entry points
+
+def hr_version() -> str:
+    return lib().hr_version().decode()
+
+
+def hr_kappa_to_m0(kappa: float) -> float:
+    return lib().hr_kappa_to_m0(float(kappa))
+
+
+def hr_m0_to_kappa(m0: float) -> float:
+    return lib().hr_m0_to_kappa(float(m0))
+
+
+def hr_gauge_packed_bytes(dims, rep: int, prec: int) -> int:
+    return int(lib().hr_gauge_packed_bytes(lattice(dims), rep, prec))
+
+
+def hr_spinor_packed_bytes(dims, rep: int, prec: int, parity: int, n_rhs: int = 1) -> int:
+    return int(lib().hr_spinor_packed_bytes(lattice(dims), rep, prec, parity, n_rhs))
+
+
+def hr_dirac_workspace_bytes(dims, rep: int, prec: int, op: int, n_rhs: int = 1) -> int:
+    return int(lib().hr_dirac_workspace_bytes(lattice(dims), rep, prec, op, n_rhs))
+
+
+def hr_gauge_pack(ctx: Context, dims, rep, prec, canonical, packed, stream=None):
+    V = _vol(dims)
+    _need(canonical, 4 * V * 4 * 8, "canonical gauge")
+    _need(packed, hr_gauge_packed_bytes(dims, rep, prec), "packed gauge")
+    return ctx.check(lib().hr_gauge_pack(ctx.handle, lattice(dims), rep, prec, _ptr(canonical),
+                                         _ptr(packed), _stream(stream)))
+
+
+def hr_spinor_pack(ctx: Context, dims, rep, prec, parity, n_rhs, canonical, packed, stream=None):
+    nc = 2 if rep == HR_FUND else 3
+    _need(canonical, n_rhs * _vol(dims) * 4 * nc * 16, "canonical spinor")
+    _need(packed, hr_spinor_packed_bytes(dims, rep, prec, parity, n_rhs), "packed spinor")
+    return ctx.check(lib().hr_spinor_pack(ctx.handle, lattice(dims), rep, prec, parity, n_rhs,
+                                          _ptr(canonical), _ptr(packed), _stream(stream)))
+
+
+def hr_spinor_unpack(ctx: Context, dims, rep, prec, parity, n_rhs, packed, canonical, stream=None):
+    nc = 2 if rep == HR_FUND else 3
+    _need(canonical, n_rhs * _vol(dims) * 4 * nc * 16, "canonical spinor")
+    _need(packed, hr_spinor_packed_bytes(dims, rep, prec, parity, n_rhs), "packed spinor")
+    return ctx.check(lib().hr_spinor_unpack(ctx.handle, lattice(dims), rep, prec, parity, n_rhs,
+                                            _ptr(packed), _ptr(canonical), _stream(stream)))
+
+
+def hr_dirac_apply(ctx: Context, dims, m0, rep, prec, gauge, inp, out, stream=None):
+    full = hr_spinor_packed_bytes(dims, rep, prec, HR_FULL, 1)
+    _need(inp, full, "in")
+    _need(out, full, "out")
+    return ctx.check(lib().hr_dirac_apply(ctx.handle, lattice(dims), float(m0), rep, prec,
+                                          _ptr(gauge), _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def hr_dirac_eo(ctx: Context, dims, m0, rep, prec, out_parity, op, n_rhs, gauge, inp, out,
+                work=None, stream=None):
+    half = hr_spinor_packed_bytes(dims, rep, prec, HR_EVEN, n_rhs)
+    _need(inp, half, "in")
+    _need(out, half, "out")
+    wb = 0 if work is None else work.numel() * work.element_size()
+    return ctx.check(lib().hr_dirac_eo(ctx.handle, lattice(dims), float(m0), rep, prec, out_parity,
+                                       op, n_rhs, _ptr(gauge), _ptr(inp), _ptr(out), _ptr(work),
+                                       wb, _stream(stream)))
+
+
+def hr_solver_default_opts() -> hr_solver_opts:
+    return lib().hr_solver_default_opts()
+
+
+def hr_cg_workspace_bytes(dims, rep: int, opts: hr_solver_opts) -> int:
+    return int(lib().hr_cg_workspace_bytes(lattice(dims), rep, ctypes.byref(opts)))
+
+
+def hr_cg_solve(ctx: Context, dims, m0, rep, opts: hr_solver_opts, gauge, b, x, work, stream=None,
+                raise_on_error: bool = True):
+    """Returns (status, hr_solve_info)."""
+    half = hr_spinor_packed_bytes(dims, rep, HR_F64, HR_EVEN, opts.n_rhs)
+    _need(b, half, "b")
+    _need(x, half, "x")
+    info = hr_solve_info()
+    wb = 0 if work is None else work.numel() * work.element_size()
+    rc = lib().hr_cg_solve(ctx.handle, lattice(dims), float(m0), rep, ctypes.byref(opts),
+                           _ptr(gauge), _ptr(b), _ptr(x), ctypes.byref(info), _ptr(work), wb,
+                           _stream(stream))
+    if raise_on_error and rc not in (HR_OK, HR_ERR_NOT_CONVERGED):
+        ctx.check(rc)
+    return rc, info
+
+
+def hr_force(ctx: Context, dims, gauge, a_full, b_full, beta, force, stream=None):
+    _need(force, 4 * _vol(dims) * 3 * 8, "force")
+    return ctx.check(lib().hr_force(ctx.handle, lattice(dims), _ptr(gauge), _ptr(a_full),
+                                    _ptr(b_full), float(beta), _ptr(force), _stream(stream)))
+
+
+def hr_link_grad(ctx: Context, dims, a_full, b_full, beta, grad, stream=None):
+    _need(grad, 4 * _vol(dims) * 4 * 8, "grad")
+    return ctx.check(lib().hr_link_grad(ctx.handle, lattice(dims), _ptr(a_full), _ptr(b_full),
+                                        float(beta), _ptr(grad), _stream(stream)))
+
+
+def hr_norm2(ctx: Context, dims, rep, v, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    ctx.check(lib().hr_norm2(ctx.handle, lattice(dims), rep, _ptr(v), ctypes.byref(out),
+                             _stream(stream)))
+    return out.value
+
+
+def hr_axpy(ctx: Context, dims, rep, a, x, y, stream=None):
+    return ctx.check(lib().hr_axpy(ctx.handle, lattice(dims), rep, float(a), _ptr(x), _ptr(y),
+                                   _stream(stream)))
+
+
+def hr_gamma5(ctx: Context, dims, rep, v, stream=None):
+    return ctx.check(lib().hr_gamma5(ctx.handle, lattice(dims), rep, _ptr(v), _stream(stream)))
+
+
+def _vol(dims) -> int:
+    v = 1
+    for d in dims:
+        v *= int(d)
+    return v
