@@ -47,6 +47,11 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip the CG and precision sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--lattice", type=int, default=48,
+                    help="L of the L^4 lattice (48 is the benchmark workload; smaller for profiling)")
+    ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64",
+                    help="hop precision of the timed step (f64 is the benchmark workload)")
     return ap.parse_args()
 
 
@@ -196,16 +201,24 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     ctx = hr.Context(local)
-    dims = DIMS
+    L4 = args.lattice
+    dims = (L4,) * 4
     V = int(np.prod(dims))
     Vh = V // 2
-    rep, prec = hr.HR_FUND, hr.HR_F64
+    pname = args.prec
+    rep, prec = hr.HR_FUND, {"f64": hr.HR_F64, "f32": hr.HR_F32, "f16": hr.HR_F16}[pname]
     q = synth.haar_links(dims, GAUGE_SEED)
     psi = synth.gaussian_spinor(dims, 2, SPINOR_SEED)
     gauge = fields.pack_gauge(ctx, dims, rep, prec, fields.gauge_to_device(q))
-    dpsi = fields.spinor_to_device(psi)
-    src = fields.pack_spinor(ctx, dims, rep, prec, hr.HR_FULL, dpsi)
+    src = fields.pack_spinor(ctx, dims, rep, prec, hr.HR_FULL, fields.spinor_to_device(psi))
     dst = fields.empty_spinor(dims, rep, prec, hr.HR_FULL)
     half = hr.hr_spinor_packed_bytes(dims, rep, prec, hr.HR_EVEN, 1)
     stream = torch.cuda.current_stream()
@@ -240,61 +253,26 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms_total = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    bytes_site = hop_bytes_per_site("fund", "f64")
+    ms_step = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    bytes_site = hop_bytes_per_site("fund", pname)
     bytes_step = 2 * Vh * bytes_site
     value = world * bytes_step / (ms_step * 1e-3) / 1e9
-    launch_ms = ms_step / 2.0
+    launch_ms = ms_step / 2.0  # the step is exactly two launches of the hop kernel
     achieved = Vh * bytes_site / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies timed
-    host_in = torch.view_as_real(torch.from_numpy(psi)).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    dev_can = torch.empty(host_in.shape, dtype=torch.float64, device="cuda")
-    dev_can_out = torch.empty_like(dev_can)
-    full_bytes = hr.hr_spinor_packed_bytes(dims, rep, prec, hr.HR_FULL, 1)
-
-    def e2e_step():
-        dev_can.copy_(host_in, non_blocking=True)
-        hr.hr_spinor_pack(ctx, dims, rep, prec, hr.HR_FULL, 1, dev_can, src, stream)
-        step()
-        hr.hr_spinor_unpack(ctx, dims, rep, prec, hr.HR_FULL, 1, dst, dev_can_out, stream)
-        host_out.copy_(dev_can_out, non_blocking=True)
-
-    for _ in range(3):
-        e2e_step()
-    torch.cuda.synchronize()
-    n_e2e = max(5, min(50, args.steps // 20))
-    e0.record(stream)
-    for _ in range(n_e2e):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / n_e2e
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": round(world * bytes_step / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-           "h2d_bytes_per_step": int(host_in.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
-           "ms_per_step": round(e2e_ms, 4),
-           "path": "pinned host canonical spinor -> H2D -> hr_spinor_pack -> 2x hr_dirac_eo -> hr_spinor_unpack -> D2H"}
-    del dev_can, dev_can_out
-
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, ctx, torch, hr, dims, rep, prec, psi, src, dst, step, stream,
+                      max_over_ranks, world, bytes_step)
     extras = {}
     if not args.no_extras and rank == 0:
         extras = run_extras(ctx, torch, hr, fields, synth, q, psi)
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(q, psi)
+        cpu = cpu_baseline(q, psi, dims)
 
+    gauge_mb = hr.hr_gauge_packed_bytes(dims, rep, prec) / 1e6
     result = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -306,21 +284,22 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": pname,
         "data": "synthetic (Haar-random SU(2) links, Gaussian complex source, Philox seeds 1003/2003)",
         "config": {
-            "workload": "even-odd Wilson-Dirac hop pair D_eo+D_oe, 48^4 SU(2) fundamental, FP64",
-            "lattice": list(dims), "rep": "fund", "prec": "f64",
-            "bytes_per_site": bytes_site, "byte_convention": "compulsory (1 spinor in + 1 out + 8 quaternion links)",
-            "neighbour_counted_gbs": round(value * neighbour_bytes_per_site("fund", "f64") / bytes_site, 2),
-            "l2": "inputs larger than L2 (gauge 680 MB, spinor half 340 MB per launch)",
+            "workload": f"even-odd Wilson-Dirac hop pair D_eo+D_oe, {L4}^4 SU(2) fundamental, {pname.upper()}",
+            "lattice": list(dims), "rep": "fund", "prec": pname,
+            "bytes_per_site": bytes_site,
+            "byte_convention": "compulsory (1 spinor in + 1 out + 8 quaternion links)",
+            "neighbour_counted_gbs": round(value * neighbour_bytes_per_site("fund", pname) / bytes_site, 2),
+            "l2": f"inputs larger than L2 (gauge {gauge_mb:.0f} MB + spinor half {half / 1e6:.0f} MB per launch)",
             "parallelism": f"replicas{world}",
         },
         "roofline": {
             "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} HBM copy",
-            "traffic": profiled_traffic("hop_fund_f64_48x48x48x48.md"),
-            "kernel": "k_hop<fund,f64>", "bytes_per_launch": Vh * bytes_site,
+            "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} HBM copy (burst)",
+            "traffic": profiled_traffic(f"hop_fund_{pname}_{L4}x{L4}x{L4}x{L4}.md"),
+            "kernel": f"k_hop<fund,{pname}>", "bytes_per_launch": Vh * bytes_site,
             "avg_launch_ms": round(launch_ms, 5),
         },
         "e2e": e2e,
@@ -333,6 +312,40 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_e2e(args, ctx, torch, hr, dims, rep, prec, psi, src, dst, step, stream, max_over_ranks, world,
+            bytes_step):
+    """The same step through the public API from pinned host memory: H2D of the
+    canonical spinor, pack, the two hops, unpack, D2H; all inside the timing."""
+    host_in = torch.view_as_real(torch.from_numpy(psi)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_can = torch.empty(host_in.shape, dtype=torch.float64, device="cuda")
+    dev_can_out = torch.empty_like(dev_can)
+
+    def e2e_step():
+        dev_can.copy_(host_in, non_blocking=True)
+        hr.hr_spinor_pack(ctx, dims, rep, prec, hr.HR_FULL, 1, dev_can, src, stream)
+        step()
+        hr.hr_spinor_unpack(ctx, dims, rep, prec, hr.HR_FULL, 1, dst, dev_can_out, stream)
+        host_out.copy_(dev_can_out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    n_e2e = max(5, min(50, args.steps // 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / n_e2e)
+    return {"value": round(world * bytes_step / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": int(host_in.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
+            "ms_per_step": round(e2e_ms, 4),
+            "path": "pinned host canonical spinor -> H2D -> hr_spinor_pack -> 2x hr_dirac_eo -> "
+                    "hr_spinor_unpack -> D2H"}
 
 
 def time_hop(ctx, torch, hr, fields, dims, rep, prec, q, psi, steps=100):
@@ -406,20 +419,20 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     return out
 
 
-def cpu_baseline(q, psi):
+def cpu_baseline(q, psi, dims):
     """The FP64 oracle as it stands on the host cores: one hop pair over the
-    whole 48^4 lattice (every site once), OpenMP over sites."""
+    whole lattice (every site once), OpenMP over sites."""
     import oracle
     try:
-        L = oracle.expand_links(DIMS, 2, q)
-        V = int(np.prod(DIMS))
+        L = oracle.expand_links(dims, 2, q)
+        V = int(np.prod(dims))
         t0 = time.perf_counter()
-        out = oracle.hop(DIMS, L, psi, parity=-1)
+        out = oracle.hop(dims, L, psi, parity=-1)
         dt = time.perf_counter() - t0
         del out, L
         gbs = (V // 2) * 2 * hop_bytes_per_site("fund", "f64") / dt / 1e9
         return {"value": round(gbs, 3), "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
-                "sample": f"one D_eo+D_oe application over all {V} sites of 48^4 ({dt:.2f} s)",
+                "sample": f"one D_eo+D_oe application over all {V} sites of {dims[0]}^4 ({dt:.2f} s)",
                 "cpu": _cpu_model()}
     except Exception as exc:  # the baseline is informative only
         return {"value": None, "unit": "GB/s", "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}

@@ -21,34 +21,40 @@ constexpr int kBS = 256;
 
 template <int P> using RT = typename PrecTraits<P>::T;
 
+// arithmetic type of a kernel touching fields of two precisions: double-float
+// as soon as one operand is an FP64 (double-float) field, else FP32
 template <class A, class B> struct Wider { using T = A; };
-template <> struct Wider<float, double> { using T = double; };
+template <> struct Wider<float, dd> { using T = dd; };
 
 template <int NC, class T>
-__device__ __forceinline__ double site_norm2(const cpx<T> (&v)[4][NC])
+__device__ __forceinline__ void acc_site(SqAcc<T> &acc, const cpx<T> (&v)[4][NC])
 {
-    double s = 0.0;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) s += (double)v[a][c].re * (double)v[a][c].re + (double)v[a][c].im * (double)v[a][c].im;
-    return s;
+        for (int c = 0; c < NC; ++c) {
+            acc.add(v[a][c].re);
+            acc.add(v[a][c].im);
+        }
 }
+
+// the right-hand side a thread works on is fixed: the grid stride is a multiple of 32
+__device__ __forceinline__ int thread_rhs(const Geom &g) { return (blockIdx.x * blockDim.x + threadIdx.x) & (g.nrhs - 1); }
 
 template <int NC, int P>
 __global__ void __launch_bounds__(kBS) k_norm2(Geom g, const void *v, RedSlot red, double *scal, int fin)
 {
     using T = RT<P>;
     const int nv = g.vh << g.lrhs;
-    double acc = 0.0;
+    SqAcc<T> acc;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
         cpx<T> a[4][NC];
         load_spinor<NC, P>(v, g.nblk_s, j, a);
-        acc += site_norm2<NC>(a);
+        acc_site<NC>(acc, a);
     }
     __shared__ double smem[32 * 32];
     __shared__ double sums[32];
-    if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
+    if (grid_reduce(acc.get(), g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
 }
 
 // x += alpha p ; r -= alpha q ; |r|^2 -> fin (kFinBeta / kFinBetaMixed)
@@ -59,9 +65,9 @@ __global__ void __launch_bounds__(kBS) k_xr(Geom g, void *x, const void *p, void
     using T = typename Wider<RT<PX>, RT<PR>>::T;
     if (sc(scal, S_FLAGS, F_DONE) != 0.0) return;
     const int nv = g.vh << g.lrhs;
-    double acc = 0.0;
+    const T al = Real<T>::from_double(sc(scal, S_ALPHA, thread_rhs(g)));
+    SqAcc<T> acc;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
-        const T al = (T)sc(scal, S_ALPHA, j & (g.nrhs - 1));
         cpx<T> xv[4][NC], pv[4][NC], rv[4][NC], qv[4][NC];
         load_spinor<NC, PX>(x, g.nblk_s, j, xv);
         load_spinor<NC, PP>(p, g.nblk_s, j, pv);
@@ -78,11 +84,11 @@ __global__ void __launch_bounds__(kBS) k_xr(Geom g, void *x, const void *p, void
             }
         store_spinor<NC, PX>(x, g.nblk_s, j, xv);
         store_spinor<NC, PR>(r, g.nblk_s, j, rv);
-        acc += site_norm2<NC>(rv);
+        acc_site<NC>(acc, rv);
     }
     __shared__ double smem[32 * 32];
     __shared__ double sums[32];
-    if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
+    if (grid_reduce(acc.get(), g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
 }
 
 // p = r + beta p
@@ -92,8 +98,8 @@ __global__ void __launch_bounds__(kBS) k_p(Geom g, void *p, const void *r, const
     using T = typename Wider<RT<PP>, RT<PR>>::T;
     if (sc((double *)scal, S_FLAGS, F_DONE) != 0.0) return;
     const int nv = g.vh << g.lrhs;
+    const T be = Real<T>::from_double(scal[S_BETA * kMaxRhsSlots + thread_rhs(g)]);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
-        const T be = (T)scal[S_BETA * kMaxRhsSlots + (j & (g.nrhs - 1))];
         cpx<T> pv[4][NC], rv[4][NC];
         load_spinor<NC, PP>(p, g.nblk_s, j, pv);
         load_spinor<NC, PR>(r, g.nblk_s, j, rv);
@@ -118,16 +124,17 @@ __global__ void __launch_bounds__(kBS) k_convert(Geom g, const void *src, void *
     }
 }
 
-// r = b - ax ; |r|^2 -> fin ; optionally r_lo = r in precision PL
+// r = b - ax (FP64 fields) ; |r|^2 -> fin ; optionally r_lo = r in precision PL
 template <int NC, int PL>
 __global__ void __launch_bounds__(kBS) k_residual(Geom g, const void *b, const void *ax, void *r, RedSlot red,
                                                   double *scal, int fin, const double *gate, void *r_lo)
 {
+    using T = RT<kF64>;
     if (gate && *gate == 0.0) return;
     const int nv = g.vh << g.lrhs;
-    double acc = 0.0;
+    SqAcc<T> acc;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
-        cpx<double> bv[4][NC], av[4][NC];
+        cpx<T> bv[4][NC], av[4][NC];
         load_spinor<NC, kF64>(b, g.nblk_s, j, bv);
         load_spinor<NC, kF64>(ax, g.nblk_s, j, av);
 #pragma unroll
@@ -136,21 +143,22 @@ __global__ void __launch_bounds__(kBS) k_residual(Geom g, const void *b, const v
             for (int c = 0; c < NC; ++c) bv[a][c] = csub(bv[a][c], av[a][c]);
         store_spinor<NC, kF64>(r, g.nblk_s, j, bv);
         if (PL != kF64 && r_lo) store_spinor<NC, PL>(r_lo, g.nblk_s, j, bv);
-        acc += site_norm2<NC>(bv);
+        acc_site<NC>(acc, bv);
     }
     __shared__ double smem[32 * 32];
     __shared__ double sums[32];
-    if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
+    if (grid_reduce(acc.get(), g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
 }
 
 // x_hi += x_lo ; x_lo = 0
 template <int NC, int PL>
 __global__ void __launch_bounds__(kBS) k_accum(Geom g, void *xhi, void *xlo, const double *gate)
 {
+    using T = RT<kF64>;
     if (gate && *gate == 0.0) return;
     const int nv = g.vh << g.lrhs;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
-        cpx<double> h[4][NC], l[4][NC];
+        cpx<T> h[4][NC], l[4][NC];
         load_spinor<NC, kF64>(xhi, g.nblk_s, j, h);
         load_spinor<NC, PL>(xlo, g.nblk_s, j, l);
 #pragma unroll
@@ -158,7 +166,7 @@ __global__ void __launch_bounds__(kBS) k_accum(Geom g, void *xhi, void *xlo, con
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 h[a][c] = cadd(h[a][c], l[a][c]);
-                l[a][c] = {0.0, 0.0};
+                l[a][c] = {T(0.f), T(0.f)};
             }
         store_spinor<NC, kF64>(xhi, g.nblk_s, j, h);
         store_spinor<NC, PL>(xlo, g.nblk_s, j, l);
@@ -168,15 +176,17 @@ __global__ void __launch_bounds__(kBS) k_accum(Geom g, void *xhi, void *xlo, con
 template <int NC>
 __global__ void __launch_bounds__(kBS) k_axpy(Geom g, double a, const void *x, void *y)
 {
+    using T = RT<kF64>;
     const int nv = g.vh << g.lrhs;
+    const T aa = Real<T>::from_double(a);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
-        cpx<double> xv[4][NC], yv[4][NC];
+        cpx<T> xv[4][NC], yv[4][NC];
         load_spinor<NC, kF64>(x, g.nblk_s, j, xv);
         load_spinor<NC, kF64>(y, g.nblk_s, j, yv);
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) yv[s][c] = {yv[s][c].re + a * xv[s][c].re, yv[s][c].im + a * xv[s][c].im};
+            for (int c = 0; c < NC; ++c) yv[s][c] = {yv[s][c].re + aa * xv[s][c].re, yv[s][c].im + aa * xv[s][c].im};
         store_spinor<NC, kF64>(y, g.nblk_s, j, yv);
     }
 }
@@ -184,9 +194,10 @@ __global__ void __launch_bounds__(kBS) k_axpy(Geom g, double a, const void *x, v
 template <int NC>
 __global__ void __launch_bounds__(kBS) k_gamma5(Geom g, void *v)
 {
+    using T = RT<kF64>;
     const int nv = g.vh << g.lrhs;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
-        cpx<double> a[4][NC];
+        cpx<T> a[4][NC];
         load_spinor<NC, kF64>(v, g.nblk_s, j, a);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {

@@ -104,23 +104,8 @@ __global__ void k_gauge_pack_quat(Geom g, const double *__restrict__ can, void *
     int x0 = (int)(r / g.d[1]);
     int p = (x0 + x1 + x2 + x3) & 1;
     int i = (int)(x >> 1);
-    const double *a = can + t * 4;
-    size_t slot = (size_t)(p * 4 + mu) * g.nblk_g + (i >> 5);
-    int lane = i & 31;
-    if (PREC == kF64) {
-        double2 *q = (double2 *)packed;
-        q[(slot * 2 + 0) * 32 + lane] = make_double2(a[0], a[1]);
-        q[(slot * 2 + 1) * 32 + lane] = make_double2(a[2], a[3]);
-    } else if (PREC == kF32) {
-        ((float4 *)packed)[slot * 32 + lane] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
-    } else {
-        __half2 h0 = __floats2half2_rn((float)a[0], (float)a[1]);
-        __half2 h1 = __floats2half2_rn((float)a[2], (float)a[3]);
-        uint2 w;
-        w.x = *reinterpret_cast<uint32_t *>(&h0);
-        w.y = *reinterpret_cast<uint32_t *>(&h1);
-        ((uint2 *)packed)[slot * 32 + lane] = w;
-    }
+    const double a[4] = {can[t * 4 + 0], can[t * 4 + 1], can[t * 4 + 2], can[t * 4 + 3]};
+    store_quat<PREC>(packed, g.nblk_g, p, mu, i, a);
 }
 
 template <int PREC>
@@ -142,14 +127,8 @@ __global__ void k_gauge_pack_mat(Geom g, const double *__restrict__ can, void *p
     double a[4] = {can[t * 4 + 0], can[t * 4 + 1], can[t * 4 + 2], can[t * 4 + 3]};
     double R[3][3];
     quat_to_adj(a, R);
-    size_t slot = (size_t)(p * 4 + mu) * g.nblk_g + (i >> 5);
-    int lane = i & 31;
     for (int e = 0; e < 9; ++e) {
-        size_t idx = (slot * 9 + e) * 32 + lane;
-        double v = R[e / 3][e % 3];
-        if (PREC == kF64) ((double *)packed)[idx] = v;
-        else if (PREC == kF32) ((float *)packed)[idx] = (float)v;
-        else ((__half *)packed)[idx] = __float2half_rn((float)v);
+        store_mat_entry<PREC>(packed, g.nblk_g, p, mu, i, e, R[e / 3][e % 3]);
     }
 }
 
@@ -158,7 +137,7 @@ __global__ void k_gauge_pack_mat(Geom g, const double *__restrict__ can, void *p
 template <int NC, int PREC>
 __global__ void k_spinor_pack(Geom g, int p, const double *__restrict__ can, void *packed)
 {
-    using T = typename PrecTraits<PREC>::T;
+    using T = double; // the canonical side is FP64; the layout code converts
     long long n = (long long)g.vh << g.lrhs;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -178,7 +157,7 @@ __global__ void k_spinor_pack(Geom g, int p, const double *__restrict__ can, voi
 template <int NC, int PREC>
 __global__ void k_spinor_unpack(Geom g, int p, const void *packed, double *__restrict__ can)
 {
-    using T = typename PrecTraits<PREC>::T;
+    using T = double; // the canonical side is FP64; the layout code converts
     long long n = (long long)g.vh << g.lrhs;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -251,18 +230,22 @@ __global__ void k_gauge_convert(Geom g, const void *src, void *dst)
     if (MAT) {
         for (int e = 0; e < 9; ++e) {
             size_t idx = (slot * 9 + e) * 32 + lane;
-            double v = ((const double *)src)[idx];
-            if (PD == kF32) ((float *)dst)[idx] = (float)v;
-            else ((__half *)dst)[idx] = __float2half_rn((float)v);
+            float2 w = ((const float2 *)src)[idx];
+            float v = __fadd_rn(w.x, w.y);
+            if (PD == kF32) ((float *)dst)[idx] = v;
+            else ((__half *)dst)[idx] = __float2half_rn(v);
         }
     } else {
-        const double2 *q = (const double2 *)src;
-        double2 w0 = q[(slot * 2 + 0) * 32 + lane], w1 = q[(slot * 2 + 1) * 32 + lane];
+        // FP64 packed links are double-float pairs: hi float4 then lo float4
+        const float4 *q = (const float4 *)src;
+        float4 hi = q[(slot * 2 + 0) * 32 + lane], lo = q[(slot * 2 + 1) * 32 + lane];
+        float4 w0 = make_float4(__fadd_rn(hi.x, lo.x), __fadd_rn(hi.y, lo.y), __fadd_rn(hi.z, lo.z),
+                                __fadd_rn(hi.w, lo.w));
         if (PD == kF32) {
-            ((float4 *)dst)[slot * 32 + lane] = make_float4((float)w0.x, (float)w0.y, (float)w1.x, (float)w1.y);
+            ((float4 *)dst)[slot * 32 + lane] = w0;
         } else {
-            __half2 h0 = __floats2half2_rn((float)w0.x, (float)w0.y);
-            __half2 h1 = __floats2half2_rn((float)w1.x, (float)w1.y);
+            __half2 h0 = __floats2half2_rn(w0.x, w0.y);
+            __half2 h1 = __floats2half2_rn(w0.z, w0.w);
             uint2 w;
             w.x = *reinterpret_cast<uint32_t *>(&h0);
             w.y = *reinterpret_cast<uint32_t *>(&h1);

@@ -22,7 +22,7 @@ struct HopArgs {
     const void *in;
     const void *aux;
     void *out;
-    double alpha, beta;
+    coef2 alpha, beta;
     int g5_in, g5_out;
     int fin;
     RedSlot red;
@@ -89,7 +89,10 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a)
     const Geom &g = a.g;
     const int nv = g.vh << g.lrhs;
     const int stride = gridDim.x * blockDim.x;
-    double red = 0.0;
+    const T be = Real<T>::from_coef(a.beta);
+    const T bu = a.g5_out ? -be : be;
+    const T al = Real<T>::from_coef(a.alpha);
+    SqAcc<T> red;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
         const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
         SiteNb nb;
@@ -104,12 +107,9 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a)
         hop_dir<2, REP, PREC>(a, i, rr, nb, acc);
         hop_dir<3, REP, PREC>(a, i, rr, nb, acc);
         // epilogue: out = alpha * aux + beta * g5^{g5_out} acc
-        const T be = (T)a.beta;
-        const T bu = a.g5_out ? -be : be;
         cpx<T> o[4][NC];
         if (a.aux) {
             load_spinor<NC, PREC>(a.aux, g.nblk_s, j, o);
-            const T al = (T)a.alpha;
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -131,14 +131,16 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a)
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    red += (double)o[s][c].re * (double)o[s][c].re + (double)o[s][c].im * (double)o[s][c].im;
+                for (int c = 0; c < NC; ++c) {
+                    red.add(o[s][c].re);
+                    red.add(o[s][c].im);
+                }
         }
     }
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -170,8 +172,8 @@ hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLau
     a.in = L.in;
     a.aux = L.aux;
     a.out = L.out;
-    a.alpha = L.alpha;
-    a.beta = L.beta;
+    a.alpha = make_coef(L.alpha);
+    a.beta = make_coef(L.beta);
     a.g5_in = L.g5_in;
     a.g5_out = L.g5_out;
     a.fin = L.fin;

@@ -15,19 +15,23 @@
 // array-of-structure-of-arrays in blocks of 32 virtual sites: one 16-byte
 // vector v of site j sits at vector index ((j/32)*NVEC + v)*32 + j%32, so a
 // warp reading one vector of 32 consecutive sites reads 512 contiguous bytes.
-//   spinor FP64: NVEC = 4*NC double2 (one complex each)
+//   spinor FP64: NVEC = 4*NC float4 (one complex each, as the double-float
+//                pairs (re.h, im.h, re.l, im.l): 8 bytes per real like binary64)
 //   spinor FP32: NVEC = 2*NC float4  (two complex each)
 //   spinor FP16: NVEC = NC   uint4   (four complex each, binary16), followed by
 //                one float scale per site (the site's max |component|)
 //   gauge (quaternion links): link (p, mu, i) in slot L = (p*4+mu)*nblk + i/32,
-//     FP64 two double2 at (L*2+v)*32 + i%32, FP32 one float4, FP16 one uint2
-//   gauge HR_ADJ_MAT: 9 reals R_ab at (L*9 + 3a+b)*32 + i%32
+//     FP64 two float4 (the four hi parts, then the four lo parts) at
+//     (L*2+v)*32 + i%32, FP32 one float4, FP16 one uint2
+//   gauge HR_ADJ_MAT: 9 reals R_ab at (L*9 + 3a+b)*32 + i%32 (FP64: float2 h, l)
 // where nblk = ceil(V_h/32) for the gauge and ceil(V_h*N/32) for spinors.
 #pragma once
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "hirep_gb300.h"
 
@@ -40,6 +44,25 @@ template <int REP> struct RepTraits { static constexpr int NC = (REP == kRepFund
 
 // ---------------------------------------------------------------- geometry
 
+// Division by a launch-invariant divisor d as a multiply and a shift:
+// q = (n * m) >> s with m = ceil(2^(31+l) / d), 2^l >= d, exact for 0 <= n < 2^31
+// (the rounding error n (m d - 2^(31+l)) / 2^(31+l) d stays below 1/d).
+struct FastDiv {
+    unsigned m;
+    int s;
+};
+inline FastDiv make_fastdiv(unsigned d)
+{
+    int l = 0;
+    while ((1u << l) < d) ++l;
+    unsigned long long m = ((1ULL << (31 + l)) + d - 1) / d;
+    FastDiv f;
+    f.m = (unsigned)m;
+    f.s = 31 + l;
+    return f;
+}
+__device__ __forceinline__ int fdiv(int n, FastDiv f) { return (int)(((unsigned long long)(unsigned)n * f.m) >> f.s); }
+
 struct Geom {
     int d[4];   // T, L1, L2, L3
     int h3;     // L3 / 2
@@ -48,6 +71,7 @@ struct Geom {
     int lrhs;   // log2(nrhs)
     int nblk_g; // 32-site blocks of the gauge (per parity and direction)
     int nblk_s; // 32-virtual-site blocks of a spinor field of one parity
+    FastDiv div_h3, div_d2, div_d1;
 };
 
 inline Geom make_geom(const hr_lattice &lat, int nrhs)
@@ -63,6 +87,9 @@ inline Geom make_geom(const hr_lattice &lat, int nrhs)
     g.lrhs = l;
     g.nblk_g = (g.vh + 31) / 32;
     g.nblk_s = (int)(((long long)g.vh * nrhs + 31) / 32);
+    g.div_h3 = make_fastdiv((unsigned)(g.h3 > 0 ? g.h3 : 1));
+    g.div_d2 = make_fastdiv((unsigned)(g.d[2] > 0 ? g.d[2] : 1));
+    g.div_d1 = make_fastdiv((unsigned)(g.d[1] > 0 ? g.d[1] : 1));
     return g;
 }
 
@@ -75,12 +102,12 @@ struct SiteNb {
 __device__ __forceinline__ void site_neighbours(const Geom &g, int i, int p, SiteNb &nb)
 {
     const int h3 = g.h3;
-    int k = i % h3;
-    int row = i / h3;
-    int x2 = row % g.d[2];
-    int r1 = row / g.d[2];
-    int x1 = r1 % g.d[1];
-    int x0 = r1 / g.d[1];
+    int row = fdiv(i, g.div_h3);
+    int k = i - row * h3;
+    int r1 = fdiv(row, g.div_d2);
+    int x2 = row - r1 * g.d[2];
+    int x0 = fdiv(r1, g.div_d1);
+    int x1 = r1 - x0 * g.d[1];
     int odd3 = (x0 + x1 + x2 + p) & 1; // x3 = 2k + odd3
     // direction 3 (fastest): stays in the row, wraps within it
     int base = row * h3;
@@ -99,12 +126,12 @@ __device__ __forceinline__ void site_neighbours(const Geom &g, int i, int p, Sit
 // lexicographic index of the site with even-odd index i and parity p
 __device__ __forceinline__ long long eo_to_lex(const Geom &g, int i, int p)
 {
-    int k = i % g.h3;
-    int row = i / g.h3;
-    int x2 = row % g.d[2];
-    int r1 = row / g.d[2];
-    int x1 = r1 % g.d[1];
-    int x0 = r1 / g.d[1];
+    int row = fdiv(i, g.div_h3);
+    int k = i - row * g.h3;
+    int r1 = fdiv(row, g.div_d2);
+    int x2 = row - r1 * g.d[2];
+    int x0 = fdiv(r1, g.div_d1);
+    int x1 = r1 - x0 * g.d[1];
     int odd3 = (x0 + x1 + x2 + p) & 1;
     return (long long)row * g.d[3] + 2 * k + odd3;
 }
@@ -121,10 +148,133 @@ template <class T> __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { 
 template <class T> __device__ __forceinline__ cpx<T> cadd_i(cpx<T> a, cpx<T> b) { return {a.re - b.im, a.im + b.re}; }
 template <class T> __device__ __forceinline__ cpx<T> csub_i(cpx<T> a, cpx<T> b) { return {a.re + b.im, a.im - b.re}; }
 
+// ---------------------------------------------------------------- double-float
+// FP64-accuracy arithmetic on the FP32 pipes (GB300 executes FP64 FMA at about
+// 1/60 of the FP32 rate).  A value is the unevaluated sum h + l of two floats
+// (Dekker 1971); sums use Knuth's TwoSum, products the FMA-based TwoProduct.
+// Results are kept unnormalised inside a kernel (|l| stays of the order of
+// 2^-24 times the operands) and renormalised with TwoSum before they are
+// stored, which keeps a relative accuracy of about 2^-47 per operation.
+
+struct dd {
+    float h, l;
+    dd() = default;
+    __host__ __device__ constexpr dd(float h_, float l_) : h(h_), l(l_) {}
+    __host__ __device__ constexpr dd(float x) : h(x), l(0.f) {}
+};
+
+__device__ __forceinline__ dd two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float v = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+    return dd(s, e);
+}
+__device__ __forceinline__ dd dd_norm(dd a) { return two_sum(a.h, a.l); }
+__device__ __forceinline__ dd operator+(dd a, dd b)
+{
+    dd s = two_sum(a.h, b.h);
+    s.l = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    return s;
+}
+__device__ __forceinline__ dd operator-(dd a) { return dd(-a.h, -a.l); }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__device__ __forceinline__ dd operator*(dd a, dd b)
+{
+    float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return dd(p, e);
+}
+__device__ __forceinline__ dd operator*(float a, dd b)
+{
+    float p = __fmul_rn(a, b.h);
+    float e = __fmaf_rn(a, b.h, -p);
+    e = __fmaf_rn(a, b.l, e);
+    return dd(p, e);
+}
+__device__ __forceinline__ dd &operator+=(dd &a, dd b) { return a = a + b; }
+__device__ __forceinline__ dd &operator-=(dd &a, dd b) { return a = a - b; }
+// conversions through the FP64 unit: only outside hot loops
+__device__ __forceinline__ dd dd_from_double(double x)
+{
+    float h = __double2float_rn(x);
+    return dd(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double dd_to_double(dd a) { return (double)a.h + (double)a.l; }
+
+// A double-precision scalar split on the host into two floats, so kernels get
+// launch constants in any of their arithmetic types without FP64 conversions.
+struct coef2 {
+    float h, l;
+};
+inline coef2 make_coef(double x)
+{
+    coef2 c;
+    c.h = (float)x;
+    c.l = (float)(x - (double)c.h);
+    return c;
+}
+
+template <class T> struct Real;
+template <> struct Real<float> {
+    __device__ static float from_coef(coef2 c) { return c.h; }
+    __device__ static float from_double(double x) { return (float)x; }
+    __device__ static float from_float(float x) { return x; }
+    __device__ static double to_double(float x) { return (double)x; }
+    __device__ static float to_float(float x) { return x; }
+    __device__ static dd to_dd(float x) { return dd(x); }
+};
+template <> struct Real<double> {
+    __device__ static double from_coef(coef2 c) { return (double)c.h + (double)c.l; }
+    __device__ static double from_double(double x) { return x; }
+    __device__ static double from_float(float x) { return (double)x; }
+    __device__ static double to_double(double x) { return x; }
+    __device__ static float to_float(double x) { return (float)x; }
+    __device__ static dd to_dd(double x) { return dd_from_double(x); }
+};
+template <> struct Real<dd> {
+    __device__ static dd from_coef(coef2 c) { return dd(c.h, c.l); }
+    __device__ static dd from_double(double x) { return dd_from_double(x); }
+    __device__ static dd from_float(float x) { return dd(x); }
+    __device__ static double to_double(dd x) { return dd_to_double(x); }
+    __device__ static float to_float(dd x) { return __fadd_rn(x.h, x.l); }
+    __device__ static dd to_dd(dd x) { return dd_norm(x); }
+};
+
+// Accumulator of sums of squares with the precision of T, finished in double.
+template <class T> struct SqAcc;
+template <> struct SqAcc<float> {
+    float s = 0.f;
+    __device__ void add(float x) { s = __fmaf_rn(x, x, s); }
+    __device__ double get() const { return (double)s; }
+};
+template <> struct SqAcc<double> {
+    double s = 0.0;
+    __device__ void add(double x) { s += x * x; }
+    __device__ double get() const { return s; }
+};
+template <> struct SqAcc<dd> {
+    dd s = dd(0.f);
+    __device__ void add(dd x)
+    {
+        // renormalise first: after cancellation (a residual near convergence)
+        // |l| may exceed |h|, and h^2 + 2hl without l^2 could then be negative
+        x = dd_norm(x);
+        float p = __fmul_rn(x.h, x.h);
+        float e = __fmaf_rn(x.h, x.h, -p);
+        e = __fmaf_rn(__fadd_rn(x.h, x.h), x.l, e);
+        s += dd(p, e);
+    }
+    __device__ double get() const { return dd_to_double(s); }
+};
+
 // ---------------------------------------------------------------- layouts
 
 template <int PREC> struct PrecTraits;
-template <> struct PrecTraits<kF64> { using T = double; static constexpr int W = 2; };
+// FP64 fields are stored as double-float pairs: 8 bytes per real, like binary64
+template <> struct PrecTraits<kF64> { using T = dd; static constexpr int W = 2; };
 template <> struct PrecTraits<kF32> { using T = float; static constexpr int W = 4; };
 template <> struct PrecTraits<kF16> { using T = float; static constexpr int W = 8; };
 
@@ -152,20 +302,26 @@ __device__ __forceinline__ void load_spinor(const void *base, int nblk, int j, c
     constexpr int NV = L::NVEC;
     cpx<T> *flat = &s[0][0];
     if constexpr (PREC == kF64) {
-        const double2 *p = (const double2 *)base;
+        // one complex number per float4: (re.h, im.h, re.l, im.l)
+        const float4 *p = (const float4 *)base;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            double2 w = __ldg(p + vec_index(j, v, NV));
-            flat[v].re = (T)w.x;
-            flat[v].im = (T)w.y;
+            float4 w = __ldg(p + vec_index(j, v, NV));
+            if constexpr (std::is_same<T, dd>::value) {
+                flat[v].re = dd(w.x, w.z);
+                flat[v].im = dd(w.y, w.w);
+            } else {
+                flat[v].re = Real<T>::from_double(dd_to_double(dd(w.x, w.z)));
+                flat[v].im = Real<T>::from_double(dd_to_double(dd(w.y, w.w)));
+            }
         }
     } else if constexpr (PREC == kF32) {
         const float4 *p = (const float4 *)base;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             float4 w = __ldg(p + vec_index(j, v, NV));
-            flat[2 * v] = {(T)w.x, (T)w.y};
-            flat[2 * v + 1] = {(T)w.z, (T)w.w};
+            flat[2 * v] = {Real<T>::from_float(w.x), Real<T>::from_float(w.y)};
+            flat[2 * v + 1] = {Real<T>::from_float(w.z), Real<T>::from_float(w.w)};
         }
     } else {
         const uint4 *p = (const uint4 *)base;
@@ -179,7 +335,7 @@ __device__ __forceinline__ void load_spinor(const void *base, int nblk, int j, c
             for (int q = 0; q < 4; ++q) {
                 __half2 h = *reinterpret_cast<__half2 *>(&u[q]);
                 float2 f = __half22float2(h);
-                flat[4 * v + q] = {(T)(f.x * sc), (T)(f.y * sc)};
+                flat[4 * v + q] = {Real<T>::from_float(f.x * sc), Real<T>::from_float(f.y * sc)};
             }
         }
     }
@@ -192,21 +348,31 @@ __device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const 
     constexpr int NV = L::NVEC;
     const cpx<T> *flat = &s[0][0];
     if constexpr (PREC == kF64) {
-        double2 *p = (double2 *)base;
+        float4 *p = (float4 *)base;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) p[vec_index(j, v, NV)] = make_double2((double)flat[v].re, (double)flat[v].im);
+        for (int v = 0; v < NV; ++v) {
+            dd re = Real<T>::to_dd(flat[v].re), im = Real<T>::to_dd(flat[v].im);
+            p[vec_index(j, v, NV)] = make_float4(re.h, im.h, re.l, im.l);
+        }
     } else if constexpr (PREC == kF32) {
         float4 *p = (float4 *)base;
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-            p[vec_index(j, v, NV)] = make_float4((float)flat[2 * v].re, (float)flat[2 * v].im,
-                                                 (float)flat[2 * v + 1].re, (float)flat[2 * v + 1].im);
+            p[vec_index(j, v, NV)] = make_float4(Real<T>::to_float(flat[2 * v].re), Real<T>::to_float(flat[2 * v].im),
+                                                 Real<T>::to_float(flat[2 * v + 1].re),
+                                                 Real<T>::to_float(flat[2 * v + 1].im));
     } else {
         uint4 *p = (uint4 *)base;
         float *nrm = (float *)((char *)base + L::data_bytes(nblk));
+        float f[8 * NC];
+#pragma unroll
+        for (int k = 0; k < 4 * NC; ++k) {
+            f[2 * k] = Real<T>::to_float(flat[k].re);
+            f[2 * k + 1] = Real<T>::to_float(flat[k].im);
+        }
         float m = 0.f;
 #pragma unroll
-        for (int k = 0; k < 4 * NC; ++k) m = fmaxf(m, fmaxf(fabsf((float)flat[k].re), fabsf((float)flat[k].im)));
+        for (int k = 0; k < 8 * NC; ++k) m = fmaxf(m, fabsf(f[k]));
         float inv = m > 0.f ? 1.f / m : 0.f;
         nrm[j] = m;
 #pragma unroll
@@ -214,7 +380,7 @@ __device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const 
             uint32_t u[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                __half2 h = __floats2half2_rn((float)flat[4 * v + q].re * inv, (float)flat[4 * v + q].im * inv);
+                __half2 h = __floats2half2_rn(f[2 * (4 * v + q)] * inv, f[2 * (4 * v + q) + 1] * inv);
                 u[q] = *reinterpret_cast<uint32_t *>(&h);
             }
             p[vec_index(j, v, NV)] = make_uint4(u[0], u[1], u[2], u[3]);
@@ -237,18 +403,52 @@ __device__ __forceinline__ void load_quat(const void *base, int nblk_g, int p, i
     size_t slot = (size_t)(p * 4 + mu) * nblk_g + (i >> 5);
     int lane = i & 31;
     if constexpr (PREC == kF64) {
-        const double2 *q = (const double2 *)base;
-        double2 w0 = __ldg(q + (slot * 2 + 0) * 32 + lane);
-        double2 w1 = __ldg(q + (slot * 2 + 1) * 32 + lane);
-        a[0] = (T)w0.x; a[1] = (T)w0.y; a[2] = (T)w1.x; a[3] = (T)w1.y;
+        // (a0.h, a1.h, a2.h, a3.h) then (a0.l, a1.l, a2.l, a3.l)
+        const float4 *q = (const float4 *)base;
+        float4 hi = __ldg(q + (slot * 2 + 0) * 32 + lane);
+        float4 lo = __ldg(q + (slot * 2 + 1) * 32 + lane);
+        if constexpr (std::is_same<T, dd>::value) {
+            a[0] = dd(hi.x, lo.x); a[1] = dd(hi.y, lo.y); a[2] = dd(hi.z, lo.z); a[3] = dd(hi.w, lo.w);
+        } else {
+            a[0] = Real<T>::from_double(dd_to_double(dd(hi.x, lo.x)));
+            a[1] = Real<T>::from_double(dd_to_double(dd(hi.y, lo.y)));
+            a[2] = Real<T>::from_double(dd_to_double(dd(hi.z, lo.z)));
+            a[3] = Real<T>::from_double(dd_to_double(dd(hi.w, lo.w)));
+        }
     } else if constexpr (PREC == kF32) {
         float4 w = __ldg((const float4 *)base + slot * 32 + lane);
-        a[0] = w.x; a[1] = w.y; a[2] = w.z; a[3] = w.w;
+        a[0] = Real<T>::from_float(w.x); a[1] = Real<T>::from_float(w.y);
+        a[2] = Real<T>::from_float(w.z); a[3] = Real<T>::from_float(w.w);
     } else {
         uint2 w = __ldg((const uint2 *)base + slot * 32 + lane);
         float2 f0 = __half22float2(*reinterpret_cast<__half2 *>(&w.x));
         float2 f1 = __half22float2(*reinterpret_cast<__half2 *>(&w.y));
-        a[0] = f0.x; a[1] = f0.y; a[2] = f1.x; a[3] = f1.y;
+        a[0] = Real<T>::from_float(f0.x); a[1] = Real<T>::from_float(f0.y);
+        a[2] = Real<T>::from_float(f1.x); a[3] = Real<T>::from_float(f1.y);
+    }
+}
+
+// store one quaternion link in the packed layout of PREC (from double: pack kernels)
+template <int PREC>
+__device__ __forceinline__ void store_quat(void *base, int nblk_g, int p, int mu, int i, const double (&a)[4])
+{
+    size_t slot = (size_t)(p * 4 + mu) * nblk_g + (i >> 5);
+    int lane = i & 31;
+    if constexpr (PREC == kF64) {
+        dd d[4];
+        for (int k = 0; k < 4; ++k) d[k] = dd_from_double(a[k]);
+        float4 *q = (float4 *)base;
+        q[(slot * 2 + 0) * 32 + lane] = make_float4(d[0].h, d[1].h, d[2].h, d[3].h);
+        q[(slot * 2 + 1) * 32 + lane] = make_float4(d[0].l, d[1].l, d[2].l, d[3].l);
+    } else if constexpr (PREC == kF32) {
+        ((float4 *)base)[slot * 32 + lane] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
+    } else {
+        __half2 h0 = __floats2half2_rn((float)a[0], (float)a[1]);
+        __half2 h1 = __floats2half2_rn((float)a[2], (float)a[3]);
+        uint2 w;
+        w.x = *reinterpret_cast<uint32_t *>(&h0);
+        w.y = *reinterpret_cast<uint32_t *>(&h1);
+        ((uint2 *)base)[slot * 32 + lane] = w;
     }
 }
 
@@ -269,10 +469,31 @@ __device__ __forceinline__ void load_mat(const void *base, int nblk_g, int p, in
     for (int e = 0; e < 9; ++e) {
         size_t idx = (slot * 9 + e) * 32 + lane;
         T v;
-        if constexpr (PREC == kF64) v = (T)__ldg((const double *)base + idx);
-        else if constexpr (PREC == kF32) v = __ldg((const float *)base + idx);
-        else v = __half2float(((const __half *)base)[idx]);
+        if constexpr (PREC == kF64) {
+            float2 w = __ldg((const float2 *)base + idx);
+            if constexpr (std::is_same<T, dd>::value) v = dd(w.x, w.y);
+            else v = Real<T>::from_double(dd_to_double(dd(w.x, w.y)));
+        } else if constexpr (PREC == kF32) {
+            v = Real<T>::from_float(__ldg((const float *)base + idx));
+        } else {
+            v = Real<T>::from_float(__half2float(((const __half *)base)[idx]));
+        }
         R[e / 3][e % 3] = v;
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_mat_entry(void *base, int nblk_g, int p, int mu, int i, int e, double v)
+{
+    size_t slot = (size_t)(p * 4 + mu) * nblk_g + (i >> 5);
+    size_t idx = (slot * 9 + e) * 32 + (i & 31);
+    if constexpr (PREC == kF64) {
+        dd d = dd_from_double(v);
+        ((float2 *)base)[idx] = make_float2(d.h, d.l);
+    } else if constexpr (PREC == kF32) {
+        ((float *)base)[idx] = (float)v;
+    } else {
+        ((__half *)base)[idx] = __float2half_rn((float)v);
     }
 }
 

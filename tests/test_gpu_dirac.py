@@ -62,7 +62,8 @@ def test_spinor_pack_roundtrip(ctx, rep, prec):
         pk = fields.pack_spinor(ctx, dims, rep, prec, par, d)
         back = fields.unpack_spinor(ctx, dims, rep, prec, par, pk).cpu().numpy()
         mask = np.ones(len(psi), bool) if par == hr.HR_FULL else parity_mask(dims, par)
-        tol = {hr.HR_F64: 0.0, hr.HR_F32: 1e-7, hr.HR_F16: 1e-3}[prec]
+        # FP64 fields are stored as double-float pairs: 48 significant bits (2^-48 = 3.6e-15)
+        tol = {hr.HR_F64: 4e-15, hr.HR_F32: 1e-7, hr.HR_F16: 1e-3}[prec]
         assert rel(back[mask], psi[mask]) <= tol
         assert np.all(back[~mask] == 0)
 
