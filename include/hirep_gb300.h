@@ -221,6 +221,31 @@ hr_status hr_axpy(hr_ctx *ctx, hr_lattice lat, hr_rep rep, double a, const void 
 /* v = g5 v on a packed FP64 field of one parity (in place). */
 hr_status hr_gamma5(hr_ctx *ctx, hr_lattice lat, hr_rep rep, void *v, hr_stream stream);
 
+/* ---------------------------------------------------------------------- */
+/* allocation-free reduction (a library service; the paper has no           */
+/* counterpart)                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* result[r] = |v_r|^2 for the n_rhs packed FP64 spinor fields of one parity
+ * in v (multi-RHS layout when n_rhs > 1), written to the DEVICE array
+ * `result` (n_rhs doubles) asynchronously on `stream`.
+ *
+ * For callers that may not allocate device memory at all -- hr_ctx_create
+ * calls cudaMalloc, so they cannot hold a context -- this call needs neither
+ * a context nor a workspace and calls no allocating routine.  Its scratch (the
+ * block partial sums and a completion counter) is a fixed 256 KiB device
+ * array inside the library, which every GPU that loads the library keeps
+ * until the process exits; it has room for up to 32 right-hand sides.
+ * The first call on a device looks up that array's device address: make it
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (different streams or threads) race and return wrong sums, so
+ * serialise them.  Errors (no message is recorded, there is no context):
+ * n_rhs > 32 -> HR_ERR_WORKSPACE; n_rhs not a power of two, odd or oversized
+ * extents -> HR_ERR_UNSUPPORTED; extent < 2, bad rep, null pointer ->
+ * HR_ERR_INVALID_ARG; a failed launch -> HR_ERR_CUDA. */
+hr_status hr_norm2_noalloc(hr_lattice lat, hr_rep rep, int n_rhs, const void *v, double *result,
+                           hr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,7 @@ EXPORTED = [
     "hr_m0_to_kappa", "hr_gauge_packed_bytes", "hr_spinor_packed_bytes", "hr_gauge_pack",
     "hr_spinor_pack", "hr_spinor_unpack", "hr_dirac_workspace_bytes", "hr_dirac_apply",
     "hr_dirac_eo", "hr_solver_default_opts", "hr_cg_workspace_bytes", "hr_cg_solve", "hr_force",
-    "hr_link_grad", "hr_norm2", "hr_axpy", "hr_gamma5",
+    "hr_link_grad", "hr_norm2", "hr_axpy", "hr_gamma5", "hr_norm2_noalloc",
 ]
 
 
@@ -96,6 +96,7 @@ def lib():
                 "hr_norm2": ([P, LAT, I, P, ctypes.POINTER(D), P], I),
                 "hr_axpy": ([P, LAT, I, D, P, P, P], I),
                 "hr_gamma5": ([P, LAT, I, P, P], I),
+                "hr_norm2_noalloc": ([LAT, I, I, P, P, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -306,3 +307,12 @@ def _vol(dims) -> int:
     for d in dims:
         v *= int(d)
     return v
+
+
+def hr_norm2_noalloc(dims, rep, n_rhs, v, result, stream=None) -> int:
+    """|v_r|^2 into the device tensor ``result`` without a context or any
+    allocation (for callers that may not allocate device memory). Returns the
+    status code; raises nothing."""
+    _need(result, 8 * int(n_rhs), "result")
+    return int(lib().hr_norm2_noalloc(lattice(dims), rep, int(n_rhs), _ptr(v), _ptr(result),
+                                      _stream(stream)))
