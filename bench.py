@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the CG and precision sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-autotune", action="store_true", help="use the default hop launch shape")
     ap.add_argument("--lattice", type=int, default=48,
                     help="L of the L^4 lattice (48 is the benchmark workload; smaller for profiling)")
     ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64",
@@ -226,6 +227,13 @@ def run_ours(args):
     L = hr.lib()
     lat = hr.lattice(dims)
     p_g, p_s, p_d = gauge.data_ptr(), src.data_ptr(), dst.data_ptr()
+    tuned = None
+    if not args.no_autotune:
+        # pick the hop kernel's launch shape for this configuration (untimed set-up)
+        res = hr.hr_autotune_hop(ctx, dims, rep, prec, hr.HR_EVEN, 1, gauge, p_s + half, p_d, reps=20)
+        tuned = {"variant": ["registers", "cp.async staged"][res.variant], "block": res.block,
+                 "tuned_ms": round(res.best_ms, 5), "default_ms": round(res.default_ms, 5),
+                 "shapes_timed": res.candidates}
 
     def step():
         # out_e = D_eo in_o ; out_o = D_oe in_e   (two hop launches)
@@ -284,11 +292,14 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": pname,
+        "dtype": {"f64": "df64", "f32": "f32", "f16": "f16"}[pname],
         "data": "synthetic (Haar-random SU(2) links, Gaussian complex source, Philox seeds 1003/2003)",
         "config": {
             "workload": f"even-odd Wilson-Dirac hop pair D_eo+D_oe, {L4}^4 SU(2) fundamental, {pname.upper()}",
             "lattice": list(dims), "rep": "fund", "prec": pname,
+            "arithmetic": ("double-float: each real an unevaluated pair of fp32 (hi + lo), TwoSum/"
+                           "TwoProduct on the FP32 pipes, ~2^-48 relative" if pname == "f64" else pname),
+            "launch": tuned,
             "bytes_per_site": bytes_site,
             "byte_convention": "compulsory (1 spinor in + 1 out + 8 quaternion links)",
             "neighbour_counted_gbs": round(value * neighbour_bytes_per_site("fund", pname) / bytes_site, 2),
@@ -416,7 +427,60 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
         for k in ("mixed_f32", "mixed_f16"):
             cg[k]["speedup_vs_fp64"] = round(cg["fp64"]["seconds_median"] / cg[k]["seconds_median"], 3)
     out["cg_32"] = cg
+    del gauge, bp
+    torch.cuda.empty_cache()
+    out["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
     return out
+
+
+def run_multi_rhs(ctx, torch, hr, fields, synth):
+    """24^4 fundamental: N_rhs Gaussian sources sharing one smeared gauge field,
+    FP32-inner / FP64-outer CG to 1e-10, and the FP32 multi-RHS hop's GB/s."""
+    d = (24, 24, 24, 24)
+    Vh = int(np.prod(d)) // 2
+    q, nsm, plaq = synth.ape_smear_to_plaquette(synth.haar_links(d, 1004), d, 0.6)
+    gauge = fields.pack_gauge(ctx, d, hr.HR_FUND, hr.HR_F64, fields.gauge_to_device(q))
+    g32 = fields.pack_gauge(ctx, d, hr.HR_FUND, hr.HR_F32, fields.gauge_to_device(q))
+    res = {"lattice": list(d), "m0": -0.2, "tol": 1e-10, "plaquette": round(plaq, 4), "inner": "f32"}
+    t1 = None
+    for n in (1, 4, 8, 16, 32):
+        bs = synth.gaussian_spinor(d, 2, 2004, n_rhs=n)
+        dev = fields.spinor_to_device(bs if n > 1 else bs[0])
+        bp = fields.pack_spinor(ctx, d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, dev)
+        opts = hr.hr_solver_default_opts()
+        opts.inner_prec = hr.HR_F32
+        opts.n_rhs = n
+        work = fields.empty_bytes(hr.hr_cg_workspace_bytes(d, hr.HR_FUND, opts))
+        times = []
+        info = rc = None
+        for _ in range(3):
+            xp = fields.zeros_spinor(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, n)
+            rc, info = hr.hr_cg_solve(ctx, d, -0.2, hr.HR_FUND, opts, gauge, bp, xp, work)
+            times.append(info.seconds)
+        t = statistics.median(times)
+        if n == 1:
+            t1 = t
+        # multi-RHS FP32 hop: each link load serves n spinors
+        src = fields.pack_spinor(ctx, d, hr.HR_FUND, hr.HR_F32, hr.HR_ODD, dev)
+        dst = fields.empty_spinor(d, hr.HR_FUND, hr.HR_F32, hr.HR_EVEN, n)
+        for _ in range(3):
+            hr.hr_dirac_eo(ctx, d, 0.0, hr.HR_FUND, hr.HR_F32, hr.HR_EVEN, hr.HR_OP_HOP, n, g32, src, dst)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(50):
+            hr.hr_dirac_eo(ctx, d, 0.0, hr.HR_FUND, hr.HR_F32, hr.HR_EVEN, hr.HR_OP_HOP, n, g32, src, dst)
+        e1.record()
+        torch.cuda.synchronize()
+        hop_ms = e0.elapsed_time(e1) / 50
+        hop_bytes = Vh * (n * 2 * 64 + 8 * 16)  # n spinors in and out, links once
+        res[f"n{n}"] = {"status": hr.STATUS_NAMES.get(rc, rc), "solve_s": round(t, 4),
+                        "per_rhs_s": round(t / n, 5), "per_rhs_speedup_vs_n1": round(t1 / (t / n), 3),
+                        "iters": info.iters, "true_rel_residual": info.true_rel_residual,
+                        "hop_ms": round(hop_ms, 5), "hop_gbs": round(hop_bytes / (hop_ms * 1e-3) / 1e9, 1)}
+        del work, bp, src, dst, dev
+        torch.cuda.empty_cache()
+    return res
 
 
 def cpu_baseline(q, psi, dims):

@@ -208,6 +208,34 @@ hr_status hr_link_grad(hr_ctx *ctx, hr_lattice lat, const void *a_full, const vo
                        double beta, double *grad, hr_stream stream);
 
 /* ---------------------------------------------------------------------- */
+/* autotuning of the hop kernel's launch shape                              */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int variant;       /* 0: operands loaded into registers, 1: cp.async staged in shared memory */
+    int block;         /* threads per block                                               */
+    double best_ms;    /* mean time of one hop launch with the chosen shape               */
+    double default_ms; /* the same for the shape in use before tuning                     */
+    int candidates;    /* shapes timed                                                    */
+} hr_tune_result;
+
+/* Time every kernel variant and block size for the hop of this configuration
+ * (rep, prec, extents, n_rhs) on the caller's buffers -- `out` (parity
+ * out_parity) is overwritten with D_{p,1-p} in, `reps` timed launches per
+ * shape -- and use the fastest for all later hop launches of the
+ * configuration on this context (operators and solvers included).  If the
+ * environment variable HR_AUTOTUNE_CACHE names a file, the choice is written
+ * there as JSON and read back by later contexts.  Synchronises the stream.
+ * (The paper measures a hand-tuned kernel, Sec. 3; tuning per shape is this
+ * library's way to reach the bandwidth bound on each lattice.) */
+hr_status hr_autotune_hop(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity out_parity,
+                          int n_rhs, const void *gauge, const void *in, void *out, int reps,
+                          hr_tune_result *result, hr_stream stream);
+/* The launch shape the context uses now for this configuration. */
+hr_status hr_tune_lookup(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, int n_rhs, int *variant,
+                         int *block);
+
+/* ---------------------------------------------------------------------- */
 /* vector utilities on packed FP64 spinors (n vectors of one parity)        */
 /* ---------------------------------------------------------------------- */
 

@@ -312,10 +312,11 @@ hr_status hr_ctx_create(hr_ctx **out, int device)
         hr_ctx_destroy(ctx);
         return HR_ERR_CUDA;
     }
-    const char *tune = getenv("HR_AUTOTUNE");
-    ctx->autotune = tune && tune[0] == '1';
     const char *path = getenv("HR_AUTOTUNE_CACHE");
-    if (path) ctx->tune_cache_path = path;
+    if (path && path[0]) {
+        ctx->tune_cache_path = path;
+        tune_cache_load(ctx);
+    }
     *out = ctx;
     return HR_OK;
 }

@@ -2,13 +2,25 @@
 // D_eo / D_oe, the Schur complement Mhat, Mhat^+, Mhat^+ Mhat and the full D.
 //
 // One thread per output (virtual) site.  For each of the 8 directions the
-// thread loads the neighbour spinor (128-bit loads, AoSoA blocks of 32 sites),
-// projects it to a half spinor with (1 -/+ g_mu), multiplies both spin
+// thread takes the neighbour spinor (16-byte vectors, AoSoA blocks of 32
+// sites), projects it to a half spinor with (1 -/+ g_mu), multiplies both spin
 // components by the link rebuilt in registers from its quaternion (or by the
 // stored 3x3 adjoint matrix), and adds the two rebuilt spin pairs into the
 // accumulator.  The periodic wrap is resolved in the neighbour index; there is
 // no halo.  The epilogue forms out = alpha*aux + beta*[g5] H [g5] in and, when
 // asked, reduces |out|^2 per right-hand side (fused CG reduction).
+//
+// Two variants of the same arithmetic:
+//   k_hop        loads each direction's operands straight into registers;
+//   k_hop_staged copies direction k+1's spinor and link into shared memory with
+//                cp.async while direction k is computed (double buffer, one
+//                thread's own slots, no block barrier), so memory latency
+//                overlaps the arithmetic without costing registers.
+// The autotuner (hr_autotune) picks variant and block size per configuration.
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
 #include "hr_host.h"
 
 using namespace hr;
@@ -23,6 +35,7 @@ struct HopArgs {
     const void *aux;
     void *out;
     coef2 alpha, beta;
+    int beta_pow2; // beta is a power of two and there is no aux: exact scaling
     int g5_in, g5_out;
     int fin;
     RedSlot red;
@@ -31,12 +44,14 @@ struct HopArgs {
     const double *done; // skip all work when *done != 0 (solver converged)
 };
 
-template <int MU, bool FWD, int REP, int PREC, class T, int NC>
-__device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int link_par, int j_nb, bool neg_upper,
-                                         cpx<T> (&acc)[4][NC])
+__device__ __forceinline__ dd mul_pow2(dd x, float s) { return dd(x.h * s, x.l * s); }
+__device__ __forceinline__ float mul_pow2(float x, float s) { return x * s; }
+
+// projection, colour multiplication and accumulation of one direction
+template <int MU, bool FWD, int REP, class T, int NC, class LINK>
+__device__ __forceinline__ void hop_compute(cpx<T> (&s)[4][NC], const LINK &link, bool neg_upper,
+                                            cpx<T> (&acc)[4][NC])
 {
-    cpx<T> s[4][NC];
-    load_spinor<NC, PREC>(a.in, a.g.nblk_s, j_nb, s);
     if (neg_upper) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -47,10 +62,25 @@ __device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int li
     cpx<T> h[2][NC], r[2][NC];
     spin_project<MU, FWD>(s, h);
     if constexpr (REP == kRepFund) {
+        su2_mul<!FWD>(link, h[0], r[0]);
+        su2_mul<!FWD>(link, h[1], r[1]);
+    } else {
+        so3_mul<!FWD>(link, h[0], r[0]);
+        so3_mul<!FWD>(link, h[1], r[1]);
+    }
+    spin_accumulate<MU, FWD>(acc, r);
+}
+
+template <int MU, bool FWD, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int link_par, int j_nb, bool neg_upper,
+                                         cpx<T> (&acc)[4][NC])
+{
+    cpx<T> s[4][NC];
+    load_spinor<NC, PREC>(a.in, a.g.nblk_s, j_nb, s);
+    if constexpr (REP == kRepFund) {
         T q[4];
         load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
-        su2_mul<!FWD>(q, h[0], r[0]);
-        su2_mul<!FWD>(q, h[1], r[1]);
+        hop_compute<MU, FWD, REP>(s, q, neg_upper, acc);
     } else {
         T R[3][3];
         if constexpr (REP == kRepAdj) {
@@ -60,10 +90,8 @@ __device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int li
         } else {
             load_mat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, R);
         }
-        so3_mul<!FWD>(R, h[0], r[0]);
-        so3_mul<!FWD>(R, h[1], r[1]);
+        hop_compute<MU, FWD, REP>(s, R, neg_upper, acc);
     }
-    spin_accumulate<MU, FWD>(acc, r);
 }
 
 template <int MU, int REP, int PREC, class T, int NC>
@@ -76,16 +104,59 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, int rr, const S
     hop_term<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, a.g5_in != 0, acc);
 }
 
+// out = alpha * aux + beta * g5^{g5_out} acc, stored; |out|^2 into red
+template <int PREC, class T, int NC>
+__device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<T> (&acc)[4][NC], T al, T be, T bu,
+                                             SqAcc<T> &red)
+{
+    cpx<T> o[4][NC];
+    if (a.aux) {
+        load_spinor<NC, PREC>(a.aux, a.g.nblk_s, j, o);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                T b = s < 2 ? bu : be;
+                o[s][c] = {al * o[s][c].re + b * acc[s][c].re, al * o[s][c].im + b * acc[s][c].im};
+            }
+    } else if (a.beta_pow2) {
+        const float bh = a.g5_out ? -a.beta.h : a.beta.h;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float b = s < 2 ? bh : a.beta.h;
+                o[s][c] = {mul_pow2(acc[s][c].re, b), mul_pow2(acc[s][c].im, b)};
+            }
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                T b = s < 2 ? bu : be;
+                o[s][c] = {b * acc[s][c].re, b * acc[s][c].im};
+            }
+    }
+    store_spinor<NC, PREC>(a.out, a.g.nblk_s, j, o);
+    if (a.fin) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                red.add(o[s][c].re);
+                red.add(o[s][c].im);
+            }
+    }
+}
+
 template <int REP, int PREC>
 __global__ void __launch_bounds__(256) k_hop(HopArgs a)
 {
     using T = typename PrecTraits<PREC>::T;
     constexpr int NC = RepTraits<REP>::NC;
-    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) {
-        // nothing to do; a reducing launch still has to leave the counter clean,
-        // which it does because no block reaches the reduction
-        return;
-    }
+    // nothing to do (gated off, or the solver converged); a reducing launch
+    // leaves its counter clean because no block reaches the reduction
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
     const Geom &g = a.g;
     const int nv = g.vh << g.lrhs;
     const int stride = gridDim.x * blockDim.x;
@@ -106,36 +177,7 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a)
         hop_dir<1, REP, PREC>(a, i, rr, nb, acc);
         hop_dir<2, REP, PREC>(a, i, rr, nb, acc);
         hop_dir<3, REP, PREC>(a, i, rr, nb, acc);
-        // epilogue: out = alpha * aux + beta * g5^{g5_out} acc
-        cpx<T> o[4][NC];
-        if (a.aux) {
-            load_spinor<NC, PREC>(a.aux, g.nblk_s, j, o);
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    T b = s < 2 ? bu : be;
-                    o[s][c] = {al * o[s][c].re + b * acc[s][c].re, al * o[s][c].im + b * acc[s][c].im};
-                }
-        } else {
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    T b = s < 2 ? bu : be;
-                    o[s][c] = {b * acc[s][c].re, b * acc[s][c].im};
-                }
-        }
-        store_spinor<NC, PREC>(a.out, g.nblk_s, j, o);
-        if (a.fin) {
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    red.add(o[s][c].re);
-                    red.add(o[s][c].im);
-                }
-        }
+        hop_epilogue<PREC>(a, j, acc, al, be, bu, red);
     }
     if (a.fin) {
         __shared__ double smem[32 * 32];
@@ -144,26 +186,197 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a)
     }
 }
 
+// ---------------------------------------------------------------- staged variant
+
+template <int REP, int PREC> struct Stage {
+    static constexpr int NC = RepTraits<REP>::NC;
+    static constexpr int NV = SpinorLayout<NC, PREC>::NVEC;
+    static constexpr int NQ = QuatSlots<PREC>::n;
+    static constexpr int NSLOT = NV + NQ + (PREC == kF16 ? 1 : 0); // 16-byte slots per direction
+    static size_t smem_bytes(int block) { return (size_t)2 * NSLOT * block * 16; }
+};
+
+// direction K = 2 mu + (0 forward, 1 backward): queue its operands' copies
+template <int K, int REP, int PREC>
+__device__ __forceinline__ void stage_issue(const HopArgs &a, int i, int rr, const SiteNb &nb, uint4 *buf, int bd)
+{
+    using S = Stage<REP, PREC>;
+    constexpr int MU = K >> 1;
+    constexpr bool FWD = (K & 1) == 0;
+    const int jn = ((FWD ? nb.fwd[MU] : nb.bwd[MU]) << a.g.lrhs) + rr;
+    const int site_link = FWD ? i : nb.bwd[MU];
+    const int link_par = FWD ? a.p : 1 - a.p;
+    const uint4 *src = (const uint4 *)a.in;
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) cp_async16(buf + v * bd, src + vec_index(jn, v, S::NV));
+#pragma unroll
+    for (int v = 0; v < S::NQ; ++v) {
+        const void *q = quat_addr<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, v);
+        if constexpr (PREC == kF16) cp_async8(buf + (S::NV + v) * bd, q);
+        else cp_async16(buf + (S::NV + v) * bd, q);
+    }
+    if constexpr (PREC == kF16) {
+        const float *nrm = (const float *)((const char *)a.in + SpinorLayout<S::NC, PREC>::data_bytes(a.g.nblk_s));
+        cp_async4(buf + (S::NV + S::NQ) * bd, nrm + jn);
+    }
+}
+
+template <int K, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void stage_compute(const HopArgs &a, const uint4 *buf, int bd, cpx<T> (&acc)[4][NC])
+{
+    using S = Stage<REP, PREC>;
+    constexpr int MU = K >> 1;
+    constexpr bool FWD = (K & 1) == 0;
+    uint4 w[S::NV];
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) w[v] = buf[v * bd];
+    float sc = 1.f;
+    if constexpr (PREC == kF16) sc = *reinterpret_cast<const float *>(buf + (S::NV + S::NQ) * bd);
+    cpx<T> s[4][NC];
+    spinor_from_vecs<NC, PREC>(w, sc, s);
+    uint4 qv[S::NQ];
+#pragma unroll
+    for (int v = 0; v < S::NQ; ++v) qv[v] = buf[(S::NV + v) * bd];
+    T q[4];
+    quat_from_vecs<PREC>(qv, q);
+    if constexpr (REP == kRepFund) {
+        hop_compute<MU, FWD, REP>(s, q, a.g5_in != 0, acc);
+    } else {
+        T R[3][3];
+        quat_to_adj(q, R);
+        hop_compute<MU, FWD, REP>(s, R, a.g5_in != 0, acc);
+    }
+}
+
+// one pipeline step: queue direction K+1 into the other buffer, wait for K, compute K
+template <int K, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void stage_step(const HopArgs &a, int i, int rr, const SiteNb &nb, uint4 *b0, uint4 *b1,
+                                           int bd, cpx<T> (&acc)[4][NC])
+{
+    uint4 *cur = (K & 1) ? b1 : b0;
+    uint4 *nxt = (K & 1) ? b0 : b1;
+    if constexpr (K < 7) {
+        stage_issue<K + 1, REP, PREC>(a, i, rr, nb, nxt, bd);
+        cp_async_commit();
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
+    stage_compute<K, REP, PREC>(a, cur, bd, acc);
+}
+
 template <int REP, int PREC>
-hr_status launch_t(hr_ctx *ctx, const Geom &g, const HopArgs &a, cudaStream_t s)
+__global__ void __launch_bounds__(256) k_hop_staged(HopArgs a)
+{
+    using T = typename PrecTraits<PREC>::T;
+    using S = Stage<REP, PREC>;
+    constexpr int NC = S::NC;
+    extern __shared__ uint4 stage_mem[];
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const int bd = blockDim.x;
+    // this thread's slots: [buffer][slot][thread], consecutive threads -> consecutive 16 B
+    uint4 *b0 = stage_mem + threadIdx.x;
+    uint4 *b1 = stage_mem + S::NSLOT * bd + threadIdx.x;
+    const T be = Real<T>::from_coef(a.beta);
+    const T bu = a.g5_out ? -be : be;
+    const T al = Real<T>::from_coef(a.alpha);
+    SqAcc<T> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        stage_issue<0, REP, PREC>(a, i, rr, nb, b0, bd);
+        cp_async_commit();
+        cpx<T> acc[4][NC];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[s][c] = {T(0), T(0)};
+        stage_step<0, REP, PREC>(a, i, rr, nb, b0, b1, bd, acc);
+        stage_step<1, REP, PREC>(a, i, rr, nb, b0, b1, bd, acc);
+        stage_step<2, REP, PREC>(a, i, rr, nb, b0, b1, bd, acc);
+        stage_step<3, REP, PREC>(a, i, rr, nb, b0, b1, bd, acc);
+        stage_step<4, REP, PREC>(a, i, rr, nb, b0, b1, bd, acc);
+        stage_step<5, REP, PREC>(a, i, rr, nb, b0, b1, bd, acc);
+        stage_step<6, REP, PREC>(a, i, rr, nb, b0, b1, bd, acc);
+        stage_step<7, REP, PREC>(a, i, rr, nb, b0, b1, bd, acc);
+        hop_epilogue<PREC>(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+// ---------------------------------------------------------------- launch
+
+constexpr int kVarSimple = 0, kVarStaged = 1;
+
+template <int REP, int PREC> constexpr bool has_staged() { return REP != kRepAdjMat; }
+
+// default choice before (or without) autotuning
+inline HopChoice default_choice(int rep, int prec)
+{
+    HopChoice c;
+    c.variant = (rep != HR_ADJ_MAT && prec == kF64) ? kVarStaged : kVarSimple;
+    c.block = 128;
+    return c;
+}
+
+template <int REP, int PREC>
+hr_status launch_t(hr_ctx *ctx, const Geom &g, const HopArgs &a, HopChoice c, cudaStream_t s)
 {
     const long long nv = (long long)g.vh << g.lrhs;
-    int bs = 128;
-    auto it = ctx->tuned_block.find("hop");
-    if (it != ctx->tuned_block.end()) bs = it->second;
     // non-reducing launches cover all sites; reducing ones are capped so the
     // per-block partials fit the context's scratch
     int cap = a.fin ? kMaxBlocks : (1 << 30);
-    int grid = grid_for(nv, bs, cap);
-    k_hop<REP, PREC><<<grid, bs, 0, s>>>(a);
+    int grid = grid_for(nv, c.block, cap);
+    if constexpr (has_staged<REP, PREC>()) {
+        if (c.variant == kVarStaged) {
+            size_t sm = Stage<REP, PREC>::smem_bytes(c.block);
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaFuncSetAttribute(k_hop_staged<REP, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Stage<REP, PREC>::smem_bytes(256));
+                attr_set = true;
+            }
+            k_hop_staged<REP, PREC><<<grid, c.block, sm, s>>>(a);
+            return check_launch(ctx, "staged hop kernel");
+        }
+    }
+    k_hop<REP, PREC><<<grid, c.block, 0, s>>>(a);
     return check_launch(ctx, "hop kernel");
 }
 
-} // namespace
+hr_status dispatch(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs &a, HopChoice c, cudaStream_t s)
+{
+    switch (rep * 3 + prec) {
+    case 0: return launch_t<kRepFund, kF64>(ctx, g, a, c, s);
+    case 1: return launch_t<kRepFund, kF32>(ctx, g, a, c, s);
+    case 2: return launch_t<kRepFund, kF16>(ctx, g, a, c, s);
+    case 3: return launch_t<kRepAdj, kF64>(ctx, g, a, c, s);
+    case 4: return launch_t<kRepAdj, kF32>(ctx, g, a, c, s);
+    case 5: return launch_t<kRepAdj, kF16>(ctx, g, a, c, s);
+    case 6: return launch_t<kRepAdjMat, kF64>(ctx, g, a, c, s);
+    case 7: return launch_t<kRepAdjMat, kF32>(ctx, g, a, c, s);
+    case 8: return launch_t<kRepAdjMat, kF16>(ctx, g, a, c, s);
+    }
+    return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+}
 
-namespace hr {
+bool is_pow2(double x)
+{
+    if (!(x != 0.0)) return false;
+    int e;
+    double m = std::frexp(std::fabs(x), &e);
+    return m == 0.5;
+}
 
-hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, cudaStream_t s)
+HopArgs make_args(hr_ctx *ctx, const Geom &g, const HopLaunch &L)
 {
     HopArgs a;
     a.g = g;
@@ -174,6 +387,7 @@ hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLau
     a.out = L.out;
     a.alpha = make_coef(L.alpha);
     a.beta = make_coef(L.beta);
+    a.beta_pow2 = (!L.aux && is_pow2(L.beta)) ? 1 : 0;
     a.g5_in = L.g5_in;
     a.g5_out = L.g5_out;
     a.fin = L.fin;
@@ -181,18 +395,42 @@ hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLau
     a.scal = ctx->d_scal;
     a.gate = L.gate;
     a.done = L.done;
-    switch (rep * 3 + prec) {
-    case 0: return launch_t<kRepFund, kF64>(ctx, g, a, s);
-    case 1: return launch_t<kRepFund, kF32>(ctx, g, a, s);
-    case 2: return launch_t<kRepFund, kF16>(ctx, g, a, s);
-    case 3: return launch_t<kRepAdj, kF64>(ctx, g, a, s);
-    case 4: return launch_t<kRepAdj, kF32>(ctx, g, a, s);
-    case 5: return launch_t<kRepAdj, kF16>(ctx, g, a, s);
-    case 6: return launch_t<kRepAdjMat, kF64>(ctx, g, a, s);
-    case 7: return launch_t<kRepAdjMat, kF32>(ctx, g, a, s);
-    case 8: return launch_t<kRepAdjMat, kF16>(ctx, g, a, s);
-    }
-    return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+    return a;
+}
+
+} // namespace
+
+namespace hr {
+
+std::string tune_key(const Geom &g, int rep, int prec)
+{
+    char buf[128];
+    snprintf(buf, sizeof buf, "hop:r%d:p%d:%dx%dx%dx%d:n%d", rep, prec, g.d[0], g.d[1], g.d[2], g.d[3], g.nrhs);
+    return buf;
+}
+
+HopChoice hop_choice(hr_ctx *ctx, const Geom &g, int rep, int prec)
+{
+    auto it = ctx->tuned.find(tune_key(g, rep, prec));
+    if (it != ctx->tuned.end()) return it->second;
+    return default_choice(rep, prec);
+}
+
+hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, cudaStream_t s)
+{
+    return dispatch(ctx, g, rep, prec, make_args(ctx, g, L), hop_choice(ctx, g, rep, prec), s);
+}
+
+hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, HopChoice c,
+                          cudaStream_t s)
+{
+    return dispatch(ctx, g, rep, prec, make_args(ctx, g, L), c, s);
+}
+
+bool hop_variant_available(int rep, int prec, int variant)
+{
+    (void)prec;
+    return variant == kVarSimple || (variant == kVarStaged && rep != HR_ADJ_MAT);
 }
 
 // Even-site operators from two hops each:

@@ -19,6 +19,11 @@ constexpr int kMaxRhs = 32;
 constexpr int kNumCounters = 64;
 constexpr int kScalDoubles = 64 * kMaxRhs;
 
+// launch shape of the hop kernel chosen by the autotuner
+struct HopChoice {
+    int variant; // 0: registers only, 1: cp.async staged
+    int block;   // threads per block
+};
 } // namespace hr
 
 struct hr_ctx {
@@ -30,9 +35,8 @@ struct hr_ctx {
     double *d_scal = nullptr;      // kScalDoubles
     double *h_scal = nullptr;      // pinned mirror
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    std::map<std::string, int> tuned_block; // autotuner: key -> threads per block
-    std::string tune_cache_path;
-    bool autotune = false;
+    std::map<std::string, hr::HopChoice> tuned; // autotuner: configuration key -> launch shape
+    std::string tune_cache_path;                // JSON cache (HR_AUTOTUNE_CACHE), "" = none
 };
 
 namespace hr {
@@ -80,6 +84,14 @@ struct HopLaunch {
     const double *done;    // skip the launch's work when *done != 0 (nullable)
 };
 hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, cudaStream_t s);
+hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, HopChoice c,
+                          cudaStream_t s);
+HopChoice hop_choice(hr_ctx *ctx, const Geom &g, int rep, int prec);
+std::string tune_key(const Geom &g, int rep, int prec);
+bool hop_variant_available(int rep, int prec, int variant);
+// autotuner cache file (hr_tune.cu)
+void tune_cache_load(hr_ctx *ctx);
+bool tune_cache_save(hr_ctx *ctx);
 // out = op(in) on even sites, work = odd temporary (+ even temporary for NORMAL)
 hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, int op, const void *gauge,
                       const void *in, void *out, void *work_odd, void *work_even, int fin_schur,

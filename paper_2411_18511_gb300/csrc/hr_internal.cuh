@@ -388,6 +388,41 @@ __device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const 
     }
 }
 
+// Decode the NV raw 16-byte vectors of one packed site (plus the FP16 scale)
+// into values: the same conversion as load_spinor, for data staged in shared
+// memory.
+template <int NC, int PREC, class T>
+__device__ __forceinline__ void spinor_from_vecs(const uint4 *w, float sc, cpx<T> (&s)[4][NC])
+{
+    constexpr int NV = SpinorLayout<NC, PREC>::NVEC;
+    cpx<T> *flat = &s[0][0];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const uint4 u = w[v];
+        if constexpr (PREC == kF64) {
+            float4 f = *reinterpret_cast<const float4 *>(&u);
+            if constexpr (std::is_same<T, dd>::value) {
+                flat[v].re = dd(f.x, f.z);
+                flat[v].im = dd(f.y, f.w);
+            } else {
+                flat[v].re = Real<T>::from_double(dd_to_double(dd(f.x, f.z)));
+                flat[v].im = Real<T>::from_double(dd_to_double(dd(f.y, f.w)));
+            }
+        } else if constexpr (PREC == kF32) {
+            float4 f = *reinterpret_cast<const float4 *>(&u);
+            flat[2 * v] = {Real<T>::from_float(f.x), Real<T>::from_float(f.y)};
+            flat[2 * v + 1] = {Real<T>::from_float(f.z), Real<T>::from_float(f.w)};
+        } else {
+            uint32_t q4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&q4[q]));
+                flat[4 * v + q] = {Real<T>::from_float(f.x * sc), Real<T>::from_float(f.y * sc)};
+            }
+        }
+    }
+}
+
 // Gauge: quaternion links
 template <int PREC> struct GaugeQuat {
     static size_t bytes(int nblk_g)
@@ -451,6 +486,70 @@ __device__ __forceinline__ void store_quat(void *base, int nblk_g, int p, int mu
         ((uint2 *)base)[slot * 32 + lane] = w;
     }
 }
+
+// quaternion link from its raw vectors (FP64: hi then lo float4; FP32: one
+// float4; FP16: the first 8 bytes)
+template <int PREC, class T>
+__device__ __forceinline__ void quat_from_vecs(const uint4 *w, T (&a)[4])
+{
+    if constexpr (PREC == kF64) {
+        float4 hi = *reinterpret_cast<const float4 *>(&w[0]);
+        float4 lo = *reinterpret_cast<const float4 *>(&w[1]);
+        if constexpr (std::is_same<T, dd>::value) {
+            a[0] = dd(hi.x, lo.x); a[1] = dd(hi.y, lo.y); a[2] = dd(hi.z, lo.z); a[3] = dd(hi.w, lo.w);
+        } else {
+            a[0] = Real<T>::from_double(dd_to_double(dd(hi.x, lo.x)));
+            a[1] = Real<T>::from_double(dd_to_double(dd(hi.y, lo.y)));
+            a[2] = Real<T>::from_double(dd_to_double(dd(hi.z, lo.z)));
+            a[3] = Real<T>::from_double(dd_to_double(dd(hi.w, lo.w)));
+        }
+    } else if constexpr (PREC == kF32) {
+        float4 f = *reinterpret_cast<const float4 *>(&w[0]);
+        a[0] = Real<T>::from_float(f.x); a[1] = Real<T>::from_float(f.y);
+        a[2] = Real<T>::from_float(f.z); a[3] = Real<T>::from_float(f.w);
+    } else {
+        uint32_t x = w[0].x, y = w[0].y;
+        float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&x));
+        float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&y));
+        a[0] = Real<T>::from_float(f0.x); a[1] = Real<T>::from_float(f0.y);
+        a[2] = Real<T>::from_float(f1.x); a[3] = Real<T>::from_float(f1.y);
+    }
+}
+
+// number of 16-byte staging slots a quaternion link takes
+template <int PREC> struct QuatSlots { static constexpr int n = (PREC == kF64) ? 2 : 1; };
+
+// global address of quaternion vector v (FP16: an 8-byte element)
+template <int PREC>
+__device__ __forceinline__ const void *quat_addr(const void *base, int nblk_g, int p, int mu, int i, int v)
+{
+    size_t slot = (size_t)(p * 4 + mu) * nblk_g + (i >> 5);
+    int lane = i & 31;
+    if constexpr (PREC == kF64) return (const uint4 *)base + (slot * 2 + v) * 32 + lane;
+    else if constexpr (PREC == kF32) return (const uint4 *)base + slot * 32 + lane;
+    else return (const uint2 *)base + slot * 32 + lane;
+}
+
+// ---------------------------------------------------------------- async copies
+// cp.async global -> shared (Ampere and later, sm_103a included): the copy runs
+// in the background; commit_group / wait_group order a thread's own copies.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int PREC> struct GaugeMat {
     static size_t bytes(int nblk_g)

@@ -1,0 +1,156 @@
+// hr_tune.cu -- autotuner for the launch shape of the hop kernel.
+//
+// For one configuration (representation, precision, lattice extents, number of
+// right-hand sides) it times every available kernel variant (registers-only or
+// cp.async-staged) at several block sizes with CUDA events on the caller's own
+// buffers, keeps the fastest, and uses it for every later hop launch of that
+// configuration on the context (Mhat, Mhat^+ Mhat and the CG solvers included).
+// Choices persist across processes in a small JSON file named by the
+// environment variable HR_AUTOTUNE_CACHE: {"<key>": [variant, block], ...}.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hr_host.h"
+
+using namespace hr;
+
+namespace hr {
+
+void tune_cache_load(hr_ctx *ctx)
+{
+    FILE *f = fopen(ctx->tune_cache_path.c_str(), "r");
+    if (!f) return;
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, n);
+    fclose(f);
+    // tolerant scan of "key": [v, b] pairs
+    size_t pos = 0;
+    while (true) {
+        size_t q0 = txt.find('"', pos);
+        if (q0 == std::string::npos) break;
+        size_t q1 = txt.find('"', q0 + 1);
+        if (q1 == std::string::npos) break;
+        std::string key = txt.substr(q0 + 1, q1 - q0 - 1);
+        size_t br = txt.find('[', q1);
+        if (br == std::string::npos) break;
+        int v = -1, b = -1;
+        if (sscanf(txt.c_str() + br, "[%d , %d]", &v, &b) == 2 && (v == 0 || v == 1) && b >= 32 && b <= 1024 &&
+            (b % 32) == 0 && key.rfind("hop:", 0) == 0) {
+            HopChoice c;
+            c.variant = v;
+            c.block = b;
+            ctx->tuned[key] = c;
+        }
+        pos = txt.find(']', br);
+        if (pos == std::string::npos) break;
+    }
+}
+
+bool tune_cache_save(hr_ctx *ctx)
+{
+    if (ctx->tune_cache_path.empty()) return true;
+    std::string tmp = ctx->tune_cache_path + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fprintf(f, "{\n");
+    size_t k = 0;
+    for (const auto &kv : ctx->tuned) {
+        fprintf(f, "  \"%s\": [%d, %d]%s\n", kv.first.c_str(), kv.second.variant, kv.second.block,
+                (++k < ctx->tuned.size()) ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    return rename(tmp.c_str(), ctx->tune_cache_path.c_str()) == 0;
+}
+
+} // namespace hr
+
+extern "C" {
+
+hr_status hr_autotune_hop(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity out_parity, int n_rhs,
+                          const void *gauge, const void *in, void *out, int reps, hr_tune_result *result,
+                          hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (result) std::memset(result, 0, sizeof *result);
+    if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+    hr_status st = validate_lattice(ctx, lat, n_rhs);
+    if (st) return st;
+    if (out_parity != HR_EVEN && out_parity != HR_ODD) return set_error(ctx, HR_ERR_INVALID_ARG, "bad parity");
+    if (!gauge || !in || !out || in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "bad field pointers");
+    if (reps < 1 || reps > 10000) return set_error(ctx, HR_ERR_INVALID_ARG, "reps must lie in [1, 10000]");
+    Geom g = make_geom(lat, n_rhs);
+    cudaStream_t s = (cudaStream_t)stream;
+    HopLaunch L{};
+    L.p = out_parity;
+    L.gauge = gauge;
+    L.in = in;
+    L.out = out;
+    L.beta = -0.5;
+    const int blocks[] = {64, 128, 192, 256};
+    HopChoice best{-1, 0}, def = hop_choice(ctx, g, rep, prec);
+    float best_ms = 1e30f, def_ms = -1.f;
+    // the default shape first, so its time is measured in the same conditions
+    std::vector<HopChoice> cands;
+    cands.push_back(def);
+    for (int v = 0; v < 2; ++v) {
+        if (!hop_variant_available(rep, prec, v)) continue;
+        for (int b : blocks) {
+            if (v == def.variant && b == def.block) continue;
+            cands.push_back(HopChoice{v, b});
+        }
+    }
+    for (size_t k = 0; k < cands.size(); ++k) {
+        const HopChoice c = cands[k];
+        for (int w = 0; w < 2; ++w) {
+            st = launch_hop_with(ctx, g, rep, prec, L, c, s);
+            if (st) return st;
+        }
+        cudaError_t e = cudaEventRecord(ctx->ev0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            st = launch_hop_with(ctx, g, rep, prec, L, c, s);
+            if (st) return st;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+        ms /= reps;
+        if (k == 0) def_ms = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    ctx->tuned[tune_key(g, rep, prec)] = best;
+    if (!tune_cache_save(ctx))
+        return set_error(ctx, HR_ERR_INVALID_ARG, "cannot write the autotune cache %s", ctx->tune_cache_path.c_str());
+    if (result) {
+        result->variant = best.variant;
+        result->block = best.block;
+        result->best_ms = best_ms;
+        result->default_ms = def_ms;
+        result->candidates = (int)cands.size();
+    }
+    return HR_OK;
+}
+
+hr_status hr_tune_lookup(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, int n_rhs, int *variant, int *block)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep) || !valid_prec(prec) || !variant || !block)
+        return set_error(ctx, HR_ERR_INVALID_ARG, "bad arguments");
+    hr_status st = validate_lattice(ctx, lat, n_rhs);
+    if (st) return st;
+    HopChoice c = hop_choice(ctx, make_geom(lat, n_rhs), rep, prec);
+    *variant = c.variant;
+    *block = c.block;
+    return HR_OK;
+}
+
+} // extern "C"

@@ -34,7 +34,8 @@ EXPORTED = [
     "hr_m0_to_kappa", "hr_gauge_packed_bytes", "hr_spinor_packed_bytes", "hr_gauge_pack",
     "hr_spinor_pack", "hr_spinor_unpack", "hr_dirac_workspace_bytes", "hr_dirac_apply",
     "hr_dirac_eo", "hr_solver_default_opts", "hr_cg_workspace_bytes", "hr_cg_solve", "hr_force",
-    "hr_link_grad", "hr_norm2", "hr_axpy", "hr_gamma5", "hr_norm2_noalloc",
+    "hr_link_grad", "hr_norm2", "hr_axpy", "hr_gamma5", "hr_norm2_noalloc", "hr_autotune_hop",
+    "hr_tune_lookup",
 ]
 
 
@@ -52,6 +53,11 @@ class hr_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner_prec", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("n_rhs", ctypes.c_int),
                 ("x0_is_guess", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class hr_tune_result(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("block", ctypes.c_int), ("best_ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 
 class hr_solve_info(ctypes.Structure):
@@ -97,6 +103,8 @@ def lib():
                 "hr_axpy": ([P, LAT, I, D, P, P, P], I),
                 "hr_gamma5": ([P, LAT, I, P, P], I),
                 "hr_norm2_noalloc": ([LAT, I, I, P, P, P], I),
+                "hr_autotune_hop": ([P, LAT, I, I, I, I, P, P, P, I, ctypes.POINTER(hr_tune_result), P], I),
+                "hr_tune_lookup": ([P, LAT, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -316,3 +324,21 @@ def hr_norm2_noalloc(dims, rep, n_rhs, v, result, stream=None) -> int:
     _need(result, 8 * int(n_rhs), "result")
     return int(lib().hr_norm2_noalloc(lattice(dims), rep, int(n_rhs), _ptr(v), _ptr(result),
                                       _stream(stream)))
+
+
+def hr_autotune_hop(ctx: Context, dims, rep, prec, out_parity, n_rhs, gauge, inp, out, reps=20,
+                    stream=None) -> hr_tune_result:
+    half = hr_spinor_packed_bytes(dims, rep, prec, HR_EVEN, n_rhs)
+    _need(inp, half, "in")
+    _need(out, half, "out")
+    res = hr_tune_result()
+    ctx.check(lib().hr_autotune_hop(ctx.handle, lattice(dims), rep, prec, out_parity, n_rhs, _ptr(gauge),
+                                    _ptr(inp), _ptr(out), int(reps), ctypes.byref(res), _stream(stream)))
+    return res
+
+
+def hr_tune_lookup(ctx: Context, dims, rep, prec, n_rhs=1):
+    v, b = ctypes.c_int(-1), ctypes.c_int(-1)
+    ctx.check(lib().hr_tune_lookup(ctx.handle, lattice(dims), rep, prec, n_rhs, ctypes.byref(v),
+                                   ctypes.byref(b)))
+    return v.value, b.value

@@ -105,9 +105,45 @@ def quat_conj(a: np.ndarray) -> np.ndarray:
     return out
 
 
-def _grid(q: np.ndarray, dims) -> np.ndarray:
+def _soa(q: np.ndarray, dims) -> np.ndarray:
+    """(4, V, 4) links -> (4 mu, 4 comp, T, L1, L2, L3), components contiguous."""
     t, l1, l2, l3 = dims
-    return q.reshape(4, t, l1, l2, l3, 4)
+    return np.ascontiguousarray(np.moveaxis(q.reshape(4, t, l1, l2, l3, 4), -1, 1))
+
+
+def _aos(u: np.ndarray, dims) -> np.ndarray:
+    return np.ascontiguousarray(np.moveaxis(u, 1, -1)).reshape(4, lattice_volume(dims), 4)
+
+
+def _qmul(a, b, conj_a=False, conj_b=False):
+    """Quaternion (SU(2)) product on component-major arrays (4, ...)."""
+    a0, a1, a2, a3 = a[0], a[1], a[2], a[3]
+    b0, b1, b2, b3 = b[0], b[1], b[2], b[3]
+    if conj_a:
+        a1, a2, a3 = -a1, -a2, -a3
+    if conj_b:
+        b1, b2, b3 = -b1, -b2, -b3
+    out = np.empty(np.broadcast_shapes(a.shape, b.shape))
+    out[0] = a0 * b0 - a1 * b1 - a2 * b2 - a3 * b3
+    out[1] = a0 * b1 + b0 * a1 - (a2 * b3 - a3 * b2)
+    out[2] = a0 * b2 + b0 * a2 - (a3 * b1 - a1 * b3)
+    out[3] = a0 * b3 + b0 * a3 - (a1 * b2 - a2 * b1)
+    return out
+
+
+def _shift(x, axis, step):
+    """x(y + step * axis-hat) for component-major fields (lattice axes start at 1)."""
+    return np.roll(x, -step, axis=axis + 1)
+
+
+def _plaquette_soa(u) -> float:
+    acc = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            p = _qmul(u[mu], _shift(u[nu], mu, 1))
+            p = _qmul(p, _shift(u[mu], nu, 1), conj_b=True)
+            acc += float(np.sum(_qmul(p, u[nu], conj_b=True)[0]))
+    return acc / (6.0 * u[0, 0].size)
 
 
 def mean_plaquette(q: np.ndarray, dims) -> float:
@@ -115,37 +151,31 @@ def mean_plaquette(q: np.ndarray, dims) -> float:
 
     For a quaternion, (1/2) Re tr U = a0.
     """
-    u = _grid(q, dims)
-    acc = 0.0
-    for mu in range(4):
-        for nu in range(mu + 1, 4):
-            p = quat_mul(u[mu], np.roll(u[nu], -1, axis=mu))
-            p = quat_mul(p, quat_conj(np.roll(u[mu], -1, axis=nu)))
-            p = quat_mul(p, quat_conj(u[nu]))
-            acc += float(np.sum(p[..., 0]))
-    return acc / (6.0 * lattice_volume(dims))
+    return _plaquette_soa(_soa(q, dims))
 
 
-def _ape_step(q: np.ndarray, dims, alpha: float) -> np.ndarray:
-    u = _grid(q, dims)
-    new = np.empty_like(u)
+def _staples(u):
+    """Sum over nu != mu of the forward and backward staples of every link."""
+    st = np.zeros_like(u)
     for mu in range(4):
-        staple = np.zeros_like(u[mu])
         for nu in range(4):
             if nu == mu:
                 continue
-            # forward staple U_nu(x) U_mu(x+nu) U_nu(x+mu)^+
-            s = quat_mul(u[nu], np.roll(u[mu], -1, axis=nu))
-            staple += quat_mul(s, quat_conj(np.roll(u[nu], -1, axis=mu)))
-            # backward staple U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu)
-            unm = np.roll(u[nu], 1, axis=nu)
-            s = quat_mul(quat_conj(unm), np.roll(u[mu], 1, axis=nu))
-            staple += quat_mul(s, np.roll(unm, -1, axis=mu))
-        w = (1.0 - alpha) * u[mu] + (alpha / 6.0) * staple
-        # a real combination of SU(2) elements is a real multiple of one:
-        # projecting back onto SU(2) is normalising the quaternion
-        new[mu] = w / np.linalg.norm(w, axis=-1, keepdims=True)
-    return new.reshape(q.shape)
+            # forward: U_nu(x) U_mu(x+nu) U_nu(x+mu)^+
+            s = _qmul(u[nu], _shift(u[mu], nu, 1))
+            st[mu] += _qmul(s, _shift(u[nu], mu, 1), conj_b=True)
+            # backward: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu)
+            unm = _shift(u[nu], nu, -1)
+            s = _qmul(unm, _shift(u[mu], nu, -1), conj_a=True)
+            st[mu] += _qmul(s, _shift(unm, mu, 1))
+    return st
+
+
+def _ape_mix(u, st, alpha):
+    # a real combination of SU(2) elements is a real multiple of one:
+    # projecting back onto SU(2) is normalising the quaternion
+    w = (1.0 - alpha) * u + (alpha / 6.0) * st
+    return w / np.sqrt(np.sum(w * w, axis=1, keepdims=True))
 
 
 def ape_smear_to_plaquette(q: np.ndarray, dims, target: float = 0.6,
@@ -156,27 +186,29 @@ def ape_smear_to_plaquette(q: np.ndarray, dims, target: float = 0.6,
     within 1e-3 of ``target`` instead of overshooting it.  Returns
     ``(q_smeared, n_steps, plaquette)``.
     """
-    cur = q.copy()
-    p = mean_plaquette(cur, dims)
+    u = _soa(q, dims)
+    p = _plaquette_soa(u)
     steps = 0
     while p < target and steps < max_steps:
-        nxt = _ape_step(cur, dims, alpha)
-        pn = mean_plaquette(nxt, dims)
+        st = _staples(u)
+        nxt = _ape_mix(u, st, alpha)
+        pn = _plaquette_soa(nxt)
         steps += 1
         if pn <= target + 1e-3:
-            cur, p = nxt, pn
+            u, p = nxt, pn
             continue
         lo, hi = 0.0, alpha
+        trial, pt = nxt, pn
         for _ in range(40):
             mid = 0.5 * (lo + hi)
-            trial = _ape_step(cur, dims, mid)
-            pt = mean_plaquette(trial, dims)
+            trial = _ape_mix(u, st, mid)
+            pt = _plaquette_soa(trial)
             if abs(pt - target) < 1e-3:
                 break
             if pt < target:
                 lo = mid
             else:
                 hi = mid
-        cur, p = trial, pt
+        u, p = trial, pt
         break
-    return cur, steps, p
+    return _aos(u, dims), steps, p

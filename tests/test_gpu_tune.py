@@ -1,0 +1,103 @@
+"""The hop autotuner and both kernel variants (registers-only and cp.async
+staged), checked against the oracle for every shape the tuner may choose."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2411_18511_gb300 import hr, fields  # noqa: E402
+
+TOL = {hr.HR_F64: 1e-13, hr.HR_F32: 1e-6, hr.HR_F16: 4e-3}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return hr.Context(0)
+
+
+def hop_error(ctx, dims, rep, prec, seed=5):
+    nc = 2 if rep == hr.HR_FUND else 3
+    q = synth.haar_links(dims, seed)
+    psi = synth.gaussian_spinor(dims, nc, seed + 1)
+    L = oracle.expand_links(dims, nc, q)
+    gauge = fields.pack_gauge(ctx, dims, rep, prec, fields.gauge_to_device(q))
+    src = fields.pack_spinor(ctx, dims, rep, prec, hr.HR_ODD, fields.spinor_to_device(psi))
+    dst = fields.empty_spinor(dims, rep, prec, hr.HR_EVEN)
+    hr.hr_dirac_eo(ctx, dims, 0.0, rep, prec, hr.HR_EVEN, hr.HR_OP_HOP, 1, gauge, src, dst)
+    got = fields.unpack_spinor(ctx, dims, rep, prec, hr.HR_EVEN, dst).cpu().numpy()
+    even = oracle.parity_mask(dims) == 0
+    pin = psi.copy()
+    pin[even] = 0
+    want = -0.5 * oracle.hop(dims, L, pin, parity=0)
+    return np.linalg.norm(got[even] - want[even]) / np.linalg.norm(want[even])
+
+
+def key(dims, rep, prec, n_rhs=1):
+    return f"hop:r{rep}:p{prec}:{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}:n{n_rhs}"
+
+
+@pytest.mark.parametrize("variant,block", [(0, 64), (0, 256), (1, 64), (1, 192)])
+def test_forced_shapes_from_cache_match_oracle(tmp_path, monkeypatch, variant, block):
+    dims = (6, 4, 2, 6)  # 144 sites per parity: ragged last block of 32
+    cache = tmp_path / "tune.json"
+    entries = {}
+    for rep in (hr.HR_FUND, hr.HR_ADJ):
+        for prec in (hr.HR_F64, hr.HR_F32, hr.HR_F16):
+            entries[key(dims, rep, prec)] = [variant, block]
+    cache.write_text(json.dumps(entries))
+    monkeypatch.setenv("HR_AUTOTUNE_CACHE", str(cache))
+    c = hr.Context(0)
+    for rep in (hr.HR_FUND, hr.HR_ADJ):
+        for prec in (hr.HR_F64, hr.HR_F32, hr.HR_F16):
+            assert hr.hr_tune_lookup(c, dims, rep, prec) == (variant, block)
+            assert hop_error(c, dims, rep, prec) <= TOL[prec], (rep, prec, variant, block)
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [hr.HR_F64, hr.HR_F32])
+@pytest.mark.parametrize("rep", [hr.HR_FUND, hr.HR_ADJ])
+def test_autotune_chooses_and_persists(tmp_path, monkeypatch, rep, prec):
+    dims = (8, 8, 8, 8)
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("HR_AUTOTUNE_CACHE", str(cache))
+    c = hr.Context(0)
+    nc = 2 if rep == hr.HR_FUND else 3
+    q = synth.haar_links(dims, 9)
+    psi = synth.gaussian_spinor(dims, nc, 10)
+    gauge = fields.pack_gauge(c, dims, rep, prec, fields.gauge_to_device(q))
+    src = fields.pack_spinor(c, dims, rep, prec, hr.HR_ODD, fields.spinor_to_device(psi))
+    dst = fields.empty_spinor(dims, rep, prec, hr.HR_EVEN)
+    res = hr.hr_autotune_hop(c, dims, rep, prec, hr.HR_EVEN, 1, gauge, src, dst, reps=5)
+    assert res.variant in (0, 1) and res.block in (64, 128, 192, 256)
+    assert res.candidates >= 4 and 0 < res.best_ms <= res.default_ms
+    assert hr.hr_tune_lookup(c, dims, rep, prec) == (res.variant, res.block)
+    saved = json.loads(cache.read_text())
+    assert saved[key(dims, rep, prec)] == [res.variant, res.block]
+    assert hop_error(c, dims, rep, prec) <= TOL[prec]
+    c.close()
+    c2 = hr.Context(0)
+    assert hr.hr_tune_lookup(c2, dims, rep, prec) == (res.variant, res.block)
+    c2.close()
+
+
+def test_autotune_rejects_bad_arguments(ctx):
+    dims = (4, 4, 4, 4)
+    g = fields.empty_bytes(hr.hr_gauge_packed_bytes(dims, 0, 0))
+    s = fields.empty_spinor(dims, 0, 0, 0)
+    with pytest.raises(hr.HrError):
+        hr.hr_autotune_hop(ctx, dims, 0, 0, hr.HR_FULL, 1, g, s, fields.empty_spinor(dims, 0, 0, 0))
+    with pytest.raises(hr.HrError):
+        hr.hr_autotune_hop(ctx, dims, 0, 0, hr.HR_EVEN, 1, g, s, s)
+    with pytest.raises(hr.HrError):
+        hr.hr_autotune_hop(ctx, dims, 0, 0, hr.HR_EVEN, 1, g, s, fields.empty_spinor(dims, 0, 0, 0), reps=0)
