@@ -430,7 +430,47 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     del gauge, bp
     torch.cuda.empty_cache()
     out["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
+    torch.cuda.empty_cache()
+    out["batch_12"] = run_batch(ctx, torch, hr, fields, synth)
     return out
+
+
+def run_batch(ctx, torch, hr, fields, synth):
+    """12 lattices of 8^4..24^4 (Haar links, own seeds): one batched persistent
+    FP64 CG against the 12 single-lattice solves one after the other."""
+    sizes = [8, 8, 10, 12, 12, 14, 16, 16, 18, 20, 22, 24]
+    dims = [(L,) * 4 for L in sizes]
+    m0 = -0.2
+    gauges, bs = [], []
+    for k, d in enumerate(dims):
+        q = synth.haar_links(d, 1100 + k)
+        b = synth.gaussian_spinor(d, 2, 2100 + k)
+        gauges.append(fields.pack_gauge(ctx, d, hr.HR_FUND, hr.HR_F64, fields.gauge_to_device(q)))
+        bs.append(fields.pack_spinor(ctx, d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, fields.spinor_to_device(b)))
+    opts = hr.hr_solver_default_opts()
+    work = fields.empty_bytes(hr.hr_cg_batch_workspace_bytes(dims, hr.HR_FUND))
+    tb, infos = [], None
+    for _ in range(3):
+        xs = [fields.zeros_spinor(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN) for d in dims]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, infos = hr.hr_cg_solve_batch(ctx, dims, m0, hr.HR_FUND, opts, gauges, bs, xs, work)
+        torch.cuda.synchronize()
+        tb.append(time.perf_counter() - t0)
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, d in enumerate(dims):
+            x = fields.zeros_spinor(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
+            w = fields.empty_bytes(hr.hr_cg_workspace_bytes(d, hr.HR_FUND, opts))
+            hr.hr_cg_solve(ctx, d, m0, hr.HR_FUND, opts, gauges[k], bs[k], x, w)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return {"lattices": sizes, "m0": m0, "tol": opts.tol, "status": hr.STATUS_NAMES.get(rc, rc),
+            "batch_wall_s": round(statistics.median(tb), 4), "sequential_wall_s": round(statistics.median(ts), 4),
+            "speedup": round(statistics.median(ts) / statistics.median(tb), 3),
+            "iters": [i.iters for i in infos], "max_true_rel_residual": max(i.true_rel_residual for i in infos)}
 
 
 def run_multi_rhs(ctx, torch, hr, fields, synth):

@@ -191,6 +191,24 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep,
                       const hr_solver_opts *opts, const void *gauge, const void *b, void *x,
                       hr_solve_info *info, void *work, size_t work_bytes, hr_stream stream);
 
+/* Work bytes of hr_cg_solve_batch for these lattices (0 if invalid). */
+size_t hr_cg_batch_workspace_bytes(int n_lat, const hr_lattice *lats, hr_rep rep);
+
+/* Solve Mhat^+ Mhat x_l = b_l for n_lat (1..64) independent lattices of any
+ * sizes at once (FP64 CG, one RHS each, HR_FUND or HR_ADJ).  The paper notes
+ * that SU(2) lattices below 16^4 lose efficiency to fixed overheads (Sec. 3);
+ * here every CG phase is one persistent launch over a work list of all the
+ * lattices' 128-site tiles, with per-lattice scalars and convergence flags on
+ * the device, and a chunk of iterations replays as one CUDA graph.  gauges[l]:
+ * packed HR_F64 gauge of lats[l]; b[l], x[l]: packed HR_F64 even spinors.
+ * infos[l] (may be NULL) receives each lattice's iterations and true residual
+ * (seconds = the whole batch).  Synchronises the stream.  Returns
+ * HR_ERR_NOT_CONVERGED if any lattice misses tol within maxiter. */
+hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, double m0, hr_rep rep,
+                            const hr_solver_opts *opts, const void *const *gauges, const void *const *b,
+                            void *const *x, hr_solve_info *infos, void *work, size_t work_bytes,
+                            hr_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* link derivatives                                                         */
 /* ---------------------------------------------------------------------- */

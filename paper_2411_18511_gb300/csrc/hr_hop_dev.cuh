@@ -1,0 +1,154 @@
+// hr_hop_dev.cuh -- device code of the Wilson hop shared by the single-lattice
+// kernels (hr_hop.cu) and the batched persistent solver (hr_batch.cu): the launch
+// arguments, one direction's projection / colour multiplication / accumulation,
+// and the epilogue out = alpha aux + beta [g5] H [g5] in with the fused |out|^2.
+#pragma once
+
+#include "hr_host.h"
+
+namespace hr {
+
+struct HopArgs {
+    Geom g;
+    int p;
+    const void *gauge;
+    const void *in;
+    const void *aux;
+    void *out;
+    coef2 alpha, beta;
+    int beta_pow2; // beta is a power of two and there is no aux: exact scaling
+    int g5_in, g5_out;
+    int fin;
+    RedSlot red;
+    double *scal;
+    const double *gate;
+    const double *done; // skip all work when *done != 0 (solver converged)
+};
+
+__device__ __forceinline__ dd mul_pow2(dd x, float s) { return dd(x.h * s, x.l * s); }
+__device__ __forceinline__ float mul_pow2(float x, float s) { return x * s; }
+
+// projection, colour multiplication and accumulation of one direction
+template <int MU, bool FWD, int REP, class T, int NC, class LINK>
+__device__ __forceinline__ void hop_compute(cpx<T> (&s)[4][NC], const LINK &link, bool neg_upper,
+                                            cpx<T> (&acc)[4][NC])
+{
+    if (neg_upper) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            s[0][c] = {-s[0][c].re, -s[0][c].im};
+            s[1][c] = {-s[1][c].re, -s[1][c].im};
+        }
+    }
+    cpx<T> h[2][NC], r[2][NC];
+    spin_project<MU, FWD>(s, h);
+    if constexpr (REP == kRepFund) {
+        su2_mul<!FWD>(link, h[0], r[0]);
+        su2_mul<!FWD>(link, h[1], r[1]);
+    } else {
+        so3_mul<!FWD>(link, h[0], r[0]);
+        so3_mul<!FWD>(link, h[1], r[1]);
+    }
+    spin_accumulate<MU, FWD>(acc, r);
+}
+
+template <int MU, bool FWD, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int link_par, int j_nb, bool neg_upper,
+                                         cpx<T> (&acc)[4][NC])
+{
+    cpx<T> s[4][NC];
+    load_spinor<NC, PREC>(a.in, a.g.nblk_s, j_nb, s);
+    if constexpr (REP == kRepFund) {
+        T q[4];
+        load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+        hop_compute<MU, FWD, REP>(s, q, neg_upper, acc);
+    } else {
+        T R[3][3];
+        if constexpr (REP == kRepAdj) {
+            T q[4];
+            load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+            quat_to_adj(q, R);
+        } else {
+            load_mat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, R);
+        }
+        hop_compute<MU, FWD, REP>(s, R, neg_upper, acc);
+    }
+}
+
+template <int MU, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void hop_dir(const HopArgs &a, int i, int rr, const SiteNb &nb, cpx<T> (&acc)[4][NC])
+{
+    const int l = a.g.lrhs;
+    // forward: (1 - g_mu) U_mu(x) psi(x + mu); the link sits at x (parity p)
+    hop_term<MU, true, REP, PREC>(a, i, a.p, (nb.fwd[MU] << l) + rr, a.g5_in != 0, acc);
+    // backward: (1 + g_mu) U_mu(x - mu)^+ psi(x - mu); the link sits at x - mu (parity 1-p)
+    hop_term<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, a.g5_in != 0, acc);
+}
+
+// out = alpha * aux + beta * g5^{g5_out} acc, stored; |out|^2 into red
+template <int PREC, class T, int NC>
+__device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<T> (&acc)[4][NC], T al, T be, T bu,
+                                             SqAcc<T> &red)
+{
+    cpx<T> o[4][NC];
+    if (a.aux) {
+        load_spinor<NC, PREC>(a.aux, a.g.nblk_s, j, o);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                T b = s < 2 ? bu : be;
+                o[s][c] = {al * o[s][c].re + b * acc[s][c].re, al * o[s][c].im + b * acc[s][c].im};
+            }
+    } else if (a.beta_pow2) {
+        const float bh = a.g5_out ? -a.beta.h : a.beta.h;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float b = s < 2 ? bh : a.beta.h;
+                o[s][c] = {mul_pow2(acc[s][c].re, b), mul_pow2(acc[s][c].im, b)};
+            }
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                T b = s < 2 ? bu : be;
+                o[s][c] = {b * acc[s][c].re, b * acc[s][c].im};
+            }
+    }
+    store_spinor<NC, PREC>(a.out, a.g.nblk_s, j, o);
+    if (a.fin) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                red.add(o[s][c].re);
+                red.add(o[s][c].im);
+            }
+    }
+}
+
+// one output site j (virtual index) of the unrolled hop: all 8 directions and the epilogue
+template <int REP, int PREC, class T>
+__device__ __forceinline__ void hop_site(const HopArgs &a, int j, T al, T be, T bu, SqAcc<T> &red)
+{
+    constexpr int NC = RepTraits<REP>::NC;
+    const Geom &g = a.g;
+    const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+    SiteNb nb;
+    site_neighbours(g, i, a.p, nb);
+    cpx<T> acc[4][NC];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[s][c] = {T(0), T(0)};
+    hop_dir<0, REP, PREC>(a, i, rr, nb, acc);
+    hop_dir<1, REP, PREC>(a, i, rr, nb, acc);
+    hop_dir<2, REP, PREC>(a, i, rr, nb, acc);
+    hop_dir<3, REP, PREC>(a, i, rr, nb, acc);
+    hop_epilogue<PREC>(a, j, acc, al, be, bu, red);
+}
+
+} // namespace hr

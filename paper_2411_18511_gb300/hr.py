@@ -35,7 +35,7 @@ EXPORTED = [
     "hr_spinor_pack", "hr_spinor_unpack", "hr_dirac_workspace_bytes", "hr_dirac_apply",
     "hr_dirac_eo", "hr_solver_default_opts", "hr_cg_workspace_bytes", "hr_cg_solve", "hr_force",
     "hr_link_grad", "hr_norm2", "hr_axpy", "hr_gamma5", "hr_norm2_noalloc", "hr_autotune_hop",
-    "hr_tune_lookup",
+    "hr_tune_lookup", "hr_cg_batch_workspace_bytes", "hr_cg_solve_batch",
 ]
 
 
@@ -103,6 +103,10 @@ def lib():
                 "hr_axpy": ([P, LAT, I, D, P, P, P], I),
                 "hr_gamma5": ([P, LAT, I, P, P], I),
                 "hr_norm2_noalloc": ([LAT, I, I, P, P, P], I),
+                "hr_cg_batch_workspace_bytes": ([I, ctypes.POINTER(LAT), I], S),
+                "hr_cg_solve_batch": ([P, I, ctypes.POINTER(LAT), D, I, ctypes.POINTER(hr_solver_opts),
+                                       ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                       ctypes.POINTER(hr_solve_info), P, S, P], I),
                 "hr_autotune_hop": ([P, LAT, I, I, I, I, P, P, P, I, ctypes.POINTER(hr_tune_result), P], I),
                 "hr_tune_lookup": ([P, LAT, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
             }
@@ -342,3 +346,35 @@ def hr_tune_lookup(ctx: Context, dims, rep, prec, n_rhs=1):
     ctx.check(lib().hr_tune_lookup(ctx.handle, lattice(dims), rep, prec, n_rhs, ctypes.byref(v),
                                    ctypes.byref(b)))
     return v.value, b.value
+
+
+def _lattice_array(dims_list):
+    arr = (hr_lattice * len(dims_list))()
+    for k, d in enumerate(dims_list):
+        arr[k] = lattice(d)
+    return arr
+
+
+def hr_cg_batch_workspace_bytes(dims_list, rep) -> int:
+    return int(lib().hr_cg_batch_workspace_bytes(len(dims_list), _lattice_array(dims_list), rep))
+
+
+def hr_cg_solve_batch(ctx: Context, dims_list, m0, rep, opts: hr_solver_opts, gauges, bs, xs, work,
+                      stream=None, raise_on_error: bool = True):
+    """Batched solve of len(dims_list) lattices; returns (status, [hr_solve_info])."""
+    n = len(dims_list)
+    for k, d in enumerate(dims_list):
+        half = hr_spinor_packed_bytes(d, rep, HR_F64, HR_EVEN, 1)
+        _need(bs[k], half, f"b[{k}]")
+        _need(xs[k], half, f"x[{k}]")
+    P = ctypes.c_void_p
+    garr = (P * n)(*[_ptr(g) for g in gauges])
+    barr = (P * n)(*[_ptr(b) for b in bs])
+    xarr = (P * n)(*[_ptr(x) for x in xs])
+    infos = (hr_solve_info * n)()
+    wb = 0 if work is None else work.numel() * work.element_size()
+    rc = lib().hr_cg_solve_batch(ctx.handle, n, _lattice_array(dims_list), float(m0), rep, ctypes.byref(opts),
+                                 garr, barr, xarr, infos, _ptr(work), wb, _stream(stream))
+    if raise_on_error and rc not in (HR_OK, HR_ERR_NOT_CONVERGED):
+        ctx.check(rc)
+    return rc, list(infos)
