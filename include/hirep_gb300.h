@@ -231,7 +231,10 @@ hr_status hr_link_grad(hr_ctx *ctx, hr_lattice lat, const void *a_full, const vo
 
 typedef struct {
     int variant;       /* 0: unrolled directions, operands in registers; 1: unrolled, cp.async
-                          staged in shared memory; 2: looped directions, registers; 3: looped, staged */
+                          staged in shared memory; 2: generic looped directions, registers;
+                          3: generic looped, staged; 4: loop over mu with switched projections,
+                          registers; 5: switched, staged; 6: unrolled with the next direction's
+                          operands prefetched into registers */
     int block;         /* threads per block                                               */
     double best_ms;    /* mean time of one hop launch with the chosen shape               */
     double default_ms; /* the same for the shape in use before tuning                     */

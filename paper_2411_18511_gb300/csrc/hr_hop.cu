@@ -363,19 +363,242 @@ __global__ void __launch_bounds__(256) k_hop_loop(HopArgs a)
     }
 }
 
+// ---------------------------------------------------------------- switched variants
+// A middle way between the unrolled and the generic kernels: the loop runs over
+// mu; the projection and the reconstruction of each direction are the
+// compile-time code of the unrolled kernel, picked by a uniform switch, while
+// the colour multiplication -- most of the arithmetic -- is compiled once for
+// forward and once for backward directions.  About half the code of the
+// unrolled kernel and none of the generic kernel's selects.
+
+template <bool FWD, class T, int NC>
+__device__ __forceinline__ void sw_project(int mu, const cpx<T> (&s)[4][NC], cpx<T> (&h)[2][NC])
+{
+    switch (mu) {
+    case 0: spin_project<0, FWD>(s, h); break;
+    case 1: spin_project<1, FWD>(s, h); break;
+    case 2: spin_project<2, FWD>(s, h); break;
+    default: spin_project<3, FWD>(s, h); break;
+    }
+}
+
+template <bool FWD, class T, int NC>
+__device__ __forceinline__ void sw_accumulate(int mu, cpx<T> (&acc)[4][NC], const cpx<T> (&r)[2][NC])
+{
+    switch (mu) {
+    case 0: spin_accumulate<0, FWD>(acc, r); break;
+    case 1: spin_accumulate<1, FWD>(acc, r); break;
+    case 2: spin_accumulate<2, FWD>(acc, r); break;
+    default: spin_accumulate<3, FWD>(acc, r); break;
+    }
+}
+
+template <bool FWD, int REP, class T, int NC>
+__device__ __forceinline__ void sw_direction(int mu, cpx<T> (&s)[4][NC], T (&q)[4], bool neg_upper,
+                                             cpx<T> (&acc)[4][NC])
+{
+    if (neg_upper) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            s[0][c] = {-s[0][c].re, -s[0][c].im};
+            s[1][c] = {-s[1][c].re, -s[1][c].im};
+        }
+    }
+    cpx<T> h[2][NC], r[2][NC];
+    sw_project<FWD>(mu, s, h);
+    if constexpr (REP == kRepFund) {
+        su2_mul<!FWD>(q, h[0], r[0]);
+        su2_mul<!FWD>(q, h[1], r[1]);
+    } else {
+        T R[3][3];
+        quat_to_adj(q, R);
+        so3_mul<!FWD>(R, h[0], r[0]);
+        so3_mul<!FWD>(R, h[1], r[1]);
+    }
+    sw_accumulate<FWD>(mu, acc, r);
+}
+
+template <int REP, int PREC, bool STAGED>
+__global__ void __launch_bounds__(256) k_hop_sw(HopArgs a)
+{
+    using T = typename PrecTraits<PREC>::T;
+    using S = Stage<REP, PREC>;
+    constexpr int NC = S::NC;
+    extern __shared__ uint4 stage_mem[];
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const int bd = blockDim.x;
+    uint4 *const buf0 = stage_mem + threadIdx.x;
+    const int buf_step = S::NSLOT * bd;
+    const T be = Real<T>::from_coef(a.beta);
+    const T bu = a.g5_out ? -be : be;
+    const T al = Real<T>::from_coef(a.alpha);
+    SqAcc<T> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        cpx<T> acc[4][NC];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[s][c] = {T(0), T(0)};
+        if constexpr (STAGED) {
+            loop_issue<REP, PREC>(a, nb, i, rr, 0, buf0, bd);
+            cp_async_commit();
+        }
+#pragma unroll 1
+        for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+            for (int fb = 0; fb < 2; ++fb) {
+                const int k = 2 * mu + fb;
+                cpx<T> s[4][NC];
+                T q[4];
+                if constexpr (STAGED) {
+                    if (k < 7) {
+                        loop_issue<REP, PREC>(a, nb, i, rr, k + 1, buf0 + ((k + 1) & 1) * buf_step, bd);
+                        cp_async_commit();
+                        cp_async_wait<1>();
+                    } else {
+                        cp_async_wait<0>();
+                    }
+                    const uint4 *cur = buf0 + (k & 1) * buf_step;
+                    uint4 w[S::NV];
+#pragma unroll
+                    for (int v = 0; v < S::NV; ++v) w[v] = cur[v * bd];
+                    float sc = 1.f;
+                    if constexpr (PREC == kF16) sc = *reinterpret_cast<const float *>(cur + (S::NV + S::NQ) * bd);
+                    spinor_from_vecs<NC, PREC>(w, sc, s);
+                    uint4 qv[S::NQ];
+#pragma unroll
+                    for (int v = 0; v < S::NQ; ++v) qv[v] = cur[(S::NV + v) * bd];
+                    quat_from_vecs<PREC>(qv, q);
+                } else {
+                    int nbr, ls;
+                    dir_sites(nb, i, k, nbr, ls);
+                    load_spinor<NC, PREC>(a.in, g.nblk_s, (nbr << g.lrhs) + rr, s);
+                    load_quat<PREC>(a.gauge, g.nblk_g, fb ? 1 - a.p : a.p, mu, ls, q);
+                }
+                if (fb == 0) sw_direction<true, REP>(mu, s, q, a.g5_in != 0, acc);
+                else sw_direction<false, REP>(mu, s, q, a.g5_in != 0, acc);
+            }
+        }
+        hop_epilogue<PREC>(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+// ---------------------------------------------------------------- prefetching variant
+// Unrolled like k_hop, but the operands of direction k+1 are loaded into a
+// second set of registers before direction k is computed, so every load has a
+// whole direction of arithmetic to arrive in.  Costs registers (two operand
+// sets) and so occupancy; the autotuner decides whether it pays.
+
+template <int K, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void pf_load(const HopArgs &a, int i, int rr, const SiteNb &nb, cpx<T> (&s)[4][NC],
+                                        T (&q)[4], float &sc)
+{
+    constexpr int MU = K >> 1;
+    constexpr bool FWD = (K & 1) == 0;
+    const int nbr = FWD ? nb.fwd[MU] : nb.bwd[MU];
+    load_spinor_raw<NC, PREC>(a.in, a.g.nblk_s, (nbr << a.g.lrhs) + rr, s, sc);
+    load_quat<PREC>(a.gauge, a.g.nblk_g, FWD ? a.p : 1 - a.p, MU, FWD ? i : nb.bwd[MU], q);
+}
+
+template <int K, int REP, int PREC, class T, int NC>
+__device__ __forceinline__ void pf_compute(const HopArgs &a, cpx<T> (&s)[4][NC], T (&q)[4], float sc,
+                                           cpx<T> (&acc)[4][NC])
+{
+    constexpr int MU = K >> 1;
+    constexpr bool FWD = (K & 1) == 0;
+    if constexpr (REP == kRepFund) {
+        if constexpr (PREC == kF16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = q[k] * sc;
+        }
+        hop_compute<MU, FWD, REP>(s, q, a.g5_in != 0, acc);
+    } else {
+        T R[3][3];
+        quat_to_adj(q, R);
+        if constexpr (PREC == kF16) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) R[k / 3][k % 3] = R[k / 3][k % 3] * sc;
+        }
+        hop_compute<MU, FWD, REP>(s, R, a.g5_in != 0, acc);
+    }
+}
+
+template <int REP, int PREC>
+__global__ void __launch_bounds__(256) k_hop_pf(HopArgs a)
+{
+    using T = typename PrecTraits<PREC>::T;
+    constexpr int NC = RepTraits<REP>::NC;
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const T be = Real<T>::from_coef(a.beta);
+    const T bu = a.g5_out ? -be : be;
+    const T al = Real<T>::from_coef(a.alpha);
+    SqAcc<T> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        cpx<T> acc[4][NC];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[s][c] = {T(0), T(0)};
+        cpx<T> sA[4][NC], sB[4][NC];
+        T qA[4], qB[4];
+        float cA, cB;
+        pf_load<0, REP, PREC>(a, i, rr, nb, sA, qA, cA);
+        pf_load<1, REP, PREC>(a, i, rr, nb, sB, qB, cB);
+        pf_compute<0, REP, PREC>(a, sA, qA, cA, acc);
+        pf_load<2, REP, PREC>(a, i, rr, nb, sA, qA, cA);
+        pf_compute<1, REP, PREC>(a, sB, qB, cB, acc);
+        pf_load<3, REP, PREC>(a, i, rr, nb, sB, qB, cB);
+        pf_compute<2, REP, PREC>(a, sA, qA, cA, acc);
+        pf_load<4, REP, PREC>(a, i, rr, nb, sA, qA, cA);
+        pf_compute<3, REP, PREC>(a, sB, qB, cB, acc);
+        pf_load<5, REP, PREC>(a, i, rr, nb, sB, qB, cB);
+        pf_compute<4, REP, PREC>(a, sA, qA, cA, acc);
+        pf_load<6, REP, PREC>(a, i, rr, nb, sA, qA, cA);
+        pf_compute<5, REP, PREC>(a, sB, qB, cB, acc);
+        pf_load<7, REP, PREC>(a, i, rr, nb, sB, qB, cB);
+        pf_compute<6, REP, PREC>(a, sA, qA, cA, acc);
+        pf_compute<7, REP, PREC>(a, sB, qB, cB, acc);
+        hop_epilogue<PREC>(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
 // ---------------------------------------------------------------- launch
 
-constexpr int kVarSimple = 0, kVarStaged = 1, kVarLoop = 2, kVarLoopStaged = 3;
+constexpr int kVarSimple = 0, kVarStaged = 1, kVarLoop = 2, kVarLoopStaged = 3, kVarSwitch = 4,
+              kVarSwitchStaged = 5, kVarPrefetch = 6;
+constexpr int kNumVariants = 7;
 
 template <int REP, int PREC> constexpr bool has_staged() { return REP != kRepAdjMat; }
 
-// default choice before (or without) autotuning: the compact looped kernel
-// for double-float arithmetic, the unrolled one for FP32 / FP16
+// default choice before (or without) autotuning: the unrolled kernel (256
+// threads for double-float, 128 otherwise), the fastest on GB300 without tuning
 inline HopChoice default_choice(int rep, int prec)
 {
     HopChoice c;
-    c.variant = (rep != HR_ADJ_MAT && prec == kF64) ? kVarLoop : kVarSimple;
-    c.block = 128;
+    c.variant = kVarSimple;
+    c.block = (prec == kF64) ? 256 : 128;
     return c;
 }
 
@@ -411,6 +634,23 @@ hr_status launch_t(hr_ctx *ctx, const Geom &g, const HopArgs &a, HopChoice c, cu
             }
             k_hop_loop<REP, PREC, true><<<grid, c.block, sm, s>>>(a);
             return check_launch(ctx, "looped staged hop kernel");
+        }
+        if (c.variant == kVarSwitch) {
+            k_hop_sw<REP, PREC, false><<<grid, c.block, 0, s>>>(a);
+            return check_launch(ctx, "switched hop kernel");
+        }
+        if (c.variant == kVarPrefetch) {
+            k_hop_pf<REP, PREC><<<grid, c.block, 0, s>>>(a);
+            return check_launch(ctx, "prefetching hop kernel");
+        }
+        if (c.variant == kVarSwitchStaged) {
+            static bool attr_set3 = false;
+            if (!attr_set3) {
+                cudaFuncSetAttribute(k_hop_sw<REP, PREC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_max);
+                attr_set3 = true;
+            }
+            k_hop_sw<REP, PREC, true><<<grid, c.block, sm, s>>>(a);
+            return check_launch(ctx, "switched staged hop kernel");
         }
     }
     k_hop<REP, PREC><<<grid, c.block, 0, s>>>(a);
@@ -495,7 +735,7 @@ hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const H
 bool hop_variant_available(int rep, int prec, int variant)
 {
     (void)prec;
-    return variant == kVarSimple || (variant >= kVarStaged && variant <= kVarLoopStaged && rep != HR_ADJ_MAT);
+    return variant == kVarSimple || (variant >= kVarStaged && variant < kNumVariants && rep != HR_ADJ_MAT);
 }
 
 // Even-site operators from two hops each:

@@ -57,10 +57,17 @@ __device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int li
                                          cpx<T> (&acc)[4][NC])
 {
     cpx<T> s[4][NC];
-    load_spinor<NC, PREC>(a.in, a.g.nblk_s, j_nb, s);
+    // binary16 sites come unscaled; the projection and the colour product are
+    // linear, so the site's scale multiplies the link instead (4 or 9 numbers)
+    float sc;
+    load_spinor_raw<NC, PREC>(a.in, a.g.nblk_s, j_nb, s, sc);
     if constexpr (REP == kRepFund) {
         T q[4];
         load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+        if constexpr (PREC == kF16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = q[k] * sc;
+        }
         hop_compute<MU, FWD, REP>(s, q, neg_upper, acc);
     } else {
         T R[3][3];
@@ -70,6 +77,10 @@ __device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int li
             quat_to_adj(q, R);
         } else {
             load_mat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, R);
+        }
+        if constexpr (PREC == kF16) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) R[k / 3][k % 3] = R[k / 3][k % 3] * sc;
         }
         hop_compute<MU, FWD, REP>(s, R, neg_upper, acc);
     }

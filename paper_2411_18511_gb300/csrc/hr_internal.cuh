@@ -341,6 +341,34 @@ __device__ __forceinline__ void load_spinor(const void *base, int nblk, int j, c
     }
 }
 
+// As load_spinor, but a binary16 site is returned unscaled with its scale in
+// `sc` (1 for the other precisions), so a linear operation can apply the scale
+// to fewer numbers (the 4 link components instead of the 8 NC spinor reals).
+template <int NC, int PREC, class T>
+__device__ __forceinline__ void load_spinor_raw(const void *base, int nblk, int j, cpx<T> (&s)[4][NC], float &sc)
+{
+    if constexpr (PREC == kF16) {
+        using L = SpinorLayout<NC, PREC>;
+        constexpr int NV = L::NVEC;
+        cpx<T> *flat = &s[0][0];
+        const uint4 *p = (const uint4 *)base;
+        sc = __ldg((const float *)((const char *)base + L::data_bytes(nblk)) + j);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            uint4 w = __ldg(p + vec_index(j, v, NV));
+            uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 f = __half22float2(*reinterpret_cast<__half2 *>(&u[q]));
+                flat[4 * v + q] = {Real<T>::from_float(f.x), Real<T>::from_float(f.y)};
+            }
+        }
+    } else {
+        sc = 1.f;
+        load_spinor<NC, PREC>(base, nblk, j, s);
+    }
+}
+
 template <int NC, int PREC, class T>
 __device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const cpx<T> (&s)[4][NC])
 {
