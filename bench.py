@@ -118,7 +118,7 @@ def neighbour_bytes_per_site(rep: str, prec: str) -> int:
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_18511_gb300", "csrc")
-    for f in ("hr_internal.cuh", "hr_hop.cu"):
+    for f in ("hr_internal.cuh", "hr_hop_dev.cuh", "hr_hop.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
