@@ -259,8 +259,24 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
     // capture `chunk` iterations once, replay the graph
     int chunk = opts->check_every > 0 ? opts->check_every : 16;
     if (chunk > opts->maxiter) chunk = opts->maxiter;
-    Graph G;
+    // The graph bakes in every launch parameter: buffers, lattice, m0, the hop
+    // shapes in use.  Solves that repeat them (a benchmark, an MD trajectory
+    // with persistent buffers) reuse the instantiated graph from the context.
+    char keybuf[512];
     {
+        HopChoice c64 = hop_choice(ctx, sv.g, rep, kF64), clo = hop_choice(ctx, sv.g, rep, opts->inner_prec);
+        unsigned long long m0bits;
+        std::memcpy(&m0bits, &m0, sizeof m0bits);
+        snprintf(keybuf, sizeof keybuf, "cg:%d:%d:%d:%d:%d:%d:%d:%llx:%d:%d:%p:%p:%p:%p:%d.%d:%d.%d:%zu", lat.dims[0],
+                 lat.dims[1], lat.dims[2], lat.dims[3], sv.g.nrhs, rep, opts->inner_prec, m0bits, chunk,
+                 (int)sizeof(void *), gauge, b, x, work, c64.variant, c64.block, clo.variant, clo.block, work_bytes);
+    }
+    cudaGraphExec_t exec = nullptr;
+    auto cached = ctx->graphs.find(keybuf);
+    if (cached != ctx->graphs.end()) {
+        exec = cached->second.second;
+    } else {
+        Graph G;
         cudaStream_t cs;
         e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_err(ctx, e, "capture stream");
@@ -278,6 +294,21 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
         if (e2 != cudaSuccess) return cuda_err(ctx, e2, "end capture");
         e = cudaGraphInstantiate(&G.e, G.g, 0);
         if (e != cudaSuccess) return cuda_err(ctx, e, "graph instantiate");
+        // keep at most kMaxGraphs; the oldest entry goes first
+        if (ctx->graph_order.size() >= kMaxGraphs) {
+            auto old = ctx->graphs.find(ctx->graph_order.front());
+            if (old != ctx->graphs.end()) {
+                cudaGraphExecDestroy(old->second.second);
+                cudaGraphDestroy(old->second.first);
+                ctx->graphs.erase(old);
+            }
+            ctx->graph_order.erase(ctx->graph_order.begin());
+        }
+        ctx->graphs[keybuf] = std::make_pair(G.g, G.e);
+        ctx->graph_order.push_back(keybuf);
+        exec = G.e;
+        G.g = nullptr; // owned by the context now
+        G.e = nullptr;
     }
 
     int restarts = 0;
@@ -288,7 +319,7 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
     for (;;) {
         // iterate until the device says every RHS stopped, or maxiter
         for (;;) {
-            e = cudaGraphLaunch(G.e, s);
+            e = cudaGraphLaunch(exec, s);
             if (e != cudaSuccess) return cuda_err(ctx, e, "graph launch");
             launched += chunk;
             st = read_scalars(ctx, S_FLAGS, 1, s);

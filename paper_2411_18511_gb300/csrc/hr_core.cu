@@ -331,6 +331,10 @@ hr_status hr_ctx_destroy(hr_ctx *ctx)
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (auto &kv : ctx->graphs) {
+        cudaGraphExecDestroy(kv.second.second);
+        cudaGraphDestroy(kv.second.first);
+    }
     delete ctx;
     return HR_OK;
 }

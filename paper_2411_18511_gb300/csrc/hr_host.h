@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <map>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -37,7 +39,13 @@ struct hr_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::map<std::string, hr::HopChoice> tuned; // autotuner: configuration key -> launch shape
     std::string tune_cache_path;                // JSON cache (HR_AUTOTUNE_CACHE), "" = none
+    // instantiated CG iteration graphs, keyed by everything they bake in
+    std::map<std::string, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
+    std::vector<std::string> graph_order;
 };
+namespace hr {
+constexpr size_t kMaxGraphs = 8;
+}
 
 namespace hr {
 
