@@ -55,7 +55,7 @@ __device__ __forceinline__ int find_lat(const BatchLat *L, int n, int tile)
 // and runs the scalar update `fin` (and `fin2` after it, if nonzero).
 __device__ void tile_reduce(double v, const BatchLat &L, int tile, int counter, int fin, int fin2)
 {
-    __shared__ double wsum[kTile / 32];
+    __shared__ double wsum[kTile]; // >= 32 per warp for sum_partials
     __shared__ bool last;
     __shared__ double sums[32];
     v = warp_sum_strided(v, 1);
@@ -72,14 +72,8 @@ __device__ void tile_reduce(double v, const BatchLat &L, int tile, int counter, 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x == 0) {
-        const volatile double *pp = L.partials;
-        double s = 0;
-        for (int k = 0; k < L.ntiles; ++k) s += pp[k];
-        sums[0] = s;
-        L.counters[counter] = 0u;
-    }
-    __syncthreads();
+    sum_partials(L.partials, (unsigned)L.ntiles, 1, sums, wsum);
+    if (threadIdx.x == 0) L.counters[counter] = 0u;
     finish_reduction(fin, sums, 1, L.scal);
     if (fin2) {
         __syncthreads();

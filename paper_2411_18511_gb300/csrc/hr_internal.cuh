@@ -725,6 +725,31 @@ __device__ __forceinline__ double warp_sum_strided(double v, int nrhs)
     return v;
 }
 
+// sums[r] = sum over b < nparts of partials[b*nrhs + r], by the whole block.
+// Thread t takes right-hand side t % nrhs and every (blockDim/nrhs)-th partial;
+// the per-thread sums meet in a fixed tree, so the result does not depend on
+// which block runs this.  The partials are read through L2 (ld.cg): other
+// blocks wrote them.  Ends with a block barrier; smem >= 32 doubles per warp.
+__device__ inline void sum_partials(const double *partials, unsigned nparts, int nrhs, double *sums, double *smem)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int r = threadIdx.x & (nrhs - 1);
+    const unsigned step = blockDim.x / nrhs;
+    double s = 0;
+#pragma unroll 4
+    for (unsigned b = threadIdx.x / nrhs; b < nparts; b += step) s += __ldcg(partials + (size_t)b * nrhs + r);
+    s = warp_sum_strided(s, nrhs);
+    __syncthreads();
+    if (lane < nrhs) smem[warp * 32 + lane] = s;
+    __syncthreads();
+    if (threadIdx.x < nrhs) {
+        double t = 0;
+        for (int w = 0; w < nwarps; ++w) t += smem[w * 32 + threadIdx.x];
+        sums[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
 template <int MAXW = 32>
 __device__ inline bool grid_reduce(double v, int nrhs, RedSlot slot, double *sums, double *smem /* >= 32*32 */)
 {
@@ -747,14 +772,8 @@ __device__ inline bool grid_reduce(double v, int nrhs, RedSlot slot, double *sum
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (threadIdx.x < nrhs) {
-        double s = 0;
-        const volatile double *pp = slot.partials;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += pp[(size_t)b * nrhs + threadIdx.x];
-        sums[threadIdx.x] = s;
-    }
+    sum_partials(slot.partials, gridDim.x, nrhs, sums, smem);
     if (threadIdx.x == 0) *slot.counter = 0u;
-    __syncthreads();
     return true;
 }
 
