@@ -165,7 +165,10 @@ typedef struct {
     double reliable_delta; /* mixed precision: reliable update when |r| < delta max|r|  */
     int n_rhs;             /* independent right-hand sides solved together (>= 1)      */
     int x0_is_guess;       /* 1: x holds an initial guess; 0: start from x = 0          */
-    int check_every;       /* host convergence check interval in iterations (0: auto) */
+    int check_every;       /* 0: the device runs the whole loop (one graph launch, a  */
+                           /* conditional WHILE node; reliable updates in IF nodes);   */
+                           /* N > 0: replay a graph of N iterations, host check after */
+                           /* each.  Either way at most maxiter iterations run.        */
 } hr_solver_opts;
 
 typedef struct {

@@ -344,6 +344,7 @@ hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, doub
     std::vector<double> scal0(S_NSLOTS * kMaxRhsSlots, 0.0);
     scal0[S_ACTIVE * kMaxRhsSlots] = 1.0;
     scal0[S_DELTA2 * kMaxRhsSlots + 1] = opts->tol * opts->tol;
+    scal0[S_DELTA2 * kMaxRhsSlots + 2] = opts->maxiter;
     int tile0 = 0;
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < n_lat; ++l) {

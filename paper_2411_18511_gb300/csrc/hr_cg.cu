@@ -6,8 +6,10 @@
 //   second one reduces |Mhat p|^2 = <p, A p> and sets alpha on the device),
 //   one fused x/r update with the |r|^2 reduction (sets beta and the per-RHS
 //   convergence flags on the device) and one p update.  No host round trip per
-//   iteration: a chunk of iterations is captured once into a CUDA graph and
-//   replayed; the host reads the device flags once per chunk.
+//   iteration.  By default the whole loop is one CUDA graph: a conditional
+//   WHILE node whose body is one iteration, its condition set on the device,
+//   so a solve is a single graph launch (check_every > 0 instead replays a
+//   graph of that many iterations and checks the device flags on the host).
 // * Mixed precision with reliable updates (Clark et al., Comput. Phys. Commun.
 //   181 (2010) 1517): the recurrence runs on FP32 or FP16 copies of the gauge
 //   field and of p, r, q with FP32 arithmetic and an FP32 solution increment.
@@ -15,7 +17,8 @@
 //   target), a device-gated block adds the increment into the FP64 solution,
 //   recomputes r = b - A x in FP64 and restarts the low-precision residual from
 //   it, keeping the search direction.  Convergence is only declared on an FP64
-//   residual.
+//   residual.  In the one-graph solve the update is a conditional IF node, so
+//   iterations without one launch nothing for it.
 // * n_rhs independent right-hand sides run as one "virtual site" field: every
 //   link load serves all of them, and alpha, beta and convergence are per RHS.
 #include <cmath>
@@ -38,6 +41,22 @@ struct Graph {
     }
 };
 
+// keep at most kMaxGraphs instantiated graphs in the context; the oldest goes first
+void cache_graph(hr_ctx *ctx, const std::string &key, const Graph &G)
+{
+    if (ctx->graph_order.size() >= kMaxGraphs) {
+        auto old = ctx->graphs.find(ctx->graph_order.front());
+        if (old != ctx->graphs.end()) {
+            cudaGraphExecDestroy(old->second.second);
+            cudaGraphDestroy(old->second.first);
+            ctx->graphs.erase(old);
+        }
+        ctx->graph_order.erase(ctx->graph_order.begin());
+    }
+    ctx->graphs[key] = std::make_pair(G.g, G.e);
+    ctx->graph_order.push_back(key);
+}
+
 hr_status cuda_err(hr_ctx *ctx, cudaError_t e, const char *what)
 {
     if (e == cudaSuccess) return HR_OK;
@@ -45,12 +64,13 @@ hr_status cuda_err(hr_ctx *ctx, cudaError_t e, const char *what)
     return set_error(ctx, HR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-hr_status init_scalars(hr_ctx *ctx, int nrhs, double tol, double delta, cudaStream_t s)
+hr_status init_scalars(hr_ctx *ctx, int nrhs, double tol, double delta, int maxiter, cudaStream_t s)
 {
     std::vector<double> h(kScalDoubles, 0.0);
     for (int r = 0; r < nrhs; ++r) h[S_ACTIVE * kMaxRhsSlots + r] = 1.0;
     h[S_DELTA2 * kMaxRhsSlots + 0] = delta * delta;
     h[S_DELTA2 * kMaxRhsSlots + 1] = tol * tol;
+    h[S_DELTA2 * kMaxRhsSlots + 2] = maxiter;
     std::memcpy(ctx->h_scal, h.data(), sizeof(double) * kScalDoubles);
     cudaError_t e = cudaMemcpyAsync(ctx->d_scal, ctx->h_scal, sizeof(double) * kScalDoubles, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -67,6 +87,28 @@ hr_status read_scalars(hr_ctx *ctx, int first, int n, cudaStream_t s)
 }
 
 inline const double *flag_ptr(hr_ctx *ctx, int f) { return ctx->d_scal + S_FLAGS * kMaxRhsSlots + f; }
+
+enum CtlWhat { kCtlGate = 0, kCtlLoop = 1 };
+constexpr int kIterPerPass = 8; // iterations per pass of the device loop body
+
+// Device-side control of the solve graph.  kCtlGate: run the reliable update
+// (IF node) this iteration?  kCtlLoop: run another pass of the loop body (WHILE
+// node)?  The loop stops when the done flag is up (every RHS stopped, maxiter
+// reached or a NaN seen) and, as a backstop, after 2 maxiter + 64 passes.
+__global__ void k_cg_ctl(double *scal, cudaGraphConditionalHandle h, int what, int maxiter)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double *f = scal + S_FLAGS * kMaxRhsSlots;
+    const bool done = f[F_DONE] != 0.0;
+    unsigned v;
+    if (what == kCtlGate) {
+        v = (!done && f[F_GATE] != 0.0) ? 1u : 0u;
+    } else {
+        f[F_BODY] += 1.0;
+        v = (!done && f[F_ITERS] < (double)maxiter && f[F_BODY] < 2.0 * maxiter + 64.0) ? 1u : 0u;
+    }
+    cudaGraphSetConditional(h, v);
+}
 
 struct Solver {
     hr_ctx *ctx;
@@ -126,27 +168,47 @@ struct Solver {
         return apply_eo_op(ctx, g, m0, rep, kF64, HR_OP_NORMAL, gauge, v, ax, t64, u64, fin, gate, done, s);
     }
 
-    hr_status iteration()
+    // One iteration = part_a (q = A p with <p,q> -> alpha; x, r update with
+    // |r|^2 -> beta), then for the mixed solver the reliable update, then
+    // part_b (p = r + beta p).
+    hr_status part_a()
     {
-        hr_status st;
         const double *done = flag_ptr(ctx, F_DONE);
+        hr_status st;
         if (!mixed()) {
             st = apply64(p64, q64, kFinAlpha, nullptr, done);
             if (!st) st = blas_xr(ctx, g, rep, kF64, kF64, kF64, kF64, x, p64, r64, q64, s);
-            if (!st) st = blas_p(ctx, g, rep, kF64, kF64, p64, r64, s);
             return st;
         }
         const int P = o.inner_prec;
-        Geom g1 = g; // the low-precision gauge is indexed like any gauge
-        st = apply_eo_op(ctx, g1, m0, rep, P, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha, nullptr,
+        st = apply_eo_op(ctx, g, m0, rep, P, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha, nullptr,
                          done, s);
         if (!st) st = blas_xr(ctx, g, rep, kF32, P, P, P, x_lo, p_lo, r_lo, q_lo, s);
-        // reliable update, gated on the device
-        const double *gate = flag_ptr(ctx, F_GATE);
-        if (!st) st = blas_accum(ctx, g, rep, kF32, x, x_lo, gate, s);
+        return st;
+    }
+
+    // x += x_lo, r = b - A x in FP64, restart the low-precision residual;
+    // every launch skips its work unless *gate != 0 (gate == nullptr: always run)
+    hr_status reliable_update(const double *gate)
+    {
+        hr_status st = blas_accum(ctx, g, rep, kF32, x, x_lo, gate, s);
         if (!st) st = apply64(x, q64, kFinNone, gate, nullptr);
-        if (!st) st = blas_residual(ctx, g, rep, b, q64, r64, kFinResidual, gate, P, r_lo, s);
-        if (!st) st = blas_p(ctx, g, rep, P, P, p_lo, r_lo, s);
+        if (!st) st = blas_residual(ctx, g, rep, b, q64, r64, kFinResidual, gate, o.inner_prec, r_lo, s);
+        return st;
+    }
+
+    hr_status part_b()
+    {
+        if (!mixed()) return blas_p(ctx, g, rep, kF64, kF64, p64, r64, s);
+        return blas_p(ctx, g, rep, o.inner_prec, o.inner_prec, p_lo, r_lo, s);
+    }
+
+    // the iteration with the reliable update gated inside its kernels
+    hr_status iteration()
+    {
+        hr_status st = part_a();
+        if (!st && mixed()) st = reliable_update(flag_ptr(ctx, F_GATE));
+        if (!st) st = part_b();
         return st;
     }
 
@@ -161,7 +223,7 @@ struct Solver {
 
     hr_status start()
     {
-        hr_status st = init_scalars(ctx, g.nrhs, o.tol, o.reliable_delta, s);
+        hr_status st = init_scalars(ctx, g.nrhs, o.tol, o.reliable_delta, o.maxiter, s);
         if (st) return st;
         if (mixed()) {
             st = gauge_convert(ctx, make_geom_gauge(), rep, o.inner_prec, gauge, gauge_lo, s);
@@ -191,6 +253,103 @@ struct Solver {
 
     Geom make_geom_gauge() const { return g; }
 };
+
+// The whole solve loop as one graph: a WHILE node whose body is `per_pass`
+// iterations, with the reliable update of the mixed solver in an IF node per
+// iteration.  Kernels set every condition on the device (k_cg_ctl), so a solve
+// is one graph launch.  A pass of a WHILE body and a taken IF node each cost
+// about 25 us of scheduling on this hardware (a skipped IF about 9 us), so the
+// body holds several iterations; those after convergence skip their work on
+// the done flag.
+hr_status capture_while_graph(Solver &sv, int per_pass, cudaGraph_t *out)
+{
+    hr_ctx *ctx = sv.ctx;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    cudaGraph_t G = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaStream_t user = sv.s;
+    bool capturing = false;
+    hr_status st = HR_OK;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](const char *what) -> hr_status {
+        if (capturing) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs, &junk);
+        }
+        if (cs) cudaStreamDestroy(cs);
+        if (G) cudaGraphDestroy(G);
+        sv.s = user;
+        if (st) return st;
+        return cuda_err(ctx, e != cudaSuccess ? e : cudaErrorUnknown, what);
+    };
+    auto begin = [&](cudaGraph_t into, const cudaGraphNode_t *dep, size_t ndep) {
+        e = cudaStreamBeginCaptureToGraph(cs, into, dep, nullptr, ndep, mode);
+        capturing = e == cudaSuccess;
+        return capturing;
+    };
+    auto end = [&]() {
+        cudaGraph_t same = nullptr;
+        capturing = false;
+        e = cudaStreamEndCapture(cs, &same);
+        return e == cudaSuccess;
+    };
+    auto cond_node = [&](cudaGraph_t parent, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                         const cudaGraphNode_t *dep, size_t ndep, cudaGraphNode_t *node, cudaGraph_t *child) {
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = h;
+        np.conditional.type = type;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(node, parent, dep, nullptr, ndep, &np);
+        if (e == cudaSuccess) *child = np.conditional.phGraph_out[0];
+        return e == cudaSuccess;
+    };
+    const int maxiter = sv.o.maxiter;
+
+    if ((e = cudaGraphCreate(&G, 0)) != cudaSuccess) return fail("graph create");
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail("capture stream");
+    cudaGraphConditionalHandle hloop;
+    if ((e = cudaGraphConditionalHandleCreate(&hloop, G, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return fail("loop condition");
+    cudaGraphNode_t wnode;
+    cudaGraph_t body = nullptr;
+    if (!cond_node(G, hloop, cudaGraphCondTypeWhile, nullptr, 0, &wnode, &body)) return fail("while node");
+    sv.s = cs;
+    if (!begin(body, nullptr, 0)) return fail("begin capture");
+    for (int k = 0; k < per_pass; ++k) {
+        if ((st = sv.part_a())) return fail("iteration");
+        if (sv.mixed()) {
+            // each IF node has its own condition handle
+            cudaGraphConditionalHandle hgate;
+            if ((e = cudaGraphConditionalHandleCreate(&hgate, body, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+                return fail("gate condition");
+            k_cg_ctl<<<1, 32, 0, cs>>>(ctx->d_scal, hgate, kCtlGate, maxiter);
+            if ((st = check_launch(ctx, "cg control"))) return fail("cg control");
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t *d = nullptr;
+            size_t nd = 0;
+            if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &d, nullptr, &nd)) != cudaSuccess)
+                return fail("capture info");
+            std::vector<cudaGraphNode_t> deps(d, d + nd);
+            if (!end()) return fail("end capture");
+            cudaGraphNode_t inode;
+            cudaGraph_t ifbody = nullptr;
+            if (!cond_node(body, hgate, cudaGraphCondTypeIf, deps.data(), deps.size(), &inode, &ifbody))
+                return fail("if node");
+            if (!begin(ifbody, nullptr, 0)) return fail("begin capture");
+            if ((st = sv.reliable_update(nullptr))) return fail("reliable update");
+            if (!end()) return fail("end capture");
+            if (!begin(body, &inode, 1)) return fail("begin capture");
+        }
+        if ((st = sv.part_b())) return fail("iteration");
+    }
+    k_cg_ctl<<<1, 32, 0, cs>>>(ctx->d_scal, hloop, kCtlLoop, maxiter);
+    if ((st = check_launch(ctx, "cg control"))) return fail("cg control");
+    if (!end()) return fail("end capture");
+    cudaStreamDestroy(cs);
+    sv.s = user;
+    *out = G;
+    return HR_OK;
+}
 
 } // namespace
 
@@ -256,25 +415,39 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
     st = sv.start();
     if (st) return st;
 
-    // capture `chunk` iterations once, replay the graph
-    int chunk = opts->check_every > 0 ? opts->check_every : 16;
+    // check_every == 0: the whole loop is one graph (device-side WHILE);
+    // check_every == N: a graph of N iterations, replayed with a host check after each
+    const bool device_loop = opts->check_every <= 0;
+    int chunk = device_loop ? kIterPerPass : opts->check_every;
     if (chunk > opts->maxiter) chunk = opts->maxiter;
-    // The graph bakes in every launch parameter: buffers, lattice, m0, the hop
-    // shapes in use.  Solves that repeat them (a benchmark, an MD trajectory
+    // The graph bakes in every launch parameter: buffers, lattice, m0, maxiter,
+    // the hop shapes in use.  Solves that repeat them (a benchmark, an MD trajectory
     // with persistent buffers) reuse the instantiated graph from the context.
     char keybuf[512];
     {
         HopChoice c64 = hop_choice(ctx, sv.g, rep, kF64), clo = hop_choice(ctx, sv.g, rep, opts->inner_prec);
         unsigned long long m0bits;
         std::memcpy(&m0bits, &m0, sizeof m0bits);
-        snprintf(keybuf, sizeof keybuf, "cg:%d:%d:%d:%d:%d:%d:%d:%llx:%d:%d:%p:%p:%p:%p:%d.%d:%d.%d:%zu", lat.dims[0],
-                 lat.dims[1], lat.dims[2], lat.dims[3], sv.g.nrhs, rep, opts->inner_prec, m0bits, chunk,
-                 (int)sizeof(void *), gauge, b, x, work, c64.variant, c64.block, clo.variant, clo.block, work_bytes);
+        snprintf(keybuf, sizeof keybuf, "cg:%d:%d:%d:%d:%d:%d:%d:%llx:%d:%d:%d:%p:%p:%p:%p:%d.%d:%d.%d:%zu",
+                 lat.dims[0], lat.dims[1], lat.dims[2], lat.dims[3], sv.g.nrhs, rep, opts->inner_prec, m0bits,
+                 device_loop ? -chunk : chunk,
+                 opts->maxiter, (int)sizeof(void *), gauge, b, x, work, c64.variant, c64.block, clo.variant,
+                 clo.block, work_bytes);
     }
     cudaGraphExec_t exec = nullptr;
     auto cached = ctx->graphs.find(keybuf);
     if (cached != ctx->graphs.end()) {
         exec = cached->second.second;
+    } else if (device_loop) {
+        Graph G;
+        st = capture_while_graph(sv, chunk, &G.g);
+        if (st) return st;
+        e = cudaGraphInstantiate(&G.e, G.g, 0);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "graph instantiate");
+        cache_graph(ctx, keybuf, G);
+        exec = G.e;
+        G.g = nullptr; // owned by the context now
+        G.e = nullptr;
     } else {
         Graph G;
         cudaStream_t cs;
@@ -294,18 +467,7 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
         if (e2 != cudaSuccess) return cuda_err(ctx, e2, "end capture");
         e = cudaGraphInstantiate(&G.e, G.g, 0);
         if (e != cudaSuccess) return cuda_err(ctx, e, "graph instantiate");
-        // keep at most kMaxGraphs; the oldest entry goes first
-        if (ctx->graph_order.size() >= kMaxGraphs) {
-            auto old = ctx->graphs.find(ctx->graph_order.front());
-            if (old != ctx->graphs.end()) {
-                cudaGraphExecDestroy(old->second.second);
-                cudaGraphDestroy(old->second.first);
-                ctx->graphs.erase(old);
-            }
-            ctx->graph_order.erase(ctx->graph_order.begin());
-        }
-        ctx->graphs[keybuf] = std::make_pair(G.g, G.e);
-        ctx->graph_order.push_back(keybuf);
+        cache_graph(ctx, keybuf, G);
         exec = G.e;
         G.g = nullptr; // owned by the context now
         G.e = nullptr;
@@ -321,7 +483,7 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
         for (;;) {
             e = cudaGraphLaunch(exec, s);
             if (e != cudaSuccess) return cuda_err(ctx, e, "graph launch");
-            launched += chunk;
+            launched += device_loop ? 1 : chunk;
             st = read_scalars(ctx, S_FLAGS, 1, s);
             if (st) return st;
             const double *f = ctx->h_scal;
@@ -330,7 +492,8 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
                 numeric = true;
                 break;
             }
-            if (f[F_DONE] != 0.0 || iters >= opts->maxiter || launched >= 2LL * opts->maxiter + chunk) break;
+            if (device_loop || f[F_DONE] != 0.0 || iters >= opts->maxiter || launched >= 2LL * opts->maxiter + chunk)
+                break;
         }
         if (numeric) break;
         if (sv.mixed()) {

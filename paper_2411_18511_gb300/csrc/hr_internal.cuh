@@ -792,11 +792,12 @@ enum ScalSlot {
     S_RMAX = 7,    // max |r|^2 since the last reliable update
     S_RROLD = 8,   // |r|^2 before the current iteration
     S_OUT = 9,     // generic reduction output
-    S_FLAGS = 10,  // [0] all done, [1] reliable-update gate, [2] NaN/Inf seen, [3] iterations
-    S_DELTA2 = 11, // [0] reliable-update threshold delta^2
+    S_FLAGS = 10,  // [0] all done, [1] reliable-update gate, [2] NaN/Inf seen, [3] iterations,
+                   // [4] reliable updates, [5] device-loop passes
+    S_DELTA2 = 11, // [0] reliable-update threshold delta^2, [1] tol^2, [2] maxiter (<= 0: none)
     S_NSLOTS = 12
 };
-constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4;
+constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4, F_BODY = 5;
 
 enum FinishMode {
     kFinNone = 0,
@@ -878,8 +879,13 @@ __device__ inline void finish_reduction(int mode, const double *sums, int nrhs, 
         bool all_done = true;
         for (int k = 0; k < nrhs; ++k) all_done = all_done && (sc(scal, S_ACTIVE, k) == 0.0);
         if (sc(scal, S_FLAGS, F_NUMERIC) != 0.0) all_done = true;
+        if (mode == kFinBeta || mode == kFinBetaMixed) {
+            // the iteration cap also stops the recurrence (work already queued skips)
+            const double it = sc(scal, S_FLAGS, F_ITERS) + 1.0, cap = sc(scal, S_DELTA2, 2);
+            sc(scal, S_FLAGS, F_ITERS) = it;
+            if (cap > 0.0 && it >= cap) all_done = true;
+        }
         sc(scal, S_FLAGS, F_DONE) = all_done ? 1.0 : 0.0;
-        if (mode == kFinBeta || mode == kFinBetaMixed) sc(scal, S_FLAGS, F_ITERS) += 1.0;
         if (mode == kFinResidual) {
             sc(scal, S_FLAGS, F_GATE) = 0.0;
             sc(scal, S_FLAGS, F_NRELIABLE) += 1.0;

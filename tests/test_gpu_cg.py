@@ -38,8 +38,9 @@ def true_rel_residual(dims, L, m0, b, x):
     return np.linalg.norm(r) / np.linalg.norm(b)
 
 
-def run_solve(ctx, dims, rep, q, m0, b, inner, n_rhs=1, tol=1e-10, maxiter=20000):
+def run_solve(ctx, dims, rep, q, m0, b, inner, n_rhs=1, tol=1e-10, maxiter=20000, check_every=0):
     opts = hr.hr_solver_default_opts()
+    opts.check_every = check_every
     opts.tol = tol
     opts.maxiter = maxiter
     opts.inner_prec = inner
@@ -86,6 +87,34 @@ def test_cg_multi_rhs_matches_single(ctx, smeared_8):
     L = oracle.expand_links(dims, 2, q)
     for r in range(n):
         assert true_rel_residual(dims, L, m0, bs[r], xs[r]) <= 1e-10
+
+
+@pytest.mark.parametrize("inner", [hr.HR_F64, hr.HR_F32, hr.HR_F16])
+def test_cg_device_loop_matches_host_chunks(ctx, smeared_8, inner):
+    """The one-launch solve (device WHILE loop, reliable update in an IF node)
+    and the chunked solve (host check every 7 iterations, reliable update gated
+    inside its kernels) run the same arithmetic: identical x and counts."""
+    dims, q = smeared_8
+    b = synth.gaussian_spinor(dims, 2, 2003)
+    b[oracle.parity_mask(dims) == 1] = 0
+    rc0, i0, x0 = run_solve(ctx, dims, hr.HR_FUND, q, -0.2, b, inner, check_every=0)
+    rc1, i1, x1 = run_solve(ctx, dims, hr.HR_FUND, q, -0.2, b, inner, check_every=7)
+    assert rc0 == hr.HR_OK and rc1 == hr.HR_OK
+    assert i0.iters == i1.iters and i0.n_reliable_updates == i1.n_reliable_updates
+    assert np.array_equal(x0, x1)
+    assert i0.true_rel_residual == i1.true_rel_residual <= 1e-10
+
+
+@pytest.mark.parametrize("check_every", [0, 4])
+def test_cg_maxiter_is_exact(ctx, smeared_8, check_every):
+    """The iteration cap stops the recurrence on the device, also inside a
+    graph of 4 (or, device loop, 8) iterations that 9 does not divide."""
+    dims, q = smeared_8
+    b = synth.gaussian_spinor(dims, 2, 4001)
+    b[oracle.parity_mask(dims) == 1] = 0
+    rc, info, x = run_solve(ctx, dims, hr.HR_FUND, q, -0.2, b, hr.HR_F32, maxiter=9, check_every=check_every)
+    assert rc == hr.HR_ERR_NOT_CONVERGED
+    assert info.iters == 9
 
 
 def test_cg_not_converged_status(ctx, smeared_8):
