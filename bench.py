@@ -261,7 +261,9 @@ def run_ours(args):
         # pick the hop kernel's launch shape for this configuration (untimed set-up)
         res = hr.hr_autotune_hop(ctx, dims, rep, prec, hr.HR_EVEN, 1, gauge, p_s + half, p_d, reps=20)
         names = ["unrolled", "unrolled cp.async staged", "generic loop", "generic loop staged",
-                 "switched loop", "switched loop staged", "unrolled register prefetch"]
+                 "switched loop", "switched loop staged", "unrolled register prefetch",
+                 "unrolled, 96 registers", "bulk-copy tiled", "bulk-copy tiled, 96 registers",
+                 "paired f32x2 (colour lanes)", "paired f32x2, cp.async staged"]
         tuned = {"variant": names[res.variant] if 0 <= res.variant < len(names) else str(res.variant),
                  "block": res.block,
                  "tuned_ms": round(res.best_ms, 5), "default_ms": round(res.default_ms, 5),

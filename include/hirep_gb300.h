@@ -237,7 +237,12 @@ typedef struct {
                           staged in shared memory; 2: generic looped directions, registers;
                           3: generic looped, staged; 4: loop over mu with switched projections,
                           registers; 5: switched, staged; 6: unrolled with the next direction's
-                          operands prefetched into registers */
+                          operands prefetched into registers; 7: as 0, capped at 96
+                          registers per thread (more resident warps); 8: tiled, the
+                          near-direction neighbours bulk-copied (TMA) into shared memory;
+                          9: as 8, 96 registers; 10: fundamental FP64 only, the two
+                          colours in the lanes of packed f32x2 FMAs; 11: as 10, operands
+                          staged by cp.async one direction ahead */
     int block;         /* threads per block                                               */
     double best_ms;    /* mean time of one hop launch with the chosen shape               */
     double default_ms; /* the same for the shape in use before tuning                     */

@@ -23,13 +23,15 @@ struct HopArgs {
     double *scal;
     const double *gate;
     const double *done; // skip all work when *done != 0 (solver converged)
+    float unit, nil;    // 1 and 0, passed at run time so the compiler keeps the
+                        // +-1 multipliers of the packed-FMA additions as FMAs
 };
 
 __device__ __forceinline__ dd mul_pow2(dd x, float s) { return dd(x.h * s, x.l * s); }
 __device__ __forceinline__ float mul_pow2(float x, float s) { return x * s; }
 
 // projection, colour multiplication and accumulation of one direction
-template <int MU, bool FWD, int REP, class T, int NC, class LINK>
+template <int MU, bool FWD, int REP, bool FIRST = false, class T, int NC, class LINK>
 __device__ __forceinline__ void hop_compute(cpx<T> (&s)[4][NC], const LINK &link, bool neg_upper,
                                             cpx<T> (&acc)[4][NC])
 {
@@ -49,18 +51,16 @@ __device__ __forceinline__ void hop_compute(cpx<T> (&s)[4][NC], const LINK &link
         so3_mul<!FWD>(link, h[0], r[0]);
         so3_mul<!FWD>(link, h[1], r[1]);
     }
-    spin_accumulate<MU, FWD>(acc, r);
+    spin_accumulate<MU, FWD, T, NC, FIRST>(acc, r);
 }
 
-template <int MU, bool FWD, int REP, int PREC, class T, int NC>
-__device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int link_par, int j_nb, bool neg_upper,
-                                         cpx<T> (&acc)[4][NC])
+// one direction's term for a neighbour spinor s already loaded (binary16: s
+// unscaled, sc its scale; the projection and the colour product are linear, so
+// the scale multiplies the link instead, 4 or 9 numbers)
+template <int MU, bool FWD, int REP, int PREC, bool FIRST = false, class T, int NC>
+__device__ __forceinline__ void hop_term_with(const HopArgs &a, int site_link, int link_par, cpx<T> (&s)[4][NC],
+                                              float sc, bool neg_upper, cpx<T> (&acc)[4][NC])
 {
-    cpx<T> s[4][NC];
-    // binary16 sites come unscaled; the projection and the colour product are
-    // linear, so the site's scale multiplies the link instead (4 or 9 numbers)
-    float sc;
-    load_spinor_raw<NC, PREC>(a.in, a.g.nblk_s, j_nb, s, sc);
     if constexpr (REP == kRepFund) {
         T q[4];
         load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
@@ -68,7 +68,7 @@ __device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int li
 #pragma unroll
             for (int k = 0; k < 4; ++k) q[k] = q[k] * sc;
         }
-        hop_compute<MU, FWD, REP>(s, q, neg_upper, acc);
+        hop_compute<MU, FWD, REP, FIRST>(s, q, neg_upper, acc);
     } else {
         T R[3][3];
         if constexpr (REP == kRepAdj) {
@@ -82,18 +82,36 @@ __device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int li
 #pragma unroll
             for (int k = 0; k < 9; ++k) R[k / 3][k % 3] = R[k / 3][k % 3] * sc;
         }
-        hop_compute<MU, FWD, REP>(s, R, neg_upper, acc);
+        hop_compute<MU, FWD, REP, FIRST>(s, R, neg_upper, acc);
     }
 }
 
-template <int MU, int REP, int PREC, class T, int NC>
+template <int MU, bool FWD, int REP, int PREC, bool FIRST = false, class T, int NC>
+__device__ __forceinline__ void hop_term(const HopArgs &a, int site_link, int link_par, int j_nb, bool neg_upper,
+                                         cpx<T> (&acc)[4][NC])
+{
+    cpx<T> s[4][NC];
+    float sc;
+    load_spinor_raw<NC, PREC>(a.in, a.g.nblk_s, j_nb, s, sc);
+    hop_term_with<MU, FWD, REP, PREC, FIRST>(a, site_link, link_par, s, sc, neg_upper, acc);
+}
+
+// G5IN: 0 / 1 = the input is (not) multiplied by g5, fixed at compile time;
+// -1 = read a.g5_in at run time
+template <int G5IN> __device__ __forceinline__ bool g5_in_of(const HopArgs &a)
+{
+    if constexpr (G5IN < 0) return a.g5_in != 0;
+    else return G5IN != 0;
+}
+
+template <int MU, int REP, int PREC, int G5IN, bool FIRST = false, class T, int NC>
 __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, int rr, const SiteNb &nb, cpx<T> (&acc)[4][NC])
 {
     const int l = a.g.lrhs;
     // forward: (1 - g_mu) U_mu(x) psi(x + mu); the link sits at x (parity p)
-    hop_term<MU, true, REP, PREC>(a, i, a.p, (nb.fwd[MU] << l) + rr, a.g5_in != 0, acc);
+    hop_term<MU, true, REP, PREC, FIRST>(a, i, a.p, (nb.fwd[MU] << l) + rr, g5_in_of<G5IN>(a), acc);
     // backward: (1 + g_mu) U_mu(x - mu)^+ psi(x - mu); the link sits at x - mu (parity 1-p)
-    hop_term<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, a.g5_in != 0, acc);
+    hop_term<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, g5_in_of<G5IN>(a), acc);
 }
 
 // out = alpha * aux + beta * g5^{g5_out} acc, stored; |out|^2 into red
@@ -142,7 +160,7 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<
 }
 
 // one output site j (virtual index) of the unrolled hop: all 8 directions and the epilogue
-template <int REP, int PREC, class T>
+template <int REP, int PREC, int G5IN = -1, class T>
 __device__ __forceinline__ void hop_site(const HopArgs &a, int j, T al, T be, T bu, SqAcc<T> &red)
 {
     constexpr int NC = RepTraits<REP>::NC;
@@ -150,15 +168,11 @@ __device__ __forceinline__ void hop_site(const HopArgs &a, int j, T al, T be, T 
     const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
     SiteNb nb;
     site_neighbours(g, i, a.p, nb);
-    cpx<T> acc[4][NC];
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[s][c] = {T(0), T(0)};
-    hop_dir<0, REP, PREC>(a, i, rr, nb, acc);
-    hop_dir<1, REP, PREC>(a, i, rr, nb, acc);
-    hop_dir<2, REP, PREC>(a, i, rr, nb, acc);
-    hop_dir<3, REP, PREC>(a, i, rr, nb, acc);
+    cpx<T> acc[4][NC]; // set by the first term
+    hop_dir<0, REP, PREC, G5IN, true>(a, i, rr, nb, acc);
+    hop_dir<1, REP, PREC, G5IN>(a, i, rr, nb, acc);
+    hop_dir<2, REP, PREC, G5IN>(a, i, rr, nb, acc);
+    hop_dir<3, REP, PREC, G5IN>(a, i, rr, nb, acc);
     hop_epilogue<PREC>(a, j, acc, al, be, bu, red);
 }
 

@@ -23,9 +23,10 @@ constexpr int kScalDoubles = 64 * kMaxRhs;
 
 // launch shape of the hop kernel chosen by the autotuner
 struct HopChoice {
-    int variant; // 0: registers only, 1: cp.async staged
+    int variant; // kernel variant, 0 .. kNumHopVariants-1 (hr_hop.cu)
     int block;   // threads per block
 };
+constexpr int kNumHopVariants = 12;
 } // namespace hr
 
 struct hr_ctx {

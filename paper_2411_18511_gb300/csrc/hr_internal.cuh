@@ -15,8 +15,12 @@
 // array-of-structure-of-arrays in blocks of 32 virtual sites: one 16-byte
 // vector v of site j sits at vector index ((j/32)*NVEC + v)*32 + j%32, so a
 // warp reading one vector of 32 consecutive sites reads 512 contiguous bytes.
-//   spinor FP64: NVEC = 4*NC float4 (one complex each, as the double-float
-//                pairs (re.h, im.h, re.l, im.l): 8 bytes per real like binary64)
+//   spinor FP64: NVEC = 4*NC float4, 8 bytes per real like binary64, in
+//                double-float parts.  NC = 2 (colour-paired): spin s has vector
+//                2s = hi parts (c0.re, c1.re, c0.im, c1.im), vector 2s+1 = the
+//                lo parts in the same order, so a vector holds the two colours
+//                of one part side by side (what the packed f32x2 hop uses).
+//                NC = 3: one complex per float4, (re.h, im.h, re.l, im.l).
 //   spinor FP32: NVEC = 2*NC float4  (two complex each)
 //   spinor FP16: NVEC = NC   uint4   (four complex each, binary16), followed by
 //                one float scale per site (the site's max |component|)
@@ -295,6 +299,48 @@ __device__ __forceinline__ size_t vec_index(int j, int v, int nvec)
     return ((size_t)(j >> 5) * nvec + v) * 32 + (j & 31);
 }
 
+// FP64 vectors <-> values (layout above)
+template <int NC, class T>
+__device__ __forceinline__ void f64_from_vecs(const float4 *w, cpx<T> (&s)[4][NC])
+{
+    auto val = [](float h, float l) -> T {
+        if constexpr (std::is_same<T, dd>::value) return dd(h, l);
+        else return Real<T>::from_double(dd_to_double(dd(h, l)));
+    };
+    if constexpr (NC == 2) {
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            const float4 hi = w[2 * sp], lo = w[2 * sp + 1];
+            s[sp][0] = {val(hi.x, lo.x), val(hi.z, lo.z)};
+            s[sp][1] = {val(hi.y, lo.y), val(hi.w, lo.w)};
+        }
+    } else {
+        cpx<T> *flat = &s[0][0];
+#pragma unroll
+        for (int v = 0; v < 4 * NC; ++v) flat[v] = {val(w[v].x, w[v].z), val(w[v].y, w[v].w)};
+    }
+}
+template <int NC, class T>
+__device__ __forceinline__ void f64_to_vecs(const cpx<T> (&s)[4][NC], float4 *w)
+{
+    if constexpr (NC == 2) {
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            const dd r0 = Real<T>::to_dd(s[sp][0].re), i0 = Real<T>::to_dd(s[sp][0].im);
+            const dd r1 = Real<T>::to_dd(s[sp][1].re), i1 = Real<T>::to_dd(s[sp][1].im);
+            w[2 * sp] = make_float4(r0.h, r1.h, i0.h, i1.h);
+            w[2 * sp + 1] = make_float4(r0.l, r1.l, i0.l, i1.l);
+        }
+    } else {
+        const cpx<T> *flat = &s[0][0];
+#pragma unroll
+        for (int v = 0; v < 4 * NC; ++v) {
+            const dd re = Real<T>::to_dd(flat[v].re), im = Real<T>::to_dd(flat[v].im);
+            w[v] = make_float4(re.h, im.h, re.l, im.l);
+        }
+    }
+}
+
 template <int NC, int PREC, class T>
 __device__ __forceinline__ void load_spinor(const void *base, int nblk, int j, cpx<T> (&s)[4][NC])
 {
@@ -302,19 +348,11 @@ __device__ __forceinline__ void load_spinor(const void *base, int nblk, int j, c
     constexpr int NV = L::NVEC;
     cpx<T> *flat = &s[0][0];
     if constexpr (PREC == kF64) {
-        // one complex number per float4: (re.h, im.h, re.l, im.l)
         const float4 *p = (const float4 *)base;
+        float4 w[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            float4 w = __ldg(p + vec_index(j, v, NV));
-            if constexpr (std::is_same<T, dd>::value) {
-                flat[v].re = dd(w.x, w.z);
-                flat[v].im = dd(w.y, w.w);
-            } else {
-                flat[v].re = Real<T>::from_double(dd_to_double(dd(w.x, w.z)));
-                flat[v].im = Real<T>::from_double(dd_to_double(dd(w.y, w.w)));
-            }
-        }
+        for (int v = 0; v < NV; ++v) w[v] = __ldg(p + vec_index(j, v, NV));
+        f64_from_vecs<NC>(w, s);
     } else if constexpr (PREC == kF32) {
         const float4 *p = (const float4 *)base;
 #pragma unroll
@@ -377,11 +415,10 @@ __device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const 
     const cpx<T> *flat = &s[0][0];
     if constexpr (PREC == kF64) {
         float4 *p = (float4 *)base;
+        float4 w[NV];
+        f64_to_vecs<NC>(s, w);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            dd re = Real<T>::to_dd(flat[v].re), im = Real<T>::to_dd(flat[v].im);
-            p[vec_index(j, v, NV)] = make_float4(re.h, im.h, re.l, im.l);
-        }
+        for (int v = 0; v < NV; ++v) p[vec_index(j, v, NV)] = w[v];
     } else if constexpr (PREC == kF32) {
         float4 *p = (float4 *)base;
 #pragma unroll
@@ -423,29 +460,27 @@ template <int NC, int PREC, class T>
 __device__ __forceinline__ void spinor_from_vecs(const uint4 *w, float sc, cpx<T> (&s)[4][NC])
 {
     constexpr int NV = SpinorLayout<NC, PREC>::NVEC;
-    cpx<T> *flat = &s[0][0];
+    if constexpr (PREC == kF64) {
+        float4 f[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const uint4 u = w[v];
-        if constexpr (PREC == kF64) {
-            float4 f = *reinterpret_cast<const float4 *>(&u);
-            if constexpr (std::is_same<T, dd>::value) {
-                flat[v].re = dd(f.x, f.z);
-                flat[v].im = dd(f.y, f.w);
+        for (int v = 0; v < NV; ++v) f[v] = *reinterpret_cast<const float4 *>(&w[v]);
+        f64_from_vecs<NC>(f, s);
+    } else {
+        cpx<T> *flat = &s[0][0];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const uint4 u = w[v];
+            if constexpr (PREC == kF32) {
+                float4 f = *reinterpret_cast<const float4 *>(&u);
+                flat[2 * v] = {Real<T>::from_float(f.x), Real<T>::from_float(f.y)};
+                flat[2 * v + 1] = {Real<T>::from_float(f.z), Real<T>::from_float(f.w)};
             } else {
-                flat[v].re = Real<T>::from_double(dd_to_double(dd(f.x, f.z)));
-                flat[v].im = Real<T>::from_double(dd_to_double(dd(f.y, f.w)));
-            }
-        } else if constexpr (PREC == kF32) {
-            float4 f = *reinterpret_cast<const float4 *>(&u);
-            flat[2 * v] = {Real<T>::from_float(f.x), Real<T>::from_float(f.y)};
-            flat[2 * v + 1] = {Real<T>::from_float(f.z), Real<T>::from_float(f.w)};
-        } else {
-            uint32_t q4[4] = {u.x, u.y, u.z, u.w};
+                uint32_t q4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&q4[q]));
-                flat[4 * v + q] = {Real<T>::from_float(f.x * sc), Real<T>::from_float(f.y * sc)};
+                for (int q = 0; q < 4; ++q) {
+                    float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&q4[q]));
+                    flat[4 * v + q] = {Real<T>::from_float(f.x * sc), Real<T>::from_float(f.y * sc)};
+                }
             }
         }
     }
@@ -579,6 +614,52 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Bulk (TMA, non-tensor) copies global -> shared completing on an mbarrier
+// (sm_90 and later): one thread queues a contiguous copy of `bytes` (a multiple
+// of 16, both addresses 16-byte aligned) and the barrier's transaction count
+// tells the waiting threads when it has landed.
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(b), "r"(count) : "memory");
+    // make the initialised barrier visible to the async (TMA) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar)
+{
+    unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(b) : "memory");
+}
+// order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy ones (a bulk copy overwriting data the block has read)
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_copy_g2s(void *smem, const void *gmem, unsigned bytes, unsigned long long *bar)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(s),
+                 "l"(gmem), "r"(bytes), "r"(b)
+                 : "memory");
+}
+// Wait for phase `parity` of the barrier to complete, for at most about
+// `max_cycles` SM clock cycles; false if it did not (the caller records an
+// error and must not reuse the destination before a later wait succeeds).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, long long max_cycles)
+{
+    unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(b), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (clock64() - t0 > max_cycles) return false;
+    }
+}
+
 template <int PREC> struct GaugeMat {
     static size_t bytes(int nblk_g)
     {
@@ -684,26 +765,49 @@ __device__ __forceinline__ void spin_project(const cpx<T> (&s)[4][NC], cpx<T> (&
     }
 }
 
+// acc (+)= r, -r, i r or -i r; FIRST: acc holds nothing yet, so assign (the
+// first direction of a site saves the additions to zero)
+template <bool FIRST, class T> __device__ __forceinline__ cpx<T> acc_add(cpx<T> a, cpx<T> b)
+{
+    if constexpr (FIRST) return b;
+    else return cadd(a, b);
+}
+template <bool FIRST, class T> __device__ __forceinline__ cpx<T> acc_sub(cpx<T> a, cpx<T> b)
+{
+    if constexpr (FIRST) return {-b.re, -b.im};
+    else return csub(a, b);
+}
+template <bool FIRST, class T> __device__ __forceinline__ cpx<T> acc_add_i(cpx<T> a, cpx<T> b)
+{
+    if constexpr (FIRST) return {-b.im, b.re};
+    else return cadd_i(a, b);
+}
+template <bool FIRST, class T> __device__ __forceinline__ cpx<T> acc_sub_i(cpx<T> a, cpx<T> b)
+{
+    if constexpr (FIRST) return {b.im, -b.re};
+    else return csub_i(a, b);
+}
+
 // acc += (r, P r): the lower two spins of (1 -/+ g_mu) rebuilt from the upper two
-template <int MU, bool FWD, class T, int NC>
+template <int MU, bool FWD, class T, int NC, bool FIRST = false>
 __device__ __forceinline__ void spin_accumulate(cpx<T> (&acc)[4][NC], const cpx<T> (&r)[2][NC])
 {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        acc[0][c] = cadd(acc[0][c], r[0][c]);
-        acc[1][c] = cadd(acc[1][c], r[1][c]);
+        acc[0][c] = acc_add<FIRST>(acc[0][c], r[0][c]);
+        acc[1][c] = acc_add<FIRST>(acc[1][c], r[1][c]);
         if constexpr (MU == 0) {
-            if (FWD) { acc[2][c] = csub(acc[2][c], r[0][c]); acc[3][c] = csub(acc[3][c], r[1][c]); }
-            else { acc[2][c] = cadd(acc[2][c], r[0][c]); acc[3][c] = cadd(acc[3][c], r[1][c]); }
+            if (FWD) { acc[2][c] = acc_sub<FIRST>(acc[2][c], r[0][c]); acc[3][c] = acc_sub<FIRST>(acc[3][c], r[1][c]); }
+            else { acc[2][c] = acc_add<FIRST>(acc[2][c], r[0][c]); acc[3][c] = acc_add<FIRST>(acc[3][c], r[1][c]); }
         } else if constexpr (MU == 1) {
-            if (FWD) { acc[2][c] = csub_i(acc[2][c], r[1][c]); acc[3][c] = csub_i(acc[3][c], r[0][c]); }
-            else { acc[2][c] = cadd_i(acc[2][c], r[1][c]); acc[3][c] = cadd_i(acc[3][c], r[0][c]); }
+            if (FWD) { acc[2][c] = acc_sub_i<FIRST>(acc[2][c], r[1][c]); acc[3][c] = acc_sub_i<FIRST>(acc[3][c], r[0][c]); }
+            else { acc[2][c] = acc_add_i<FIRST>(acc[2][c], r[1][c]); acc[3][c] = acc_add_i<FIRST>(acc[3][c], r[0][c]); }
         } else if constexpr (MU == 2) {
-            if (FWD) { acc[2][c] = csub(acc[2][c], r[1][c]); acc[3][c] = cadd(acc[3][c], r[0][c]); }
-            else { acc[2][c] = cadd(acc[2][c], r[1][c]); acc[3][c] = csub(acc[3][c], r[0][c]); }
+            if (FWD) { acc[2][c] = acc_sub<FIRST>(acc[2][c], r[1][c]); acc[3][c] = acc_add<FIRST>(acc[3][c], r[0][c]); }
+            else { acc[2][c] = acc_add<FIRST>(acc[2][c], r[1][c]); acc[3][c] = acc_sub<FIRST>(acc[3][c], r[0][c]); }
         } else {
-            if (FWD) { acc[2][c] = csub_i(acc[2][c], r[0][c]); acc[3][c] = cadd_i(acc[3][c], r[1][c]); }
-            else { acc[2][c] = cadd_i(acc[2][c], r[0][c]); acc[3][c] = csub_i(acc[3][c], r[1][c]); }
+            if (FWD) { acc[2][c] = acc_sub_i<FIRST>(acc[2][c], r[0][c]); acc[3][c] = acc_add_i<FIRST>(acc[3][c], r[1][c]); }
+            else { acc[2][c] = acc_add_i<FIRST>(acc[2][c], r[0][c]); acc[3][c] = acc_sub_i<FIRST>(acc[3][c], r[1][c]); }
         }
     }
 }
@@ -793,11 +897,12 @@ enum ScalSlot {
     S_RROLD = 8,   // |r|^2 before the current iteration
     S_OUT = 9,     // generic reduction output
     S_FLAGS = 10,  // [0] all done, [1] reliable-update gate, [2] NaN/Inf seen, [3] iterations,
-                   // [4] reliable updates, [5] device-loop passes
+                   // [4] reliable updates, [5] device-loop passes, [6] device error (a
+                   // bulk copy that did not land in time)
     S_DELTA2 = 11, // [0] reliable-update threshold delta^2, [1] tol^2, [2] maxiter (<= 0: none)
     S_NSLOTS = 12
 };
-constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4, F_BODY = 5;
+constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4, F_BODY = 5, F_DEVERR = 6;
 
 enum FinishMode {
     kFinNone = 0,

@@ -38,7 +38,7 @@ void tune_cache_load(hr_ctx *ctx)
         size_t br = txt.find('[', q1);
         if (br == std::string::npos) break;
         int v = -1, b = -1;
-        if (sscanf(txt.c_str() + br, "[%d , %d]", &v, &b) == 2 && v >= 0 && v <= 6 && b >= 32 && b <= 1024 &&
+        if (sscanf(txt.c_str() + br, "[%d , %d]", &v, &b) == 2 && v >= 0 && v < kNumHopVariants && b >= 32 && b <= 1024 &&
             (b % 32) == 0 && key.rfind("hop:", 0) == 0) {
             HopChoice c;
             c.variant = v;
@@ -97,7 +97,7 @@ hr_status hr_autotune_hop(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec,
     // the default shape first, so its time is measured in the same conditions
     std::vector<HopChoice> cands;
     cands.push_back(def);
-    for (int v = 0; v < 7; ++v) {
+    for (int v = 0; v < kNumHopVariants; ++v) {
         if (!hop_variant_available(rep, prec, v)) continue;
         for (int b : blocks) {
             if (v == def.variant && b == def.block) continue;

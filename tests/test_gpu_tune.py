@@ -1,5 +1,6 @@
-"""The hop autotuner and both kernel variants (registers-only and cp.async
-staged), checked against the oracle for every shape the tuner may choose."""
+"""The hop autotuner and its kernel variants (registers-only, cp.async staged,
+looped, bulk-copy tiled, ...), checked against the oracle for every shape the
+tuner may choose."""
 
 import json
 import os
@@ -47,7 +48,9 @@ def key(dims, rep, prec, n_rhs=1):
     return f"hop:r{rep}:p{prec}:{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}:n{n_rhs}"
 
 
-@pytest.mark.parametrize("variant,block", [(0, 64), (0, 256), (1, 64), (1, 192), (2, 128), (2, 256), (3, 64), (3, 128), (4, 128), (4, 256), (5, 64), (5, 128), (6, 128), (6, 256)])
+@pytest.mark.parametrize("variant,block", [(0, 64), (0, 256), (1, 64), (1, 192), (2, 128), (2, 256), (3, 64), (3, 128), (4, 128), (4, 256), (5, 64), (5, 128), (6, 128), (6, 256), (7, 64), (7, 128), (7, 256),
+                                           (8, 64), (8, 128), (8, 256), (9, 64), (9, 128), (10, 64),
+                                           (10, 256), (11, 64), (11, 256)])
 def test_forced_shapes_from_cache_match_oracle(tmp_path, monkeypatch, variant, block):
     dims = (6, 4, 2, 6)  # 144 sites per parity: ragged last block of 32
     cache = tmp_path / "tune.json"
@@ -79,7 +82,7 @@ def test_autotune_chooses_and_persists(tmp_path, monkeypatch, rep, prec):
     src = fields.pack_spinor(c, dims, rep, prec, hr.HR_ODD, fields.spinor_to_device(psi))
     dst = fields.empty_spinor(dims, rep, prec, hr.HR_EVEN)
     res = hr.hr_autotune_hop(c, dims, rep, prec, hr.HR_EVEN, 1, gauge, src, dst, reps=5)
-    assert res.variant in range(7) and res.block in (64, 128, 192, 256)
+    assert res.variant in range(12) and res.block in (64, 128, 192, 256)
     assert res.candidates >= 4 and 0 < res.best_ms <= res.default_ms
     assert hr.hr_tune_lookup(c, dims, rep, prec) == (res.variant, res.block)
     saved = json.loads(cache.read_text())
@@ -101,3 +104,51 @@ def test_autotune_rejects_bad_arguments(ctx):
         hr.hr_autotune_hop(ctx, dims, 0, 0, hr.HR_EVEN, 1, g, s, s)
     with pytest.raises(hr.HrError):
         hr.hr_autotune_hop(ctx, dims, 0, 0, hr.HR_EVEN, 1, g, s, fields.empty_spinor(dims, 0, 0, 0), reps=0)
+
+
+def _forced_context(tmp_path, monkeypatch, name, dims, reps, precs, n_rhs, variant, block):
+    cache = tmp_path / f"{name}.json"
+    cache.write_text(json.dumps({key(dims, r, p, n_rhs): [variant, block] for r in reps for p in precs}))
+    monkeypatch.setenv("HR_AUTOTUNE_CACHE", str(cache))
+    return hr.Context(0)
+
+
+@pytest.mark.parametrize("n_rhs", [1, 4])
+@pytest.mark.parametrize("variant,block", [(8, 64), (8, 256), (9, 128), (10, 128), (10, 192), (11, 128),
+                                           (11, 192)])
+def test_variant_bitwise_equals_plain(tmp_path, monkeypatch, variant, block, n_rhs):
+    """The bulk-copy tiled kernels (8, 9) take the near-direction neighbours
+    from shared memory, the paired kernels (10, 11) run two colours per f32x2
+    instruction; all form every sum in the plain kernel's order, so every
+    operator (hop, Schur, normal: g5 inputs, aux terms, fused norms) must agree
+    bit for bit, on a lattice whose tiles straddle rows, wraps and a ragged
+    end."""
+    dims = (4, 6, 6, 10)  # h3 = 5, 360 sites per parity
+    reps, precs = (hr.HR_FUND, hr.HR_ADJ), (hr.HR_F64, hr.HR_F32)
+    base = _forced_context(tmp_path, monkeypatch, "plain", dims, reps, precs, n_rhs, 0, 128)
+    tiled = _forced_context(tmp_path, monkeypatch, "tiled", dims, reps, precs, n_rhs, variant, block)
+    for rep in reps:
+        nc = 2 if rep == hr.HR_FUND else 3
+        q = synth.haar_links(dims, 31)
+        psi = synth.gaussian_spinor(dims, nc, 32, n_rhs=n_rhs) if n_rhs > 1 else synth.gaussian_spinor(dims, nc, 32)
+        for prec in precs:
+            assert hr.hr_tune_lookup(tiled, dims, rep, prec, n_rhs) == (variant, block)
+            outs = []
+            for c in (base, tiled):
+                gauge = fields.pack_gauge(c, dims, rep, prec, fields.gauge_to_device(q))
+                res = []
+                for op, par in ((hr.HR_OP_HOP, hr.HR_EVEN), (hr.HR_OP_HOP, hr.HR_ODD),
+                                (hr.HR_OP_SCHUR, hr.HR_EVEN), (hr.HR_OP_SCHUR_DAG, hr.HR_EVEN),
+                                (hr.HR_OP_NORMAL, hr.HR_EVEN)):
+                    src_par = (1 - par) if op == hr.HR_OP_HOP else hr.HR_EVEN
+                    src = fields.pack_spinor(c, dims, rep, prec, src_par, fields.spinor_to_device(psi))
+                    dst = fields.empty_spinor(dims, rep, prec, par, n_rhs)
+                    wb = hr.hr_dirac_workspace_bytes(dims, rep, prec, op, n_rhs)
+                    work = fields.empty_bytes(wb) if wb else None
+                    hr.hr_dirac_eo(c, dims, -0.3, rep, prec, par, op, n_rhs, gauge, src, dst, work)
+                    res.append(fields.unpack_spinor(c, dims, rep, prec, par, dst, n_rhs).cpu().numpy())
+                outs.append(res)
+            for a, b in zip(*outs):
+                assert np.array_equal(a, b), (rep, prec)
+    base.close()
+    tiled.close()
