@@ -40,20 +40,29 @@ HBM_FALLBACK = 6800.0
 # FP32-pipe roofline of GB300: 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)
 FP32_PEAK_GOPS = 152 * 128 * 2.070
 # Essential FP32-pipe operations per output site of the double-float fundamental hop
-# (TwoSum = 6, TwoProduct with cross terms = 4, double-float add = 8):
-# per direction 8 projection adds (64) + 8 colour-product outputs of 4 products and
-# 3 adds each (320) + 16 reconstruction adds (128) = 512; 8 directions + epilogue
-# (scaling 32, renormalisation 96) = 4224.
-DF_OPS_PER_SITE_FUND = 8 * 512 + 128
+# (TwoSum = 6, TwoProduct with cross terms = 4, double-float add = 8): per direction
+# 8 projection adds (64) + 8 colour-product outputs of 4 products and 3 adds each
+# (320) = 384, and 16 reconstruction adds (128) for every direction but the first
+# (which assigns); the epilogue scales (32) and renormalises (96) the 16 reals.
+DF_OPS_PER_SITE_FUND = 8 * 384 + 7 * 128 + 32 + 96
+# kernel symbol of each hop variant (the tuner's index)
+HOP_KERNELS = ["k_hop", "k_hop_staged", "k_hop_loop", "k_hop_loop", "k_hop_sw", "k_hop_sw", "k_hop_pf",
+               "k_hop_r96", "k_hop_tile", "k_hop_tile_r96", "k_hop_x2", "k_hop_x2s", "k_hop_x2_r96",
+               "k_hop_x2s_r96"]
+HOP_VARIANT_NAMES = ["unrolled", "unrolled cp.async staged", "generic loop", "generic loop staged",
+                     "switched loop", "switched loop staged", "unrolled register prefetch",
+                     "unrolled, 96 registers", "bulk-copy tiled", "bulk-copy tiled, 96 registers",
+                     "paired f32x2 (colour lanes)", "paired f32x2, cp.async staged",
+                     "paired f32x2, 96 registers", "paired f32x2, cp.async staged, 96 registers"]
 
 
-def roofline(pname, vh, bytes_site, launch_ms, achieved_gbs, peak_gbs, peak_kind, traffic):
+def roofline(pname, vh, bytes_site, launch_ms, achieved_gbs, peak_gbs, peak_kind, traffic, kernel):
     """The dominant kernel's roofline.  FP32/FP16 hops are bound by HBM; the
     double-float FP64 hop needs more FP32-pipe operations per site than the
     FP32 pipes deliver in the time HBM needs for its bytes, so it is ALU bound."""
     hbm = {"achieved": round(achieved_gbs, 2), "peak": peak_gbs, "unit": "GB/s",
            "frac": round(achieved_gbs / peak_gbs, 4), "peak_kind": f"{peak_kind} HBM copy (burst)"}
-    base = {"traffic": traffic, "kernel": f"k_hop<fund,{pname}>", "bytes_per_launch": vh * bytes_site,
+    base = {"traffic": traffic, "kernel": kernel, "bytes_per_launch": vh * bytes_site,
             "avg_launch_ms": round(launch_ms, 5)}
     if pname != "f64":
         return {"bound": "hbm", **hbm, **base}
@@ -118,7 +127,8 @@ def neighbour_bytes_per_site(rep: str, prec: str) -> int:
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_18511_gb300", "csrc")
-    for f in ("hr_internal.cuh", "hr_hop_dev.cuh", "hr_hop.cu"):
+    for f in ("hr_internal.cuh", "hr_hop_dev.cuh", "hr_hop_fam.h", "hr_hop.cu", "hr_hop_staged.cu",
+              "hr_hop_loop.cu", "hr_hop_tile.cu", "hr_hop_x2.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -260,10 +270,7 @@ def run_ours(args):
     if not args.no_autotune:
         # pick the hop kernel's launch shape for this configuration (untimed set-up)
         res = hr.hr_autotune_hop(ctx, dims, rep, prec, hr.HR_EVEN, 1, gauge, p_s + half, p_d, reps=20)
-        names = ["unrolled", "unrolled cp.async staged", "generic loop", "generic loop staged",
-                 "switched loop", "switched loop staged", "unrolled register prefetch",
-                 "unrolled, 96 registers", "bulk-copy tiled", "bulk-copy tiled, 96 registers",
-                 "paired f32x2 (colour lanes)", "paired f32x2, cp.async staged"]
+        names = HOP_VARIANT_NAMES
         tuned = {"variant": names[res.variant] if 0 <= res.variant < len(names) else str(res.variant),
                  "block": res.block,
                  "tuned_ms": round(res.best_ms, 5), "default_ms": round(res.default_ms, 5),
@@ -296,6 +303,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms_step = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    variant, block = hr.hr_tune_lookup(ctx, dims, rep, prec)
+    kernel = f"{HOP_KERNELS[variant] if 0 <= variant < len(HOP_KERNELS) else variant}<fund,{pname}> x{block}"
     bytes_site = hop_bytes_per_site("fund", pname)
     bytes_step = 2 * Vh * bytes_site
     value = world * bytes_step / (ms_step * 1e-3) / 1e9
@@ -341,7 +350,7 @@ def run_ours(args):
             "parallelism": f"replicas{world}",
         },
         "roofline": roofline(pname, Vh, bytes_site, launch_ms, achieved, peak, peak_kind,
-                             profiled_traffic(f"hop_fund_{pname}_{L4}x{L4}x{L4}x{L4}.md")),
+                             profiled_traffic(f"hop_fund_{pname}_{L4}x{L4}x{L4}x{L4}.md"), kernel),
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,

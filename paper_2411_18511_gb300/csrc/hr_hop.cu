@@ -112,7 +112,9 @@ hr_status dispatch(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs 
     case kVarTile:
     case kVarTileR96: done = launch_hop_tiled(ctx, g, rep, prec, a, c, grid, s, st); break;
     case kVarPaired:
-    case kVarPairedStaged: done = launch_hop_paired(ctx, g, rep, prec, a, c, grid, s, st); break;
+    case kVarPairedStaged:
+    case kVarPairedR96:
+    case kVarPairedStagedR96: done = launch_hop_paired(ctx, g, rep, prec, a, c, grid, s, st); break;
     default: break;
     }
     // the plain kernels: variants 0 and 7, and any variant without a kernel here
@@ -185,7 +187,7 @@ bool hop_variant_available(int rep, int prec, int variant)
 {
     (void)prec;
     // the paired kernel pairs the two colours of the fundamental FP64 layout
-    if (variant == kVarPaired || variant == kVarPairedStaged) return rep == HR_FUND && prec == HR_F64;
+    if (variant >= kVarPaired && variant <= kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
     // the 96-register caps spill heavily with three colours: fundamental only
     if (variant == kVarSimpleR96) return rep == HR_FUND;
     if (variant == kVarTileR96) return rep == HR_FUND && prec != HR_F16;

@@ -5,8 +5,8 @@
 //   hr_hop_loop.cu    2, 3 generic direction loop (registers / staged),
 //                     4, 5 loop over mu with switched projections
 //   hr_hop_tile.cu    8, 9 near-direction window bulk-copied into shared memory
-//   hr_hop_x2.cu      10, 11 fundamental FP64 on packed f32x2 FMAs (registers /
-//                     cp.async staged)
+//   hr_hop_x2.cu      10-13 fundamental FP64 on packed f32x2 FMAs (registers /
+//                     cp.async staged, compiler's registers / 96)
 // All compute the same operator; the autotuner picks per configuration.
 #pragma once
 
@@ -27,11 +27,13 @@ enum HopVariant : int {
     kVarTile = 8,
     kVarTileR96 = 9,
     kVarPaired = 10,
-    kVarPairedStaged = 11
+    kVarPairedStaged = 11,
+    kVarPairedR96 = 12,
+    kVarPairedStagedR96 = 13
 };
-static_assert(kVarPairedStaged + 1 == kNumHopVariants, "variant list");
+static_assert(kVarPairedStagedR96 + 1 == kNumHopVariants, "variant list");
 
-// per-thread shared-memory slots of the cp.async staged variants (1, 3, 5, 11)
+// per-thread shared-memory slots of the cp.async staged variants (1, 3, 5, 11, 13)
 template <int REP, int PREC> struct Stage {
     static constexpr int NC = RepTraits<REP>::NC;
     static constexpr int NV = SpinorLayout<NC, PREC>::NVEC;

@@ -1,6 +1,7 @@
-// hr_hop_x2.cu -- the paired hop (variants 10, 11): fundamental double-float
+// hr_hop_x2.cu -- the paired hop (variants 10-13): fundamental double-float
 // arithmetic with the two colours in the lanes of packed f32x2 FMAs, operands
-// from registers (10) or staged by cp.async one direction ahead (11).
+// from registers (10, 12) or staged by cp.async one direction ahead (11, 13);
+// 12 and 13 cap the registers at 96 for more resident warps.
 #include <algorithm>
 #include <cstdlib>
 
@@ -160,6 +161,22 @@ template <bool FWD> __device__ __forceinline__ cdd2 su2_x2(const K2 &k, const Li
 
 // one direction: acc (+)= (1 -/+ g_mu) U psi(neighbour) in doublet form.  NEG:
 // the input's upper spins are negated (g5 in), folded into the signs.
+// acc_t (+)= i^F r_t and acc_{2+u} (+)= i^{d_u + F} r_t for the u with rho_u = t
+template <int T, class D, int F, bool FIRST>
+__device__ __forceinline__ void x2_rebuild(const K2 &k, const cdd2 &r, cdd2 (&acc)[4])
+{
+    if constexpr (FIRST) acc[T] = pow_i<F>(k, r);
+    else acc[T] = cadd_pow_i<F>(k, acc[T], r);
+    if constexpr (D::rho0 == T) {
+        if constexpr (FIRST) acc[2] = pow_i<(D::d0 + F) & 3>(k, r);
+        else acc[2] = cadd_pow_i<(D::d0 + F) & 3>(k, acc[2], r);
+    }
+    if constexpr (D::rho1 == T) {
+        if constexpr (FIRST) acc[3] = pow_i<(D::d1 + F) & 3>(k, r);
+        else acc[3] = cadd_pow_i<(D::d1 + F) & 3>(k, acc[3], r);
+    }
+}
+
 template <int MU, bool FWD, bool FIRST, bool NEG>
 __device__ __forceinline__ void x2_compute(const K2 &k, const float4 (&w)[8], const float4 &qh, const float4 &ql,
                                            cdd2 (&acc)[4])
@@ -176,21 +193,10 @@ __device__ __forceinline__ void x2_compute(const K2 &k, const float4 (&w)[8], co
     const cdd2 h0 = cadd_pow_i<(D::c0 + F) & 3>(k, s[0], s[D::pi0]);
     const cdd2 h1 = cadd_pow_i<(D::c1 + F) & 3>(k, s[1], s[D::pi1]);
     const Link2 U = link2(qh, ql);
-    const cdd2 r0 = su2_x2<FWD>(k, U, h0);
-    const cdd2 r1 = su2_x2<FWD>(k, U, h1);
-    const cdd2 &u0 = D::rho0 ? r1 : r0;
-    const cdd2 &u1 = D::rho1 ? r1 : r0;
-    if constexpr (FIRST) {
-        acc[0] = pow_i<F>(k, r0);
-        acc[1] = pow_i<F>(k, r1);
-        acc[2] = pow_i<(D::d0 + F) & 3>(k, u0);
-        acc[3] = pow_i<(D::d1 + F) & 3>(k, u1);
-    } else {
-        acc[0] = cadd_pow_i<F>(k, acc[0], r0);
-        acc[1] = cadd_pow_i<F>(k, acc[1], r1);
-        acc[2] = cadd_pow_i<(D::d0 + F) & 3>(k, acc[2], u0);
-        acc[3] = cadd_pow_i<(D::d1 + F) & 3>(k, acc[3], u1);
-    }
+    // r_t = U h_t, each added into its upper spin and its lower partner at once
+    // (rho maps the lower spins to r0 / r1), so only one r is live at a time
+    x2_rebuild<0, D, F, FIRST>(k, su2_x2<FWD>(k, U, h0), acc);
+    x2_rebuild<1, D, F, FIRST>(k, su2_x2<FWD>(k, U, h1), acc);
 }
 
 template <int MU, bool FWD, bool FIRST, bool NEG>
@@ -254,7 +260,7 @@ __device__ __forceinline__ void x2_stage_step(const HopArgs &a, const K2 &k, int
 }
 
 template <int G5IN>
-__global__ void __launch_bounds__(256) k_hop_x2s(HopArgs a)
+__device__ __forceinline__ void x2s_body(const HopArgs &a)
 {
     using S = Stage<kRepFund, kF64>;
     static_assert(S::NSLOT == 10, "8 spinor + 2 link vectors per direction");
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(256) k_hop_x2s(HopArgs a)
 }
 
 template <int G5IN>
-__global__ void __launch_bounds__(256) k_hop_x2(HopArgs a)
+__device__ __forceinline__ void x2_body(const HopArgs &a)
 {
     using T = dd;
     constexpr bool NEG = G5IN != 0;
@@ -328,28 +334,33 @@ __global__ void __launch_bounds__(256) k_hop_x2(HopArgs a)
     }
 }
 
+// registers as the compiler likes (about 100 / 128), or capped at 96: five
+// 128-thread blocks per SM (the staged form's 40 KB of slots each still fit)
+template <int G5IN> __global__ void __launch_bounds__(256) k_hop_x2(HopArgs a) { x2_body<G5IN>(a); }
+template <int G5IN> __global__ void __maxnreg__(96) k_hop_x2_r96(HopArgs a) { x2_body<G5IN>(a); }
+template <int G5IN> __global__ void __launch_bounds__(256) k_hop_x2s(HopArgs a) { x2s_body<G5IN>(a); }
+template <int G5IN> __global__ void __maxnreg__(96) k_hop_x2s_r96(HopArgs a) { x2s_body<G5IN>(a); }
+
 template <int REP, int PREC> struct Launch {
     static bool run(hr_ctx *ctx, const Geom &, const HopArgs &a, HopChoice c, int grid, cudaStream_t s,
                     hr_status &st)
     {
         if constexpr (REP == kRepFund && PREC == kF64) {
-            if (c.variant == kVarPairedStaged) {
-                using S = Stage<kRepFund, kF64>;
-                static bool attr_set = false;
-                if (!attr_set) {
-                    for (auto f : {k_hop_x2s<0>, k_hop_x2s<1>})
-                        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)S::smem_bytes(256));
-                    attr_set = true;
-                }
-                const size_t sm = S::smem_bytes(c.block);
-                if (a.g5_in) k_hop_x2s<1><<<grid, c.block, sm, s>>>(a);
-                else k_hop_x2s<0><<<grid, c.block, sm, s>>>(a);
-                st = check_launch(ctx, "paired staged hop kernel");
-                return true;
+            using S = Stage<kRepFund, kF64>;
+            static bool attr_set = false;
+            if (!attr_set) {
+                for (auto f : {k_hop_x2s<0>, k_hop_x2s<1>, k_hop_x2s_r96<0>, k_hop_x2s_r96<1>})
+                    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes(256));
+                attr_set = true;
             }
-            if (a.g5_in) k_hop_x2<1><<<grid, c.block, 0, s>>>(a);
-            else k_hop_x2<0><<<grid, c.block, 0, s>>>(a);
+            const size_t sm = S::smem_bytes(c.block);
+            const bool g5 = a.g5_in != 0;
+            switch (c.variant) {
+            case kVarPairedStaged: (g5 ? k_hop_x2s<1> : k_hop_x2s<0>)<<<grid, c.block, sm, s>>>(a); break;
+            case kVarPairedStagedR96: (g5 ? k_hop_x2s_r96<1> : k_hop_x2s_r96<0>)<<<grid, c.block, sm, s>>>(a); break;
+            case kVarPairedR96: (g5 ? k_hop_x2_r96<1> : k_hop_x2_r96<0>)<<<grid, c.block, 0, s>>>(a); break;
+            default: (g5 ? k_hop_x2<1> : k_hop_x2<0>)<<<grid, c.block, 0, s>>>(a); break;
+            }
             st = check_launch(ctx, "paired hop kernel");
             return true;
         }

@@ -26,7 +26,7 @@ struct HopChoice {
     int variant; // kernel variant, 0 .. kNumHopVariants-1 (hr_hop.cu)
     int block;   // threads per block
 };
-constexpr int kNumHopVariants = 12;
+constexpr int kNumHopVariants = 14;
 } // namespace hr
 
 struct hr_ctx {

@@ -50,7 +50,7 @@ def key(dims, rep, prec, n_rhs=1):
 
 @pytest.mark.parametrize("variant,block", [(0, 64), (0, 256), (1, 64), (1, 192), (2, 128), (2, 256), (3, 64), (3, 128), (4, 128), (4, 256), (5, 64), (5, 128), (6, 128), (6, 256), (7, 64), (7, 128), (7, 256),
                                            (8, 64), (8, 128), (8, 256), (9, 64), (9, 128), (10, 64),
-                                           (10, 256), (11, 64), (11, 256)])
+                                           (10, 256), (11, 64), (11, 256), (12, 128), (13, 128)])
 def test_forced_shapes_from_cache_match_oracle(tmp_path, monkeypatch, variant, block):
     dims = (6, 4, 2, 6)  # 144 sites per parity: ragged last block of 32
     cache = tmp_path / "tune.json"
@@ -82,7 +82,7 @@ def test_autotune_chooses_and_persists(tmp_path, monkeypatch, rep, prec):
     src = fields.pack_spinor(c, dims, rep, prec, hr.HR_ODD, fields.spinor_to_device(psi))
     dst = fields.empty_spinor(dims, rep, prec, hr.HR_EVEN)
     res = hr.hr_autotune_hop(c, dims, rep, prec, hr.HR_EVEN, 1, gauge, src, dst, reps=5)
-    assert res.variant in range(12) and res.block in (64, 128, 192, 256)
+    assert res.variant in range(14) and res.block in (64, 128, 192, 256)
     assert res.candidates >= 4 and 0 < res.best_ms <= res.default_ms
     assert hr.hr_tune_lookup(c, dims, rep, prec) == (res.variant, res.block)
     saved = json.loads(cache.read_text())
@@ -115,10 +115,10 @@ def _forced_context(tmp_path, monkeypatch, name, dims, reps, precs, n_rhs, varia
 
 @pytest.mark.parametrize("n_rhs", [1, 4])
 @pytest.mark.parametrize("variant,block", [(8, 64), (8, 256), (9, 128), (10, 128), (10, 192), (11, 128),
-                                           (11, 192)])
+                                           (11, 192), (12, 64), (13, 128)])
 def test_variant_bitwise_equals_plain(tmp_path, monkeypatch, variant, block, n_rhs):
     """The bulk-copy tiled kernels (8, 9) take the near-direction neighbours
-    from shared memory, the paired kernels (10, 11) run two colours per f32x2
+    from shared memory, the paired kernels (10-13) run two colours per f32x2
     instruction; all form every sum in the plain kernel's order, so every
     operator (hop, Schur, normal: g5 inputs, aux terms, fused norms) must agree
     bit for bit, on a lattice whose tiles straddle rows, wraps and a ragged
