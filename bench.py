@@ -304,7 +304,10 @@ def run_ours(args):
     clocks = sampler.stop()
     ms_step = max_over_ranks(e0.elapsed_time(e1)) / args.steps
     variant, block = hr.hr_tune_lookup(ctx, dims, rep, prec)
-    kernel = f"{HOP_KERNELS[variant] if 0 <= variant < len(HOP_KERNELS) else variant}<fund,{pname}> x{block}"
+    kname = HOP_KERNELS[variant] if 0 <= variant < len(HOP_KERNELS) else str(variant)
+    if pname != "f64" and kname in ("k_hop_x2", "k_hop_x2s"):
+        kname = kname.replace("x2", "f2")  # the FP32-arithmetic paired kernels
+    kernel = f"{kname}<fund,{pname}> x{block}"
     bytes_site = hop_bytes_per_site("fund", pname)
     bytes_step = 2 * Vh * bytes_site
     value = world * bytes_step / (ms_step * 1e-3) / 1e9

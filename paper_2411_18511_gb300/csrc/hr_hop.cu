@@ -186,8 +186,10 @@ hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const H
 bool hop_variant_available(int rep, int prec, int variant)
 {
     (void)prec;
-    // the paired kernel pairs the two colours of the fundamental FP64 layout
-    if (variant >= kVarPaired && variant <= kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
+    // the paired kernels pair the two colours of the fundamental layouts (FP32
+    // arithmetic: variants 10 and 11 only)
+    if (variant == kVarPaired || variant == kVarPairedStaged) return rep == HR_FUND;
+    if (variant == kVarPairedR96 || variant == kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
     // the 96-register caps spill heavily with three colours: fundamental only
     if (variant == kVarSimpleR96) return rep == HR_FUND;
     if (variant == kVarTileR96) return rep == HR_FUND && prec != HR_F16;

@@ -341,6 +341,289 @@ template <int G5IN> __global__ void __maxnreg__(96) k_hop_x2_r96(HopArgs a) { x2
 template <int G5IN> __global__ void __launch_bounds__(256) k_hop_x2s(HopArgs a) { x2s_body<G5IN>(a); }
 template <int G5IN> __global__ void __maxnreg__(96) k_hop_x2s_r96(HopArgs a) { x2s_body<G5IN>(a); }
 
+// ---------------------------------------------------------------- FP32 / FP16 storage
+// The same pairing for the FP32-arithmetic hops: the FP32 and FP16 layouts are
+// colour-paired too (per spin (c0.re, c1.re, c0.im, c1.im)), a vector gives
+// lane pairs at once, and each colour-product output is one packed multiply
+// and three packed FMAs.  Results agree with the scalar kernels to rounding
+// (their FMA contraction is the compiler's), not bit for bit.
+
+struct cf2 {
+    float2 re, im; // a colour doublet of complex numbers
+};
+
+template <int S> __device__ __forceinline__ float2 fadd_s(const K2 &k, float2 a, float2 b)
+{
+    return __ffma2_rn(b, S > 0 ? k.one : k.mone, a); // a + S b
+}
+// x + i^C y
+template <int C> __device__ __forceinline__ cf2 fadd_pow_i(const K2 &k, const cf2 &x, const cf2 &y)
+{
+    if constexpr (C == 0) return {fadd_s<1>(k, x.re, y.re), fadd_s<1>(k, x.im, y.im)};
+    else if constexpr (C == 1) return {fadd_s<-1>(k, x.re, y.im), fadd_s<1>(k, x.im, y.re)};
+    else if constexpr (C == 2) return {fadd_s<-1>(k, x.re, y.re), fadd_s<-1>(k, x.im, y.im)};
+    else return {fadd_s<1>(k, x.re, y.im), fadd_s<-1>(k, x.im, y.re)};
+}
+// i^C y
+template <int C> __device__ __forceinline__ cf2 fpow_i(const K2 &k, const cf2 &y)
+{
+    const auto neg = [&](float2 v) { return __ffma2_rn(v, k.mone, k.zero); };
+    if constexpr (C == 0) return y;
+    else if constexpr (C == 1) return {neg(y.im), y.re};
+    else if constexpr (C == 2) return {neg(y.re), neg(y.im)};
+    else return {y.im, neg(y.re)};
+}
+
+// link coefficient pairs (see Link2) and their negations
+struct Link2f {
+    float2 c0, c1, c2, c3, n1, n2, n3;
+};
+__device__ __forceinline__ Link2f link2f(float a0, float a1, float a2, float a3)
+{
+    Link2f L;
+    L.c0 = make_float2(a0, a0);
+    L.c1 = make_float2(a1, a1);
+    L.c2 = make_float2(a2, -a2);
+    L.c3 = make_float2(a3, -a3);
+    L.n1 = make_float2(-a1, -a1);
+    L.n2 = make_float2(-a2, a2);
+    L.n3 = make_float2(-a3, a3);
+    return L;
+}
+// r = U h (FWD) or U^+ h: re = C0 hr -/+ C3 hi +/- C2 sr -/+ C1 si,
+// im = C0 hi +/- C3 hr +/- C2 si +/- C1 sr (s = swap(h); upper signs forward)
+template <bool FWD> __device__ __forceinline__ cf2 su2_f2(const K2 &k, const Link2f &U, const cf2 &h)
+{
+    const float2 sr = swap2(h.re), si = swap2(h.im);
+    const float2 p3 = FWD ? U.c3 : U.n3, m3 = FWD ? U.n3 : U.c3;
+    const float2 p2 = FWD ? U.c2 : U.n2, p1 = FWD ? U.c1 : U.n1, m1 = FWD ? U.n1 : U.c1;
+    cf2 r;
+    r.re = __ffma2_rn(U.c0, h.re, k.zero);
+    r.re = __ffma2_rn(m3, h.im, r.re);
+    r.re = __ffma2_rn(p2, sr, r.re);
+    r.re = __ffma2_rn(m1, si, r.re);
+    r.im = __ffma2_rn(U.c0, h.im, k.zero);
+    r.im = __ffma2_rn(p3, h.re, r.im);
+    r.im = __ffma2_rn(p2, si, r.im);
+    r.im = __ffma2_rn(p1, sr, r.im);
+    return r;
+}
+
+template <int T, class D, int F, bool FIRST>
+__device__ __forceinline__ void f2_rebuild(const K2 &k, const cf2 &r, cf2 (&acc)[4])
+{
+    if constexpr (FIRST) acc[T] = fpow_i<F>(k, r);
+    else acc[T] = fadd_pow_i<F>(k, acc[T], r);
+    if constexpr (D::rho0 == T) {
+        if constexpr (FIRST) acc[2] = fpow_i<(D::d0 + F) & 3>(k, r);
+        else acc[2] = fadd_pow_i<(D::d0 + F) & 3>(k, acc[2], r);
+    }
+    if constexpr (D::rho1 == T) {
+        if constexpr (FIRST) acc[3] = fpow_i<(D::d1 + F) & 3>(k, r);
+        else acc[3] = fadd_pow_i<(D::d1 + F) & 3>(k, acc[3], r);
+    }
+}
+
+// one direction from the site's 8 packed reals (spin t: re pair, im pair) and
+// the link scaled by sc (binary16: the neighbour's scale rides on the link)
+template <int MU, bool FWD, bool FIRST, bool NEG>
+__device__ __forceinline__ void f2_compute(const K2 &k, const float2 (&sv)[8], float a0, float a1, float a2, float a3,
+                                           cf2 (&acc)[4])
+{
+    using D = X2Dir<MU, FWD>;
+    cf2 s[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) s[t] = {sv[2 * t], sv[2 * t + 1]};
+    constexpr int F = NEG ? 2 : 0;
+    const cf2 h0 = fadd_pow_i<(D::c0 + F) & 3>(k, s[0], s[D::pi0]);
+    const cf2 h1 = fadd_pow_i<(D::c1 + F) & 3>(k, s[1], s[D::pi1]);
+    const Link2f U = link2f(a0, a1, a2, a3);
+    f2_rebuild<0, D, F, FIRST>(k, su2_f2<FWD>(k, U, h0), acc);
+    f2_rebuild<1, D, F, FIRST>(k, su2_f2<FWD>(k, U, h1), acc);
+}
+
+// the packed reals of a site as 8 lane pairs, and its binary16 scale
+template <int PREC>
+__device__ __forceinline__ void f2_load_site(const HopArgs &a, int j, float2 (&sv)[8], float &sc)
+{
+    if constexpr (PREC == kF32) {
+        const float4 *p = (const float4 *)a.in;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 w = __ldg(p + vec_index(j, v, 4));
+            sv[2 * v] = make_float2(w.x, w.y);
+            sv[2 * v + 1] = make_float2(w.z, w.w);
+        }
+        sc = 1.f;
+    } else {
+        const uint4 *p = (const uint4 *)a.in;
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const uint4 w = __ldg(p + vec_index(j, v, 2));
+            const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sv[4 * v + q] = __half22float2(*reinterpret_cast<const __half2 *>(&u[q]));
+        }
+        sc = __ldg((const float *)((const char *)a.in + SpinorLayout<2, kF16>::data_bytes(a.g.nblk_s)) + j);
+    }
+}
+
+template <int MU, bool FWD, bool FIRST, bool NEG, int PREC>
+__device__ __forceinline__ void f2_term(const HopArgs &a, const K2 &k, int site_link, int link_par, int j_nb,
+                                        cf2 (&acc)[4])
+{
+    float2 sv[8];
+    float sc;
+    f2_load_site<PREC>(a, j_nb, sv, sc);
+    float q[4];
+    load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+    if constexpr (PREC == kF16) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q[c] *= sc;
+    }
+    f2_compute<MU, FWD, FIRST, NEG>(k, sv, q[0], q[1], q[2], q[3], acc);
+}
+
+template <int MU, bool FIRST, bool NEG, int PREC>
+__device__ __forceinline__ void f2_dir(const HopArgs &a, const K2 &k, int i, int rr, const SiteNb &nb, cf2 (&acc)[4])
+{
+    const int l = a.g.lrhs;
+    f2_term<MU, true, FIRST, NEG, PREC>(a, k, i, a.p, (nb.fwd[MU] << l) + rr, acc);
+    f2_term<MU, false, false, NEG, PREC>(a, k, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, acc);
+}
+
+template <int PREC, int G5IN>
+__device__ __forceinline__ void f2_body(const HopArgs &a)
+{
+    constexpr bool NEG = G5IN != 0;
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const K2 k = {make_float2(a.unit, a.unit), make_float2(-a.unit, -a.unit), make_float2(a.nil, a.nil)};
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const float be = a.beta.h;
+    const float bu = a.g5_out ? -be : be;
+    const float al = a.alpha.h;
+    SqAcc<float> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        cf2 acc[4];
+        f2_dir<0, true, NEG, PREC>(a, k, i, rr, nb, acc);
+        f2_dir<1, false, NEG, PREC>(a, k, i, rr, nb, acc);
+        f2_dir<2, false, NEG, PREC>(a, k, i, rr, nb, acc);
+        f2_dir<3, false, NEG, PREC>(a, k, i, rr, nb, acc);
+        cpx<float> o[4][2];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            o[t][0] = {acc[t].re.x, acc[t].im.x};
+            o[t][1] = {acc[t].re.y, acc[t].im.y};
+        }
+        hop_epilogue<PREC>(a, j, o, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+// staged form: direction K+1's operands copied by cp.async while K is computed
+template <int K, bool NEG, int PREC>
+__device__ __forceinline__ void f2_stage_step(const HopArgs &a, const K2 &k, int i, int rr, const SiteNb &nb,
+                                              uint4 *b0, uint4 *b1, int bd, cf2 (&acc)[4])
+{
+    using S = Stage<kRepFund, PREC>;
+    uint4 *cur = (K & 1) ? b1 : b0;
+    uint4 *nxt = (K & 1) ? b0 : b1;
+    if constexpr (K < 7) {
+        stage_issue<K + 1, kRepFund, PREC>(a, i, rr, nb, nxt, bd);
+        cp_async_commit();
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
+    float2 sv[8];
+    float q[4];
+    if constexpr (PREC == kF32) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 w = *reinterpret_cast<const float4 *>(cur + v * bd);
+            sv[2 * v] = make_float2(w.x, w.y);
+            sv[2 * v + 1] = make_float2(w.z, w.w);
+        }
+        const float4 qv = *reinterpret_cast<const float4 *>(cur + S::NV * bd);
+        q[0] = qv.x; q[1] = qv.y; q[2] = qv.z; q[3] = qv.w;
+    } else {
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const uint4 w = cur[v * bd];
+            const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sv[4 * v + c] = __half22float2(*reinterpret_cast<const __half2 *>(&u[c]));
+        }
+        // the link slot holds 8 bytes (cp.async of a uint2), the scale slot 4
+        const uint2 qw = *reinterpret_cast<const uint2 *>(cur + S::NV * bd);
+        const float2 q01 = __half22float2(*reinterpret_cast<const __half2 *>(&qw.x));
+        const float2 q23 = __half22float2(*reinterpret_cast<const __half2 *>(&qw.y));
+        const float sc = *reinterpret_cast<const float *>(cur + (S::NV + S::NQ) * bd);
+        q[0] = q01.x * sc; q[1] = q01.y * sc; q[2] = q23.x * sc; q[3] = q23.y * sc;
+    }
+    f2_compute<(K >> 1), (K & 1) == 0, K == 0, NEG>(k, sv, q[0], q[1], q[2], q[3], acc);
+}
+
+template <int PREC, int G5IN>
+__device__ __forceinline__ void f2s_body(const HopArgs &a)
+{
+    using S = Stage<kRepFund, PREC>;
+    constexpr bool NEG = G5IN != 0;
+    extern __shared__ uint4 f2_stage_mem[];
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const K2 k = {make_float2(a.unit, a.unit), make_float2(-a.unit, -a.unit), make_float2(a.nil, a.nil)};
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const int bd = blockDim.x;
+    uint4 *b0 = f2_stage_mem + threadIdx.x;
+    uint4 *b1 = f2_stage_mem + S::NSLOT * bd + threadIdx.x;
+    const float be = a.beta.h;
+    const float bu = a.g5_out ? -be : be;
+    const float al = a.alpha.h;
+    SqAcc<float> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        stage_issue<0, kRepFund, PREC>(a, i, rr, nb, b0, bd);
+        cp_async_commit();
+        cf2 acc[4];
+        f2_stage_step<0, NEG, PREC>(a, k, i, rr, nb, b0, b1, bd, acc);
+        f2_stage_step<1, NEG, PREC>(a, k, i, rr, nb, b0, b1, bd, acc);
+        f2_stage_step<2, NEG, PREC>(a, k, i, rr, nb, b0, b1, bd, acc);
+        f2_stage_step<3, NEG, PREC>(a, k, i, rr, nb, b0, b1, bd, acc);
+        f2_stage_step<4, NEG, PREC>(a, k, i, rr, nb, b0, b1, bd, acc);
+        f2_stage_step<5, NEG, PREC>(a, k, i, rr, nb, b0, b1, bd, acc);
+        f2_stage_step<6, NEG, PREC>(a, k, i, rr, nb, b0, b1, bd, acc);
+        f2_stage_step<7, NEG, PREC>(a, k, i, rr, nb, b0, b1, bd, acc);
+        cpx<float> o[4][2];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            o[t][0] = {acc[t].re.x, acc[t].im.x};
+            o[t][1] = {acc[t].re.y, acc[t].im.y};
+        }
+        hop_epilogue<PREC>(a, j, o, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+template <int PREC, int G5IN> __global__ void __launch_bounds__(256) k_hop_f2(HopArgs a) { f2_body<PREC, G5IN>(a); }
+template <int PREC, int G5IN> __global__ void __launch_bounds__(256) k_hop_f2s(HopArgs a) { f2s_body<PREC, G5IN>(a); }
+
 template <int REP, int PREC> struct Launch {
     static bool run(hr_ctx *ctx, const Geom &, const HopArgs &a, HopChoice c, int grid, cudaStream_t s,
                     hr_status &st)
@@ -361,6 +644,24 @@ template <int REP, int PREC> struct Launch {
             case kVarPairedR96: (g5 ? k_hop_x2_r96<1> : k_hop_x2_r96<0>)<<<grid, c.block, 0, s>>>(a); break;
             default: (g5 ? k_hop_x2<1> : k_hop_x2<0>)<<<grid, c.block, 0, s>>>(a); break;
             }
+            st = check_launch(ctx, "paired hop kernel");
+            return true;
+        } else if constexpr (REP == kRepFund) {
+            // FP32 arithmetic: the register-capped forms are not built (the
+            // kernels need far fewer registers): those variants run the plain kernel
+            if (c.variant != kVarPaired && c.variant != kVarPairedStaged) return false;
+            using S = Stage<kRepFund, PREC>;
+            static bool attr_set = false;
+            if (!attr_set) {
+                for (auto f : {k_hop_f2s<PREC, 0>, k_hop_f2s<PREC, 1>})
+                    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes(256));
+                attr_set = true;
+            }
+            const bool g5 = a.g5_in != 0;
+            if (c.variant == kVarPairedStaged)
+                (g5 ? k_hop_f2s<PREC, 1> : k_hop_f2s<PREC, 0>)<<<grid, c.block, S::smem_bytes(c.block), s>>>(a);
+            else
+                (g5 ? k_hop_f2<PREC, 1> : k_hop_f2<PREC, 0>)<<<grid, c.block, 0, s>>>(a);
             st = check_launch(ctx, "paired hop kernel");
             return true;
         }

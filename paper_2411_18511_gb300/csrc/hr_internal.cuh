@@ -21,9 +21,11 @@
 //                lo parts in the same order, so a vector holds the two colours
 //                of one part side by side (what the packed f32x2 hop uses).
 //                NC = 3: one complex per float4, (re.h, im.h, re.l, im.l).
-//   spinor FP32: NVEC = 2*NC float4  (two complex each)
-//   spinor FP16: NVEC = NC   uint4   (four complex each, binary16), followed by
-//                one float scale per site (the site's max |component|)
+//   spinor FP32: NVEC = 2*NC float4, FP16: NVEC = NC uint4 (binary16, followed
+//                by one float scale per site, the site's max |component|): the
+//                8*NC reals in packed order -- NC = 2 (colour-paired): spin s
+//                gives (c0.re, c1.re, c0.im, c1.im); NC = 3: (re, im) of each
+//                (spin, colour) in turn.
 //   gauge (quaternion links): link (p, mu, i) in slot L = (p*4+mu)*nblk + i/32,
 //     FP64 two float4 (the four hi parts, then the four lo parts) at
 //     (L*2+v)*32 + i%32, FP32 one float4, FP16 one uint2
@@ -299,6 +301,56 @@ __device__ __forceinline__ size_t vec_index(int j, int v, int nvec)
     return ((size_t)(j >> 5) * nvec + v) * 32 + (j & 31);
 }
 
+// position of Re / Im of (spin sp, colour c) among the 8 NC reals of a site in
+// the packed order of the FP32 / FP16 layouts (and of the FP64 hi/lo vectors
+// when NC = 2)
+template <int NC> __host__ __device__ constexpr int packed_re(int sp, int c)
+{
+    return NC == 2 ? 4 * sp + c : 2 * (NC * sp + c);
+}
+template <int NC> __host__ __device__ constexpr int packed_im(int sp, int c)
+{
+    return NC == 2 ? 4 * sp + 2 + c : 2 * (NC * sp + c) + 1;
+}
+template <int NC, class T>
+__device__ __forceinline__ void values_from_packed(const float *r, float sc, cpx<T> (&s)[4][NC])
+{
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            s[sp][c] = {Real<T>::from_float(r[packed_re<NC>(sp, c)] * sc),
+                        Real<T>::from_float(r[packed_im<NC>(sp, c)] * sc)};
+}
+template <int NC, class T> __device__ __forceinline__ void values_to_packed(const cpx<T> (&s)[4][NC], float *r)
+{
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            r[packed_re<NC>(sp, c)] = Real<T>::to_float(s[sp][c].re);
+            r[packed_im<NC>(sp, c)] = Real<T>::to_float(s[sp][c].im);
+        }
+}
+__device__ __forceinline__ void float4_to_floats(const float4 &w, float *f)
+{
+    f[0] = w.x;
+    f[1] = w.y;
+    f[2] = w.z;
+    f[3] = w.w;
+}
+// the 8 binary16 reals of one uint4, in order
+__device__ __forceinline__ void halves_to_floats(const uint4 &w, float *f)
+{
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 t = __half22float2(*reinterpret_cast<const __half2 *>(&u[q]));
+        f[2 * q] = t.x;
+        f[2 * q + 1] = t.y;
+    }
+}
+
 // FP64 vectors <-> values (layout above)
 template <int NC, class T>
 __device__ __forceinline__ void f64_from_vecs(const float4 *w, cpx<T> (&s)[4][NC])
@@ -346,7 +398,6 @@ __device__ __forceinline__ void load_spinor(const void *base, int nblk, int j, c
 {
     using L = SpinorLayout<NC, PREC>;
     constexpr int NV = L::NVEC;
-    cpx<T> *flat = &s[0][0];
     if constexpr (PREC == kF64) {
         const float4 *p = (const float4 *)base;
         float4 w[NV];
@@ -355,27 +406,18 @@ __device__ __forceinline__ void load_spinor(const void *base, int nblk, int j, c
         f64_from_vecs<NC>(w, s);
     } else if constexpr (PREC == kF32) {
         const float4 *p = (const float4 *)base;
+        float r[8 * NC];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            float4 w = __ldg(p + vec_index(j, v, NV));
-            flat[2 * v] = {Real<T>::from_float(w.x), Real<T>::from_float(w.y)};
-            flat[2 * v + 1] = {Real<T>::from_float(w.z), Real<T>::from_float(w.w)};
-        }
+        for (int v = 0; v < NV; ++v) float4_to_floats(__ldg(p + vec_index(j, v, NV)), &r[4 * v]);
+        values_from_packed<NC>(r, 1.f, s);
     } else {
         const uint4 *p = (const uint4 *)base;
         const float *nrm = (const float *)((const char *)base + L::data_bytes(nblk));
-        float sc = __ldg(nrm + j);
+        const float sc = __ldg(nrm + j);
+        float r[8 * NC];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            uint4 w = __ldg(p + vec_index(j, v, NV));
-            uint32_t u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                __half2 h = *reinterpret_cast<__half2 *>(&u[q]);
-                float2 f = __half22float2(h);
-                flat[4 * v + q] = {Real<T>::from_float(f.x * sc), Real<T>::from_float(f.y * sc)};
-            }
-        }
+        for (int v = 0; v < NV; ++v) halves_to_floats(__ldg(p + vec_index(j, v, NV)), &r[8 * v]);
+        values_from_packed<NC>(r, sc, s);
     }
 }
 
@@ -388,19 +430,12 @@ __device__ __forceinline__ void load_spinor_raw(const void *base, int nblk, int 
     if constexpr (PREC == kF16) {
         using L = SpinorLayout<NC, PREC>;
         constexpr int NV = L::NVEC;
-        cpx<T> *flat = &s[0][0];
         const uint4 *p = (const uint4 *)base;
         sc = __ldg((const float *)((const char *)base + L::data_bytes(nblk)) + j);
+        float r[8 * NC];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            uint4 w = __ldg(p + vec_index(j, v, NV));
-            uint32_t u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float2 f = __half22float2(*reinterpret_cast<__half2 *>(&u[q]));
-                flat[4 * v + q] = {Real<T>::from_float(f.x), Real<T>::from_float(f.y)};
-            }
-        }
+        for (int v = 0; v < NV; ++v) halves_to_floats(__ldg(p + vec_index(j, v, NV)), &r[8 * v]);
+        values_from_packed<NC>(r, 1.f, s);
     } else {
         sc = 1.f;
         load_spinor<NC, PREC>(base, nblk, j, s);
@@ -412,7 +447,6 @@ __device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const 
 {
     using L = SpinorLayout<NC, PREC>;
     constexpr int NV = L::NVEC;
-    const cpx<T> *flat = &s[0][0];
     if constexpr (PREC == kF64) {
         float4 *p = (float4 *)base;
         float4 w[NV];
@@ -421,20 +455,15 @@ __device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const 
         for (int v = 0; v < NV; ++v) p[vec_index(j, v, NV)] = w[v];
     } else if constexpr (PREC == kF32) {
         float4 *p = (float4 *)base;
+        float r[8 * NC];
+        values_to_packed<NC>(s, r);
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-            p[vec_index(j, v, NV)] = make_float4(Real<T>::to_float(flat[2 * v].re), Real<T>::to_float(flat[2 * v].im),
-                                                 Real<T>::to_float(flat[2 * v + 1].re),
-                                                 Real<T>::to_float(flat[2 * v + 1].im));
+        for (int v = 0; v < NV; ++v) p[vec_index(j, v, NV)] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
     } else {
         uint4 *p = (uint4 *)base;
         float *nrm = (float *)((char *)base + L::data_bytes(nblk));
         float f[8 * NC];
-#pragma unroll
-        for (int k = 0; k < 4 * NC; ++k) {
-            f[2 * k] = Real<T>::to_float(flat[k].re);
-            f[2 * k + 1] = Real<T>::to_float(flat[k].im);
-        }
+        values_to_packed<NC>(s, f);
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 8 * NC; ++k) m = fmaxf(m, fabsf(f[k]));
@@ -445,7 +474,7 @@ __device__ __forceinline__ void store_spinor(void *base, int nblk, int j, const 
             uint32_t u[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                __half2 h = __floats2half2_rn(f[2 * (4 * v + q)] * inv, f[2 * (4 * v + q) + 1] * inv);
+                __half2 h = __floats2half2_rn(f[8 * v + 2 * q] * inv, f[8 * v + 2 * q + 1] * inv);
                 u[q] = *reinterpret_cast<uint32_t *>(&h);
             }
             p[vec_index(j, v, NV)] = make_uint4(u[0], u[1], u[2], u[3]);
@@ -465,24 +494,16 @@ __device__ __forceinline__ void spinor_from_vecs(const uint4 *w, float sc, cpx<T
 #pragma unroll
         for (int v = 0; v < NV; ++v) f[v] = *reinterpret_cast<const float4 *>(&w[v]);
         f64_from_vecs<NC>(f, s);
+    } else if constexpr (PREC == kF32) {
+        float r[8 * NC];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) float4_to_floats(*reinterpret_cast<const float4 *>(&w[v]), &r[4 * v]);
+        values_from_packed<NC>(r, 1.f, s);
     } else {
-        cpx<T> *flat = &s[0][0];
+        float r[8 * NC];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const uint4 u = w[v];
-            if constexpr (PREC == kF32) {
-                float4 f = *reinterpret_cast<const float4 *>(&u);
-                flat[2 * v] = {Real<T>::from_float(f.x), Real<T>::from_float(f.y)};
-                flat[2 * v + 1] = {Real<T>::from_float(f.z), Real<T>::from_float(f.w)};
-            } else {
-                uint32_t q4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&q4[q]));
-                    flat[4 * v + q] = {Real<T>::from_float(f.x * sc), Real<T>::from_float(f.y * sc)};
-                }
-            }
-        }
+        for (int v = 0; v < NV; ++v) halves_to_floats(w[v], &r[8 * v]);
+        values_from_packed<NC>(r, sc, s);
     }
 }
 
