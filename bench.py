@@ -37,6 +37,10 @@ METRIC = "Dirac-op GB/s & % HBM peak at 48^4 SU(2); mixed vs FP64 CG time to 1e-
 DIMS = (48, 48, 48, 48)
 GAUGE_SEED, SPINOR_SEED = 1003, 2003
 HBM_FALLBACK = 6800.0
+HBM_NOMINAL_GBS = 8000.0  # the HBM3e figure the target is quoted against
+# Wilson hopping-term flops per output site, 8*16*Nc^2 + 7*4*Nc*2 (fund 624,
+# adjoint with real 3x3 links 744), the convention of the paper's field
+HOP_FLOPS = {"fund": 624, "adj": 744}
 # FP32-pipe roofline of GB300: 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)
 FP32_PEAK_GOPS = 152 * 128 * 2.070
 # Essential FP32-pipe operations per output site of the double-float fundamental hop
@@ -349,6 +353,8 @@ def run_ours(args):
             "bytes_per_site": bytes_site,
             "byte_convention": "compulsory (1 spinor in + 1 out + 8 quaternion links)",
             "neighbour_counted_gbs": round(value * neighbour_bytes_per_site("fund", pname) / bytes_site, 2),
+            "gflops": round(value * HOP_FLOPS["fund"] / bytes_site, 1),
+            "pct_of_nominal_8000": round(100 * value / HBM_NOMINAL_GBS, 1),
             "l2": f"inputs larger than L2 (gauge {gauge_mb:.0f} MB + spinor half {half / 1e6:.0f} MB per launch)",
             "parallelism": f"replicas{world}",
         },
@@ -400,12 +406,14 @@ def run_e2e(args, ctx, torch, hr, dims, rep, prec, psi, src, dst, step, stream, 
                     "hr_spinor_unpack -> D2H"}
 
 
-def time_hop(ctx, torch, hr, fields, dims, rep, prec, q, psi, steps=100):
-    """Average GB/s of one hop launch (compulsory bytes) for a rep/prec."""
+def time_hop(ctx, torch, hr, fields, dims, rep, prec, q, psi, steps=100, peak=None):
+    """Average GB/s of one hop launch (compulsory bytes) for a rep/prec, with
+    the autotuner's launch shape for the configuration."""
     gauge = fields.pack_gauge(ctx, dims, rep, prec, fields.gauge_to_device(q))
     src = fields.pack_spinor(ctx, dims, rep, prec, hr.HR_ODD, psi)
     dst = fields.empty_spinor(dims, rep, prec, hr.HR_EVEN)
-    for _ in range(5):
+    res = hr.hr_autotune_hop(ctx, dims, rep, prec, hr.HR_EVEN, 1, gauge, src, dst, reps=10)
+    for _ in range(20):
         hr.hr_dirac_eo(ctx, dims, 0.0, rep, prec, hr.HR_EVEN, hr.HR_OP_HOP, 1, gauge, src, dst)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -421,7 +429,15 @@ def time_hop(ctx, torch, hr, fields, dims, rep, prec, q, psi, steps=100):
     b = hop_bytes_per_site(rname, pname)
     if rep == hr.HR_ADJ_MAT:
         b += 8 * ({"f64": 72, "f32": 36, "f16": 18}[pname] - {"f64": 32, "f32": 16, "f16": 8}[pname])
-    return {"ms": round(ms, 5), "gbs": round(Vh * b / (ms * 1e-3) / 1e9, 1), "bytes_per_site": b}
+    gbs = Vh * b / (ms * 1e-3) / 1e9
+    out = {"ms": round(ms, 5), "gbs": round(gbs, 1), "bytes_per_site": b,
+           "gflops": round(Vh * HOP_FLOPS[rname] / (ms * 1e-3) / 1e9, 1),
+           "pct_of_nominal_8000": round(100 * gbs / HBM_NOMINAL_GBS, 1),
+           "launch": {"variant": HOP_VARIANT_NAMES[res.variant] if 0 <= res.variant < len(HOP_VARIANT_NAMES)
+                      else res.variant, "block": res.block}}
+    if peak:
+        out["pct_of_measured_copy"] = round(100 * gbs / peak, 1)
+    return out
 
 
 def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
@@ -431,13 +447,14 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     # precision / representation sweep of the hop at 48^4 (config: adjoint FP64 and FP32, 200 applications)
     fund_psi = fields.spinor_to_device(psi48)
     for prec in (hr.HR_F32, hr.HR_F16):
-        out[f"hop_fund_{ {1: 'f32', 2: 'f16'}[prec]}_48"] = time_hop(ctx, torch, hr, fields, dims, hr.HR_FUND, prec, q48, fund_psi)
+        out[f"hop_fund_{ {1: 'f32', 2: 'f16'}[prec]}_48"] = time_hop(ctx, torch, hr, fields, dims, hr.HR_FUND, prec, q48,
+                                                                      fund_psi, peak=measured_peaks()[0])
     del fund_psi
     adj_psi = fields.spinor_to_device(synth.gaussian_spinor(dims, 3, 2004))
     for rep, rn in ((hr.HR_ADJ, "adj"), (hr.HR_ADJ_MAT, "adjmat")):
         for prec in (hr.HR_F64, hr.HR_F32):
             out[f"hop_{rn}_{ {0: 'f64', 1: 'f32'}[prec]}_48"] = time_hop(
-                ctx, torch, hr, fields, dims, rep, prec, q48, adj_psi, steps=200)
+                ctx, torch, hr, fields, dims, rep, prec, q48, adj_psi, steps=200, peak=measured_peaks()[0])
     del adj_psi
     torch.cuda.empty_cache()
     # CG time to solution at 32^4 (smeared links, plaquette ~0.6, m0 = -0.2, tol 1e-10)
@@ -469,11 +486,11 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
             work = fields.empty_bytes(hr.hr_cg_workspace_bytes(d32, hr.HR_FUND, opts))
             times = []
             info = rc = None
-            for rep_i in range(4):  # the first solve also captures the iteration graph
+            for rep_i in range(6):  # one warm-up solve (it also captures the solve graph), five timed
                 rc, info = hr.hr_cg_solve(ctx, d32, -0.2, hr.HR_FUND, opts, gauge, bp, xp, work)
                 times.append(info.seconds)
             rec = {"status": hr.STATUS_NAMES.get(rc, rc), "seconds_median": round(statistics.median(times[1:]), 4),
-                   "first_solve_s": round(times[0], 4), "iters": info.iters,
+                   "first_solve_s": round(times[0], 4), "timed_solves": len(times) - 1, "iters": info.iters,
                    "reliable_updates": info.n_reliable_updates, "true_rel_residual": info.true_rel_residual,
                    "reliable_delta": delta}
             sweep[str(delta)] = rec["seconds_median"]
@@ -489,10 +506,46 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     out["cg_32"] = cg
     del gauge, bp
     torch.cuda.empty_cache()
+    out["diff_solve_16"] = run_diff_solve(torch, synth)
+    torch.cuda.empty_cache()
     out["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
     torch.cuda.empty_cache()
     out["batch_12"] = run_batch(ctx, torch, hr, fields, synth)
     return out
+
+
+def run_diff_solve(torch, synth):
+    """16^4 fund FP64: S = Re<eta, (Mhat^+ Mhat)^-1 eta> through the autograd
+    solve; forward (one solve) and backward (one adjoint solve and the link
+    gradient) wall times."""
+    from paper_2411_18511_gb300 import autograd as ag
+    import oracle
+    d = (16, 16, 16, 16)
+    m0 = -0.2
+    q, nsm, plaq = synth.ape_smear_to_plaquette(synth.haar_links(d, 1005), d, 0.6)
+    eta = synth.gaussian_spinor(d, 2, 2005)
+    eta[oracle.parity_mask(d) == 1] = 0
+    qt = torch.tensor(q, device="cuda")
+    et = torch.tensor(eta, device="cuda")
+    fwd, bwd = [], []
+    for _ in range(4):
+        qg = qt.clone().requires_grad_(True)
+        eg = et.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = ag.EoSolve.apply(qg, eg, d, m0, 1e-10)
+        S = torch.sum(eg.conj() * x).real
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        S.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        fwd.append(t1 - t0)
+        bwd.append(t2 - t1)
+    return {"lattice": list(d), "m0": m0, "tol": 1e-10, "plaquette": round(plaq, 4),
+            "forward_s": round(statistics.median(fwd[1:]), 4), "backward_s": round(statistics.median(bwd[1:]), 4),
+            "backward_over_forward": round(statistics.median(bwd[1:]) / statistics.median(fwd[1:]), 2),
+            "note": "wall times incl. packing; backward = adjoint solve + link gradient kernels"}
 
 
 def run_batch(ctx, torch, hr, fields, synth):
@@ -550,6 +603,14 @@ def run_multi_rhs(ctx, torch, hr, fields, synth):
         opts = hr.hr_solver_default_opts()
         opts.inner_prec = hr.HR_F32
         opts.n_rhs = n
+        # the solver's hop shapes (FP32 inner, FP64 reliable updates) tuned for this N
+        tuned = {}
+        for tp, gp in ((hr.HR_F32, g32), (hr.HR_F64, gauge)):
+            ts = fields.pack_spinor(ctx, d, hr.HR_FUND, tp, hr.HR_ODD, dev)
+            td = fields.empty_spinor(d, hr.HR_FUND, tp, hr.HR_EVEN, n)
+            tr = hr.hr_autotune_hop(ctx, d, hr.HR_FUND, tp, hr.HR_EVEN, n, gp, ts, td, reps=10)
+            tuned[{hr.HR_F32: "f32", hr.HR_F64: "f64"}[tp]] = [tr.variant, tr.block]
+            del ts, td
         work = fields.empty_bytes(hr.hr_cg_workspace_bytes(d, hr.HR_FUND, opts))
         times = []
         info = rc = None
@@ -577,7 +638,8 @@ def run_multi_rhs(ctx, torch, hr, fields, synth):
         res[f"n{n}"] = {"status": hr.STATUS_NAMES.get(rc, rc), "solve_s": round(t, 4),
                         "per_rhs_s": round(t / n, 5), "per_rhs_speedup_vs_n1": round(t1 / (t / n), 3),
                         "iters": info.iters, "true_rel_residual": info.true_rel_residual,
-                        "hop_ms": round(hop_ms, 5), "hop_gbs": round(hop_bytes / (hop_ms * 1e-3) / 1e9, 1)}
+                        "hop_ms": round(hop_ms, 5), "hop_gbs": round(hop_bytes / (hop_ms * 1e-3) / 1e9, 1),
+                        "tuned_hop_shapes": tuned}
         del work, bp, src, dst, dev
         torch.cuda.empty_cache()
     return res
@@ -593,10 +655,23 @@ def cpu_baseline(q, psi, dims):
         t0 = time.perf_counter()
         out = oracle.hop(dims, L, psi, parity=-1)
         dt = time.perf_counter() - t0
-        del out, L
         gbs = (V // 2) * 2 * hop_bytes_per_site("fund", "f64") / dt / 1e9
+        # the same oracle on one core, over a sample of 1/16 of the sites
+        rng = np.random.default_rng(7)
+        sites = np.sort(rng.choice(V, V // 16, replace=False)).astype(np.int64)
+        prev = oracle.set_num_threads(1)
+        try:
+            t0 = time.perf_counter()
+            oracle.hop_sites(dims, L, psi, sites)
+            dt1 = time.perf_counter() - t0
+        finally:
+            oracle.set_num_threads(prev)
+        gbs1 = len(sites) * hop_bytes_per_site("fund", "f64") / dt1 / 1e9
+        del out, L
         return {"value": round(gbs, 3), "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
                 "sample": f"one D_eo+D_oe application over all {V} sites of {dims[0]}^4 ({dt:.2f} s)",
+                "single_core": {"value": round(gbs1, 3), "unit": "GB/s", "cores": 1,
+                                "sample": f"{len(sites)} random sites, one hop each ({dt1:.2f} s)"},
                 "cpu": _cpu_model()}
     except Exception as exc:  # the baseline is informative only
         return {"value": None, "unit": "GB/s", "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}

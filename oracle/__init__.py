@@ -74,6 +74,7 @@ def _load():
                 "or_gamma": [I, P],
                 "or_adjoint_link": [P, P],
                 "or_num_threads": [],
+                "or_set_num_threads": [I],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -108,6 +109,11 @@ def volume(dims) -> int:
 
 def num_threads() -> int:
     return int(_load().or_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops from now on; returns the previous count."""
+    return int(_load().or_set_num_threads(int(n)))
 
 
 def gamma(mu: int) -> np.ndarray:

@@ -519,3 +519,15 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* threads for the following parallel loops (n >= 1); returns the previous count */
+int or_set_num_threads(int n)
+{
+    int prev = or_num_threads();
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return prev;
+}
