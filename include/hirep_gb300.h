@@ -202,7 +202,9 @@ size_t hr_cg_batch_workspace_bytes(int n_lat, const hr_lattice *lats, hr_rep rep
  * that SU(2) lattices below 16^4 lose efficiency to fixed overheads (Sec. 3);
  * here every CG phase is one persistent launch over a work list of all the
  * lattices' 128-site tiles, with per-lattice scalars and convergence flags on
- * the device, and a chunk of iterations replays as one CUDA graph.  gauges[l]:
+ * the device; the iteration loop runs on the device as one CUDA graph
+ * (check_every > 0: a graph of that many iterations with a host check after
+ * each), and converged lattices drop out of the work.  gauges[l]:
  * packed HR_F64 gauge of lats[l]; b[l], x[l]: packed HR_F64 even spinors.
  * infos[l] (may be NULL) receives each lattice's iterations and true residual
  * (seconds = the whole batch).  Synchronises the stream.  Returns

@@ -8,13 +8,14 @@
 // whose blocks walk a work list of (lattice, 128-site tile) entries.  Each
 // lattice keeps its own device scalars (alpha, beta, |r|^2, convergence flag);
 // reductions finish per lattice in its last tile (deterministic tile order);
-// converged lattices drop out of the work.  A chunk of iterations is captured
-// once in a CUDA graph and replayed until every lattice has converged.
+// converged lattices drop out of the work.  The iteration loop runs on the
+// device as one CUDA graph: a conditional WHILE node over passes of 8
+// iterations, its condition set from the lattices' done flags.
 #include <cmath>
 #include <cstring>
 #include <vector>
 
-#include "hr_hop_dev.cuh"
+#include "hr_hop_x2.cuh"
 
 using namespace hr;
 
@@ -42,6 +43,7 @@ struct BatchArgs {
     int total_tiles;
     int use_x;       // hop phases act on x instead of p (true residual)
     int ignore_done; // run converged lattices too (true residual)
+    float unit, nil; // 1 and 0 at run time (the paired arithmetic's multipliers)
 };
 
 __device__ __forceinline__ int find_lat(const BatchLat *L, int n, int tile)
@@ -109,7 +111,24 @@ __global__ void __launch_bounds__(kTile) k_batch_hop(BatchArgs B)
         const T al = Real<T>::from_coef(a.alpha);
         SqAcc<T> red;
         const int j = (tile - L.tile0) * kTile + threadIdx.x;
-        if (j < L.g.vh) hop_site<REP, kF64>(a, j, al, be, bu, red);
+        if (j < L.g.vh) {
+            if constexpr (REP == kRepFund) {
+                // the paired (f32x2) double-float arithmetic of the single-lattice
+                // hop: the same sums in the same order, half the instructions
+                constexpr bool NEG = PHASE == 2;
+                const K2 k = {make_float2(B.unit, B.unit), make_float2(-B.unit, -B.unit), make_float2(B.nil, B.nil)};
+                SiteNb nb;
+                site_neighbours(a.g, j, a.p, nb);
+                cdd2 acc[4];
+                x2_dir<0, true, NEG>(a, k, j, 0, nb, acc);
+                x2_dir<1, false, NEG>(a, k, j, 0, nb, acc);
+                x2_dir<2, false, NEG>(a, k, j, 0, nb, acc);
+                x2_dir<3, false, NEG>(a, k, j, 0, nb, acc);
+                x2_epilogue(a, j, acc, al, be, bu, red);
+            } else {
+                hop_site<REP, kF64>(a, j, al, be, bu, red);
+            }
+        }
         if (PHASE == 1) tile_reduce(red.get(), L, tile, 0, kFinAlpha, 0);
     }
 }
@@ -285,6 +304,71 @@ hr_status batch_launch_iteration(hr_ctx *ctx, const BatchArgs &B, int grid, cuda
     return check_launch(ctx, "batched CG iteration");
 }
 
+// Device-side control of the one-graph batch solve: another pass of the WHILE
+// body while some lattice is still iterating (its done flag also covers
+// maxiter and NaN), at most 2 maxiter + 64 passes (counted in lattice 0's
+// scalar block).
+__global__ void k_batch_ctl(BatchArgs B, cudaGraphConditionalHandle h, int maxiter)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    bool all = true;
+    for (int l = 0; l < B.nlat; ++l) all = all && sc(B.lat[l].scal, S_FLAGS, F_DONE) != 0.0;
+    double &passes = sc(B.lat[0].scal, S_FLAGS, F_BODY);
+    passes += 1.0;
+    cudaGraphSetConditional(h, (!all && passes < 2.0 * maxiter + 64.0) ? 1u : 0u);
+}
+
+constexpr int kBatchIterPerPass = 8;
+
+// The whole batched loop as one graph: a WHILE node whose body is
+// kBatchIterPerPass iterations and the control kernel (iterations of
+// converged lattices skip their tiles).
+template <int REP>
+hr_status capture_batch_while(hr_ctx *ctx, const BatchArgs &B, int grid, int maxiter, cudaGraph_t *out)
+{
+    cudaGraph_t G = nullptr;
+    cudaStream_t cs = nullptr;
+    bool capturing = false;
+    hr_status st = HR_OK;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](const char *what) -> hr_status {
+        if (capturing) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs, &junk);
+        }
+        if (cs) cudaStreamDestroy(cs);
+        if (G) cudaGraphDestroy(G);
+        if (st) return st;
+        return set_error(ctx, HR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    if ((e = cudaGraphCreate(&G, 0)) != cudaSuccess) return fail("graph create");
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail("capture stream");
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return fail("loop condition");
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if ((e = cudaGraphAddNode(&wnode, G, nullptr, nullptr, 0, &np)) != cudaSuccess) return fail("while node");
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return fail("begin capture");
+    capturing = true;
+    for (int k = 0; k < kBatchIterPerPass && !st; ++k) st = batch_launch_iteration<REP>(ctx, B, grid, cs);
+    if (st) return fail("batched CG iteration");
+    k_batch_ctl<<<1, 32, 0, cs>>>(B, h, maxiter);
+    if ((st = check_launch(ctx, "batch control"))) return fail("batch control");
+    cudaGraph_t same = nullptr;
+    capturing = false;
+    if ((e = cudaStreamEndCapture(cs, &same)) != cudaSuccess) return fail("end capture");
+    cudaStreamDestroy(cs);
+    *out = G;
+    return HR_OK;
+}
+
 template <int REP>
 hr_status batch_true_residual(hr_ctx *ctx, BatchArgs B, int grid, cudaStream_t s)
 {
@@ -381,6 +465,8 @@ hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, doub
     B.total_tiles = P.total_tiles;
     B.use_x = 0;
     B.ignore_done = 0;
+    B.unit = 1.f;
+    B.nil = 0.f;
     int grid = ctx->sm_count > 0 ? ctx->sm_count * 8 : 1024;
     if (grid > P.total_tiles) grid = P.total_tiles;
 
@@ -389,11 +475,19 @@ hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, doub
     hr_status st = check_launch(ctx, "batch start");
     if (st) return st;
 
-    // capture a chunk of iterations once
-    int chunk = opts->check_every > 0 ? opts->check_every : 16;
+    // check_every == 0: the whole loop is one graph (device-side WHILE);
+    // check_every == N: a graph of N iterations, replayed with a host check after each
+    const bool device_loop = opts->check_every <= 0;
+    int chunk = device_loop ? kBatchIterPerPass : opts->check_every;
     if (chunk > opts->maxiter) chunk = opts->maxiter;
     GraphExec G;
-    {
+    if (device_loop) {
+        st = rep == HR_FUND ? capture_batch_while<kRepFund>(ctx, B, grid, opts->maxiter, &G.g)
+                            : capture_batch_while<kRepAdj>(ctx, B, grid, opts->maxiter, &G.g);
+        if (st) return st;
+        e = cudaGraphInstantiate(&G.e, G.g, 0);
+        if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "batch graph: %s", cudaGetErrorString(e));
+    } else {
         cudaStream_t cs;
         e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "capture stream: %s", cudaGetErrorString(e));
@@ -429,7 +523,8 @@ hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, doub
             numeric = numeric || f[F_NUMERIC] != 0.0;
             if ((int)f[F_ITERS] > max_iters) max_iters = (int)f[F_ITERS];
         }
-        if (all || numeric || max_iters >= opts->maxiter || launched >= 2LL * opts->maxiter + chunk) break;
+        if (device_loop || all || numeric || max_iters >= opts->maxiter || launched >= 2LL * opts->maxiter + chunk)
+            break;
     }
     // true residuals
     st = rep == HR_FUND ? batch_true_residual<kRepFund>(ctx, B, grid, s) : batch_true_residual<kRepAdj>(ctx, B, grid, s);

@@ -62,6 +62,35 @@ def test_batch_solves_every_lattice(ctx, rep):
         assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
 
 
+@pytest.mark.parametrize("rep", [hr.HR_FUND, hr.HR_ADJ])
+def test_batch_device_loop_matches_host_chunks(ctx, rep):
+    """The one-launch batch (device WHILE loop) and the chunked batch (host
+    check every 5 iterations) run the same arithmetic: identical solutions and
+    iteration counts; with maxiter 7 both stop at exactly 7."""
+    m0 = -0.2
+    sols = []
+    for check_every in (0, 5):
+        probs = [make_problem(ctx, d, rep, 400 + 10 * k) for k, d in enumerate(LATTICES)]
+        opts = hr.hr_solver_default_opts()
+        opts.check_every = check_every
+        work = fields.empty_bytes(hr.hr_cg_batch_workspace_bytes(LATTICES, rep))
+        rc, infos = hr.hr_cg_solve_batch(ctx, LATTICES, m0, rep, opts, [p[2] for p in probs],
+                                         [p[3] for p in probs], [p[4] for p in probs], work)
+        assert rc == hr.HR_OK
+        xs = [fields.unpack_spinor(ctx, d, rep, hr.HR_F64, hr.HR_EVEN, probs[k][4]).cpu().numpy()
+              for k, d in enumerate(LATTICES)]
+        sols.append(([i.iters for i in infos], xs))
+        opts.maxiter = 7
+        probs = [make_problem(ctx, d, rep, 400 + 10 * k) for k, d in enumerate(LATTICES)]
+        rc, infos = hr.hr_cg_solve_batch(ctx, LATTICES, m0, rep, opts, [p[2] for p in probs],
+                                         [p[3] for p in probs], [p[4] for p in probs], work)
+        assert rc == hr.HR_ERR_NOT_CONVERGED
+        assert all(i.iters == 7 for i in infos)
+    assert sols[0][0] == sols[1][0]
+    for a, b in zip(sols[0][1], sols[1][1]):
+        assert np.array_equal(a, b)
+
+
 def test_batch_argument_checks(ctx):
     opts = hr.hr_solver_default_opts()
     assert hr.hr_cg_batch_workspace_bytes([(4, 4, 4, 3)], hr.HR_FUND) == 0
