@@ -176,11 +176,18 @@ struct Solver {
         const double *done = flag_ptr(ctx, F_DONE);
         hr_status st;
         if (!mixed()) {
-            st = apply64(p64, q64, kFinAlpha, nullptr, done);
-            if (!st) st = blas_xr(ctx, g, rep, kF64, kF64, kF64, kF64, x, p64, r64, q64, s);
-            return st;
+            // q = A p with the x/r update and |r|^2 fused into the last hop
+            const CgFuse fz{x, p64, r64, kFinBeta};
+            return apply_eo_op(ctx, g, m0, rep, kF64, HR_OP_NORMAL, gauge, p64, q64, t64, u64, kFinAlpha, nullptr,
+                               done, s, &fz);
         }
         const int P = o.inner_prec;
+        if (P == kF32) {
+            // x_lo, p, r are all FP32: fused as above
+            const CgFuse fz{x_lo, p_lo, r_lo, kFinBetaMixed};
+            return apply_eo_op(ctx, g, m0, rep, P, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha,
+                               nullptr, done, s, &fz);
+        }
         st = apply_eo_op(ctx, g, m0, rep, P, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha, nullptr,
                          done, s);
         if (!st) st = blas_xr(ctx, g, rep, kF32, P, P, P, x_lo, p_lo, r_lo, q_lo, s);

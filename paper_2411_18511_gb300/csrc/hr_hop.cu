@@ -151,6 +151,9 @@ HopArgs make_args(hr_ctx *ctx, const Geom &g, const HopLaunch &L)
     a.done = L.done;
     a.unit = 1.f;
     a.nil = 0.f;
+    a.cg_x = L.cg_x;
+    a.cg_p = L.cg_p;
+    a.cg_r = L.cg_r;
     return a;
 }
 
@@ -204,7 +207,7 @@ bool hop_variant_available(int rep, int prec, int variant)
 // with A = 4 + m0 and c = 1 / (4 A).
 hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, int op, const void *gauge,
                       const void *in, void *out, void *work_odd, void *work_even, int fin_schur, const double *gate,
-                      const double *done, cudaStream_t s)
+                      const double *done, cudaStream_t s, const CgFuse *fuse)
 {
     const double A = 4.0 + m0, c = 1.0 / (4.0 * A);
     hr_status st;
@@ -212,7 +215,7 @@ hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, 
     L.gauge = gauge;
     L.gate = gate;
     L.done = done;
-    auto schur = [&](const void *src, void *dst, bool dag, int fin) -> hr_status {
+    auto schur = [&](const void *src, void *dst, bool dag, int fin, const CgFuse *fz) -> hr_status {
         HopLaunch h1 = L;
         h1.p = 1;
         h1.in = src;
@@ -235,15 +238,21 @@ hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, 
         h2.g5_in = 0;
         h2.g5_out = dag ? 1 : 0;
         h2.fin = fin;
+        if (fz) {
+            h2.fin = fz->fin;
+            h2.cg_x = fz->x;
+            h2.cg_p = fz->p;
+            h2.cg_r = fz->r;
+        }
         return launch_hop(ctx, g, rep, prec, h2, s);
     };
     switch (op) {
-    case HR_OP_SCHUR: return schur(in, out, false, fin_schur);
-    case HR_OP_SCHUR_DAG: return schur(in, out, true, fin_schur);
+    case HR_OP_SCHUR: return schur(in, out, false, fin_schur, nullptr);
+    case HR_OP_SCHUR_DAG: return schur(in, out, true, fin_schur, nullptr);
     case HR_OP_NORMAL:
-        st = schur(in, work_even, false, fin_schur);
+        st = schur(in, work_even, false, fin_schur, nullptr);
         if (st) return st;
-        return schur(work_even, out, true, kFinNone);
+        return schur(work_even, out, true, kFinNone, fuse);
     }
     return set_error(ctx, HR_ERR_INVALID_ARG, "bad op %d", op);
 }

@@ -25,6 +25,9 @@ struct HopArgs {
     const double *done; // skip all work when *done != 0 (solver converged)
     float unit, nil;    // 1 and 0, passed at run time so the compiler keeps the
                         // +-1 multipliers of the packed-FMA additions as FMAs
+    void *cg_x;         // fused CG update (cg_r != nullptr): x += alpha p,
+    const void *cg_p;   // r -= alpha out, |r|^2 reduced; out is not stored
+    void *cg_r;
 };
 
 __device__ __forceinline__ dd mul_pow2(dd x, float s) { return dd(x.h * s, x.l * s); }
@@ -146,6 +149,29 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<
                 T b = s < 2 ? bu : be;
                 o[s][c] = {b * acc[s][c].re, b * acc[s][c].im};
             }
+    }
+    if (a.cg_r) {
+        // the CG's x/r update on this site, with q = o in registers (the
+        // vector kernel's arithmetic, in the hop's precision)
+        const T alr = Real<T>::from_double(a.scal[S_ALPHA * kMaxRhsSlots + (j & (a.g.nrhs - 1))]);
+        cpx<T> xv[4][NC], pv[4][NC], rv[4][NC];
+        load_spinor<NC, PREC>(a.cg_x, a.g.nblk_s, j, xv);
+        load_spinor<NC, PREC>(a.cg_p, a.g.nblk_s, j, pv);
+        load_spinor<NC, PREC>(a.cg_r, a.g.nblk_s, j, rv);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                xv[s][c].re += alr * pv[s][c].re;
+                xv[s][c].im += alr * pv[s][c].im;
+                rv[s][c].re -= alr * o[s][c].re;
+                rv[s][c].im -= alr * o[s][c].im;
+                red.add(rv[s][c].re);
+                red.add(rv[s][c].im);
+            }
+        store_spinor<NC, PREC>(a.cg_x, a.g.nblk_s, j, xv);
+        store_spinor<NC, PREC>(a.cg_r, a.g.nblk_s, j, rv);
+        return;
     }
     store_spinor<NC, PREC>(a.out, a.g.nblk_s, j, o);
     if (a.fin) {

@@ -91,6 +91,18 @@ struct HopLaunch {
     int fin;               // FinishMode of the |out|^2 reduction (kFinNone: no reduction)
     const double *gate;    // skip the launch's work unless *gate != 0 (nullable)
     const double *done;    // skip the launch's work when *done != 0 (nullable)
+    // fused CG update (nullable): instead of storing out, x += alpha p and
+    // r -= alpha out with alpha per RHS from the scalar block, |r|^2 -> fin
+    void *cg_x;
+    const void *cg_p;
+    void *cg_r;
+};
+// a CG x/r update fused into the last hop of an operator (same precision)
+struct CgFuse {
+    void *x;
+    const void *p;
+    void *r;
+    int fin; // kFinBeta or kFinBetaMixed
 };
 hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, cudaStream_t s);
 hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, HopChoice c,
@@ -104,7 +116,7 @@ bool tune_cache_save(hr_ctx *ctx);
 // out = op(in) on even sites, work = odd temporary (+ even temporary for NORMAL)
 hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, int op, const void *gauge,
                       const void *in, void *out, void *work_odd, void *work_even, int fin_schur,
-                      const double *gate, const double *done, cudaStream_t s);
+                      const double *gate, const double *done, cudaStream_t s, const CgFuse *fuse = nullptr);
 
 // ---- BLAS launches (hr_blas.cu) ----
 hr_status blas_norm2(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *v, int fin, cudaStream_t s);
