@@ -56,7 +56,7 @@ HOP_KERNELS = ["k_hop", "k_hop_staged", "k_hop_loop", "k_hop_loop", "k_hop_sw", 
 HOP_VARIANT_NAMES = ["unrolled", "unrolled cp.async staged", "generic loop", "generic loop staged",
                      "switched loop", "switched loop staged", "unrolled register prefetch",
                      "unrolled, 96 registers", "bulk-copy tiled", "bulk-copy tiled, 96 registers",
-                     "paired f32x2 (colour lanes)", "paired f32x2, cp.async staged",
+                     "paired f32x2", "paired f32x2, cp.async staged",
                      "paired f32x2, 96 registers", "paired f32x2, cp.async staged, 96 registers"]
 
 

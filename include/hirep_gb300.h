@@ -242,10 +242,11 @@ typedef struct {
                           operands prefetched into registers; 7: as 0, capped at 96
                           registers per thread (more resident warps); 8: tiled, the
                           near-direction neighbours bulk-copied (TMA) into shared memory;
-                          9: as 8, 96 registers; 10: fundamental FP64 only, the two
-                          colours in the lanes of packed f32x2 FMAs; 11: as 10, operands
-                          staged by cp.async one direction ahead; 12, 13: 10, 11 capped
-                          at 96 registers */
+                          9: as 8, 96 registers; 10: packed f32x2 FMAs, two numbers per
+                          instruction (fundamental: the two colours; adjoint FP64: re and
+                          im); 11: as 10, operands staged by cp.async one direction ahead
+                          (fundamental, adjoint FP64 with quaternion links); 12, 13: 10,
+                          11 for fundamental FP64 capped at 96 registers */
     int block;         /* threads per block                                               */
     double best_ms;    /* mean time of one hop launch with the chosen shape               */
     double default_ms; /* the same for the shape in use before tuning                     */

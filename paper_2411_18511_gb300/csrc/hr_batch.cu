@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kTile) k_batch_hop(BatchArgs B)
                 // the paired (f32x2) double-float arithmetic of the single-lattice
                 // hop: the same sums in the same order, half the instructions
                 constexpr bool NEG = PHASE == 2;
-                const K2 k = {make_float2(B.unit, B.unit), make_float2(-B.unit, -B.unit), make_float2(B.nil, B.nil)};
+                const K2 k = make_k2(B.unit, B.nil);
                 SiteNb nb;
                 site_neighbours(a.g, j, a.p, nb);
                 cdd2 acc[4];

@@ -189,9 +189,10 @@ hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const H
 bool hop_variant_available(int rep, int prec, int variant)
 {
     (void)prec;
-    // the paired kernels pair the two colours of the fundamental layouts (FP32
-    // arithmetic: variants 10 and 11 only)
-    if (variant == kVarPaired || variant == kVarPairedStaged) return rep == HR_FUND;
+    // the paired kernels: fundamental (colour lanes) at every precision, adjoint
+    // FP64 ((re, im) lanes; staged for quaternion links only)
+    if (variant == kVarPaired) return rep == HR_FUND || prec == HR_F64;
+    if (variant == kVarPairedStaged) return rep == HR_FUND || (rep == HR_ADJ && prec == HR_F64);
     if (variant == kVarPairedR96 || variant == kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
     // the 96-register caps spill heavily with three colours: fundamental only
     if (variant == kVarSimpleR96) return rep == HR_FUND;

@@ -1,7 +1,9 @@
-// hr_hop_x2.cu -- the paired hop (variants 10-13): fundamental double-float
-// arithmetic with the two colours in the lanes of packed f32x2 FMAs, operands
-// from registers (10, 12) or staged by cp.async one direction ahead (11, 13);
-// 12 and 13 cap the registers at 96 for more resident warps.
+// hr_hop_x2.cu -- the paired hops (variants 10-13) on packed f32x2 FMAs:
+// fundamental double-float with the two colours in the lanes, operands from
+// registers (10, 12) or staged by cp.async one direction ahead (11, 13; 12 and
+// 13 capped at 96 registers); adjoint double-float with (re, im) in the lanes
+// (10, and 11 staged for quaternion links); FP32 arithmetic for FP32 / FP16
+// storage (10, 11).
 #include <algorithm>
 #include <cstdlib>
 
@@ -44,7 +46,7 @@ __device__ __forceinline__ void x2s_body(const HopArgs &a)
     constexpr bool NEG = G5IN != 0;
     extern __shared__ uint4 x2_stage_mem[];
     if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
-    const K2 k = {make_float2(a.unit, a.unit), make_float2(-a.unit, -a.unit), make_float2(a.nil, a.nil)};
+    const K2 k = make_k2(a.unit, a.nil);
     const Geom &g = a.g;
     const int nv = g.vh << g.lrhs;
     const int stride = gridDim.x * blockDim.x;
@@ -85,7 +87,7 @@ __device__ __forceinline__ void x2_body(const HopArgs &a)
     using T = dd;
     constexpr bool NEG = G5IN != 0;
     if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
-    const K2 k = {make_float2(a.unit, a.unit), make_float2(-a.unit, -a.unit), make_float2(a.nil, a.nil)};
+    const K2 k = make_k2(a.unit, a.nil);
     const Geom &g = a.g;
     const int nv = g.vh << g.lrhs;
     const int stride = gridDim.x * blockDim.x;
@@ -274,7 +276,7 @@ __device__ __forceinline__ void f2_body(const HopArgs &a)
 {
     constexpr bool NEG = G5IN != 0;
     if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
-    const K2 k = {make_float2(a.unit, a.unit), make_float2(-a.unit, -a.unit), make_float2(a.nil, a.nil)};
+    const K2 k = make_k2(a.unit, a.nil);
     const Geom &g = a.g;
     const int nv = g.vh << g.lrhs;
     const int stride = gridDim.x * blockDim.x;
@@ -357,7 +359,7 @@ __device__ __forceinline__ void f2s_body(const HopArgs &a)
     constexpr bool NEG = G5IN != 0;
     extern __shared__ uint4 f2_stage_mem[];
     if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
-    const K2 k = {make_float2(a.unit, a.unit), make_float2(-a.unit, -a.unit), make_float2(a.nil, a.nil)};
+    const K2 k = make_k2(a.unit, a.nil);
     const Geom &g = a.g;
     const int nv = g.vh << g.lrhs;
     const int stride = gridDim.x * blockDim.x;
@@ -401,6 +403,240 @@ __device__ __forceinline__ void f2s_body(const HopArgs &a)
 template <int PREC, int G5IN> __global__ void __launch_bounds__(256) k_hop_f2(HopArgs a) { f2_body<PREC, G5IN>(a); }
 template <int PREC, int G5IN> __global__ void __launch_bounds__(256) k_hop_f2s(HopArgs a) { f2s_body<PREC, G5IN>(a); }
 
+// ---------------------------------------------------------------- adjoint FP64, (re, im) lanes
+// With three colours the lanes are the real and imaginary parts of one complex
+// double-float: the FP64 layout for three colours already stores (re.h, im.h,
+// re.l, im.l), and the adjoint links are real, so a colour product scales both
+// lanes by one link entry (a duplicated lane pair).  A factor +-i swaps the
+// lanes with a (-1, 1) or (1, -1) sign pattern.  Sums in the scalar kernel's
+// order: bit-identical results, as for the fundamental pairing.
+
+// x + i^C y for complex (re, im) lane pairs
+template <int C> __device__ __forceinline__ dd2 cx_add_pow_i(const K2 &k, const dd2 &x, const dd2 &y)
+{
+    if constexpr (C == 0) return add2v(k, x, y, k.one);
+    else if constexpr (C == 2) return add2v(k, x, y, k.mone);
+    else if constexpr (C == 1) return add2v(k, x, swap2(y), k.mp); // (x.re - y.im, x.im + y.re)
+    else return add2v(k, x, swap2(y), k.pm);                       // (x.re + y.im, x.im - y.re)
+}
+// i^C y
+template <int C> __device__ __forceinline__ dd2 cx_pow_i(const K2 &k, const dd2 &y)
+{
+    if constexpr (C == 0) return y;
+    else if constexpr (C == 2) return neg2(k, y);
+    else {
+        const float2 sg = C == 1 ? k.mp : k.pm;
+        const dd2 t = swap2(y);
+        return {__ffma2_rn(t.h, sg, k.zero), __ffma2_rn(t.l, sg, k.zero)};
+    }
+}
+
+// r_t,b = sum_c M_bc h_t,c for both half-spinor components t at one output
+// colour b, M = R (forward) or R^T (backward), in the scalar kernel's order
+template <bool FWD, int B>
+__device__ __forceinline__ void so3_row_x2(const K2 &k, const dd (&R)[3][3], const dd2 (&h)[2][3], dd2 (&r)[2])
+{
+    dd2 c[3];
+    float2 n[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const dd m = FWD ? R[B][e] : R[e][B];
+        c[e] = {make_float2(m.h, m.h), make_float2(m.l, m.l)};
+        n[e] = make_float2(-m.h, -m.h);
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        r[t] = first_prod2<1>(k, mul2(k, c[0], n[0], h[t][0]));
+        r[t] = acc_prod2<1>(k, r[t], mul2(k, c[1], n[1], h[t][1]));
+        r[t] = acc_prod2<1>(k, r[t], mul2(k, c[2], n[2], h[t][2]));
+    }
+}
+
+// acc_t,b (+)= i^F r_t and acc_{2+u},b (+)= i^{d_u + F} r_{rho_u} at colour b
+template <class D, int F, bool FIRST, int B>
+__device__ __forceinline__ void x2a_rebuild(const K2 &k, const dd2 (&r)[2], dd2 (&acc)[4][3])
+{
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if constexpr (FIRST) acc[t][B] = cx_pow_i<F>(k, r[t]);
+        else acc[t][B] = cx_add_pow_i<F>(k, acc[t][B], r[t]);
+    }
+    if constexpr (FIRST) {
+        acc[2][B] = cx_pow_i<(D::d0 + F) & 3>(k, r[D::rho0]);
+        acc[3][B] = cx_pow_i<(D::d1 + F) & 3>(k, r[D::rho1]);
+    } else {
+        acc[2][B] = cx_add_pow_i<(D::d0 + F) & 3>(k, acc[2][B], r[D::rho0]);
+        acc[3][B] = cx_add_pow_i<(D::d1 + F) & 3>(k, acc[3][B], r[D::rho1]);
+    }
+}
+
+template <int MU, bool FWD, bool FIRST, bool NEG>
+__device__ __forceinline__ void x2a_compute(const K2 &k, const float4 (&w)[12], const dd (&R)[3][3], dd2 (&acc)[4][3])
+{
+    using D = X2Dir<MU, FWD>;
+    constexpr int F = NEG ? 2 : 0;
+    dd2 h[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const auto sv = [&](int t) -> dd2 {
+            const float4 v = w[3 * t + c];
+            return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+        };
+        h[0][c] = cx_add_pow_i<(D::c0 + F) & 3>(k, sv(0), sv(D::pi0));
+        h[1][c] = cx_add_pow_i<(D::c1 + F) & 3>(k, sv(1), sv(D::pi1));
+    }
+    dd2 r[2];
+    so3_row_x2<FWD, 0>(k, R, h, r);
+    x2a_rebuild<D, F, FIRST, 0>(k, r, acc);
+    so3_row_x2<FWD, 1>(k, R, h, r);
+    x2a_rebuild<D, F, FIRST, 1>(k, r, acc);
+    so3_row_x2<FWD, 2>(k, R, h, r);
+    x2a_rebuild<D, F, FIRST, 2>(k, r, acc);
+}
+
+template <int REP>
+__device__ __forceinline__ void x2a_link(const HopArgs &a, int link_par, int mu, int site_link, dd (&R)[3][3])
+{
+    if constexpr (REP == kRepAdj) {
+        dd q[4];
+        load_quat<kF64>(a.gauge, a.g.nblk_g, link_par, mu, site_link, q);
+        quat_to_adj(q, R);
+    } else {
+        load_mat<kF64>(a.gauge, a.g.nblk_g, link_par, mu, site_link, R);
+    }
+}
+
+template <int MU, bool FWD, bool FIRST, bool NEG, int REP>
+__device__ __forceinline__ void x2a_term(const HopArgs &a, const K2 &k, int site_link, int link_par, int j_nb,
+                                         dd2 (&acc)[4][3])
+{
+    const float4 *sp = (const float4 *)a.in;
+    float4 w[12];
+#pragma unroll
+    for (int v = 0; v < 12; ++v) w[v] = __ldg(sp + vec_index(j_nb, v, 12));
+    dd R[3][3];
+    x2a_link<REP>(a, link_par, MU, site_link, R);
+    x2a_compute<MU, FWD, FIRST, NEG>(k, w, R, acc);
+}
+
+__device__ __forceinline__ void x2a_epilogue(const HopArgs &a, int j, const dd2 (&acc)[4][3], dd al, dd be, dd bu,
+                                             SqAcc<dd> &red)
+{
+    cpx<dd> o[4][3];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[t][c] = {dd(acc[t][c].h.x, acc[t][c].l.x), dd(acc[t][c].h.y, acc[t][c].l.y)};
+    hop_epilogue<kF64>(a, j, o, al, be, bu, red);
+}
+
+template <int REP, int G5IN>
+__device__ __forceinline__ void x2a_body(const HopArgs &a)
+{
+    constexpr bool NEG = G5IN != 0;
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const K2 k = make_k2(a.unit, a.nil);
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const int l = g.lrhs;
+    const dd be = Real<dd>::from_coef(a.beta);
+    const dd bu = a.g5_out ? -be : be;
+    const dd al = Real<dd>::from_coef(a.alpha);
+    SqAcc<dd> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> l, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        dd2 acc[4][3];
+        x2a_term<0, true, true, NEG, REP>(a, k, i, a.p, (nb.fwd[0] << l) + rr, acc);
+        x2a_term<0, false, false, NEG, REP>(a, k, nb.bwd[0], 1 - a.p, (nb.bwd[0] << l) + rr, acc);
+        x2a_term<1, true, false, NEG, REP>(a, k, i, a.p, (nb.fwd[1] << l) + rr, acc);
+        x2a_term<1, false, false, NEG, REP>(a, k, nb.bwd[1], 1 - a.p, (nb.bwd[1] << l) + rr, acc);
+        x2a_term<2, true, false, NEG, REP>(a, k, i, a.p, (nb.fwd[2] << l) + rr, acc);
+        x2a_term<2, false, false, NEG, REP>(a, k, nb.bwd[2], 1 - a.p, (nb.bwd[2] << l) + rr, acc);
+        x2a_term<3, true, false, NEG, REP>(a, k, i, a.p, (nb.fwd[3] << l) + rr, acc);
+        x2a_term<3, false, false, NEG, REP>(a, k, nb.bwd[3], 1 - a.p, (nb.bwd[3] << l) + rr, acc);
+        x2a_epilogue(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+// staged form (quaternion links): direction K+1's operands copied by cp.async while K is computed
+template <int K, bool NEG>
+__device__ __forceinline__ void x2a_stage_step(const HopArgs &a, const K2 &k, int i, int rr, const SiteNb &nb,
+                                               uint4 *b0, uint4 *b1, int bd, dd2 (&acc)[4][3])
+{
+    uint4 *cur = (K & 1) ? b1 : b0;
+    uint4 *nxt = (K & 1) ? b0 : b1;
+    if constexpr (K < 7) {
+        stage_issue<K + 1, kRepAdj, kF64>(a, i, rr, nb, nxt, bd);
+        cp_async_commit();
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
+    float4 w[12];
+#pragma unroll
+    for (int v = 0; v < 12; ++v) w[v] = *reinterpret_cast<const float4 *>(cur + v * bd);
+    const float4 qh = *reinterpret_cast<const float4 *>(cur + 12 * bd);
+    const float4 ql = *reinterpret_cast<const float4 *>(cur + 13 * bd);
+    const dd q[4] = {dd(qh.x, ql.x), dd(qh.y, ql.y), dd(qh.z, ql.z), dd(qh.w, ql.w)};
+    dd R[3][3];
+    quat_to_adj(q, R);
+    x2a_compute<(K >> 1), (K & 1) == 0, K == 0, NEG>(k, w, R, acc);
+}
+
+template <int G5IN>
+__device__ __forceinline__ void x2as_body(const HopArgs &a)
+{
+    using S = Stage<kRepAdj, kF64>;
+    static_assert(S::NSLOT == 14, "12 spinor + 2 link vectors per direction");
+    constexpr bool NEG = G5IN != 0;
+    extern __shared__ uint4 x2a_stage_mem[];
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const K2 k = make_k2(a.unit, a.nil);
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const int bd = blockDim.x;
+    uint4 *b0 = x2a_stage_mem + threadIdx.x;
+    uint4 *b1 = x2a_stage_mem + S::NSLOT * bd + threadIdx.x;
+    const dd be = Real<dd>::from_coef(a.beta);
+    const dd bu = a.g5_out ? -be : be;
+    const dd al = Real<dd>::from_coef(a.alpha);
+    SqAcc<dd> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        stage_issue<0, kRepAdj, kF64>(a, i, rr, nb, b0, bd);
+        cp_async_commit();
+        dd2 acc[4][3];
+        x2a_stage_step<0, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
+        x2a_stage_step<1, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
+        x2a_stage_step<2, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
+        x2a_stage_step<3, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
+        x2a_stage_step<4, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
+        x2a_stage_step<5, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
+        x2a_stage_step<6, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
+        x2a_stage_step<7, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
+        x2a_epilogue(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+template <int REP, int G5IN> __global__ void __maxnreg__(128) k_hop_x2a(HopArgs a) { x2a_body<REP, G5IN>(a); }
+template <int G5IN> __global__ void __launch_bounds__(256) k_hop_x2as(HopArgs a) { x2as_body<G5IN>(a); }
+
 template <int REP, int PREC> struct Launch {
     static bool run(hr_ctx *ctx, const Geom &, const HopArgs &a, HopChoice c, int grid, cudaStream_t s,
                     hr_status &st)
@@ -422,6 +658,28 @@ template <int REP, int PREC> struct Launch {
             default: (g5 ? k_hop_x2<1> : k_hop_x2<0>)<<<grid, c.block, 0, s>>>(a); break;
             }
             st = check_launch(ctx, "paired hop kernel");
+            return true;
+        } else if constexpr (PREC == kF64) {
+            // adjoint (quaternion or stored 3x3 links): (re, im) lanes
+            if (c.variant != kVarPaired && c.variant != kVarPairedStaged) return false;
+            const bool g5 = a.g5_in != 0;
+            if constexpr (REP == kRepAdj) {
+                if (c.variant == kVarPairedStaged) {
+                    using S = Stage<kRepAdj, kF64>;
+                    static bool attr_set = false;
+                    if (!attr_set) {
+                        for (auto f : {k_hop_x2as<0>, k_hop_x2as<1>})
+                            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)S::smem_bytes(256));
+                        attr_set = true;
+                    }
+                    (g5 ? k_hop_x2as<1> : k_hop_x2as<0>)<<<grid, c.block, S::smem_bytes(c.block), s>>>(a);
+                    st = check_launch(ctx, "paired adjoint hop kernel");
+                    return true;
+                }
+            }
+            (g5 ? k_hop_x2a<REP, 1> : k_hop_x2a<REP, 0>)<<<grid, c.block, 0, s>>>(a);
+            st = check_launch(ctx, "paired adjoint hop kernel");
             return true;
         } else if constexpr (REP == kRepFund) {
             // FP32 arithmetic: the register-capped forms are not built (the

@@ -28,14 +28,20 @@ struct cdd2 {
     dd2 re, im; // a colour doublet of complex numbers
 };
 struct K2 {
-    float2 one, mone, zero;
+    float2 one, mone, zero; // (1, 1), (-1, -1), (0, 0)
+    float2 mp, pm;          // (-1, 1), (1, -1): a factor i or -i on (re, im) lanes
 };
-
-// a + S b on both lanes (Knuth's TwoSum on the hi parts, lo parts added)
-template <int S> __device__ __forceinline__ dd2 add2(const K2 &k, const dd2 &a, const dd2 &b)
+// the constants from run-time 1 and 0, so that the compiler keeps them as FMA operands
+__device__ __forceinline__ K2 make_k2(float unit, float nil)
 {
-    const float2 sg = S > 0 ? k.one : k.mone;
-    const float2 s = __ffma2_rn(b.h, sg, a.h);   // fl(a + S b)
+    return {make_float2(unit, unit), make_float2(-unit, -unit), make_float2(nil, nil), make_float2(-unit, unit),
+            make_float2(unit, -unit)};
+}
+
+// a + sg b lane by lane, sg a pair of +-1 (Knuth's TwoSum on the hi parts, lo parts added)
+__device__ __forceinline__ dd2 add2v(const K2 &k, const dd2 &a, const dd2 &b, float2 sg)
+{
+    const float2 s = __ffma2_rn(b.h, sg, a.h);   // fl(a + sg b)
     const float2 w = __ffma2_rn(s, k.mone, a.h); // a - s, exact
     const float2 t = __ffma2_rn(w, k.one, s);    // the part of s that came from a
     const float2 da = __ffma2_rn(t, k.mone, a.h);
@@ -43,6 +49,12 @@ template <int S> __device__ __forceinline__ dd2 add2(const K2 &k, const dd2 &a, 
     const float2 e = __ffma2_rn(da, k.one, db);
     const float2 lo = __ffma2_rn(b.l, sg, a.l);
     return {s, __ffma2_rn(e, k.one, lo)};
+}
+
+// a + S b on both lanes
+template <int S> __device__ __forceinline__ dd2 add2(const K2 &k, const dd2 &a, const dd2 &b)
+{
+    return add2v(k, a, b, S > 0 ? k.one : k.mone);
 }
 
 // c x = -P + L: P = fl(-c.h x.h) exactly, L = the product's rounding error
