@@ -194,6 +194,27 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep,
                       const hr_solver_opts *opts, const void *gauge, const void *b, void *x,
                       hr_solve_info *info, void *work, size_t work_bytes, hr_stream stream);
 
+/* Full-lattice systems solved through the even-odd preconditioned operator. */
+typedef enum { HR_SYSTEM_D = 0, HR_SYSTEM_DDAG_D = 1 } hr_system;
+
+/* Work bytes for hr_solve_full (0 if the options are invalid; n_rhs must be 1). */
+size_t hr_solve_full_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *opts, hr_system system);
+
+/* Solve D x = b (HR_SYSTEM_D) or D^+ D x = b (HR_SYSTEM_DDAG_D) on all sites
+ * through the even-odd reduction of Sec. 2.1: the source bhat = b_e - D_eo b_o /
+ * (4+m0), the Schur system Mhat x_e = bhat solved by hr_cg_solve on
+ * Mhat^+ Mhat x_e = Mhat^+ bhat (opts: tol, maxiter, inner precision,
+ * reliable_delta; n_rhs = 1), and the odd sites x_o = (b_o - D_oe x_e) /
+ * (4+m0); D^+ D is two such solves, x = D^-1 g5 D^-1 g5 b.  gauge: packed
+ * HR_F64 gauge of `rep`; b, x: full packed HR_F64 spinors (HR_FULL layout).
+ * info->true_rel_residual = |b - op x| / |b| of the full system, recomputed in
+ * FP64; iters and reliable updates are summed over the Schur solves.
+ * Synchronises the stream.  Errors as hr_cg_solve (HR_ERR_NOT_CONVERGED if a
+ * Schur solve misses tol within maxiter). */
+hr_status hr_solve_full(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_solver_opts *opts,
+                        hr_system system, const void *gauge, const void *b, void *x, hr_solve_info *info,
+                        void *work, size_t work_bytes, hr_stream stream);
+
 /* Work bytes of hr_cg_solve_batch for these lattices (0 if invalid). */
 size_t hr_cg_batch_workspace_bytes(int n_lat, const hr_lattice *lats, hr_rep rep);
 

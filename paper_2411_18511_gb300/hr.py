@@ -23,6 +23,7 @@ HR_FUND, HR_ADJ, HR_ADJ_MAT = 0, 1, 2
 HR_F64, HR_F32, HR_F16 = 0, 1, 2
 HR_EVEN, HR_ODD, HR_FULL = 0, 1, 2
 HR_OP_HOP, HR_OP_SCHUR, HR_OP_SCHUR_DAG, HR_OP_NORMAL = 0, 1, 2, 3
+HR_SYSTEM_D, HR_SYSTEM_DDAG_D = 0, 1
 
 STATUS_NAMES = {0: "HR_OK", 1: "HR_ERR_INVALID_ARG", 2: "HR_ERR_UNSUPPORTED", 3: "HR_ERR_CUDA",
                 4: "HR_ERR_NOT_CONVERGED", 5: "HR_ERR_NUMERIC", 6: "HR_ERR_TIMEOUT",
@@ -35,7 +36,8 @@ EXPORTED = [
     "hr_spinor_pack", "hr_spinor_unpack", "hr_dirac_workspace_bytes", "hr_dirac_apply",
     "hr_dirac_eo", "hr_solver_default_opts", "hr_cg_workspace_bytes", "hr_cg_solve", "hr_force",
     "hr_link_grad", "hr_norm2", "hr_axpy", "hr_gamma5", "hr_norm2_noalloc", "hr_autotune_hop",
-    "hr_tune_lookup", "hr_cg_batch_workspace_bytes", "hr_cg_solve_batch",
+    "hr_tune_lookup", "hr_cg_batch_workspace_bytes", "hr_cg_solve_batch", "hr_solve_full_workspace_bytes",
+    "hr_solve_full",
 ]
 
 
@@ -109,6 +111,9 @@ def lib():
                                        ctypes.POINTER(hr_solve_info), P, S, P], I),
                 "hr_autotune_hop": ([P, LAT, I, I, I, I, P, P, P, I, ctypes.POINTER(hr_tune_result), P], I),
                 "hr_tune_lookup": ([P, LAT, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+                "hr_solve_full_workspace_bytes": ([LAT, I, ctypes.POINTER(hr_solver_opts), I], S),
+                "hr_solve_full": ([P, LAT, D, I, ctypes.POINTER(hr_solver_opts), I, P, P, P,
+                                   ctypes.POINTER(hr_solve_info), P, S, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -281,6 +286,27 @@ def hr_cg_solve(ctx: Context, dims, m0, rep, opts: hr_solver_opts, gauge, b, x, 
     rc = lib().hr_cg_solve(ctx.handle, lattice(dims), float(m0), rep, ctypes.byref(opts),
                            _ptr(gauge), _ptr(b), _ptr(x), ctypes.byref(info), _ptr(work), wb,
                            _stream(stream))
+    if raise_on_error and rc not in (HR_OK, HR_ERR_NOT_CONVERGED):
+        ctx.check(rc)
+    return rc, info
+
+
+def hr_solve_full_workspace_bytes(dims, rep, opts: hr_solver_opts, system: int) -> int:
+    return int(lib().hr_solve_full_workspace_bytes(lattice(dims), rep, ctypes.byref(opts), system))
+
+
+def hr_solve_full(ctx: Context, dims, m0, rep, opts: hr_solver_opts, system, gauge, b, x, work, stream=None,
+                  raise_on_error: bool = True):
+    """D x = b (HR_SYSTEM_D) or D^+ D x = b (HR_SYSTEM_DDAG_D) on full packed
+    FP64 spinors.  Returns (status, hr_solve_info)."""
+    full = hr_spinor_packed_bytes(dims, rep, HR_F64, HR_FULL, 1)
+    _need(b, full, "b")
+    _need(x, full, "x")
+    info = hr_solve_info()
+    wb = 0 if work is None else work.numel() * work.element_size()
+    rc = lib().hr_solve_full(ctx.handle, lattice(dims), float(m0), rep, ctypes.byref(opts), int(system),
+                             _ptr(gauge), _ptr(b), _ptr(x), ctypes.byref(info), _ptr(work), wb,
+                             _stream(stream))
     if raise_on_error and rc not in (HR_OK, HR_ERR_NOT_CONVERGED):
         ctx.check(rc)
     return rc, info
