@@ -544,7 +544,7 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
         info->seconds = ms * 1e-3;
     }
     if (ctx->h_scal[F_DEVERR] != 0.0)
-        return set_error(ctx, HR_ERR_CUDA, "a bulk copy into shared memory did not land within its time limit");
+        return set_error(ctx, HR_ERR_TIMEOUT, "a bulk copy into shared memory did not land within its time limit");
     if (numeric) return set_error(ctx, HR_ERR_NUMERIC, "NaN or Inf in the CG residual");
     if (!converged)
         return set_error(ctx, HR_ERR_NOT_CONVERGED, "not converged: |b-Ax|/|b| = %.3e after %d iterations", worst, iters);
