@@ -317,6 +317,8 @@ hr_status hr_ctx_create(hr_ctx **out, int device)
         ctx->tune_cache_path = path;
         tune_cache_load(ctx);
     }
+    const char *inj = getenv("HR_INJECT_TILE_NO_COPY");
+    ctx->inject_tile_no_copy = (inj && inj[0] == '1') ? 1 : 0;
     *out = ctx;
     return HR_OK;
 }

@@ -154,6 +154,8 @@ HopArgs make_args(hr_ctx *ctx, const Geom &g, const HopLaunch &L)
     a.cg_x = L.cg_x;
     a.cg_p = L.cg_p;
     a.cg_r = L.cg_r;
+    a.inject_no_copy = ctx->inject_tile_no_copy;
+    a.wait_cycles = ctx->inject_tile_no_copy ? (1LL << 20) : (1LL << 31); // ~0.5 ms / ~1 s
     return a;
 }
 

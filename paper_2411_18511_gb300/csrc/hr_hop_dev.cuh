@@ -28,6 +28,9 @@ struct HopArgs {
     void *cg_x;         // fused CG update (cg_r != nullptr): x += alpha p,
     const void *cg_p;   // r -= alpha out, |r|^2 reduced; out is not stored
     void *cg_r;
+    long long wait_cycles; // bound of a device wait (tiled kernels' bulk copies)
+    int inject_no_copy;    // failure injection for tests: announce the tiled
+                           // kernels' copies but never queue them
 };
 
 __device__ __forceinline__ dd mul_pow2(dd x, float s) { return dd(x.h * s, x.l * s); }

@@ -32,7 +32,6 @@ template <int REP, int PREC> struct TileStage {
     static size_t smem_bytes(const Geom &g, int block) { return kHead + (size_t)max_blocks(g, block) * kBlockBytes; }
 };
 constexpr size_t kTileSmemMax = 100 * 1024; // larger windows use the plain kernel
-constexpr long long kWaitCycles = 1LL << 31; // about a second at GB300 clocks
 
 template <int MU, bool FWD, int REP, int PREC, class T, int NC>
 __device__ __forceinline__ void tile_term(const HopArgs &a, int site_link, int link_par, int j_nb, bool neg_upper,
@@ -91,8 +90,9 @@ __device__ __forceinline__ void hop_tile_body(const HopArgs &a)
         if (use_stage && threadIdx.x == 0) {
             // the block's reads of the previous window are ordered before this copy
             fence_proxy_async_smem();
-            bulk_copy_g2s(tile_smem + S::kHead, (const uint4 *)a.in + (size_t)b_lo * NV * 32,
-                          (unsigned)((size_t)(b_hi - b_lo) * S::kBlockBytes), bar);
+            const unsigned bytes = (unsigned)((size_t)(b_hi - b_lo) * S::kBlockBytes);
+            if (a.inject_no_copy) mbar_arrive_expect_tx(bar, bytes); // test: the copy never comes
+            else bulk_copy_g2s(tile_smem + S::kHead, (const uint4 *)a.in + (size_t)b_lo * NV * 32, bytes, bar);
         }
         const int j = j0 + threadIdx.x;
         const bool act = j < nv;
@@ -108,7 +108,7 @@ __device__ __forceinline__ void hop_tile_body(const HopArgs &a)
         }
         // a copy that has not landed after about a second: take every neighbour
         // from global memory (same result) and let the block vote below
-        const bool landed = use_stage && mbar_wait_bounded(bar, phase, kWaitCycles);
+        const bool landed = use_stage && mbar_wait_bounded(bar, phase, a.wait_cycles);
         if (act) {
             tile_term<2, true, REP, PREC>(a, i, a.p, (nb.fwd[2] << l) + rr, neg, stage, js_lo, js_hi, landed, acc);
             tile_term<2, false, REP, PREC>(a, nb.bwd[2], 1 - a.p, (nb.bwd[2] << l) + rr, neg, stage, js_lo, js_hi,
@@ -125,13 +125,13 @@ __device__ __forceinline__ void hop_tile_body(const HopArgs &a)
         if (tile + (int)gridDim.x >= ntiles) {
             // the block's last tile: a thread that saw the copy land may leave;
             // one that did not waits once more before the block can exit
-            if (!landed && !mbar_wait_bounded(bar, phase, kWaitCycles) && a.scal)
+            if (!landed && !mbar_wait_bounded(bar, phase, a.wait_cycles) && a.scal)
                 sc(a.scal, S_FLAGS, F_DEVERR) = 1.0;
             break;
         }
         if (__syncthreads_or(!landed)) {
             if (threadIdx.x == 0) {
-                s_landed = mbar_wait_bounded(bar, phase, kWaitCycles) ? 1 : 0;
+                s_landed = mbar_wait_bounded(bar, phase, a.wait_cycles) ? 1 : 0;
                 if (a.scal) sc(a.scal, S_FLAGS, F_DEVERR) = 1.0;
             }
             __syncthreads();

@@ -43,6 +43,10 @@ struct hr_ctx {
     // instantiated CG iteration graphs, keyed by everything they bake in
     std::map<std::string, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
     std::vector<std::string> graph_order;
+    // failure injection for tests (HR_INJECT_TILE_NO_COPY=1 when the context is
+    // created): the tiled hop's bulk copies are announced but never queued, so
+    // its bounded waits run out (shortened to about half a millisecond)
+    int inject_tile_no_copy = 0;
 };
 namespace hr {
 constexpr size_t kMaxGraphs = 8;

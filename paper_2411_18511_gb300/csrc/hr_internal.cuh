@@ -654,11 +654,18 @@ __device__ __forceinline__ void mbar_inval(unsigned long long *bar)
 // order this thread's earlier generic-proxy shared-memory accesses before
 // later async-proxy ones (a bulk copy overwriting data the block has read)
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// announce `bytes` of transactions on the barrier and arrive (the phase
+// completes when the bytes have landed)
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void bulk_copy_g2s(void *smem, const void *gmem, unsigned bytes, unsigned long long *bar)
 {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     unsigned b = (unsigned)__cvta_generic_to_shared(bar);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+    mbar_arrive_expect_tx(bar, bytes);
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(s),
                  "l"(gmem), "r"(bytes), "r"(b)
                  : "memory");

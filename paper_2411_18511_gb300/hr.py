@@ -191,6 +191,10 @@ class Context:
         except Exception:
             pass
 
+    def last_error(self) -> str:
+        msg = lib().hr_last_error(self._h)
+        return msg.decode() if msg else ""
+
     def check(self, rc: int):
         if rc != HR_OK:
             msg = lib().hr_last_error(self._h)
