@@ -33,8 +33,9 @@
  * - Packed layouts are opaque device buffers sized by hr_*_packed_bytes; the
  *   kernels read and write packed data only.  A packed spinor of one parity
  *   holds V_h sites; a "full" packed spinor is the even half followed by the
- *   odd half.  Packed buffers must be 256-byte aligned (cudaMalloc and torch
- *   allocations are).
+ *   odd half.  Packed buffers and work buffers must be 16-byte aligned,
+ *   canonical buffers 8-byte aligned (cudaMalloc and torch allocations are);
+ *   a null or misaligned buffer returns HR_ERR_INVALID_ARG before any launch.
  * - Ownership: the caller owns every buffer (device pointers, allocated by
  *   the caller) and the stream.  No hot call allocates memory.  Work buffers
  *   are passed in, sized by hr_workspace_bytes.  Calls are asynchronous on

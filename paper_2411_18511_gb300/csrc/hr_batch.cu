@@ -412,12 +412,14 @@ hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, doub
     for (int l = 0; l < n_lat; ++l) {
         hr_status st = validate_lattice(ctx, lats[l], 1);
         if (st) return st;
-        if (!gauges[l] || !b[l] || !x[l] || b[l] == x[l])
-            return set_error(ctx, HR_ERR_INVALID_ARG, "lattice %d: bad field pointers", l);
+        if (b[l] == x[l]) return set_error(ctx, HR_ERR_INVALID_ARG, "lattice %d: b and x alias", l);
+        st = check_buffers(ctx, {gauges[l], b[l], x[l]});
+        if (st) return st;
     }
     BatchPlan P = plan_batch(n_lat, lats, rep);
     if (!work || work_bytes < P.bytes)
         return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", P.bytes, work_bytes);
+    if (hr_status sw = check_buffers(ctx, {work})) return sw;
     if (infos) std::memset(infos, 0, sizeof(hr_solve_info) * n_lat);
     cudaStream_t s = (cudaStream_t)stream;
     char *w = (char *)work;

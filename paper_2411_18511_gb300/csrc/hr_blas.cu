@@ -345,7 +345,9 @@ hr_status hr_norm2(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *v, doubl
     if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
-    if (!v || !result) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    if (!result) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    st = check_buffers(ctx, {v});
+    if (st) return st;
     Geom g = make_geom(lat, 1);
     cudaStream_t s = (cudaStream_t)stream;
     st = blas_norm2(ctx, g, rep, kF64, v, kFinStore, s);
@@ -364,7 +366,8 @@ hr_status hr_axpy(hr_ctx *ctx, hr_lattice lat, hr_rep rep, double a, const void 
     if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
-    if (!x || !y) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    st = check_buffers(ctx, {x, y});
+    if (st) return st;
     return blas_axpy(ctx, make_geom(lat, 1), rep, a, x, y, (cudaStream_t)stream);
 }
 
@@ -374,7 +377,8 @@ hr_status hr_gamma5(hr_ctx *ctx, hr_lattice lat, hr_rep rep, void *v, hr_stream 
     if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
-    if (!v) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    st = check_buffers(ctx, {v});
+    if (st) return st;
     return blas_gamma5(ctx, make_geom(lat, 1), rep, v, (cudaStream_t)stream);
 }
 

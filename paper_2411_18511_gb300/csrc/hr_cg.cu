@@ -397,7 +397,8 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
         return set_error(ctx, HR_ERR_INVALID_ARG, "reliable_delta must lie in (0, 1)");
     hr_status st = validate_lattice(ctx, lat, opts->n_rhs);
     if (st) return st;
-    if (!gauge || !b || !x) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+    st = check_buffers(ctx, {gauge, b, x}, {}, {work});
+    if (st) return st;
     if (b == x) return set_error(ctx, HR_ERR_INVALID_ARG, "b and x must not alias");
     if (!(4.0 + m0 != 0.0)) return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero");
     size_t need = hr_cg_workspace_bytes(lat, rep, opts);

@@ -46,6 +46,24 @@ static bool lattice_ok(const hr_lattice &lat, int nrhs)
     return (v / 2) * nrhs * 12 < (1LL << 31);
 }
 
+hr_status check_buffers(hr_ctx *ctx, std::initializer_list<const void *> packed,
+                        std::initializer_list<const void *> canonical, std::initializer_list<const void *> nullable)
+{
+    int k = 0;
+    for (const void *p : packed) {
+        if (!p) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer (argument %d)", k);
+        if ((uintptr_t)p & 15u) return set_error(ctx, HR_ERR_INVALID_ARG, "packed buffer %p not 16-byte aligned", p);
+        ++k;
+    }
+    for (const void *p : canonical) {
+        if (!p) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+        if ((uintptr_t)p & 7u) return set_error(ctx, HR_ERR_INVALID_ARG, "canonical buffer %p not 8-byte aligned", p);
+    }
+    for (const void *p : nullable)
+        if (p && ((uintptr_t)p & 15u)) return set_error(ctx, HR_ERR_INVALID_ARG, "work buffer %p not 16-byte aligned", p);
+    return HR_OK;
+}
+
 hr_status validate_lattice(hr_ctx *ctx, const hr_lattice &lat, int nrhs)
 {
     for (int k = 0; k < 4; ++k) {
@@ -197,7 +215,8 @@ hr_status spinor_convert(hr_ctx *ctx, hr_lattice lat, int rep, int prec, int par
     if (parity < 0 || parity > 2) return set_error(ctx, HR_ERR_INVALID_ARG, "bad parity %d", parity);
     hr_status st = validate_lattice(ctx, lat, n_rhs);
     if (st) return st;
-    if (!can || !packed) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+    st = check_buffers(ctx, {packed}, {can});
+    if (st) return st;
     Geom g = make_geom(lat, n_rhs);
     size_t half = spinor_half_bytes(g, rep, prec);
     int nc = rep_nc(rep);
@@ -368,7 +387,8 @@ hr_status hr_gauge_pack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, c
     if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
-    if (!canonical || !packed) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+    st = check_buffers(ctx, {packed}, {canonical});
+    if (st) return st;
     Geom g = make_geom(lat, 1);
     cudaStream_t s = (cudaStream_t)stream;
     // zero the padding lanes so packed buffers are fully defined

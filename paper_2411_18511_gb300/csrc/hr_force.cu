@@ -123,7 +123,9 @@ hr_status launch(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *af,
     if (!ctx) return HR_ERR_INVALID_ARG;
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
-    if (!af || !bf || !out || (mode == 0 && !gauge)) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    if (mode == 0 && !gauge) return set_error(ctx, HR_ERR_INVALID_ARG, "null pointer");
+    st = check_buffers(ctx, {af, bf}, {out}, {gauge});
+    if (st) return st;
     ForceArgs A;
     A.g = make_geom(lat, 1);
     size_t half = spinor_half_bytes(A.g, HR_FUND, kF64);

@@ -285,7 +285,8 @@ hr_status hr_dirac_eo(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, hr_pre
     if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
     hr_status st = validate_lattice(ctx, lat, n_rhs);
     if (st) return st;
-    if (!gauge || !in || !out) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+    st = check_buffers(ctx, {gauge, in, out}, {}, {work});
+    if (st) return st;
     if (in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "in and out must not alias");
     if (!(4.0 + m0 != 0.0)) return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero");
     Geom g = make_geom(lat, n_rhs);
@@ -320,7 +321,8 @@ hr_status hr_dirac_apply(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, hr_
     if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
-    if (!gauge || !in || !out) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+    st = check_buffers(ctx, {gauge, in, out});
+    if (st) return st;
     if (in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "in and out must not alias");
     Geom g = make_geom(lat, 1);
     size_t half = spinor_half_bytes(g, rep, prec);

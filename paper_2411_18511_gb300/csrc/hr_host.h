@@ -4,6 +4,8 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
+#include <initializer_list>
 #include <map>
 #include <string>
 #include <utility>
@@ -55,6 +57,13 @@ constexpr size_t kMaxGraphs = 8;
 namespace hr {
 
 hr_status set_error(hr_ctx *ctx, hr_status st, const char *fmt, ...);
+// Device buffers handed to an entry point: packed fields and work buffers are
+// read and written as 16-byte vectors, canonical fields as doubles.  A null or
+// misaligned one is an argument error, caught before any launch.  (nullable:
+// only checked when not null.)
+hr_status check_buffers(hr_ctx *ctx, std::initializer_list<const void *> packed,
+                        std::initializer_list<const void *> canonical = {},
+                        std::initializer_list<const void *> nullable = {});
 hr_status check_launch(hr_ctx *ctx, const char *what);
 hr_status validate_lattice(hr_ctx *ctx, const hr_lattice &lat, int nrhs);
 bool valid_rep(int rep);

@@ -63,7 +63,7 @@ extern "C" hr_status hr_norm2_noalloc(hr_lattice lat, hr_rep rep, int n_rhs, con
                                       hr_stream stream)
 {
     if (!valid_rep(rep)) return HR_ERR_INVALID_ARG;
-    if (!v || !result) return HR_ERR_INVALID_ARG;
+    if (!v || !result || ((uintptr_t)v & 15u)) return HR_ERR_INVALID_ARG; // packed: 16-byte vectors
     // the fixed scratch holds kMaxRhs partial sums per block: more RHS do not fit
     if (n_rhs > kMaxRhs) return HR_ERR_WORKSPACE;
     if (n_rhs < 1 || (n_rhs & (n_rhs - 1))) return HR_ERR_UNSUPPORTED;

@@ -135,7 +135,8 @@ hr_status hr_solve_full(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, cons
     if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
-    if (!gauge || !b || !x) return set_error(ctx, HR_ERR_INVALID_ARG, "null field pointer");
+    st = check_buffers(ctx, {gauge, b, x}, {}, {work});
+    if (st) return st;
     if (b == x) return set_error(ctx, HR_ERR_INVALID_ARG, "b and x must not alias");
     if (!(4.0 + m0 != 0.0)) return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero");
     const size_t need = hr_solve_full_workspace_bytes(lat, rep, opts, system);

@@ -81,7 +81,9 @@ hr_status hr_autotune_hop(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec,
     hr_status st = validate_lattice(ctx, lat, n_rhs);
     if (st) return st;
     if (out_parity != HR_EVEN && out_parity != HR_ODD) return set_error(ctx, HR_ERR_INVALID_ARG, "bad parity");
-    if (!gauge || !in || !out || in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "bad field pointers");
+    if (in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "bad field pointers");
+    st = check_buffers(ctx, {gauge, in, out});
+    if (st) return st;
     if (reps < 1 || reps > 10000) return set_error(ctx, HR_ERR_INVALID_ARG, "reps must lie in [1, 10000]");
     Geom g = make_geom(lat, n_rhs);
     cudaStream_t s = (cudaStream_t)stream;

@@ -174,6 +174,18 @@ def test_invalid_arguments_return_codes(ctx):
     rc = L.hr_dirac_eo(ctx.handle, hr.lattice(dims), 0.1, 7, 0, 0, hr.HR_OP_HOP, 1, hr._ptr(g), hr._ptr(s),
                        hr._ptr(o), None, 0, None)
     assert rc == hr.HR_ERR_INVALID_ARG
+    # misaligned buffers are refused before any launch (the kernels move 16-byte vectors)
+    big = fields.empty_bytes(hr.hr_spinor_packed_bytes(dims, 0, 0, 0, 1) + 64)
+    for off in (4, 8):
+        rc = L.hr_dirac_eo(ctx.handle, hr.lattice(dims), 0.1, 0, 0, 0, hr.HR_OP_HOP, 1, hr._ptr(g),
+                           big.data_ptr() + off, hr._ptr(o), None, 0, None)
+        assert rc == hr.HR_ERR_INVALID_ARG
+        assert b"aligned" in L.hr_last_error(ctx.handle)
+    rc = L.hr_gamma5(ctx.handle, hr.lattice(dims), 0, big.data_ptr() + 8, None)
+    assert rc == hr.HR_ERR_INVALID_ARG
+    res = torch.empty(1, dtype=torch.float64, device="cuda")
+    rc = L.hr_norm2_noalloc(hr.lattice(dims), 0, 1, big.data_ptr() + 4, res.data_ptr(), None)
+    assert rc == hr.HR_ERR_INVALID_ARG
     torch.cuda.synchronize()
 
 
