@@ -157,3 +157,69 @@ def test_variant_bitwise_equals_plain(tmp_path, monkeypatch, variant, block, n_r
                     assert np.array_equal(a, b), (rep, prec)
     base.close()
     tiled.close()
+
+
+def _spinor_padding_bytes(dims, rep, prec, n_rhs=1):
+    """Byte offsets of the padding lanes (virtual sites >= V_h N) of one packed
+    spinor half: the ragged last 32-site block, and the FP16 scales after it."""
+    nc = 2 if rep == hr.HR_FUND else 3
+    vh = int(np.prod(dims)) // 2
+    nv = vh * n_rhs
+    nblk = (nv + 31) // 32
+    nvec = {hr.HR_F64: 4 * nc, hr.HR_F32: 2 * nc, hr.HR_F16: nc}[prec]
+    idx = []
+    for j in range(nv, nblk * 32):
+        for v in range(nvec):
+            base = (((j // 32) * nvec + v) * 32 + (j % 32)) * 16
+            idx.extend(range(base, base + 16))
+        if prec == hr.HR_F16:
+            base = nblk * 32 * nvec * 16 + 4 * j
+            idx.extend(range(base, base + 4))
+    return np.asarray(idx, dtype=np.int64)
+
+
+def _gauge_padding_bytes(dims, prec):
+    """Byte offsets of the padding lanes (sites >= V_h) of a packed quaternion gauge."""
+    vh = int(np.prod(dims)) // 2
+    nblk = (vh + 31) // 32
+    per = {hr.HR_F64: 16, hr.HR_F32: 16, hr.HR_F16: 8}[prec]
+    nv = 2 if prec == hr.HR_F64 else 1
+    idx = []
+    for slot in range(8 * nblk):
+        if slot % nblk != nblk - 1:
+            continue
+        for lane in range(vh - (nblk - 1) * 32, 32):
+            for v in range(nv):
+                base = ((slot * nv + v) * 32 + lane) * per
+                idx.extend(range(base, base + per))
+    return np.asarray(idx, dtype=np.int64)
+
+
+@pytest.mark.parametrize("variant,block", [(0, 64), (1, 128), (2, 64), (4, 128), (6, 128), (7, 64), (8, 64),
+                                           (10, 64), (11, 128)])
+def test_padding_lanes_are_never_read(tmp_path, monkeypatch, variant, block):
+    """NaN canaries in the padding lanes of the ragged last block (inputs and
+    links) must not reach any output: every kernel variant reads only real
+    sites, so the result equals the canary-free one bit for bit."""
+    dims = (2, 4, 6, 6)  # 144 sites per parity: 16 padding lanes in the last block
+    reps, precs = (hr.HR_FUND, hr.HR_ADJ), (hr.HR_F64, hr.HR_F32, hr.HR_F16)
+    c = _forced_context(tmp_path, monkeypatch, "pad", dims, reps, precs, 1, variant, block)
+    for rep in reps:
+        nc = 2 if rep == hr.HR_FUND else 3
+        q = synth.haar_links(dims, 41)
+        psi = synth.gaussian_spinor(dims, nc, 42)
+        for prec in precs:
+            gauge = fields.pack_gauge(c, dims, rep, prec, fields.gauge_to_device(q))
+            src = fields.pack_spinor(c, dims, rep, prec, hr.HR_ODD, fields.spinor_to_device(psi))
+            outs = []
+            for canary in (False, True):
+                g, s = gauge.clone(), src.clone()
+                if canary:
+                    s[torch.as_tensor(_spinor_padding_bytes(dims, rep, prec), device="cuda")] = 0xFF
+                    g[torch.as_tensor(_gauge_padding_bytes(dims, prec), device="cuda")] = 0xFF
+                dst = fields.empty_spinor(dims, rep, prec, hr.HR_EVEN)
+                hr.hr_dirac_eo(c, dims, -0.3, rep, prec, hr.HR_EVEN, hr.HR_OP_HOP, 1, g, s, dst)
+                outs.append(fields.unpack_spinor(c, dims, rep, prec, hr.HR_EVEN, dst).cpu().numpy())
+            assert np.all(np.isfinite(outs[1])), (rep, prec)
+            assert np.array_equal(outs[0], outs[1]), (rep, prec)
+    c.close()
