@@ -270,7 +270,7 @@ typedef struct {
                           (fundamental, adjoint FP64 with quaternion links); 12, 13: 10,
                           11 for fundamental FP64 capped at 96 registers */
     int block;         /* threads per block                                               */
-    double best_ms;    /* mean time of one hop launch with the chosen shape               */
+    double best_ms;    /* time of one hop launch with the chosen shape (median of 4)      */
     double default_ms; /* the same for the shape in use before tuning                     */
     int candidates;    /* shapes timed                                                    */
 } hr_tune_result;
@@ -278,7 +278,8 @@ typedef struct {
 /* Time every kernel variant and block size for the hop of this configuration
  * (rep, prec, extents, n_rhs) on the caller's buffers -- `out` (parity
  * out_parity) is overwritten with D_{p,1-p} in, `reps` timed launches per
- * shape -- and use the fastest for all later hop launches of the
+ * shape; the four fastest are timed three more times, interleaved, and the
+ * best median wins -- and use it for all later hop launches of the
  * configuration on this context (operators and solvers included).  If the
  * environment variable HR_AUTOTUNE_CACHE names a file, the choice is written
  * there as JSON and read back by later contexts.  Synchronises the stream.
