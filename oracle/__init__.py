@@ -12,7 +12,10 @@ form in Sec. 2.1 without writing either down):
 
 * ``D = (4+m0) - H/2`` with
   ``(H psi)(x) = sum_mu (1-g_mu) U_mu(x) psi(x+mu) + (1+g_mu) U_mu(x-mu)^+ psi(x-mu)``,
-  periodic in all directions, chiral gamma basis.
+  chiral gamma basis, periodic in every direction except those whose bit is set
+  in ``bc`` (bit mu: antiperiodic, ``psi(x + L_mu mu) = -psi(x)``).  ``bc`` is a
+  keyword of every operator below; a ``dims`` object with a ``bc`` attribute
+  supplies it too.
 * ``Mhat = (4+m0) - H_eo H_oe / (4 (4+m0))`` on even sites, ``Mhat^+ = g5 Mhat g5``.
 * CG: Hestenes-Stiefel on ``Mhat^+ Mhat`` from ``x0 = 0``.
 
@@ -62,14 +65,14 @@ def _load():
             D = ctypes.c_double
             sig = {
                 "or_expand_links": [P, I, P, P],
-                "or_hop": [P, I, P, I, P, P],
-                "or_hop_sites": [P, I, P, P, L, P, P],
-                "or_dirac": [P, I, P, D, P, P],
-                "or_schur": [P, I, P, D, I, P, P],
-                "or_normal": [P, I, P, D, P, P],
-                "or_cg": [P, I, P, D, P, P, D, I, P, P],
-                "or_force": [P, P, P, P, P],
-                "or_link_grad": [P, P, P, P],
+                "or_hop": [P, I, I, P, I, P, P],
+                "or_hop_sites": [P, I, I, P, P, L, P, P],
+                "or_dirac": [P, I, I, P, D, P, P],
+                "or_schur": [P, I, I, P, D, I, P, P],
+                "or_normal": [P, I, I, P, D, P, P],
+                "or_cg": [P, I, I, P, D, P, P, D, I, P, P],
+                "or_force": [P, I, P, P, P, P],
+                "or_link_grad": [P, I, P, P, P],
                 "or_plaquette": [P, P, P],
                 "or_gamma": [I, P],
                 "or_adjoint_link": [P, P],
@@ -88,6 +91,14 @@ def _dims(dims) -> np.ndarray:
     d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
     assert d.shape == (4,)
     return d
+
+
+def _bc(dims, bc) -> int:
+    """Boundary bits: the explicit keyword, else the ``bc`` attribute of ``dims``, else 0."""
+    b = int(bc) if bc is not None else int(getattr(dims, "bc", 0))
+    if not 0 <= b <= 15:
+        raise ValueError(f"bc = {b}: four bits, one per direction")
+    return b
 
 
 def _ptr(a: np.ndarray):
@@ -145,83 +156,83 @@ def _nc(L) -> int:
     return int(L.shape[-1])
 
 
-def hop(dims, L, psi, parity: int = -1, out=None) -> np.ndarray:
+def hop(dims, L, psi, parity: int = -1, out=None, bc=None) -> np.ndarray:
     """(H psi)(x) at the sites of ``parity`` (-1 = all); others stay zero (or as in ``out``)."""
     d = _dims(dims)
     psi = _c128(psi)
     out = np.zeros_like(psi) if out is None else out
-    _check(_load().or_hop(_ptr(d), _nc(L), _ptr(L), int(parity), _ptr(psi), _ptr(out)), "hop")
+    _check(_load().or_hop(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), int(parity), _ptr(psi), _ptr(out)), "hop")
     return out
 
 
-def hop_sites(dims, L, psi, sites) -> np.ndarray:
+def hop_sites(dims, L, psi, sites, bc=None) -> np.ndarray:
     """(H psi) at the listed lexicographic sites, shape [n, 4, nc]."""
     d = _dims(dims)
     psi = _c128(psi)
     s = np.ascontiguousarray(sites, dtype=np.int64)
     out = np.zeros((s.size, 4, _nc(L)), dtype=np.complex128)
-    _check(_load().or_hop_sites(_ptr(d), _nc(L), _ptr(L), _ptr(s), s.size, _ptr(psi), _ptr(out)),
+    _check(_load().or_hop_sites(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), _ptr(s), s.size, _ptr(psi), _ptr(out)),
            "hop_sites")
     return out
 
 
-def dirac(dims, L, m0: float, psi) -> np.ndarray:
+def dirac(dims, L, m0: float, psi, bc=None) -> np.ndarray:
     """Full Wilson-Dirac operator D psi on all sites."""
     d = _dims(dims)
     psi = _c128(psi)
     out = np.zeros_like(psi)
-    _check(_load().or_dirac(_ptr(d), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "dirac")
+    _check(_load().or_dirac(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "dirac")
     return out
 
 
-def schur(dims, L, m0: float, psi, dagger: bool = False) -> np.ndarray:
+def schur(dims, L, m0: float, psi, dagger: bool = False, bc=None) -> np.ndarray:
     """Mhat psi (or Mhat^+ psi) on even sites of a full-lattice array; odd sites -> 0."""
     d = _dims(dims)
     psi = _c128(psi)
     out = np.zeros_like(psi)
-    _check(_load().or_schur(_ptr(d), _nc(L), _ptr(L), float(m0), int(bool(dagger)), _ptr(psi),
+    _check(_load().or_schur(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), float(m0), int(bool(dagger)), _ptr(psi),
                             _ptr(out)), "schur")
     return out
 
 
-def normal(dims, L, m0: float, psi) -> np.ndarray:
+def normal(dims, L, m0: float, psi, bc=None) -> np.ndarray:
     """Mhat^+ Mhat psi on even sites."""
     d = _dims(dims)
     psi = _c128(psi)
     out = np.zeros_like(psi)
-    _check(_load().or_normal(_ptr(d), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "normal")
+    _check(_load().or_normal(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "normal")
     return out
 
 
-def cg(dims, L, m0: float, b, tol: float = 1e-10, maxiter: int = 10000):
+def cg(dims, L, m0: float, b, tol: float = 1e-10, maxiter: int = 10000, bc=None):
     """CG on Mhat^+ Mhat x = b (even sites). Returns (x, iters, true_rel_residual, converged)."""
     d = _dims(dims)
     b = _c128(b)
     x = np.zeros_like(b)
     it = ctypes.c_int(0)
     tr = ctypes.c_double(0.0)
-    rc = _load().or_cg(_ptr(d), _nc(L), _ptr(L), float(m0), _ptr(b), _ptr(x), float(tol),
+    rc = _load().or_cg(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), float(m0), _ptr(b), _ptr(x), float(tol),
                        int(maxiter), ctypes.byref(it), ctypes.byref(tr))
     _check(rc, "cg")
     return x, it.value, tr.value, rc == 0
 
 
-def force(dims, L, a, b) -> np.ndarray:
+def force(dims, L, a, b, bc=None) -> np.ndarray:
     """F[mu, x, a] = d Re<a, H b> / d w_a under U_mu(x) -> exp(i w.s/2) U_mu(x) (fundamental)."""
     d = _dims(dims)
     assert _nc(L) == 2
     a, b = _c128(a), _c128(b)
     F = np.zeros((4, volume(dims), 3))
-    _check(_load().or_force(_ptr(d), _ptr(L), _ptr(a), _ptr(b), _ptr(F)), "force")
+    _check(_load().or_force(_ptr(d), _bc(dims, bc), _ptr(L), _ptr(a), _ptr(b), _ptr(F)), "force")
     return F
 
 
-def link_grad(dims, a, b) -> np.ndarray:
+def link_grad(dims, a, b, bc=None) -> np.ndarray:
     """G[mu, x, k] = d Re<a, H b> / d q_k for the quaternion components of U_mu(x)."""
     d = _dims(dims)
     a, b = _c128(a), _c128(b)
     G = np.zeros((4, volume(dims), 4))
-    _check(_load().or_link_grad(_ptr(d), _ptr(a), _ptr(b), _ptr(G)), "link_grad")
+    _check(_load().or_link_grad(_ptr(d), _bc(dims, bc), _ptr(a), _ptr(b), _ptr(G)), "link_grad")
     return G
 
 
@@ -248,21 +259,21 @@ def gamma5(psi) -> np.ndarray:
     return psi * g5[None, :, None]
 
 
-def eo_source(dims, L, m0: float, b) -> np.ndarray:
+def eo_source(dims, L, m0: float, b, bc=None) -> np.ndarray:
     """bhat_e = b_e - D_eo D_oo^-1 b_o = b_e + H_eo b_o / (2 (4+m0)); odd sites zero."""
     odd = parity_mask(dims) == 1
     bo = _c128(b).copy()
     bo[~odd] = 0
-    h = hop(dims, L, bo, parity=0)
+    h = hop(dims, L, bo, parity=0, bc=bc)
     out = _c128(b) + h / (2.0 * (4.0 + m0))
     out[odd] = 0
     return out
 
 
-def eo_reconstruct(dims, L, m0: float, b, xe) -> np.ndarray:
+def eo_reconstruct(dims, L, m0: float, b, xe, bc=None) -> np.ndarray:
     """x_o = D_oo^-1 (b_o - D_oe x_e) = (b_o + H_oe x_e / 2) / (4+m0); returns full x."""
     odd = parity_mask(dims) == 1
-    h = hop(dims, L, _c128(xe), parity=1)
+    h = hop(dims, L, _c128(xe), parity=1, bc=bc)
     x = _c128(xe).copy()
     x[odd] = (_c128(b)[odd] + 0.5 * h[odd]) / (4.0 + m0)
     return x

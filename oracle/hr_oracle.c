@@ -14,7 +14,9 @@
  *              - 1/2 sum_mu [ (1-g_mu) U_mu(x) psi(x+mu)
  *                            + (1+g_mu) U_mu(x-mu)^+ psi(x-mu) ]
  *
- * with periodic boundaries in all four directions, the chiral gamma basis
+ * with periodic boundaries, or antiperiodic ones in the directions mu whose
+ * bit (bc >> mu) & 1 is set: psi(x + L_mu mu-hat) = -psi(x), so a hop whose
+ * neighbour lies across that boundary picks up a factor -1.  The chiral gamma basis
  *   g_0 = [[0, 1], [1, 0]],  g_k = [[0, -i s_k], [i s_k, 0]],  g5 = g0 g1 g2 g3,
  * SU(2) links U = a0 + i(a1 s1 + a2 s2 + a3 s3) in the fundamental
  * representation, and R_ab = 1/2 tr(s_a U s_b U^+) in the adjoint.  The hopping
@@ -109,6 +111,17 @@ static long shift(const int *d, long i, int mu, int step)
     return lex(d, x);
 }
 
+/* The boundary factor of the hop from site i to i + step * mu-hat: -1 when mu
+ * is antiperiodic (bit mu of bc) and the step crosses the lattice's edge. */
+static double wrap_sign(const int *d, int bc, long i, int mu, int step)
+{
+    if (!((bc >> mu) & 1)) return 1.0;
+    int x[4];
+    coords(d, i, x);
+    int y = x[mu] + step;
+    return (y < 0 || y >= d[mu]) ? -1.0 : 1.0;
+}
+
 static int parity(const int *d, long i)
 {
     int x[4];
@@ -122,6 +135,8 @@ static int check_dims(const int *d)
         if (d[mu] < 2 || (d[mu] & 1)) return -1;
     return 0;
 }
+
+static int check_lat(const int *d, int bc) { return (check_dims(d) || bc < 0 || bc > 15) ? -1 : 0; }
 
 /* ------------------------------------------------------------------ */
 /* links                                                               */
@@ -194,13 +209,15 @@ int or_expand_links(const int *d, int nc, const double *q, double *Lout)
 /* ------------------------------------------------------------------ */
 
 /* out[s][c] = (H psi)(x) at one site, straight from the definition */
-static void hop_site(const int *d, int nc, const cplx *L, const cplx *psi, long x, cplx *out)
+static void hop_site(const int *d, int bc, int nc, const cplx *L, const cplx *psi, long x, cplx *out)
 {
     long V = volume(d);
     int ns = 4 * nc;
     for (int k = 0; k < ns; ++k) out[k] = 0;
     for (int mu = 0; mu < 4; ++mu) {
         long xf = shift(d, x, mu, +1), xb = shift(d, x, mu, -1);
+        /* psi(x +- mu) across an antiperiodic boundary is minus the stored value */
+        double sgf = wrap_sign(d, bc, x, mu, +1), sgb = wrap_sign(d, bc, x, mu, -1);
         const cplx *Uf = L + ((long)mu * V + x) * nc * nc;
         const cplx *Ub = L + ((long)mu * V + xb) * nc * nc;
         const cplx *pf = psi + xf * ns, *pb = psi + xb * ns;
@@ -212,8 +229,8 @@ static void hop_site(const int *d, int nc, const cplx *L, const cplx *psi, long 
                     sf += Uf[c * nc + e] * pf[s * nc + e];        /* U_mu(x) psi(x+mu)     */
                     sb += conj(Ub[e * nc + c]) * pb[s * nc + e];  /* U_mu(x-mu)^+ psi(x-mu) */
                 }
-                tf[s][c] = sf;
-                tb[s][c] = sb;
+                tf[s][c] = sgf * sf;
+                tb[s][c] = sgb * sb;
             }
         for (int s = 0; s < 4; ++s)
             for (int c = 0; c < nc; ++c) {
@@ -230,10 +247,10 @@ static void hop_site(const int *d, int nc, const cplx *L, const cplx *psi, long 
 
 /* out(x) = (H psi)(x) for every x of the given parity (-1: every site).
  * Sites of the other parity in out are left untouched. */
-int or_hop(const int *d, int nc, const double *Lr, int par, const double *psir, double *outr)
+int or_hop(const int *d, int bc, int nc, const double *Lr, int par, const double *psir, double *outr)
 {
     init_tables();
-    if (check_dims(d) || (nc != 2 && nc != 3)) return -1;
+    if (check_lat(d, bc) || (nc != 2 && nc != 3)) return -1;
     long V = volume(d);
     const cplx *L = (const cplx *)Lr, *psi = (const cplx *)psir;
     cplx *out = (cplx *)outr;
@@ -241,31 +258,31 @@ int or_hop(const int *d, int nc, const double *Lr, int par, const double *psir, 
 #pragma omp parallel for schedule(static)
     for (long x = 0; x < V; ++x) {
         if (par >= 0 && parity(d, x) != par) continue;
-        hop_site(d, nc, L, psi, x, out + x * ns);
+        hop_site(d, bc, nc, L, psi, x, out + x * ns);
     }
     return 0;
 }
 
 /* out[j] = (H psi)(sites[j]); out is [n][4][nc] */
-int or_hop_sites(const int *d, int nc, const double *Lr, const long *sites, long n,
+int or_hop_sites(const int *d, int bc, int nc, const double *Lr, const long *sites, long n,
                  const double *psir, double *outr)
 {
     init_tables();
-    if (check_dims(d) || (nc != 2 && nc != 3)) return -1;
+    if (check_lat(d, bc) || (nc != 2 && nc != 3)) return -1;
     long V = volume(d);
     for (long j = 0; j < n; ++j)
         if (sites[j] < 0 || sites[j] >= V) return -2;
     const cplx *L = (const cplx *)Lr, *psi = (const cplx *)psir;
     cplx *out = (cplx *)outr;
 #pragma omp parallel for schedule(static)
-    for (long j = 0; j < n; ++j) hop_site(d, nc, L, psi, sites[j], out + j * 4 * nc);
+    for (long j = 0; j < n; ++j) hop_site(d, bc, nc, L, psi, sites[j], out + j * 4 * nc);
     return 0;
 }
 
 /* full operator: out = (4+m0) psi - 1/2 H psi */
-int or_dirac(const int *d, int nc, const double *Lr, double m0, const double *psir, double *outr)
+int or_dirac(const int *d, int bc, int nc, const double *Lr, double m0, const double *psir, double *outr)
 {
-    int rc = or_hop(d, nc, Lr, -1, psir, outr);
+    int rc = or_hop(d, bc, nc, Lr, -1, psir, outr);
     if (rc) return rc;
     long n = volume(d) * 4 * nc;
     const cplx *psi = (const cplx *)psir;
@@ -285,11 +302,11 @@ static void apply_g5(int nc, long V, cplx *v)
 /* Mhat psi on even sites (dagger = 0) or Mhat^+ psi = g5 Mhat g5 psi (dagger = 1).
  * psi, out: full-lattice arrays; only even sites of psi are read, odd sites of
  * out are set to zero. */
-int or_schur(const int *d, int nc, const double *Lr, double m0, int dagger,
+int or_schur(const int *d, int bc, int nc, const double *Lr, double m0, int dagger,
              const double *psir, double *outr)
 {
     init_tables();
-    if (check_dims(d) || (nc != 2 && nc != 3)) return -1;
+    if (check_lat(d, bc) || (nc != 2 && nc != 3)) return -1;
     long V = volume(d), n = V * 4 * nc;
     double A = 4.0 + m0;
     cplx *in = calloc(n, sizeof(cplx)), *t = calloc(n, sizeof(cplx));
@@ -299,8 +316,8 @@ int or_schur(const int *d, int nc, const double *Lr, double m0, int dagger,
     for (long x = 0; x < V; ++x)
         if (parity(d, x) == 0) memcpy(in + x * 4 * nc, psi + x * 4 * nc, 4 * nc * sizeof(cplx));
     if (dagger) apply_g5(nc, V, in);
-    or_hop(d, nc, Lr, 1, (const double *)in, (double *)t);  /* t_o = H_oe in_e   */
-    or_hop(d, nc, Lr, 0, (const double *)t, (double *)u);   /* u_e = H_eo t_o    */
+    or_hop(d, bc, nc, Lr, 1, (const double *)in, (double *)t);  /* t_o = H_oe in_e   */
+    or_hop(d, bc, nc, Lr, 0, (const double *)t, (double *)u);   /* u_e = H_eo t_o    */
     cplx *out = (cplx *)outr;
     for (long x = 0; x < V; ++x) {
         cplx *o = out + x * 4 * nc;
@@ -316,13 +333,13 @@ int or_schur(const int *d, int nc, const double *Lr, double m0, int dagger,
 }
 
 /* out = Mhat^+ Mhat psi (even sites) */
-int or_normal(const int *d, int nc, const double *Lr, double m0, const double *psir, double *outr)
+int or_normal(const int *d, int bc, int nc, const double *Lr, double m0, const double *psir, double *outr)
 {
     long n = volume(d) * 4 * nc;
     double *tmp = calloc(2 * n, sizeof(double));
     if (!tmp) return -3;
-    int rc = or_schur(d, nc, Lr, m0, 0, psir, tmp);
-    if (!rc) rc = or_schur(d, nc, Lr, m0, 1, tmp, outr);
+    int rc = or_schur(d, bc, nc, Lr, m0, 0, psir, tmp);
+    if (!rc) rc = or_schur(d, bc, nc, Lr, m0, 1, tmp, outr);
     free(tmp);
     return rc;
 }
@@ -337,11 +354,11 @@ static double dotre(long n, const cplx *a, const cplx *b)
 /* Hestenes-Stiefel CG on Mhat^+ Mhat x = b (even sites), x0 = 0.
  * Stops when the iterated residual satisfies |r| <= tol |b|; then returns the
  * true relative residual |b - A x| / |b| recomputed from x. */
-int or_cg(const int *d, int nc, const double *Lr, double m0, const double *br, double *xr,
+int or_cg(const int *d, int bc, int nc, const double *Lr, double m0, const double *br, double *xr,
           double tol, int maxiter, int *iters, double *true_rel)
 {
     init_tables();
-    if (check_dims(d) || (nc != 2 && nc != 3)) return -1;
+    if (check_lat(d, bc) || (nc != 2 && nc != 3)) return -1;
     long n = volume(d) * 4 * nc;
     const cplx *b = (const cplx *)br;
     cplx *x = (cplx *)xr;
@@ -351,7 +368,7 @@ int or_cg(const int *d, int nc, const double *Lr, double m0, const double *br, d
     double bb = dotre(n, b, b), rr = bb;
     int it = 0;
     while (it < maxiter && sqrt(rr / bb) > tol) {
-        or_normal(d, nc, Lr, m0, (const double *)p, (double *)q);
+        or_normal(d, bc, nc, Lr, m0, (const double *)p, (double *)q);
         double alpha = rr / dotre(n, p, q);
         for (long k = 0; k < n; ++k) { x[k] += alpha * p[k]; r[k] -= alpha * q[k]; }
         double rr_new = dotre(n, r, r);
@@ -360,7 +377,7 @@ int or_cg(const int *d, int nc, const double *Lr, double m0, const double *br, d
         rr = rr_new;
         ++it;
     }
-    or_normal(d, nc, Lr, m0, (const double *)x, (double *)q);
+    or_normal(d, bc, nc, Lr, m0, (const double *)x, (double *)q);
     for (long k = 0; k < n; ++k) r[k] = b[k] - q[k];
     *true_rel = sqrt(dotre(n, r, r) / bb);
     *iters = it;
@@ -377,11 +394,13 @@ int or_cg(const int *d, int nc, const double *Lr, double m0, const double *br, d
  *   df/deps = Re tr[ X (Q1 - Q2) ],
  *   Q1 = sum_s (U b(x+mu))_s [((1-g_mu) a(x))_s]^+,
  *   Q2 = sum_s b(x)_s [(U (1+g_mu) a(x+mu))_s]^+.
- * F[mu][x][a-1] = d f / d w_a = Re tr[(i s_a / 2)(Q1 - Q2)], a = 1..3. */
-int or_force(const int *d, const double *Lr, const double *ar, const double *br, double *F)
+ * F[mu][x][a-1] = d f / d w_a = Re tr[(i s_a / 2)(Q1 - Q2)], a = 1..3.
+ * Across an antiperiodic boundary both terms (the hop x -> x+mu and the hop
+ * x+mu -> x) carry the same factor -1, and so does F. */
+int or_force(const int *d, int bc, const double *Lr, const double *ar, const double *br, double *F)
 {
     init_tables();
-    if (check_dims(d)) return -1;
+    if (check_lat(d, bc)) return -1;
     long V = volume(d);
     const cplx *L = (const cplx *)Lr, *a = (const cplx *)ar, *b = (const cplx *)br;
 #pragma omp parallel for schedule(static)
@@ -416,11 +435,12 @@ int or_force(const int *d, const double *Lr, const double *ar, const double *br,
                     }
                     Q[i][j] = s;
                 }
+            double sg = wrap_sign(d, bc, x, mu, +1);
             for (int k = 1; k <= 3; ++k) {
                 cplx tr = 0;
                 for (int i = 0; i < 2; ++i)
                     for (int j = 0; j < 2; ++j) tr += 0.5 * I * SIG[k][i][j] * Q[j][i];
-                F[((long)mu * V + x) * 3 + (k - 1)] = creal(tr);
+                F[((long)mu * V + x) * 3 + (k - 1)] = sg * creal(tr);
             }
         }
     }
@@ -429,11 +449,12 @@ int or_force(const int *d, const double *Lr, const double *ar, const double *br,
 
 /* G[mu][x][k] = d Re<a, H b> / d a_k for the link quaternion of U_mu(x),
  * U = sum_k a_k E_k with E_0 = 1, E_k = i s_k:
- *   = Re[a(x)^+ (1-g_mu) E_k b(x+mu)] + Re[a(x+mu)^+ (1+g_mu) E_k^+ b(x)]. */
-int or_link_grad(const int *d, const double *ar, const double *br, double *G)
+ *   = Re[a(x)^+ (1-g_mu) E_k b(x+mu)] + Re[a(x+mu)^+ (1+g_mu) E_k^+ b(x)],
+ * times -1 when the link crosses an antiperiodic boundary (as for the force). */
+int or_link_grad(const int *d, int bc, const double *ar, const double *br, double *G)
 {
     init_tables();
-    if (check_dims(d)) return -1;
+    if (check_lat(d, bc)) return -1;
     long V = volume(d);
     const cplx *a = (const cplx *)ar, *b = (const cplx *)br;
 #pragma omp parallel for schedule(static)
@@ -456,7 +477,7 @@ int or_link_grad(const int *d, const double *ar, const double *br, double *G)
                                 acc += conj(a[(xf * 4 + s) * 2 + i]) * gp * Ed[i][j] * b[(x * 4 + t) * 2 + j];
                             }
                     }
-                G[((long)mu * V + x) * 4 + k] = creal(acc);
+                G[((long)mu * V + x) * 4 + k] = wrap_sign(d, bc, x, mu, +1) * creal(acc);
             }
         }
     }

@@ -66,14 +66,17 @@ def link_matrices(dims, q, nc):
     return out
 
 
-def hopping_dense(dims, q, nc) -> np.ndarray:
+def hopping_dense(dims, q, nc, bc=0) -> np.ndarray:
     """Dense H with (H psi)(x) = sum_mu (1-g) U_mu(x) psi(x+mu) + (1+g) U_mu(x-mu)^+ psi(x-mu).
 
     Index order (site, spin, colour).  On an extent-2 direction the forward and
-    backward neighbours coincide and the two blocks add.
+    backward neighbours coincide and the two blocks add.  Bit mu of ``bc`` makes
+    direction mu antiperiodic: a block whose neighbour is reached through the
+    lattice's edge in that direction enters with a minus sign.
     """
     V = int(np.prod(dims))
     idx = site_index(dims)
+    xs = np.indices(dims).reshape(4, -1)  # xs[mu, x] = coordinate mu of site x
     U = link_matrices(dims, q, nc)
     n = V * 4 * nc
     H = np.zeros((V, 4, nc, V, 4, nc), dtype=complex)
@@ -81,17 +84,20 @@ def hopping_dense(dims, q, nc) -> np.ndarray:
     for mu in range(4):
         fwd = np.roll(idx, -1, axis=mu).reshape(-1)  # fwd[x] = x + mu
         bwd = np.roll(idx, 1, axis=mu).reshape(-1)   # bwd[x] = x - mu
+        anti = (bc >> mu) & 1
         pm = one - GAMMA[mu]
         pp = one + GAMMA[mu]
         for x in range(V):
-            H[x, :, :, fwd[x], :, :] += np.einsum("st,cd->sctd", pm, U[mu, x])
-            H[x, :, :, bwd[x], :, :] += np.einsum("st,cd->sctd", pp, U[mu, bwd[x]].conj().T)
+            sf = -1.0 if anti and xs[mu, x] == dims[mu] - 1 else 1.0
+            sb = -1.0 if anti and xs[mu, x] == 0 else 1.0
+            H[x, :, :, fwd[x], :, :] += sf * np.einsum("st,cd->sctd", pm, U[mu, x])
+            H[x, :, :, bwd[x], :, :] += sb * np.einsum("st,cd->sctd", pp, U[mu, bwd[x]].conj().T)
     return H.reshape(n, n)
 
 
-def dirac_dense(dims, q, nc, m0) -> np.ndarray:
+def dirac_dense(dims, q, nc, m0, bc=0) -> np.ndarray:
     n = int(np.prod(dims)) * 4 * nc
-    return (4.0 + m0) * np.eye(n) - 0.5 * hopping_dense(dims, q, nc)
+    return (4.0 + m0) * np.eye(n) - 0.5 * hopping_dense(dims, q, nc, bc)
 
 
 def parity_of_sites(dims) -> np.ndarray:

@@ -5,7 +5,8 @@ even-odd preconditioned form (Sec. 2.1, Table 1) without printing a formula or
 a worked example, so the oracle is pinned by closed forms and invariants of
 that operator:
 
-* free-field plane waves: D e^{ipx} u = [m0 + sum(1-cos p) + i sum g sin p] e^{ipx} u
+* free-field plane waves: D e^{ipx} u = [m0 + sum(1-cos p) + i sum g sin p] e^{ipx} u,
+  with p_mu = 2 pi n / L_mu, or (2n+1) pi / L_mu in antiperiodic directions
 * flat non-trivial connections (momentum shifted by the link's eigenphases)
 * gamma5-hermiticity, gauge covariance
 * brute force against an independent dense build (tests/dense_ref.py), on
@@ -152,25 +153,71 @@ def test_antiperiodic_links_in_time(nc):
     assert V == 64
 
 
+@pytest.mark.parametrize("nc", [2, 3])
+@pytest.mark.parametrize("bc", [1, 5, 8, 15])
+def test_free_field_antiperiodic_plane_wave(nc, bc):
+    """Antiperiodic in direction mu: the momenta are p_mu = (2n+1) pi / L_mu,
+    and e^{ipx} u restricted to the box is an eigenvector with the free symbol."""
+    dims = (4, 6, 2, 4)
+    L = oracle.expand_links(dims, nc, synth.identity_links(dims))
+    x = coords(dims)
+    m0 = -0.1
+    anti = np.array([(bc >> mu) & 1 for mu in range(4)])
+    for trial in range(3):
+        n = np.array([RNG.integers(0, d) for d in dims])
+        p = (2 * n + anti) * np.pi / np.array(dims)
+        u = RNG.normal(size=(4, nc)) + 1j * RNG.normal(size=(4, nc))
+        phase = np.exp(1j * (x @ p))
+        psi = phase[:, None, None] * u[None]
+        want = phase[:, None, None] * (free_field_symbol(p, m0) @ u)[None]
+        assert rel(oracle.dirac(dims, L, m0, psi, bc=bc), want) < 1e-14
+        # the periodic operator does not have this eigenvector
+        assert rel(oracle.dirac(dims, L, m0, psi), want) > 1e-3
+
+
+def test_antiperiodic_fundamental_equals_negated_boundary_links():
+    """For SU(2) fundamental fermions -1 is a gauge link: the antiperiodic operator
+    is the periodic one with the links U_mu(x), x_mu = L_mu - 1, negated.  The
+    adjoint representation is blind to that sign (R(-U) = R(U))."""
+    dims = (4, 2, 4, 6)
+    q = synth.haar_links(dims, 131)
+    x = coords(dims)
+    for bc in (1, 6, 15):
+        qn = q.copy()
+        for mu in range(4):
+            if (bc >> mu) & 1:
+                qn[mu, x[:, mu] == dims[mu] - 1] *= -1.0
+        for nc in (2, 3):
+            psi = synth.gaussian_spinor(dims, nc, 132)
+            got = oracle.dirac(dims, oracle.expand_links(dims, nc, q), 0.2, psi, bc=bc)
+            neg = oracle.dirac(dims, oracle.expand_links(dims, nc, qn), 0.2, psi)
+            if nc == 2:
+                assert rel(got, neg) < 1e-15
+            else:
+                per = oracle.dirac(dims, oracle.expand_links(dims, nc, q), 0.2, psi)
+                assert rel(neg, per) < 1e-15 and rel(got, per) > 1e-2
+
+
 # ---------------------------------------------------------------- invariants
 
 @pytest.mark.parametrize("nc", [2, 3])
-def test_gamma5_hermiticity(nc):
+@pytest.mark.parametrize("bc", [0, 15])
+def test_gamma5_hermiticity(nc, bc):
     dims = (4, 2, 4, 6)
     q = synth.haar_links(dims, 21)
     L = oracle.expand_links(dims, nc, q)
     phi = synth.gaussian_spinor(dims, nc, 22)
     psi = synth.gaussian_spinor(dims, nc, 23)
     m0 = 0.05
-    lhs = inner(phi, oracle.dirac(dims, L, m0, psi))
-    rhs = inner(oracle.gamma5(oracle.dirac(dims, L, m0, oracle.gamma5(phi))), psi)
+    lhs = inner(phi, oracle.dirac(dims, L, m0, psi, bc=bc))
+    rhs = inner(oracle.gamma5(oracle.dirac(dims, L, m0, oracle.gamma5(phi), bc=bc)), psi)
     assert abs(lhs - rhs) / abs(lhs) < 1e-14
     # the even-odd Schur operator and its stated adjoint
     even = oracle.parity_mask(dims) == 0
     phi[~even] = 0
     psi[~even] = 0
-    lhs = inner(phi, oracle.schur(dims, L, m0, psi))
-    rhs = inner(oracle.schur(dims, L, m0, phi, dagger=True), psi)
+    lhs = inner(phi, oracle.schur(dims, L, m0, psi, bc=bc))
+    rhs = inner(oracle.schur(dims, L, m0, phi, dagger=True, bc=bc), psi)
     assert abs(lhs - rhs) / abs(lhs) < 1e-14
 
 
@@ -198,22 +245,24 @@ def test_gauge_covariance(nc):
 
 @pytest.mark.parametrize("nc", [2, 3])
 @pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 4)])
-def test_dense_bruteforce_full_operator(nc, dims):
+@pytest.mark.parametrize("bc", [0, 1, 10, 15])
+def test_dense_bruteforce_full_operator(nc, dims, bc):
     q = synth.haar_links(dims, 41)
     L = oracle.expand_links(dims, nc, q)
-    D = dr.dirac_dense(dims, q, nc, 0.1)
+    D = dr.dirac_dense(dims, q, nc, 0.1, bc)
     for seed in (42, 43):
         psi = synth.gaussian_spinor(dims, nc, seed)
-        assert rel(oracle.dirac(dims, L, 0.1, psi).reshape(-1), D @ psi.reshape(-1)) < 1e-14
+        assert rel(oracle.dirac(dims, L, 0.1, psi, bc=bc).reshape(-1), D @ psi.reshape(-1)) < 1e-14
 
 
 @pytest.mark.parametrize("nc", [2, 3])
-def test_dense_schur_complement(nc):
+@pytest.mark.parametrize("bc", [0, 9])
+def test_dense_schur_complement(nc, bc):
     dims = (2, 4, 2, 2)
     m0 = -0.2
     q = synth.haar_links(dims, 51)
     L = oracle.expand_links(dims, nc, q)
-    D = dr.dirac_dense(dims, q, nc, m0)
+    D = dr.dirac_dense(dims, q, nc, m0, bc)
     Dee, Deo, Doe, Doo, e, o = dr.eo_blocks(dims, nc, D)
     np.testing.assert_allclose(Dee, (4 + m0) * np.eye(len(e)), atol=0)
     np.testing.assert_allclose(Doo, (4 + m0) * np.eye(len(o)), atol=0)
@@ -226,12 +275,12 @@ def test_dense_schur_complement(nc):
     psi = synth.gaussian_spinor(dims, nc, 52)
     psi[oracle.parity_mask(dims) == 1] = 0
     flat = psi.reshape(-1)
-    got = oracle.schur(dims, L, m0, psi).reshape(-1)
+    got = oracle.schur(dims, L, m0, psi, bc=bc).reshape(-1)
     assert rel(got[e], Mhat @ flat[e]) < 1e-14
     assert np.all(got[o] == 0)
-    gotd = oracle.schur(dims, L, m0, psi, dagger=True).reshape(-1)
+    gotd = oracle.schur(dims, L, m0, psi, dagger=True, bc=bc).reshape(-1)
     assert rel(gotd[e], Mhat.conj().T @ flat[e]) < 1e-14
-    gotn = oracle.normal(dims, L, m0, psi).reshape(-1)
+    gotn = oracle.normal(dims, L, m0, psi, bc=bc).reshape(-1)
     assert rel(gotn[e], Mhat.conj().T @ (Mhat @ flat[e])) < 1e-14
 
 
@@ -254,19 +303,20 @@ def test_hop_sites_matches_parity_hop():
 # ---------------------------------------------------------------- solvers
 
 @pytest.mark.parametrize("nc", [2, 3])
-def test_cg_against_dense_solve(nc):
+@pytest.mark.parametrize("bc", [0, 1])
+def test_cg_against_dense_solve(nc, bc):
     dims = (2, 4, 2, 4)
     m0 = -0.2
     q = synth.haar_links(dims, 71)
     L = oracle.expand_links(dims, nc, q)
-    D = dr.dirac_dense(dims, q, nc, m0)
+    D = dr.dirac_dense(dims, q, nc, m0, bc)
     Dee, Deo, Doe, Doo, e, o = dr.eo_blocks(dims, nc, D)
     Mhat = Dee - Deo @ np.linalg.solve(Doo, Doe)
     A = Mhat.conj().T @ Mhat
     assert np.linalg.eigvalsh(A).min() > 0
     b = synth.gaussian_spinor(dims, nc, 72)
     b[oracle.parity_mask(dims) == 1] = 0
-    x, iters, true_rel, ok = oracle.cg(dims, L, m0, b, tol=1e-12)
+    x, iters, true_rel, ok = oracle.cg(dims, L, m0, b, tol=1e-12, bc=bc)
     assert ok and true_rel <= 1e-12
     xd = np.linalg.solve(A, b.reshape(-1)[e])
     assert rel(x.reshape(-1)[e], xd) < 1e-10
@@ -276,21 +326,22 @@ def test_cg_against_dense_solve(nc):
 
 
 @pytest.mark.parametrize("nc", [2, 3])
-def test_eo_solve_of_full_operator(nc):
+@pytest.mark.parametrize("bc", [0, 1])
+def test_eo_solve_of_full_operator(nc, bc):
     """Source preparation + Schur solve + odd reconstruction solves D x = b."""
     dims = (4, 2, 2, 4)
     m0 = 0.1
     q = synth.haar_links(dims, 81)
     L = oracle.expand_links(dims, nc, q)
     b = synth.gaussian_spinor(dims, nc, 82)
-    bhat = oracle.eo_source(dims, L, m0, b)
+    bhat = oracle.eo_source(dims, L, m0, b, bc=bc)
     # solve Mhat x_e = bhat via CG on Mhat^+ Mhat x_e = Mhat^+ bhat
-    rhs = oracle.schur(dims, L, m0, bhat, dagger=True)
-    xe, it, tr, ok = oracle.cg(dims, L, m0, rhs, tol=1e-13)
+    rhs = oracle.schur(dims, L, m0, bhat, dagger=True, bc=bc)
+    xe, it, tr, ok = oracle.cg(dims, L, m0, rhs, tol=1e-13, bc=bc)
     assert ok
-    x = oracle.eo_reconstruct(dims, L, m0, b, xe)
-    assert rel(oracle.dirac(dims, L, m0, x), b) < 1e-11
-    D = dr.dirac_dense(dims, q, nc, m0)
+    x = oracle.eo_reconstruct(dims, L, m0, b, xe, bc=bc)
+    assert rel(oracle.dirac(dims, L, m0, x, bc=bc), b) < 1e-11
+    D = dr.dirac_dense(dims, q, nc, m0, bc)
     assert rel(x.reshape(-1), np.linalg.solve(D, b.reshape(-1))) < 1e-10
 
 
@@ -303,16 +354,18 @@ def _su2_exp(w):
     return np.concatenate([[np.cos(th)], np.sin(th) * n])
 
 
-def test_link_grad_matches_finite_differences():
+@pytest.mark.parametrize("bc", [0, 5])
+def test_link_grad_matches_finite_differences(bc):
     dims = (2, 4, 2, 2)
     V = int(np.prod(dims))
     q = synth.haar_links(dims, 91)
     a = synth.gaussian_spinor(dims, 2, 92)
     b = synth.gaussian_spinor(dims, 2, 93)
-    G = oracle.link_grad(dims, a, b)
+    G = oracle.link_grad(dims, a, b, bc=bc)
 
     def f(qq):
-        return inner(a, oracle.hop(dims, oracle.expand_links(dims, 2, qq), b)).real
+        # the operator itself from the independent dense build
+        return inner(a.reshape(-1), dr.hopping_dense(dims, qq, 2, bc) @ b.reshape(-1)).real
 
     eps = 1e-6
     for _ in range(12):
@@ -324,7 +377,8 @@ def test_link_grad_matches_finite_differences():
         assert abs(fd - G[mu, x, k]) < 1e-7 * max(1.0, abs(fd))
 
 
-def test_force_matches_finite_differences_of_solve_loss():
+@pytest.mark.parametrize("bc", [0, 3])
+def test_force_matches_finite_differences_of_solve_loss(bc):
     """S = Re<eta, (Mhat^+ Mhat)^-1 eta>; F = dS/dw under U -> exp(i w.s/2) U.
 
     dS = 2c Re[<Y, dH_eo H_oe X> + <H_eo^+ Y, dH_oe X>],  X = A^-1 eta,
@@ -343,19 +397,19 @@ def test_force_matches_finite_differences_of_solve_loss():
     eta[~even] = 0
 
     def S(qq):
-        D = dr.dirac_dense(dims, qq, 2, m0)
+        D = dr.dirac_dense(dims, qq, 2, m0, bc)
         Dee, Deo, Doe, Doo, e, o = dr.eo_blocks(dims, 2, D)
         M = Dee - Deo @ np.linalg.solve(Doo, Doe)
         y = eta.reshape(-1)[e]
         return np.vdot(y, np.linalg.solve(M.conj().T @ M, y)).real
 
-    X, it, tr, ok = oracle.cg(dims, L, m0, eta, tol=1e-14, maxiter=5000)
-    Y = oracle.schur(dims, L, m0, X)
-    Z = oracle.hop(dims, L, X, parity=1)                        # H_oe X on odd sites
-    W = oracle.gamma5(oracle.hop(dims, L, oracle.gamma5(Y), parity=1))  # H_eo^+ Y on odd sites
+    X, it, tr, ok = oracle.cg(dims, L, m0, eta, tol=1e-14, maxiter=5000, bc=bc)
+    Y = oracle.schur(dims, L, m0, X, bc=bc)
+    Z = oracle.hop(dims, L, X, parity=1, bc=bc)                        # H_oe X on odd sites
+    W = oracle.gamma5(oracle.hop(dims, L, oracle.gamma5(Y), parity=1, bc=bc))  # H_eo^+ Y on odd sites
     a = np.where(even[:, None, None], Y, W)
     b = np.where(even[:, None, None], X, Z)
-    F = 2.0 / (4.0 * A4) * oracle.force(dims, L, a, b)
+    F = 2.0 / (4.0 * A4) * oracle.force(dims, L, a, b, bc=bc)
     eps = 1e-5
     for _ in range(10):
         mu, x = RNG.integers(4), RNG.integers(V)
