@@ -90,7 +90,23 @@ typedef enum {
     HR_OP_NORMAL = 3     /* out_e = Mhat^+ Mhat in_e                                  */
 } hr_op;
 
-typedef struct { int dims[4]; } hr_lattice; /* (T, L1, L2, L3) */
+/* A lattice: extents (T, L1, L2, L3), each even and >= 2, and its fermion
+ * boundary conditions.  Bit mu of bc (HR_BC_ANTIPERIODIC(mu), mu = 0 is time)
+ * makes direction mu antiperiodic, psi(x + L_mu mu-hat) = -psi(x); bc = 0 is
+ * periodic in all four directions.  (The paper, arXiv:2411.18511, states no
+ * boundary condition; antiperiodic time is the usual choice for fermions.)
+ *
+ * Where bc acts: hr_gauge_pack folds the sign into the packed links of the
+ * last slice x_mu = L_mu - 1 of each antiperiodic direction (every hop that
+ * crosses the boundary uses one of those links), so a packed gauge field
+ * carries its boundary conditions into every operator, solver and force
+ * applied with it.  hr_link_grad, which takes no gauge field, applies the
+ * sign itself.  Other calls ignore bc.  bc outside [0, 15]: HR_ERR_INVALID_ARG. */
+typedef struct {
+    int dims[4];
+    int bc;
+} hr_lattice;
+#define HR_BC_ANTIPERIODIC(mu) (1 << (mu))
 
 typedef struct hr_ctx hr_ctx;
 
@@ -123,7 +139,12 @@ size_t hr_gauge_packed_bytes(hr_lattice lat, hr_rep rep, hr_prec prec);
 size_t hr_spinor_packed_bytes(hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity parity, int n_rhs);
 
 /* canonical gauge (device, double[4][V][4]) -> packed (device).  For HR_ADJ_MAT
- * the 3x3 adjoint matrices are built on the GPU from the quaternions. */
+ * the 3x3 adjoint matrices are built on the GPU from the quaternions.  The
+ * boundary sign of lat.bc is folded in: HR_FUND stores -q on the boundary
+ * slice; HR_ADJ stores the representative of +-q whose q0 has its sign bit
+ * clear, and sets that bit on the boundary slice (R(q) = R(-q), so the sign
+ * bit is free to carry the factor -1 that the kernels apply to R); HR_ADJ_MAT
+ * stores -R there.  A packed gauge field is therefore specific to its rep. */
 hr_status hr_gauge_pack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec,
                         const double *canonical, void *packed, hr_stream stream);
 
@@ -247,8 +268,9 @@ hr_status hr_force(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *a
                    const void *b_full, double beta, double *force, hr_stream stream);
 
 /* grad[mu][x][k] += beta * d Re<a_f, H b_f> / d q_k for the quaternion
- * components q_k of U_mu(x) (U = sum_k q_k E_k, E_0 = 1, E_k = i s_k).
- * grad: device double[4][V][4]. */
+ * components q_k of U_mu(x) (U = sum_k q_k E_k, E_0 = 1, E_k = i s_k), with
+ * the boundary sign of lat.bc on the links of the last slice of each
+ * antiperiodic direction.  grad: device double[4][V][4]. */
 hr_status hr_link_grad(hr_ctx *ctx, hr_lattice lat, const void *a_full, const void *b_full,
                        double beta, double *grad, hr_stream stream);
 

@@ -51,7 +51,7 @@ def _check_dims(q: torch.Tensor, dims):
         V *= int(d)
     if tuple(q.shape) != (4, V, 4):
         raise ValueError(f"links must have shape (4, {V}, 4), got {tuple(q.shape)}")
-    return tuple(int(d) for d in dims)
+    return hr.Lattice(dims, getattr(dims, "bc", 0))  # keeps the boundary conditions
 
 
 class _Lattice:

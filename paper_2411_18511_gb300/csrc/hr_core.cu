@@ -42,6 +42,7 @@ static bool lattice_ok(const hr_lattice &lat, int nrhs)
         v *= lat.dims[k];
     }
     if (nrhs < 1 || nrhs > kMaxRhs || (nrhs & (nrhs - 1))) return false;
+    if (lat.bc & ~15) return false;
     // virtual-site indices and 16-byte vector indices must fit the kernels' int arithmetic
     return (v / 2) * nrhs * 12 < (1LL << 31);
 }
@@ -72,6 +73,7 @@ hr_status validate_lattice(hr_ctx *ctx, const hr_lattice &lat, int nrhs)
     }
     if (nrhs < 1 || nrhs > kMaxRhs || (nrhs & (nrhs - 1)))
         return set_error(ctx, HR_ERR_UNSUPPORTED, "n_rhs = %d: must be a power of two in [1, %d]", nrhs, kMaxRhs);
+    if (lat.bc & ~15) return set_error(ctx, HR_ERR_INVALID_ARG, "bc = %d: one bit per direction, [0, 15]", lat.bc);
     if (!lattice_ok(lat, nrhs)) return set_error(ctx, HR_ERR_UNSUPPORTED, "lattice too large for 32-bit site indexing");
     return HR_OK;
 }
@@ -105,9 +107,17 @@ size_t gauge_bytes(const Geom &g, int rep, int prec)
 
 namespace {
 
-// one thread per link (mu, lex site)
+// the link U_mu(x) sits on the boundary slice x_mu = L_mu - 1 of an antiperiodic direction
+__device__ __forceinline__ bool boundary_link(const Geom &g, int mu, const int (&x)[4])
+{
+    return ((g.bc >> mu) & 1) && x[mu] == g.d[mu] - 1;
+}
+
+// one thread per link (mu, lex site).  canon (adjoint): store the representative
+// of +-q with the sign bit of q0 clear, then set it on boundary links; the
+// fundamental stores -q on boundary links.
 template <int PREC>
-__global__ void k_gauge_pack_quat(Geom g, const double *__restrict__ can, void *packed)
+__global__ void k_gauge_pack_quat(Geom g, int canon, const double *__restrict__ can, void *packed)
 {
     long long V = 2LL * g.vh;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,7 +132,11 @@ __global__ void k_gauge_pack_quat(Geom g, const double *__restrict__ can, void *
     int x0 = (int)(r / g.d[1]);
     int p = (x0 + x1 + x2 + x3) & 1;
     int i = (int)(x >> 1);
-    const double a[4] = {can[t * 4 + 0], can[t * 4 + 1], can[t * 4 + 2], can[t * 4 + 3]};
+    double a[4] = {can[t * 4 + 0], can[t * 4 + 1], can[t * 4 + 2], can[t * 4 + 3]};
+    const int xc[4] = {x0, x1, x2, x3};
+    const bool neg = (canon && sign_bit(a[0])) != boundary_link(g, mu, xc);
+    if (neg)
+        for (int k = 0; k < 4; ++k) a[k] = -a[k];
     store_quat<PREC>(packed, g.nblk_g, p, mu, i, a);
 }
 
@@ -143,10 +157,14 @@ __global__ void k_gauge_pack_mat(Geom g, const double *__restrict__ can, void *p
     int p = (x0 + x1 + x2 + x3) & 1;
     int i = (int)(x >> 1);
     double a[4] = {can[t * 4 + 0], can[t * 4 + 1], can[t * 4 + 2], can[t * 4 + 3]};
+    if (sign_bit(a[0]))
+        for (int k = 0; k < 4; ++k) a[k] = -a[k]; // R(q) = R(-q); quat_to_adj reads the sign bit
     double R[3][3];
     quat_to_adj(a, R);
+    const int xc[4] = {x0, x1, x2, x3};
+    const double sg = boundary_link(g, mu, xc) ? -1.0 : 1.0;
     for (int e = 0; e < 9; ++e) {
-        store_mat_entry<PREC>(packed, g.nblk_g, p, mu, i, e, R[e / 3][e % 3]);
+        store_mat_entry<PREC>(packed, g.nblk_g, p, mu, i, e, sg * R[e / 3][e % 3]);
     }
 }
 
@@ -258,8 +276,10 @@ __global__ void k_gauge_convert(Geom g, const void *src, void *dst)
         // FP64 packed links are double-float pairs: hi float4 then lo float4
         const float4 *q = (const float4 *)src;
         float4 hi = q[(slot * 2 + 0) * 32 + lane], lo = q[(slot * 2 + 1) * 32 + lane];
-        float4 w0 = make_float4(__fadd_rn(hi.x, lo.x), __fadd_rn(hi.y, lo.y), __fadd_rn(hi.z, lo.z),
-                                __fadd_rn(hi.w, lo.w));
+        // the sign of hi survives (-0 + 0 would round to +0 and lose the
+        // adjoint links' boundary bit on a link with q0 = 0)
+        float4 w0 = make_float4(copysignf(__fadd_rn(hi.x, lo.x), hi.x), copysignf(__fadd_rn(hi.y, lo.y), hi.y),
+                                copysignf(__fadd_rn(hi.z, lo.z), hi.z), copysignf(__fadd_rn(hi.w, lo.w), hi.w));
         if (PD == kF32) {
             ((float4 *)dst)[slot * 32 + lane] = w0;
         } else {
@@ -401,9 +421,10 @@ hr_status hr_gauge_pack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, c
         else if (prec == kF32) k_gauge_pack_mat<kF32><<<grid, bs, 0, s>>>(g, canonical, packed);
         else k_gauge_pack_mat<kF16><<<grid, bs, 0, s>>>(g, canonical, packed);
     } else {
-        if (prec == kF64) k_gauge_pack_quat<kF64><<<grid, bs, 0, s>>>(g, canonical, packed);
-        else if (prec == kF32) k_gauge_pack_quat<kF32><<<grid, bs, 0, s>>>(g, canonical, packed);
-        else k_gauge_pack_quat<kF16><<<grid, bs, 0, s>>>(g, canonical, packed);
+        const int canon = rep == HR_ADJ ? 1 : 0;
+        if (prec == kF64) k_gauge_pack_quat<kF64><<<grid, bs, 0, s>>>(g, canon, canonical, packed);
+        else if (prec == kF32) k_gauge_pack_quat<kF32><<<grid, bs, 0, s>>>(g, canon, canonical, packed);
+        else k_gauge_pack_quat<kF16><<<grid, bs, 0, s>>>(g, canon, canonical, packed);
     }
     return check_launch(ctx, "gauge pack");
 }

@@ -12,6 +12,8 @@
 //   su(2) force          F_a = Re tr[(i s_a/2)(U M1 - M2 U^+)]   for U -> exp(i w.s/2) U.
 // One thread per site (both parities in one launch); it writes all four
 // directions of its own links, so no two threads touch the same output.
+// Antiperiodic directions: the two terms that contain a link on the boundary
+// slice both cross the boundary and carry its factor -1.
 #include "hr_host.h"
 
 using namespace hr;
@@ -36,8 +38,11 @@ __device__ __forceinline__ c2 cmulc(c2 a, c2 b) { return {a.re * b.re + a.im * b
 __device__ __forceinline__ c2 cplus(c2 a, c2 b) { return {a.re + b.re, a.im + b.im}; }
 __device__ __forceinline__ c2 cminus(c2 a, c2 b) { return {a.re - b.re, a.im - b.im}; }
 
+// sg: -1 for a link on the boundary slice of an antiperiodic direction.  The
+// force reads the packed links, which carry that sign already; the quaternion
+// gradient takes no gauge field and applies it here.
 template <int MU>
-__device__ __forceinline__ void link_terms(const ForceArgs &A, int p, int i, int ifw, long long lex)
+__device__ __forceinline__ void link_terms(const ForceArgs &A, int p, int i, int ifw, long long lex, double sg)
 {
     const Geom &g = A.g;
     cpx<double> ax[4][2], axf[4][2], bx[4][2], bxf[4][2];
@@ -78,7 +83,7 @@ __device__ __forceinline__ void link_terms(const ForceArgs &A, int p, int i, int
         G[0] = M1[0][0].re + M1[1][1].re + M2[0][0].re + M2[1][1].re;
         for (int k = 0; k < 3; ++k) G[k + 1] = -t1[k].im + t2[k].im;
         double *o = A.out + ((long long)MU * V + lex) * 4;
-        for (int k = 0; k < 4; ++k) o[k] += A.beta * G[k];
+        for (int k = 0; k < 4; ++k) o[k] += sg * A.beta * G[k];
     } else {
         double q[4];
         load_quat<kF64>(A.gauge, g.nblk_g, p, MU, i, q);
@@ -111,10 +116,18 @@ __global__ void k_link_deriv(ForceArgs A)
     SiteNb nb;
     site_neighbours(g, i, p, nb);
     long long lex = eo_to_lex(g, i, p);
-    link_terms<0>(A, p, i, nb.fwd[0], lex);
-    link_terms<1>(A, p, i, nb.fwd[1], lex);
-    link_terms<2>(A, p, i, nb.fwd[2], lex);
-    link_terms<3>(A, p, i, nb.fwd[3], lex);
+    // coordinates of the site: boundary slices of the antiperiodic directions
+    int x[4];
+    long long r = lex;
+    for (int k = 3; k >= 0; --k) {
+        x[k] = (int)(r % g.d[k]);
+        r /= g.d[k];
+    }
+    auto sg = [&](int mu) { return (A.mode == 1 && ((g.bc >> mu) & 1) && x[mu] == g.d[mu] - 1) ? -1.0 : 1.0; };
+    link_terms<0>(A, p, i, nb.fwd[0], lex, sg(0));
+    link_terms<1>(A, p, i, nb.fwd[1], lex, sg(1));
+    link_terms<2>(A, p, i, nb.fwd[2], lex, sg(2));
+    link_terms<3>(A, p, i, nb.fwd[3], lex, sg(3));
 }
 
 hr_status launch(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *af, const void *bf, double beta,

@@ -77,6 +77,7 @@ struct Geom {
     int lrhs;   // log2(nrhs)
     int nblk_g; // 32-site blocks of the gauge (per parity and direction)
     int nblk_s; // 32-virtual-site blocks of a spinor field of one parity
+    int bc;     // antiperiodic directions (bit mu); used where links are packed
     FastDiv div_h3, div_d2, div_d1;
 };
 
@@ -93,6 +94,7 @@ inline Geom make_geom(const hr_lattice &lat, int nrhs)
     g.lrhs = l;
     g.nblk_g = (g.vh + 31) / 32;
     g.nblk_s = (int)(((long long)g.vh * nrhs + 31) / 32);
+    g.bc = lat.bc;
     g.div_h3 = make_fastdiv((unsigned)(g.h3 > 0 ? g.h3 : 1));
     g.div_d2 = make_fastdiv((unsigned)(g.d[2] > 0 ? g.d[2] : 1));
     g.div_d1 = make_fastdiv((unsigned)(g.d[1] > 0 ? g.d[1] : 1));
@@ -734,6 +736,14 @@ __device__ __forceinline__ void store_mat_entry(void *base, int nblk_g, int p, i
 }
 
 // Adjoint link of a unit quaternion: R_bc = (a0^2-|a|^2) d_bc + 2 a_b a_c + 2 a0 eps_bck a_k
+__device__ __forceinline__ bool sign_bit(float x) { return (__float_as_uint(x) >> 31) != 0; }
+__device__ __forceinline__ bool sign_bit(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool sign_bit(const dd &x) { return sign_bit(x.h); }
+
+// R_ab = 1/2 tr(s_a U s_b U^+) = (a0^2 - |a|^2) d_ab + 2 a_a a_b + 2 a0 e_abc a_c,
+// negated when the sign bit of a0 is set: R(q) = R(-q), and the packed
+// adjoint links keep that bit clear except on an antiperiodic boundary slice,
+// where it carries the factor -1 of the boundary condition
 template <class T> __device__ __forceinline__ void quat_to_adj(const T (&a)[4], T (&R)[3][3])
 {
     T w = a[0] * a[0] - (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
@@ -741,6 +751,10 @@ template <class T> __device__ __forceinline__ void quat_to_adj(const T (&a)[4], 
     R[0][0] = w + b1 * a[1]; R[0][1] = b1 * a[2] + c * a[3]; R[0][2] = b1 * a[3] - c * a[2];
     R[1][0] = b2 * a[1] - c * a[3]; R[1][1] = w + b2 * a[2]; R[1][2] = b2 * a[3] + c * a[1];
     R[2][0] = b3 * a[1] + c * a[2]; R[2][1] = b3 * a[2] - c * a[1]; R[2][2] = w + b3 * a[3];
+    if (sign_bit(a[0])) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k / 3][k % 3] = -R[k / 3][k % 3];
+    }
 }
 
 // ---------------------------------------------------------------- colour algebra

@@ -25,6 +25,12 @@ HR_EVEN, HR_ODD, HR_FULL = 0, 1, 2
 HR_OP_HOP, HR_OP_SCHUR, HR_OP_SCHUR_DAG, HR_OP_NORMAL = 0, 1, 2, 3
 HR_SYSTEM_D, HR_SYSTEM_DDAG_D = 0, 1
 
+
+def HR_BC_ANTIPERIODIC(mu: int) -> int:
+    """Bit of ``hr_lattice.bc`` that makes direction mu (0 = time) antiperiodic."""
+    return 1 << int(mu)
+
+
 STATUS_NAMES = {0: "HR_OK", 1: "HR_ERR_INVALID_ARG", 2: "HR_ERR_UNSUPPORTED", 3: "HR_ERR_CUDA",
                 4: "HR_ERR_NOT_CONVERGED", 5: "HR_ERR_NUMERIC", 6: "HR_ERR_TIMEOUT",
                 7: "HR_ERR_WORKSPACE"}
@@ -48,7 +54,23 @@ class HrError(RuntimeError):
 
 
 class hr_lattice(ctypes.Structure):
-    _fields_ = [("dims", ctypes.c_int * 4)]
+    _fields_ = [("dims", ctypes.c_int * 4), ("bc", ctypes.c_int)]
+
+
+class Lattice(tuple):
+    """Extents (T, L1, L2, L3) with fermion boundary conditions: ``bc`` bit mu
+    makes direction mu antiperiodic.  A tuple, so it serves wherever extents do;
+    every call of this module that takes ``dims`` reads ``bc`` from it."""
+
+    def __new__(cls, dims, bc: int = 0):
+        self = super().__new__(cls, (int(d) for d in dims))
+        if len(self) != 4:
+            raise ValueError("four extents")
+        self.bc = int(bc)
+        return self
+
+    def __repr__(self):
+        return f"Lattice({tuple(self)}, bc={self.bc})"
 
 
 class hr_solver_opts(ctypes.Structure):
@@ -133,6 +155,7 @@ def lattice(dims) -> hr_lattice:
     lat = hr_lattice()
     for k in range(4):
         lat.dims[k] = int(dims[k])
+    lat.bc = int(getattr(dims, "bc", 0))
     return lat
 
 

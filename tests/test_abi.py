@@ -62,6 +62,22 @@ def test_invalid_lattices_have_no_size(dims):
     assert hr.hr_gauge_packed_bytes(dims, hr.HR_FUND, hr.HR_F64) == 0
 
 
+def test_boundary_bits():
+    """hr_lattice.bc: one antiperiodic bit per direction; other bits make the lattice invalid."""
+    d = (4, 4, 4, 4)
+    base = hr.hr_gauge_packed_bytes(d, hr.HR_FUND, hr.HR_F64)
+    for bc in (1, 9, 15):
+        lat = hr.Lattice(d, bc)
+        assert lat == d and lat.bc == bc
+        assert hr.lattice(lat).bc == bc
+        assert hr.hr_gauge_packed_bytes(lat, hr.HR_FUND, hr.HR_F64) == base
+    assert hr.HR_BC_ANTIPERIODIC(0) == 1 and hr.HR_BC_ANTIPERIODIC(3) == 8
+    assert hr.lattice(d).bc == 0
+    for bc in (16, -1, 255):
+        assert hr.hr_gauge_packed_bytes(hr.Lattice(d, bc), hr.HR_FUND, hr.HR_F64) == 0
+        assert hr.hr_spinor_packed_bytes(hr.Lattice(d, bc), hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, 1) == 0
+
+
 def test_invalid_enums_and_rhs_have_no_size():
     d = (4, 4, 4, 4)
     assert hr.hr_spinor_packed_bytes(d, 5, hr.HR_F64, hr.HR_EVEN, 1) == 0
