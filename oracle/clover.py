@@ -1,0 +1,217 @@
+"""Clover and exponential-clover site terms of the Wilson-Dirac operator:
+plain numpy, FP64 (test infrastructure, like the rest of ``oracle``).
+
+The paper (arXiv:2411.18511, Sec. 2.2) names the clover improvement
+(Sheikholeslami-Wohlert) and its exponential variant (Francis et al.) as an
+extra site-diagonal term, precomputed per gauge field with its inverse, and
+writes neither down.  The readings here are the textbook ones:
+
+    Q_mn(x)  = the four plaquette leaves of the (mu, nu) plane that start and
+               end at x, each traversed mu-first (counter-clockwise),
+    F_mn(x)  = (Q_mn(x) - Q_mn(x)^+) / 8,
+    s_mn     = (i/2) [g_mu, g_nu],
+    C(x)     = (i/4) sum_{mu != nu} s_mn F_mn(x)     (Hermitian, 4 nc x 4 nc),
+    clover:       A(x) = (4 + m0) + c_sw C(x),
+    exponential:  A(x) = (4 + m0) exp(c_sw C(x) / (4 + m0)),
+
+and the operator with the site term:
+
+    D = A - H/2,   Mhat = A_ee - H_eo A_oo^-1 H_oe / 4,   Mhat^+ = g5 Mhat g5,
+    source bhat = b_e + H_eo A_oo^-1 b_o / 2,   x_o = A_oo^-1 (b_o + H_oe x_e / 2).
+
+Site matrices act on the (spin, colour) index s * nc + c of a spinor
+[V][4][nc].  The gauge loops use the links as given (fermion boundary signs
+cancel around a closed loop); the hops take the ``bc`` of the rest of the
+oracle.  Library routines used as steps: ``numpy.linalg.inv`` for A_oo^-1 and
+``numpy.linalg.eigh`` for the exponential of the Hermitian C.
+
+Pinned in tests/test_oracle_clover.py: the closed form of a constant abelian
+field (F_01 = i sin(B) s_3 on every site), the free field (A = 4 + m0),
+Hermiticity and chirality of A, gauge covariance, and an independent dense
+build (tests/dense_ref.py).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+KIND_SW, KIND_EXP = 0, 1
+
+
+def _gammas():
+    from . import gamma  # the oracle's own table
+
+    return [gamma(mu) for mu in range(4)]
+
+
+def sigma(mu: int, nu: int) -> np.ndarray:
+    """s_mn = (i/2) [g_mu, g_nu] (4 x 4, Hermitian)."""
+    g = _gammas()
+    return 0.5j * (g[mu] @ g[nu] - g[nu] @ g[mu])
+
+
+def _neighbours(dims):
+    """fwd[mu][x] = x + mu-hat and bwd[mu][x] = x - mu-hat (periodic)."""
+    idx = np.arange(int(np.prod(dims))).reshape(dims)
+    fwd = [np.roll(idx, -1, axis=mu).reshape(-1) for mu in range(4)]
+    bwd = [np.roll(idx, 1, axis=mu).reshape(-1) for mu in range(4)]
+    return fwd, bwd
+
+
+def _mm(*ms):
+    out = ms[0]
+    for m in ms[1:]:
+        out = np.einsum("xab,xbc->xac", out, m)
+    return out
+
+
+def _dag(m):
+    return np.conj(np.swapaxes(m, -1, -2))
+
+
+def clover_leaves(dims, L, mu: int, nu: int) -> np.ndarray:
+    """Q_mn(x) for every site: [V, nc, nc]."""
+    fwd, bwd = _neighbours(dims)
+    Um, Un = L[mu], L[nu]
+    f, b = fwd, bwd
+    xpm, xpn = f[mu], f[nu]
+    xmm, xmn = b[mu], b[nu]
+    xmm_pn = f[nu][xmm]       # x - mu + nu
+    xmm_mn = b[nu][xmm]       # x - mu - nu
+    xmn_pm = f[mu][xmn]       # x - nu + mu
+    q = _mm(Um, Un[xpm], _dag(Um[xpn]), _dag(Un))
+    q = q + _mm(Un, _dag(Um[xmm_pn]), _dag(Un[xmm]), Um[xmm])
+    q = q + _mm(_dag(Um[xmm]), _dag(Un[xmm_mn]), Um[xmm_mn], Un[xmn])
+    q = q + _mm(_dag(Un[xmn]), Um[xmn], Un[xmn_pm], _dag(Um))
+    return q
+
+
+def field_strength(dims, L) -> np.ndarray:
+    """F[mu, nu] = (Q_mn - Q_mn^+) / 8, shape [4, 4, V, nc, nc] (zero for mu = nu)."""
+    V, nc = L.shape[1], L.shape[-1]
+    F = np.zeros((4, 4, V, nc, nc), dtype=np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu != nu:
+                Q = clover_leaves(dims, L, mu, nu)
+                F[mu, nu] = (Q - _dag(Q)) / 8.0
+    return F
+
+
+def clover_generator(dims, L) -> np.ndarray:
+    """C(x) = (i/4) sum_{mu != nu} s_mn (x) F_mn(x), shape [V, 4 nc, 4 nc]."""
+    F = field_strength(dims, L)
+    V, nc = L.shape[1], L.shape[-1]
+    C = np.zeros((V, 4, nc, 4, nc), dtype=np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu != nu:
+                C += 0.25j * np.einsum("st,xab->xsatb", sigma(mu, nu), F[mu, nu])
+    return C.reshape(V, 4 * nc, 4 * nc)
+
+
+def site_term(dims, L, m0: float, csw: float, kind: int = KIND_SW) -> np.ndarray:
+    """A(x) for every site, [V, 4 nc, 4 nc]."""
+    C = clover_generator(dims, L)
+    n = C.shape[-1]
+    a = 4.0 + m0
+    if kind == KIND_SW:
+        return a * np.eye(n)[None] + csw * C
+    if kind != KIND_EXP:
+        raise ValueError("kind: KIND_SW or KIND_EXP")
+    # exp of the Hermitian csw C / a from its eigen-decomposition
+    w, U = np.linalg.eigh(csw * C / a)
+    return a * np.einsum("xij,xj,xkj->xik", U, np.exp(w), np.conj(U))
+
+
+def apply_site(A, psi) -> np.ndarray:
+    """(A psi)(x) = A(x) psi(x) for a spinor [V, 4, nc]."""
+    V, _, nc = psi.shape
+    return np.einsum("xij,xj->xi", A, psi.reshape(V, 4 * nc)).reshape(V, 4, nc)
+
+
+def _parity(dims):
+    from . import parity_mask
+
+    return parity_mask(dims)
+
+
+def dirac(dims, L, A, psi, bc=None) -> np.ndarray:
+    """D psi = A psi - H psi / 2 on all sites."""
+    from . import hop
+
+    psi = np.asarray(psi, dtype=np.complex128)
+    return apply_site(A, psi) - 0.5 * hop(dims, L, psi, bc=bc)
+
+
+def schur(dims, L, A, psi, dagger: bool = False, bc=None) -> np.ndarray:
+    """Mhat psi (or Mhat^+ psi) on the even sites of a full-lattice array; odd sites -> 0."""
+    from . import gamma5, hop
+
+    par = _parity(dims)
+    even, odd = par == 0, par == 1
+    inp = np.array(psi, dtype=np.complex128)
+    inp[odd] = 0
+    if dagger:
+        inp = gamma5(inp)
+    t = hop(dims, L, inp, parity=1, bc=bc)           # H_oe in (odd sites)
+    Ainv = np.linalg.inv(A[odd])
+    t[odd] = apply_site(Ainv, t[odd])                 # A_oo^-1 H_oe in
+    u = hop(dims, L, t, parity=0, bc=bc)              # H_eo A_oo^-1 H_oe in
+    out = np.zeros_like(inp)
+    out[even] = apply_site(A[even], inp[even]) - 0.25 * u[even]
+    if dagger:
+        out = gamma5(out)
+    return out
+
+
+def normal(dims, L, A, psi, bc=None) -> np.ndarray:
+    """Mhat^+ Mhat psi on even sites."""
+    return schur(dims, L, A, schur(dims, L, A, psi, bc=bc), dagger=True, bc=bc)
+
+
+def cg(dims, L, A, b, tol: float = 1e-10, maxiter: int = 10000, bc=None):
+    """Hestenes-Stiefel CG on Mhat^+ Mhat x = b (even sites) from x = 0.
+    Returns (x, iters, true_rel_residual, converged)."""
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = b.copy()
+    bb = np.vdot(b, b).real
+    rr = bb
+    it = 0
+    while it < maxiter and np.sqrt(rr / bb) > tol:
+        q = normal(dims, L, A, p, bc=bc)
+        alpha = rr / np.vdot(p, q).real
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    true = np.linalg.norm(b - normal(dims, L, A, x, bc=bc)) / np.sqrt(bb)
+    return x, it, true, bool(np.sqrt(rr / bb) <= tol)
+
+
+def eo_source(dims, L, A, b, bc=None) -> np.ndarray:
+    """bhat_e = b_e - D_eo A_oo^-1 b_o = b_e + H_eo A_oo^-1 b_o / 2; odd sites zero."""
+    from . import hop
+
+    par = _parity(dims)
+    odd = par == 1
+    t = np.zeros_like(np.asarray(b, dtype=np.complex128))
+    t[odd] = apply_site(np.linalg.inv(A[odd]), np.asarray(b, dtype=np.complex128)[odd])
+    out = np.array(b, dtype=np.complex128) + 0.5 * hop(dims, L, t, parity=0, bc=bc)
+    out[odd] = 0
+    return out
+
+
+def eo_reconstruct(dims, L, A, b, xe, bc=None) -> np.ndarray:
+    """x_o = A_oo^-1 (b_o - D_oe x_e) = A_oo^-1 (b_o + H_oe x_e / 2); returns the full x."""
+    from . import hop
+
+    odd = _parity(dims) == 1
+    h = hop(dims, L, np.asarray(xe, dtype=np.complex128), parity=1, bc=bc)
+    x = np.array(xe, dtype=np.complex128)
+    x[odd] = apply_site(np.linalg.inv(A[odd]), np.asarray(b, dtype=np.complex128)[odd] + 0.5 * h[odd])
+    return x

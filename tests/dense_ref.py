@@ -110,3 +110,75 @@ def eo_blocks(dims, nc, M):
     e = np.where(par == 0)[0]
     o = np.where(par == 1)[0]
     return M[np.ix_(e, e)], M[np.ix_(e, o)], M[np.ix_(o, e)], M[np.ix_(o, o)], e, o
+
+
+# ---------------------------------------------------------------- clover term
+
+def sigma_dense(mu, nu) -> np.ndarray:
+    """s_mn = (i/2)(g_mu g_nu - g_nu g_mu)."""
+    return 0.5j * (GAMMA[mu] @ GAMMA[nu] - GAMMA[nu] @ GAMMA[mu])
+
+
+def clover_site_dense(dims, q, nc, m0, csw, exponential=False) -> np.ndarray:
+    """Site matrices A(x) [V, 4 nc, 4 nc], site by site with explicit loops:
+    the four leaves of each plane walked link by link from the explicit link
+    matrices, F = (Q - Q^+)/8, C = (i/4) sum_{mu != nu} s_mn (x) F_mn,
+    A = (4+m0) + csw C, or (4+m0) expm(csw C / (4+m0))."""
+    from scipy.linalg import expm
+
+    V = int(np.prod(dims))
+    U = link_matrices(dims, q, nc)
+    xs = np.indices(dims).reshape(4, -1).T
+    idx = site_index(dims)
+
+    def at(x):
+        return idx[tuple(np.mod(x, dims))]
+
+    def step(x, mu, s):
+        y = np.array(x)
+        y[mu] += s
+        return y
+
+    def link(x, mu, s):
+        """the matrix that transports along one step: +1 U_mu(x), -1 U_mu(x - mu)^+"""
+        if s > 0:
+            return U[mu, at(x)]
+        return U[mu, at(step(x, mu, -1))].conj().T
+
+    def loop(x, path):
+        m = np.eye(nc, dtype=complex)
+        y = np.array(x)
+        for mu, s in path:
+            m = m @ link(y, mu, s)
+            y = step(y, mu, s)
+        assert np.all(np.mod(y, dims) == np.mod(x, dims))
+        return m
+
+    A = np.zeros((V, 4 * nc, 4 * nc), dtype=complex)
+    a = 4.0 + m0
+    for k in range(V):
+        x = xs[k]
+        C = np.zeros((4 * nc, 4 * nc), dtype=complex)
+        for mu in range(4):
+            for nu in range(4):
+                if mu == nu:
+                    continue
+                Q = (loop(x, [(mu, 1), (nu, 1), (mu, -1), (nu, -1)])
+                     + loop(x, [(nu, 1), (mu, -1), (nu, -1), (mu, 1)])
+                     + loop(x, [(mu, -1), (nu, -1), (mu, 1), (nu, 1)])
+                     + loop(x, [(nu, -1), (mu, 1), (nu, 1), (mu, -1)]))
+                F = (Q - Q.conj().T) / 8.0
+                C += 0.25j * np.kron(sigma_dense(mu, nu), F)
+        A[k] = expm(csw * C / a) * a if exponential else a * np.eye(4 * nc) + csw * C
+    return A
+
+
+def dirac_clover_dense(dims, q, nc, A, bc=0) -> np.ndarray:
+    """Dense D = A - H/2 with the site matrices A on the diagonal blocks."""
+    V = int(np.prod(dims))
+    n = V * 4 * nc
+    D = -0.5 * hopping_dense(dims, q, nc, bc)
+    for x in range(V):
+        s = slice(x * 4 * nc, (x + 1) * 4 * nc)
+        D[s, s] += A[x]
+    return D
