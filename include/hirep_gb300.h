@@ -237,6 +237,78 @@ hr_status hr_solve_full(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, cons
                         hr_system system, const void *gauge, const void *b, void *x, hr_solve_info *info,
                         void *work, size_t work_bytes, hr_stream stream);
 
+/* ---------------------------------------------------------------------- */
+/* clover and exponential-clover site terms (Sec. 2.2)                      */
+/* ---------------------------------------------------------------------- */
+
+/* Sec. 2.2 adds the site-diagonal clover term (Sheikholeslami-Wohlert) or its
+ * exponential form (Francis et al.) and precomputes it, with its inverse, once
+ * per gauge field; it states no formula.  With Q_mn(x) the four plaquette
+ * leaves of the (mu, nu) plane at x (mu-first), F_mn = (Q_mn - Q_mn^+)/8,
+ * s_mn = (i/2)[g_mu, g_nu] and C = (i/4) sum_{mu != nu} s_mn F_mn:
+ *   HR_CLOVER_SW:  A(x) = (4 + m0) + c_sw C(x)
+ *   HR_CLOVER_EXP: A(x) = (4 + m0) exp(c_sw C(x) / (4 + m0))
+ * and the operator is D = A - H/2, its Schur form on even sites
+ * Mhat = A_ee - H_eo A_oo^-1 H_oe / 4, Mhat^+ = g5 Mhat g5.  m0 and c_sw are
+ * baked into the packed field: the *_clover calls take no m0. */
+typedef enum { HR_CLOVER_SW = 0, HR_CLOVER_EXP = 1 } hr_clover_kind;
+
+/* Bytes of a packed clover field: A and A^-1 on both parities, two Hermitian
+ * (2 nc) x (2 nc) blocks per site (chiral halves), HR_F64 (double-float pairs)
+ * or HR_F32; 0 for HR_F16 or an invalid lattice.  The FP16 operators use the
+ * HR_F32 field.  HR_ADJ and HR_ADJ_MAT share the adjoint layout. */
+size_t hr_clover_packed_bytes(hr_lattice lat, hr_rep rep, hr_prec prec);
+
+/* Build the packed clover field of `rep` from the canonical gauge (device,
+ * double[4][V][4], the links as they are: boundary signs cancel around the
+ * leaves) in FP64 arithmetic on the GPU.  HR_CLOVER_SW inverts each block by
+ * Gauss-Jordan elimination (HR_ERR_NUMERIC if one is singular);
+ * HR_CLOVER_EXP takes the exponential and its inverse exp(-...) by scaling
+ * and squaring.  Synchronises the stream (it reads the singularity flag). */
+hr_status hr_clover_build(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_clover_kind kind,
+                          double m0, double c_sw, const double *canonical, void *clover, hr_stream stream);
+
+/* out = A in (inverse = 0) or A^-1 in (inverse != 0) on the sites of
+ * `parity` (HR_EVEN / HR_ODD): packed spinors of precision prec with n_rhs
+ * right-hand sides; clover: the packed field in the clover precision of prec
+ * (HR_F64 for HR_F64, HR_F32 otherwise).  in may equal out. */
+hr_status hr_clover_apply(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity parity, int inverse,
+                          int n_rhs, const void *clover, const void *in, void *out, hr_stream stream);
+
+/* out = D in = A in - H in / 2 on all sites (HR_FULL packed spinors): two hop
+ * launches with A applied to the local term in their epilogue. */
+hr_status hr_dirac_apply_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, const void *gauge,
+                                const void *clover, const void *in, void *out, hr_stream stream);
+
+/* hr_dirac_eo with the clover site term: HR_OP_SCHUR, HR_OP_SCHUR_DAG and
+ * HR_OP_NORMAL apply Mhat = A_ee - H_eo A_oo^-1 H_oe / 4 (A_oo^-1 in the first
+ * hop's epilogue, A_ee in the second's); HR_OP_HOP is the plain hop.  Work
+ * bytes as hr_dirac_workspace_bytes. */
+hr_status hr_dirac_eo_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity out_parity,
+                             hr_op op, int n_rhs, const void *gauge, const void *clover, const void *in,
+                             void *out, void *work, size_t work_bytes, hr_stream stream);
+
+/* Work bytes of hr_cg_solve_clover (the mixed solvers keep an HR_F32 copy of
+ * the clover field in it). */
+size_t hr_cg_clover_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *opts);
+
+/* hr_cg_solve on Mhat^+ Mhat with the clover site term; clover: the packed
+ * HR_F64 field (hr_clover_build).  Same options, errors and info. */
+hr_status hr_cg_solve_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const hr_solver_opts *opts,
+                             const void *gauge, const void *clover, const void *b, void *x, hr_solve_info *info,
+                             void *work, size_t work_bytes, hr_stream stream);
+
+/* Work bytes of hr_solve_full_clover. */
+size_t hr_solve_full_clover_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *opts,
+                                            hr_system system);
+
+/* hr_solve_full with the clover site term: bhat = b_e + H_eo A_oo^-1 b_o / 2,
+ * Mhat x_e = bhat by hr_cg_solve_clover, x_o = A_oo^-1 (b_o + H_oe x_e / 2);
+ * D^+ D = g5 D g5 D as for the Wilson operator.  clover: packed HR_F64 field. */
+hr_status hr_solve_full_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const hr_solver_opts *opts,
+                               hr_system system, const void *gauge, const void *clover, const void *b, void *x,
+                               hr_solve_info *info, void *work, size_t work_bytes, hr_stream stream);
+
 /* Work bytes of hr_cg_solve_batch for these lattices (0 if invalid). */
 size_t hr_cg_batch_workspace_bytes(int n_lat, const hr_lattice *lats, hr_rep rep);
 

@@ -117,6 +117,7 @@ struct Solver {
     int rep;
     hr_solver_opts o;
     const void *gauge;
+    const void *clov64;  // packed FP64 clover field, or nullptr (Wilson)
     const void *b;
     void *x;
     cudaStream_t s;
@@ -124,11 +125,12 @@ struct Solver {
     void *r64, *p64, *q64, *u64, *t64;
     // low precision buffers
     void *gauge_lo, *r_lo, *p_lo, *q_lo, *u_lo, *t_lo, *x_lo;
+    void *clov_lo; // FP32 copy of the clover field (mixed solvers)
     size_t h64, hlo, h32, glo;
 
     bool mixed() const { return o.inner_prec != HR_F64; }
 
-    static size_t layout(const Geom &g, int rep, const hr_solver_opts &o, Solver *sv, void *work)
+    static size_t layout(const Geom &g, int rep, const hr_solver_opts &o, bool clover, Solver *sv, void *work)
     {
         size_t h64 = spinor_half_bytes(g, rep, kF64);
         char *w = (char *)work;
@@ -152,7 +154,9 @@ struct Solver {
             void *r = take(h64), *q = take(h64), *u = take(h64), *t = take(h64);
             void *gl = take(glo), *rl = take(hlo), *pl = take(hlo), *ql = take(hlo), *ul = take(hlo), *tl = take(hlo);
             void *xl = take(h32);
+            void *cl = clover ? take(4 * clover_half_bytes(g, rep, kF32)) : nullptr;
             if (sv) {
+                sv->clov_lo = cl;
                 sv->r64 = r; sv->q64 = q; sv->u64 = u; sv->t64 = t; sv->p64 = nullptr;
                 sv->gauge_lo = gl; sv->r_lo = rl; sv->p_lo = pl; sv->q_lo = ql; sv->u_lo = ul; sv->t_lo = tl;
                 sv->x_lo = xl;
@@ -165,7 +169,8 @@ struct Solver {
     // ax = A v in FP64 (gated launches skip unless *gate != 0)
     hr_status apply64(const void *v, void *ax, int fin, const double *gate, const double *done)
     {
-        return apply_eo_op(ctx, g, m0, rep, kF64, HR_OP_NORMAL, gauge, v, ax, t64, u64, fin, gate, done, s);
+        return apply_eo_op(ctx, g, m0, rep, kF64, HR_OP_NORMAL, gauge, v, ax, t64, u64, fin, gate, done, s, nullptr,
+                           clov64);
     }
 
     // One iteration = part_a (q = A p with <p,q> -> alpha; x, r update with
@@ -179,17 +184,17 @@ struct Solver {
             // q = A p with the x/r update and |r|^2 fused into the last hop
             const CgFuse fz{x, p64, r64, kFinBeta};
             return apply_eo_op(ctx, g, m0, rep, kF64, HR_OP_NORMAL, gauge, p64, q64, t64, u64, kFinAlpha, nullptr,
-                               done, s, &fz);
+                               done, s, &fz, clov64);
         }
         const int P = o.inner_prec;
         if (P == kF32) {
             // x_lo, p, r are all FP32: fused as above
             const CgFuse fz{x_lo, p_lo, r_lo, kFinBetaMixed};
             return apply_eo_op(ctx, g, m0, rep, P, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha,
-                               nullptr, done, s, &fz);
+                               nullptr, done, s, &fz, clov_lo);
         }
         st = apply_eo_op(ctx, g, m0, rep, P, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha, nullptr,
-                         done, s);
+                         done, s, nullptr, clov_lo);
         if (!st) st = blas_xr(ctx, g, rep, kF32, P, P, P, x_lo, p_lo, r_lo, q_lo, s);
         return st;
     }
@@ -234,6 +239,7 @@ struct Solver {
         if (st) return st;
         if (mixed()) {
             st = gauge_convert(ctx, make_geom_gauge(), rep, o.inner_prec, gauge, gauge_lo, s);
+            if (!st && clov64) st = clover_convert_f32(ctx, g, rep, clov64, clov_lo, s);
             if (st) return st;
         }
         st = blas_norm2(ctx, g, rep, kF64, b, kFinBB, s);
@@ -375,17 +381,22 @@ hr_solver_opts hr_solver_default_opts(void)
     return o;
 }
 
-size_t hr_cg_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *opts)
+} // extern "C"
+
+namespace {
+
+size_t cg_workspace(hr_lattice lat, hr_rep rep, const hr_solver_opts *opts, bool clover)
 {
     if (!opts || !valid_rep(rep) || !valid_prec(opts->inner_prec) || opts->n_rhs < 1 || opts->n_rhs > kMaxRhs)
         return 0;
     if (hr_spinor_packed_bytes(lat, rep, HR_F64, HR_EVEN, opts->n_rhs) == 0) return 0;
-    return Solver::layout(make_geom(lat, opts->n_rhs), rep, *opts, nullptr, nullptr);
+    return Solver::layout(make_geom(lat, opts->n_rhs), rep, *opts, clover, nullptr, nullptr);
 }
 
-hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_solver_opts *opts,
-                      const void *gauge, const void *b, void *x, hr_solve_info *info, void *work, size_t work_bytes,
-                      hr_stream stream)
+// the CG of hr_cg_solve and hr_cg_solve_clover (clover == nullptr: Wilson, m0 used)
+hr_status cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_solver_opts *opts, const void *gauge,
+                   const void *clover, const void *b, void *x, hr_solve_info *info, void *work, size_t work_bytes,
+                   hr_stream stream)
 {
     if (!ctx) return HR_ERR_INVALID_ARG;
     if (info) std::memset(info, 0, sizeof *info);
@@ -397,11 +408,11 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
         return set_error(ctx, HR_ERR_INVALID_ARG, "reliable_delta must lie in (0, 1)");
     hr_status st = validate_lattice(ctx, lat, opts->n_rhs);
     if (st) return st;
-    st = check_buffers(ctx, {gauge, b, x}, {}, {work});
+    st = check_buffers(ctx, {gauge, b, x}, {}, {work, clover});
     if (st) return st;
     if (b == x) return set_error(ctx, HR_ERR_INVALID_ARG, "b and x must not alias");
-    if (!(4.0 + m0 != 0.0)) return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero");
-    size_t need = hr_cg_workspace_bytes(lat, rep, opts);
+    if (!clover && !(4.0 + m0 != 0.0)) return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero");
+    size_t need = cg_workspace(lat, rep, opts, clover != nullptr);
     if (!work || work_bytes < need)
         return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, work_bytes);
 
@@ -412,10 +423,11 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
     sv.rep = rep;
     sv.o = *opts;
     sv.gauge = gauge;
+    sv.clov64 = clover;
     sv.b = b;
     sv.x = x;
     sv.s = (cudaStream_t)stream;
-    Solver::layout(sv.g, rep, *opts, &sv, work);
+    Solver::layout(sv.g, rep, *opts, clover != nullptr, &sv, work);
     cudaStream_t s = sv.s;
 
     cudaError_t e = cudaEventRecord(ctx->ev0, s);
@@ -436,10 +448,10 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
         HopChoice c64 = hop_choice(ctx, sv.g, rep, kF64), clo = hop_choice(ctx, sv.g, rep, opts->inner_prec);
         unsigned long long m0bits;
         std::memcpy(&m0bits, &m0, sizeof m0bits);
-        snprintf(keybuf, sizeof keybuf, "cg:%d:%d:%d:%d:%d:%d:%d:%llx:%d:%d:%d:%p:%p:%p:%p:%d.%d:%d.%d:%zu",
+        snprintf(keybuf, sizeof keybuf, "cg:%d:%d:%d:%d:%d:%d:%d:%llx:%d:%d:%d:%p:%p:%p:%p:%p:%d.%d:%d.%d:%zu",
                  lat.dims[0], lat.dims[1], lat.dims[2], lat.dims[3], sv.g.nrhs, rep, opts->inner_prec, m0bits,
                  device_loop ? -chunk : chunk,
-                 opts->maxiter, (int)sizeof(void *), gauge, b, x, work, c64.variant, c64.block, clo.variant,
+                 opts->maxiter, (int)sizeof(void *), gauge, clover, b, x, work, c64.variant, c64.block, clo.variant,
                  clo.block, work_bytes);
     }
     cudaGraphExec_t exec = nullptr;
@@ -550,6 +562,37 @@ hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const 
     if (!converged)
         return set_error(ctx, HR_ERR_NOT_CONVERGED, "not converged: |b-Ax|/|b| = %.3e after %d iterations", worst, iters);
     return HR_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+size_t hr_cg_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *opts)
+{
+    return cg_workspace(lat, rep, opts, false);
+}
+
+size_t hr_cg_clover_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *opts)
+{
+    return cg_workspace(lat, rep, opts, true);
+}
+
+hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_solver_opts *opts,
+                      const void *gauge, const void *b, void *x, hr_solve_info *info, void *work, size_t work_bytes,
+                      hr_stream stream)
+{
+    return cg_solve(ctx, lat, m0, rep, opts, gauge, nullptr, b, x, info, work, work_bytes, stream);
+}
+
+hr_status hr_cg_solve_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const hr_solver_opts *opts, const void *gauge,
+                             const void *clover, const void *b, void *x, hr_solve_info *info, void *work,
+                             size_t work_bytes, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (info) std::memset(info, 0, sizeof *info);
+    if (!clover) return set_error(ctx, HR_ERR_INVALID_ARG, "null clover field");
+    return cg_solve(ctx, lat, 0.0, rep, opts, gauge, clover, b, x, info, work, work_bytes, stream);
 }
 
 } // extern "C"

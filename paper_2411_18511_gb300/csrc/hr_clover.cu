@@ -1,0 +1,554 @@
+// hr_clover.cu -- the clover and exponential-clover site terms
+// (arXiv:2411.18511 Sec. 2.2): building the packed field once per gauge field
+// (A and A^-1, or (4+m0) exp(+-c_sw C/(4+m0)), on both parities), converting it
+// to FP32 for the mixed-precision operators, applying it on one parity, and
+// the full and even-odd operators with the site term.  The products inside the
+// hop (A_ee on the aux term, A_oo^-1 on the result) run in the hop epilogue
+// (hr_hop_dev.cuh), so every hop kernel variant carries them.
+//
+// Build (native FP64: a precomputation, not the hot path).  Per site x:
+//   Q_mn   the four leaves of the (mu, nu) plane from x, mu-first,
+//   F_mn = (Q_mn - Q_mn^+) / 8, B_l = e_jkl F_jk / 2 (B_1 = F_23, B_2 = F_31, B_3 = F_12),
+//   in the chiral basis s_0k = diag(-s_k, s_k) and s_jk = -e_jkl diag(s_l, s_l), so
+//   C = (i/4) sum s_mn F_mn = diag(C+, C-),
+//   C+ = sum_l s_l (x) (-(i/2)(F_0l + B_l)),   C- = sum_l s_l (x) ((i/2)(F_0l - B_l)),
+//   clover:      A = (4+m0) + c_sw C,            A^-1 by Gauss-Jordan elimination,
+//   exponential: A = (4+m0) exp(c_sw C/(4+m0)),  A^-1 = exp(-c_sw C/(4+m0)) / (4+m0),
+// the exponential by scaling and squaring of a degree-16 Taylor polynomial
+// (the argument is scaled below 1/2 in the 1-norm: truncation < 1e-19).
+// Storing the explicit inverse instead of LDL factors: the same n^2 reals, and
+// a matrix-vector product has no sequential dependency chain.
+#include <cmath>
+
+#include "hr_clover.cuh"
+#include "hr_host.h"
+
+using namespace hr;
+
+namespace {
+
+struct zc {
+    double re, im;
+};
+__device__ __forceinline__ zc zadd(zc a, zc b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ zc zsub(zc a, zc b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ zc zmul(zc a, zc b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ zc zconj(zc a) { return {a.re, -a.im}; }
+__device__ __forceinline__ zc zscale(double s, zc a) { return {s * a.re, s * a.im}; }
+
+template <int NC> struct CM {
+    zc m[NC][NC];
+};
+
+// U_mu(x) as a colour matrix from the canonical quaternion (fundamental
+// 2x2, or the real adjoint R_ab = 1/2 tr(s_a U s_b U^+))
+template <int NC> __device__ CM<NC> link_mat(const double *can, long long V, int mu, long long x)
+{
+    const double *q = can + ((long long)mu * V + x) * 4;
+    const double a0 = q[0], a1 = q[1], a2 = q[2], a3 = q[3];
+    CM<NC> U;
+    if constexpr (NC == 2) {
+        U.m[0][0] = {a0, a3};
+        U.m[0][1] = {a2, a1};
+        U.m[1][0] = {-a2, a1};
+        U.m[1][1] = {a0, -a3};
+    } else {
+        const double w = a0 * a0 - (a1 * a1 + a2 * a2 + a3 * a3);
+        const double a[3] = {a1, a2, a3};
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) U.m[r][c] = {2.0 * a[r] * a[c] + (r == c ? w : 0.0), 0.0};
+        U.m[0][1].re += 2.0 * a0 * a3;
+        U.m[0][2].re -= 2.0 * a0 * a2;
+        U.m[1][0].re -= 2.0 * a0 * a3;
+        U.m[1][2].re += 2.0 * a0 * a1;
+        U.m[2][0].re += 2.0 * a0 * a2;
+        U.m[2][1].re -= 2.0 * a0 * a1;
+    }
+    return U;
+}
+
+// A B, with either factor optionally daggered
+template <int NC> __device__ CM<NC> cmul(const CM<NC> &A, bool da, const CM<NC> &B, bool db)
+{
+    CM<NC> C;
+    for (int r = 0; r < NC; ++r)
+        for (int c = 0; c < NC; ++c) {
+            zc s = {0.0, 0.0};
+            for (int k = 0; k < NC; ++k) {
+                const zc a = da ? zconj(A.m[k][r]) : A.m[r][k];
+                const zc b = db ? zconj(B.m[c][k]) : B.m[k][c];
+                s = zadd(s, zmul(a, b));
+            }
+            C.m[r][c] = s;
+        }
+    return C;
+}
+
+__device__ long long lex_of(const Geom &g, const int (&x)[4])
+{
+    return (((long long)x[0] * g.d[1] + x[1]) * g.d[2] + x[2]) * g.d[3] + x[3];
+}
+// the site x + s1 m1 + s2 m2 (periodic; s = 0 leaves a direction alone)
+__device__ long long nb(const Geom &g, const int (&x)[4], int m1, int s1, int m2 = 0, int s2 = 0)
+{
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    y[m1] = (y[m1] + s1 + g.d[m1]) % g.d[m1];
+    y[m2] = (y[m2] + s2 + g.d[m2]) % g.d[m2];
+    return lex_of(g, y);
+}
+
+// F_mn(x) = (Q_mn - Q_mn^+)/8 from the four leaves that start at x
+template <int NC> __device__ CM<NC> field_strength(const Geom &g, const double *can, const int (&x)[4], int mu, int nu)
+{
+    const long long V = 2LL * g.vh;
+    const long long x0 = lex_of(g, x);
+    const long long xpm = nb(g, x, mu, 1), xpn = nb(g, x, nu, 1), xmm = nb(g, x, mu, -1), xmn = nb(g, x, nu, -1);
+    const long long xmm_pn = nb(g, x, mu, -1, nu, 1), xmm_mn = nb(g, x, mu, -1, nu, -1), xmn_pm = nb(g, x, nu, -1, mu, 1);
+    auto U = [&](int d, long long s) { return link_mat<NC>(can, V, d, s); };
+    // U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    CM<NC> Q = cmul(cmul(U(mu, x0), false, U(nu, xpm), false), false, cmul(U(nu, x0), false, U(mu, xpn), false), true);
+    // U_nu(x) U_mu(x-mu+nu)^+ U_nu(x-mu)^+ U_mu(x-mu)
+    CM<NC> t = cmul(cmul(U(nu, x0), false, U(mu, xmm_pn), true), false, cmul(U(nu, xmm), true, U(mu, xmm), false), false);
+    for (int r = 0; r < NC; ++r)
+        for (int c = 0; c < NC; ++c) Q.m[r][c] = zadd(Q.m[r][c], t.m[r][c]);
+    // U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
+    t = cmul(cmul(U(nu, xmm_mn), false, U(mu, xmm), false), true, cmul(U(mu, xmm_mn), false, U(nu, xmn), false), false);
+    for (int r = 0; r < NC; ++r)
+        for (int c = 0; c < NC; ++c) Q.m[r][c] = zadd(Q.m[r][c], t.m[r][c]);
+    // U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
+    t = cmul(cmul(U(nu, xmn), true, U(mu, xmn), false), false, cmul(U(mu, x0), false, U(nu, xmn_pm), true), true);
+    for (int r = 0; r < NC; ++r)
+        for (int c = 0; c < NC; ++c) Q.m[r][c] = zadd(Q.m[r][c], t.m[r][c]);
+    CM<NC> F;
+    for (int r = 0; r < NC; ++r)
+        for (int c = 0; c < NC; ++c) F.m[r][c] = zscale(0.125, zsub(Q.m[r][c], zconj(Q.m[c][r])));
+    return F;
+}
+
+template <int N> struct ZM {
+    zc m[N][N];
+};
+
+template <int N> __device__ ZM<N> zmm(const ZM<N> &A, const ZM<N> &B)
+{
+    ZM<N> C;
+#pragma unroll 1
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) {
+            zc s = {0.0, 0.0};
+            for (int k = 0; k < N; ++k) s = zadd(s, zmul(A.m[r][k], B.m[k][c]));
+            C.m[r][c] = s;
+        }
+    return C;
+}
+
+// exp(X) by scaling and squaring of the degree-16 Taylor polynomial
+template <int N> __device__ ZM<N> expm(ZM<N> X)
+{
+    double nrm = 0.0;
+    for (int c = 0; c < N; ++c) {
+        double s = 0.0;
+        for (int r = 0; r < N; ++r) s += hypot(X.m[r][c].re, X.m[r][c].im);
+        nrm = fmax(nrm, s);
+    }
+    int sq = 0;
+    while (nrm > 0.5 && sq < 60) {
+        nrm *= 0.5;
+        ++sq;
+    }
+    const double sc = ldexp(1.0, -sq);
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) X.m[r][c] = zscale(sc, X.m[r][c]);
+    // Horner: E = 1 + X (1 + X/2 (1 + X/3 (... (1 + X/16))))
+    ZM<N> E;
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) E.m[r][c] = {r == c ? 1.0 : 0.0, 0.0};
+#pragma unroll 1
+    for (int k = 16; k >= 1; --k) {
+        ZM<N> T = zmm(X, E);
+        for (int r = 0; r < N; ++r)
+            for (int c = 0; c < N; ++c) E.m[r][c] = zadd(zscale(1.0 / k, T.m[r][c]), {r == c ? 1.0 : 0.0, 0.0});
+    }
+#pragma unroll 1
+    for (int k = 0; k < sq; ++k) E = zmm(E, E);
+    return E;
+}
+
+// A^-1 by Gauss-Jordan elimination with partial pivoting (false if singular)
+template <int N> __device__ bool inverse(ZM<N> A, ZM<N> &I)
+{
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) I.m[r][c] = {r == c ? 1.0 : 0.0, 0.0};
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+        int piv = k;
+        double best = -1.0;
+        for (int r = k; r < N; ++r) {
+            const double m = A.m[r][k].re * A.m[r][k].re + A.m[r][k].im * A.m[r][k].im;
+            if (m > best) {
+                best = m;
+                piv = r;
+            }
+        }
+        if (!(best > 0.0)) return false;
+        if (piv != k)
+            for (int c = 0; c < N; ++c) {
+                zc t = A.m[k][c];
+                A.m[k][c] = A.m[piv][c];
+                A.m[piv][c] = t;
+                t = I.m[k][c];
+                I.m[k][c] = I.m[piv][c];
+                I.m[piv][c] = t;
+            }
+        const zc p = A.m[k][k];
+        const double pn = p.re * p.re + p.im * p.im;
+        const zc pinv = {p.re / pn, -p.im / pn};
+        for (int c = 0; c < N; ++c) {
+            A.m[k][c] = zmul(A.m[k][c], pinv);
+            I.m[k][c] = zmul(I.m[k][c], pinv);
+        }
+        for (int r = 0; r < N; ++r) {
+            if (r == k) continue;
+            const zc f = A.m[r][k];
+            for (int c = 0; c < N; ++c) {
+                A.m[r][c] = zsub(A.m[r][c], zmul(f, A.m[k][c]));
+                I.m[r][c] = zsub(I.m[r][c], zmul(f, I.m[k][c]));
+            }
+        }
+    }
+    return true;
+}
+
+// the n^2 reals of a Hermitian block (diagonal, then the upper triangle as re, im)
+template <int N> __device__ void block_reals(const ZM<N> &M, double *out)
+{
+    int r = 0;
+    for (int k = 0; k < N; ++k) out[r++] = M.m[k][k].re;
+    for (int p = 0; p < N; ++p)
+        for (int q = p + 1; q < N; ++q) {
+            out[r++] = M.m[p][q].re;
+            out[r++] = M.m[p][q].im;
+        }
+}
+
+template <int NC, int CP> __device__ void store_site(void *half, int i, const double *reals)
+{
+    using L = CloverLayout<NC, CP>;
+    float4 *base = (float4 *)half;
+#pragma unroll 1
+    for (int v = 0; v < L::NVEC; ++v) {
+        float4 w;
+        if constexpr (CP == kF64) {
+            const double a = reals[2 * v], b = reals[2 * v + 1];
+            const float ah = (float)a, bh = (float)b;
+            w = make_float4(ah, (float)(a - (double)ah), bh, (float)(b - (double)bh));
+        } else {
+            w = make_float4((float)reals[4 * v], (float)reals[4 * v + 1], (float)reals[4 * v + 2],
+                            (float)reals[4 * v + 3]);
+        }
+        base[((size_t)(i >> 5) * L::NVEC + v) * 32 + (i & 31)] = w;
+    }
+}
+
+struct BuildArgs {
+    Geom g;
+    const double *can;
+    double m0, csw;
+    int kind;
+    void *half[4]; // A even, A odd, A^-1 even, A^-1 odd
+    unsigned *bad; // set when an A is singular
+};
+
+// one thread per lexicographic site
+template <int NC, int CP> __global__ void __launch_bounds__(64) k_clover_build(BuildArgs B)
+{
+    constexpr int N = 2 * NC;
+    const Geom &g = B.g;
+    const long long V = 2LL * g.vh;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= V) return;
+    int x[4];
+    long long r = t;
+    for (int k = 3; k >= 0; --k) {
+        x[k] = (int)(r % g.d[k]);
+        r /= g.d[k];
+    }
+    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const int i = (int)(t >> 1);
+    // F_mn for the six planes
+    CM<NC> F01 = field_strength<NC>(g, B.can, x, 0, 1), F02 = field_strength<NC>(g, B.can, x, 0, 2),
+           F03 = field_strength<NC>(g, B.can, x, 0, 3), F12 = field_strength<NC>(g, B.can, x, 1, 2),
+           F13 = field_strength<NC>(g, B.can, x, 1, 3), F23 = field_strength<NC>(g, B.can, x, 2, 3);
+    const CM<NC> *E[3] = {&F01, &F02, &F03};
+    const double a = 4.0 + B.m0;
+    double reals[2][2 * N * N]; // [forward / inverse][both blocks]
+#pragma unroll 1
+    for (int b = 0; b < 2; ++b) {
+        // G_l = -(i/2)(F_0l + B_l) (upper block) or (i/2)(F_0l - B_l) (lower)
+        ZM<N> C;
+        for (int rr = 0; rr < N; ++rr)
+            for (int cc = 0; cc < N; ++cc) C.m[rr][cc] = {0.0, 0.0};
+        for (int l = 0; l < 3; ++l) {
+            const CM<NC> &Bm = l == 0 ? F23 : l == 1 ? F13 : F12;
+            const double sB = l == 1 ? -1.0 : 1.0; // B_2 = F_31 = -F_13
+            for (int c = 0; c < NC; ++c)
+                for (int d = 0; d < NC; ++d) {
+                    const zc f = E[l]->m[c][d], bb = zscale(sB, Bm.m[c][d]);
+                    const zc s = b == 0 ? zadd(f, bb) : zsub(f, bb);
+                    // times -(i/2) or +(i/2)
+                    const double h = b == 0 ? -0.5 : 0.5;
+                    const zc G = {-h * s.im, h * s.re};
+                    // s_l (x) G: s_1 = [[0,1],[1,0]], s_2 = [[0,-i],[i,0]], s_3 = diag(1,-1)
+                    if (l == 0) {
+                        C.m[c][NC + d] = zadd(C.m[c][NC + d], G);
+                        C.m[NC + c][d] = zadd(C.m[NC + c][d], G);
+                    } else if (l == 1) {
+                        C.m[c][NC + d] = zadd(C.m[c][NC + d], {G.im, -G.re});  // -i G
+                        C.m[NC + c][d] = zadd(C.m[NC + c][d], {-G.im, G.re});  // +i G
+                    } else {
+                        C.m[c][d] = zadd(C.m[c][d], G);
+                        C.m[NC + c][NC + d] = zsub(C.m[NC + c][NC + d], G);
+                    }
+                }
+        }
+        ZM<N> A, Ai;
+        if (B.kind == HR_CLOVER_EXP) {
+            ZM<N> X = C, Y = C;
+            for (int rr = 0; rr < N; ++rr)
+                for (int cc = 0; cc < N; ++cc) {
+                    X.m[rr][cc] = zscale(B.csw / a, C.m[rr][cc]);
+                    Y.m[rr][cc] = zscale(-B.csw / a, C.m[rr][cc]);
+                }
+            A = expm(X);
+            Ai = expm(Y);
+            for (int rr = 0; rr < N; ++rr)
+                for (int cc = 0; cc < N; ++cc) {
+                    A.m[rr][cc] = zscale(a, A.m[rr][cc]);
+                    Ai.m[rr][cc] = zscale(1.0 / a, Ai.m[rr][cc]);
+                }
+        } else {
+            for (int rr = 0; rr < N; ++rr)
+                for (int cc = 0; cc < N; ++cc)
+                    A.m[rr][cc] = zadd(zscale(B.csw, C.m[rr][cc]), {rr == cc ? a : 0.0, 0.0});
+            if (!inverse(A, Ai)) atomicExch(B.bad, 1u);
+        }
+        block_reals(A, &reals[0][b * N * N]);
+        block_reals(Ai, &reals[1][b * N * N]);
+    }
+    store_site<NC, CP>(B.half[p], i, reals[0]);
+    store_site<NC, CP>(B.half[2 + p], i, reals[1]);
+}
+
+// FP64 -> FP32 field, one thread per FP32 vector
+template <int NC> __global__ void k_clover_to_f32(int nvec_total, const float4 *src, float4 *dst)
+{
+    using L64 = CloverLayout<NC, kF64>;
+    using L32 = CloverLayout<NC, kF32>;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nvec_total) return;
+    const int lane = t & 31, v = (t >> 5) % L32::NVEC, blk = (t >> 5) / L32::NVEC;
+    const float4 a = src[((size_t)blk * L64::NVEC + 2 * v) * 32 + lane];
+    const float4 b = src[((size_t)blk * L64::NVEC + 2 * v + 1) * 32 + lane];
+    dst[((size_t)blk * L32::NVEC + v) * 32 + lane] = make_float4(a.x + a.y, a.z + a.w, b.x + b.y, b.z + b.w);
+}
+
+// out = A in (or A^-1 in) on the sites of one parity (every right-hand side)
+template <int NC, int PREC> __global__ void k_clover_apply(Geom g, const void *half, const void *in, void *out)
+{
+    using T = typename PrecTraits<PREC>::T;
+    const int nv = g.vh << g.lrhs;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<T> v[4][NC];
+        load_spinor<NC, PREC>(in, g.nblk_s, j, v);
+        clover_apply<clover_prec(PREC)>(half, j >> g.lrhs, v);
+        store_spinor<NC, PREC>(out, g.nblk_s, j, v);
+    }
+}
+
+bool valid_clover_prec(int prec) { return prec == kF64 || prec == kF32; }
+
+} // namespace
+
+namespace hr {
+
+size_t clover_half_bytes(const Geom &g, int rep, int cp)
+{
+    if (rep_nc(rep) == 2) return cp == kF64 ? CloverLayout<2, kF64>::half_bytes(g.nblk_g) : CloverLayout<2, kF32>::half_bytes(g.nblk_g);
+    return cp == kF64 ? CloverLayout<3, kF64>::half_bytes(g.nblk_g) : CloverLayout<3, kF32>::half_bytes(g.nblk_g);
+}
+
+const void *clover_half(const void *base, const Geom &g, int rep, int cp, bool inverse, int parity)
+{
+    if (!base) return nullptr;
+    return (const char *)base + (size_t)((inverse ? 2 : 0) + parity) * clover_half_bytes(g, rep, cp);
+}
+
+hr_status clover_convert_f32(hr_ctx *ctx, const Geom &g, int rep, const void *src, void *dst, cudaStream_t s)
+{
+    const int nc = rep_nc(rep);
+    const size_t h64 = clover_half_bytes(g, rep, kF64), h32 = clover_half_bytes(g, rep, kF32);
+    const int nvec = g.nblk_g * 32 * (nc == 2 ? CloverLayout<2, kF32>::NVEC : CloverLayout<3, kF32>::NVEC);
+    const int bs = 256, grid = (nvec + bs - 1) / bs;
+    for (int h = 0; h < 4; ++h) {
+        const float4 *a = (const float4 *)((const char *)src + h * h64);
+        float4 *b = (float4 *)((char *)dst + h * h32);
+        if (nc == 2) k_clover_to_f32<2><<<grid, bs, 0, s>>>(nvec, a, b);
+        else k_clover_to_f32<3><<<grid, bs, 0, s>>>(nvec, a, b);
+    }
+    return check_launch(ctx, "clover convert");
+}
+
+hr_status clover_apply_half(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *half, const void *in,
+                            void *out, cudaStream_t s)
+{
+    const long long nv = (long long)g.vh << g.lrhs;
+    const int bs = 128, grid = grid_for(nv, bs, 1 << 30);
+    const bool three = rep_nc(rep) == 3;
+    switch (prec) {
+    case kF64:
+        if (three) k_clover_apply<3, kF64><<<grid, bs, 0, s>>>(g, half, in, out);
+        else k_clover_apply<2, kF64><<<grid, bs, 0, s>>>(g, half, in, out);
+        break;
+    case kF32:
+        if (three) k_clover_apply<3, kF32><<<grid, bs, 0, s>>>(g, half, in, out);
+        else k_clover_apply<2, kF32><<<grid, bs, 0, s>>>(g, half, in, out);
+        break;
+    default:
+        if (three) k_clover_apply<3, kF16><<<grid, bs, 0, s>>>(g, half, in, out);
+        else k_clover_apply<2, kF16><<<grid, bs, 0, s>>>(g, half, in, out);
+        break;
+    }
+    return check_launch(ctx, "clover apply");
+}
+
+} // namespace hr
+
+extern "C" {
+
+size_t hr_clover_packed_bytes(hr_lattice lat, hr_rep rep, hr_prec prec)
+{
+    if (!valid_rep(rep) || !valid_clover_prec(prec) || hr_gauge_packed_bytes(lat, rep, prec) == 0) return 0;
+    return 4 * clover_half_bytes(make_geom(lat, 1), rep, prec);
+}
+
+hr_status hr_clover_build(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_clover_kind kind, double m0,
+                          double c_sw, const double *canonical, void *clover, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
+    if (!valid_clover_prec(prec)) return set_error(ctx, HR_ERR_UNSUPPORTED, "clover fields are FP64 or FP32");
+    if (kind != HR_CLOVER_SW && kind != HR_CLOVER_EXP) return set_error(ctx, HR_ERR_INVALID_ARG, "bad clover kind");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    st = check_buffers(ctx, {clover}, {canonical});
+    if (st) return st;
+    if (!(4.0 + m0 != 0.0) || !std::isfinite(m0) || !std::isfinite(c_sw))
+        return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero and finite, c_sw finite");
+    const Geom g = make_geom(lat, 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    BuildArgs B;
+    B.g = g;
+    B.can = canonical;
+    B.m0 = m0;
+    B.csw = c_sw;
+    B.kind = kind;
+    for (int h = 0; h < 4; ++h) B.half[h] = (void *)clover_half(clover, g, rep, prec, h >= 2, h & 1);
+    B.bad = ctx->d_counters + C_STATUS;
+    cudaError_t e = cudaMemsetAsync(B.bad, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "status reset: %s", cudaGetErrorString(e));
+    const long long V = 2LL * g.vh;
+    const int bs = 64, grid = (int)((V + bs - 1) / bs);
+    const bool three = rep_nc(rep) == 3;
+    if (prec == kF64) {
+        if (three) k_clover_build<3, kF64><<<grid, bs, 0, s>>>(B);
+        else k_clover_build<2, kF64><<<grid, bs, 0, s>>>(B);
+    } else {
+        if (three) k_clover_build<3, kF32><<<grid, bs, 0, s>>>(B);
+        else k_clover_build<2, kF32><<<grid, bs, 0, s>>>(B);
+    }
+    st = check_launch(ctx, "clover build");
+    if (st) return st;
+    unsigned bad = 0;
+    e = cudaMemcpyAsync(&bad, B.bad, sizeof bad, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "clover build status: %s", cudaGetErrorString(e));
+    if (bad) return set_error(ctx, HR_ERR_NUMERIC, "a clover site block is singular (no inverse)");
+    return HR_OK;
+}
+
+hr_status hr_clover_apply(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity parity, int inverse,
+                          int n_rhs, const void *clover, const void *in, void *out, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+    if (parity != HR_EVEN && parity != HR_ODD) return set_error(ctx, HR_ERR_INVALID_ARG, "parity HR_EVEN or HR_ODD");
+    hr_status st = validate_lattice(ctx, lat, n_rhs);
+    if (st) return st;
+    st = check_buffers(ctx, {clover, in, out});
+    if (st) return st;
+    const Geom g = make_geom(lat, n_rhs);
+    const Geom g1 = make_geom(lat, 1);
+    const void *half = clover_half(clover, g1, rep, clover_prec(prec), inverse != 0, parity);
+    return clover_apply_half(ctx, g, rep, prec, half, in, out, (cudaStream_t)stream);
+}
+
+hr_status hr_dirac_apply_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, const void *gauge,
+                                const void *clover, const void *in, void *out, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    st = check_buffers(ctx, {gauge, clover, in, out});
+    if (st) return st;
+    if (in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "in and out must not alias");
+    const Geom g = make_geom(lat, 1);
+    const size_t half = spinor_half_bytes(g, rep, prec);
+    cudaStream_t s = (cudaStream_t)stream;
+    // out_p = A_pp in_p - 1/2 H_{p,1-p} in_{1-p}: one hop per parity, A on the aux term
+    for (int p = 0; p < 2; ++p) {
+        HopLaunch L{};
+        L.p = p;
+        L.gauge = gauge;
+        L.in = (const char *)in + (1 - p) * half;
+        L.aux = (const char *)in + p * half;
+        L.out = (char *)out + p * half;
+        L.alpha = 1.0;
+        L.beta = -0.5;
+        L.clov = clover_half(clover, g, rep, clover_prec(prec), false, p);
+        L.clov_mode = kClovAux;
+        st = launch_hop(ctx, g, rep, prec, L, s);
+        if (st) return st;
+    }
+    return HR_OK;
+}
+
+hr_status hr_dirac_eo_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity out_parity, hr_op op,
+                             int n_rhs, const void *gauge, const void *clover, const void *in, void *out, void *work,
+                             size_t work_bytes, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!clover) return set_error(ctx, HR_ERR_INVALID_ARG, "null clover field");
+    if (op == HR_OP_HOP) return hr_dirac_eo(ctx, lat, 0.0, rep, prec, out_parity, op, n_rhs, gauge, in, out, work,
+                                             work_bytes, stream);
+    if (!valid_rep(rep) || !valid_prec(prec)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+    hr_status st = validate_lattice(ctx, lat, n_rhs);
+    if (st) return st;
+    st = check_buffers(ctx, {gauge, clover, in, out}, {}, {work});
+    if (st) return st;
+    if (in == out) return set_error(ctx, HR_ERR_INVALID_ARG, "in and out must not alias");
+    if (op != HR_OP_SCHUR && op != HR_OP_SCHUR_DAG && op != HR_OP_NORMAL)
+        return set_error(ctx, HR_ERR_INVALID_ARG, "bad op %d", (int)op);
+    if (out_parity != HR_EVEN) return set_error(ctx, HR_ERR_INVALID_ARG, "Schur operators act on even sites");
+    const size_t need = hr_dirac_workspace_bytes(lat, rep, prec, op, n_rhs);
+    if (!work || work_bytes < need)
+        return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, work_bytes);
+    const Geom g = make_geom(lat, n_rhs);
+    const size_t half = spinor_half_bytes(g, rep, prec);
+    void *wo = work;
+    void *we = (op == HR_OP_NORMAL) ? (char *)work + half : nullptr;
+    return apply_eo_op(ctx, g, 0.0, rep, prec, op, gauge, in, out, wo, we, kFinNone, nullptr, nullptr,
+                       (cudaStream_t)stream, nullptr, clover);
+}
+
+} // extern "C"

@@ -156,6 +156,8 @@ HopArgs make_args(hr_ctx *ctx, const Geom &g, const HopLaunch &L)
     a.cg_r = L.cg_r;
     a.inject_no_copy = ctx->inject_tile_no_copy;
     a.wait_cycles = ctx->inject_tile_no_copy ? (1LL << 20) : (1LL << 31); // ~0.5 ms / ~1 s
+    a.clov = L.clov;
+    a.clov_mode = L.clov ? L.clov_mode : kClovNone;
     return a;
 }
 
@@ -207,11 +209,18 @@ bool hop_variant_available(int rep, int prec, int variant)
 //   Mhat    : t_o = H_oe in;        out = A in - c H_eo t_o
 //   Mhat^+  : t_o = H_oe g5 in;     out = A in - c g5 H_eo t_o
 //   normal  : u = Mhat in (|u|^2 reduced with fin_schur), out = Mhat^+ u
-// with A = 4 + m0 and c = 1 / (4 A).
+// with A = 4 + m0 and c = 1 / (4 A); with a clover field A is the site term
+// (A_oo^-1 applied to t_o in the first hop's epilogue, A_ee to in in the
+// second's) and c = 1/4.
 hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, int op, const void *gauge,
                       const void *in, void *out, void *work_odd, void *work_even, int fin_schur, const double *gate,
-                      const double *done, cudaStream_t s, const CgFuse *fuse)
+                      const double *done, cudaStream_t s, const CgFuse *fuse, const void *clover)
 {
+    // with a clover field (in the operator's clover precision):
+    //   t_o = A_oo^-1 H_oe in;  out = A_ee in - 1/4 H_eo t_o
+    const int cp = clover_prec(prec);
+    const void *clov_inv_odd = clover_half(clover, g, rep, cp, true, 1);
+    const void *clov_even = clover_half(clover, g, rep, cp, false, 0);
     const double A = 4.0 + m0, c = 1.0 / (4.0 * A);
     hr_status st;
     HopLaunch L{};
@@ -229,6 +238,10 @@ hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, 
         h1.g5_in = dag ? 1 : 0;
         h1.g5_out = 0;
         h1.fin = kFinNone;
+        if (clover) {
+            h1.clov = clov_inv_odd;
+            h1.clov_mode = kClovOut;
+        }
         hr_status e = launch_hop(ctx, g, rep, prec, h1, s);
         if (e) return e;
         HopLaunch h2 = L;
@@ -241,6 +254,12 @@ hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, 
         h2.g5_in = 0;
         h2.g5_out = dag ? 1 : 0;
         h2.fin = fin;
+        if (clover) {
+            h2.alpha = 1.0;
+            h2.beta = -0.25;
+            h2.clov = clov_even;
+            h2.clov_mode = kClovAux;
+        }
         if (fz) {
             h2.fin = fz->fin;
             h2.cg_x = fz->x;

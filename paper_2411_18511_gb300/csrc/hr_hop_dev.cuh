@@ -4,6 +4,7 @@
 // and the epilogue out = alpha aux + beta [g5] H [g5] in with the fused |out|^2.
 #pragma once
 
+#include "hr_clover.cuh"
 #include "hr_host.h"
 
 namespace hr {
@@ -31,7 +32,17 @@ struct HopArgs {
     long long wait_cycles; // bound of a device wait (tiled kernels' bulk copies)
     int inject_no_copy;    // failure injection for tests: announce the tiled
                            // kernels' copies but never queue them
+    const void *clov;      // clover half-field of the output parity (kClovAux / kClovOut), or nullptr
+    int clov_mode;
 };
+
+// the clover site product out of line: kernels that never take it keep their
+// register allocation and instruction stream
+template <int CP, class T, int NC>
+__device__ __noinline__ void clover_site(const void *half, int i, cpx<T> (&v)[4][NC])
+{
+    clover_apply<CP>(half, i, v);
+}
 
 __device__ __forceinline__ dd mul_pow2(dd x, float s) { return dd(x.h * s, x.l * s); }
 __device__ __forceinline__ float mul_pow2(float x, float s) { return x * s; }
@@ -125,9 +136,11 @@ template <int PREC, class T, int NC>
 __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<T> (&acc)[4][NC], T al, T be, T bu,
                                              SqAcc<T> &red)
 {
+    constexpr int CP = clover_prec(PREC);
     cpx<T> o[4][NC];
     if (a.aux) {
         load_spinor<NC, PREC>(a.aux, a.g.nblk_s, j, o);
+        if (a.clov_mode == kClovAux) clover_site<CP>(a.clov, j >> a.g.lrhs, o);
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -153,6 +166,7 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<
                 o[s][c] = {b * acc[s][c].re, b * acc[s][c].im};
             }
     }
+    if (a.clov_mode == kClovOut) clover_site<CP>(a.clov, j >> a.g.lrhs, o);
     if (a.cg_r) {
         // the CG's x/r update on this site, with q = o in registers (the
         // vector kernel's arithmetic, in the hop's precision)

@@ -90,7 +90,11 @@ inline int grid_for(long long n, int block, int cap)
 }
 
 // counters used by the reducing kernels (each reduction site has its own)
-enum Counter { C_HOP = 0, C_XR = 1, C_RES = 2, C_NORM = 3, C_DOT = 4, C_MISC = 5, C_BATCH = 16 };
+enum Counter { C_HOP = 0, C_XR = 1, C_RES = 2, C_NORM = 3, C_DOT = 4, C_MISC = 5, C_BATCH = 16, C_STATUS = 63 };
+
+// clover site term in a hop epilogue (hr_clover.cuh): none, A(x) on the aux
+// term (out = alpha A aux + beta acc), or A(x) on the result (out = A (alpha aux + beta acc))
+enum ClovMode { kClovNone = 0, kClovAux = 1, kClovOut = 2 };
 
 // ---- hop launches (hr_hop.cu) ----
 struct HopLaunch {
@@ -109,6 +113,10 @@ struct HopLaunch {
     void *cg_x;
     const void *cg_p;
     void *cg_r;
+    // clover site term (nullable): the half-field of the output parity
+    // (clover_half) and how the epilogue applies it (ClovMode)
+    const void *clov;
+    int clov_mode;
 };
 // a CG x/r update fused into the last hop of an operator (same precision)
 struct CgFuse {
@@ -129,7 +137,19 @@ bool tune_cache_save(hr_ctx *ctx);
 // out = op(in) on even sites, work = odd temporary (+ even temporary for NORMAL)
 hr_status apply_eo_op(hr_ctx *ctx, const Geom &g, double m0, int rep, int prec, int op, const void *gauge,
                       const void *in, void *out, void *work_odd, void *work_even, int fin_schur,
-                      const double *gate, const double *done, cudaStream_t s, const CgFuse *fuse = nullptr);
+                      const double *gate, const double *done, cudaStream_t s, const CgFuse *fuse = nullptr,
+                      const void *clover = nullptr);
+
+// ---- clover site term (hr_clover.cu) ----
+// bytes of one of the four half-fields of a packed clover field (cp: kF64 / kF32)
+size_t clover_half_bytes(const Geom &g, int rep, int cp);
+// the half-field of A (inverse = false) or A^-1 on `parity`; nullptr for a null base
+const void *clover_half(const void *base, const Geom &g, int rep, int cp, bool inverse, int parity);
+// FP64 packed clover field -> FP32 packed clover field
+hr_status clover_convert_f32(hr_ctx *ctx, const Geom &g, int rep, const void *src, void *dst, cudaStream_t s);
+// out = A in on the sites of one parity, A from the half-field `half`
+hr_status clover_apply_half(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *half, const void *in,
+                            void *out, cudaStream_t s);
 
 // ---- BLAS launches (hr_blas.cu) ----
 hr_status blas_norm2(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *v, int fin, cudaStream_t s);

@@ -47,6 +47,13 @@ def pack_gauge(ctx, dims, rep, prec, q_dev, stream=None) -> torch.Tensor:
     return out
 
 
+def build_clover(ctx, dims, rep, prec, kind, m0, c_sw, q_dev, stream=None) -> torch.Tensor:
+    """Packed clover field (hr_clover_build) from canonical device links."""
+    out = empty_bytes(hr.hr_clover_packed_bytes(dims, rep, prec), q_dev.device)
+    hr.hr_clover_build(ctx, dims, rep, prec, kind, m0, c_sw, q_dev, out, stream)
+    return out
+
+
 def pack_spinor(ctx, dims, rep, prec, parity, psi_dev, stream=None) -> torch.Tensor:
     """psi_dev: complex128 [V,4,nc] or [n_rhs,V,4,nc] (canonical, on the device)."""
     n_rhs = 1 if psi_dev.dim() == 3 else psi_dev.shape[0]

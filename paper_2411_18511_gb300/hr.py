@@ -24,6 +24,7 @@ HR_F64, HR_F32, HR_F16 = 0, 1, 2
 HR_EVEN, HR_ODD, HR_FULL = 0, 1, 2
 HR_OP_HOP, HR_OP_SCHUR, HR_OP_SCHUR_DAG, HR_OP_NORMAL = 0, 1, 2, 3
 HR_SYSTEM_D, HR_SYSTEM_DDAG_D = 0, 1
+HR_CLOVER_SW, HR_CLOVER_EXP = 0, 1
 
 
 def HR_BC_ANTIPERIODIC(mu: int) -> int:
@@ -43,7 +44,9 @@ EXPORTED = [
     "hr_dirac_eo", "hr_solver_default_opts", "hr_cg_workspace_bytes", "hr_cg_solve", "hr_force",
     "hr_link_grad", "hr_norm2", "hr_axpy", "hr_gamma5", "hr_norm2_noalloc", "hr_autotune_hop",
     "hr_tune_lookup", "hr_cg_batch_workspace_bytes", "hr_cg_solve_batch", "hr_solve_full_workspace_bytes",
-    "hr_solve_full",
+    "hr_solve_full", "hr_clover_packed_bytes", "hr_clover_build", "hr_clover_apply", "hr_dirac_apply_clover",
+    "hr_dirac_eo_clover", "hr_cg_clover_workspace_bytes", "hr_cg_solve_clover",
+    "hr_solve_full_clover_workspace_bytes", "hr_solve_full_clover",
 ]
 
 
@@ -136,6 +139,17 @@ def lib():
                 "hr_solve_full_workspace_bytes": ([LAT, I, ctypes.POINTER(hr_solver_opts), I], S),
                 "hr_solve_full": ([P, LAT, D, I, ctypes.POINTER(hr_solver_opts), I, P, P, P,
                                    ctypes.POINTER(hr_solve_info), P, S, P], I),
+                "hr_clover_packed_bytes": ([LAT, I, I], S),
+                "hr_clover_build": ([P, LAT, I, I, I, D, D, P, P, P], I),
+                "hr_clover_apply": ([P, LAT, I, I, I, I, I, P, P, P, P], I),
+                "hr_dirac_apply_clover": ([P, LAT, I, I, P, P, P, P, P], I),
+                "hr_dirac_eo_clover": ([P, LAT, I, I, I, I, I, P, P, P, P, P, S, P], I),
+                "hr_cg_clover_workspace_bytes": ([LAT, I, ctypes.POINTER(hr_solver_opts)], S),
+                "hr_cg_solve_clover": ([P, LAT, I, ctypes.POINTER(hr_solver_opts), P, P, P, P,
+                                        ctypes.POINTER(hr_solve_info), P, S, P], I),
+                "hr_solve_full_clover_workspace_bytes": ([LAT, I, ctypes.POINTER(hr_solver_opts), I], S),
+                "hr_solve_full_clover": ([P, LAT, I, ctypes.POINTER(hr_solver_opts), I, P, P, P, P,
+                                          ctypes.POINTER(hr_solve_info), P, S, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -334,6 +348,86 @@ def hr_solve_full(ctx: Context, dims, m0, rep, opts: hr_solver_opts, system, gau
     rc = lib().hr_solve_full(ctx.handle, lattice(dims), float(m0), rep, ctypes.byref(opts), int(system),
                              _ptr(gauge), _ptr(b), _ptr(x), ctypes.byref(info), _ptr(work), wb,
                              _stream(stream))
+    if raise_on_error and rc not in (HR_OK, HR_ERR_NOT_CONVERGED):
+        ctx.check(rc)
+    return rc, info
+
+
+# ---- clover and exponential-clover site terms
+
+def hr_clover_packed_bytes(dims, rep: int, prec: int) -> int:
+    return int(lib().hr_clover_packed_bytes(lattice(dims), rep, prec))
+
+
+def hr_clover_build(ctx: Context, dims, rep, prec, kind, m0, c_sw, canonical, clover, stream=None):
+    """Packed clover field (A and A^-1 on both parities) from the canonical gauge."""
+    _need(canonical, 4 * _vol(dims) * 4 * 8, "canonical gauge")
+    _need(clover, hr_clover_packed_bytes(dims, rep, prec), "clover")
+    return ctx.check(lib().hr_clover_build(ctx.handle, lattice(dims), rep, prec, int(kind), float(m0), float(c_sw),
+                                           _ptr(canonical), _ptr(clover), _stream(stream)))
+
+
+def hr_clover_apply(ctx: Context, dims, rep, prec, parity, inverse, n_rhs, clover, inp, out, stream=None):
+    half = hr_spinor_packed_bytes(dims, rep, prec, parity, n_rhs)
+    _need(inp, half, "in")
+    _need(out, half, "out")
+    return ctx.check(lib().hr_clover_apply(ctx.handle, lattice(dims), rep, prec, parity, int(bool(inverse)), n_rhs,
+                                           _ptr(clover), _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def hr_dirac_apply_clover(ctx: Context, dims, rep, prec, gauge, clover, inp, out, stream=None):
+    full = hr_spinor_packed_bytes(dims, rep, prec, HR_FULL, 1)
+    _need(inp, full, "in")
+    _need(out, full, "out")
+    return ctx.check(lib().hr_dirac_apply_clover(ctx.handle, lattice(dims), rep, prec, _ptr(gauge), _ptr(clover),
+                                                 _ptr(inp), _ptr(out), _stream(stream)))
+
+
+def hr_dirac_eo_clover(ctx: Context, dims, rep, prec, out_parity, op, n_rhs, gauge, clover, inp, out,
+                       work=None, stream=None):
+    half = hr_spinor_packed_bytes(dims, rep, prec, HR_EVEN, n_rhs)
+    _need(inp, half, "in")
+    _need(out, half, "out")
+    wb = 0 if work is None else work.numel() * work.element_size()
+    return ctx.check(lib().hr_dirac_eo_clover(ctx.handle, lattice(dims), rep, prec, out_parity, op, n_rhs,
+                                              _ptr(gauge), _ptr(clover), _ptr(inp), _ptr(out), _ptr(work), wb,
+                                              _stream(stream)))
+
+
+def hr_cg_clover_workspace_bytes(dims, rep: int, opts: hr_solver_opts) -> int:
+    return int(lib().hr_cg_clover_workspace_bytes(lattice(dims), rep, ctypes.byref(opts)))
+
+
+def hr_cg_solve_clover(ctx: Context, dims, rep, opts: hr_solver_opts, gauge, clover, b, x, work, stream=None,
+                       raise_on_error: bool = True):
+    """CG on Mhat^+ Mhat with the clover site term.  Returns (status, hr_solve_info)."""
+    half = hr_spinor_packed_bytes(dims, rep, HR_F64, HR_EVEN, opts.n_rhs)
+    _need(b, half, "b")
+    _need(x, half, "x")
+    info = hr_solve_info()
+    wb = 0 if work is None else work.numel() * work.element_size()
+    rc = lib().hr_cg_solve_clover(ctx.handle, lattice(dims), rep, ctypes.byref(opts), _ptr(gauge), _ptr(clover),
+                                  _ptr(b), _ptr(x), ctypes.byref(info), _ptr(work), wb, _stream(stream))
+    if raise_on_error and rc not in (HR_OK, HR_ERR_NOT_CONVERGED):
+        ctx.check(rc)
+    return rc, info
+
+
+def hr_solve_full_clover_workspace_bytes(dims, rep, opts: hr_solver_opts, system: int) -> int:
+    return int(lib().hr_solve_full_clover_workspace_bytes(lattice(dims), rep, ctypes.byref(opts), system))
+
+
+def hr_solve_full_clover(ctx: Context, dims, rep, opts: hr_solver_opts, system, gauge, clover, b, x, work,
+                         stream=None, raise_on_error: bool = True):
+    """D x = b or D^+ D x = b with the clover site term.  Returns (status, hr_solve_info)."""
+    full = hr_spinor_packed_bytes(dims, rep, HR_F64, HR_FULL, 1)
+    _need(b, full, "b")
+    _need(x, full, "x")
+    info = hr_solve_info()
+    wb = 0 if work is None else work.numel() * work.element_size()
+    rc = lib().hr_solve_full_clover(ctx.handle, lattice(dims), rep, ctypes.byref(opts), int(system), _ptr(gauge),
+                                    _ptr(clover), _ptr(b), _ptr(x), ctypes.byref(info), _ptr(work), wb,
+                                    _stream(stream))
     if raise_on_error and rc not in (HR_OK, HR_ERR_NOT_CONVERGED):
         ctx.check(rc)
     return rc, info
