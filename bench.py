@@ -529,13 +529,92 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
         for k in ("mixed_f32", "mixed_f16"):
             cg[k]["speedup_vs_fp64"] = round(cg["fp64"]["seconds_median"] / cg[k]["seconds_median"], 3)
     out["cg_32"] = cg
+    out["cg_32_clover"] = run_cg_clover(ctx, hr, fields, d32, q32, gauge, bp, xp, cg)
     del gauge, bp
+    torch.cuda.empty_cache()
+    out["clover_48"] = run_clover_48(ctx, torch, hr, fields, q48, psi48)
     torch.cuda.empty_cache()
     out["diff_solve_16"] = run_diff_solve(torch, synth)
     torch.cuda.empty_cache()
     out["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
     torch.cuda.empty_cache()
     out["batch_12"] = run_batch(ctx, torch, hr, fields, synth)
+    return out
+
+
+def run_cg_clover(ctx, hr, fields, d32, q32, gauge, bp, xp, cg_wilson):
+    """The 32^4 solves of cg_32 with the clover term (c_sw = 1, m0 = -0.2):
+    FP64 and mixed precision (each at the reliable_delta that won for the
+    Wilson operator), median of five solves after one warm-up."""
+    m0, csw = -0.2, 1.0
+    t0 = time.perf_counter()
+    clov = fields.build_clover(ctx, d32, hr.HR_FUND, hr.HR_F64, hr.HR_CLOVER_SW, m0, csw,
+                               fields.gauge_to_device(q32))
+    out = {"c_sw": csw, "m0": m0, "kind": "clover (Sheikholeslami-Wohlert)",
+           "build_s": round(time.perf_counter() - t0, 3)}
+    for name, inner in (("fp64", hr.HR_F64), ("mixed_f32", hr.HR_F32), ("mixed_f16", hr.HR_F16)):
+        opts = hr.hr_solver_default_opts()
+        opts.inner_prec = inner
+        opts.reliable_delta = cg_wilson.get(name, {}).get("reliable_delta", 0.1)
+        work = fields.empty_bytes(hr.hr_cg_clover_workspace_bytes(d32, hr.HR_FUND, opts))
+        times = []
+        rc = info = None
+        for _ in range(6):
+            rc, info = hr.hr_cg_solve_clover(ctx, d32, hr.HR_FUND, opts, gauge, clov, bp, xp, work)
+            times.append(info.seconds)
+        out[name] = {"status": hr.STATUS_NAMES.get(rc, rc), "seconds_median": round(statistics.median(times[1:]), 4),
+                     "iters": info.iters, "reliable_updates": info.n_reliable_updates,
+                     "true_rel_residual": info.true_rel_residual, "reliable_delta": opts.reliable_delta}
+        del work
+    if out["fp64"]["seconds_median"] > 0:
+        for k in ("mixed_f32", "mixed_f16"):
+            out[k]["speedup_vs_fp64"] = round(out["fp64"]["seconds_median"] / out[k]["seconds_median"], 3)
+    return out
+
+
+def run_clover_48(ctx, torch, hr, fields, q48, psi48, reps=30):
+    """48^4 fund FP64: one Schur operator application Mhat (two hops) with and
+    without the clover site term (clover and exponential clover), the cost of
+    the diagonal term the paper measures (Sec. 2.2, Fig. 3), and the one-off
+    build of the field.  Bytes per even site: Wilson 1152 (two hops of 512 +
+    the aux spinor 128); with the term + 2 x 256 (A_oo^-1 and A_ee blocks)."""
+    dims = DIMS
+    m0, csw = -0.2, 1.0
+    qd = fields.gauge_to_device(q48)
+    gauge = fields.pack_gauge(ctx, dims, hr.HR_FUND, hr.HR_F64, qd)
+    src = fields.pack_spinor(ctx, dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, fields.spinor_to_device(psi48))
+    dst = fields.empty_spinor(dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
+    work = fields.empty_bytes(hr.hr_dirac_workspace_bytes(dims, hr.HR_FUND, hr.HR_F64, hr.HR_OP_SCHUR))
+    Vh = int(np.prod(dims)) // 2
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"lattice": list(dims), "m0": m0, "c_sw": csw, "applications": reps}
+    ms_w = timed(lambda: hr.hr_dirac_eo(ctx, dims, m0, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, hr.HR_OP_SCHUR, 1,
+                                        gauge, src, dst, work))
+    out["wilson"] = {"ms": round(ms_w, 4), "gbs": round(Vh * 1152 / (ms_w * 1e-3) / 1e9, 1)}
+    for name, kind in (("clover", hr.HR_CLOVER_SW), ("exp_clover", hr.HR_CLOVER_EXP)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        clov = fields.build_clover(ctx, dims, hr.HR_FUND, hr.HR_F64, kind, m0, csw, qd)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        ms = timed(lambda: hr.hr_dirac_eo_clover(ctx, dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, hr.HR_OP_SCHUR, 1,
+                                                 gauge, clov, src, dst, work))
+        out[name] = {"ms": round(ms, 4), "gbs": round(Vh * (1152 + 512) / (ms * 1e-3) / 1e9, 1),
+                     "time_vs_wilson": round(ms / ms_w, 3), "build_s": round(build_s, 3)}
+        del clov
+    del gauge, src, dst, work, qd
     return out
 
 

@@ -27,7 +27,7 @@ using namespace hr;
 
 namespace {
 
-template <int REP, int PREC, int G5IN>
+template <int REP, int PREC, int G5IN, bool CLOV = false>
 __device__ __forceinline__ void hop_body(const HopArgs &a)
 {
     using T = typename PrecTraits<PREC>::T;
@@ -42,7 +42,7 @@ __device__ __forceinline__ void hop_body(const HopArgs &a)
     const T al = Real<T>::from_coef(a.alpha);
     SqAcc<T> red;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride)
-        hop_site<REP, PREC, G5IN>(a, j, al, be, bu, red);
+        hop_site<REP, PREC, G5IN, CLOV>(a, j, al, be, bu, red);
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
@@ -65,6 +65,15 @@ template <int REP, int PREC, int G5IN>
 __global__ void __maxnreg__(96) k_hop_r96(HopArgs a)
 {
     hop_body<REP, PREC, G5IN>(a);
+}
+
+// The unrolled kernel with the clover site term in its epilogue: clover
+// launches run this one (or the paired staged kernel for fundamental FP64),
+// whatever the tuned shape, so that no other kernel carries the clover code.
+template <int REP, int PREC, int G5IN>
+__global__ void __launch_bounds__(256) k_hop_clov(HopArgs a)
+{
+    hop_body<REP, PREC, G5IN, true>(a);
 }
 
 // ---------------------------------------------------------------- launch
@@ -93,10 +102,30 @@ template <int REP, int PREC> struct PlainLaunch {
     }
 };
 
+template <int REP, int PREC> struct ClovLaunch {
+    static bool run(hr_ctx *ctx, const HopArgs &a, int grid, int block, cudaStream_t s, hr_status &st)
+    {
+        if (a.g5_in) k_hop_clov<REP, PREC, 1><<<grid, block, 0, s>>>(a);
+        else k_hop_clov<REP, PREC, 0><<<grid, block, 0, s>>>(a);
+        st = check_launch(ctx, "hop kernel (clover epilogue)");
+        return true;
+    }
+};
+
 hr_status dispatch(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs &a, HopChoice c, cudaStream_t s)
 {
     if (rep < 0 || rep > 2 || prec < 0 || prec > 2) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
     const long long nv = (long long)g.vh << g.lrhs;
+    if (a.clov_mode != kClovNone) {
+        // the clover instantiations: paired staged for fundamental FP64, else unrolled
+        const bool paired = rep == HR_FUND && prec == kF64;
+        const int block = paired ? 256 : 128;
+        const int grid = grid_for(nv, block, a.fin ? kMaxBlocks : (1 << 30));
+        hr_status st = HR_OK;
+        if (paired) launch_hop_clover_paired(ctx, a, grid, block, s, st);
+        else for_config<ClovLaunch>(rep, prec, ctx, a, grid, block, s, st);
+        return st;
+    }
     // non-reducing launches cover all sites; reducing ones are capped so the
     // per-block partials fit the context's scratch
     const int grid = grid_for(nv, c.block, a.fin ? kMaxBlocks : (1 << 30));

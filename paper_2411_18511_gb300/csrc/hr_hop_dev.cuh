@@ -36,13 +36,7 @@ struct HopArgs {
     int clov_mode;
 };
 
-// the clover site product out of line: kernels that never take it keep their
-// register allocation and instruction stream
-template <int CP, class T, int NC>
-__device__ __noinline__ void clover_site(const void *half, int i, cpx<T> (&v)[4][NC])
-{
-    clover_apply<CP>(half, i, v);
-}
+
 
 __device__ __forceinline__ dd mul_pow2(dd x, float s) { return dd(x.h * s, x.l * s); }
 __device__ __forceinline__ float mul_pow2(float x, float s) { return x * s; }
@@ -131,8 +125,10 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, int rr, const S
     hop_term<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, g5_in_of<G5IN>(a), acc);
 }
 
-// out = alpha * aux + beta * g5^{g5_out} acc, stored; |out|^2 into red
-template <int PREC, class T, int NC>
+// out = alpha * aux + beta * g5^{g5_out} acc, stored; |out|^2 into red.
+// CLOV: the kernel instantiation that also applies the clover site term
+// (a.clov_mode); the others carry no trace of it.
+template <int PREC, bool CLOV = false, class T, int NC>
 __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<T> (&acc)[4][NC], T al, T be, T bu,
                                              SqAcc<T> &red)
 {
@@ -140,7 +136,8 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<
     cpx<T> o[4][NC];
     if (a.aux) {
         load_spinor<NC, PREC>(a.aux, a.g.nblk_s, j, o);
-        if (a.clov_mode == kClovAux) clover_site<CP>(a.clov, j >> a.g.lrhs, o);
+        if constexpr (CLOV)
+            if (a.clov_mode == kClovAux) clover_apply<CP>(a.clov, j >> a.g.lrhs, o);
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -166,7 +163,8 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<
                 o[s][c] = {b * acc[s][c].re, b * acc[s][c].im};
             }
     }
-    if (a.clov_mode == kClovOut) clover_site<CP>(a.clov, j >> a.g.lrhs, o);
+    if constexpr (CLOV)
+        if (a.clov_mode == kClovOut) clover_apply<CP>(a.clov, j >> a.g.lrhs, o);
     if (a.cg_r) {
         // the CG's x/r update on this site, with q = o in registers (the
         // vector kernel's arithmetic, in the hop's precision)
@@ -203,7 +201,7 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<
 }
 
 // one output site j (virtual index) of the unrolled hop: all 8 directions and the epilogue
-template <int REP, int PREC, int G5IN = -1, class T>
+template <int REP, int PREC, int G5IN = -1, bool CLOV = false, class T>
 __device__ __forceinline__ void hop_site(const HopArgs &a, int j, T al, T be, T bu, SqAcc<T> &red)
 {
     constexpr int NC = RepTraits<REP>::NC;
@@ -216,7 +214,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &a, int j, T al, T be, T 
     hop_dir<1, REP, PREC, G5IN>(a, i, rr, nb, acc);
     hop_dir<2, REP, PREC, G5IN>(a, i, rr, nb, acc);
     hop_dir<3, REP, PREC, G5IN>(a, i, rr, nb, acc);
-    hop_epilogue<PREC>(a, j, acc, al, be, bu, red);
+    hop_epilogue<PREC, CLOV>(a, j, acc, al, be, bu, red);
 }
 
 } // namespace hr

@@ -98,5 +98,7 @@ bool launch_hop_tiled(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopAr
                       cudaStream_t s, hr_status &st);
 bool launch_hop_paired(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs &a, HopChoice c, int grid,
                        cudaStream_t s, hr_status &st);
+// the paired staged kernel with the clover epilogue (fundamental FP64)
+void launch_hop_clover_paired(hr_ctx *ctx, const HopArgs &a, int grid, int block, cudaStream_t s, hr_status &st);
 
 } // namespace hr

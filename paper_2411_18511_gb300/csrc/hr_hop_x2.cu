@@ -38,7 +38,7 @@ __device__ __forceinline__ void x2_stage_step(const HopArgs &a, const K2 &k, int
     x2_compute<(K >> 1), (K & 1) == 0, K == 0, NEG>(k, w, qh, ql, acc);
 }
 
-template <int G5IN>
+template <int G5IN, bool CLOV = false>
 __device__ __forceinline__ void x2s_body(const HopArgs &a)
 {
     using S = Stage<kRepFund, kF64>;
@@ -72,7 +72,7 @@ __device__ __forceinline__ void x2s_body(const HopArgs &a)
         x2_stage_step<5, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
         x2_stage_step<6, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
         x2_stage_step<7, NEG>(a, k, i, rr, nb, b0, b1, bd, acc);
-        x2_epilogue(a, j, acc, al, be, bu, red);
+        x2_epilogue<CLOV>(a, j, acc, al, be, bu, red);
     }
     if (a.fin) {
         __shared__ double smem[32 * 32];
@@ -118,6 +118,7 @@ __device__ __forceinline__ void x2_body(const HopArgs &a)
 template <int G5IN> __global__ void __launch_bounds__(256) k_hop_x2(HopArgs a) { x2_body<G5IN>(a); }
 template <int G5IN> __global__ void __maxnreg__(96) k_hop_x2_r96(HopArgs a) { x2_body<G5IN>(a); }
 template <int G5IN> __global__ void __launch_bounds__(256) k_hop_x2s(HopArgs a) { x2s_body<G5IN>(a); }
+template <int G5IN> __global__ void __launch_bounds__(256) k_hop_x2s_clov(HopArgs a) { x2s_body<G5IN, true>(a); }
 template <int G5IN> __global__ void __maxnreg__(96) k_hop_x2s_r96(HopArgs a) { x2s_body<G5IN>(a); }
 
 // ---------------------------------------------------------------- FP32 / FP16 storage
@@ -707,6 +708,19 @@ template <int REP, int PREC> struct Launch {
 } // namespace
 
 namespace hr {
+
+void launch_hop_clover_paired(hr_ctx *ctx, const HopArgs &a, int grid, int block, cudaStream_t s, hr_status &st)
+{
+    using S = Stage<kRepFund, kF64>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        for (auto f : {k_hop_x2s_clov<0>, k_hop_x2s_clov<1>})
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes(256));
+        attr_set = true;
+    }
+    (a.g5_in ? k_hop_x2s_clov<1> : k_hop_x2s_clov<0>)<<<grid, block, S::smem_bytes(block), s>>>(a);
+    st = check_launch(ctx, "paired hop kernel (clover epilogue)");
+}
 
 bool launch_hop_paired(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs &a, HopChoice c, int grid,
                        cudaStream_t s, hr_status &st)

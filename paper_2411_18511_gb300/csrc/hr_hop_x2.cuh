@@ -231,6 +231,7 @@ __device__ __forceinline__ void x2_dir(const HopArgs &a, const K2 &k, int i, int
 }
 
 // the site's epilogue: doublets back to values, then the shared epilogue
+template <bool CLOV = false>
 __device__ __forceinline__ void x2_epilogue(const HopArgs &a, int j, const cdd2 (&acc)[4], dd al, dd be, dd bu,
                                             SqAcc<dd> &red)
 {
@@ -240,7 +241,7 @@ __device__ __forceinline__ void x2_epilogue(const HopArgs &a, int j, const cdd2 
         o[t][0] = {dd(acc[t].re.h.x, acc[t].re.l.x), dd(acc[t].im.h.x, acc[t].im.l.x)};
         o[t][1] = {dd(acc[t].re.h.y, acc[t].re.l.y), dd(acc[t].im.h.y, acc[t].im.l.y)};
     }
-    hop_epilogue<kF64>(a, j, o, al, be, bu, red);
+    hop_epilogue<kF64, CLOV>(a, j, o, al, be, bu, red);
 }
 
 

@@ -746,15 +746,17 @@ __device__ __forceinline__ bool sign_bit(const dd &x) { return sign_bit(x.h); }
 // where it carries the factor -1 of the boundary condition
 template <class T> __device__ __forceinline__ void quat_to_adj(const T (&a)[4], T (&R)[3][3])
 {
+    // the sign s enters through the factors: every term of R has one of them
+    // (s w on the diagonal, 2 s a_k and 2 s a0 in the products), so no extra
+    // value stays live
+    const bool neg = sign_bit(a[0]);
+    const float two = neg ? -2.f : 2.f;
     T w = a[0] * a[0] - (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
-    T b1 = 2 * a[1], b2 = 2 * a[2], b3 = 2 * a[3], c = 2 * a[0];
+    if (neg) w = -w;
+    T b1 = two * a[1], b2 = two * a[2], b3 = two * a[3], c = two * a[0];
     R[0][0] = w + b1 * a[1]; R[0][1] = b1 * a[2] + c * a[3]; R[0][2] = b1 * a[3] - c * a[2];
     R[1][0] = b2 * a[1] - c * a[3]; R[1][1] = w + b2 * a[2]; R[1][2] = b2 * a[3] + c * a[1];
     R[2][0] = b3 * a[1] + c * a[2]; R[2][1] = b3 * a[2] - c * a[1]; R[2][2] = w + b3 * a[3];
-    if (sign_bit(a[0])) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) R[k / 3][k % 3] = -R[k / 3][k % 3];
-    }
 }
 
 // ---------------------------------------------------------------- colour algebra

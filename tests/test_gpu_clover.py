@@ -131,8 +131,9 @@ def _forced(tmp_path, monkeypatch, lat, rep, prec, variant, block, n_rhs=1):
 
 
 @pytest.mark.parametrize("variant", list(range(14)))
-def test_every_hop_variant_carries_the_site_term(tmp_path, monkeypatch, variant):
-    """Each kernel variant's epilogue (fundamental FP64, exponential clover)."""
+def test_clover_launches_do_not_depend_on_the_tuned_shape(tmp_path, monkeypatch, variant):
+    """Clover launches run their own kernel instantiations whatever shape the
+    tuner chose for the Wilson hop (fundamental FP64, exponential clover)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     lat = (4, 6, 8, 10)
