@@ -131,16 +131,18 @@ def neighbour_bytes_per_site(rep: str, prec: str) -> int:
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_18511_gb300", "csrc")
-    for f in ("hr_internal.cuh", "hr_hop_dev.cuh", "hr_hop_fam.h", "hr_hop.cu", "hr_hop_staged.cu",
-              "hr_hop_loop.cu", "hr_hop_tile.cu", "hr_hop_x2.cu"):
+    for f in ("hr_internal.cuh", "hr_clover.cuh", "hr_host.h", "hr_hop_dev.cuh", "hr_hop_fam.h", "hr_hop_x2.cuh",
+              "hr_hop.cu", "hr_hop_staged.cu", "hr_hop_loop.cu", "hr_hop_tile.cu", "hr_hop_x2.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name: str):
-    """Per-launch DRAM bytes of a kernel from a committed ncu summary, if it was
-    taken on the current kernel source (a 'source_hash:' line must match)."""
+def profiled_traffic(name: str, variant: int, block: int):
+    """Per-launch DRAM bytes of the hop kernel in launch shape (variant, block)
+    from a committed ncu summary ('traffic_bytes_per_launch v<variant> b<block>:'
+    lines), if it was taken on the current kernel source (its 'source_hash:'
+    line must match); else None."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
@@ -154,7 +156,7 @@ def profiled_traffic(name: str):
     if vals.get("source_hash") != kernel_source_hash():
         return None
     try:
-        return float(vals["traffic_bytes_per_launch"])
+        return float(vals[f"traffic_bytes_per_launch v{variant} b{block}"])
     except (KeyError, ValueError):
         return None
 
@@ -359,7 +361,7 @@ def run_ours(args):
             "parallelism": f"replicas{world}",
         },
         "roofline": roofline(pname, Vh, bytes_site, launch_ms, achieved, peak, peak_kind,
-                             profiled_traffic(f"hop_fund_{pname}_{L4}x{L4}x{L4}x{L4}.md"), kernel),
+                             profiled_traffic(f"hop_fund_{pname}_{L4}x{L4}x{L4}x{L4}.md", variant, block), kernel),
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
