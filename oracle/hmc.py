@@ -1,0 +1,185 @@
+"""Hybrid Monte Carlo molecular dynamics for SU(2) with two flavours of
+even-odd preconditioned Wilson fermions: plain numpy, FP64 (test
+infrastructure, like the rest of ``oracle``).
+
+The paper (arXiv:2411.18511, Sec. 1 and Sec. 2.1) names HMC as the consumer of
+the even-odd operator and of its inverters, and prints none of its formulas.
+The readings here are the textbook ones:
+
+* Gauge action (Wilson plaquette, SU(2)):
+  ``S_g = beta sum_{x, mu<nu} (1 - 1/2 Re tr P_mn(x))``.
+* Pseudofermion action on even sites: ``S_f = Re <eta, (Mhat^+ Mhat)^-1 eta>``,
+  drawn as ``eta = Mhat^+ xi`` with ``P(xi) ~ exp(-xi^+ xi)``.
+* Momenta p_a(x, mu), a = 1..3, kinetic energy ``1/2 sum p_a^2``; the flow
+  ``dU/dt = i (p.s/2) U``, ``dp_a/dt = -F_a`` with ``F_a = dS/dw_a`` under
+  ``U -> exp(i w.s/2) U`` conserves ``H = 1/2 sum p^2 + S_g + S_f``.
+* Integrators: leapfrog (half momentum steps at the ends) and Omelyan's
+  second-order minimum-norm scheme (lambda = 0.1931833275037836).
+
+Pinned in tests/test_oracle_hmc.py: the gauge force against central finite
+differences of S_g, the link update against a matrix exponential,
+reversibility of both integrators, second-order scaling of Delta H with the
+step size, and the fermion part through ``oracle.force`` (pinned by finite
+differences of a dense solve in tests/test_oracle_pins.py).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+LEAPFROG, OMELYAN = 0, 1
+OMELYAN_LAMBDA = 0.1931833275037836
+
+_SIG = [np.array([[0, 1], [1, 0]], dtype=complex), np.array([[0, -1j], [1j, 0]]),
+        np.array([[1, 0], [0, -1]], dtype=complex)]
+
+
+def _su2(q):
+    """2x2 matrices a0 + i a.s of quaternions [..., 4]."""
+    a0, a1, a2, a3 = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    m = np.empty(q.shape[:-1] + (2, 2), dtype=complex)
+    m[..., 0, 0] = a0 + 1j * a3
+    m[..., 0, 1] = a2 + 1j * a1
+    m[..., 1, 0] = -a2 + 1j * a1
+    m[..., 1, 1] = a0 - 1j * a3
+    return m
+
+
+def _quat(m):
+    """Quaternion of a 2x2 matrix of the form a0 + i a.s."""
+    return np.stack([m[..., 0, 0].real, m[..., 0, 1].imag, m[..., 0, 1].real, m[..., 0, 0].imag], axis=-1)
+
+
+def _shift(dims, mu, step):
+    idx = np.arange(int(np.prod(dims))).reshape(dims)
+    return np.roll(idx, -step, axis=mu).reshape(-1)
+
+
+def gauge_action(dims, q, beta: float) -> float:
+    """S_g = beta sum_{x, mu<nu} (1 - 1/2 Re tr P_mn(x)), from the oracle's plaquette."""
+    from . import plaquette
+
+    V = int(np.prod(dims))
+    return beta * 6 * V * (1.0 - plaquette(dims, q))
+
+
+def staples(dims, q, mu: int) -> np.ndarray:
+    """V_mu(x) = sum_{nu != mu} [U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+ + U_nu(x+mu-nu)^+ U_mu(x-nu)^+ U_nu(x-nu)],
+    so that every plaquette containing U_mu(x) is tr(U_mu(x) V_mu(x)) (summed): [V, 2, 2]."""
+    U = _su2(q)
+    dag = lambda m: np.conj(np.swapaxes(m, -1, -2))  # noqa: E731
+    mm = lambda a, b: np.einsum("xab,xbc->xac", a, b)  # noqa: E731
+    fm = _shift(dims, mu, 1)
+    S = np.zeros((U.shape[1], 2, 2), dtype=complex)
+    for nu in range(4):
+        if nu == mu:
+            continue
+        fn, bn = _shift(dims, nu, 1), _shift(dims, nu, -1)
+        fm_bn = _shift(dims, nu, -1)[fm]  # x + mu - nu
+        S += mm(mm(U[nu][fm], dag(U[mu][fn])), dag(U[nu]))
+        S += mm(mm(dag(U[nu][fm_bn]), dag(U[mu][bn])), U[nu][bn])
+    return S
+
+
+def gauge_force(dims, q, beta: float) -> np.ndarray:
+    """F[mu, x, a] = dS_g/dw_a under U_mu(x) -> exp(i w.s/2) U_mu(x):
+    S_g holds U_mu(x) as -beta/2 Re tr(U V) + const, so F_a = -beta/2 Re tr((i s_a/2) U V)."""
+    U = _su2(q)
+    F = np.zeros((4, U.shape[1], 3))
+    for mu in range(4):
+        W = np.einsum("xab,xbc->xac", U[mu], staples(dims, q, mu))
+        for a in range(3):
+            F[mu, :, a] = -0.5 * beta * np.einsum("ab,xba->x", 0.5j * _SIG[a], W).real
+    return F
+
+
+def link_update(q, p, eps: float) -> np.ndarray:
+    """U -> exp(i eps p.s/2) U for every link (exp(i t n.s) = cos t + i sin t n.s)."""
+    norm = np.linalg.norm(p, axis=-1)
+    th = 0.5 * eps * norm
+    with np.errstate(invalid="ignore", divide="ignore"):
+        n = np.where(norm[..., None] > 0, p / norm[..., None], 0.0)
+    E = np.zeros(q.shape[:-1] + (2, 2), dtype=complex)
+    E[..., 0, 0] = np.cos(th)
+    E[..., 1, 1] = np.cos(th)
+    for a in range(3):
+        E += 1j * (np.sin(th) * n[..., a])[..., None, None] * _SIG[a]
+    return _quat(np.einsum("...ab,...bc->...ac", E, _su2(q)))
+
+
+def kinetic(p) -> float:
+    return 0.5 * float(np.sum(p * p))
+
+
+class Fermions:
+    """The pseudofermion part for the links q: S_f and its force (one CG solve)."""
+
+    def __init__(self, dims, m0: float, eta, bc=0, tol: float = 1e-13):
+        self.dims, self.m0, self.eta, self.bc, self.tol = dims, m0, eta, bc, tol
+        self.iters = 0
+
+    def solve(self, q):
+        from . import cg, expand_links
+
+        L = expand_links(self.dims, 2, q)
+        x, it, tr, ok = cg(self.dims, L, self.m0, self.eta, tol=self.tol, maxiter=50000, bc=self.bc)
+        assert ok, tr
+        self.iters += it
+        return L, x
+
+    def action(self, q) -> float:
+        _, x = self.solve(q)
+        return float(np.vdot(self.eta, x).real)
+
+    def force(self, q) -> np.ndarray:
+        """dS_f/dw = 2c dRe<a, H b>/dw with a = (Y, H_eo^+ Y), b = (X, H_oe X), X = (Mhat^+ Mhat)^-1 eta,
+        Y = Mhat X, c = 1/(4 (4+m0))."""
+        from . import force, gamma5, hop, parity_mask, schur
+
+        L, X = self.solve(q)
+        d, bc = self.dims, self.bc
+        Y = schur(d, L, self.m0, X, bc=bc)
+        Z = hop(d, L, X, parity=1, bc=bc)
+        W = gamma5(hop(d, L, gamma5(Y), parity=1, bc=bc))
+        even = parity_mask(d) == 0
+        a = np.where(even[:, None, None], Y, W)
+        b = np.where(even[:, None, None], X, Z)
+        return 2.0 / (4.0 * (4.0 + self.m0)) * force(d, L, a, b, bc=bc)
+
+
+def trajectory(dims, q, p, beta: float, n_steps: int, tau: float, integrator: int = LEAPFROG, fermions=None):
+    """One MD trajectory from (q, p).  Returns (q, p, info) with info holding
+    H at both ends and its parts."""
+    q = np.array(q, dtype=float)
+    p = np.array(p, dtype=float)
+    eps = tau / n_steps
+
+    def force(qq):
+        F = gauge_force(dims, qq, beta)
+        if fermions is not None:
+            F = F + fermions.force(qq)
+        return F
+
+    def hamiltonian(qq, pp):
+        parts = {"kinetic": kinetic(pp), "gauge": gauge_action(dims, qq, beta),
+                 "fermion": fermions.action(qq) if fermions is not None else 0.0}
+        return sum(parts.values()), parts
+
+    H0, parts0 = hamiltonian(q, p)
+    if integrator == LEAPFROG:
+        for _ in range(n_steps):
+            p = p - 0.5 * eps * force(q)
+            q = link_update(q, p, eps)
+            p = p - 0.5 * eps * force(q)
+    elif integrator == OMELYAN:
+        lam = OMELYAN_LAMBDA
+        for _ in range(n_steps):
+            p = p - lam * eps * force(q)
+            q = link_update(q, p, 0.5 * eps)
+            p = p - (1.0 - 2.0 * lam) * eps * force(q)
+            q = link_update(q, p, 0.5 * eps)
+            p = p - lam * eps * force(q)
+    else:
+        raise ValueError("integrator: LEAPFROG or OMELYAN")
+    H1, parts1 = hamiltonian(q, p)
+    return q, p, {"H0": H0, "H1": H1, "dH": H1 - H0, "start": parts0, "end": parts1}

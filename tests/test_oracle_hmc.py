@@ -1,0 +1,120 @@
+"""Pins of the oracle's HMC molecular dynamics (oracle/hmc.py).
+
+The paper (arXiv:2411.18511) names HMC as the consumer of the even-odd solver
+without writing it down; the oracle takes the textbook scheme, and these
+tests tie it to facts that do not come from it:
+
+* the gauge force equals central finite differences of the gauge action (the
+  action itself comes from the plaquette, pinned in test_oracle_pins.py);
+* the link update equals the matrix exponential (scipy.linalg.expm);
+* leapfrog and Omelyan trajectories are reversible: flipping the momenta at
+  the end and integrating again returns to the start;
+* both are second-order integrators: halving the step size divides Delta H
+  by about four;
+* the fermion force is oracle.force composed as in the HMC (that composition
+  is pinned against finite differences of a dense solve in test_oracle_pins.py).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import hmc
+
+RNG = np.random.default_rng(777)
+
+
+def smeared(dims, seed):
+    q, _, _ = synth.ape_smear_to_plaquette(synth.haar_links(dims, seed), dims, 0.6)
+    return q
+
+
+def momenta(dims, seed):
+    return np.random.default_rng(seed).normal(size=(4, int(np.prod(dims)), 3))
+
+
+def pseudofermion(dims, m0, seed):
+    """A Gaussian even-site pseudofermion field (its distribution does not
+    matter to these properties of the integrator)."""
+    xi = synth.gaussian_spinor(dims, 2, seed) / np.sqrt(2.0)
+    xi[oracle.parity_mask(dims) == 1] = 0
+    return xi
+
+
+def exp_update(q, mu, x, w, eps):
+    """U_mu(x) -> exp(i eps w.s/2) U_mu(x)."""
+    out = q.copy()
+    out[mu, x] = hmc.link_update(q[mu, x][None], w[None], eps)[0]
+    return out
+
+
+def test_gauge_force_matches_finite_differences():
+    dims = (4, 2, 2, 4)
+    V = int(np.prod(dims))
+    beta = 2.3
+    q = synth.haar_links(dims, 11)
+    F = hmc.gauge_force(dims, q, beta)
+    eps = 1e-5
+    for _ in range(12):
+        mu, x = RNG.integers(4), RNG.integers(V)
+        w = RNG.normal(size=3)
+        fd = (hmc.gauge_action(dims, exp_update(q, mu, x, w, eps), beta)
+              - hmc.gauge_action(dims, exp_update(q, mu, x, w, -eps), beta)) / (2 * eps)
+        assert abs(fd - F[mu, x] @ w) < 1e-7 * max(1.0, abs(fd)), (fd, F[mu, x] @ w)
+
+
+def test_link_update_is_the_matrix_exponential():
+    from scipy.linalg import expm
+
+    dims = (2, 2, 2, 2)
+    q = synth.haar_links(dims, 21)
+    p = momenta(dims, 22)
+    eps = 0.37
+    qn = hmc.link_update(q, p, eps)
+    s = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+    for mu in range(4):
+        for x in range(0, q.shape[1], 3):
+            X = 0.5j * eps * sum(p[mu, x, a] * s[a] for a in range(3))
+            want = expm(X) @ hmc._su2(q[mu, x])
+            np.testing.assert_allclose(hmc._su2(qn[mu, x]), want, atol=1e-14)
+    np.testing.assert_allclose(np.linalg.norm(qn, axis=-1), 1.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("integrator", [hmc.LEAPFROG, hmc.OMELYAN])
+@pytest.mark.parametrize("with_fermions", [False, True])
+def test_reversibility(integrator, with_fermions):
+    dims = (4, 2, 2, 2) if with_fermions else (4, 4, 2, 2)
+    beta, m0 = 2.2, 0.1
+    q = smeared(dims, 31)
+    p = momenta(dims, 32)
+    ferm = hmc.Fermions(dims, m0, pseudofermion(dims, m0, 33), bc=1) if with_fermions else None
+    q1, p1, i1 = hmc.trajectory(dims, q, p, beta, 4, 0.4, integrator, ferm)
+    q2, p2, i2 = hmc.trajectory(dims, q1, -p1, beta, 4, 0.4, integrator, ferm)
+    assert np.abs(q2 - q).max() < 1e-10
+    assert np.abs(-p2 - p).max() < 1e-9
+    assert abs(i1["dH"] + i2["dH"]) < 1e-9
+    assert np.abs(q1 - q).max() > 1e-3  # it moved
+
+
+@pytest.mark.parametrize("integrator", [hmc.LEAPFROG, hmc.OMELYAN])
+@pytest.mark.parametrize("with_fermions", [False, True])
+def test_delta_h_is_second_order(integrator, with_fermions):
+    dims = (4, 2, 2, 2) if with_fermions else (4, 4, 4, 4)
+    beta, m0 = 2.2, 0.1
+    q = smeared(dims, 41)
+    p = momenta(dims, 42)
+    ferm = hmc.Fermions(dims, m0, pseudofermion(dims, m0, 43)) if with_fermions else None
+    dh = [abs(hmc.trajectory(dims, q, p, beta, n, 0.5, integrator, ferm)[2]["dH"]) for n in (8, 16, 32)]
+    assert 3.8 < dh[0] / dh[1] < 4.2 and 3.8 < dh[1] / dh[2] < 4.2, dh
+
+
+def test_omelyan_error_is_far_below_leapfrog():
+    """The minimum-norm scheme's leading error coefficient is an order of magnitude
+    below leapfrog's (Omelyan et al.); at equal step counts Delta H is far smaller."""
+    dims = (4, 4, 4, 4)
+    q = smeared(dims, 51)
+    p = momenta(dims, 52)
+    lf = abs(hmc.trajectory(dims, q, p, 2.2, 16, 0.5, hmc.LEAPFROG)[2]["dH"])
+    om = abs(hmc.trajectory(dims, q, p, 2.2, 16, 0.5, hmc.OMELYAN)[2]["dH"])
+    assert om < lf / 5, (om, lf)
