@@ -309,6 +309,75 @@ hr_status hr_solve_full_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const hr
                                hr_system system, const void *gauge, const void *clover, const void *b, void *x,
                                hr_solve_info *info, void *work, size_t work_bytes, hr_stream stream);
 
+/* ---------------------------------------------------------------------- */
+/* HMC molecular dynamics (Sec. 1 and 2.1 name the HMC as the consumer)      */
+/* ---------------------------------------------------------------------- */
+
+/* SU(2) with two flavours of even-odd preconditioned Wilson fermions in the
+ * fundamental representation; the paper writes no formula, these are the
+ * textbook ones:
+ *   S_g = beta sum_{x, mu<nu} (1 - 1/2 Re tr P_mn(x))   (Wilson plaquette)
+ *   S_f = Re <eta, (Mhat^+ Mhat)^-1 eta>               (pseudofermion on even sites)
+ *   H = 1/2 sum p_a(x,mu)^2 + S_g + S_f, momenta p in su(2) (3 reals per link),
+ *   flow U -> exp(i eps p.s/2) U, p -> p - eps F, F_a = dS/dw_a under
+ *   U -> exp(i w.s/2) U (the force convention of hr_force).
+ * Links: canonical quaternions, device double[4][V][4]; momenta and forces:
+ * device double[4][V][3], lexicographic sites. */
+
+/* force[mu][x][a] += coeff * dS_g/dw_a (F_a = beta/2 vec(U V)_a, V the staple sum). */
+hr_status hr_gauge_force(hr_ctx *ctx, hr_lattice lat, double beta, const double *gauge, double coeff,
+                         double *force, hr_stream stream);
+/* *action = S_g (synchronises the stream). */
+hr_status hr_gauge_action(hr_ctx *ctx, hr_lattice lat, double beta, const double *gauge, double *action,
+                          hr_stream stream);
+/* U_mu(x) <- exp(i eps p_mu(x).s/2) U_mu(x) for every link, renormalised to unit length. */
+hr_status hr_link_update(hr_ctx *ctx, hr_lattice lat, double eps, const double *mom, double *gauge,
+                         hr_stream stream);
+/* mom <- mom - eps force. */
+hr_status hr_mom_update(hr_ctx *ctx, hr_lattice lat, double eps, const double *force, double *mom,
+                        hr_stream stream);
+/* *energy = 1/2 sum mom^2 (synchronises the stream). */
+hr_status hr_kinetic_energy(hr_ctx *ctx, hr_lattice lat, const double *mom, double *energy, hr_stream stream);
+
+typedef enum { HR_INTEGRATOR_LEAPFROG = 0, HR_INTEGRATOR_OMELYAN = 1 } hr_integrator;
+
+typedef struct {
+    double beta;              /* gauge coupling                                       */
+    double m0;                /* Wilson mass of the two fundamental flavours           */
+    int fermions;             /* 0: pure gauge; 1: with the pseudofermion eta          */
+    int n_steps;              /* integration steps per trajectory (>= 1)               */
+    double tau;               /* trajectory length (> 0)                               */
+    hr_integrator integrator; /* leapfrog, or Omelyan's minimum-norm 2nd-order scheme  */
+    hr_solver_opts solver;    /* CG of the force and of S_f (tol, inner precision, ...) */
+} hr_hmc_params;
+
+typedef struct {
+    double dH;                                         /* H(end) - H(start)          */
+    double kinetic_start, kinetic_end;
+    double gauge_action_start, gauge_action_end;
+    double fermion_action_start, fermion_action_end;
+    double plaquette;                                  /* <1/2 tr P> at the end      */
+    int cg_iters;                                      /* summed over the solves     */
+    int solves;
+    double seconds;                                    /* host wall time             */
+} hr_hmc_info;
+
+/* Work bytes of hr_hmc_trajectory (0 if the parameters are invalid). */
+size_t hr_hmc_workspace_bytes(hr_lattice lat, const hr_hmc_params *prm);
+
+/* One molecular-dynamics trajectory of n_steps steps of length tau / n_steps
+ * from (gauge, mom), both updated in place; eta: packed HR_F64 even spinor
+ * (prm->fermions; the caller draws it as Mhat^+ xi with P(xi) ~ exp(-xi^+ xi)),
+ * NULL for pure gauge.  Leapfrog: p -= eps/2 F, U <- exp(i eps p) U,
+ * p -= eps/2 F; Omelyan: p -= l eps F, U <- exp(i eps/2 p) U, p -= (1-2l) eps F,
+ * U <- exp(i eps/2 p) U, p -= l eps F, l = 0.1931833275037836; the force of
+ * the current links is reused between steps.  Each fermion force and S_f takes
+ * one hr_cg_solve (from x = 0) on the packed links (lat.bc applies).  The
+ * Metropolis test on info->dH and the draw of mom and eta are the caller's.
+ * Synchronises the stream. */
+hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *prm, double *gauge, double *mom,
+                            const void *eta, hr_hmc_info *info, void *work, size_t work_bytes, hr_stream stream);
+
 /* Work bytes of hr_cg_solve_batch for these lattices (0 if invalid). */
 size_t hr_cg_batch_workspace_bytes(int n_lat, const hr_lattice *lats, hr_rep rep);
 

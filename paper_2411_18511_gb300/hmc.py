@@ -1,0 +1,67 @@
+"""Hybrid Monte Carlo for SU(2) with two flavours of even-odd preconditioned
+Wilson fermions (fundamental) on one GPU: the Markov chain around
+``hr_hmc_trajectory`` (the molecular dynamics runs in the library's kernels).
+
+Each step draws Gaussian momenta and a pseudofermion eta = Mhat^+ xi with
+P(xi) ~ exp(-xi^+ xi), integrates one trajectory, and accepts the new links
+with probability min(1, exp(-dH)); a rejected trajectory restores the links.
+The random numbers come from a seeded torch generator on the device.
+"""
+
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import fields, hr
+
+
+class HMC:
+    def __init__(self, ctx: hr.Context, dims, beta: float, m0: float = 0.0, fermions: bool = True,
+                 n_steps: int = 10, tau: float = 1.0, integrator: int = hr.HR_INTEGRATOR_OMELYAN,
+                 solver: hr.hr_solver_opts | None = None, seed: int = 0, device="cuda"):
+        self.ctx, self.dims, self.device = ctx, dims, device
+        self.prm = hr.hr_hmc_params_default(beta, m0, fermions, n_steps, tau, integrator)
+        if solver is not None:
+            self.prm.solver = solver
+        self.work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(dims, self.prm), device)
+        self.V = fields.volume(dims)
+        self.gen = torch.Generator(device=device)
+        self.gen.manual_seed(int(seed))
+        self.accepted = 0
+        self.trajectories = 0
+
+    def draw_momenta(self) -> torch.Tensor:
+        return torch.randn((4, self.V, 3), dtype=torch.float64, device=self.device, generator=self.gen)
+
+    def draw_pseudofermion(self, q: torch.Tensor) -> torch.Tensor:
+        """Packed even eta = Mhat^+ xi for the links q, xi complex Gaussian with <|xi|^2> = 1."""
+        d = self.dims
+        shape = (self.V, 4, 2)
+        xi = torch.complex(torch.randn(shape, dtype=torch.float64, device=self.device, generator=self.gen),
+                           torch.randn(shape, dtype=torch.float64, device=self.device, generator=self.gen))
+        xi = xi / math.sqrt(2.0)
+        gauge = fields.pack_gauge(self.ctx, d, hr.HR_FUND, hr.HR_F64, q)
+        xp = fields.pack_spinor(self.ctx, d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, xi)
+        eta = fields.empty_spinor(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, device=self.device)
+        work = fields.empty_bytes(hr.hr_dirac_workspace_bytes(d, hr.HR_FUND, hr.HR_F64, hr.HR_OP_SCHUR_DAG),
+                                  self.device)
+        hr.hr_dirac_eo(self.ctx, d, self.prm.m0, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, hr.HR_OP_SCHUR_DAG, 1,
+                       gauge, xp, eta, work)
+        return eta
+
+    def step(self, q: torch.Tensor):
+        """One HMC update of the links q (device double[4][V][4], in place).
+        Returns (accepted, hr_hmc_info)."""
+        backup = q.clone()
+        p = self.draw_momenta()
+        eta = self.draw_pseudofermion(q) if self.prm.fermions else None
+        info = hr.hr_hmc_trajectory(self.ctx, self.dims, self.prm, q, p, eta, self.work)
+        u = torch.rand((), dtype=torch.float64, device=self.device, generator=self.gen).item()
+        accept = info.dH <= 0.0 or u < math.exp(-info.dH)
+        if not accept:
+            q.copy_(backup)
+        self.trajectories += 1
+        self.accepted += int(accept)
+        return accept, info

@@ -25,6 +25,7 @@ HR_EVEN, HR_ODD, HR_FULL = 0, 1, 2
 HR_OP_HOP, HR_OP_SCHUR, HR_OP_SCHUR_DAG, HR_OP_NORMAL = 0, 1, 2, 3
 HR_SYSTEM_D, HR_SYSTEM_DDAG_D = 0, 1
 HR_CLOVER_SW, HR_CLOVER_EXP = 0, 1
+HR_INTEGRATOR_LEAPFROG, HR_INTEGRATOR_OMELYAN = 0, 1
 
 
 def HR_BC_ANTIPERIODIC(mu: int) -> int:
@@ -46,7 +47,8 @@ EXPORTED = [
     "hr_tune_lookup", "hr_cg_batch_workspace_bytes", "hr_cg_solve_batch", "hr_solve_full_workspace_bytes",
     "hr_solve_full", "hr_clover_packed_bytes", "hr_clover_build", "hr_clover_apply", "hr_dirac_apply_clover",
     "hr_dirac_eo_clover", "hr_cg_clover_workspace_bytes", "hr_cg_solve_clover",
-    "hr_solve_full_clover_workspace_bytes", "hr_solve_full_clover",
+    "hr_solve_full_clover_workspace_bytes", "hr_solve_full_clover", "hr_gauge_force", "hr_gauge_action",
+    "hr_link_update", "hr_mom_update", "hr_kinetic_energy", "hr_hmc_workspace_bytes", "hr_hmc_trajectory",
 ]
 
 
@@ -80,6 +82,20 @@ class hr_solver_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner_prec", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("n_rhs", ctypes.c_int),
                 ("x0_is_guess", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class hr_hmc_params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("m0", ctypes.c_double), ("fermions", ctypes.c_int),
+                ("n_steps", ctypes.c_int), ("tau", ctypes.c_double), ("integrator", ctypes.c_int),
+                ("solver", hr_solver_opts)]
+
+
+class hr_hmc_info(ctypes.Structure):
+    _fields_ = [("dH", ctypes.c_double), ("kinetic_start", ctypes.c_double), ("kinetic_end", ctypes.c_double),
+                ("gauge_action_start", ctypes.c_double), ("gauge_action_end", ctypes.c_double),
+                ("fermion_action_start", ctypes.c_double), ("fermion_action_end", ctypes.c_double),
+                ("plaquette", ctypes.c_double), ("cg_iters", ctypes.c_int), ("solves", ctypes.c_int),
+                ("seconds", ctypes.c_double)]
 
 
 class hr_tune_result(ctypes.Structure):
@@ -150,6 +166,14 @@ def lib():
                 "hr_solve_full_clover_workspace_bytes": ([LAT, I, ctypes.POINTER(hr_solver_opts), I], S),
                 "hr_solve_full_clover": ([P, LAT, I, ctypes.POINTER(hr_solver_opts), I, P, P, P, P,
                                           ctypes.POINTER(hr_solve_info), P, S, P], I),
+                "hr_gauge_force": ([P, LAT, D, P, D, P, P], I),
+                "hr_gauge_action": ([P, LAT, D, P, ctypes.POINTER(D), P], I),
+                "hr_link_update": ([P, LAT, D, P, P, P], I),
+                "hr_mom_update": ([P, LAT, D, P, P, P], I),
+                "hr_kinetic_energy": ([P, LAT, P, ctypes.POINTER(D), P], I),
+                "hr_hmc_workspace_bytes": ([LAT, ctypes.POINTER(hr_hmc_params)], S),
+                "hr_hmc_trajectory": ([P, LAT, ctypes.POINTER(hr_hmc_params), P, P, P,
+                                       ctypes.POINTER(hr_hmc_info), P, S, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -431,6 +455,74 @@ def hr_solve_full_clover(ctx: Context, dims, rep, opts: hr_solver_opts, system, 
     if raise_on_error and rc not in (HR_OK, HR_ERR_NOT_CONVERGED):
         ctx.check(rc)
     return rc, info
+
+
+# ---- HMC molecular dynamics
+
+def _links(dims):
+    return 4 * _vol(dims)
+
+
+def hr_gauge_force(ctx: Context, dims, beta, gauge, coeff, force, stream=None):
+    _need(gauge, _links(dims) * 4 * 8, "gauge")
+    _need(force, _links(dims) * 3 * 8, "force")
+    return ctx.check(lib().hr_gauge_force(ctx.handle, lattice(dims), float(beta), _ptr(gauge), float(coeff),
+                                          _ptr(force), _stream(stream)))
+
+
+def hr_gauge_action(ctx: Context, dims, beta, gauge, stream=None) -> float:
+    _need(gauge, _links(dims) * 4 * 8, "gauge")
+    out = ctypes.c_double(0.0)
+    ctx.check(lib().hr_gauge_action(ctx.handle, lattice(dims), float(beta), _ptr(gauge), ctypes.byref(out),
+                                    _stream(stream)))
+    return out.value
+
+
+def hr_link_update(ctx: Context, dims, eps, mom, gauge, stream=None):
+    _need(mom, _links(dims) * 3 * 8, "mom")
+    _need(gauge, _links(dims) * 4 * 8, "gauge")
+    return ctx.check(lib().hr_link_update(ctx.handle, lattice(dims), float(eps), _ptr(mom), _ptr(gauge),
+                                          _stream(stream)))
+
+
+def hr_mom_update(ctx: Context, dims, eps, force, mom, stream=None):
+    _need(force, _links(dims) * 3 * 8, "force")
+    _need(mom, _links(dims) * 3 * 8, "mom")
+    return ctx.check(lib().hr_mom_update(ctx.handle, lattice(dims), float(eps), _ptr(force), _ptr(mom),
+                                         _stream(stream)))
+
+
+def hr_kinetic_energy(ctx: Context, dims, mom, stream=None) -> float:
+    _need(mom, _links(dims) * 3 * 8, "mom")
+    out = ctypes.c_double(0.0)
+    ctx.check(lib().hr_kinetic_energy(ctx.handle, lattice(dims), _ptr(mom), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def hr_hmc_params_default(beta: float, m0: float = 0.0, fermions: bool = True, n_steps: int = 10,
+                          tau: float = 1.0, integrator: int = HR_INTEGRATOR_OMELYAN) -> hr_hmc_params:
+    prm = hr_hmc_params()
+    prm.beta, prm.m0, prm.fermions = float(beta), float(m0), int(bool(fermions))
+    prm.n_steps, prm.tau, prm.integrator = int(n_steps), float(tau), int(integrator)
+    prm.solver = hr_solver_default_opts()
+    return prm
+
+
+def hr_hmc_workspace_bytes(dims, prm: hr_hmc_params) -> int:
+    return int(lib().hr_hmc_workspace_bytes(lattice(dims), ctypes.byref(prm)))
+
+
+def hr_hmc_trajectory(ctx: Context, dims, prm: hr_hmc_params, gauge, mom, eta, work, stream=None):
+    """One MD trajectory, gauge and mom updated in place.  Returns hr_hmc_info."""
+    _need(gauge, _links(dims) * 4 * 8, "gauge")
+    _need(mom, _links(dims) * 3 * 8, "mom")
+    if prm.fermions:
+        _need(eta, hr_spinor_packed_bytes(dims, HR_FUND, HR_F64, HR_EVEN, 1), "eta")
+    info = hr_hmc_info()
+    wb = 0 if work is None else work.numel() * work.element_size()
+    ctx.check(lib().hr_hmc_trajectory(ctx.handle, lattice(dims), ctypes.byref(prm), _ptr(gauge), _ptr(mom),
+                                      _ptr(eta), ctypes.byref(info), _ptr(work), wb, _stream(stream)))
+    return info
 
 
 def hr_force(ctx: Context, dims, gauge, a_full, b_full, beta, force, stream=None):

@@ -1,0 +1,152 @@
+"""HMC molecular dynamics on the GPU against the oracle (oracle/hmc.py, pinned in
+tests/test_oracle_hmc.py): gauge force and action, link and momentum updates,
+kinetic energy, and whole leapfrog / Omelyan trajectories with and without the
+pseudofermion (same inputs; CG to 1e-13 on both sides), reversibility, and the
+Markov chain driver."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import hmc as ohmc
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2411_18511_gb300 import fields, hr  # noqa: E402
+from paper_2411_18511_gb300.hmc import HMC  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return hr.Context(0)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def smeared(dims, seed):
+    q, _, _ = synth.ape_smear_to_plaquette(synth.haar_links(dims, seed), dims, 0.6)
+    return q
+
+
+@pytest.mark.parametrize("dims", [(4, 6, 2, 4), (8, 4, 4, 6)])
+def test_gauge_force_and_action(ctx, dims):
+    beta = 2.3
+    q = synth.haar_links(dims, 11)
+    F = torch.zeros((4, int(np.prod(dims)), 3), dtype=torch.float64, device="cuda")
+    hr.hr_gauge_force(ctx, dims, beta, dev(q), 1.0, F)
+    want = ohmc.gauge_force(dims, q, beta)
+    assert rel(F.cpu().numpy(), want) <= 1e-13
+    hr.hr_gauge_force(ctx, dims, beta, dev(q), -0.5, F)  # accumulates
+    assert rel(F.cpu().numpy(), 0.5 * want) <= 1e-13
+    S = hr.hr_gauge_action(ctx, dims, beta, dev(q))
+    assert abs(S - ohmc.gauge_action(dims, q, beta)) <= 1e-12 * abs(S)
+
+
+def test_updates_and_kinetic_energy(ctx):
+    dims = (4, 4, 2, 6)
+    V = int(np.prod(dims))
+    q = synth.haar_links(dims, 21)
+    p = np.random.default_rng(22).normal(size=(4, V, 3))
+    F = np.random.default_rng(23).normal(size=(4, V, 3))
+    qd, pd = dev(q), dev(p)
+    hr.hr_link_update(ctx, dims, 0.37, pd, qd)
+    np.testing.assert_allclose(qd.cpu().numpy(), ohmc.link_update(q, p, 0.37), atol=1e-14)
+    hr.hr_mom_update(ctx, dims, 0.25, dev(F), pd)
+    np.testing.assert_allclose(pd.cpu().numpy(), p - 0.25 * F, atol=1e-15)
+    K = hr.hr_kinetic_energy(ctx, dims, pd)
+    assert abs(K - ohmc.kinetic(p - 0.25 * F)) <= 1e-12 * K
+
+
+def eta_field(ctx, lat, m0, seed):
+    """A Gaussian even pseudofermion (full-lattice array) and its packed form."""
+    eta = synth.gaussian_spinor(lat, 2, seed) / np.sqrt(2.0)
+    eta[oracle.parity_mask(lat) == 1] = 0
+    packed = fields.pack_spinor(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, fields.spinor_to_device(eta))
+    return eta, packed
+
+
+def run_gpu(ctx, lat, q, p, prm, eta_packed):
+    qd, pd = dev(q), dev(p)
+    work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(lat, prm))
+    info = hr.hr_hmc_trajectory(ctx, lat, prm, qd, pd, eta_packed, work)
+    return qd.cpu().numpy(), pd.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("integrator", [hr.HR_INTEGRATOR_LEAPFROG, hr.HR_INTEGRATOR_OMELYAN])
+@pytest.mark.parametrize("fermions", [False, True])
+def test_trajectory_matches_oracle(ctx, integrator, fermions):
+    lat = hr.Lattice((4, 2, 2, 4), 1)
+    beta, m0 = 2.2, 0.1
+    q = smeared(lat, 31)
+    p = np.random.default_rng(32).normal(size=(4, int(np.prod(lat)), 3))
+    prm = hr.hr_hmc_params_default(beta, m0, fermions, 3, 0.3, integrator)
+    prm.solver.tol = 1e-13
+    eta, eta_p = eta_field(ctx, lat, m0, 33)
+    qg, pg, info = run_gpu(ctx, lat, q, p, prm, eta_p if fermions else None)
+    ferm = ohmc.Fermions(lat, m0, eta, bc=1) if fermions else None
+    qo, po, io = ohmc.trajectory(lat, q, p, beta, 3, 0.3, integrator, ferm)
+    assert np.abs(qg - qo).max() <= 1e-11
+    assert np.abs(pg - po).max() <= 1e-9
+    assert abs(info.dH - io["dH"]) <= 1e-9, (info.dH, io["dH"])
+    assert abs(info.gauge_action_end - io["end"]["gauge"]) <= 1e-9
+    assert abs(info.kinetic_end - io["end"]["kinetic"]) <= 1e-9
+    if fermions:
+        assert abs(info.fermion_action_end - io["end"]["fermion"]) <= 1e-9
+        assert info.solves >= 4 and info.cg_iters > 0
+    assert np.abs(qg - q).max() > 1e-3
+
+
+@pytest.mark.parametrize("inner", [hr.HR_F64, hr.HR_F16])
+def test_trajectory_is_reversible(ctx, inner):
+    lat = hr.Lattice((8, 8, 4, 4), 1)
+    beta, m0 = 2.2, 0.05
+    q = smeared(lat, 41)
+    p = np.random.default_rng(42).normal(size=(4, int(np.prod(lat)), 3))
+    prm = hr.hr_hmc_params_default(beta, m0, True, 5, 0.5, hr.HR_INTEGRATOR_OMELYAN)
+    prm.solver.tol = 1e-12
+    prm.solver.inner_prec = inner
+    _, eta_p = eta_field(ctx, lat, m0, 43)
+    q1, p1, i1 = run_gpu(ctx, lat, q, p, prm, eta_p)
+    q2, p2, i2 = run_gpu(ctx, lat, q1, -p1, prm, eta_p)
+    assert np.abs(q2 - q).max() <= 1e-9
+    assert np.abs(p2 + p).max() <= 1e-7
+    assert abs(i1.dH + i2.dH) <= 1e-7
+    assert abs(i1.dH) < 1.0
+
+
+def test_markov_chain(ctx):
+    lat = hr.Lattice((4, 4, 4, 4), 1)
+    q = dev(smeared(lat, 51))
+    chain = HMC(ctx, lat, beta=2.2, m0=0.1, fermions=True, n_steps=8, tau=0.5, seed=52)
+    plaq = []
+    for _ in range(4):
+        acc, info = chain.step(q)
+        assert np.isfinite(info.dH) and abs(info.dH) < 2.0
+        plaq.append(info.plaquette if acc else None)
+    assert chain.accepted >= 2
+    np.testing.assert_allclose(np.linalg.norm(q.cpu().numpy(), axis=-1), 1.0, atol=1e-13)
+
+
+def test_argument_checks(ctx):
+    lat = (4, 4, 4, 4)
+    prm = hr.hr_hmc_params_default(2.0, 0.1, True, 0, 1.0)
+    assert hr.hr_hmc_workspace_bytes(lat, prm) > 0
+    q = dev(synth.identity_links(lat))
+    p = torch.zeros((4, 256, 3), dtype=torch.float64, device="cuda")
+    work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(lat, prm))
+    with pytest.raises(hr.HrError):
+        hr.hr_hmc_trajectory(ctx, lat, prm, q, p, None, work)  # n_steps = 0
+    prm.n_steps = 2
+    with pytest.raises(hr.HrError):
+        hr.hr_hmc_trajectory(ctx, lat, prm, q, p, None, work)  # fermions without eta
