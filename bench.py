@@ -541,7 +541,55 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     out["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
     torch.cuda.empty_cache()
     out["batch_12"] = run_batch(ctx, torch, hr, fields, synth)
+    torch.cuda.empty_cache()
+    out["hmc_16"] = run_hmc(ctx, torch, hr, fields, synth)
     return out
+
+
+def run_hmc(ctx, torch, hr, fields, synth):
+    """16^4 HMC with two flavours of Wilson fermions (beta = 2.2, m0 = -0.2,
+    antiperiodic time, tau = 1): wall time of one trajectory (MD through
+    hr_hmc_trajectory, with its CG solves), Delta H, force evaluations, for
+    leapfrog and Omelyan at the same step count and with FP64 / FP16-inner
+    solvers; a short chain from the smeared start for the acceptance."""
+    from paper_2411_18511_gb300.hmc import HMC
+    lat = hr.Lattice((16, 16, 16, 16), 1)
+    beta, m0 = 2.2, -0.2
+    q0, _, plaq = synth.ape_smear_to_plaquette(synth.haar_links(lat, 1006), lat, 0.6)
+    qd0 = fields.gauge_to_device(q0)
+    # thermalisation: molecular dynamics from fresh momenta, kept without a Metropolis test
+    warm = HMC(ctx, lat, beta=beta, m0=m0, fermions=True, n_steps=12, tau=1.0, seed=3006)
+    for _ in range(6):
+        eta = warm.draw_pseudofermion(qd0)
+        info = hr.hr_hmc_trajectory(ctx, lat, warm.prm, qd0, warm.draw_momenta(), eta, warm.work)
+    del warm
+    out = {"lattice": list(lat), "beta": beta, "m0": m0, "tau": 1.0, "bc": "antiperiodic in time",
+           "smeared_start_plaquette": round(plaq, 4), "thermalised_plaquette": round(info.plaquette, 4),
+           "thermalisation": "6 Omelyan trajectories of 12 steps without accept/reject"}
+    for name, integ, steps, inner in (("leapfrog_f64", hr.HR_INTEGRATOR_LEAPFROG, 24, hr.HR_F64),
+                                      ("omelyan_f64", hr.HR_INTEGRATOR_OMELYAN, 12, hr.HR_F64),
+                                      ("omelyan_f16_inner", hr.HR_INTEGRATOR_OMELYAN, 12, hr.HR_F16)):
+        solver = hr.hr_solver_default_opts()
+        solver.inner_prec = inner
+        solver.reliable_delta = 0.01 if inner != hr.HR_F64 else 0.1
+        chain = HMC(ctx, lat, beta=beta, m0=m0, fermions=True, n_steps=steps, tau=1.0, integrator=integ,
+                    solver=solver, seed=2006)
+        q = qd0.clone()
+        secs, dhs, iters = [], [], []
+        for _ in range(4):
+            torch.cuda.synchronize()
+            acc, info = chain.step(q)
+            secs.append(info.seconds)
+            dhs.append(info.dH)
+            iters.append(info.cg_iters)
+        forces = steps + 1 if integ == hr.HR_INTEGRATOR_LEAPFROG else 2 * steps + 1
+        out[name] = {"n_steps": steps, "force_evaluations": forces,
+                     "trajectory_s_median": round(statistics.median(secs[1:]), 4),
+                     "dH": [round(float(x), 4) for x in dhs], "accepted": f"{chain.accepted}/{chain.trajectories}",
+                     "cg_iters_per_trajectory": int(statistics.median(iters)), "end_plaquette": round(info.plaquette, 4)}
+        del chain, q
+    return out
+
 
 
 def run_cg_clover(ctx, hr, fields, d32, q32, gauge, bp, xp, cg_wilson):
