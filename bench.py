@@ -375,27 +375,28 @@ def run_ours(args):
 
 
 def run_e2e(args, ctx, torch, hr, dims, rep, prec, psi, src, dst, step, stream, max_over_ranks, world,
-            bytes_step):
+            bytes_step, nbuf=3):
     """The same step through the public API from pinned host memory: H2D of the
     canonical spinor, pack, the two hops, unpack, D2H; all inside the timing.
-    Steps are pipelined over three streams with two device buffer sets, so the
-    H2D copy of step k+1 and the D2H copy of step k-1 overlap step k's kernels
-    (the link carries both directions at once); every step still moves its
-    whole input to the device and its whole result back."""
+    Steps are pipelined over three streams with three device buffer sets, so
+    the H2D copy of step k+1 and the D2H copy of step k-1 overlap step k's
+    kernels (the link carries both directions at once); every step still moves
+    its whole input to the device and its whole result back.  Beside it, the
+    same H2D and D2H copies alone (host_link): the ceiling the link sets."""
     host_in = torch.view_as_real(torch.from_numpy(psi)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    dev_in = [torch.empty(host_in.shape, dtype=torch.float64, device="cuda") for _ in range(2)]
-    dev_out = [torch.empty_like(dev_in[0]) for _ in range(2)]
+    dev_in = [torch.empty(host_in.shape, dtype=torch.float64, device="cuda") for _ in range(nbuf)]
+    dev_out = [torch.empty_like(dev_in[0]) for _ in range(nbuf)]
     s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
-    h2d_done = [torch.cuda.Event() for _ in range(2)]
-    comp_done = [torch.cuda.Event() for _ in range(2)]
-    d2h_done = [torch.cuda.Event() for _ in range(2)]
-    used = [False, False]
+    h2d_done = [torch.cuda.Event() for _ in range(nbuf)]
+    comp_done = [torch.cuda.Event() for _ in range(nbuf)]
+    d2h_done = [torch.cuda.Event() for _ in range(nbuf)]
+    used = [False] * nbuf
 
     def e2e_step(k):
-        b = k & 1
+        b = k % nbuf
         if used[b]:
-            s_h2d.wait_event(comp_done[b])  # step k-2 has read dev_in[b]
+            s_h2d.wait_event(comp_done[b])  # step k-nbuf has read dev_in[b]
         with torch.cuda.stream(s_h2d):
             dev_in[b].copy_(host_in, non_blocking=True)
         h2d_done[b].record(s_h2d)
@@ -403,7 +404,7 @@ def run_e2e(args, ctx, torch, hr, dims, rep, prec, psi, src, dst, step, stream, 
         hr.hr_spinor_pack(ctx, dims, rep, prec, hr.HR_FULL, 1, dev_in[b], src, stream)
         step()
         if used[b]:
-            stream.wait_event(d2h_done[b])  # step k-2's result has left dev_out[b]
+            stream.wait_event(d2h_done[b])  # step k-nbuf's result has left dev_out[b]
         hr.hr_spinor_unpack(ctx, dims, rep, prec, hr.HR_FULL, 1, dst, dev_out[b], stream)
         comp_done[b].record(stream)
         s_d2h.wait_event(comp_done[b])
@@ -412,23 +413,53 @@ def run_e2e(args, ctx, torch, hr, dims, rep, prec, psi, src, dst, step, stream, 
         d2h_done[b].record(s_d2h)
         used[b] = True
 
-    for k in range(3):
+    # warm-up: a whole untimed pass (the first pass through freshly pinned
+    # buffers runs about 10 % slower than the ones after it)
+    n_e2e = max(6, min(50, args.steps // 20))
+    for k in range(n_e2e):
         e2e_step(k)
     torch.cuda.synchronize()
-    n_e2e = max(6, min(50, args.steps // 20))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     s_h2d.wait_event(e0)
     s_d2h.wait_event(e0)
     for k in range(n_e2e):
-        e2e_step(3 + k)
-    stream.wait_event(d2h_done[(3 + n_e2e - 1) & 1])
+        e2e_step(n_e2e + k)
+    stream.wait_event(d2h_done[(2 * n_e2e - 1) % nbuf])
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / n_e2e)
+    # the host link's ceiling for this traffic: the same H2D and D2H copies
+    # alone, concurrent on their two streams, no kernels
+    for k in range(2):
+        with torch.cuda.stream(s_h2d):
+            dev_in[0].copy_(host_in, non_blocking=True)
+        with torch.cuda.stream(s_d2h):
+            host_out.copy_(dev_out[0], non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s_h2d.wait_event(e0)
+    s_d2h.wait_event(e0)
+    for k in range(n_e2e):
+        with torch.cuda.stream(s_h2d):
+            dev_in[0].copy_(host_in, non_blocking=True)
+        with torch.cuda.stream(s_d2h):
+            host_out.copy_(dev_out[0], non_blocking=True)
+    h2d_done[0].record(s_h2d)
+    d2h_done[0].record(s_d2h)
+    stream.wait_event(h2d_done[0])
+    stream.wait_event(d2h_done[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = max_over_ranks(e0.elapsed_time(e1) / n_e2e)
+    link_bytes = 2 * host_in.numel() * 8
     return {"value": round(world * bytes_step / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": int(host_in.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8),
             "ms_per_step": round(e2e_ms, 4),
+            "host_link": {"copies_only_ms_per_step": round(copy_ms, 4),
+                          "copies_only_gbs": round(link_bytes / (copy_ms * 1e-3) / 1e9, 1),
+                          "e2e_link_gbs": round(link_bytes / (e2e_ms * 1e-3) / 1e9, 1),
+                          "frac_of_copies_only": round(copy_ms / e2e_ms, 3)},
             "path": "pinned host canonical spinor -> H2D -> hr_spinor_pack -> 2x hr_dirac_eo -> "
                     "hr_spinor_unpack -> D2H, pipelined over 3 streams (H2D, kernels, D2H)"}
 
