@@ -883,9 +883,25 @@ __device__ inline void sum_partials(const double *partials, unsigned nparts, int
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int r = threadIdx.x & (nrhs - 1);
     const unsigned step = blockDim.x / nrhs;
-    double s = 0;
-#pragma unroll 4
-    for (unsigned b = threadIdx.x / nrhs; b < nparts; b += step) s += __ldcg(partials + (size_t)b * nrhs + r);
+    // sixteen independent accumulators keep sixteen L2 loads in flight per
+    // thread (a single running sum leaves this one block latency-bound when
+    // there are many partials, e.g. 4096 blocks x 32 right-hand sides);
+    // combined in a fixed order
+    constexpr int K = 16;
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    unsigned b = threadIdx.x / nrhs;
+    for (; b + (K - 1) * step < nparts; b += K * step) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += __ldcg(partials + (size_t)(b + k * step) * nrhs + r);
+    }
+    for (int k = 0; b < nparts; b += step, ++k) acc[k & (K - 1)] += __ldcg(partials + (size_t)b * nrhs + r);
+#pragma unroll
+    for (int w = K / 2; w > 0; w >>= 1)
+#pragma unroll
+        for (int k = 0; k < w; ++k) acc[k] += acc[k + w];
+    double s = acc[0];
     s = warp_sum_strided(s, nrhs);
     __syncthreads();
     if (lane < nrhs) smem[warp * 32 + lane] = s;
