@@ -15,6 +15,8 @@ The readings here are the textbook ones:
   ``U -> exp(i w.s/2) U`` conserves ``H = 1/2 sum p^2 + S_g + S_f``.
 * Integrators: leapfrog (half momentum steps at the ends) and Omelyan's
   second-order minimum-norm scheme (lambda = 0.1931833275037836).
+* Hasenbusch mass preconditioning: two pseudofermions, one at a heavier mass
+  and one for the ratio of the two determinants (class ``Hasenbusch``).
 
 Pinned in tests/test_oracle_hmc.py: the gauge force against central finite
 differences of S_g, the link update against a matrix exponential,
@@ -145,6 +147,62 @@ class Fermions:
         a = np.where(even[:, None, None], Y, W)
         b = np.where(even[:, None, None], X, Z)
         return 2.0 / (4.0 * (4.0 + self.m0)) * force(d, L, a, b, bc=bc)
+
+
+class Hasenbusch:
+    """Two flavours through Hasenbusch's mass preconditioning (two pseudofermions):
+    det(Mhat^+ Mhat) = det(Mhat_H^+ Mhat_H) det[(Mhat^+ Mhat) / (Mhat_H^+ Mhat_H)],
+    S = Re <eta, (Mhat_H^+ Mhat_H)^-1 eta> + Re <eta2, (Mhat^+ Mhat)^-1 eta2>,
+    eta2 = Mhat_H^+ phi (it depends on the links), Mhat_H the Schur operator at
+    the heavier mass m0_h.  The heat bath draws eta = Mhat_H^+ xi1 and
+    phi = Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2, so that S = |xi1|^2 + |xi2|^2.
+    The force of the second term adds, to the usual one, the variation of eta2:
+    2 Re <X2, dMhat_H^+ phi> = -2 c_H dRe <a', H b'> with a' = (g5 X2, H_eo^+ g5 X2),
+    b' = (g5 phi, H_oe g5 phi), c_H = 1/(4 (4 + m0_h))."""
+
+    def __init__(self, dims, m0: float, m0_h: float, eta, phi, bc=0, tol: float = 1e-13):
+        self.dims, self.m0, self.m0_h, self.bc, self.tol = dims, m0, m0_h, bc, tol
+        self.heavy = Fermions(dims, m0_h, eta, bc=bc, tol=tol)
+        self.phi = np.asarray(phi, dtype=np.complex128)
+        self.iters = 0
+
+    def _eta2(self, L):
+        from . import schur
+
+        return schur(self.dims, L, self.m0_h, self.phi, dagger=True, bc=self.bc)
+
+    def _ratio(self, q):
+        from . import cg, expand_links
+
+        L = expand_links(self.dims, 2, q)
+        eta2 = self._eta2(L)
+        x, it, tr, ok = cg(self.dims, L, self.m0, eta2, tol=self.tol, maxiter=50000, bc=self.bc)
+        assert ok, tr
+        self.iters += it
+        return L, eta2, x
+
+    def action(self, q) -> float:
+        _, eta2, x = self._ratio(q)
+        return self.heavy.action(q) + float(np.vdot(eta2, x).real)
+
+    def force(self, q) -> np.ndarray:
+        from . import force, gamma5, hop, parity_mask, schur
+
+        L, eta2, X = self._ratio(q)
+        d, bc = self.dims, self.bc
+        even = parity_mask(d) == 0
+
+        def pair(u, v):
+            """a = (u, H_eo^+ u), b = (v, H_oe v) as full fields."""
+            W = gamma5(hop(d, L, gamma5(u), parity=1, bc=bc))
+            Z = hop(d, L, v, parity=1, bc=bc)
+            return np.where(even[:, None, None], u, W), np.where(even[:, None, None], v, Z)
+
+        a, b = pair(schur(d, L, self.m0, X, bc=bc), X)
+        F = 2.0 / (4.0 * (4.0 + self.m0)) * force(d, L, a, b, bc=bc)
+        a2, b2 = pair(gamma5(X), gamma5(self.phi))
+        F = F - 2.0 / (4.0 * (4.0 + self.m0_h)) * force(d, L, a2, b2, bc=bc)
+        return F + self.heavy.force(q)
 
 
 def trajectory(dims, q, p, beta: float, n_steps: int, tau: float, integrator: int = LEAPFROG, fermions=None):

@@ -118,3 +118,74 @@ def test_omelyan_error_is_far_below_leapfrog():
     lf = abs(hmc.trajectory(dims, q, p, 2.2, 16, 0.5, hmc.LEAPFROG)[2]["dH"])
     om = abs(hmc.trajectory(dims, q, p, 2.2, 16, 0.5, hmc.OMELYAN)[2]["dH"])
     assert om < lf / 5, (om, lf)
+
+
+# ---------------------------------------------------------------- Hasenbusch
+
+def _dense_schur(dims, q, m0, bc):
+    from tests import dense_ref as dr
+
+    D = dr.dirac_dense(dims, q, 2, m0, bc)
+    Dee, Deo, Doe, Doo, e, o = dr.eo_blocks(dims, 2, D)
+    return Dee - Deo @ np.linalg.solve(Doo, Doe), e
+
+
+def _hasenbusch_fields(dims, q, m0, m0_h, bc, seed):
+    """eta = Mhat_H^+ xi1 and phi = Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2 from dense matrices."""
+    M, e = _dense_schur(dims, q, m0, bc)
+    MH, _ = _dense_schur(dims, q, m0_h, bc)
+    rng = np.random.default_rng(seed)
+    n = len(e)
+    xi1 = (rng.normal(size=n) + 1j * rng.normal(size=n)) / np.sqrt(2)
+    xi2 = (rng.normal(size=n) + 1j * rng.normal(size=n)) / np.sqrt(2)
+    V = int(np.prod(dims))
+    eta = np.zeros(V * 8, dtype=complex)
+    phi = np.zeros(V * 8, dtype=complex)
+    eta[e] = MH.conj().T @ xi1
+    phi[e] = MH @ np.linalg.solve(MH.conj().T @ MH, M.conj().T @ xi2)
+    return eta.reshape(V, 4, 2), phi.reshape(V, 4, 2), xi1, xi2
+
+
+def test_hasenbusch_heat_bath_and_force():
+    """S = |xi1|^2 + |xi2|^2 right after the heat bath, and the force equals
+    central finite differences of S evaluated with dense solves."""
+    dims = (2, 2, 2, 4)
+    V = int(np.prod(dims))
+    m0, m0_h, bc = 0.05, 0.6, 1
+    q = smeared(dims, 61)
+    eta, phi, xi1, xi2 = _hasenbusch_fields(dims, q, m0, m0_h, bc, 62)
+    ferm = hmc.Hasenbusch(dims, m0, m0_h, eta, phi, bc=bc)
+    S0 = ferm.action(q)
+    assert abs(S0 - (np.vdot(xi1, xi1).real + np.vdot(xi2, xi2).real)) < 1e-10 * S0
+
+    def S_dense(qq):
+        M, e = _dense_schur(dims, qq, m0, bc)
+        MH, _ = _dense_schur(dims, qq, m0_h, bc)
+        y1 = eta.reshape(-1)[e]
+        y2 = MH.conj().T @ phi.reshape(-1)[e]
+        return (np.vdot(y1, np.linalg.solve(MH.conj().T @ MH, y1)).real
+                + np.vdot(y2, np.linalg.solve(M.conj().T @ M, y2)).real)
+
+    assert abs(S_dense(q) - S0) < 1e-10 * S0
+    F = ferm.force(q)
+    eps = 1e-5
+    for _ in range(8):
+        mu, x = RNG.integers(4), RNG.integers(V)
+        w = RNG.normal(size=3)
+        fd = (S_dense(exp_update(q, mu, x, w, eps)) - S_dense(exp_update(q, mu, x, w, -eps))) / (2 * eps)
+        assert abs(fd - F[mu, x] @ w) <= 1e-6 * max(1.0, abs(fd)), (fd, F[mu, x] @ w)
+
+
+@pytest.mark.parametrize("integrator", [hmc.LEAPFROG, hmc.OMELYAN])
+def test_hasenbusch_trajectory_reversible_and_second_order(integrator):
+    dims = (4, 2, 2, 2)
+    m0, m0_h, bc = 0.05, 0.5, 1
+    q = smeared(dims, 71)
+    p = momenta(dims, 72)
+    eta, phi, _, _ = _hasenbusch_fields(dims, q, m0, m0_h, bc, 73)
+    ferm = hmc.Hasenbusch(dims, m0, m0_h, eta, phi, bc=bc)
+    q1, p1, i1 = hmc.trajectory(dims, q, p, 2.2, 4, 0.4, integrator, ferm)
+    q2, p2, i2 = hmc.trajectory(dims, q1, -p1, 2.2, 4, 0.4, integrator, ferm)
+    assert np.abs(q2 - q).max() < 1e-10 and np.abs(p2 + p).max() < 1e-9
+    dh = [abs(hmc.trajectory(dims, q, p, 2.2, n, 0.5, integrator, ferm)[2]["dH"]) for n in (8, 16)]
+    assert 3.8 < dh[0] / dh[1] < 4.2, dh
