@@ -349,6 +349,8 @@ typedef struct {
     double tau;               /* trajectory length (> 0)                               */
     hr_integrator integrator; /* leapfrog, or Omelyan's minimum-norm 2nd-order scheme  */
     hr_solver_opts solver;    /* CG of the force and of S_f (tol, inner precision, ...) */
+    int hasenbusch;           /* 1: Hasenbusch mass preconditioning (two pseudofermions) */
+    double m0_hasenbusch;     /* its heavier mass                                      */
 } hr_hmc_params;
 
 typedef struct {
@@ -368,7 +370,12 @@ size_t hr_hmc_workspace_bytes(hr_lattice lat, const hr_hmc_params *prm);
 /* One molecular-dynamics trajectory of n_steps steps of length tau / n_steps
  * from (gauge, mom), both updated in place; eta: packed HR_F64 even spinor
  * (prm->fermions; the caller draws it as Mhat^+ xi with P(xi) ~ exp(-xi^+ xi)),
- * NULL for pure gauge.  Leapfrog: p -= eps/2 F, U <- exp(i eps p) U,
+ * NULL for pure gauge.  With prm->hasenbusch (Hasenbusch's mass
+ * preconditioning, a standard HMC acceleration the paper cites in Sec. 2.2),
+ * S_f = Re<eta, (Mhat_H^+ Mhat_H)^-1 eta> + Re<eta2, (Mhat^+ Mhat)^-1 eta2>,
+ * eta2 = Mhat_H^+ phi, Mhat_H the Schur operator at m0_hasenbusch: eta is
+ * drawn as Mhat_H^+ xi1 and phi (packed HR_F64 even) as
+ * Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2; each force then takes two solves.  Leapfrog: p -= eps/2 F, U <- exp(i eps p) U,
  * p -= eps/2 F; Omelyan: p -= l eps F, U <- exp(i eps/2 p) U, p -= (1-2l) eps F,
  * U <- exp(i eps/2 p) U, p -= l eps F, l = 0.1931833275037836; the force of
  * the current links is reused between steps.  Each fermion force and S_f takes
@@ -376,7 +383,8 @@ size_t hr_hmc_workspace_bytes(hr_lattice lat, const hr_hmc_params *prm);
  * Metropolis test on info->dH and the draw of mom and eta are the caller's.
  * Synchronises the stream. */
 hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *prm, double *gauge, double *mom,
-                            const void *eta, hr_hmc_info *info, void *work, size_t work_bytes, hr_stream stream);
+                            const void *eta, const void *phi, hr_hmc_info *info, void *work, size_t work_bytes,
+                            hr_stream stream);
 
 /* Work bytes of hr_cg_solve_batch for these lattices (0 if invalid). */
 size_t hr_cg_batch_workspace_bytes(int n_lat, const hr_lattice *lats, hr_rep rep);

@@ -18,6 +18,10 @@
 // is F_a = beta/2 w_a.  The fermion force is hr_force on the packed links
 // (which carry the boundary conditions) with a = (Y, H_eo^+ Y), b = (X, H_oe X),
 // X = (Mhat^+ Mhat)^-1 eta, Y = Mhat X, coefficient 2 / (4 (4 + m0)).
+// Hasenbusch mass preconditioning splits S_f into Re<eta, (Mhat_H^+ Mhat_H)^-1 eta>
+// (heavy mass m0_H) and Re<eta2, (Mhat^+ Mhat)^-1 eta2> with eta2 = Mhat_H^+ phi;
+// the second term's force adds the variation of eta2: -2 c_H dRe<a', H b'>/dw,
+// a' = (g5 X2, H_eo^+ g5 X2), b' = (g5 phi, H_oe g5 phi), c_H = 1/(4 (4 + m0_H)).
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -239,7 +243,9 @@ hr_status mom_update(hr_ctx *ctx, const Geom &g, double eps, const double *F, do
 struct HmcWork {
     void *gauge;      // packed FP64 fundamental links (with the boundary signs)
     double *F;        // force [4][V][3]
-    void *X;          // even half: (Mhat^+ Mhat)^-1 eta
+    void *X;          // even half: (Mhat^+ Mhat)^-1 eta (Hasenbusch: at the heavy mass)
+    void *X2, *eta2;  // Hasenbusch ratio term: eta2 = Mhat_H^+ phi, X2 = (Mhat^+ Mhat)^-1 eta2
+    void *e1, *e2;    // even temporaries (g5 copies)
     void *a, *b;      // full fields of the fermion force
     void *t_odd;      // odd temporary of Mhat
     void *cg;         // CG workspace
@@ -264,8 +270,15 @@ size_t layout_hmc(hr_lattice lat, const hr_hmc_params &prm, char *w, HmcWork *hw
     void *gauge = take(gb);
     void *F = take(sizeof(double) * 12 * V);
     void *X = take(half), *a = take(2 * half), *b = take(2 * half), *t = take(half);
+    void *X2 = nullptr, *eta2 = nullptr, *e1 = nullptr, *e2 = nullptr;
+    if (prm.hasenbusch) {
+        X2 = take(half);
+        eta2 = take(half);
+        e1 = take(half);
+        e2 = take(half);
+    }
     void *cg = take(cgb);
-    if (hw) *hw = HmcWork{gauge, (double *)F, X, a, b, t, cg, cgb};
+    if (hw) *hw = HmcWork{gauge, (double *)F, X, X2, eta2, e1, e2, a, b, t, cg, cgb};
     return off;
 }
 
@@ -277,6 +290,7 @@ struct Trajectory {
     double *q;
     double *p;
     const void *eta;
+    const void *phi;  // Hasenbusch ratio pseudofermion (nullptr without)
     HmcWork w;
     cudaStream_t s;
     size_t half;
@@ -286,30 +300,101 @@ struct Trajectory {
 
     hr_status pack() { return hr_gauge_pack(ctx, lat, HR_FUND, HR_F64, q, w.gauge, (hr_stream)s); }
 
-    hr_status solve()
+    // the mass of the solve with eta: the heavy one under Hasenbusch preconditioning
+    double eta_mass() const { return prm.hasenbusch ? prm.m0_hasenbusch : prm.m0; }
+
+    hr_status cg(double m0, const void *src, void *x)
     {
-        if (x_valid) return HR_OK;
-        hr_status st = pack();
-        if (st) return st;
         hr_solver_opts o = prm.solver;
         o.n_rhs = 1;
         o.x0_is_guess = 0;
         hr_solve_info info{};
-        st = hr_cg_solve(ctx, lat, prm.m0, HR_FUND, &o, w.gauge, eta, w.X, &info, w.cg, w.cg_bytes, (hr_stream)s);
+        hr_status st = hr_cg_solve(ctx, lat, m0, HR_FUND, &o, w.gauge, src, x, &info, w.cg, w.cg_bytes, (hr_stream)s);
         cg_iters += info.iters;
         ++solves;
+        return st;
+    }
+
+    hr_status solve()
+    {
+        if (x_valid) return HR_OK;
+        hr_status st = pack();
+        if (!st) st = cg(eta_mass(), eta, w.X);
+        if (!st && prm.hasenbusch) {
+            // eta2 = Mhat_H^+ phi at the current links, then the ratio term's solve
+            st = apply_eo_op(ctx, g, prm.m0_hasenbusch, HR_FUND, kF64, HR_OP_SCHUR_DAG, w.gauge, phi, w.eta2,
+                             w.t_odd, nullptr, kFinNone, nullptr, nullptr, s);
+            if (!st) st = cg(prm.m0, w.eta2, w.X2);
+        }
         if (st) return st;
         x_valid = true;
         return HR_OK;
     }
 
+    hr_status dot(const void *a, const void *b, double &out)
+    {
+        k_dot_re<<<kRedBlocks, 256, 0, s>>>(g, a, b, ctx->d_partials);
+        hr_status st = check_launch(ctx, "pseudofermion action");
+        if (!st) st = read_sum(ctx, ctx->d_partials, kRedBlocks, out, s);
+        return st;
+    }
+
     hr_status fermion_action(double &S)
     {
         hr_status st = solve();
+        if (!st) st = dot(eta, w.X, S);
+        if (!st && prm.hasenbusch) {
+            double S2 = 0.0;
+            st = dot(w.eta2, w.X2, S2);
+            S += S2;
+        }
+        return st;
+    }
+
+    hr_status copy(void *dst, const void *src)
+    {
+        cudaError_t e = cudaMemcpyAsync(dst, src, half, cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? HR_OK : set_error(ctx, HR_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+    }
+
+    // dst_odd = [g5] H_oe [g5] src_even (g5 on the input and / or the output)
+    hr_status hop_oe(const void *src, void *dst, int g5_in, int g5_out)
+    {
+        HopLaunch L{};
+        L.p = 1;
+        L.gauge = w.gauge;
+        L.in = src;
+        L.out = dst;
+        L.beta = 1.0;
+        L.g5_in = g5_in;
+        L.g5_out = g5_out;
+        return launch_hop(ctx, g, HR_FUND, kF64, L, s);
+    }
+
+    // F += coeff dRe<a, H b>/dw with a = (u, H_eo^+ u), b = (v, H_oe v), H_eo^+ = g5 H_oe g5
+    hr_status pair_force(const void *u, const void *v, double coeff)
+    {
+        char *a = (char *)w.a, *b = (char *)w.b;
+        hr_status st = copy(a, u);
+        if (!st) st = hop_oe(u, a + half, 1, 1);
+        if (!st) st = copy(b, v);
+        if (!st) st = hop_oe(v, b + half, 0, 0);
+        if (!st) st = hr_force(ctx, lat, w.gauge, a, b, coeff, w.F, (hr_stream)s);
+        return st;
+    }
+
+    // the force of Re<src, (Mhat^+ Mhat)^-1 src> at mass m0 with X its solution:
+    // 2c dRe<a, H b>/dw, a = (Mhat X, H_eo^+ Mhat X), b = (X, H_oe X), c = 1/(4 (4+m0))
+    hr_status solve_force(double m0, const void *X)
+    {
+        hr_status st = apply_eo_op(ctx, g, m0, HR_FUND, kF64, HR_OP_SCHUR, w.gauge, X, w.a, w.t_odd, nullptr,
+                                   kFinNone, nullptr, nullptr, s);
         if (st) return st;
-        k_dot_re<<<kRedBlocks, 256, 0, s>>>(g, eta, w.X, ctx->d_partials);
-        st = check_launch(ctx, "pseudofermion action");
-        if (!st) st = read_sum(ctx, ctx->d_partials, kRedBlocks, S, s);
+        char *a = (char *)w.a, *b = (char *)w.b; // Mhat X is a's even half already
+        st = hop_oe(a, a + half, 1, 1);
+        if (!st) st = copy(b, X);
+        if (!st) st = hop_oe(X, b + half, 0, 0);
+        if (!st) st = hr_force(ctx, lat, w.gauge, a, b, 2.0 / (4.0 * (4.0 + m0)), w.F, (hr_stream)s);
         return st;
     }
 
@@ -321,36 +406,17 @@ struct Trajectory {
         hr_status st = gauge_force(ctx, g, prm.beta, q, 1.0, w.F, s);
         if (!st && prm.fermions) {
             st = solve();
-            char *a = (char *)w.a, *b = (char *)w.b;
-            // a = (Y, H_eo^+ Y) with Y = Mhat X and H_eo^+ = g5 H_oe g5; b = (X, H_oe X)
-            if (!st)
-                st = apply_eo_op(ctx, g, prm.m0, HR_FUND, kF64, HR_OP_SCHUR, w.gauge, w.X, a, w.t_odd, nullptr, kFinNone,
-                                 nullptr, nullptr, s);
-            if (!st) {
-                HopLaunch L{};
-                L.p = 1;
-                L.gauge = w.gauge;
-                L.in = a;
-                L.out = a + half;
-                L.beta = 1.0;
-                L.g5_in = 1;
-                L.g5_out = 1;
-                st = launch_hop(ctx, g, HR_FUND, kF64, L, s);
+            if (!st) st = solve_force(eta_mass(), w.X);
+            if (!st && prm.hasenbusch) {
+                // the ratio term: its solve's force, and the variation of eta2 = Mhat_H^+ phi,
+                // -2 c_H dRe<a', H b'>/dw with a' = (g5 X2, H_eo^+ g5 X2), b' = (g5 phi, H_oe g5 phi)
+                st = solve_force(prm.m0, w.X2);
+                if (!st) st = copy(w.e1, w.X2);
+                if (!st) st = blas_gamma5(ctx, g, HR_FUND, w.e1, s);
+                if (!st) st = copy(w.e2, phi);
+                if (!st) st = blas_gamma5(ctx, g, HR_FUND, w.e2, s);
+                if (!st) st = pair_force(w.e1, w.e2, -2.0 / (4.0 * (4.0 + prm.m0_hasenbusch)));
             }
-            if (!st) {
-                cudaError_t e2 = cudaMemcpyAsync(b, w.X, half, cudaMemcpyDeviceToDevice, s);
-                if (e2 != cudaSuccess) st = set_error(ctx, HR_ERR_CUDA, "copy: %s", cudaGetErrorString(e2));
-            }
-            if (!st) {
-                HopLaunch L{};
-                L.p = 1;
-                L.gauge = w.gauge;
-                L.in = w.X;
-                L.out = b + half;
-                L.beta = 1.0;
-                st = launch_hop(ctx, g, HR_FUND, kF64, L, s);
-            }
-            if (!st) st = hr_force(ctx, lat, w.gauge, a, b, 2.0 / (4.0 * (4.0 + prm.m0)), w.F, (hr_stream)s);
         }
         if (!st) force_valid = true;
         return st;
@@ -445,7 +511,8 @@ size_t hr_hmc_workspace_bytes(hr_lattice lat, const hr_hmc_params *prm)
 }
 
 hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *prm, double *gauge, double *mom,
-                            const void *eta, hr_hmc_info *info, void *work, size_t work_bytes, hr_stream stream)
+                            const void *eta, const void *phi, hr_hmc_info *info, void *work, size_t work_bytes,
+                            hr_stream stream)
 {
     if (!ctx) return HR_ERR_INVALID_ARG;
     if (info) std::memset(info, 0, sizeof *info);
@@ -457,8 +524,12 @@ hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *pr
     if (prm->integrator != HR_INTEGRATOR_LEAPFROG && prm->integrator != HR_INTEGRATOR_OMELYAN)
         return set_error(ctx, HR_ERR_INVALID_ARG, "bad integrator");
     if (prm->fermions && !(4.0 + prm->m0 != 0.0)) return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero");
-    st = check_buffers(ctx, prm->fermions ? std::initializer_list<const void *>{eta} : std::initializer_list<const void *>{},
-                       {gauge, mom}, {work});
+    if (prm->fermions && prm->hasenbusch && !(4.0 + prm->m0_hasenbusch != 0.0))
+        return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0_hasenbusch must be nonzero");
+    if (prm->hasenbusch && !prm->fermions) return set_error(ctx, HR_ERR_INVALID_ARG, "Hasenbusch needs fermions");
+    if (prm->fermions && prm->hasenbusch) st = check_buffers(ctx, {eta, phi}, {gauge, mom}, {work});
+    else if (prm->fermions) st = check_buffers(ctx, {eta}, {gauge, mom}, {work});
+    else st = check_buffers(ctx, {}, {gauge, mom}, {work});
     if (st) return st;
     const size_t need = hr_hmc_workspace_bytes(lat, prm);
     if (need == 0) return set_error(ctx, HR_ERR_INVALID_ARG, "bad solver options");
@@ -474,6 +545,7 @@ hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *pr
     T.q = gauge;
     T.p = mom;
     T.eta = eta;
+    T.phi = prm->hasenbusch ? phi : nullptr;
     T.s = (cudaStream_t)stream;
     T.half = hr_spinor_packed_bytes(lat, HR_FUND, HR_F64, HR_EVEN, 1);
     layout_hmc(lat, *prm, (char *)work, &T.w);

@@ -5,7 +5,10 @@ Wilson fermions (fundamental) on one GPU: the Markov chain around
 Each step draws Gaussian momenta and a pseudofermion eta = Mhat^+ xi with
 P(xi) ~ exp(-xi^+ xi), integrates one trajectory, and accepts the new links
 with probability min(1, exp(-dH)); a rejected trajectory restores the links.
-The random numbers come from a seeded torch generator on the device.
+With Hasenbusch mass preconditioning (``m0_hasenbusch``) it draws two:
+eta = Mhat_H^+ xi1 and phi = Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2 (one
+solve at the heavy mass).  The random numbers come from a seeded torch
+generator on the device.
 """
 
 from __future__ import annotations
@@ -20,11 +23,15 @@ from . import fields, hr
 class HMC:
     def __init__(self, ctx: hr.Context, dims, beta: float, m0: float = 0.0, fermions: bool = True,
                  n_steps: int = 10, tau: float = 1.0, integrator: int = hr.HR_INTEGRATOR_OMELYAN,
-                 solver: hr.hr_solver_opts | None = None, seed: int = 0, device="cuda"):
+                 solver: hr.hr_solver_opts | None = None, seed: int = 0, device="cuda",
+                 m0_hasenbusch: float | None = None):
         self.ctx, self.dims, self.device = ctx, dims, device
         self.prm = hr.hr_hmc_params_default(beta, m0, fermions, n_steps, tau, integrator)
         if solver is not None:
             self.prm.solver = solver
+        if m0_hasenbusch is not None:
+            self.prm.hasenbusch = 1
+            self.prm.m0_hasenbusch = float(m0_hasenbusch)
         self.work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(dims, self.prm), device)
         self.V = fields.volume(dims)
         self.gen = torch.Generator(device=device)
@@ -35,29 +42,48 @@ class HMC:
     def draw_momenta(self) -> torch.Tensor:
         return torch.randn((4, self.V, 3), dtype=torch.float64, device=self.device, generator=self.gen)
 
-    def draw_pseudofermion(self, q: torch.Tensor) -> torch.Tensor:
-        """Packed even eta = Mhat^+ xi for the links q, xi complex Gaussian with <|xi|^2> = 1."""
-        d = self.dims
+    def _xi(self):
+        """Packed even complex Gaussian field with <|xi|^2> = 1 per component."""
         shape = (self.V, 4, 2)
         xi = torch.complex(torch.randn(shape, dtype=torch.float64, device=self.device, generator=self.gen),
                            torch.randn(shape, dtype=torch.float64, device=self.device, generator=self.gen))
-        xi = xi / math.sqrt(2.0)
-        gauge = fields.pack_gauge(self.ctx, d, hr.HR_FUND, hr.HR_F64, q)
-        xp = fields.pack_spinor(self.ctx, d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, xi)
-        eta = fields.empty_spinor(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, device=self.device)
-        work = fields.empty_bytes(hr.hr_dirac_workspace_bytes(d, hr.HR_FUND, hr.HR_F64, hr.HR_OP_SCHUR_DAG),
-                                  self.device)
-        hr.hr_dirac_eo(self.ctx, d, self.prm.m0, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, hr.HR_OP_SCHUR_DAG, 1,
-                       gauge, xp, eta, work)
-        return eta
+        return fields.pack_spinor(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, xi / math.sqrt(2.0))
+
+    def _schur(self, gauge, m0, src, dagger):
+        d = self.dims
+        op = hr.HR_OP_SCHUR_DAG if dagger else hr.HR_OP_SCHUR
+        out = fields.empty_spinor(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, device=self.device)
+        work = fields.empty_bytes(hr.hr_dirac_workspace_bytes(d, hr.HR_FUND, hr.HR_F64, op), self.device)
+        hr.hr_dirac_eo(self.ctx, d, m0, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, op, 1, gauge, src, out, work)
+        return out
+
+    def draw_pseudofermion(self, q: torch.Tensor):
+        """Packed even eta = Mhat^+ xi for the links q (Hasenbusch: eta = Mhat_H^+ xi1
+        and phi = Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2; returns (eta, phi))."""
+        gauge = fields.pack_gauge(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, q)
+        if not self.prm.hasenbusch:
+            return self._schur(gauge, self.prm.m0, self._xi(), True)
+        mh = self.prm.m0_hasenbusch
+        eta = self._schur(gauge, mh, self._xi(), True)
+        rhs = self._schur(gauge, self.prm.m0, self._xi(), True)
+        opts = hr.hr_solver_opts.from_buffer_copy(self.prm.solver)
+        opts.tol = min(opts.tol, 1e-12)
+        y = fields.zeros_spinor(self.dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, device=self.device)
+        work = fields.empty_bytes(hr.hr_cg_workspace_bytes(self.dims, hr.HR_FUND, opts), self.device)
+        hr.hr_cg_solve(self.ctx, self.dims, mh, hr.HR_FUND, opts, gauge, rhs, y, work)
+        return eta, self._schur(gauge, mh, y, False)
 
     def step(self, q: torch.Tensor):
         """One HMC update of the links q (device double[4][V][4], in place).
         Returns (accepted, hr_hmc_info)."""
         backup = q.clone()
         p = self.draw_momenta()
-        eta = self.draw_pseudofermion(q) if self.prm.fermions else None
-        info = hr.hr_hmc_trajectory(self.ctx, self.dims, self.prm, q, p, eta, self.work)
+        eta = phi = None
+        if self.prm.fermions:
+            eta = self.draw_pseudofermion(q)
+            if self.prm.hasenbusch:
+                eta, phi = eta
+        info = hr.hr_hmc_trajectory(self.ctx, self.dims, self.prm, q, p, eta, self.work, phi=phi)
         u = torch.rand((), dtype=torch.float64, device=self.device, generator=self.gen).item()
         accept = info.dH <= 0.0 or u < math.exp(-info.dH)
         if not accept:

@@ -87,7 +87,7 @@ class hr_solver_opts(ctypes.Structure):
 class hr_hmc_params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("m0", ctypes.c_double), ("fermions", ctypes.c_int),
                 ("n_steps", ctypes.c_int), ("tau", ctypes.c_double), ("integrator", ctypes.c_int),
-                ("solver", hr_solver_opts)]
+                ("solver", hr_solver_opts), ("hasenbusch", ctypes.c_int), ("m0_hasenbusch", ctypes.c_double)]
 
 
 class hr_hmc_info(ctypes.Structure):
@@ -172,7 +172,7 @@ def lib():
                 "hr_mom_update": ([P, LAT, D, P, P, P], I),
                 "hr_kinetic_energy": ([P, LAT, P, ctypes.POINTER(D), P], I),
                 "hr_hmc_workspace_bytes": ([LAT, ctypes.POINTER(hr_hmc_params)], S),
-                "hr_hmc_trajectory": ([P, LAT, ctypes.POINTER(hr_hmc_params), P, P, P,
+                "hr_hmc_trajectory": ([P, LAT, ctypes.POINTER(hr_hmc_params), P, P, P, P,
                                        ctypes.POINTER(hr_hmc_info), P, S, P], I),
             }
             for name, (args, res) in sig.items():
@@ -512,16 +512,20 @@ def hr_hmc_workspace_bytes(dims, prm: hr_hmc_params) -> int:
     return int(lib().hr_hmc_workspace_bytes(lattice(dims), ctypes.byref(prm)))
 
 
-def hr_hmc_trajectory(ctx: Context, dims, prm: hr_hmc_params, gauge, mom, eta, work, stream=None):
-    """One MD trajectory, gauge and mom updated in place.  Returns hr_hmc_info."""
+def hr_hmc_trajectory(ctx: Context, dims, prm: hr_hmc_params, gauge, mom, eta, work, stream=None, phi=None):
+    """One MD trajectory, gauge and mom updated in place (phi: the Hasenbusch
+    ratio pseudofermion when prm.hasenbusch).  Returns hr_hmc_info."""
     _need(gauge, _links(dims) * 4 * 8, "gauge")
     _need(mom, _links(dims) * 3 * 8, "mom")
+    half = hr_spinor_packed_bytes(dims, HR_FUND, HR_F64, HR_EVEN, 1)
     if prm.fermions:
-        _need(eta, hr_spinor_packed_bytes(dims, HR_FUND, HR_F64, HR_EVEN, 1), "eta")
+        _need(eta, half, "eta")
+    if prm.hasenbusch:
+        _need(phi, half, "phi")
     info = hr_hmc_info()
     wb = 0 if work is None else work.numel() * work.element_size()
     ctx.check(lib().hr_hmc_trajectory(ctx.handle, lattice(dims), ctypes.byref(prm), _ptr(gauge), _ptr(mom),
-                                      _ptr(eta), ctypes.byref(info), _ptr(work), wb, _stream(stream)))
+                                      _ptr(eta), _ptr(phi), ctypes.byref(info), _ptr(work), wb, _stream(stream)))
     return info
 
 

@@ -76,10 +76,10 @@ def eta_field(ctx, lat, m0, seed):
     return eta, packed
 
 
-def run_gpu(ctx, lat, q, p, prm, eta_packed):
+def run_gpu(ctx, lat, q, p, prm, eta_packed, phi_packed=None):
     qd, pd = dev(q), dev(p)
     work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(lat, prm))
-    info = hr.hr_hmc_trajectory(ctx, lat, prm, qd, pd, eta_packed, work)
+    info = hr.hr_hmc_trajectory(ctx, lat, prm, qd, pd, eta_packed, work, phi=phi_packed)
     return qd.cpu().numpy(), pd.cpu().numpy(), info
 
 
@@ -150,3 +150,67 @@ def test_argument_checks(ctx):
     prm.n_steps = 2
     with pytest.raises(hr.HrError):
         hr.hr_hmc_trajectory(ctx, lat, prm, q, p, None, work)  # fermions without eta
+    prm.hasenbusch, prm.m0_hasenbusch = 1, 0.5
+    eta = fields.zeros_spinor(lat, 0, 0, hr.HR_EVEN)
+    work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(lat, prm))
+    with pytest.raises(hr.HrError):
+        hr.hr_hmc_trajectory(ctx, lat, prm, q, p, eta, work)  # Hasenbusch without phi
+
+
+# ---------------------------------------------------------------- Hasenbusch
+
+@pytest.mark.parametrize("integrator", [hr.HR_INTEGRATOR_LEAPFROG, hr.HR_INTEGRATOR_OMELYAN])
+def test_hasenbusch_trajectory_matches_oracle(ctx, integrator):
+    lat = hr.Lattice((4, 2, 2, 4), 1)
+    beta, m0, mh = 2.2, 0.05, 0.5
+    q = smeared(lat, 61)
+    p = np.random.default_rng(62).normal(size=(4, int(np.prod(lat)), 3))
+    prm = hr.hr_hmc_params_default(beta, m0, True, 3, 0.3, integrator)
+    prm.hasenbusch, prm.m0_hasenbusch = 1, mh
+    prm.solver.tol = 1e-13
+    eta, eta_p = eta_field(ctx, lat, m0, 63)
+    phi, phi_p = eta_field(ctx, lat, m0, 64)
+    qg, pg, info = run_gpu(ctx, lat, q, p, prm, eta_p, phi_p)
+    ferm = ohmc.Hasenbusch(lat, m0, mh, eta, phi, bc=1)
+    qo, po, io = ohmc.trajectory(lat, q, p, beta, 3, 0.3, integrator, ferm)
+    assert np.abs(qg - qo).max() <= 1e-11
+    assert np.abs(pg - po).max() <= 1e-9
+    assert abs(info.dH - io["dH"]) <= 1e-9, (info.dH, io["dH"])
+    assert abs(info.fermion_action_end - io["end"]["fermion"]) <= 1e-9
+    assert info.solves >= 8
+
+
+def test_hasenbusch_heat_bath_and_chain(ctx):
+    """The driver's two pseudofermions give S_f = |xi1|^2 + |xi2|^2 before the first
+    step (checked with fields drawn the driver's way from known xi), and a short
+    chain with Hasenbusch accepts."""
+    lat = hr.Lattice((4, 4, 4, 4), 1)
+    m0, mh = 0.05, 0.5
+    q = dev(smeared(lat, 71))
+    chain = HMC(ctx, lat, beta=2.2, m0=m0, fermions=True, n_steps=6, tau=0.5, seed=72, m0_hasenbusch=mh)
+    gauge = fields.pack_gauge(ctx, lat, hr.HR_FUND, hr.HR_F64, q)
+    rng = np.random.default_rng(73)
+    xis = []
+    for _ in range(2):
+        xi = (rng.normal(size=(int(np.prod(lat)), 4, 2)) + 1j * rng.normal(size=(int(np.prod(lat)), 4, 2))) / np.sqrt(2)
+        xi[oracle.parity_mask(lat) == 1] = 0
+        xis.append(xi)
+    packed = [fields.pack_spinor(ctx, lat, 0, 0, hr.HR_EVEN, fields.spinor_to_device(x)) for x in xis]
+    eta = chain._schur(gauge, mh, packed[0], True)
+    rhs = chain._schur(gauge, m0, packed[1], True)
+    opts = hr.hr_solver_default_opts()
+    opts.tol = 1e-13
+    y = fields.zeros_spinor(lat, 0, 0, hr.HR_EVEN)
+    hr.hr_cg_solve(ctx, lat, mh, 0, opts, gauge, rhs, y, fields.empty_bytes(hr.hr_cg_workspace_bytes(lat, 0, opts)))
+    phi = chain._schur(gauge, mh, y, False)
+    p = torch.zeros((4, int(np.prod(lat)), 3), dtype=torch.float64, device="cuda")
+    prm = hr.hr_hmc_params_default(2.2, m0, True, 1, 1e-6)
+    prm.hasenbusch, prm.m0_hasenbusch = 1, mh
+    prm.solver.tol = 1e-13
+    info = hr.hr_hmc_trajectory(ctx, lat, prm, q.clone(), p, eta, chain.work, phi=phi)
+    want = sum(float(np.vdot(x, x).real) for x in xis)
+    assert abs(info.fermion_action_start - want) <= 1e-9 * want
+    for _ in range(3):
+        acc, info = chain.step(q)
+        assert np.isfinite(info.dH) and abs(info.dH) < 2.0
+    assert chain.accepted >= 2
