@@ -13,9 +13,11 @@ form in Sec. 2.1 without writing either down):
 * ``D = (4+m0) - H/2`` with
   ``(H psi)(x) = sum_mu (1-g_mu) U_mu(x) psi(x+mu) + (1+g_mu) U_mu(x-mu)^+ psi(x-mu)``,
   chiral gamma basis, periodic in every direction except those whose bit is set
-  in ``bc`` (bit mu: antiperiodic, ``psi(x + L_mu mu) = -psi(x)``).  ``bc`` is a
-  keyword of every operator below; a ``dims`` object with a ``bc`` attribute
-  supplies it too.
+  in ``bc`` (bit mu: antiperiodic, ``psi(x + L_mu mu) = -psi(x)``) or whose
+  twist angle ``theta[mu]`` is nonzero (``psi(x + L_mu mu) = e^{i theta_mu}
+  psi(x)``; with the bit as well, the product of both factors).  ``bc`` and
+  ``theta`` are keywords of every operator below; a ``dims`` object with ``bc``
+  and ``theta`` attributes supplies them too.
 * ``Mhat = (4+m0) - H_eo H_oe / (4 (4+m0))`` on even sites, ``Mhat^+ = g5 Mhat g5``.
 * CG: Hestenes-Stiefel on ``Mhat^+ Mhat`` from ``x0 = 0``.
 
@@ -65,14 +67,14 @@ def _load():
             D = ctypes.c_double
             sig = {
                 "or_expand_links": [P, I, P, P],
-                "or_hop": [P, I, I, P, I, P, P],
-                "or_hop_sites": [P, I, I, P, P, L, P, P],
-                "or_dirac": [P, I, I, P, D, P, P],
-                "or_schur": [P, I, I, P, D, I, P, P],
-                "or_normal": [P, I, I, P, D, P, P],
-                "or_cg": [P, I, I, P, D, P, P, D, I, P, P],
-                "or_force": [P, I, P, P, P, P],
-                "or_link_grad": [P, I, P, P, P],
+                "or_hop": [P, I, P, I, P, I, P, P],
+                "or_hop_sites": [P, I, P, I, P, P, L, P, P],
+                "or_dirac": [P, I, P, I, P, D, P, P],
+                "or_schur": [P, I, P, I, P, D, I, P, P],
+                "or_normal": [P, I, P, I, P, D, P, P],
+                "or_cg": [P, I, P, I, P, D, P, P, D, I, P, P],
+                "or_force": [P, I, P, P, P, P, P],
+                "or_link_grad": [P, I, P, P, P, P],
                 "or_plaquette": [P, P, P],
                 "or_gamma": [I, P],
                 "or_adjoint_link": [P, P],
@@ -99,6 +101,22 @@ def _bc(dims, bc) -> int:
     if not 0 <= b <= 15:
         raise ValueError(f"bc = {b}: four bits, one per direction")
     return b
+
+
+def _theta(dims, theta):
+    """Twist angles: the explicit keyword, else the ``theta`` attribute of ``dims``;
+    a float64[4] array kept alive by the caller, or None (no twist)."""
+    t = theta if theta is not None else getattr(dims, "theta", None)
+    if t is None:
+        return None
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float64))
+    if t.shape != (4,) or not np.all(np.isfinite(t)):
+        raise ValueError("theta: four finite angles, one per direction")
+    return t if np.any(t != 0.0) else None
+
+
+def _tp(t):
+    return None if t is None else t.ctypes.data_as(ctypes.c_void_p)
 
 
 def _ptr(a: np.ndarray):
@@ -156,83 +174,91 @@ def _nc(L) -> int:
     return int(L.shape[-1])
 
 
-def hop(dims, L, psi, parity: int = -1, out=None, bc=None) -> np.ndarray:
+def hop(dims, L, psi, parity: int = -1, out=None, bc=None, theta=None) -> np.ndarray:
     """(H psi)(x) at the sites of ``parity`` (-1 = all); others stay zero (or as in ``out``)."""
     d = _dims(dims)
+    th = _theta(dims, theta)
     psi = _c128(psi)
     out = np.zeros_like(psi) if out is None else out
-    _check(_load().or_hop(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), int(parity), _ptr(psi), _ptr(out)), "hop")
+    _check(_load().or_hop(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), int(parity), _ptr(psi), _ptr(out)), "hop")
     return out
 
 
-def hop_sites(dims, L, psi, sites, bc=None) -> np.ndarray:
+def hop_sites(dims, L, psi, sites, bc=None, theta=None) -> np.ndarray:
     """(H psi) at the listed lexicographic sites, shape [n, 4, nc]."""
     d = _dims(dims)
+    th = _theta(dims, theta)
     psi = _c128(psi)
     s = np.ascontiguousarray(sites, dtype=np.int64)
     out = np.zeros((s.size, 4, _nc(L)), dtype=np.complex128)
-    _check(_load().or_hop_sites(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), _ptr(s), s.size, _ptr(psi), _ptr(out)),
+    _check(_load().or_hop_sites(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), _ptr(s), s.size, _ptr(psi), _ptr(out)),
            "hop_sites")
     return out
 
 
-def dirac(dims, L, m0: float, psi, bc=None) -> np.ndarray:
+def dirac(dims, L, m0: float, psi, bc=None, theta=None) -> np.ndarray:
     """Full Wilson-Dirac operator D psi on all sites."""
     d = _dims(dims)
+    th = _theta(dims, theta)
     psi = _c128(psi)
     out = np.zeros_like(psi)
-    _check(_load().or_dirac(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "dirac")
+    _check(_load().or_dirac(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "dirac")
     return out
 
 
-def schur(dims, L, m0: float, psi, dagger: bool = False, bc=None) -> np.ndarray:
+def schur(dims, L, m0: float, psi, dagger: bool = False, bc=None, theta=None) -> np.ndarray:
     """Mhat psi (or Mhat^+ psi) on even sites of a full-lattice array; odd sites -> 0."""
     d = _dims(dims)
+    th = _theta(dims, theta)
     psi = _c128(psi)
     out = np.zeros_like(psi)
-    _check(_load().or_schur(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), float(m0), int(bool(dagger)), _ptr(psi),
+    _check(_load().or_schur(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), float(m0), int(bool(dagger)), _ptr(psi),
                             _ptr(out)), "schur")
     return out
 
 
-def normal(dims, L, m0: float, psi, bc=None) -> np.ndarray:
+def normal(dims, L, m0: float, psi, bc=None, theta=None) -> np.ndarray:
     """Mhat^+ Mhat psi on even sites."""
     d = _dims(dims)
+    th = _theta(dims, theta)
     psi = _c128(psi)
     out = np.zeros_like(psi)
-    _check(_load().or_normal(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "normal")
+    _check(_load().or_normal(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "normal")
     return out
 
 
-def cg(dims, L, m0: float, b, tol: float = 1e-10, maxiter: int = 10000, bc=None):
+def cg(dims, L, m0: float, b, tol: float = 1e-10, maxiter: int = 10000, bc=None, theta=None):
     """CG on Mhat^+ Mhat x = b (even sites). Returns (x, iters, true_rel_residual, converged)."""
     d = _dims(dims)
+    th = _theta(dims, theta)
     b = _c128(b)
     x = np.zeros_like(b)
     it = ctypes.c_int(0)
     tr = ctypes.c_double(0.0)
-    rc = _load().or_cg(_ptr(d), _bc(dims, bc), _nc(L), _ptr(L), float(m0), _ptr(b), _ptr(x), float(tol),
+    rc = _load().or_cg(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), float(m0), _ptr(b), _ptr(x), float(tol),
                        int(maxiter), ctypes.byref(it), ctypes.byref(tr))
     _check(rc, "cg")
     return x, it.value, tr.value, rc == 0
 
 
-def force(dims, L, a, b, bc=None) -> np.ndarray:
+def force(dims, L, a, b, bc=None, theta=None) -> np.ndarray:
     """F[mu, x, a] = d Re<a, H b> / d w_a under U_mu(x) -> exp(i w.s/2) U_mu(x) (fundamental)."""
     d = _dims(dims)
+    th = _theta(dims, theta)
     assert _nc(L) == 2
     a, b = _c128(a), _c128(b)
     F = np.zeros((4, volume(dims), 3))
-    _check(_load().or_force(_ptr(d), _bc(dims, bc), _ptr(L), _ptr(a), _ptr(b), _ptr(F)), "force")
+    _check(_load().or_force(_ptr(d), _bc(dims, bc), _tp(th), _ptr(L), _ptr(a), _ptr(b), _ptr(F)), "force")
     return F
 
 
-def link_grad(dims, a, b, bc=None) -> np.ndarray:
+def link_grad(dims, a, b, bc=None, theta=None) -> np.ndarray:
     """G[mu, x, k] = d Re<a, H b> / d q_k for the quaternion components of U_mu(x)."""
     d = _dims(dims)
+    th = _theta(dims, theta)
     a, b = _c128(a), _c128(b)
     G = np.zeros((4, volume(dims), 4))
-    _check(_load().or_link_grad(_ptr(d), _bc(dims, bc), _ptr(a), _ptr(b), _ptr(G)), "link_grad")
+    _check(_load().or_link_grad(_ptr(d), _bc(dims, bc), _tp(th), _ptr(a), _ptr(b), _ptr(G)), "link_grad")
     return G
 
 
@@ -259,21 +285,21 @@ def gamma5(psi) -> np.ndarray:
     return psi * g5[None, :, None]
 
 
-def eo_source(dims, L, m0: float, b, bc=None) -> np.ndarray:
+def eo_source(dims, L, m0: float, b, bc=None, theta=None) -> np.ndarray:
     """bhat_e = b_e - D_eo D_oo^-1 b_o = b_e + H_eo b_o / (2 (4+m0)); odd sites zero."""
     odd = parity_mask(dims) == 1
     bo = _c128(b).copy()
     bo[~odd] = 0
-    h = hop(dims, L, bo, parity=0, bc=bc)
+    h = hop(dims, L, bo, parity=0, bc=bc, theta=theta)
     out = _c128(b) + h / (2.0 * (4.0 + m0))
     out[odd] = 0
     return out
 
 
-def eo_reconstruct(dims, L, m0: float, b, xe, bc=None) -> np.ndarray:
+def eo_reconstruct(dims, L, m0: float, b, xe, bc=None, theta=None) -> np.ndarray:
     """x_o = D_oo^-1 (b_o - D_oe x_e) = (b_o + H_oe x_e / 2) / (4+m0); returns full x."""
     odd = parity_mask(dims) == 1
-    h = hop(dims, L, _c128(xe), parity=1, bc=bc)
+    h = hop(dims, L, _c128(xe), parity=1, bc=bc, theta=theta)
     x = _c128(xe).copy()
     x[odd] = (_c128(b)[odd] + 0.5 * h[odd]) / (4.0 + m0)
     return x

@@ -136,15 +136,15 @@ def _parity(dims):
     return parity_mask(dims)
 
 
-def dirac(dims, L, A, psi, bc=None) -> np.ndarray:
+def dirac(dims, L, A, psi, bc=None, theta=None) -> np.ndarray:
     """D psi = A psi - H psi / 2 on all sites."""
     from . import hop
 
     psi = np.asarray(psi, dtype=np.complex128)
-    return apply_site(A, psi) - 0.5 * hop(dims, L, psi, bc=bc)
+    return apply_site(A, psi) - 0.5 * hop(dims, L, psi, bc=bc, theta=theta)
 
 
-def schur(dims, L, A, psi, dagger: bool = False, bc=None) -> np.ndarray:
+def schur(dims, L, A, psi, dagger: bool = False, bc=None, theta=None) -> np.ndarray:
     """Mhat psi (or Mhat^+ psi) on the even sites of a full-lattice array; odd sites -> 0."""
     from . import gamma5, hop
 
@@ -154,10 +154,10 @@ def schur(dims, L, A, psi, dagger: bool = False, bc=None) -> np.ndarray:
     inp[odd] = 0
     if dagger:
         inp = gamma5(inp)
-    t = hop(dims, L, inp, parity=1, bc=bc)           # H_oe in (odd sites)
+    t = hop(dims, L, inp, parity=1, bc=bc, theta=theta)           # H_oe in (odd sites)
     Ainv = np.linalg.inv(A[odd])
     t[odd] = apply_site(Ainv, t[odd])                 # A_oo^-1 H_oe in
-    u = hop(dims, L, t, parity=0, bc=bc)              # H_eo A_oo^-1 H_oe in
+    u = hop(dims, L, t, parity=0, bc=bc, theta=theta)              # H_eo A_oo^-1 H_oe in
     out = np.zeros_like(inp)
     out[even] = apply_site(A[even], inp[even]) - 0.25 * u[even]
     if dagger:
@@ -165,12 +165,12 @@ def schur(dims, L, A, psi, dagger: bool = False, bc=None) -> np.ndarray:
     return out
 
 
-def normal(dims, L, A, psi, bc=None) -> np.ndarray:
+def normal(dims, L, A, psi, bc=None, theta=None) -> np.ndarray:
     """Mhat^+ Mhat psi on even sites."""
-    return schur(dims, L, A, schur(dims, L, A, psi, bc=bc), dagger=True, bc=bc)
+    return schur(dims, L, A, schur(dims, L, A, psi, bc=bc, theta=theta), dagger=True, bc=bc, theta=theta)
 
 
-def cg(dims, L, A, b, tol: float = 1e-10, maxiter: int = 10000, bc=None):
+def cg(dims, L, A, b, tol: float = 1e-10, maxiter: int = 10000, bc=None, theta=None):
     """Hestenes-Stiefel CG on Mhat^+ Mhat x = b (even sites) from x = 0.
     Returns (x, iters, true_rel_residual, converged)."""
     b = np.asarray(b, dtype=np.complex128)
@@ -181,7 +181,7 @@ def cg(dims, L, A, b, tol: float = 1e-10, maxiter: int = 10000, bc=None):
     rr = bb
     it = 0
     while it < maxiter and np.sqrt(rr / bb) > tol:
-        q = normal(dims, L, A, p, bc=bc)
+        q = normal(dims, L, A, p, bc=bc, theta=theta)
         alpha = rr / np.vdot(p, q).real
         x = x + alpha * p
         r = r - alpha * q
@@ -189,11 +189,11 @@ def cg(dims, L, A, b, tol: float = 1e-10, maxiter: int = 10000, bc=None):
         p = r + (rr_new / rr) * p
         rr = rr_new
         it += 1
-    true = np.linalg.norm(b - normal(dims, L, A, x, bc=bc)) / np.sqrt(bb)
+    true = np.linalg.norm(b - normal(dims, L, A, x, bc=bc, theta=theta)) / np.sqrt(bb)
     return x, it, true, bool(np.sqrt(rr / bb) <= tol)
 
 
-def eo_source(dims, L, A, b, bc=None) -> np.ndarray:
+def eo_source(dims, L, A, b, bc=None, theta=None) -> np.ndarray:
     """bhat_e = b_e - D_eo A_oo^-1 b_o = b_e + H_eo A_oo^-1 b_o / 2; odd sites zero."""
     from . import hop
 
@@ -201,17 +201,17 @@ def eo_source(dims, L, A, b, bc=None) -> np.ndarray:
     odd = par == 1
     t = np.zeros_like(np.asarray(b, dtype=np.complex128))
     t[odd] = apply_site(np.linalg.inv(A[odd]), np.asarray(b, dtype=np.complex128)[odd])
-    out = np.array(b, dtype=np.complex128) + 0.5 * hop(dims, L, t, parity=0, bc=bc)
+    out = np.array(b, dtype=np.complex128) + 0.5 * hop(dims, L, t, parity=0, bc=bc, theta=theta)
     out[odd] = 0
     return out
 
 
-def eo_reconstruct(dims, L, A, b, xe, bc=None) -> np.ndarray:
+def eo_reconstruct(dims, L, A, b, xe, bc=None, theta=None) -> np.ndarray:
     """x_o = A_oo^-1 (b_o - D_oe x_e) = A_oo^-1 (b_o + H_oe x_e / 2); returns the full x."""
     from . import hop
 
     odd = _parity(dims) == 1
-    h = hop(dims, L, np.asarray(xe, dtype=np.complex128), parity=1, bc=bc)
+    h = hop(dims, L, np.asarray(xe, dtype=np.complex128), parity=1, bc=bc, theta=theta)
     x = np.array(xe, dtype=np.complex128)
     x[odd] = apply_site(np.linalg.inv(A[odd]), np.asarray(b, dtype=np.complex128)[odd] + 0.5 * h[odd])
     return x

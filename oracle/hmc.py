@@ -116,15 +116,15 @@ def kinetic(p) -> float:
 class Fermions:
     """The pseudofermion part for the links q: S_f and its force (one CG solve)."""
 
-    def __init__(self, dims, m0: float, eta, bc=0, tol: float = 1e-13):
-        self.dims, self.m0, self.eta, self.bc, self.tol = dims, m0, eta, bc, tol
+    def __init__(self, dims, m0: float, eta, bc=0, tol: float = 1e-13, theta=None):
+        self.dims, self.m0, self.eta, self.bc, self.tol, self.theta = dims, m0, eta, bc, tol, theta
         self.iters = 0
 
     def solve(self, q):
         from . import cg, expand_links
 
         L = expand_links(self.dims, 2, q)
-        x, it, tr, ok = cg(self.dims, L, self.m0, self.eta, tol=self.tol, maxiter=50000, bc=self.bc)
+        x, it, tr, ok = cg(self.dims, L, self.m0, self.eta, tol=self.tol, maxiter=50000, bc=self.bc, theta=self.theta)
         assert ok, tr
         self.iters += it
         return L, x
@@ -140,13 +140,13 @@ class Fermions:
 
         L, X = self.solve(q)
         d, bc = self.dims, self.bc
-        Y = schur(d, L, self.m0, X, bc=bc)
-        Z = hop(d, L, X, parity=1, bc=bc)
-        W = gamma5(hop(d, L, gamma5(Y), parity=1, bc=bc))
+        Y = schur(d, L, self.m0, X, bc=bc, theta=self.theta)
+        Z = hop(d, L, X, parity=1, bc=bc, theta=self.theta)
+        W = gamma5(hop(d, L, gamma5(Y), parity=1, bc=bc, theta=self.theta))
         even = parity_mask(d) == 0
         a = np.where(even[:, None, None], Y, W)
         b = np.where(even[:, None, None], X, Z)
-        return 2.0 / (4.0 * (4.0 + self.m0)) * force(d, L, a, b, bc=bc)
+        return 2.0 / (4.0 * (4.0 + self.m0)) * force(d, L, a, b, bc=bc, theta=self.theta)
 
 
 class Hasenbusch:
@@ -160,23 +160,23 @@ class Hasenbusch:
     2 Re <X2, dMhat_H^+ phi> = -2 c_H dRe <a', H b'> with a' = (g5 X2, H_eo^+ g5 X2),
     b' = (g5 phi, H_oe g5 phi), c_H = 1/(4 (4 + m0_h))."""
 
-    def __init__(self, dims, m0: float, m0_h: float, eta, phi, bc=0, tol: float = 1e-13):
-        self.dims, self.m0, self.m0_h, self.bc, self.tol = dims, m0, m0_h, bc, tol
-        self.heavy = Fermions(dims, m0_h, eta, bc=bc, tol=tol)
+    def __init__(self, dims, m0: float, m0_h: float, eta, phi, bc=0, tol: float = 1e-13, theta=None):
+        self.dims, self.m0, self.m0_h, self.bc, self.tol, self.theta = dims, m0, m0_h, bc, tol, theta
+        self.heavy = Fermions(dims, m0_h, eta, bc=bc, tol=tol, theta=theta)
         self.phi = np.asarray(phi, dtype=np.complex128)
         self.iters = 0
 
     def _eta2(self, L):
         from . import schur
 
-        return schur(self.dims, L, self.m0_h, self.phi, dagger=True, bc=self.bc)
+        return schur(self.dims, L, self.m0_h, self.phi, dagger=True, bc=self.bc, theta=self.theta)
 
     def _ratio(self, q):
         from . import cg, expand_links
 
         L = expand_links(self.dims, 2, q)
         eta2 = self._eta2(L)
-        x, it, tr, ok = cg(self.dims, L, self.m0, eta2, tol=self.tol, maxiter=50000, bc=self.bc)
+        x, it, tr, ok = cg(self.dims, L, self.m0, eta2, tol=self.tol, maxiter=50000, bc=self.bc, theta=self.theta)
         assert ok, tr
         self.iters += it
         return L, eta2, x
@@ -194,14 +194,14 @@ class Hasenbusch:
 
         def pair(u, v):
             """a = (u, H_eo^+ u), b = (v, H_oe v) as full fields."""
-            W = gamma5(hop(d, L, gamma5(u), parity=1, bc=bc))
-            Z = hop(d, L, v, parity=1, bc=bc)
+            W = gamma5(hop(d, L, gamma5(u), parity=1, bc=bc, theta=self.theta))
+            Z = hop(d, L, v, parity=1, bc=bc, theta=self.theta)
             return np.where(even[:, None, None], u, W), np.where(even[:, None, None], v, Z)
 
-        a, b = pair(schur(d, L, self.m0, X, bc=bc), X)
-        F = 2.0 / (4.0 * (4.0 + self.m0)) * force(d, L, a, b, bc=bc)
+        a, b = pair(schur(d, L, self.m0, X, bc=bc, theta=self.theta), X)
+        F = 2.0 / (4.0 * (4.0 + self.m0)) * force(d, L, a, b, bc=bc, theta=self.theta)
         a2, b2 = pair(gamma5(X), gamma5(self.phi))
-        F = F - 2.0 / (4.0 * (4.0 + self.m0_h)) * force(d, L, a2, b2, bc=bc)
+        F = F - 2.0 / (4.0 * (4.0 + self.m0_h)) * force(d, L, a2, b2, bc=bc, theta=self.theta)
         return F + self.heavy.force(q)
 
 

@@ -14,9 +14,13 @@
  *              - 1/2 sum_mu [ (1-g_mu) U_mu(x) psi(x+mu)
  *                            + (1+g_mu) U_mu(x-mu)^+ psi(x-mu) ]
  *
- * with periodic boundaries, or antiperiodic ones in the directions mu whose
- * bit (bc >> mu) & 1 is set: psi(x + L_mu mu-hat) = -psi(x), so a hop whose
- * neighbour lies across that boundary picks up a factor -1.  The chiral gamma basis
+ * with periodic boundaries, antiperiodic ones in the directions mu whose bit
+ * (bc >> mu) & 1 is set, psi(x + L_mu mu-hat) = -psi(x), and twisted ones with
+ * angle theta_mu, psi(x + L_mu mu-hat) = e^{i theta_mu} psi(x) (both together:
+ * the product of the two factors).  A hop whose neighbour lies across the
+ * boundary of direction mu picks up the factor that carries the stored value
+ * over: e^{+i theta_mu} (times -1 if antiperiodic) stepping forward across it,
+ * e^{-i theta_mu} (times -1) stepping backward.  theta may be NULL: no twist.  The chiral gamma basis
  *   g_0 = [[0, 1], [1, 0]],  g_k = [[0, -i s_k], [i s_k, 0]],  g5 = g0 g1 g2 g3,
  * SU(2) links U = a0 + i(a1 s1 + a2 s2 + a3 s3) in the fundamental
  * representation, and R_ab = 1/2 tr(s_a U s_b U^+) in the adjoint.  The hopping
@@ -111,15 +115,18 @@ static long shift(const int *d, long i, int mu, int step)
     return lex(d, x);
 }
 
-/* The boundary factor of the hop from site i to i + step * mu-hat: -1 when mu
- * is antiperiodic (bit mu of bc) and the step crosses the lattice's edge. */
-static double wrap_sign(const int *d, int bc, long i, int mu, int step)
+/* The boundary factor of the hop from site i to i + step * mu-hat (step = +-1):
+ * 1 unless the step crosses the lattice's edge in direction mu; then -1 if mu
+ * is antiperiodic (bit mu of bc), times e^{i step theta_mu} if th is given. */
+static cplx wrap_phase(const int *d, int bc, const double *th, long i, int mu, int step)
 {
-    if (!((bc >> mu) & 1)) return 1.0;
     int x[4];
     coords(d, i, x);
     int y = x[mu] + step;
-    return (y < 0 || y >= d[mu]) ? -1.0 : 1.0;
+    if (y >= 0 && y < d[mu]) return 1.0;
+    cplx f = ((bc >> mu) & 1) ? -1.0 : 1.0;
+    if (th && th[mu] != 0.0) f *= cexp(I * (double)step * th[mu]);
+    return f;
 }
 
 static int parity(const int *d, long i)
@@ -136,7 +143,14 @@ static int check_dims(const int *d)
     return 0;
 }
 
-static int check_lat(const int *d, int bc) { return (check_dims(d) || bc < 0 || bc > 15) ? -1 : 0; }
+static int check_lat(const int *d, int bc, const double *th)
+{
+    if (check_dims(d) || bc < 0 || bc > 15) return -1;
+    if (th)
+        for (int mu = 0; mu < 4; ++mu)
+            if (!isfinite(th[mu])) return -1;
+    return 0;
+}
 
 /* ------------------------------------------------------------------ */
 /* links                                                               */
@@ -209,15 +223,16 @@ int or_expand_links(const int *d, int nc, const double *q, double *Lout)
 /* ------------------------------------------------------------------ */
 
 /* out[s][c] = (H psi)(x) at one site, straight from the definition */
-static void hop_site(const int *d, int bc, int nc, const cplx *L, const cplx *psi, long x, cplx *out)
+static void hop_site(const int *d, int bc, const double *th, int nc, const cplx *L, const cplx *psi, long x,
+                     cplx *out)
 {
     long V = volume(d);
     int ns = 4 * nc;
     for (int k = 0; k < ns; ++k) out[k] = 0;
     for (int mu = 0; mu < 4; ++mu) {
         long xf = shift(d, x, mu, +1), xb = shift(d, x, mu, -1);
-        /* psi(x +- mu) across an antiperiodic boundary is minus the stored value */
-        double sgf = wrap_sign(d, bc, x, mu, +1), sgb = wrap_sign(d, bc, x, mu, -1);
+        /* psi(x +- mu) across the boundary is the stored value times its factor */
+        cplx sgf = wrap_phase(d, bc, th, x, mu, +1), sgb = wrap_phase(d, bc, th, x, mu, -1);
         const cplx *Uf = L + ((long)mu * V + x) * nc * nc;
         const cplx *Ub = L + ((long)mu * V + xb) * nc * nc;
         const cplx *pf = psi + xf * ns, *pb = psi + xb * ns;
@@ -247,10 +262,10 @@ static void hop_site(const int *d, int bc, int nc, const cplx *L, const cplx *ps
 
 /* out(x) = (H psi)(x) for every x of the given parity (-1: every site).
  * Sites of the other parity in out are left untouched. */
-int or_hop(const int *d, int bc, int nc, const double *Lr, int par, const double *psir, double *outr)
+int or_hop(const int *d, int bc, const double *th, int nc, const double *Lr, int par, const double *psir, double *outr)
 {
     init_tables();
-    if (check_lat(d, bc) || (nc != 2 && nc != 3)) return -1;
+    if (check_lat(d, bc, th) || (nc != 2 && nc != 3)) return -1;
     long V = volume(d);
     const cplx *L = (const cplx *)Lr, *psi = (const cplx *)psir;
     cplx *out = (cplx *)outr;
@@ -258,31 +273,31 @@ int or_hop(const int *d, int bc, int nc, const double *Lr, int par, const double
 #pragma omp parallel for schedule(static)
     for (long x = 0; x < V; ++x) {
         if (par >= 0 && parity(d, x) != par) continue;
-        hop_site(d, bc, nc, L, psi, x, out + x * ns);
+        hop_site(d, bc, th, nc, L, psi, x, out + x * ns);
     }
     return 0;
 }
 
 /* out[j] = (H psi)(sites[j]); out is [n][4][nc] */
-int or_hop_sites(const int *d, int bc, int nc, const double *Lr, const long *sites, long n,
+int or_hop_sites(const int *d, int bc, const double *th, int nc, const double *Lr, const long *sites, long n,
                  const double *psir, double *outr)
 {
     init_tables();
-    if (check_lat(d, bc) || (nc != 2 && nc != 3)) return -1;
+    if (check_lat(d, bc, th) || (nc != 2 && nc != 3)) return -1;
     long V = volume(d);
     for (long j = 0; j < n; ++j)
         if (sites[j] < 0 || sites[j] >= V) return -2;
     const cplx *L = (const cplx *)Lr, *psi = (const cplx *)psir;
     cplx *out = (cplx *)outr;
 #pragma omp parallel for schedule(static)
-    for (long j = 0; j < n; ++j) hop_site(d, bc, nc, L, psi, sites[j], out + j * 4 * nc);
+    for (long j = 0; j < n; ++j) hop_site(d, bc, th, nc, L, psi, sites[j], out + j * 4 * nc);
     return 0;
 }
 
 /* full operator: out = (4+m0) psi - 1/2 H psi */
-int or_dirac(const int *d, int bc, int nc, const double *Lr, double m0, const double *psir, double *outr)
+int or_dirac(const int *d, int bc, const double *th, int nc, const double *Lr, double m0, const double *psir, double *outr)
 {
-    int rc = or_hop(d, bc, nc, Lr, -1, psir, outr);
+    int rc = or_hop(d, bc, th, nc, Lr, -1, psir, outr);
     if (rc) return rc;
     long n = volume(d) * 4 * nc;
     const cplx *psi = (const cplx *)psir;
@@ -302,11 +317,11 @@ static void apply_g5(int nc, long V, cplx *v)
 /* Mhat psi on even sites (dagger = 0) or Mhat^+ psi = g5 Mhat g5 psi (dagger = 1).
  * psi, out: full-lattice arrays; only even sites of psi are read, odd sites of
  * out are set to zero. */
-int or_schur(const int *d, int bc, int nc, const double *Lr, double m0, int dagger,
+int or_schur(const int *d, int bc, const double *th, int nc, const double *Lr, double m0, int dagger,
              const double *psir, double *outr)
 {
     init_tables();
-    if (check_lat(d, bc) || (nc != 2 && nc != 3)) return -1;
+    if (check_lat(d, bc, th) || (nc != 2 && nc != 3)) return -1;
     long V = volume(d), n = V * 4 * nc;
     double A = 4.0 + m0;
     cplx *in = calloc(n, sizeof(cplx)), *t = calloc(n, sizeof(cplx));
@@ -316,8 +331,8 @@ int or_schur(const int *d, int bc, int nc, const double *Lr, double m0, int dagg
     for (long x = 0; x < V; ++x)
         if (parity(d, x) == 0) memcpy(in + x * 4 * nc, psi + x * 4 * nc, 4 * nc * sizeof(cplx));
     if (dagger) apply_g5(nc, V, in);
-    or_hop(d, bc, nc, Lr, 1, (const double *)in, (double *)t);  /* t_o = H_oe in_e   */
-    or_hop(d, bc, nc, Lr, 0, (const double *)t, (double *)u);   /* u_e = H_eo t_o    */
+    or_hop(d, bc, th, nc, Lr, 1, (const double *)in, (double *)t);  /* t_o = H_oe in_e   */
+    or_hop(d, bc, th, nc, Lr, 0, (const double *)t, (double *)u);   /* u_e = H_eo t_o    */
     cplx *out = (cplx *)outr;
     for (long x = 0; x < V; ++x) {
         cplx *o = out + x * 4 * nc;
@@ -333,13 +348,13 @@ int or_schur(const int *d, int bc, int nc, const double *Lr, double m0, int dagg
 }
 
 /* out = Mhat^+ Mhat psi (even sites) */
-int or_normal(const int *d, int bc, int nc, const double *Lr, double m0, const double *psir, double *outr)
+int or_normal(const int *d, int bc, const double *th, int nc, const double *Lr, double m0, const double *psir, double *outr)
 {
     long n = volume(d) * 4 * nc;
     double *tmp = calloc(2 * n, sizeof(double));
     if (!tmp) return -3;
-    int rc = or_schur(d, bc, nc, Lr, m0, 0, psir, tmp);
-    if (!rc) rc = or_schur(d, bc, nc, Lr, m0, 1, tmp, outr);
+    int rc = or_schur(d, bc, th, nc, Lr, m0, 0, psir, tmp);
+    if (!rc) rc = or_schur(d, bc, th, nc, Lr, m0, 1, tmp, outr);
     free(tmp);
     return rc;
 }
@@ -354,11 +369,11 @@ static double dotre(long n, const cplx *a, const cplx *b)
 /* Hestenes-Stiefel CG on Mhat^+ Mhat x = b (even sites), x0 = 0.
  * Stops when the iterated residual satisfies |r| <= tol |b|; then returns the
  * true relative residual |b - A x| / |b| recomputed from x. */
-int or_cg(const int *d, int bc, int nc, const double *Lr, double m0, const double *br, double *xr,
+int or_cg(const int *d, int bc, const double *th, int nc, const double *Lr, double m0, const double *br, double *xr,
           double tol, int maxiter, int *iters, double *true_rel)
 {
     init_tables();
-    if (check_lat(d, bc) || (nc != 2 && nc != 3)) return -1;
+    if (check_lat(d, bc, th) || (nc != 2 && nc != 3)) return -1;
     long n = volume(d) * 4 * nc;
     const cplx *b = (const cplx *)br;
     cplx *x = (cplx *)xr;
@@ -368,7 +383,7 @@ int or_cg(const int *d, int bc, int nc, const double *Lr, double m0, const doubl
     double bb = dotre(n, b, b), rr = bb;
     int it = 0;
     while (it < maxiter && sqrt(rr / bb) > tol) {
-        or_normal(d, bc, nc, Lr, m0, (const double *)p, (double *)q);
+        or_normal(d, bc, th, nc, Lr, m0, (const double *)p, (double *)q);
         double alpha = rr / dotre(n, p, q);
         for (long k = 0; k < n; ++k) { x[k] += alpha * p[k]; r[k] -= alpha * q[k]; }
         double rr_new = dotre(n, r, r);
@@ -377,7 +392,7 @@ int or_cg(const int *d, int bc, int nc, const double *Lr, double m0, const doubl
         rr = rr_new;
         ++it;
     }
-    or_normal(d, bc, nc, Lr, m0, (const double *)x, (double *)q);
+    or_normal(d, bc, th, nc, Lr, m0, (const double *)x, (double *)q);
     for (long k = 0; k < n; ++k) r[k] = b[k] - q[k];
     *true_rel = sqrt(dotre(n, r, r) / bb);
     *iters = it;
@@ -395,12 +410,13 @@ int or_cg(const int *d, int bc, int nc, const double *Lr, double m0, const doubl
  *   Q1 = sum_s (U b(x+mu))_s [((1-g_mu) a(x))_s]^+,
  *   Q2 = sum_s b(x)_s [(U (1+g_mu) a(x+mu))_s]^+.
  * F[mu][x][a-1] = d f / d w_a = Re tr[(i s_a / 2)(Q1 - Q2)], a = 1..3.
- * Across an antiperiodic boundary both terms (the hop x -> x+mu and the hop
- * x+mu -> x) carry the same factor -1, and so does F. */
-int or_force(const int *d, int bc, const double *Lr, const double *ar, const double *br, double *F)
+ * Across the boundary the hop x -> x+mu carries its factor f (wrap_phase, step
+ * +1) and the hop x+mu -> x its factor fb (step -1): the two terms become
+ * f Q1 and fb Q2 (for antiperiodic directions both are -1). */
+int or_force(const int *d, int bc, const double *th, const double *Lr, const double *ar, const double *br, double *F)
 {
     init_tables();
-    if (check_lat(d, bc)) return -1;
+    if (check_lat(d, bc, th)) return -1;
     long V = volume(d);
     const cplx *L = (const cplx *)Lr, *a = (const cplx *)ar, *b = (const cplx *)br;
 #pragma omp parallel for schedule(static)
@@ -425,22 +441,22 @@ int or_force(const int *d, int bc, const double *Lr, const double *ar, const dou
                     Ub[s][c] = U[c * 2 + 0] * b[(xf * 4 + s) * 2 + 0] + U[c * 2 + 1] * b[(xf * 4 + s) * 2 + 1];
                     Upa[s][c] = U[c * 2 + 0] * pa2[s][0] + U[c * 2 + 1] * pa2[s][1];
                 }
+            cplx f = wrap_phase(d, bc, th, x, mu, +1), fb = wrap_phase(d, bc, th, xf, mu, -1);
             cplx Q[2][2];
             for (int i = 0; i < 2; ++i)
                 for (int j = 0; j < 2; ++j) {
-                    cplx s = 0;
+                    cplx q1 = 0, q2 = 0;
                     for (int sp = 0; sp < 4; ++sp) {
-                        s += Ub[sp][i] * conj(pa[sp][j]);
-                        s -= b[(x * 4 + sp) * 2 + i] * conj(Upa[sp][j]);
+                        q1 += Ub[sp][i] * conj(pa[sp][j]);
+                        q2 += b[(x * 4 + sp) * 2 + i] * conj(Upa[sp][j]);
                     }
-                    Q[i][j] = s;
+                    Q[i][j] = f * q1 - fb * q2;
                 }
-            double sg = wrap_sign(d, bc, x, mu, +1);
             for (int k = 1; k <= 3; ++k) {
                 cplx tr = 0;
                 for (int i = 0; i < 2; ++i)
                     for (int j = 0; j < 2; ++j) tr += 0.5 * I * SIG[k][i][j] * Q[j][i];
-                F[((long)mu * V + x) * 3 + (k - 1)] = sg * creal(tr);
+                F[((long)mu * V + x) * 3 + (k - 1)] = creal(tr);
             }
         }
     }
@@ -449,18 +465,20 @@ int or_force(const int *d, int bc, const double *Lr, const double *ar, const dou
 
 /* G[mu][x][k] = d Re<a, H b> / d a_k for the link quaternion of U_mu(x),
  * U = sum_k a_k E_k with E_0 = 1, E_k = i s_k:
- *   = Re[a(x)^+ (1-g_mu) E_k b(x+mu)] + Re[a(x+mu)^+ (1+g_mu) E_k^+ b(x)],
- * times -1 when the link crosses an antiperiodic boundary (as for the force). */
-int or_link_grad(const int *d, int bc, const double *ar, const double *br, double *G)
+ *   = Re[f a(x)^+ (1-g_mu) E_k b(x+mu)] + Re[fb a(x+mu)^+ (1+g_mu) E_k^+ b(x)],
+ * f and fb the boundary factors of the two hops (1 off the boundary), as for
+ * the force. */
+int or_link_grad(const int *d, int bc, const double *th, const double *ar, const double *br, double *G)
 {
     init_tables();
-    if (check_lat(d, bc)) return -1;
+    if (check_lat(d, bc, th)) return -1;
     long V = volume(d);
     const cplx *a = (const cplx *)ar, *b = (const cplx *)br;
 #pragma omp parallel for schedule(static)
     for (long x = 0; x < V; ++x) {
         for (int mu = 0; mu < 4; ++mu) {
             long xf = shift(d, x, mu, +1);
+            cplx f = wrap_phase(d, bc, th, x, mu, +1), fb = wrap_phase(d, bc, th, xf, mu, -1);
             for (int k = 0; k < 4; ++k) {
                 cplx E[2][2], Ed[2][2];
                 for (int i = 0; i < 2; ++i)
@@ -473,11 +491,11 @@ int or_link_grad(const int *d, int bc, const double *ar, const double *br, doubl
                         cplx gm = one - GAM[mu][s][t], gp = one + GAM[mu][s][t];
                         for (int i = 0; i < 2; ++i)
                             for (int j = 0; j < 2; ++j) {
-                                acc += conj(a[(x * 4 + s) * 2 + i]) * gm * E[i][j] * b[(xf * 4 + t) * 2 + j];
-                                acc += conj(a[(xf * 4 + s) * 2 + i]) * gp * Ed[i][j] * b[(x * 4 + t) * 2 + j];
+                                acc += f * conj(a[(x * 4 + s) * 2 + i]) * gm * E[i][j] * b[(xf * 4 + t) * 2 + j];
+                                acc += fb * conj(a[(xf * 4 + s) * 2 + i]) * gp * Ed[i][j] * b[(x * 4 + t) * 2 + j];
                             }
                     }
-                G[((long)mu * V + x) * 4 + k] = wrap_sign(d, bc, x, mu, +1) * creal(acc);
+                G[((long)mu * V + x) * 4 + k] = creal(acc);
             }
         }
     }

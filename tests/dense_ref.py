@@ -66,13 +66,15 @@ def link_matrices(dims, q, nc):
     return out
 
 
-def hopping_dense(dims, q, nc, bc=0) -> np.ndarray:
+def hopping_dense(dims, q, nc, bc=0, theta=None) -> np.ndarray:
     """Dense H with (H psi)(x) = sum_mu (1-g) U_mu(x) psi(x+mu) + (1+g) U_mu(x-mu)^+ psi(x-mu).
 
     Index order (site, spin, colour).  On an extent-2 direction the forward and
     backward neighbours coincide and the two blocks add.  Bit mu of ``bc`` makes
     direction mu antiperiodic: a block whose neighbour is reached through the
-    lattice's edge in that direction enters with a minus sign.
+    lattice's edge in that direction enters with a minus sign.  A twist angle
+    ``theta[mu]`` multiplies such a block by e^{+i theta_mu} when the neighbour
+    is reached forward, e^{-i theta_mu} when backward.
     """
     V = int(np.prod(dims))
     idx = site_index(dims)
@@ -85,19 +87,23 @@ def hopping_dense(dims, q, nc, bc=0) -> np.ndarray:
         fwd = np.roll(idx, -1, axis=mu).reshape(-1)  # fwd[x] = x + mu
         bwd = np.roll(idx, 1, axis=mu).reshape(-1)   # bwd[x] = x - mu
         anti = (bc >> mu) & 1
+        tw = 0.0 if theta is None else float(theta[mu])
         pm = one - GAMMA[mu]
         pp = one + GAMMA[mu]
         for x in range(V):
-            sf = -1.0 if anti and xs[mu, x] == dims[mu] - 1 else 1.0
-            sb = -1.0 if anti and xs[mu, x] == 0 else 1.0
+            sf = sb = 1.0 + 0j
+            if xs[mu, x] == dims[mu] - 1:
+                sf = (-1.0 if anti else 1.0) * np.exp(1j * tw)
+            if xs[mu, x] == 0:
+                sb = (-1.0 if anti else 1.0) * np.exp(-1j * tw)
             H[x, :, :, fwd[x], :, :] += sf * np.einsum("st,cd->sctd", pm, U[mu, x])
             H[x, :, :, bwd[x], :, :] += sb * np.einsum("st,cd->sctd", pp, U[mu, bwd[x]].conj().T)
     return H.reshape(n, n)
 
 
-def dirac_dense(dims, q, nc, m0, bc=0) -> np.ndarray:
+def dirac_dense(dims, q, nc, m0, bc=0, theta=None) -> np.ndarray:
     n = int(np.prod(dims)) * 4 * nc
-    return (4.0 + m0) * np.eye(n) - 0.5 * hopping_dense(dims, q, nc, bc)
+    return (4.0 + m0) * np.eye(n) - 0.5 * hopping_dense(dims, q, nc, bc, theta)
 
 
 def parity_of_sites(dims) -> np.ndarray:
