@@ -101,10 +101,24 @@ typedef enum {
  * crosses the boundary uses one of those links), so a packed gauge field
  * carries its boundary conditions into every operator, solver and force
  * applied with it.  hr_link_grad, which takes no gauge field, applies the
- * sign itself.  Other calls ignore bc.  bc outside [0, 15]: HR_ERR_INVALID_ARG. */
+ * sign itself.  Other calls ignore bc.  bc outside [0, 15]: HR_ERR_INVALID_ARG.
+ *
+ * theta[mu] twists direction mu by a U(1) phase, psi(x + L_mu mu-hat) =
+ * e^{i theta_mu} psi(x) (times -1 if bit mu of bc is set as well): a hop that
+ * crosses that boundary forward picks up e^{+i theta_mu}, backward
+ * e^{-i theta_mu}.  theta = 0 in all four directions (a zero-initialised
+ * struct) is the untwisted lattice, and theta_mu = pi is the antiperiodic
+ * sign.  The twist is not folded into the packed links (a phased SU(2) link
+ * is no quaternion): the hop kernels apply it, so every call that applies the
+ * operator to a twisted lattice -- hr_dirac_apply / _eo (and their clover
+ * forms), the solvers, hr_force, hr_link_grad, hr_hmc_trajectory -- takes the
+ * same lattice.  Those calls run a separate, untuned hop kernel for twisted
+ * lattices; hr_cg_solve_batch returns HR_ERR_UNSUPPORTED for them.  A
+ * non-finite angle: HR_ERR_INVALID_ARG. */
 typedef struct {
     int dims[4];
     int bc;
+    double theta[4];
 } hr_lattice;
 #define HR_BC_ANTIPERIODIC(mu) (1 << (mu))
 

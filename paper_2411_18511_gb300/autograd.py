@@ -51,7 +51,7 @@ def _check_dims(q: torch.Tensor, dims):
         V *= int(d)
     if tuple(q.shape) != (4, V, 4):
         raise ValueError(f"links must have shape (4, {V}, 4), got {tuple(q.shape)}")
-    return hr.Lattice(dims, getattr(dims, "bc", 0))  # keeps the boundary conditions
+    return hr.Lattice(dims, getattr(dims, "bc", 0), getattr(dims, "theta", None))  # keeps the boundary conditions
 
 
 class _Lattice:

@@ -412,6 +412,8 @@ hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, doub
     for (int l = 0; l < n_lat; ++l) {
         hr_status st = validate_lattice(ctx, lats[l], 1);
         if (st) return st;
+        if (make_geom(lats[l], 1).twisted)
+            return set_error(ctx, HR_ERR_UNSUPPORTED, "batched solver: lattice %d has twisted boundaries", l);
         if (b[l] == x[l]) return set_error(ctx, HR_ERR_INVALID_ARG, "lattice %d: b and x alias", l);
         st = check_buffers(ctx, {gauges[l], b[l], x[l]});
         if (st) return st;

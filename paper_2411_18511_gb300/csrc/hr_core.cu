@@ -1,5 +1,6 @@
 // hr_core.cu -- context, error reporting, sizes and the layout-conversion
 // kernels (canonical <-> packed) of libhirep_gb300.
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 
@@ -74,6 +75,8 @@ hr_status validate_lattice(hr_ctx *ctx, const hr_lattice &lat, int nrhs)
     if (nrhs < 1 || nrhs > kMaxRhs || (nrhs & (nrhs - 1)))
         return set_error(ctx, HR_ERR_UNSUPPORTED, "n_rhs = %d: must be a power of two in [1, %d]", nrhs, kMaxRhs);
     if (lat.bc & ~15) return set_error(ctx, HR_ERR_INVALID_ARG, "bc = %d: one bit per direction, [0, 15]", lat.bc);
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(lat.theta[k])) return set_error(ctx, HR_ERR_INVALID_ARG, "theta[%d] is not finite", k);
     if (!lattice_ok(lat, nrhs)) return set_error(ctx, HR_ERR_UNSUPPORTED, "lattice too large for 32-bit site indexing");
     return HR_OK;
 }

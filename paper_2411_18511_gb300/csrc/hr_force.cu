@@ -12,8 +12,13 @@
 //   su(2) force          F_a = Re tr[(i s_a/2)(U M1 - M2 U^+)]   for U -> exp(i w.s/2) U.
 // One thread per site (both parities in one launch); it writes all four
 // directions of its own links, so no two threads touch the same output.
-// Antiperiodic directions: the two terms that contain a link on the boundary
-// slice both cross the boundary and carry its factor -1.
+// Boundaries: the two terms that contain a link on the boundary slice both
+// cross the boundary.  An antiperiodic sign multiplies both (the packed links
+// carry it; the quaternion gradient, which takes no gauge field, applies it);
+// a twist e^{i theta} multiplies the forward hop's term and e^{-i theta} the
+// backward hop's, i.e. M1 -> e^{i theta} M1 and M2 -> e^{-i theta} M2.
+#include <cmath>
+
 #include "hr_host.h"
 
 using namespace hr;
@@ -28,6 +33,7 @@ struct ForceArgs {
     double beta;
     double *out;
     int mode; // 0: su(2) force [4][V][3], 1: quaternion gradient [4][V][4]
+    double tc[4], ts[4]; // e^{i theta_mu} of twisted directions (1, 0 otherwise)
 };
 
 struct c2 {
@@ -40,9 +46,11 @@ __device__ __forceinline__ c2 cminus(c2 a, c2 b) { return {a.re - b.re, a.im - b
 
 // sg: -1 for a link on the boundary slice of an antiperiodic direction.  The
 // force reads the packed links, which carry that sign already; the quaternion
-// gradient takes no gauge field and applies it here.
+// gradient takes no gauge field and applies it here.  edge: the link lies on
+// the boundary slice (x_mu = L_mu - 1), where a twist applies.
 template <int MU>
-__device__ __forceinline__ void link_terms(const ForceArgs &A, int p, int i, int ifw, long long lex, double sg)
+__device__ __forceinline__ void link_terms(const ForceArgs &A, int p, int i, int ifw, long long lex, double sg,
+                                           bool edge)
 {
     const Geom &g = A.g;
     cpx<double> ax[4][2], axf[4][2], bx[4][2], bxf[4][2];
@@ -69,6 +77,14 @@ __device__ __forceinline__ void link_terms(const ForceArgs &A, int p, int i, int
             M1[c][d] = s1;
             M2[c][d] = s2;
         }
+    if (edge && A.g.twisted) {
+        const c2 f = {A.tc[MU], A.ts[MU]}, fb = {A.tc[MU], -A.ts[MU]};
+        for (int c = 0; c < 2; ++c)
+            for (int d = 0; d < 2; ++d) {
+                M1[c][d] = cmul(f, M1[c][d]);
+                M2[c][d] = cmul(fb, M2[c][d]);
+            }
+    }
     const long long V = 2LL * g.vh;
     if (A.mode == 1) {
         // tr(s_1 M) = M10 + M01, tr(s_2 M) = i (M01 - M10), tr(s_3 M) = M00 - M11
@@ -124,10 +140,10 @@ __global__ void k_link_deriv(ForceArgs A)
         r /= g.d[k];
     }
     auto sg = [&](int mu) { return (A.mode == 1 && ((g.bc >> mu) & 1) && x[mu] == g.d[mu] - 1) ? -1.0 : 1.0; };
-    link_terms<0>(A, p, i, nb.fwd[0], lex, sg(0));
-    link_terms<1>(A, p, i, nb.fwd[1], lex, sg(1));
-    link_terms<2>(A, p, i, nb.fwd[2], lex, sg(2));
-    link_terms<3>(A, p, i, nb.fwd[3], lex, sg(3));
+    link_terms<0>(A, p, i, nb.fwd[0], lex, sg(0), x[0] == g.d[0] - 1);
+    link_terms<1>(A, p, i, nb.fwd[1], lex, sg(1), x[1] == g.d[1] - 1);
+    link_terms<2>(A, p, i, nb.fwd[2], lex, sg(2), x[2] == g.d[2] - 1);
+    link_terms<3>(A, p, i, nb.fwd[3], lex, sg(3), x[3] == g.d[3] - 1);
 }
 
 hr_status launch(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *af, const void *bf, double beta,
@@ -150,6 +166,10 @@ hr_status launch(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *af,
     A.beta = beta;
     A.out = out;
     A.mode = mode;
+    for (int k = 0; k < 4; ++k) {
+        A.tc[k] = std::cos(lat.theta[k]);
+        A.ts[k] = std::sin(lat.theta[k]);
+    }
     int bs = 128;
     int grid = (int)((2LL * A.g.vh + bs - 1) / bs);
     k_link_deriv<<<grid, bs, 0, (cudaStream_t)stream>>>(A);

@@ -12,7 +12,8 @@
 //
 // This file holds the plain unrolled kernels (variants 0 and 7), the dispatch
 // over all variants (the other families are in hr_hop_staged.cu, hr_hop_loop.cu,
-// hr_hop_tile.cu and hr_hop_x2.cu; hr_hop_fam.h lists them), the operators built
+// hr_hop_tile.cu and hr_hop_x2.cu; hr_hop_fam.h lists them; lattices with
+// twisted boundaries take the kernel of hr_hop_twist.cu), the operators built
 // from hops and their C ABI.  The autotuner (hr_tune.cu) picks variant and
 // block size per configuration.
 #include <algorithm>
@@ -116,6 +117,12 @@ hr_status dispatch(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs 
 {
     if (rep < 0 || rep > 2 || prec < 0 || prec > 2) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
     const long long nv = (long long)g.vh << g.lrhs;
+    if (g.twisted) {
+        // twisted boundaries: one kernel for every mode, whatever the tuned shape
+        hr_status st = HR_OK;
+        launch_hop_twisted(ctx, rep, prec, a, s, st);
+        return st;
+    }
     if (a.clov_mode != kClovNone) {
         // the clover instantiations: paired staged for fundamental FP64, else unrolled
         const bool paired = rep == HR_FUND && prec == kF64;

@@ -100,5 +100,9 @@ bool launch_hop_paired(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopA
                        cudaStream_t s, hr_status &st);
 // the paired staged kernel with the clover epilogue (fundamental FP64)
 void launch_hop_clover_paired(hr_ctx *ctx, const HopArgs &a, int grid, int block, cudaStream_t s, hr_status &st);
+// the kernel of lattices with twisted boundaries (hr_hop_twist.cu): every
+// operator mode, clover included, kTwistBlock threads per block
+constexpr int kTwistBlock = 128;
+void launch_hop_twisted(hr_ctx *ctx, int rep, int prec, const HopArgs &a, cudaStream_t s, hr_status &st);
 
 } // namespace hr

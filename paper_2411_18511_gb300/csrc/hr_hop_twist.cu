@@ -1,0 +1,120 @@
+// hr_hop_twist.cu -- the hop for lattices with twisted fermion boundary
+// conditions, psi(x + L_mu mu) = e^{i theta_mu} psi(x): a hop that reaches its
+// neighbour forward across the boundary of direction mu multiplies the
+// neighbour spinor by e^{+i theta_mu}, backward by e^{-i theta_mu} (the phase
+// commutes with the spin projection and the colour product, so it is applied
+// to the loaded spinor before them).  An SU(2) link times a phase is no
+// quaternion, so the twist cannot ride in the packed links as the
+// antiperiodic sign does (that sign stays there and combines with the phase).
+//
+// One thread per output (virtual) site, the operand loads, projection, colour
+// product and epilogue of the plain kernel (hr_hop_dev.cuh), every operator
+// mode of HopArgs (Schur epilogues, fused CG update, |out|^2 reduction, clover
+// site term).  Twisted lattices always run this kernel: the dispatch sends
+// them here before consulting the autotuned variant, so the tuned kernels of
+// untwisted lattices carry no trace of the twist.
+#include "hr_host.h"
+#include "hr_hop_dev.cuh"
+#include "hr_hop_fam.h"
+
+using namespace hr;
+
+namespace {
+
+// coordinates x_mu of the site with even-odd index i and parity p
+__device__ __forceinline__ void site_coords(const Geom &g, int i, int p, int (&x)[4])
+{
+    const int row = fdiv(i, g.div_h3);
+    const int k = i - row * g.h3;
+    const int r1 = fdiv(row, g.div_d2);
+    x[2] = row - r1 * g.d[2];
+    x[0] = fdiv(r1, g.div_d1);
+    x[1] = r1 - x[0] * g.d[1];
+    x[3] = 2 * k + ((x[0] + x[1] + x[2] + p) & 1);
+}
+
+// s *= c + i sn
+template <class T, int NC> __device__ __forceinline__ void phase_spinor(cpx<T> (&s)[4][NC], T c, T sn)
+{
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) s[a][b] = {s[a][b].re * c - s[a][b].im * sn, s[a][b].re * sn + s[a][b].im * c};
+}
+
+template <int MU, int REP, int PREC, bool FIRST, class T, int NC>
+__device__ __forceinline__ void twisted_dir(const HopArgs &a, int i, int rr, const SiteNb &nb, const int (&x)[4],
+                                            cpx<T> (&acc)[4][NC])
+{
+    const Geom &g = a.g;
+    const int l = g.lrhs;
+    const bool g5 = a.g5_in != 0;
+    const T c = Real<T>::from_coef(g.tw_c[MU]), sn = Real<T>::from_coef(g.tw_s[MU]);
+    cpx<T> s[4][NC];
+    float sc;
+    // forward: (1 - g_mu) U_mu(x) psi(x + mu), e^{+i theta} across the boundary
+    load_spinor_raw<NC, PREC>(a.in, g.nblk_s, (nb.fwd[MU] << l) + rr, s, sc);
+    if (x[MU] == g.d[MU] - 1) phase_spinor(s, c, sn);
+    hop_term_with<MU, true, REP, PREC, FIRST>(a, i, a.p, s, sc, g5, acc);
+    // backward: (1 + g_mu) U_mu(x - mu)^+ psi(x - mu), e^{-i theta} across it
+    load_spinor_raw<NC, PREC>(a.in, g.nblk_s, (nb.bwd[MU] << l) + rr, s, sc);
+    if (x[MU] == 0) phase_spinor(s, c, -sn);
+    hop_term_with<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, s, sc, g5, acc);
+}
+
+template <int REP, int PREC, bool CLOV>
+__global__ void __launch_bounds__(128) k_hop_twist(HopArgs a)
+{
+    using T = typename PrecTraits<PREC>::T;
+    constexpr int NC = RepTraits<REP>::NC;
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const T be = Real<T>::from_coef(a.beta);
+    const T bu = a.g5_out ? -be : be;
+    const T al = Real<T>::from_coef(a.alpha);
+    SqAcc<T> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        int x[4];
+        site_coords(g, i, a.p, x);
+        cpx<T> acc[4][NC];
+        twisted_dir<0, REP, PREC, true>(a, i, rr, nb, x, acc);
+        twisted_dir<1, REP, PREC, false>(a, i, rr, nb, x, acc);
+        twisted_dir<2, REP, PREC, false>(a, i, rr, nb, x, acc);
+        twisted_dir<3, REP, PREC, false>(a, i, rr, nb, x, acc);
+        hop_epilogue<PREC, CLOV>(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+template <int REP, int PREC> struct TwistLaunch {
+    static bool run(hr_ctx *ctx, const HopArgs &a, int grid, cudaStream_t s, hr_status &st)
+    {
+        if (a.clov_mode != kClovNone) k_hop_twist<REP, PREC, true><<<grid, kTwistBlock, 0, s>>>(a);
+        else k_hop_twist<REP, PREC, false><<<grid, kTwistBlock, 0, s>>>(a);
+        st = check_launch(ctx, "hop kernel (twisted boundaries)");
+        return true;
+    }
+};
+
+} // namespace
+
+namespace hr {
+
+void launch_hop_twisted(hr_ctx *ctx, int rep, int prec, const HopArgs &a, cudaStream_t s, hr_status &st)
+{
+    const long long nv = (long long)a.g.vh << a.g.lrhs;
+    const int grid = grid_for(nv, kTwistBlock, a.fin ? kMaxBlocks : (1 << 30));
+    if (!for_config<TwistLaunch>(rep, prec, ctx, a, grid, s, st))
+        st = set_error(ctx, HR_ERR_INVALID_ARG, "bad rep/prec");
+}
+
+} // namespace hr

@@ -33,6 +33,7 @@
 // where nblk = ceil(V_h/32) for the gauge and ceil(V_h*N/32) for spinors.
 #pragma once
 
+#include <cmath>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -69,6 +70,19 @@ inline FastDiv make_fastdiv(unsigned d)
 }
 __device__ __forceinline__ int fdiv(int n, FastDiv f) { return (int)(((unsigned long long)(unsigned)n * f.m) >> f.s); }
 
+// A double-precision scalar split on the host into two floats, so kernels get
+// launch constants in any of their arithmetic types without FP64 conversions.
+struct coef2 {
+    float h, l;
+};
+inline coef2 make_coef(double x)
+{
+    coef2 c;
+    c.h = (float)x;
+    c.l = (float)(x - (double)c.h);
+    return c;
+}
+
 struct Geom {
     int d[4];   // T, L1, L2, L3
     int h3;     // L3 / 2
@@ -79,6 +93,11 @@ struct Geom {
     int nblk_s; // 32-virtual-site blocks of a spinor field of one parity
     int bc;     // antiperiodic directions (bit mu); used where links are packed
     FastDiv div_h3, div_d2, div_d1;
+    // twisted boundaries: e^{i theta_mu} = tw_c + i tw_s (each a float pair,
+    // h + l), applied by the twisted hop kernel only; twisted = 0 when all
+    // four angles are zero
+    int twisted;
+    coef2 tw_c[4], tw_s[4];
 };
 
 inline Geom make_geom(const hr_lattice &lat, int nrhs)
@@ -98,6 +117,12 @@ inline Geom make_geom(const hr_lattice &lat, int nrhs)
     g.div_h3 = make_fastdiv((unsigned)(g.h3 > 0 ? g.h3 : 1));
     g.div_d2 = make_fastdiv((unsigned)(g.d[2] > 0 ? g.d[2] : 1));
     g.div_d1 = make_fastdiv((unsigned)(g.d[1] > 0 ? g.d[1] : 1));
+    g.twisted = 0;
+    for (int k = 0; k < 4; ++k) {
+        g.twisted |= lat.theta[k] != 0.0;
+        g.tw_c[k] = make_coef(std::cos(lat.theta[k]));
+        g.tw_s[k] = make_coef(std::sin(lat.theta[k]));
+    }
     return g;
 }
 
@@ -211,19 +236,6 @@ __device__ __forceinline__ dd dd_from_double(double x)
     return dd(h, __double2float_rn(x - (double)h));
 }
 __device__ __forceinline__ double dd_to_double(dd a) { return (double)a.h + (double)a.l; }
-
-// A double-precision scalar split on the host into two floats, so kernels get
-// launch constants in any of their arithmetic types without FP64 conversions.
-struct coef2 {
-    float h, l;
-};
-inline coef2 make_coef(double x)
-{
-    coef2 c;
-    c.h = (float)x;
-    c.l = (float)(x - (double)c.h);
-    return c;
-}
 
 template <class T> struct Real;
 template <> struct Real<float> {

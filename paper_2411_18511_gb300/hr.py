@@ -59,23 +59,33 @@ class HrError(RuntimeError):
 
 
 class hr_lattice(ctypes.Structure):
-    _fields_ = [("dims", ctypes.c_int * 4), ("bc", ctypes.c_int)]
+    _fields_ = [("dims", ctypes.c_int * 4), ("bc", ctypes.c_int), ("theta", ctypes.c_double * 4)]
 
 
 class Lattice(tuple):
     """Extents (T, L1, L2, L3) with fermion boundary conditions: ``bc`` bit mu
-    makes direction mu antiperiodic.  A tuple, so it serves wherever extents do;
-    every call of this module that takes ``dims`` reads ``bc`` from it."""
+    makes direction mu antiperiodic; ``theta[mu]`` twists it,
+    psi(x + L_mu mu) = e^{i theta_mu} psi(x) (None: no twist).  A tuple, so it
+    serves wherever extents do; every call of this module that takes ``dims``
+    reads ``bc`` and ``theta`` from it."""
 
-    def __new__(cls, dims, bc: int = 0):
+    def __new__(cls, dims, bc: int = 0, theta=None):
         self = super().__new__(cls, (int(d) for d in dims))
         if len(self) != 4:
             raise ValueError("four extents")
         self.bc = int(bc)
+        if theta is not None:
+            theta = tuple(float(t) for t in theta)
+            if len(theta) != 4:
+                raise ValueError("four twist angles")
+            if not any(theta):
+                theta = None
+        self.theta = theta
         return self
 
     def __repr__(self):
-        return f"Lattice({tuple(self)}, bc={self.bc})"
+        tw = f", theta={self.theta}" if self.theta is not None else ""
+        return f"Lattice({tuple(self)}, bc={self.bc}{tw})"
 
 
 class hr_solver_opts(ctypes.Structure):
@@ -194,6 +204,10 @@ def lattice(dims) -> hr_lattice:
     for k in range(4):
         lat.dims[k] = int(dims[k])
     lat.bc = int(getattr(dims, "bc", 0))
+    theta = getattr(dims, "theta", None)
+    if theta is not None:
+        for k in range(4):
+            lat.theta[k] = float(theta[k])
     return lat
 
 
