@@ -567,6 +567,8 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     torch.cuda.empty_cache()
     out["clover_48"] = run_clover_48(ctx, torch, hr, fields, q48, psi48)
     torch.cuda.empty_cache()
+    out["twist_48"] = run_twist_48(ctx, torch, hr, fields, q48, psi48)
+    torch.cuda.empty_cache()
     out["diff_solve_16"] = run_diff_solve(torch, synth)
     torch.cuda.empty_cache()
     out["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
@@ -699,6 +701,42 @@ def run_clover_48(ctx, torch, hr, fields, q48, psi48, reps=30):
                      "time_vs_wilson": round(ms / ms_w, 3), "build_s": round(build_s, 3)}
         del clov
     del gauge, src, dst, work, qd
+    return out
+
+
+def run_twist_48(ctx, torch, hr, fields, q48, psi48, reps=30):
+    """48^4 fund FP64 hop with twisted boundaries (theta in time only, and in
+    all four directions): the separate, untuned kernel that applies the phase,
+    against the tuned untwisted hop on the same fields (512 B per site)."""
+    dims = DIMS
+    Vh = int(np.prod(dims)) // 2
+    qd = fields.gauge_to_device(q48)
+    pd = fields.spinor_to_device(psi48)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"lattice": list(dims), "applications": reps}
+    for name, lat in (("untwisted", hr.Lattice(dims, 1)), ("twist_t", hr.Lattice(dims, 1, (0.5, 0, 0, 0))),
+                      ("twist_all", hr.Lattice(dims, 1, (0.5, 0.3, -0.7, 1.1)))):
+        gauge = fields.pack_gauge(ctx, lat, hr.HR_FUND, hr.HR_F64, qd)
+        src = fields.pack_spinor(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_ODD, pd)
+        dst = fields.empty_spinor(lat, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
+
+        def hop():
+            hr.hr_dirac_eo(ctx, lat, 0.0, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, hr.HR_OP_HOP, 1, gauge, src, dst)
+
+        for _ in range(5):
+            hop()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            hop()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": round(ms, 4), "gbs": round(Vh * 512 / (ms * 1e-3) / 1e9, 1)}
+        del gauge, src, dst
+    for k in ("twist_t", "twist_all"):
+        out[k]["time_vs_untwisted"] = round(out[k]["ms"] / out["untwisted"]["ms"], 3)
+    del qd, pd
     return out
 
 

@@ -468,6 +468,8 @@ typedef struct {
  * configuration on this context (operators and solvers included).  If the
  * environment variable HR_AUTOTUNE_CACHE names a file, the choice is written
  * there as JSON and read back by later contexts.  Synchronises the stream.
+ * A lattice with twisted boundaries (hr_lattice.theta) runs one kernel
+ * whatever the shape: the call returns HR_OK at once, *result zeroed.
  * (The paper measures a hand-tuned kernel, Sec. 3; tuning per shape is this
  * library's way to reach the bandwidth bound on each lattice.) */
 hr_status hr_autotune_hop(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity out_parity,

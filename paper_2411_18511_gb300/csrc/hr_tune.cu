@@ -87,6 +87,9 @@ hr_status hr_autotune_hop(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec,
     if (st) return st;
     if (reps < 1 || reps > 10000) return set_error(ctx, HR_ERR_INVALID_ARG, "reps must lie in [1, 10000]");
     Geom g = make_geom(lat, n_rhs);
+    // twisted lattices run one kernel whatever the shape: nothing to tune, and
+    // the (untwisted) key of these extents keeps its own choice
+    if (g.twisted) return HR_OK;
     cudaStream_t s = (cudaStream_t)stream;
     HopLaunch L{};
     L.p = out_parity;
