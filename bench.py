@@ -593,13 +593,13 @@ def run_hmc(ctx, torch, hr, fields, synth):
     qd0 = fields.gauge_to_device(q0)
     # thermalisation: molecular dynamics from fresh momenta, kept without a Metropolis test
     warm = HMC(ctx, lat, beta=beta, m0=m0, fermions=True, n_steps=12, tau=1.0, seed=3006)
-    for _ in range(6):
+    for _ in range(30):
         eta = warm.draw_pseudofermion(qd0)
         info = hr.hr_hmc_trajectory(ctx, lat, warm.prm, qd0, warm.draw_momenta(), eta, warm.work)
     del warm
     out = {"lattice": list(lat), "beta": beta, "m0": m0, "tau": 1.0, "bc": "antiperiodic in time",
            "smeared_start_plaquette": round(plaq, 4), "thermalised_plaquette": round(info.plaquette, 4),
-           "thermalisation": "6 Omelyan trajectories of 12 steps without accept/reject"}
+           "thermalisation": "30 Omelyan trajectories of 12 steps without accept/reject"}
     for name, integ, steps, inner, mh in (("leapfrog_f64", hr.HR_INTEGRATOR_LEAPFROG, 24, hr.HR_F64, None),
                                           ("omelyan_f64", hr.HR_INTEGRATOR_OMELYAN, 12, hr.HR_F64, None),
                                           ("omelyan_f16_inner", hr.HR_INTEGRATOR_OMELYAN, 12, hr.HR_F16, None),

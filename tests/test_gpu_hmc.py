@@ -214,3 +214,25 @@ def test_hasenbusch_heat_bath_and_chain(ctx):
         acc, info = chain.step(q)
         assert np.isfinite(info.dH) and abs(info.dH) < 2.0
     assert chain.accepted >= 2
+
+
+@pytest.mark.parametrize("hasenbusch", [None, 0.4])
+def test_creutz_equality(ctx, hasenbusch):
+    """<exp(-dH)> = 1 over an equilibrium chain: a consequence of the MD being
+    reversible and area-preserving and of the heat baths drawing momenta and
+    pseudofermions from exp(-H), so it tests the whole update at once
+    (deterministic seeds; 4 standard errors of the mean)."""
+    lat = hr.Lattice((4, 4, 4, 4), 1)
+    q = dev(smeared(lat, 81))
+    chain = HMC(ctx, lat, beta=2.2, m0=0.1, fermions=True, n_steps=6, tau=0.5, seed=82,
+                m0_hasenbusch=hasenbusch)
+    for _ in range(40):
+        chain.step(q)
+    w = []
+    for _ in range(200):
+        acc, info = chain.step(q)
+        w.append(np.exp(-info.dH))
+    w = np.array(w)
+    err = w.std(ddof=1) / np.sqrt(len(w))
+    assert abs(w.mean() - 1.0) <= 4 * err + 1e-3, (w.mean(), err)
+    assert chain.accepted > 0.7 * chain.trajectories

@@ -414,3 +414,18 @@ def test_non_finite_theta_is_rejected(ctx):
     dst = fields.empty_spinor(lat, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
     with pytest.raises(hr.HrError, match="theta"):
         hr.hr_dirac_eo(ctx, lat, 0.1, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, hr.HR_OP_HOP, 1, gauge, src, dst)
+
+
+def test_tuner_skips_twisted_lattices(ctx):
+    """Tuning a twisted lattice times nothing and keeps the untwisted choice of the extents."""
+    dims = (4, 6, 8, 10)
+    plain, tw = hr.Lattice(dims), hr.Lattice(dims, 0, THETA)
+    q = synth.haar_links(dims, 171)
+    psi = fields.spinor_to_device(synth.gaussian_spinor(dims, 2, 172))
+    gauge = fields.pack_gauge(ctx, plain, hr.HR_FUND, hr.HR_F64, fields.gauge_to_device(q))
+    src = fields.pack_spinor(ctx, plain, hr.HR_FUND, hr.HR_F64, hr.HR_ODD, psi)
+    dst = fields.empty_spinor(plain, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
+    before = hr.hr_tune_lookup(ctx, plain, hr.HR_FUND, hr.HR_F64)
+    res = hr.hr_autotune_hop(ctx, tw, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, 1, gauge, src, dst, reps=2)
+    assert res.candidates == 0
+    assert hr.hr_tune_lookup(ctx, plain, hr.HR_FUND, hr.HR_F64) == before
