@@ -17,12 +17,18 @@ The readings here are the textbook ones:
   second-order minimum-norm scheme (lambda = 0.1931833275037836).
 * Hasenbusch mass preconditioning: two pseudofermions, one at a heavier mass
   and one for the ratio of the two determinants (class ``Hasenbusch``).
+* Multiple time scales (Sexton and Weingarten): with ``n_steps_gauge = m > 1``
+  the pseudofermion force moves the momenta on the outer integrator and every
+  outer link update of length t becomes m steps of the same integrator, of
+  length t/m, driven by the gauge force alone.
 
 Pinned in tests/test_oracle_hmc.py: the gauge force against central finite
 differences of S_g, the link update against a matrix exponential,
 reversibility of both integrators, second-order scaling of Delta H with the
 step size, and the fermion part through ``oracle.force`` (pinned by finite
-differences of a dense solve in tests/test_oracle_pins.py).
+differences of a dense solve in tests/test_oracle_pins.py); the two-level
+scheme against the single-level integrator (a vanishing outer force, and one
+inner leapfrog step), its reversibility and its second order.
 """
 
 from __future__ import annotations
@@ -205,12 +211,19 @@ class Hasenbusch:
         return F + self.heavy.force(q)
 
 
-def trajectory(dims, q, p, beta: float, n_steps: int, tau: float, integrator: int = LEAPFROG, fermions=None):
+def trajectory(dims, q, p, beta: float, n_steps: int, tau: float, integrator: int = LEAPFROG, fermions=None,
+               n_steps_gauge: int = 1):
     """One MD trajectory from (q, p).  Returns (q, p, info) with info holding
-    H at both ends and its parts."""
+    H at both ends and its parts.  n_steps_gauge > 1 (with fermions): two time
+    scales, see ``nested_steps``."""
     q = np.array(q, dtype=float)
     p = np.array(p, dtype=float)
     eps = tau / n_steps
+    if fermions is not None and n_steps_gauge > 1:
+        H0, parts0 = _hamiltonian(dims, q, p, beta, fermions)
+        q, p = nested_steps(dims, q, p, beta, n_steps, eps, integrator, fermions, n_steps_gauge)
+        H1, parts1 = _hamiltonian(dims, q, p, beta, fermions)
+        return q, p, {"H0": H0, "H1": H1, "dH": H1 - H0, "start": parts0, "end": parts1}
 
     def force(qq):
         F = gauge_force(dims, qq, beta)
@@ -241,3 +254,47 @@ def trajectory(dims, q, p, beta: float, n_steps: int, tau: float, integrator: in
         raise ValueError("integrator: LEAPFROG or OMELYAN")
     H1, parts1 = hamiltonian(q, p)
     return q, p, {"H0": H0, "H1": H1, "dH": H1 - H0, "start": parts0, "end": parts1}
+
+
+def _hamiltonian(dims, q, p, beta, fermions):
+    parts = {"kinetic": kinetic(p), "gauge": gauge_action(dims, q, beta), "fermion": fermions.action(q)}
+    return sum(parts.values()), parts
+
+
+def _gauge_steps(dims, q, p, beta, t, m, integrator):
+    """The inner level: m steps of length t/m driven by the gauge force alone."""
+    h = t / m
+    lam = OMELYAN_LAMBDA
+    for _ in range(m):
+        if integrator == LEAPFROG:
+            p = p - 0.5 * h * gauge_force(dims, q, beta)
+            q = link_update(q, p, h)
+            p = p - 0.5 * h * gauge_force(dims, q, beta)
+        else:
+            p = p - lam * h * gauge_force(dims, q, beta)
+            q = link_update(q, p, 0.5 * h)
+            p = p - (1.0 - 2.0 * lam) * h * gauge_force(dims, q, beta)
+            q = link_update(q, p, 0.5 * h)
+            p = p - lam * h * gauge_force(dims, q, beta)
+    return q, p
+
+
+def nested_steps(dims, q, p, beta, n_steps, eps, integrator, fermions, m):
+    """The outer level: n_steps steps of length eps whose momentum kicks use the
+    pseudofermion force alone and whose link updates of length t are m inner
+    steps of length t/m (``_gauge_steps``), same integrator on both levels."""
+    if integrator not in (LEAPFROG, OMELYAN):
+        raise ValueError("integrator: LEAPFROG or OMELYAN")
+    lam = OMELYAN_LAMBDA
+    for _ in range(n_steps):
+        if integrator == LEAPFROG:
+            p = p - 0.5 * eps * fermions.force(q)
+            q, p = _gauge_steps(dims, q, p, beta, eps, m, integrator)
+            p = p - 0.5 * eps * fermions.force(q)
+        else:
+            p = p - lam * eps * fermions.force(q)
+            q, p = _gauge_steps(dims, q, p, beta, 0.5 * eps, m, integrator)
+            p = p - (1.0 - 2.0 * lam) * eps * fermions.force(q)
+            q, p = _gauge_steps(dims, q, p, beta, 0.5 * eps, m, integrator)
+            p = p - lam * eps * fermions.force(q)
+    return q, p

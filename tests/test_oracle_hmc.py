@@ -189,3 +189,58 @@ def test_hasenbusch_trajectory_reversible_and_second_order(integrator):
     assert np.abs(q2 - q).max() < 1e-10 and np.abs(p2 + p).max() < 1e-9
     dh = [abs(hmc.trajectory(dims, q, p, 2.2, n, 0.5, integrator, ferm)[2]["dH"]) for n in (8, 16)]
     assert 3.8 < dh[0] / dh[1] < 4.2, dh
+
+
+# ---------------------------------------------------------------- multiple time scales
+
+class _NoFermions:
+    """A pseudofermion term with zero action and zero force."""
+
+    def action(self, q):
+        return 0.0
+
+    def force(self, q):
+        return np.zeros((4, q.shape[1], 3))
+
+
+@pytest.mark.parametrize("integrator", [hmc.LEAPFROG, hmc.OMELYAN])
+def test_nested_inner_level_is_the_single_level_integrator(integrator):
+    """With a vanishing outer force the two-level scheme is the gauge integrator
+    alone: n outer steps of m inner steps are n m leapfrog steps, or 2 n m
+    Omelyan steps (each outer Omelyan step drifts twice), of the single-level code."""
+    dims = (4, 4, 2, 2)
+    q = smeared(dims, 81)
+    p = momenta(dims, 82)
+    n, m = 3, 2
+    q1, p1, _ = hmc.trajectory(dims, q, p, 2.2, n, 0.6, integrator, _NoFermions(), n_steps_gauge=m)
+    k = n * m if integrator == hmc.LEAPFROG else 2 * n * m
+    q2, p2, _ = hmc.trajectory(dims, q, p, 2.2, k, 0.6, integrator)
+    assert np.abs(q1 - q2).max() < 1e-13 and np.abs(p1 - p2).max() < 1e-12
+
+
+def test_nested_leapfrog_with_one_inner_step_is_leapfrog():
+    """Momentum kicks commute, so one inner step per outer drift is plain leapfrog."""
+    dims = (4, 2, 2, 2)
+    m0 = 0.1
+    q = smeared(dims, 83)
+    p = momenta(dims, 84)
+    ferm = hmc.Fermions(dims, m0, pseudofermion(dims, m0, 85), bc=1)
+    q1, p1, i1 = hmc.trajectory(dims, q, p, 2.2, 3, 0.4, hmc.LEAPFROG, ferm)
+    qn, pn = hmc.nested_steps(dims, q, p, 2.2, 3, 0.4 / 3, hmc.LEAPFROG, ferm, 1)
+    assert np.abs(qn - q1).max() < 1e-12 and np.abs(pn - p1).max() < 1e-11
+
+
+@pytest.mark.parametrize("integrator", [hmc.LEAPFROG, hmc.OMELYAN])
+def test_nested_trajectory_reversible_and_second_order(integrator):
+    dims = (4, 2, 2, 2)
+    m0 = 0.1
+    q = smeared(dims, 86)
+    p = momenta(dims, 87)
+    ferm = hmc.Fermions(dims, m0, pseudofermion(dims, m0, 88), bc=1)
+    q1, p1, i1 = hmc.trajectory(dims, q, p, 2.2, 3, 0.4, integrator, ferm, n_steps_gauge=3)
+    q2, p2, i2 = hmc.trajectory(dims, q1, -p1, 2.2, 3, 0.4, integrator, ferm, n_steps_gauge=3)
+    assert np.abs(q2 - q).max() < 1e-10 and np.abs(p2 + p).max() < 1e-9
+    assert abs(i1["dH"] + i2["dH"]) < 1e-9
+    dh = [abs(hmc.trajectory(dims, q, p, 2.2, n, 0.5, integrator, ferm, n_steps_gauge=2)[2]["dH"])
+          for n in (8, 16, 32)]
+    assert 3.8 < dh[0] / dh[1] < 4.2 and 3.8 < dh[1] / dh[2] < 4.2, dh
