@@ -365,6 +365,8 @@ typedef struct {
     hr_solver_opts solver;    /* CG of the force and of S_f (tol, inner precision, ...) */
     int hasenbusch;           /* 1: Hasenbusch mass preconditioning (two pseudofermions) */
     double m0_hasenbusch;     /* its heavier mass                                      */
+    int n_steps_gauge;        /* two time scales: gauge-force steps per link update of */
+                              /* the fermion integrator (> 1); 0 or 1: one time scale  */
 } hr_hmc_params;
 
 typedef struct {
@@ -392,7 +394,13 @@ size_t hr_hmc_workspace_bytes(hr_lattice lat, const hr_hmc_params *prm);
  * Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2; each force then takes two solves.  Leapfrog: p -= eps/2 F, U <- exp(i eps p) U,
  * p -= eps/2 F; Omelyan: p -= l eps F, U <- exp(i eps/2 p) U, p -= (1-2l) eps F,
  * U <- exp(i eps/2 p) U, p -= l eps F, l = 0.1931833275037836; the force of
- * the current links is reused between steps.  Each fermion force and S_f takes
+ * the current links is reused between steps.  With n_steps_gauge = m > 1 and
+ * fermions (Sexton and Weingarten's multiple time scales; the paper gives no
+ * integrator), the kicks of that scheme use the pseudofermion force alone and
+ * each of its link updates, of length t, becomes m steps of length t / m of
+ * the same integrator driven by the gauge force alone: as many solves as
+ * with m = 1, m times (leapfrog; 2m, Omelyan) as many gauge-force steps.
+ * Each fermion force and S_f takes
  * one hr_cg_solve (from x = 0) on the packed links (lat.bc applies).  The
  * Metropolis test on info->dH and the draw of mom and eta are the caller's.
  * Synchronises the stream. */

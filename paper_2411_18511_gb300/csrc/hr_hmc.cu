@@ -240,9 +240,12 @@ hr_status mom_update(hr_ctx *ctx, const Geom &g, double eps, const double *F, do
 
 // ---------------------------------------------------------------- trajectory
 
+constexpr double kOmelyanLambda = 0.1931833275037836; // Omelyan's minimum-norm second-order scheme
+
 struct HmcWork {
     void *gauge;      // packed FP64 fundamental links (with the boundary signs)
     double *F;        // force [4][V][3]
+    double *Fg;       // gauge force of the inner level (two time scales)
     void *X;          // even half: (Mhat^+ Mhat)^-1 eta (Hasenbusch: at the heavy mass)
     void *X2, *eta2;  // Hasenbusch ratio term: eta2 = Mhat_H^+ phi, X2 = (Mhat^+ Mhat)^-1 eta2
     void *e1, *e2;    // even temporaries (g5 copies)
@@ -251,6 +254,9 @@ struct HmcWork {
     void *cg;         // CG workspace
     size_t cg_bytes;
 };
+
+// two time scales: the fermion integrator's link updates run inner gauge steps
+bool nested(const hr_hmc_params &prm) { return prm.fermions && prm.n_steps_gauge > 1; }
 
 size_t layout_hmc(hr_lattice lat, const hr_hmc_params &prm, char *w, HmcWork *hw)
 {
@@ -269,6 +275,7 @@ size_t layout_hmc(hr_lattice lat, const hr_hmc_params &prm, char *w, HmcWork *hw
     };
     void *gauge = take(gb);
     void *F = take(sizeof(double) * 12 * V);
+    void *Fg = nested(prm) ? take(sizeof(double) * 12 * V) : nullptr;
     void *X = take(half), *a = take(2 * half), *b = take(2 * half), *t = take(half);
     void *X2 = nullptr, *eta2 = nullptr, *e1 = nullptr, *e2 = nullptr;
     if (prm.hasenbusch) {
@@ -278,7 +285,7 @@ size_t layout_hmc(hr_lattice lat, const hr_hmc_params &prm, char *w, HmcWork *hw
         e2 = take(half);
     }
     void *cg = take(cgb);
-    if (hw) *hw = HmcWork{gauge, (double *)F, X, X2, eta2, e1, e2, a, b, t, cg, cgb};
+    if (hw) *hw = HmcWork{gauge, (double *)F, (double *)Fg, X, X2, eta2, e1, e2, a, b, t, cg, cgb};
     return off;
 }
 
@@ -398,13 +405,28 @@ struct Trajectory {
         return st;
     }
 
+    hr_status zero(double *F)
+    {
+        cudaError_t e = cudaMemsetAsync(F, 0, sizeof(double) * 24 * g.vh, s);
+        return e == cudaSuccess ? HR_OK : set_error(ctx, HR_ERR_CUDA, "force reset: %s", cudaGetErrorString(e));
+    }
+
+    // F = the gauge force plus the pseudofermion force of the current links
     hr_status force()
     {
         if (force_valid) return HR_OK;
-        cudaError_t e = cudaMemsetAsync(w.F, 0, sizeof(double) * 24 * g.vh, s);
-        if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "force reset: %s", cudaGetErrorString(e));
-        hr_status st = gauge_force(ctx, g, prm.beta, q, 1.0, w.F, s);
-        if (!st && prm.fermions) {
+        hr_status st = zero(w.F);
+        if (!st) st = gauge_force(ctx, g, prm.beta, q, 1.0, w.F, s);
+        if (!st) st = fermion_terms();
+        if (!st) force_valid = true;
+        return st;
+    }
+
+    // F += the pseudofermion force of the current links
+    hr_status fermion_terms()
+    {
+        hr_status st = HR_OK;
+        if (prm.fermions) {
             st = solve();
             if (!st) st = solve_force(eta_mass(), w.X);
             if (!st && prm.hasenbusch) {
@@ -418,7 +440,6 @@ struct Trajectory {
                 if (!st) st = pair_force(w.e1, w.e2, -2.0 / (4.0 * (4.0 + prm.m0_hasenbusch)));
             }
         }
-        if (!st) force_valid = true;
         return st;
     }
 
@@ -431,9 +452,66 @@ struct Trajectory {
 
     hr_status drift(double eps)
     {
-        force_valid = false;
+        force_valid = ferm_valid = gauge_valid = false;
         x_valid = false;
         return link_update(ctx, g, eps, p, q, s);
+    }
+
+    // ---- two time scales (n_steps_gauge > 1): F holds the pseudofermion
+    // force alone, Fg the gauge force, each reused until the links move
+    bool ferm_valid = false, gauge_valid = false;
+
+    hr_status kick_fermion(double eps)
+    {
+        hr_status st = HR_OK;
+        if (!ferm_valid) {
+            st = zero(w.F);
+            if (!st) st = fermion_terms();
+            if (!st) ferm_valid = true;
+        }
+        if (!st) st = mom_update(ctx, g, eps, w.F, p, s);
+        return st;
+    }
+
+    hr_status kick_gauge(double eps)
+    {
+        hr_status st = HR_OK;
+        if (!gauge_valid) {
+            st = zero(w.Fg);
+            if (!st) st = gauge_force(ctx, g, prm.beta, q, 1.0, w.Fg, s);
+            if (!st) gauge_valid = true;
+        }
+        if (!st) st = mom_update(ctx, g, eps, w.Fg, p, s);
+        return st;
+    }
+
+    // one step of length eps of the integrator with the given kick and drift
+    template <class Kick, class Drift> hr_status step(double eps, Kick kick_fn, Drift drift_fn)
+    {
+        hr_status st;
+        if (prm.integrator == HR_INTEGRATOR_LEAPFROG) {
+            st = kick_fn(0.5 * eps);
+            if (!st) st = drift_fn(eps);
+            if (!st) st = kick_fn(0.5 * eps);
+        } else {
+            const double lam = kOmelyanLambda;
+            st = kick_fn(lam * eps);
+            if (!st) st = drift_fn(0.5 * eps);
+            if (!st) st = kick_fn((1.0 - 2.0 * lam) * eps);
+            if (!st) st = drift_fn(0.5 * eps);
+            if (!st) st = kick_fn(lam * eps);
+        }
+        return st;
+    }
+
+    // the outer level's link update of length t: n_steps_gauge gauge steps
+    hr_status inner(double t)
+    {
+        const int m = prm.n_steps_gauge;
+        hr_status st = HR_OK;
+        for (int j = 0; j < m && !st; ++j)
+            st = step(t / m, [&](double e) { return kick_gauge(e); }, [&](double e) { return drift(e); });
+        return st;
     }
 
     double plaq = 0.0;
@@ -527,6 +605,8 @@ hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *pr
     if (prm->fermions && prm->hasenbusch && !(4.0 + prm->m0_hasenbusch != 0.0))
         return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0_hasenbusch must be nonzero");
     if (prm->hasenbusch && !prm->fermions) return set_error(ctx, HR_ERR_INVALID_ARG, "Hasenbusch needs fermions");
+    if (prm->n_steps_gauge < 0 || prm->n_steps_gauge > 1000)
+        return set_error(ctx, HR_ERR_INVALID_ARG, "n_steps_gauge must lie in [0, 1000]");
     if (prm->fermions && prm->hasenbusch) st = check_buffers(ctx, {eta, phi}, {gauge, mom}, {work});
     else if (prm->fermions) st = check_buffers(ctx, {eta}, {gauge, mom}, {work});
     else st = check_buffers(ctx, {}, {gauge, mom}, {work});
@@ -553,19 +633,12 @@ hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *pr
     double K0, Sg0, Sf0, K1, Sg1, Sf1;
     st = T.hamiltonian(K0, Sg0, Sf0);
     const double eps = prm->tau / prm->n_steps;
+    const bool two_scales = nested(*prm);
     for (int k = 0; k < prm->n_steps && !st; ++k) {
-        if (prm->integrator == HR_INTEGRATOR_LEAPFROG) {
-            st = T.kick(0.5 * eps);
-            if (!st) st = T.drift(eps);
-            if (!st) st = T.kick(0.5 * eps);
-        } else {
-            const double lam = 0.1931833275037836; // Omelyan's minimum-norm second-order scheme
-            st = T.kick(lam * eps);
-            if (!st) st = T.drift(0.5 * eps);
-            if (!st) st = T.kick((1.0 - 2.0 * lam) * eps);
-            if (!st) st = T.drift(0.5 * eps);
-            if (!st) st = T.kick(lam * eps);
-        }
+        if (two_scales)
+            st = T.step(eps, [&](double e) { return T.kick_fermion(e); }, [&](double e) { return T.inner(e); });
+        else
+            st = T.step(eps, [&](double e) { return T.kick(e); }, [&](double e) { return T.drift(e); });
     }
     if (!st) st = T.hamiltonian(K1, Sg1, Sf1);
     if (st) return st;

@@ -24,7 +24,7 @@ class HMC:
     def __init__(self, ctx: hr.Context, dims, beta: float, m0: float = 0.0, fermions: bool = True,
                  n_steps: int = 10, tau: float = 1.0, integrator: int = hr.HR_INTEGRATOR_OMELYAN,
                  solver: hr.hr_solver_opts | None = None, seed: int = 0, device="cuda",
-                 m0_hasenbusch: float | None = None):
+                 m0_hasenbusch: float | None = None, n_steps_gauge: int = 1):
         self.ctx, self.dims, self.device = ctx, dims, device
         self.prm = hr.hr_hmc_params_default(beta, m0, fermions, n_steps, tau, integrator)
         if solver is not None:
@@ -32,6 +32,7 @@ class HMC:
         if m0_hasenbusch is not None:
             self.prm.hasenbusch = 1
             self.prm.m0_hasenbusch = float(m0_hasenbusch)
+        self.prm.n_steps_gauge = int(n_steps_gauge)
         self.work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(dims, self.prm), device)
         self.V = fields.volume(dims)
         self.gen = torch.Generator(device=device)

@@ -97,7 +97,8 @@ class hr_solver_opts(ctypes.Structure):
 class hr_hmc_params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("m0", ctypes.c_double), ("fermions", ctypes.c_int),
                 ("n_steps", ctypes.c_int), ("tau", ctypes.c_double), ("integrator", ctypes.c_int),
-                ("solver", hr_solver_opts), ("hasenbusch", ctypes.c_int), ("m0_hasenbusch", ctypes.c_double)]
+                ("solver", hr_solver_opts), ("hasenbusch", ctypes.c_int), ("m0_hasenbusch", ctypes.c_double),
+                ("n_steps_gauge", ctypes.c_int)]
 
 
 class hr_hmc_info(ctypes.Structure):
@@ -519,6 +520,7 @@ def hr_hmc_params_default(beta: float, m0: float = 0.0, fermions: bool = True, n
     prm.beta, prm.m0, prm.fermions = float(beta), float(m0), int(bool(fermions))
     prm.n_steps, prm.tau, prm.integrator = int(n_steps), float(tau), int(integrator)
     prm.solver = hr_solver_default_opts()
+    prm.n_steps_gauge = 1
     return prm
 
 

@@ -236,3 +236,50 @@ def test_creutz_equality(ctx, hasenbusch):
     err = w.std(ddof=1) / np.sqrt(len(w))
     assert abs(w.mean() - 1.0) <= 4 * err + 1e-3, (w.mean(), err)
     assert chain.accepted > 0.7 * chain.trajectories
+
+
+@pytest.mark.parametrize("hasenbusch", [False, True])
+@pytest.mark.parametrize("integrator", [hr.HR_INTEGRATOR_LEAPFROG, hr.HR_INTEGRATOR_OMELYAN])
+def test_two_time_scales_match_oracle(ctx, integrator, hasenbusch):
+    """n_steps_gauge = 3: the pseudofermion force on the outer level, three gauge
+    steps per outer link update, against the oracle's nested integrator."""
+    lat = hr.Lattice((4, 2, 2, 4), 1)
+    beta, m0, mh = 2.2, 0.1, 0.6
+    q = smeared(lat, 91)
+    p = np.random.default_rng(92).normal(size=(4, int(np.prod(lat)), 3))
+    prm = hr.hr_hmc_params_default(beta, m0, True, 2, 0.3, integrator)
+    prm.solver.tol = 1e-13
+    prm.n_steps_gauge = 3
+    eta, eta_p = eta_field(ctx, lat, m0, 93)
+    phi = phi_p = None
+    if hasenbusch:
+        prm.hasenbusch, prm.m0_hasenbusch = 1, mh
+        phi, phi_p = eta_field(ctx, lat, m0, 94)
+    qg, pg, info = run_gpu(ctx, lat, q, p, prm, eta_p, phi_p)
+    ferm = ohmc.Hasenbusch(lat, m0, mh, eta, phi, bc=1) if hasenbusch else ohmc.Fermions(lat, m0, eta, bc=1)
+    qo, po, io = ohmc.trajectory(lat, q, p, beta, 2, 0.3, integrator, ferm, n_steps_gauge=3)
+    assert np.abs(qg - qo).max() <= 1e-11
+    assert np.abs(pg - po).max() <= 1e-9
+    assert abs(info.dH - io["dH"]) <= 1e-9, (info.dH, io["dH"])
+    # and it is not the one-scale trajectory
+    q1, _, _ = ohmc.trajectory(lat, q, p, beta, 2, 0.3, integrator, ferm)
+    assert np.abs(q1 - qo).max() > 1e-8
+
+
+def test_two_time_scales_reversible(ctx):
+    lat = hr.Lattice((8, 8, 4, 4), 1)
+    beta, m0 = 2.2, 0.05
+    q = smeared(lat, 95)
+    p = np.random.default_rng(96).normal(size=(4, int(np.prod(lat)), 3))
+    prm = hr.hr_hmc_params_default(beta, m0, True, 3, 0.5, hr.HR_INTEGRATOR_OMELYAN)
+    prm.solver.tol = 1e-12
+    prm.n_steps_gauge = 4
+    _, eta_p = eta_field(ctx, lat, m0, 97)
+    q1, p1, i1 = run_gpu(ctx, lat, q, p, prm, eta_p)
+    q2, p2, i2 = run_gpu(ctx, lat, q1, -p1, prm, eta_p)
+    assert np.abs(q2 - q).max() <= 1e-9
+    assert np.abs(p2 + p).max() <= 1e-7
+    assert abs(i1.dH + i2.dH) <= 1e-7
+    prm.n_steps_gauge = -1
+    with pytest.raises(hr.HrError):
+        run_gpu(ctx, lat, q, p, prm, eta_p)
