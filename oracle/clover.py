@@ -28,7 +28,10 @@ oracle.  Library routines used as steps: ``numpy.linalg.inv`` for A_oo^-1 and
 Pinned in tests/test_oracle_clover.py: the closed form of a constant abelian
 field (F_01 = i sin(B) s_3 on every site), the free field (A = 4 + m0),
 Hermiticity and chirality of A, gauge covariance, and an independent dense
-build (tests/dense_ref.py).
+build (tests/dense_ref.py).  The HMC force of the clover term (bottom of this
+file: the derivative through the leaves, the pseudofermion and det A_oo
+terms) is pinned in tests/test_oracle_clover_force.py by finite differences,
+the whole force against dense-matrix actions.
 """
 
 from __future__ import annotations
@@ -215,3 +218,132 @@ def eo_reconstruct(dims, L, A, b, xe, bc=None, theta=None) -> np.ndarray:
     x = np.array(xe, dtype=np.complex128)
     x[odd] = apply_site(np.linalg.inv(A[odd]), np.asarray(b, dtype=np.complex128)[odd] + 0.5 * h[odd])
     return x
+
+
+# ---------------------------------------------------------------- link derivatives (fundamental)
+#
+# The HMC force of the clover term (SW form).  With the site term in the
+# even-odd operator, Mhat = A_ee - H_eo A_oo^-1 H_oe / 4, two flavours weigh
+# det(D^+ D) = det(A_oo)^2 det(Mhat^+ Mhat): the pseudofermion action
+# S_pf = Re <eta, (Mhat^+ Mhat)^-1 eta> and S_det = -2 sum_{x odd} log det A(x).
+# With X = (Mhat^+ Mhat)^-1 eta, Y = Mhat X, Z = A_oo^-1 H_oe X and
+# W = A_oo^-1 H_eo^+ Y (odd sites), dS_pf = -2 Re <Y, dMhat X> splits into
+#   the hops:       1/2 d Re <a, H b>,  a = (Y, W), b = (X, Z),
+#   the site term:  Re sum_x tr[dA(x) Lam(x)],  Lam = -2 X Y^+ (even), -1/2 Z W^+ (odd),
+# and dS_det = Re sum_x tr[dA(x) Lam_det(x)], Lam_det = -2 A(x)^-1 (odd).
+# dA = c_sw dC, and C depends on the links through the leaves of F_mn.
+
+_T = [0.5j * np.array([[0, 1], [1, 0]], dtype=complex), 0.5j * np.array([[0, -1j], [1j, 0]]),
+      0.5j * np.array([[1, 0], [0, -1]], dtype=complex)]  # generators i s_a / 2
+
+
+def _leaf_factors(mu: int, nu: int):
+    """The four leaves of Q_mn(x), as in ``clover_leaves``: lists of
+    (direction, (steps along mu, steps along nu) from x, daggered)."""
+    return [[(mu, (0, 0), False), (nu, (1, 0), False), (mu, (0, 1), True), (nu, (0, 0), True)],
+            [(nu, (0, 0), False), (mu, (-1, 1), True), (nu, (-1, 0), True), (mu, (-1, 0), False)],
+            [(mu, (-1, 0), True), (nu, (-1, -1), True), (mu, (-1, -1), False), (nu, (0, -1), False)],
+            [(nu, (0, -1), True), (mu, (0, -1), False), (nu, (1, -1), False), (mu, (0, 0), True)]]
+
+
+def clover_derivative(dims, L, Lam) -> np.ndarray:
+    """G[rho, z, a] = d/dw_a Re sum_y tr[C(y) Lam(y)] under U_rho(z) -> exp(i w.s/2) U_rho(z),
+    fundamental links L [4, V, 2, 2], Lam [V, 8, 8] (index s * 2 + c).
+
+    tr[C Lam] = (i/2) sum_{mu<nu} tr_c[F_mn K_mn] with K_mn = tr_s[(s_mn (x) 1) Lam]
+    (the mu > nu terms repeat the mu < nu ones), F_mn = (Q_mn - Q_mn^+) / 8.  For a
+    leaf P = A V B whose factor V is the varied link U (V = U) or its inverse
+    (V = U^+), dU = X U with X = i w.s/2 anti-Hermitian, and
+      tr[dP K] - tr[dP^+ K] = tr[X (U B K A + A^+ K B^+ U^+)]      (V = U),
+                            = -tr[X (B K A U^+ + U A^+ K B^+)]     (V = U^+),
+    so each occurrence adds Re[(i/16) tr(T_a G)] to the link's component a."""
+    V = L.shape[1]
+    fwd, bwd = _neighbours(dims)
+    Lam = np.asarray(Lam, dtype=np.complex128).reshape(V, 4, 2, 4, 2)
+    G = np.zeros((4, V, 3))
+    eye = np.broadcast_to(np.eye(2, dtype=complex), (V, 2, 2))
+
+    def site(mu, nu, a, b):
+        """index of y + a mu-hat + b nu-hat for every y"""
+        idx = np.arange(V)
+        for _ in range(abs(a)):
+            idx = (fwd if a > 0 else bwd)[mu][idx]
+        for _ in range(abs(b)):
+            idx = (fwd if b > 0 else bwd)[nu][idx]
+        return idx
+
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            K = np.einsum("st,xtbsa->xba", sigma(mu, nu), Lam)   # K_mn(y)[b, a]
+            for leaf in _leaf_factors(mu, nu):
+                where = [site(mu, nu, a, b) for _, (a, b), _ in leaf]
+                mats = [(_dag(L[d][z]) if dag else L[d][z]) for (d, _, dag), z in zip(leaf, where)]
+                for k, (d, _, dag) in enumerate(leaf):
+                    A = _mm(eye, *mats[:k])
+                    B = _mm(eye, *mats[k + 1:])
+                    U = L[d][where[k]]
+                    if not dag:
+                        Gm = _mm(U, B, K, A) + _mm(_dag(A), K, _dag(B), _dag(U))
+                    else:
+                        Gm = -(_mm(B, K, A, _dag(U)) + _mm(U, _dag(A), K, _dag(B)))
+                    for a in range(3):
+                        val = np.real(1j / 16.0 * np.einsum("ij,xji->x", _T[a], Gm))
+                        np.add.at(G[d, :, a], where[k], val)
+    return G
+
+
+def det_action(A, dims) -> float:
+    """S_det = -2 sum_{x odd} log det A(x) (A Hermitian positive definite)."""
+    from . import parity_mask
+
+    odd = parity_mask(dims) == 1
+    sign, logdet = np.linalg.slogdet(A[odd])
+    assert np.all(sign.real > 0)
+    return float(-2.0 * np.sum(logdet.real))
+
+
+class CloverFermions:
+    """Two flavours of clover (SW) fermions through the even-odd pseudofermion:
+    S = S_pf + S_det (see above) and its su(2) force, for HMC trajectories
+    (``oracle.hmc.trajectory`` takes it as its ``fermions``)."""
+
+    def __init__(self, dims, m0: float, csw: float, eta, bc=0, tol: float = 1e-13, theta=None):
+        self.dims, self.m0, self.csw, self.eta, self.bc, self.tol, self.theta = dims, m0, csw, eta, bc, tol, theta
+        self.iters = 0
+
+    def _setup(self, q):
+        from . import expand_links
+
+        L = expand_links(self.dims, 2, q)
+        A = site_term(self.dims, L, self.m0, self.csw, KIND_SW)
+        return L, A
+
+    def solve(self, q):
+        L, A = self._setup(q)
+        x, it, tr, ok = cg(self.dims, L, A, self.eta, tol=self.tol, maxiter=50000, bc=self.bc, theta=self.theta)
+        assert ok, tr
+        self.iters += it
+        return L, A, x
+
+    def action(self, q) -> float:
+        L, A, x = self.solve(q)
+        return float(np.vdot(self.eta, x).real) + det_action(A, self.dims)
+
+    def force(self, q) -> np.ndarray:
+        from . import force, gamma5, hop, parity_mask
+
+        L, A, X = self.solve(q)
+        d, kw = self.dims, dict(bc=self.bc, theta=self.theta)
+        odd = parity_mask(d) == 1
+        Ainv = np.zeros_like(A)
+        Ainv[odd] = np.linalg.inv(A[odd])
+        Y = schur(d, L, A, X, **kw)
+        Z = apply_site(Ainv, hop(d, L, X, parity=1, **kw))                       # A_oo^-1 H_oe X
+        W = apply_site(Ainv, gamma5(hop(d, L, gamma5(Y), parity=1, **kw)))     # A_oo^-1 H_eo^+ Y
+        a = np.where(odd[:, None, None], W, Y)
+        b = np.where(odd[:, None, None], Z, X)
+        F = 0.5 * force(d, L, a, b, **kw)
+        V = X.shape[0]
+        outer = lambda u, v: np.einsum("xi,xj->xij", u.reshape(V, 8), np.conj(v.reshape(V, 8)))  # noqa: E731
+        Lam = np.where(odd[:, None, None], -0.5 * outer(Z, W) - 2.0 * Ainv, -2.0 * outer(X, Y))
+        return F + self.csw * clover_derivative(d, L, Lam)
