@@ -323,6 +323,46 @@ hr_status hr_solve_full_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const hr
                                hr_system system, const void *gauge, const void *clover, const void *b, void *x,
                                hr_solve_info *info, void *work, size_t work_bytes, hr_stream stream);
 
+/* ---- the clover term in the HMC (fundamental links, SW form) ----
+ * The paper measures the clover operator (Sec. 2.2) and names the HMC as its
+ * consumer; these calls give the molecular-dynamics force and action of the
+ * term.  With the site term, two flavours weigh det(D^+ D) = det(A_oo)^2
+ * det(Mhat^+ Mhat): S = S_pf + S_det, S_pf = Re<eta, (Mhat^+ Mhat)^-1 eta>,
+ * S_det = -2 sum_{x odd} log det A(x).  Forces are dS/dw_a under
+ * U_mu(x) -> exp(i w.s/2) U_mu(x), [4][V][3] doubles, accumulated (+=), as
+ * hr_force.  The derivative of C(x) runs through the 8 leaves of each plane
+ * that hold a link (one thread per link, native FP64). */
+
+/* Work bytes of hr_clover_insertion_force and hr_clover_fermion_force. */
+size_t hr_clover_force_workspace_bytes(hr_lattice lat);
+
+/* force += coeff c_sw d/dw Re sum_x tr[C(x) lam(x)]: gauge is the canonical
+ * FP64 field (double[4][V][4], without boundary signs, which cancel around
+ * the leaves); lam is a device array of complex doubles [V][8][8] (row and
+ * column index spin * 2 + colour, lexicographic sites). */
+hr_status hr_clover_insertion_force(hr_ctx *ctx, hr_lattice lat, double c_sw, const double *gauge,
+                                    const double *lam, double coeff, double *force, void *work, size_t work_bytes,
+                                    hr_stream stream);
+
+/* force += coeff dS/dw for S_pf (and S_det if with_det) at the links of
+ * gauge (canonical) / gauge_packed (hr_gauge_pack of the same links, HR_FUND
+ * HR_F64) and clover (HR_FUND HR_F64, hr_clover_build with HR_CLOVER_SW, m0,
+ * c_sw of those links), X = (Mhat^+ Mhat)^-1 eta (packed HR_F64 even): with
+ * Y = Mhat X, Z = A_oo^-1 H_oe X, W = A_oo^-1 H_eo^+ Y, the hops give
+ * 1/2 dRe<(Y, W), H (X, Z)> (hr_force) and the site term c_sw times the
+ * insertion force of Lam = -2 X Y^+ on even sites, -1/2 Z W^+ - 2 A^-1 [det]
+ * on odd sites.  lat.bc and lat.theta apply to the hops. */
+hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, double m0, double c_sw, const double *gauge,
+                                  const void *gauge_packed, const void *clover, const void *X, int with_det,
+                                  double coeff, double *force, void *work, size_t work_bytes, hr_stream stream);
+
+/* *logdet = sum over the sites of `parity` of log det A(x) (both chiral
+ * blocks, by Cholesky) from an FP64 clover field (HR_FUND or HR_ADJ).
+ * HR_ERR_NUMERIC if a block is not positive definite.  Synchronises the
+ * stream. */
+hr_status hr_clover_logdet(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *clover, hr_parity parity,
+                           double *logdet, hr_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* HMC molecular dynamics (Sec. 1 and 2.1 name the HMC as the consumer)      */
 /* ---------------------------------------------------------------------- */

@@ -330,9 +330,16 @@ class CloverFermions:
         return float(np.vdot(self.eta, x).real) + det_action(A, self.dims)
 
     def force(self, q) -> np.ndarray:
+        L, A, X = self.solve(q)
+        return self.force_at(q, X)
+
+    def force_at(self, q, X, det: bool = True) -> np.ndarray:
+        """The force for a given even X (X = (Mhat^+ Mhat)^-1 eta in the HMC;
+        det=False leaves out the det A_oo term)."""
         from . import force, gamma5, hop, parity_mask
 
-        L, A, X = self.solve(q)
+        L, A = self._setup(q)
+        X = np.asarray(X, dtype=np.complex128)
         d, kw = self.dims, dict(bc=self.bc, theta=self.theta)
         odd = parity_mask(d) == 1
         Ainv = np.zeros_like(A)
@@ -345,5 +352,5 @@ class CloverFermions:
         F = 0.5 * force(d, L, a, b, **kw)
         V = X.shape[0]
         outer = lambda u, v: np.einsum("xi,xj->xij", u.reshape(V, 8), np.conj(v.reshape(V, 8)))  # noqa: E731
-        Lam = np.where(odd[:, None, None], -0.5 * outer(Z, W) - 2.0 * Ainv, -2.0 * outer(X, Y))
+        Lam = np.where(odd[:, None, None], -0.5 * outer(Z, W) - (2.0 * Ainv if det else 0.0), -2.0 * outer(X, Y))
         return F + self.csw * clover_derivative(d, L, Lam)

@@ -552,3 +552,415 @@ hr_status hr_dirac_eo_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec pr
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------- HMC force of the clover term
+//
+// Fundamental links, SW form.  For a spin-colour insertion Lam(y),
+//   f = Re sum_y tr[C(y) Lam(y)] = Re sum_y (i/2) sum_{mu<nu} tr_c[F_mn(y) K_mn(y)],
+// and in the chiral blocks (C+ on spins 0, 1, C- on 2, 3, as in the build), with
+// P_l^b = sum_{s,t} (s_l)_st Lam[(2b+t, .), (2b+s, .)] (colour 2x2),
+//   K_0l = P_l^1 - P_l^0,  K_23 = -(P_1^0 + P_1^1),  K_13 = P_2^0 + P_2^1,  K_12 = -(P_3^0 + P_3^1).
+// K field: double [V][6][2][2][2] (lexicographic site, planes 01 02 03 12 13 23).
+// The link derivative of f: each link occurs in 8 leaves of each of the 3
+// planes that contain its direction; for a leaf P = A V B whose factor V is
+// the link U (or U^+), dU = X U with X = i w.s/2, and
+//   tr[dP K] - tr[dP^+ K] = tr[X (U B K A + A^+ K B^+ U^+)]     (V = U)
+//                         = -tr[X (B K A U^+ + U A^+ K B^+)]    (V = U^+),
+// so the link's component a gains Re[(i/16) tr((i s_a/2) G)] = -Re tr(s_a G) / 32.
+//
+// Two flavours of clover fermions through the even-odd pseudofermion (Mhat =
+// A_ee - H_eo A_oo^-1 H_oe / 4): with X = (Mhat^+ Mhat)^-1 eta, Y = Mhat X,
+// Z = A_oo^-1 H_oe X, W = A_oo^-1 H_eo^+ Y,
+//   dS_pf = 1/2 dRe<a, H b> (a = (Y, W), b = (X, Z)) + c_sw df[Lam],
+//   Lam = -2 X Y^+ (even), -1/2 Z W^+ (odd),
+// and S_det = -2 sum_{odd} log det A adds Lam_det = -2 A^-1 (odd).
+
+namespace {
+
+__constant__ int kPlane[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+// (s_l)_st, l = 0, 1, 2 for s_1, s_2, s_3
+__device__ __forceinline__ zc pauli(int l, int s, int t)
+{
+    if (l == 0) return {s != t ? 1.0 : 0.0, 0.0};
+    if (l == 1) return s == t ? zc{0.0, 0.0} : (s == 0 ? zc{0.0, -1.0} : zc{0.0, 1.0});
+    return {s != t ? 0.0 : (s == 0 ? 1.0 : -1.0), 0.0};
+}
+
+// P[b][l][d][c] += coef * lam((2b+t, d), (2b+s, c)) summed with (s_l)_st
+template <class Lam> __device__ void add_blocks(zc (&P)[2][3][2][2], double coef, Lam lam)
+{
+    for (int b = 0; b < 2; ++b)
+        for (int l = 0; l < 3; ++l)
+            for (int d = 0; d < 2; ++d)
+                for (int c = 0; c < 2; ++c) {
+                    zc acc = {0.0, 0.0};
+                    for (int s = 0; s < 2; ++s)
+                        for (int t = 0; t < 2; ++t) {
+                            const zc sg = pauli(l, s, t);
+                            if (sg.re == 0.0 && sg.im == 0.0) continue;
+                            acc = zadd(acc, zmul(sg, lam(2 * b + t, d, 2 * b + s, c)));
+                        }
+                    P[b][l][d][c] = zadd(P[b][l][d][c], zscale(coef, acc));
+                }
+}
+
+__device__ void store_k(double *K, long long x, const zc (&P)[2][3][2][2])
+{
+    for (int d = 0; d < 2; ++d)
+        for (int c = 0; c < 2; ++c) {
+            zc k[6];
+            k[0] = zsub(P[1][0][d][c], P[0][0][d][c]);
+            k[1] = zsub(P[1][1][d][c], P[0][1][d][c]);
+            k[2] = zsub(P[1][2][d][c], P[0][2][d][c]);
+            k[3] = zscale(-1.0, zadd(P[0][2][d][c], P[1][2][d][c])); // 12: -(P_3^0 + P_3^1)
+            k[4] = zadd(P[0][1][d][c], P[1][1][d][c]);               // 13: P_2^0 + P_2^1
+            k[5] = zscale(-1.0, zadd(P[0][0][d][c], P[1][0][d][c])); // 23: -(P_1^0 + P_1^1)
+            for (int pl = 0; pl < 6; ++pl) {
+                double *o = K + ((x * 6 + pl) * 4 + d * 2 + c) * 2;
+                o[0] = k[pl].re;
+                o[1] = k[pl].im;
+            }
+        }
+}
+
+// K from a canonical insertion Lam: complex [V][8][8], index spin * 2 + colour
+__global__ void k_clover_k_from_lam(long long V, const double *lam, double *K)
+{
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= V) return;
+    const double *L = lam + x * 128;
+    zc P[2][3][2][2] = {};
+    add_blocks(P, 1.0, [&](int t, int d, int s, int c) {
+        const int r = t * 2 + d, q = s * 2 + c;
+        return zc{L[(r * 8 + q) * 2], L[(r * 8 + q) * 2 + 1]};
+    });
+    store_k(K, x, P);
+}
+
+struct KFieldArgs {
+    Geom g;
+    const void *X, *Y; // even halves (packed FP64)
+    const void *Z, *W; // odd halves
+    const void *ainv;  // A^-1 odd half-field (packed FP64 clover), or nullptr: no det term
+    double *K;
+};
+
+// K of the two-flavour clover pseudofermion (and det A_oo) insertion
+__global__ void k_clover_k_from_fields(KFieldArgs A)
+{
+    const Geom &g = A.g;
+    const long long V = 2LL * g.vh;
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= V) return;
+    int c4[4];
+    long long r = x;
+    for (int k = 3; k >= 0; --k) {
+        c4[k] = (int)(r % g.d[k]);
+        r /= g.d[k];
+    }
+    const int p = (c4[0] + c4[1] + c4[2] + c4[3]) & 1;
+    const int i = (int)(x >> 1);
+    zc P[2][3][2][2] = {};
+    cpx<double> u[4][2], v[4][2];
+    load_spinor<2, kF64>(p == 0 ? A.X : A.Z, g.nblk_s, i, u);
+    load_spinor<2, kF64>(p == 0 ? A.Y : A.W, g.nblk_s, i, v);
+    // Lam = coef u v^+ : Lam[(t, d), (s, c)] = coef u[t][d] conj(v[s][c])
+    add_blocks(P, p == 0 ? -2.0 : -0.5, [&](int t, int d, int s, int c) {
+        return zmul(zc{u[t][d].re, u[t][d].im}, zconj(zc{v[s][c].re, v[s][c].im}));
+    });
+    if (p == 1 && A.ainv) {
+        // Lam_det = -2 A^-1: block b (spins 2b, 2b+1) as n = 4 reals per diagonal, then the upper triangle
+        // (double-float reals, converted exactly)
+        CloverReader<2, kF64, dd> rd(A.ainv, i);
+        zc M[2][4][4];
+        int q = 0;
+        for (int b = 0; b < 2; ++b) {
+            for (int k = 0; k < 4; ++k) M[b][k][k] = {dd_to_double(rd.get(q++)), 0.0};
+            for (int a = 0; a < 4; ++a)
+                for (int c = a + 1; c < 4; ++c) {
+                    const double re = dd_to_double(rd.get(q++)), im = dd_to_double(rd.get(q++));
+                    M[b][a][c] = {re, im};
+                    M[b][c][a] = {re, -im};
+                }
+        }
+        add_blocks(P, -2.0, [&](int t, int d, int s, int c) {
+            const int b = t >> 1; // same block as s (diagonal blocks only are read)
+            return M[b][(t & 1) * 2 + d][(s & 1) * 2 + c];
+        });
+    }
+    store_k(A.K, x, P);
+}
+
+// leaves of Q_mn(x): factor j of leaf l is U_{mu or nu}(x + a mu + b nu), daggered or not
+struct LeafFactor {
+    int nu_dir; // 0: mu, 1: nu
+    int a, b;
+    int dag;
+};
+__constant__ LeafFactor kLeaf[4][4] = {
+    {{0, 0, 0, 0}, {1, 1, 0, 0}, {0, 0, 1, 1}, {1, 0, 0, 1}},
+    {{1, 0, 0, 0}, {0, -1, 1, 1}, {1, -1, 0, 1}, {0, -1, 0, 0}},
+    {{0, -1, 0, 1}, {1, -1, -1, 1}, {0, -1, -1, 0}, {1, 0, -1, 0}},
+    {{1, 0, -1, 1}, {0, 0, -1, 0}, {1, 1, -1, 0}, {0, 0, 0, 1}},
+};
+
+__device__ CM<2> ident2()
+{
+    CM<2> I;
+    I.m[0][0] = {1.0, 0.0};
+    I.m[0][1] = {0.0, 0.0};
+    I.m[1][0] = {0.0, 0.0};
+    I.m[1][1] = {1.0, 0.0};
+    return I;
+}
+
+// F[rho][z][a] += scale * d/dw_a Re sum_y tr[C Lam], one thread per link (rho, z)
+__global__ void __launch_bounds__(128) k_clover_leaf_force(Geom g, const double *can, const double *K, double scale,
+                                                           double *F)
+{
+    const long long V = 2LL * g.vh;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * V) return;
+    const int rho = (int)(t / V);
+    const long long z = t - (long long)rho * V;
+    int x[4];
+    long long r = z;
+    for (int k = 3; k >= 0; --k) {
+        x[k] = (int)(r % g.d[k]);
+        r /= g.d[k];
+    }
+    const CM<2> U = link_mat<2>(can, V, rho, z);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int pl = 0; pl < 6; ++pl) {
+        const int mu = kPlane[pl][0], nu = kPlane[pl][1];
+        if (rho != mu && rho != nu) continue;
+        const int sel = rho == mu ? 0 : 1;
+        for (int l = 0; l < 4; ++l)
+            for (int k = 0; k < 4; ++k) {
+                const LeafFactor fk = kLeaf[l][k];
+                if (fk.nu_dir != sel) continue;
+                // the leaf's base y = z - a_k mu - b_k nu; factor j sits at y + a_j mu + b_j nu
+                CM<2> Am = ident2(), Bm = ident2();
+                for (int j = 0; j < 4; ++j) {
+                    if (j == k) continue;
+                    const LeafFactor fj = kLeaf[l][j];
+                    const long long sj = nb(g, x, mu, fj.a - fk.a, nu, fj.b - fk.b);
+                    const CM<2> Uj = link_mat<2>(can, V, fj.nu_dir ? nu : mu, sj);
+                    if (j < k) Am = cmul(Am, false, Uj, fj.dag != 0);
+                    else Bm = cmul(Bm, false, Uj, fj.dag != 0);
+                }
+                const long long y = nb(g, x, mu, -fk.a, nu, -fk.b);
+                CM<2> Km;
+                const double *kp = K + (y * 6 + pl) * 8;
+                for (int d = 0; d < 2; ++d)
+                    for (int c = 0; c < 2; ++c) Km.m[d][c] = {kp[(d * 2 + c) * 2], kp[(d * 2 + c) * 2 + 1]};
+                CM<2> G1, G2;
+                if (!fk.dag) {
+                    // U B K A + A^+ K B^+ U^+
+                    G1 = cmul(cmul(U, false, Bm, false), false, cmul(Km, false, Am, false), false);
+                    G2 = cmul(cmul(Am, true, Km, false), false, cmul(U, false, Bm, false), true);
+                } else {
+                    // -(B K A U^+ + U A^+ K B^+)
+                    G1 = cmul(cmul(Bm, false, Km, false), false, cmul(Am, false, U, true), false);
+                    G2 = cmul(cmul(U, false, Am, true), false, cmul(Km, false, Bm, true), false);
+                }
+                const double sgn = fk.dag ? -1.0 : 1.0;
+                const zc G00 = zadd(G1.m[0][0], G2.m[0][0]), G01 = zadd(G1.m[0][1], G2.m[0][1]);
+                const zc G10 = zadd(G1.m[1][0], G2.m[1][0]), G11 = zadd(G1.m[1][1], G2.m[1][1]);
+                // -Re tr(s_a G) / 32
+                acc[0] -= sgn * (G10.re + G01.re) / 32.0;
+                acc[1] -= sgn * (G10.im - G01.im) / 32.0;
+                acc[2] -= sgn * (G00.re - G11.re) / 32.0;
+            }
+    }
+    double *o = F + ((long long)rho * V + z) * 3;
+    for (int a = 0; a < 3; ++a) o[a] += scale * acc[a];
+}
+
+// block sums of sum_{odd sites} log det A (both blocks, Cholesky), one partial per block
+template <int NC> __global__ void __launch_bounds__(128) k_clover_logdet(Geom g, const void *half, double *partial,
+                                                                         unsigned *bad)
+{
+    constexpr int N = 2 * NC;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.vh; i += gridDim.x * blockDim.x) {
+        CloverReader<NC, kF64, dd> rd(half, i); // double-float reals, converted exactly
+        int q = 0;
+        for (int b = 0; b < 2; ++b) {
+            zc M[N][N];
+            for (int k = 0; k < N; ++k) M[k][k] = {dd_to_double(rd.get(q++)), 0.0};
+            for (int a = 0; a < N; ++a)
+                for (int c = a + 1; c < N; ++c) {
+                    const double re = dd_to_double(rd.get(q++)), im = dd_to_double(rd.get(q++));
+                    M[a][c] = {re, im};
+                    M[c][a] = {re, -im};
+                }
+            // Cholesky M = L L^+ in place (lower triangle); log det = 2 sum log L_kk
+            for (int k = 0; k < N; ++k) {
+                double dkk = M[k][k].re;
+                for (int j = 0; j < k; ++j) dkk -= M[k][j].re * M[k][j].re + M[k][j].im * M[k][j].im;
+                if (!(dkk > 0.0)) {
+                    atomicExch(bad, 1u);
+                    dkk = 1.0;
+                }
+                const double lkk = sqrt(dkk);
+                acc += 2.0 * log(lkk);
+                for (int a = k + 1; a < N; ++a) {
+                    zc s = M[a][k];
+                    for (int j = 0; j < k; ++j) s = zsub(s, zmul(M[a][j], zconj(M[k][j])));
+                    M[a][k] = zscale(1.0 / lkk, s);
+                }
+            }
+        }
+    }
+    __shared__ double red[128];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+constexpr int kLogdetBlocks = 256;
+
+size_t k_field_bytes(const Geom &g) { return ((size_t)2 * g.vh * 48 * sizeof(double) + 255) & ~(size_t)255; }
+
+hr_status leaf_force(hr_ctx *ctx, const Geom &g, const double *can, const double *K, double scale, double *F,
+                     cudaStream_t s)
+{
+    const long long n = 8LL * g.vh;
+    k_clover_leaf_force<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, can, K, scale, F);
+    return check_launch(ctx, "clover force");
+}
+
+} // namespace
+
+extern "C" {
+
+size_t hr_clover_force_workspace_bytes(hr_lattice lat)
+{
+    if (hr_gauge_packed_bytes(lat, HR_FUND, HR_F64) == 0) return 0;
+    const Geom g = make_geom(lat, 1);
+    const size_t half = spinor_half_bytes(g, HR_FUND, kF64);
+    return k_field_bytes(g) + 5 * half;
+}
+
+hr_status hr_clover_insertion_force(hr_ctx *ctx, hr_lattice lat, double c_sw, const double *gauge, const double *lam,
+                                    double coeff, double *force, void *work, size_t work_bytes, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    st = check_buffers(ctx, {work}, {gauge, lam, force});
+    if (st) return st;
+    if (!std::isfinite(c_sw) || !std::isfinite(coeff)) return set_error(ctx, HR_ERR_INVALID_ARG, "c_sw, coeff finite");
+    const Geom g = make_geom(lat, 1);
+    if (work_bytes < k_field_bytes(g))
+        return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", k_field_bytes(g), work_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long V = 2LL * g.vh;
+    k_clover_k_from_lam<<<(unsigned)((V + 127) / 128), 128, 0, s>>>(V, lam, (double *)work);
+    st = check_launch(ctx, "clover insertion");
+    if (!st) st = leaf_force(ctx, g, gauge, (const double *)work, coeff * c_sw, force, s);
+    return st;
+}
+
+hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, double m0, double c_sw, const double *gauge,
+                                  const void *gauge_packed, const void *clover, const void *X, int with_det,
+                                  double coeff, double *force, void *work, size_t work_bytes, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    st = check_buffers(ctx, {gauge_packed, clover, X, work}, {gauge, force});
+    if (st) return st;
+    if (!(4.0 + m0 != 0.0) || !std::isfinite(c_sw) || !std::isfinite(coeff))
+        return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 nonzero, c_sw and coeff finite");
+    const size_t need = hr_clover_force_workspace_bytes(lat);
+    if (work_bytes < need) return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, work_bytes);
+    const Geom g = make_geom(lat, 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t half = spinor_half_bytes(g, HR_FUND, kF64);
+    char *w = (char *)work;
+    double *K = (double *)w;
+    char *a = w + k_field_bytes(g);  // full field (Y | W)
+    char *b = a + 2 * half;          // full field (X | Z)
+    char *t_odd = b + 2 * half;
+    const void *ainv_odd = clover_half(clover, g, HR_FUND, kF64, true, 1);
+    // Y = Mhat X
+    st = apply_eo_op(ctx, g, m0, HR_FUND, kF64, HR_OP_SCHUR, gauge_packed, X, a, t_odd, nullptr, kFinNone, nullptr,
+                     nullptr, s, nullptr, clover);
+    if (st) return st;
+    // Z = A_oo^-1 H_oe X,  W = A_oo^-1 g5 H_oe g5 Y  (A commutes with g5)
+    for (int k = 0; k < 2; ++k) {
+        HopLaunch L{};
+        L.p = 1;
+        L.gauge = gauge_packed;
+        L.in = k == 0 ? X : (const void *)a;
+        L.out = k == 0 ? b + half : a + half;
+        L.beta = 1.0;
+        L.g5_in = L.g5_out = k;
+        L.clov = ainv_odd;
+        L.clov_mode = kClovOut;
+        st = launch_hop(ctx, g, HR_FUND, kF64, L, s);
+        if (st) return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(b, X, half, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+    // the hops: 1/2 dRe<a, H b>
+    st = hr_force(ctx, lat, gauge_packed, a, b, 0.5 * coeff, force, stream);
+    if (st) return st;
+    // the site term: c_sw df[Lam]
+    KFieldArgs A;
+    A.g = g;
+    A.X = b;
+    A.Y = a;
+    A.Z = b + half;
+    A.W = a + half;
+    A.ainv = with_det ? ainv_odd : nullptr;
+    A.K = K;
+    const long long V = 2LL * g.vh;
+    k_clover_k_from_fields<<<(unsigned)((V + 127) / 128), 128, 0, s>>>(A);
+    st = check_launch(ctx, "clover insertion");
+    if (!st) st = leaf_force(ctx, g, gauge, K, coeff * c_sw, force, s);
+    return st;
+}
+
+hr_status hr_clover_logdet(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *clover, hr_parity parity,
+                           double *logdet, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!logdet) return set_error(ctx, HR_ERR_INVALID_ARG, "null result pointer");
+    if (rep != HR_FUND && rep != HR_ADJ) return set_error(ctx, HR_ERR_INVALID_ARG, "HR_FUND or HR_ADJ");
+    if (parity != HR_EVEN && parity != HR_ODD) return set_error(ctx, HR_ERR_INVALID_ARG, "bad parity");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    st = check_buffers(ctx, {clover});
+    if (st) return st;
+    const Geom g = make_geom(lat, 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *half = clover_half(clover, g, rep, kF64, false, parity);
+    unsigned *bad = ctx->d_counters + C_STATUS;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "status reset: %s", cudaGetErrorString(e));
+    if (rep == HR_FUND) k_clover_logdet<2><<<kLogdetBlocks, 128, 0, s>>>(g, half, ctx->d_partials, bad);
+    else k_clover_logdet<3><<<kLogdetBlocks, 128, 0, s>>>(g, half, ctx->d_partials, bad);
+    st = check_launch(ctx, "clover log det");
+    if (st) return st;
+    double h[kLogdetBlocks];
+    unsigned hb = 0;
+    e = cudaMemcpyAsync(h, ctx->d_partials, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof hb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "log det readback: %s", cudaGetErrorString(e));
+    if (hb) return set_error(ctx, HR_ERR_NUMERIC, "a clover block is not positive definite");
+    double acc = 0.0;
+    for (int k = 0; k < kLogdetBlocks; ++k) acc += h[k];
+    *logdet = acc;
+    return HR_OK;
+}
+
+} // extern "C"

@@ -49,6 +49,7 @@ EXPORTED = [
     "hr_dirac_eo_clover", "hr_cg_clover_workspace_bytes", "hr_cg_solve_clover",
     "hr_solve_full_clover_workspace_bytes", "hr_solve_full_clover", "hr_gauge_force", "hr_gauge_action",
     "hr_link_update", "hr_mom_update", "hr_kinetic_energy", "hr_hmc_workspace_bytes", "hr_hmc_trajectory",
+    "hr_clover_force_workspace_bytes", "hr_clover_insertion_force", "hr_clover_fermion_force", "hr_clover_logdet",
 ]
 
 
@@ -168,6 +169,10 @@ def lib():
                                    ctypes.POINTER(hr_solve_info), P, S, P], I),
                 "hr_clover_packed_bytes": ([LAT, I, I], S),
                 "hr_clover_build": ([P, LAT, I, I, I, D, D, P, P, P], I),
+                "hr_clover_force_workspace_bytes": ([LAT], S),
+                "hr_clover_insertion_force": ([P, LAT, D, P, P, D, P, P, S, P], I),
+                "hr_clover_fermion_force": ([P, LAT, D, D, P, P, P, P, I, D, P, P, S, P], I),
+                "hr_clover_logdet": ([P, LAT, I, P, I, ctypes.POINTER(ctypes.c_double), P], I),
                 "hr_clover_apply": ([P, LAT, I, I, I, I, I, P, P, P, P], I),
                 "hr_dirac_apply_clover": ([P, LAT, I, I, P, P, P, P, P], I),
                 "hr_dirac_eo_clover": ([P, LAT, I, I, I, I, I, P, P, P, P, P, S, P], I),
@@ -227,6 +232,10 @@ def _stream(stream):
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)
     return ctypes.c_void_p(int(stream))
+
+
+def _nbytes(t) -> int:
+    return 0 if t is None else t.numel() * t.element_size()
 
 
 def _need(t, nbytes: int, what: str):
@@ -404,6 +413,40 @@ def hr_clover_build(ctx: Context, dims, rep, prec, kind, m0, c_sw, canonical, cl
     _need(clover, hr_clover_packed_bytes(dims, rep, prec), "clover")
     return ctx.check(lib().hr_clover_build(ctx.handle, lattice(dims), rep, prec, int(kind), float(m0), float(c_sw),
                                            _ptr(canonical), _ptr(clover), _stream(stream)))
+
+
+def hr_clover_force_workspace_bytes(dims) -> int:
+    return int(lib().hr_clover_force_workspace_bytes(lattice(dims)))
+
+
+def hr_clover_insertion_force(ctx: Context, dims, c_sw, gauge, lam, coeff, force, work, stream=None):
+    """force += coeff c_sw d/dw Re sum tr[C lam]; lam complex128 [V, 8, 8] on the device."""
+    V = _vol(dims)
+    _need(gauge, 4 * V * 4 * 8, "gauge")
+    _need(lam, V * 64 * 16, "lam")
+    _need(force, 4 * V * 3 * 8, "force")
+    return ctx.check(lib().hr_clover_insertion_force(ctx.handle, lattice(dims), float(c_sw), _ptr(gauge), _ptr(lam),
+                                                     float(coeff), _ptr(force), _ptr(work), _nbytes(work),
+                                                     _stream(stream)))
+
+
+def hr_clover_fermion_force(ctx: Context, dims, m0, c_sw, gauge, gauge_packed, clover, X, with_det, coeff, force,
+                            work, stream=None):
+    V = _vol(dims)
+    _need(gauge, 4 * V * 4 * 8, "gauge")
+    _need(force, 4 * V * 3 * 8, "force")
+    _need(X, hr_spinor_packed_bytes(dims, HR_FUND, HR_F64, HR_EVEN, 1), "X")
+    return ctx.check(lib().hr_clover_fermion_force(ctx.handle, lattice(dims), float(m0), float(c_sw), _ptr(gauge),
+                                                   _ptr(gauge_packed), _ptr(clover), _ptr(X), int(bool(with_det)),
+                                                   float(coeff), _ptr(force), _ptr(work), _nbytes(work),
+                                                   _stream(stream)))
+
+
+def hr_clover_logdet(ctx: Context, dims, rep, clover, parity, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    ctx.check(lib().hr_clover_logdet(ctx.handle, lattice(dims), rep, _ptr(clover), parity, ctypes.byref(out),
+                                     _stream(stream)))
+    return out.value
 
 
 def hr_clover_apply(ctx: Context, dims, rep, prec, parity, inverse, n_rhs, clover, inp, out, stream=None):

@@ -1,0 +1,86 @@
+"""The clover term's HMC force and action on the GPU against the oracle
+(oracle/clover.py: clover_derivative, CloverFermions, itself pinned by finite
+differences of dense-matrix actions in tests/test_oracle_clover_force.py).
+FP64 throughout: forces to 1e-12 relative L2, log det to 1e-12 relative."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import clover as ocl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2411_18511_gb300 import fields, hr  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return hr.Context(0)
+
+
+def rel(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def smeared(dims, seed):
+    q, _, _ = synth.ape_smear_to_plaquette(synth.haar_links(dims, seed), dims, 0.6)
+    return q
+
+
+@pytest.mark.parametrize("dims", [(4, 6, 2, 6), (2, 4, 4, 2)])
+def test_insertion_force_matches_oracle(ctx, dims):
+    V = int(np.prod(dims))
+    q = synth.haar_links(dims, 601)
+    rng = np.random.default_rng(602)
+    lam = rng.normal(size=(V, 8, 8)) + 1j * rng.normal(size=(V, 8, 8))
+    csw, coeff = 1.3, 0.7
+    F = torch.zeros((4, V, 3), dtype=torch.float64, device="cuda")
+    work = fields.empty_bytes(hr.hr_clover_force_workspace_bytes(dims))
+    hr.hr_clover_insertion_force(ctx, dims, csw, fields.gauge_to_device(q), torch.tensor(lam, device="cuda"), coeff,
+                                 F, work)
+    want = coeff * csw * ocl.clover_derivative(dims, oracle.expand_links(dims, 2, q), lam)
+    assert rel(F.cpu().numpy(), want) <= 1e-12
+
+
+@pytest.mark.parametrize("with_det", [0, 1])
+@pytest.mark.parametrize("lat", [hr.Lattice((4, 6, 2, 6)), hr.Lattice((4, 4, 4, 4), 1),
+                                 hr.Lattice((4, 2, 4, 6), 1, (0.4, 0.0, -1.2, 0.9))])
+def test_fermion_force_matches_oracle(ctx, lat, with_det):
+    m0, csw = 0.1, 1.2
+    V = int(np.prod(lat))
+    q = smeared(lat, 611)
+    X = synth.gaussian_spinor(lat, 2, 612)
+    X[oracle.parity_mask(lat) == 1] = 0
+    qd = fields.gauge_to_device(q)
+    gauge = fields.pack_gauge(ctx, lat, hr.HR_FUND, hr.HR_F64, qd)
+    clov = fields.build_clover(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_CLOVER_SW, m0, csw, qd)
+    Xp = fields.pack_spinor(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, fields.spinor_to_device(X))
+    F = torch.zeros((4, V, 3), dtype=torch.float64, device="cuda")
+    work = fields.empty_bytes(hr.hr_clover_force_workspace_bytes(lat))
+    hr.hr_clover_fermion_force(ctx, lat, m0, csw, qd, gauge, clov, Xp, with_det, 0.5, F, work)
+    ferm = ocl.CloverFermions(lat, m0, csw, np.zeros_like(X), bc=lat.bc)
+    want = 0.5 * ferm.force_at(q, X, det=bool(with_det))
+    assert rel(F.cpu().numpy(), want) <= 1e-12
+
+
+@pytest.mark.parametrize("rep", [hr.HR_FUND, hr.HR_ADJ])
+def test_logdet_matches_oracle(ctx, rep):
+    lat = (4, 6, 2, 6)
+    nc = 2 if rep == hr.HR_FUND else 3
+    m0, csw = 0.1, 1.2
+    q = smeared(lat, 621)
+    A = ocl.site_term(lat, oracle.expand_links(lat, nc, q), m0, csw, ocl.KIND_SW)
+    clov = fields.build_clover(ctx, lat, rep, hr.HR_F64, hr.HR_CLOVER_SW, m0, csw, fields.gauge_to_device(q))
+    for par in (hr.HR_EVEN, hr.HR_ODD):
+        m = oracle.parity_mask(lat) == par
+        want = float(np.sum(np.linalg.slogdet(A[m])[1]))
+        got = hr.hr_clover_logdet(ctx, lat, rep, clov, par)
+        assert abs(got - want) <= 1e-12 * abs(want), (par, got, want)
