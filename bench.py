@@ -587,8 +587,9 @@ def run_hmc(ctx, torch, hr, fields, synth):
     FP16-inner solvers, Hasenbusch's two pseudofermions (heavy m0 = 0.2), and
     two time scales (6 outer Omelyan steps on the pseudofermion force, 3 gauge
     steps per outer link update: half the fermion forces); a short chain from a
-    thermalised start for the acceptance.  force_evaluations counts pseudofermion
-    forces (each one or two solves)."""
+    thermalised start for the acceptance, and clover fermions (c_sw = 1) on two
+    time scales.  force_evaluations counts pseudofermion forces (each one or
+    two solves)."""
     from paper_2411_18511_gb300.hmc import HMC
     lat = hr.Lattice((16, 16, 16, 16), 1)
     beta, m0 = 2.2, -0.2
@@ -609,12 +610,14 @@ def run_hmc(ctx, torch, hr, fields, synth):
                                              ("omelyan_f16_inner", om, 12, hr.HR_F16, None, 1),
                                              ("omelyan_f16_inner_hasenbusch", om, 12, hr.HR_F16, 0.2, 1),
                                              ("omelyan_f16_inner_2scales", om, 6, hr.HR_F16, None, 3),
-                                             ("omelyan_f16_inner_hasenbusch_2scales", om, 6, hr.HR_F16, 0.2, 3)):
+                                             ("omelyan_f16_inner_hasenbusch_2scales", om, 6, hr.HR_F16, 0.2, 3),
+                                             ("omelyan_f16_inner_clover_2scales", om, 6, hr.HR_F16, None, 3)):
         solver = hr.hr_solver_default_opts()
         solver.inner_prec = inner
         solver.reliable_delta = 0.01 if inner != hr.HR_F64 else 0.1
         chain = HMC(ctx, lat, beta=beta, m0=m0, fermions=True, n_steps=steps, tau=1.0, integrator=integ,
-                    solver=solver, seed=2006, m0_hasenbusch=mh, n_steps_gauge=m)
+                    solver=solver, seed=2006, m0_hasenbusch=mh, n_steps_gauge=m,
+                    c_sw=1.0 if "clover" in name else None)
         q = qd0.clone()
         secs, dhs, iters = [], [], []
         for _ in range(4):
@@ -625,6 +628,7 @@ def run_hmc(ctx, torch, hr, fields, synth):
             iters.append(info.cg_iters)
         forces = steps + 1 if integ == hr.HR_INTEGRATOR_LEAPFROG else 2 * steps + 1
         out[name] = {"n_steps": steps, "force_evaluations": forces, "hasenbusch_m0": mh, "n_steps_gauge": m,
+                     "c_sw": 1.0 if "clover" in name else None,
                      "trajectory_s_median": round(statistics.median(secs[1:]), 4),
                      "dH": [round(float(x), 4) for x in dhs], "accepted": f"{chain.accepted}/{chain.trajectories}",
                      "cg_iters_per_trajectory": int(statistics.median(iters)), "end_plaquette": round(info.plaquette, 4)}

@@ -407,6 +407,8 @@ typedef struct {
     double m0_hasenbusch;     /* its heavier mass                                      */
     int n_steps_gauge;        /* two time scales: gauge-force steps per link update of */
                               /* the fermion integrator (> 1); 0 or 1: one time scale  */
+    int clover;               /* 1: clover (SW) fermions, c_sw below (not with hasenbusch) */
+    double c_sw;              /* their coefficient                                     */
 } hr_hmc_params;
 
 typedef struct {
@@ -440,6 +442,11 @@ size_t hr_hmc_workspace_bytes(hr_lattice lat, const hr_hmc_params *prm);
  * each of its link updates, of length t, becomes m steps of length t / m of
  * the same integrator driven by the gauge force alone: as many solves as
  * with m = 1, m times (leapfrog; 2m, Omelyan) as many gauge-force steps.
+ * With prm->clover the fermions carry the SW site term (Mhat = A_ee -
+ * H_eo A_oo^-1 H_oe / 4, eta drawn as Mhat^+ xi with that Mhat): the clover
+ * field is rebuilt from the links before each solve, S_f = Re<eta, (Mhat^+
+ * Mhat)^-1 eta> - 2 sum_{odd} log det A, and the force is
+ * hr_clover_fermion_force (hops, site term and det A_oo).
  * Each fermion force and S_f takes
  * one hr_cg_solve (from x = 0) on the packed links (lat.bc applies).  The
  * Metropolis test on info->dH and the draw of mom and eta are the caller's.

@@ -22,6 +22,7 @@
 // (heavy mass m0_H) and Re<eta2, (Mhat^+ Mhat)^-1 eta2> with eta2 = Mhat_H^+ phi;
 // the second term's force adds the variation of eta2: -2 c_H dRe<a', H b'>/dw,
 // a' = (g5 X2, H_eo^+ g5 X2), b' = (g5 phi, H_oe g5 phi), c_H = 1/(4 (4 + m0_H)).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -253,6 +254,9 @@ struct HmcWork {
     void *t_odd;      // odd temporary of Mhat
     void *cg;         // CG workspace
     size_t cg_bytes;
+    void *clover;     // clover fermions: the packed FP64 clover field of the current links
+    void *cf;         // clover force workspace
+    size_t cf_bytes;
 };
 
 // two time scales: the fermion integrator's link updates run inner gauge steps
@@ -265,7 +269,8 @@ size_t layout_hmc(hr_lattice lat, const hr_hmc_params &prm, char *w, HmcWork *hw
     hr_solver_opts o = prm.solver;
     o.n_rhs = 1;
     o.x0_is_guess = 0;
-    const size_t cgb = hr_cg_workspace_bytes(lat, HR_FUND, &o);
+    size_t cgb = hr_cg_workspace_bytes(lat, HR_FUND, &o);
+    if (prm.clover) cgb = std::max(cgb, hr_cg_clover_workspace_bytes(lat, HR_FUND, &o));
     const long long V = (long long)lat.dims[0] * lat.dims[1] * lat.dims[2] * lat.dims[3];
     size_t off = 0;
     auto take = [&](size_t n) -> void * {
@@ -285,7 +290,14 @@ size_t layout_hmc(hr_lattice lat, const hr_hmc_params &prm, char *w, HmcWork *hw
         e2 = take(half);
     }
     void *cg = take(cgb);
-    if (hw) *hw = HmcWork{gauge, (double *)F, (double *)Fg, X, X2, eta2, e1, e2, a, b, t, cg, cgb};
+    void *clover = nullptr, *cf = nullptr;
+    size_t cfb = 0;
+    if (prm.clover) {
+        clover = take(hr_clover_packed_bytes(lat, HR_FUND, HR_F64));
+        cfb = hr_clover_force_workspace_bytes(lat);
+        cf = take(cfb);
+    }
+    if (hw) *hw = HmcWork{gauge, (double *)F, (double *)Fg, X, X2, eta2, e1, e2, a, b, t, cg, cgb, clover, cf, cfb};
     return off;
 }
 
@@ -316,7 +328,10 @@ struct Trajectory {
         o.n_rhs = 1;
         o.x0_is_guess = 0;
         hr_solve_info info{};
-        hr_status st = hr_cg_solve(ctx, lat, m0, HR_FUND, &o, w.gauge, src, x, &info, w.cg, w.cg_bytes, (hr_stream)s);
+        hr_status st = prm.clover ? hr_cg_solve_clover(ctx, lat, HR_FUND, &o, w.gauge, w.clover, src, x, &info, w.cg,
+                                                       w.cg_bytes, (hr_stream)s)
+                                  : hr_cg_solve(ctx, lat, m0, HR_FUND, &o, w.gauge, src, x, &info, w.cg, w.cg_bytes,
+                                                (hr_stream)s);
         cg_iters += info.iters;
         ++solves;
         return st;
@@ -326,6 +341,8 @@ struct Trajectory {
     {
         if (x_valid) return HR_OK;
         hr_status st = pack();
+        if (!st && prm.clover)
+            st = hr_clover_build(ctx, lat, HR_FUND, HR_F64, HR_CLOVER_SW, prm.m0, prm.c_sw, q, w.clover, (hr_stream)s);
         if (!st) st = cg(eta_mass(), eta, w.X);
         if (!st && prm.hasenbusch) {
             // eta2 = Mhat_H^+ phi at the current links, then the ratio term's solve
@@ -350,6 +367,12 @@ struct Trajectory {
     {
         hr_status st = solve();
         if (!st) st = dot(eta, w.X, S);
+        if (!st && prm.clover) {
+            // S_det = -2 sum_{odd} log det A
+            double ld = 0.0;
+            st = hr_clover_logdet(ctx, lat, HR_FUND, w.clover, HR_ODD, &ld, (hr_stream)s);
+            S += -2.0 * ld;
+        }
         if (!st && prm.hasenbusch) {
             double S2 = 0.0;
             st = dot(w.eta2, w.X2, S2);
@@ -426,7 +449,12 @@ struct Trajectory {
     hr_status fermion_terms()
     {
         hr_status st = HR_OK;
-        if (prm.fermions) {
+        if (prm.fermions && prm.clover) {
+            st = solve();
+            if (!st)
+                st = hr_clover_fermion_force(ctx, lat, prm.m0, prm.c_sw, q, w.gauge, w.clover, w.X, 1, 1.0, w.F, w.cf,
+                                             w.cf_bytes, (hr_stream)s);
+        } else if (prm.fermions) {
             st = solve();
             if (!st) st = solve_force(eta_mass(), w.X);
             if (!st && prm.hasenbusch) {
@@ -605,6 +633,9 @@ hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *pr
     if (prm->fermions && prm->hasenbusch && !(4.0 + prm->m0_hasenbusch != 0.0))
         return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0_hasenbusch must be nonzero");
     if (prm->hasenbusch && !prm->fermions) return set_error(ctx, HR_ERR_INVALID_ARG, "Hasenbusch needs fermions");
+    if (prm->clover && (!prm->fermions || prm->hasenbusch || !std::isfinite(prm->c_sw)))
+        return set_error(ctx, prm->hasenbusch ? HR_ERR_UNSUPPORTED : HR_ERR_INVALID_ARG,
+                         "clover fermions: fermions on, a finite c_sw, without Hasenbusch");
     if (prm->n_steps_gauge < 0 || prm->n_steps_gauge > 1000)
         return set_error(ctx, HR_ERR_INVALID_ARG, "n_steps_gauge must lie in [0, 1000]");
     if (prm->fermions && prm->hasenbusch) st = check_buffers(ctx, {eta, phi}, {gauge, mom}, {work});

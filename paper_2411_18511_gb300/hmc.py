@@ -5,7 +5,8 @@ Wilson fermions (fundamental) on one GPU: the Markov chain around
 Each step draws Gaussian momenta and a pseudofermion eta = Mhat^+ xi with
 P(xi) ~ exp(-xi^+ xi), integrates one trajectory, and accepts the new links
 with probability min(1, exp(-dH)); a rejected trajectory restores the links.
-With Hasenbusch mass preconditioning (``m0_hasenbusch``) it draws two:
+With clover fermions (``c_sw``) eta = Mhat^+ xi with the clover Schur
+operator.  With Hasenbusch mass preconditioning (``m0_hasenbusch``) it draws two:
 eta = Mhat_H^+ xi1 and phi = Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2 (one
 solve at the heavy mass).  The random numbers come from a seeded torch
 generator on the device.
@@ -24,7 +25,7 @@ class HMC:
     def __init__(self, ctx: hr.Context, dims, beta: float, m0: float = 0.0, fermions: bool = True,
                  n_steps: int = 10, tau: float = 1.0, integrator: int = hr.HR_INTEGRATOR_OMELYAN,
                  solver: hr.hr_solver_opts | None = None, seed: int = 0, device="cuda",
-                 m0_hasenbusch: float | None = None, n_steps_gauge: int = 1):
+                 m0_hasenbusch: float | None = None, n_steps_gauge: int = 1, c_sw: float | None = None):
         self.ctx, self.dims, self.device = ctx, dims, device
         self.prm = hr.hr_hmc_params_default(beta, m0, fermions, n_steps, tau, integrator)
         if solver is not None:
@@ -33,6 +34,9 @@ class HMC:
             self.prm.hasenbusch = 1
             self.prm.m0_hasenbusch = float(m0_hasenbusch)
         self.prm.n_steps_gauge = int(n_steps_gauge)
+        if c_sw is not None:
+            self.prm.clover = 1
+            self.prm.c_sw = float(c_sw)
         self.work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(dims, self.prm), device)
         self.V = fields.volume(dims)
         self.gen = torch.Generator(device=device)
@@ -50,18 +54,25 @@ class HMC:
                            torch.randn(shape, dtype=torch.float64, device=self.device, generator=self.gen))
         return fields.pack_spinor(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, xi / math.sqrt(2.0))
 
-    def _schur(self, gauge, m0, src, dagger):
+    def _schur(self, gauge, m0, src, dagger, clover=None):
         d = self.dims
         op = hr.HR_OP_SCHUR_DAG if dagger else hr.HR_OP_SCHUR
         out = fields.empty_spinor(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, device=self.device)
         work = fields.empty_bytes(hr.hr_dirac_workspace_bytes(d, hr.HR_FUND, hr.HR_F64, op), self.device)
-        hr.hr_dirac_eo(self.ctx, d, m0, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, op, 1, gauge, src, out, work)
+        if clover is not None:
+            hr.hr_dirac_eo_clover(self.ctx, d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, op, 1, gauge, clover, src, out, work)
+        else:
+            hr.hr_dirac_eo(self.ctx, d, m0, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, op, 1, gauge, src, out, work)
         return out
 
     def draw_pseudofermion(self, q: torch.Tensor):
         """Packed even eta = Mhat^+ xi for the links q (Hasenbusch: eta = Mhat_H^+ xi1
         and phi = Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2; returns (eta, phi))."""
         gauge = fields.pack_gauge(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, q)
+        if self.prm.clover:
+            clov = fields.build_clover(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, hr.HR_CLOVER_SW, self.prm.m0,
+                                       self.prm.c_sw, q)
+            return self._schur(gauge, self.prm.m0, self._xi(), True, clov)
         if not self.prm.hasenbusch:
             return self._schur(gauge, self.prm.m0, self._xi(), True)
         mh = self.prm.m0_hasenbusch

@@ -99,7 +99,7 @@ class hr_hmc_params(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("m0", ctypes.c_double), ("fermions", ctypes.c_int),
                 ("n_steps", ctypes.c_int), ("tau", ctypes.c_double), ("integrator", ctypes.c_int),
                 ("solver", hr_solver_opts), ("hasenbusch", ctypes.c_int), ("m0_hasenbusch", ctypes.c_double),
-                ("n_steps_gauge", ctypes.c_int)]
+                ("n_steps_gauge", ctypes.c_int), ("clover", ctypes.c_int), ("c_sw", ctypes.c_double)]
 
 
 class hr_hmc_info(ctypes.Structure):

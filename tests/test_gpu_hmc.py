@@ -283,3 +283,65 @@ def test_two_time_scales_reversible(ctx):
     prm.n_steps_gauge = -1
     with pytest.raises(hr.HrError):
         run_gpu(ctx, lat, q, p, prm, eta_p)
+
+
+@pytest.mark.parametrize("m", [1, 3])
+@pytest.mark.parametrize("integrator", [hr.HR_INTEGRATOR_LEAPFROG, hr.HR_INTEGRATOR_OMELYAN])
+def test_clover_trajectory_matches_oracle(ctx, integrator, m):
+    """Clover (SW) fermions: the clover field rebuilt after every link update,
+    S_f with -2 log det A_oo, the force of hops, site term and det term, on one
+    or two time scales, against the oracle's CloverFermions."""
+    from oracle import clover as ocl
+
+    lat = hr.Lattice((4, 2, 2, 4), 1)
+    beta, m0, csw = 2.2, 0.1, 1.1
+    q = smeared(lat, 101)
+    p = np.random.default_rng(102).normal(size=(4, int(np.prod(lat)), 3))
+    prm = hr.hr_hmc_params_default(beta, m0, True, 2, 0.3, integrator)
+    prm.solver.tol = 1e-13
+    prm.n_steps_gauge = m
+    prm.clover, prm.c_sw = 1, csw
+    eta, eta_p = eta_field(ctx, lat, m0, 103)
+    qg, pg, info = run_gpu(ctx, lat, q, p, prm, eta_p)
+    ferm = ocl.CloverFermions(lat, m0, csw, eta, bc=1)
+    qo, po, io = ohmc.trajectory(lat, q, p, beta, 2, 0.3, integrator, ferm, n_steps_gauge=m)
+    assert np.abs(qg - qo).max() <= 1e-11
+    assert np.abs(pg - po).max() <= 1e-9
+    assert abs(info.dH - io["dH"]) <= 1e-9, (info.dH, io["dH"])
+    assert abs(info.fermion_action_start - io["start"]["fermion"]) <= 1e-9 * abs(io["start"]["fermion"])
+    assert abs(info.fermion_action_end - io["end"]["fermion"]) <= 1e-9 * abs(io["end"]["fermion"])
+
+
+def test_clover_chain(ctx):
+    """The chain with clover fermions: eta = Mhat^+ xi with the clover Schur
+    operator, so S_pf = |xi|^2 at the start (S_f - S_det, S_det from the library's
+    log det); a short run accepts, and a trajectory is reversible."""
+    lat = hr.Lattice((4, 4, 4, 4), 1)
+    m0, csw = 0.1, 1.0
+    q = dev(smeared(lat, 111))
+    chain = HMC(ctx, lat, beta=2.2, m0=m0, fermions=True, n_steps=6, tau=0.5, seed=112, c_sw=csw)
+    gen_state = chain.gen.get_state()
+    eta = chain.draw_pseudofermion(q)
+    chain.gen.set_state(gen_state)
+    xi = chain._xi()
+    clov = fields.build_clover(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_CLOVER_SW, m0, csw, q)
+    S_det = -2.0 * hr.hr_clover_logdet(ctx, lat, hr.HR_FUND, clov, hr.HR_ODD)
+    p = torch.zeros((4, int(np.prod(lat)), 3), dtype=torch.float64, device="cuda")
+    prm = hr.hr_hmc_params_default(2.2, m0, True, 1, 1e-6)
+    prm.clover, prm.c_sw = 1, csw
+    prm.solver.tol = 1e-13
+    info = hr.hr_hmc_trajectory(ctx, lat, prm, q.clone(), p, eta, chain.work)
+    xi_h = fields.unpack_spinor(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, xi).cpu().numpy()
+    want = float(np.vdot(xi_h, xi_h).real)
+    assert abs(info.fermion_action_start - S_det - want) <= 1e-9 * want
+    for _ in range(3):
+        acc, info = chain.step(q)
+        assert np.isfinite(info.dH) and abs(info.dH) < 2.0
+    assert chain.accepted >= 2
+    pp = torch.randn((4, int(np.prod(lat)), 3), dtype=torch.float64, device="cuda")
+    q0 = q.clone()
+    chain.prm.solver.tol = 1e-12
+    i1 = hr.hr_hmc_trajectory(ctx, lat, chain.prm, q, pp, eta, chain.work)
+    pp.neg_()
+    i2 = hr.hr_hmc_trajectory(ctx, lat, chain.prm, q, pp, eta, chain.work)
+    assert (q - q0).abs().max().item() <= 1e-9 and abs(i1.dH + i2.dH) <= 1e-7
