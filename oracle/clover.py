@@ -292,6 +292,33 @@ def clover_derivative(dims, L, Lam) -> np.ndarray:
     return G
 
 
+def exp_insertion(A, Lam, m0: float) -> np.ndarray:
+    """The insertion that carries an exponential site term's variation to C:
+    for A = a exp(X), a = 4 + m0, X = c_sw C / a,
+      d Re tr[A Lam] = c_sw Re tr[dC Lam'],  Lam' = int_0^1 exp((1-s) X) Lam exp(s X) ds
+    (dA = a int_0^1 exp(s X) dX exp((1-s) X) ds and the trace is cyclic).  In the
+    eigenbasis of X (that of A, eigenvalues mu = a e^lambda) the integral is the
+    divided difference of exp: (V^+ Lam' V)_ij = (V^+ Lam V)_ij (e^l_i - e^l_j) / (l_i - l_j),
+    i.e. the logarithmic mean of mu_i and mu_j over a.  Per chiral block (C and A
+    are block diagonal, so only the diagonal blocks of Lam' enter); Lam [V, 8, 8]."""
+    A = np.asarray(A)
+    Lam = np.asarray(Lam, dtype=np.complex128)
+    out = np.zeros_like(Lam)
+    a = 4.0 + m0
+    n = A.shape[-1] // 2
+    for b in range(2):
+        sl = slice(b * n, (b + 1) * n)
+        mu, V = np.linalg.eigh(A[:, sl, sl])
+        lam = np.log(mu / a)
+        li, lj = lam[:, :, None], lam[:, None, :]
+        d = li - lj
+        with np.errstate(invalid="ignore", divide="ignore"):
+            phi = np.where(np.abs(d) > 1e-8, (np.exp(li) - np.exp(lj)) / d, np.exp(0.5 * (li + lj)))
+        Lt = np.einsum("xki,xkl,xlj->xij", np.conj(V), Lam[:, sl, sl], V)
+        out[:, sl, sl] = np.einsum("xik,xkl,xjl->xij", V, Lt * phi, np.conj(V))
+    return out
+
+
 def det_action(A, dims) -> float:
     """S_det = -2 sum_{x odd} log det A(x) (A Hermitian positive definite)."""
     from . import parity_mask
@@ -303,19 +330,23 @@ def det_action(A, dims) -> float:
 
 
 class CloverFermions:
-    """Two flavours of clover (SW) fermions through the even-odd pseudofermion:
+    """Two flavours of clover fermions through the even-odd pseudofermion:
     S = S_pf + S_det (see above) and its su(2) force, for HMC trajectories
-    (``oracle.hmc.trajectory`` takes it as its ``fermions``)."""
+    (``oracle.hmc.trajectory`` takes it as its ``fermions``).  kind KIND_SW or
+    KIND_EXP; for the exponential form log det A = N log(4 + m0) + tr X is a
+    constant (C is traceless), so S_det has no force, and the site term's force
+    takes the insertion through ``exp_insertion``."""
 
-    def __init__(self, dims, m0: float, csw: float, eta, bc=0, tol: float = 1e-13, theta=None):
+    def __init__(self, dims, m0: float, csw: float, eta, bc=0, tol: float = 1e-13, theta=None, kind=KIND_SW):
         self.dims, self.m0, self.csw, self.eta, self.bc, self.tol, self.theta = dims, m0, csw, eta, bc, tol, theta
+        self.kind = kind
         self.iters = 0
 
     def _setup(self, q):
         from . import expand_links
 
         L = expand_links(self.dims, 2, q)
-        A = site_term(self.dims, L, self.m0, self.csw, KIND_SW)
+        A = site_term(self.dims, L, self.m0, self.csw, self.kind)
         return L, A
 
     def solve(self, q):
@@ -352,5 +383,8 @@ class CloverFermions:
         F = 0.5 * force(d, L, a, b, **kw)
         V = X.shape[0]
         outer = lambda u, v: np.einsum("xi,xj->xij", u.reshape(V, 8), np.conj(v.reshape(V, 8)))  # noqa: E731
+        if self.kind == KIND_EXP:
+            Lam = np.where(odd[:, None, None], -0.5 * outer(Z, W), -2.0 * outer(X, Y))
+            return F + self.csw * clover_derivative(d, L, exp_insertion(A, Lam, self.m0))
         Lam = np.where(odd[:, None, None], -0.5 * outer(Z, W) - (2.0 * Ainv if det else 0.0), -2.0 * outer(X, Y))
         return F + self.csw * clover_derivative(d, L, Lam)

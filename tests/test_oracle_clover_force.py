@@ -11,7 +11,10 @@ derivatives are tied to facts that do not come from them:
 * the whole two-flavour force (pseudofermion and det A_oo) against central
   finite differences of S = Re<eta, (Mhat^+ Mhat)^-1 eta> - 2 sum_odd log det A,
   both evaluated with dense matrices from tests/dense_ref.py;
-* the heat-bath normalisation S_pf = |xi|^2 for eta = Mhat^+ xi.
+* the heat-bath normalisation S_pf = |xi|^2 for eta = Mhat^+ xi;
+* the exponential form: exp_insertion (the divided differences of exp in the
+  eigenbasis of A) against finite differences of Re sum tr[A_exp Lam], and its
+  whole force against dense-matrix actions built with scipy's expm.
 """
 
 import numpy as np
@@ -117,3 +120,61 @@ def test_clover_trajectory_reversible_and_second_order(integrator):
     assert np.abs(q2 - q).max() < 1e-10 and np.abs(p2 + p).max() < 1e-9
     dh = [abs(hmc.trajectory(dims, q, p, 2.2, n, 0.5, integrator, ferm)[2]["dH"]) for n in (8, 16)]
     assert 3.8 < dh[0] / dh[1] < 4.2, dh
+
+
+# ---------------------------------------------------------------- exponential clover
+
+def test_exp_insertion_matches_finite_differences():
+    """d Re sum tr[A_exp Lam] = c_sw Re sum tr[dC Lam'] with Lam' from exp_insertion:
+    against central finite differences of the exponential site term."""
+    dims = (2, 2, 2, 4)
+    V = int(np.prod(dims))
+    m0, csw = 0.1, 1.4
+    q = synth.haar_links(dims, 541)
+    Lam = RNG.normal(size=(V, 8, 8)) + 1j * RNG.normal(size=(V, 8, 8))
+
+    def f(qq):
+        A = ocl.site_term(dims, oracle.expand_links(dims, 2, qq), m0, csw, ocl.KIND_EXP)
+        return float(np.real(np.einsum("xij,xji->", A, Lam)))
+
+    L = oracle.expand_links(dims, 2, q)
+    A = ocl.site_term(dims, L, m0, csw, ocl.KIND_EXP)
+    G = csw * ocl.clover_derivative(dims, L, ocl.exp_insertion(A, Lam, m0))
+    eps = 1e-5
+    for _ in range(12):
+        mu, x = RNG.integers(4), RNG.integers(V)
+        w = RNG.normal(size=3)
+        fd = (f(exp_update(q, mu, x, w, eps)) - f(exp_update(q, mu, x, w, -eps))) / (2 * eps)
+        assert abs(fd - G[mu, x] @ w) <= 1e-7 * max(1.0, abs(fd)), (mu, x, fd, G[mu, x] @ w)
+
+
+def _dense_action_exp(dims, q, m0, csw, eta, bc):
+    A = dr.clover_site_dense(dims, q, 2, m0, csw, exponential=True)
+    D = dr.dirac_clover_dense(dims, q, 2, A, bc)
+    Dee, Deo, Doe, Doo, e, o = dr.eo_blocks(dims, 2, D)
+    M = Dee - Deo @ np.linalg.solve(Doo, Doe)
+    y = eta.reshape(-1)[e]
+    odd = oracle.parity_mask(dims) == 1
+    S_det = -2.0 * sum(np.linalg.slogdet(A[k])[1] for k in np.where(odd)[0])
+    return np.vdot(y, np.linalg.solve(M.conj().T @ M, y)).real + S_det
+
+
+def test_exp_clover_fermion_force_matches_finite_differences():
+    """The exponential form's whole force (its det A_oo is constant) against dense-matrix actions."""
+    dims = (2, 2, 2, 4)
+    V = int(np.prod(dims))
+    m0, csw, bc = 0.1, 1.3, 1
+    q = smeared(dims, 551)
+    eta = synth.gaussian_spinor(dims, 2, 552)
+    eta[oracle.parity_mask(dims) == 1] = 0
+    ferm = ocl.CloverFermions(dims, m0, csw, eta, bc=bc, tol=1e-14, kind=ocl.KIND_EXP)
+    S0 = _dense_action_exp(dims, q, m0, csw, eta, bc)
+    assert abs(ferm.action(q) - S0) <= 1e-10 * abs(S0)
+    F = ferm.force(q)
+    eps = 1e-5
+    for _ in range(12):
+        mu, x = RNG.integers(4), RNG.integers(V)
+        w = RNG.normal(size=3)
+        fd = (_dense_action_exp(dims, exp_update(q, mu, x, w, eps), m0, csw, eta, bc)
+              - _dense_action_exp(dims, exp_update(q, mu, x, w, -eps), m0, csw, eta, bc)) / (2 * eps)
+        assert abs(fd - F[mu, x] @ w) <= 1e-6 * max(1.0, abs(fd)), (mu, x, fd, F[mu, x] @ w)
