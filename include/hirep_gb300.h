@@ -346,15 +346,20 @@ hr_status hr_clover_insertion_force(hr_ctx *ctx, hr_lattice lat, double c_sw, co
 
 /* force += coeff dS/dw for S_pf (and S_det if with_det) at the links of
  * gauge (canonical) / gauge_packed (hr_gauge_pack of the same links, HR_FUND
- * HR_F64) and clover (HR_FUND HR_F64, hr_clover_build with HR_CLOVER_SW, m0,
- * c_sw of those links), X = (Mhat^+ Mhat)^-1 eta (packed HR_F64 even): with
+ * HR_F64) and clover (HR_FUND HR_F64, hr_clover_build with kind, m0, c_sw of
+ * those links), X = (Mhat^+ Mhat)^-1 eta (packed HR_F64 even): with
  * Y = Mhat X, Z = A_oo^-1 H_oe X, W = A_oo^-1 H_eo^+ Y, the hops give
  * 1/2 dRe<(Y, W), H (X, Z)> (hr_force) and the site term c_sw times the
  * insertion force of Lam = -2 X Y^+ on even sites, -1/2 Z W^+ - 2 A^-1 [det]
- * on odd sites.  lat.bc and lat.theta apply to the hops. */
-hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, double m0, double c_sw, const double *gauge,
-                                  const void *gauge_packed, const void *clover, const void *X, int with_det,
-                                  double coeff, double *force, void *work, size_t work_bytes, hr_stream stream);
+ * on odd sites.  HR_CLOVER_EXP (A = (4+m0) exp(c_sw C / (4+m0))): the site
+ * term takes Lam' = int_0^1 exp((1-s) X) Lam exp(s X) ds, X = c_sw C / (4+m0),
+ * per chiral block from the eigen-decomposition of A (Jacobi), and S_det is a
+ * constant (tr C = 0): with_det adds nothing.  lat.bc and lat.theta apply to
+ * the hops. */
+hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, hr_clover_kind kind, double m0, double c_sw,
+                                  const double *gauge, const void *gauge_packed, const void *clover, const void *X,
+                                  int with_det, double coeff, double *force, void *work, size_t work_bytes,
+                                  hr_stream stream);
 
 /* *logdet = sum over the sites of `parity` of log det A(x) (both chiral
  * blocks, by Cholesky) from an FP64 clover field (HR_FUND or HR_ADJ).
@@ -407,8 +412,9 @@ typedef struct {
     double m0_hasenbusch;     /* its heavier mass                                      */
     int n_steps_gauge;        /* two time scales: gauge-force steps per link update of */
                               /* the fermion integrator (> 1); 0 or 1: one time scale  */
-    int clover;               /* 1: clover (SW) fermions, c_sw below (not with hasenbusch) */
+    int clover;               /* 1: clover fermions, c_sw below (not with hasenbusch)  */
     double c_sw;              /* their coefficient                                     */
+    hr_clover_kind clover_kind; /* HR_CLOVER_SW (0) or HR_CLOVER_EXP                   */
 } hr_hmc_params;
 
 typedef struct {
@@ -442,7 +448,7 @@ size_t hr_hmc_workspace_bytes(hr_lattice lat, const hr_hmc_params *prm);
  * each of its link updates, of length t, becomes m steps of length t / m of
  * the same integrator driven by the gauge force alone: as many solves as
  * with m = 1, m times (leapfrog; 2m, Omelyan) as many gauge-force steps.
- * With prm->clover the fermions carry the SW site term (Mhat = A_ee -
+ * With prm->clover the fermions carry the site term of prm->clover_kind (Mhat = A_ee -
  * H_eo A_oo^-1 H_oe / 4, eta drawn as Mhat^+ xi with that Mhat): the clover
  * field is rebuilt from the links before each solve, S_f = Re<eta, (Mhat^+
  * Mhat)^-1 eta> - 2 sum_{odd} log det A, and the force is

@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "hr_clover.cuh"
+#include "hr_eigh.cuh"
 #include "hr_host.h"
 
 using namespace hr;
@@ -643,8 +644,63 @@ struct KFieldArgs {
     const void *X, *Y; // even halves (packed FP64)
     const void *Z, *W; // odd halves
     const void *ainv;  // A^-1 odd half-field (packed FP64 clover), or nullptr: no det term
+    const void *afwd[2]; // exponential form: A on even / odd sites
+    int exp_kind;        // 1: A = a exp(c_sw C / a), the insertion goes through exp_insertion
+    double a;            // 4 + m0
     double *K;
 };
+
+// Exponential form: Lam' = int_0^1 exp((1-s) X) Lam exp(s X) ds per chiral block,
+// from the eigen-decomposition of the block of A = a exp(X) (eigenvalues mu =
+// a e^l): (V^+ Lam' V)_ij = (V^+ Lam V)_ij (e^l_i - e^l_j) / (l_i - l_j).
+__device__ void exp_insertion_block(const zd (&Ab)[4][4], double a, zd (&L)[4][4])
+{
+    zd M[4][4], V[4][4];
+    double mu[4], l[4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) M[i][j] = Ab[i][j];
+    jacobi_eigh<4>(M, V, mu);
+    for (int i = 0; i < 4; ++i) l[i] = log(mu[i] / a);
+    zd T[4][4], R[4][4];
+    for (int i = 0; i < 4; ++i) // T = V^+ L V
+        for (int j = 0; j < 4; ++j) {
+            zc acc = {0.0, 0.0};
+            for (int k = 0; k < 4; ++k)
+                for (int m = 0; m < 4; ++m)
+                    acc = zadd(acc, zmul(zmul(zconj(zc{V[k][i].re, V[k][i].im}), zc{L[k][m].re, L[k][m].im}),
+                                         zc{V[m][j].re, V[m][j].im}));
+            const double d = l[i] - l[j];
+            const double phi = fabs(d) > 1e-8 ? (exp(l[i]) - exp(l[j])) / d : exp(0.5 * (l[i] + l[j]));
+            T[i][j] = {phi * acc.re, phi * acc.im};
+        }
+    for (int i = 0; i < 4; ++i) // R = V T V^+
+        for (int j = 0; j < 4; ++j) {
+            zc acc = {0.0, 0.0};
+            for (int k = 0; k < 4; ++k)
+                for (int m = 0; m < 4; ++m)
+                    acc = zadd(acc, zmul(zmul(zc{V[i][k].re, V[i][k].im}, zc{T[k][m].re, T[k][m].im}),
+                                         zconj(zc{V[j][m].re, V[j][m].im})));
+            R[i][j] = {acc.re, acc.im};
+        }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) L[i][j] = R[i][j];
+}
+
+// the two 4 x 4 blocks of a packed FP64 clover half-field at site i
+__device__ void read_blocks(const void *half, int i, zd (&M)[2][4][4])
+{
+    CloverReader<2, kF64, dd> rd(half, i); // double-float reals, converted exactly
+    int q = 0;
+    for (int b = 0; b < 2; ++b) {
+        for (int k = 0; k < 4; ++k) M[b][k][k] = {dd_to_double(rd.get(q++)), 0.0};
+        for (int r = 0; r < 4; ++r)
+            for (int c = r + 1; c < 4; ++c) {
+                const double re = dd_to_double(rd.get(q++)), im = dd_to_double(rd.get(q++));
+                M[b][r][c] = {re, im};
+                M[b][c][r] = {re, -im};
+            }
+    }
+}
 
 // K of the two-flavour clover pseudofermion (and det A_oo) insertion
 __global__ void k_clover_k_from_fields(KFieldArgs A)
@@ -666,7 +722,27 @@ __global__ void k_clover_k_from_fields(KFieldArgs A)
     load_spinor<2, kF64>(p == 0 ? A.X : A.Z, g.nblk_s, i, u);
     load_spinor<2, kF64>(p == 0 ? A.Y : A.W, g.nblk_s, i, v);
     // Lam = coef u v^+ : Lam[(t, d), (s, c)] = coef u[t][d] conj(v[s][c])
-    add_blocks(P, p == 0 ? -2.0 : -0.5, [&](int t, int d, int s, int c) {
+    const double coef = p == 0 ? -2.0 : -0.5;
+    if (A.exp_kind) {
+        zd Ab[2][4][4], Lb[2][4][4];
+        read_blocks(A.afwd[p], i, Ab);
+        for (int b = 0; b < 2; ++b) {
+            for (int k = 0; k < 4; ++k)
+                for (int m = 0; m < 4; ++m) {
+                    const zc z = zmul(zc{u[2 * b + k / 2][k % 2].re, u[2 * b + k / 2][k % 2].im},
+                                      zconj(zc{v[2 * b + m / 2][m % 2].re, v[2 * b + m / 2][m % 2].im}));
+                    Lb[b][k][m] = {coef * z.re, coef * z.im};
+                }
+            exp_insertion_block(Ab[b], A.a, Lb[b]);
+        }
+        add_blocks(P, 1.0, [&](int t, int d, int s, int c) {
+            const zd z = Lb[t >> 1][(t & 1) * 2 + d][(s & 1) * 2 + c];
+            return zc{z.re, z.im};
+        });
+        store_k(A.K, x, P);
+        return;
+    }
+    add_blocks(P, coef, [&](int t, int d, int s, int c) {
         return zmul(zc{u[t][d].re, u[t][d].im}, zconj(zc{v[s][c].re, v[s][c].im}));
     });
     if (p == 1 && A.ainv) {
@@ -868,10 +944,13 @@ hr_status hr_clover_insertion_force(hr_ctx *ctx, hr_lattice lat, double c_sw, co
     return st;
 }
 
-hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, double m0, double c_sw, const double *gauge,
-                                  const void *gauge_packed, const void *clover, const void *X, int with_det,
-                                  double coeff, double *force, void *work, size_t work_bytes, hr_stream stream)
+hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, hr_clover_kind kind, double m0, double c_sw,
+                                  const double *gauge, const void *gauge_packed, const void *clover, const void *X,
+                                  int with_det, double coeff, double *force, void *work, size_t work_bytes,
+                                  hr_stream stream)
 {
+    if (ctx && kind != HR_CLOVER_SW && kind != HR_CLOVER_EXP)
+        return set_error(ctx, HR_ERR_INVALID_ARG, "bad clover kind");
     if (!ctx) return HR_ERR_INVALID_ARG;
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
@@ -920,7 +999,12 @@ hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, double m0, double
     A.Y = a;
     A.Z = b + half;
     A.W = a + half;
-    A.ainv = with_det ? ainv_odd : nullptr;
+    // the exponential form's det A_oo is a constant (C is traceless): no det force
+    A.ainv = (with_det && kind == HR_CLOVER_SW) ? ainv_odd : nullptr;
+    A.afwd[0] = clover_half(clover, g, HR_FUND, kF64, false, 0);
+    A.afwd[1] = clover_half(clover, g, HR_FUND, kF64, false, 1);
+    A.exp_kind = kind == HR_CLOVER_EXP;
+    A.a = 4.0 + m0;
     A.K = K;
     const long long V = 2LL * g.vh;
     k_clover_k_from_fields<<<(unsigned)((V + 127) / 128), 128, 0, s>>>(A);

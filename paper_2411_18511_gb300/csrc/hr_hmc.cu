@@ -342,7 +342,8 @@ struct Trajectory {
         if (x_valid) return HR_OK;
         hr_status st = pack();
         if (!st && prm.clover)
-            st = hr_clover_build(ctx, lat, HR_FUND, HR_F64, HR_CLOVER_SW, prm.m0, prm.c_sw, q, w.clover, (hr_stream)s);
+            st = hr_clover_build(ctx, lat, HR_FUND, HR_F64, prm.clover_kind, prm.m0, prm.c_sw, q, w.clover,
+                                 (hr_stream)s);
         if (!st) st = cg(eta_mass(), eta, w.X);
         if (!st && prm.hasenbusch) {
             // eta2 = Mhat_H^+ phi at the current links, then the ratio term's solve
@@ -452,8 +453,8 @@ struct Trajectory {
         if (prm.fermions && prm.clover) {
             st = solve();
             if (!st)
-                st = hr_clover_fermion_force(ctx, lat, prm.m0, prm.c_sw, q, w.gauge, w.clover, w.X, 1, 1.0, w.F, w.cf,
-                                             w.cf_bytes, (hr_stream)s);
+                st = hr_clover_fermion_force(ctx, lat, prm.clover_kind, prm.m0, prm.c_sw, q, w.gauge, w.clover, w.X, 1,
+                                             1.0, w.F, w.cf, w.cf_bytes, (hr_stream)s);
         } else if (prm.fermions) {
             st = solve();
             if (!st) st = solve_force(eta_mass(), w.X);
@@ -633,9 +634,10 @@ hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *pr
     if (prm->fermions && prm->hasenbusch && !(4.0 + prm->m0_hasenbusch != 0.0))
         return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0_hasenbusch must be nonzero");
     if (prm->hasenbusch && !prm->fermions) return set_error(ctx, HR_ERR_INVALID_ARG, "Hasenbusch needs fermions");
-    if (prm->clover && (!prm->fermions || prm->hasenbusch || !std::isfinite(prm->c_sw)))
+    if (prm->clover && (!prm->fermions || prm->hasenbusch || !std::isfinite(prm->c_sw) ||
+                        (prm->clover_kind != HR_CLOVER_SW && prm->clover_kind != HR_CLOVER_EXP)))
         return set_error(ctx, prm->hasenbusch ? HR_ERR_UNSUPPORTED : HR_ERR_INVALID_ARG,
-                         "clover fermions: fermions on, a finite c_sw, without Hasenbusch");
+                         "clover fermions: fermions on, a kind, a finite c_sw, without Hasenbusch");
     if (prm->n_steps_gauge < 0 || prm->n_steps_gauge > 1000)
         return set_error(ctx, HR_ERR_INVALID_ARG, "n_steps_gauge must lie in [0, 1000]");
     if (prm->fermions && prm->hasenbusch) st = check_buffers(ctx, {eta, phi}, {gauge, mom}, {work});

@@ -25,7 +25,8 @@ class HMC:
     def __init__(self, ctx: hr.Context, dims, beta: float, m0: float = 0.0, fermions: bool = True,
                  n_steps: int = 10, tau: float = 1.0, integrator: int = hr.HR_INTEGRATOR_OMELYAN,
                  solver: hr.hr_solver_opts | None = None, seed: int = 0, device="cuda",
-                 m0_hasenbusch: float | None = None, n_steps_gauge: int = 1, c_sw: float | None = None):
+                 m0_hasenbusch: float | None = None, n_steps_gauge: int = 1, c_sw: float | None = None,
+                 clover_kind: int = hr.HR_CLOVER_SW):
         self.ctx, self.dims, self.device = ctx, dims, device
         self.prm = hr.hr_hmc_params_default(beta, m0, fermions, n_steps, tau, integrator)
         if solver is not None:
@@ -37,6 +38,7 @@ class HMC:
         if c_sw is not None:
             self.prm.clover = 1
             self.prm.c_sw = float(c_sw)
+            self.prm.clover_kind = int(clover_kind)
         self.work = fields.empty_bytes(hr.hr_hmc_workspace_bytes(dims, self.prm), device)
         self.V = fields.volume(dims)
         self.gen = torch.Generator(device=device)
@@ -70,7 +72,7 @@ class HMC:
         and phi = Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2; returns (eta, phi))."""
         gauge = fields.pack_gauge(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, q)
         if self.prm.clover:
-            clov = fields.build_clover(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, hr.HR_CLOVER_SW, self.prm.m0,
+            clov = fields.build_clover(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, self.prm.clover_kind, self.prm.m0,
                                        self.prm.c_sw, q)
             return self._schur(gauge, self.prm.m0, self._xi(), True, clov)
         if not self.prm.hasenbusch:

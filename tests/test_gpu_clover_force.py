@@ -50,10 +50,11 @@ def test_insertion_force_matches_oracle(ctx, dims):
     assert rel(F.cpu().numpy(), want) <= 1e-12
 
 
+@pytest.mark.parametrize("kind", [hr.HR_CLOVER_SW, hr.HR_CLOVER_EXP])
 @pytest.mark.parametrize("with_det", [0, 1])
 @pytest.mark.parametrize("lat", [hr.Lattice((4, 6, 2, 6)), hr.Lattice((4, 4, 4, 4), 1),
                                  hr.Lattice((4, 2, 4, 6), 1, (0.4, 0.0, -1.2, 0.9))])
-def test_fermion_force_matches_oracle(ctx, lat, with_det):
+def test_fermion_force_matches_oracle(ctx, lat, with_det, kind):
     m0, csw = 0.1, 1.2
     V = int(np.prod(lat))
     q = smeared(lat, 611)
@@ -61,12 +62,13 @@ def test_fermion_force_matches_oracle(ctx, lat, with_det):
     X[oracle.parity_mask(lat) == 1] = 0
     qd = fields.gauge_to_device(q)
     gauge = fields.pack_gauge(ctx, lat, hr.HR_FUND, hr.HR_F64, qd)
-    clov = fields.build_clover(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_CLOVER_SW, m0, csw, qd)
+    clov = fields.build_clover(ctx, lat, hr.HR_FUND, hr.HR_F64, kind, m0, csw, qd)
     Xp = fields.pack_spinor(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, fields.spinor_to_device(X))
     F = torch.zeros((4, V, 3), dtype=torch.float64, device="cuda")
     work = fields.empty_bytes(hr.hr_clover_force_workspace_bytes(lat))
-    hr.hr_clover_fermion_force(ctx, lat, m0, csw, qd, gauge, clov, Xp, with_det, 0.5, F, work)
-    ferm = ocl.CloverFermions(lat, m0, csw, np.zeros_like(X), bc=lat.bc)
+    hr.hr_clover_fermion_force(ctx, lat, m0, csw, qd, gauge, clov, Xp, with_det, 0.5, F, work, kind=kind)
+    ferm = ocl.CloverFermions(lat, m0, csw, np.zeros_like(X), bc=lat.bc,
+                              kind=ocl.KIND_EXP if kind == hr.HR_CLOVER_EXP else ocl.KIND_SW)
     want = 0.5 * ferm.force_at(q, X, det=bool(with_det))
     assert rel(F.cpu().numpy(), want) <= 1e-12
 

@@ -285,9 +285,10 @@ def test_two_time_scales_reversible(ctx):
         run_gpu(ctx, lat, q, p, prm, eta_p)
 
 
+@pytest.mark.parametrize("kind", [hr.HR_CLOVER_SW, hr.HR_CLOVER_EXP])
 @pytest.mark.parametrize("m", [1, 3])
 @pytest.mark.parametrize("integrator", [hr.HR_INTEGRATOR_LEAPFROG, hr.HR_INTEGRATOR_OMELYAN])
-def test_clover_trajectory_matches_oracle(ctx, integrator, m):
+def test_clover_trajectory_matches_oracle(ctx, integrator, m, kind):
     """Clover (SW) fermions: the clover field rebuilt after every link update,
     S_f with -2 log det A_oo, the force of hops, site term and det term, on one
     or two time scales, against the oracle's CloverFermions."""
@@ -300,10 +301,10 @@ def test_clover_trajectory_matches_oracle(ctx, integrator, m):
     prm = hr.hr_hmc_params_default(beta, m0, True, 2, 0.3, integrator)
     prm.solver.tol = 1e-13
     prm.n_steps_gauge = m
-    prm.clover, prm.c_sw = 1, csw
+    prm.clover, prm.c_sw, prm.clover_kind = 1, csw, kind
     eta, eta_p = eta_field(ctx, lat, m0, 103)
     qg, pg, info = run_gpu(ctx, lat, q, p, prm, eta_p)
-    ferm = ocl.CloverFermions(lat, m0, csw, eta, bc=1)
+    ferm = ocl.CloverFermions(lat, m0, csw, eta, bc=1, kind=ocl.KIND_EXP if kind == hr.HR_CLOVER_EXP else ocl.KIND_SW)
     qo, po, io = ohmc.trajectory(lat, q, p, beta, 2, 0.3, integrator, ferm, n_steps_gauge=m)
     assert np.abs(qg - qo).max() <= 1e-11
     assert np.abs(pg - po).max() <= 1e-9
