@@ -1,9 +1,9 @@
 // hr_hop_twist.cu -- the hop for lattices with twisted fermion boundary
 // conditions, psi(x + L_mu mu) = e^{i theta_mu} psi(x): a hop that reaches its
 // neighbour forward across the boundary of direction mu multiplies the
-// neighbour spinor by e^{+i theta_mu}, backward by e^{-i theta_mu} (the phase
-// commutes with the spin projection and the colour product, so it is applied
-// to the loaded spinor before them).  An SU(2) link times a phase is no
+// spinor by e^{+i theta_mu}, backward by e^{-i theta_mu} (the phase commutes
+// with the spin projection and the colour product, so it is applied to the
+// projected half spinor, 2 NC complex products).  An SU(2) link times a phase is no
 // quaternion, so the twist cannot ride in the packed links as the
 // antiperiodic sign does (that sign stays there and combines with the phase).
 //
@@ -33,13 +33,58 @@ __device__ __forceinline__ void site_coords(const Geom &g, int i, int p, int (&x
     x[3] = 2 * k + ((x[0] + x[1] + x[2] + p) & 1);
 }
 
-// s *= c + i sn
-template <class T, int NC> __device__ __forceinline__ void phase_spinor(cpx<T> (&s)[4][NC], T c, T sn)
+// h *= c + i sn (the projected half spinor)
+template <class T, int NC> __device__ __forceinline__ void phase_half(cpx<T> (&h)[2][NC], T c, T sn)
 {
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < NC; ++b) s[a][b] = {s[a][b].re * c - s[a][b].im * sn, s[a][b].re * sn + s[a][b].im * c};
+        for (int b = 0; b < NC; ++b) h[a][b] = {h[a][b].re * c - h[a][b].im * sn, h[a][b].re * sn + h[a][b].im * c};
+}
+
+// one hop term of the twisted kernel: as hop_term_with / hop_compute, with the
+// boundary phase (e^{+-i theta}) on the projected half spinor when `cross`
+template <int MU, bool FWD, int REP, int PREC, bool FIRST, class T, int NC>
+__device__ __forceinline__ void twisted_term(const HopArgs &a, int site_link, int link_par, cpx<T> (&s)[4][NC],
+                                             float sc, bool neg_upper, bool cross, T c, T sn,
+                                             cpx<T> (&acc)[4][NC])
+{
+    if (neg_upper) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            s[0][k] = {-s[0][k].re, -s[0][k].im};
+            s[1][k] = {-s[1][k].re, -s[1][k].im};
+        }
+    }
+    cpx<T> h[2][NC], r[2][NC];
+    spin_project<MU, FWD>(s, h);
+    if (cross) phase_half(h, c, sn);
+    if constexpr (REP == kRepFund) {
+        T q[4];
+        load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+        if constexpr (PREC == kF16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = q[k] * sc;
+        }
+        su2_mul<!FWD>(q, h[0], r[0]);
+        su2_mul<!FWD>(q, h[1], r[1]);
+    } else {
+        T R[3][3];
+        if constexpr (REP == kRepAdj) {
+            T q[4];
+            load_quat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+            quat_to_adj(q, R);
+        } else {
+            load_mat<PREC>(a.gauge, a.g.nblk_g, link_par, MU, site_link, R);
+        }
+        if constexpr (PREC == kF16) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) R[k / 3][k % 3] = R[k / 3][k % 3] * sc;
+        }
+        so3_mul<!FWD>(R, h[0], r[0]);
+        so3_mul<!FWD>(R, h[1], r[1]);
+    }
+    spin_accumulate<MU, FWD, T, NC, FIRST>(acc, r);
 }
 
 template <int MU, int REP, int PREC, bool FIRST, class T, int NC>
@@ -49,17 +94,17 @@ __device__ __forceinline__ void twisted_dir(const HopArgs &a, int i, int rr, con
     const Geom &g = a.g;
     const int l = g.lrhs;
     const bool g5 = a.g5_in != 0;
+    // directions without a twist skip the phase (a uniform test: no divergence)
+    const bool tw = g.tw_s[MU].h != 0.f || g.tw_s[MU].l != 0.f || g.tw_c[MU].h != 1.f || g.tw_c[MU].l != 0.f;
     const T c = Real<T>::from_coef(g.tw_c[MU]), sn = Real<T>::from_coef(g.tw_s[MU]);
     cpx<T> s[4][NC];
     float sc;
     // forward: (1 - g_mu) U_mu(x) psi(x + mu), e^{+i theta} across the boundary
     load_spinor_raw<NC, PREC>(a.in, g.nblk_s, (nb.fwd[MU] << l) + rr, s, sc);
-    if (x[MU] == g.d[MU] - 1) phase_spinor(s, c, sn);
-    hop_term_with<MU, true, REP, PREC, FIRST>(a, i, a.p, s, sc, g5, acc);
+    twisted_term<MU, true, REP, PREC, FIRST>(a, i, a.p, s, sc, g5, tw && x[MU] == g.d[MU] - 1, c, sn, acc);
     // backward: (1 + g_mu) U_mu(x - mu)^+ psi(x - mu), e^{-i theta} across it
     load_spinor_raw<NC, PREC>(a.in, g.nblk_s, (nb.bwd[MU] << l) + rr, s, sc);
-    if (x[MU] == 0) phase_spinor(s, c, -sn);
-    hop_term_with<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, s, sc, g5, acc);
+    twisted_term<MU, false, REP, PREC, false>(a, nb.bwd[MU], 1 - a.p, s, sc, g5, tw && x[MU] == 0, c, -sn, acc);
 }
 
 template <int REP, int PREC, bool CLOV>
