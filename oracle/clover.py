@@ -364,9 +364,10 @@ class CloverFermions:
         L, A, X = self.solve(q)
         return self.force_at(q, X)
 
-    def force_at(self, q, X, det: bool = True) -> np.ndarray:
+    def force_at(self, q, X, det: bool = True, Y=None) -> np.ndarray:
         """The force for a given even X (X = (Mhat^+ Mhat)^-1 eta in the HMC;
-        det=False leaves out the det A_oo term)."""
+        det=False leaves out the det A_oo term): the derivative of
+        -2 Re <Y, dMhat X> with Y = Mhat X, or the given even Y."""
         from . import force, gamma5, hop, parity_mask
 
         L, A = self._setup(q)
@@ -375,7 +376,7 @@ class CloverFermions:
         odd = parity_mask(d) == 1
         Ainv = np.zeros_like(A)
         Ainv[odd] = np.linalg.inv(A[odd])
-        Y = schur(d, L, A, X, **kw)
+        Y = schur(d, L, A, X, **kw) if Y is None else np.asarray(Y, dtype=np.complex128)
         Z = apply_site(Ainv, hop(d, L, X, parity=1, **kw))                       # A_oo^-1 H_oe X
         W = apply_site(Ainv, gamma5(hop(d, L, gamma5(Y), parity=1, **kw)))     # A_oo^-1 H_eo^+ Y
         a = np.where(odd[:, None, None], W, Y)
@@ -388,3 +389,45 @@ class CloverFermions:
             return F + self.csw * clover_derivative(d, L, exp_insertion(A, Lam, self.m0))
         Lam = np.where(odd[:, None, None], -0.5 * outer(Z, W) - (2.0 * Ainv if det else 0.0), -2.0 * outer(X, Y))
         return F + self.csw * clover_derivative(d, L, Lam)
+
+
+class CloverHasenbusch:
+    """Clover fermions with Hasenbusch's mass preconditioning: with Mhat_H the
+    clover Schur operator at the heavier mass m0_h (same C, A_H = (4 + m0_h) +
+    c_sw C, or its exponential),
+      S = Re <eta, (Mhat_H^+ Mhat_H)^-1 eta> + Re <eta2, (Mhat^+ Mhat)^-1 eta2>
+          - 2 sum_{x odd} log det A(x),     eta2 = Mhat_H^+ phi,
+    the det term at the light mass (det D = det A_oo det Mhat, and det Mhat^+ Mhat
+    = det Mhat_H^+ Mhat_H times the ratio).  The variation of eta2 adds
+    2 Re <phi, dMhat_H X2>, i.e. minus the force of -2 Re <Y, dMhat_H X> at
+    X = X2, Y = phi."""
+
+    def __init__(self, dims, m0: float, m0_h: float, csw: float, eta, phi, bc=0, tol: float = 1e-13, theta=None,
+                 kind=KIND_SW):
+        self.dims, self.m0, self.m0_h, self.csw, self.bc, self.tol, self.theta = dims, m0, m0_h, csw, bc, tol, theta
+        self.heavy = CloverFermions(dims, m0_h, csw, eta, bc=bc, tol=tol, theta=theta, kind=kind)
+        self.light = CloverFermions(dims, m0, csw, None, bc=bc, tol=tol, theta=theta, kind=kind)
+        self.phi = np.asarray(phi, dtype=np.complex128)
+        self.iters = 0
+
+    def _ratio(self, q):
+        Lh, Ah = self.heavy._setup(q)
+        kw = dict(bc=self.bc, theta=self.theta)
+        eta2 = schur(self.dims, Lh, Ah, self.phi, dagger=True, **kw)
+        L, A = self.light._setup(q)
+        x, it, tr, ok = cg(self.dims, L, A, eta2, tol=self.tol, maxiter=50000, **kw)
+        assert ok, tr
+        self.iters += it
+        return A, eta2, x
+
+    def action(self, q) -> float:
+        _, _, Xh = self.heavy.solve(q)
+        A, eta2, X2 = self._ratio(q)
+        return (float(np.vdot(self.heavy.eta, Xh).real) + float(np.vdot(eta2, X2).real)
+                + det_action(A, self.dims))
+
+    def force(self, q) -> np.ndarray:
+        _, _, Xh = self.heavy.solve(q)
+        _, _, X2 = self._ratio(q)
+        return (self.heavy.force_at(q, Xh, det=False) + self.light.force_at(q, X2, det=True)
+                - self.heavy.force_at(q, X2, det=False, Y=self.phi))

@@ -178,3 +178,46 @@ def test_exp_clover_fermion_force_matches_finite_differences():
         fd = (_dense_action_exp(dims, exp_update(q, mu, x, w, eps), m0, csw, eta, bc)
               - _dense_action_exp(dims, exp_update(q, mu, x, w, -eps), m0, csw, eta, bc)) / (2 * eps)
         assert abs(fd - F[mu, x] @ w) <= 1e-6 * max(1.0, abs(fd)), (mu, x, fd, F[mu, x] @ w)
+
+
+@pytest.mark.parametrize("kind", [ocl.KIND_SW, ocl.KIND_EXP])
+def test_clover_hasenbusch_force_matches_finite_differences(kind):
+    """Clover fermions with Hasenbusch's two pseudofermions: S = Re<eta, (Mhat_H^+ Mhat_H)^-1 eta>
+    + Re<eta2, (Mhat^+ Mhat)^-1 eta2> - 2 sum_odd log det A, eta2 = Mhat_H^+ phi, all from dense
+    matrices; the oracle's force against its central finite differences."""
+    dims = (2, 2, 2, 4)
+    V = int(np.prod(dims))
+    m0, mh, csw, bc = 0.05, 0.5, 1.2, 1
+    q = smeared(dims, 561)
+    eta = synth.gaussian_spinor(dims, 2, 562)
+    phi = synth.gaussian_spinor(dims, 2, 563)
+    odd = oracle.parity_mask(dims) == 1
+    eta[odd] = 0
+    phi[odd] = 0
+    exponential = kind == ocl.KIND_EXP
+
+    def S(qq):
+        def schur_dense(m):
+            A = dr.clover_site_dense(dims, qq, 2, m, csw, exponential=exponential)
+            D = dr.dirac_clover_dense(dims, qq, 2, A, bc)
+            Dee, Deo, Doe, Doo, e, o = dr.eo_blocks(dims, 2, D)
+            return Dee - Deo @ np.linalg.solve(Doo, Doe), e, A
+
+        M, e, A = schur_dense(m0)
+        MH, _, _ = schur_dense(mh)
+        y1 = eta.reshape(-1)[e]
+        y2 = MH.conj().T @ phi.reshape(-1)[e]
+        S_det = -2.0 * sum(np.linalg.slogdet(A[k])[1] for k in np.where(odd)[0])
+        return (np.vdot(y1, np.linalg.solve(MH.conj().T @ MH, y1)).real
+                + np.vdot(y2, np.linalg.solve(M.conj().T @ M, y2)).real + S_det)
+
+    ferm = ocl.CloverHasenbusch(dims, m0, mh, csw, eta, phi, bc=bc, tol=1e-14, kind=kind)
+    S0 = S(q)
+    assert abs(ferm.action(q) - S0) <= 1e-10 * abs(S0)
+    F = ferm.force(q)
+    eps = 1e-5
+    for _ in range(10):
+        mu, x = RNG.integers(4), RNG.integers(V)
+        w = RNG.normal(size=3)
+        fd = (S(exp_update(q, mu, x, w, eps)) - S(exp_update(q, mu, x, w, -eps))) / (2 * eps)
+        assert abs(fd - F[mu, x] @ w) <= 1e-6 * max(1.0, abs(fd)), (mu, x, fd, F[mu, x] @ w)
