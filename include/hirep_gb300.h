@@ -348,7 +348,9 @@ hr_status hr_clover_insertion_force(hr_ctx *ctx, hr_lattice lat, double c_sw, co
  * gauge (canonical) / gauge_packed (hr_gauge_pack of the same links, HR_FUND
  * HR_F64) and clover (HR_FUND HR_F64, hr_clover_build with kind, m0, c_sw of
  * those links), X = (Mhat^+ Mhat)^-1 eta (packed HR_F64 even): with
- * Y = Mhat X, Z = A_oo^-1 H_oe X, W = A_oo^-1 H_eo^+ Y, the hops give
+ * Y = Mhat X (or the given even Y, nullable: then the call differentiates
+ * -2 Re<Y, Mhat X> at fixed X, Y, as the Hasenbusch ratio term needs),
+ * Z = A_oo^-1 H_oe X, W = A_oo^-1 H_eo^+ Y, the hops give
  * 1/2 dRe<(Y, W), H (X, Z)> (hr_force) and the site term c_sw times the
  * insertion force of Lam = -2 X Y^+ on even sites, -1/2 Z W^+ - 2 A^-1 [det]
  * on odd sites.  HR_CLOVER_EXP (A = (4+m0) exp(c_sw C / (4+m0))): the site
@@ -358,8 +360,8 @@ hr_status hr_clover_insertion_force(hr_ctx *ctx, hr_lattice lat, double c_sw, co
  * the hops. */
 hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, hr_clover_kind kind, double m0, double c_sw,
                                   const double *gauge, const void *gauge_packed, const void *clover, const void *X,
-                                  int with_det, double coeff, double *force, void *work, size_t work_bytes,
-                                  hr_stream stream);
+                                  const void *Y, int with_det, double coeff, double *force, void *work,
+                                  size_t work_bytes, hr_stream stream);
 
 /* *logdet = sum over the sites of `parity` of log det A(x) (both chiral
  * blocks, by Cholesky) from an FP64 clover field (HR_FUND or HR_ADJ).
@@ -412,7 +414,7 @@ typedef struct {
     double m0_hasenbusch;     /* its heavier mass                                      */
     int n_steps_gauge;        /* two time scales: gauge-force steps per link update of */
                               /* the fermion integrator (> 1); 0 or 1: one time scale  */
-    int clover;               /* 1: clover fermions, c_sw below (not with hasenbusch)  */
+    int clover;               /* 1: clover fermions, c_sw and clover_kind below        */
     double c_sw;              /* their coefficient                                     */
     hr_clover_kind clover_kind; /* HR_CLOVER_SW (0) or HR_CLOVER_EXP                   */
 } hr_hmc_params;

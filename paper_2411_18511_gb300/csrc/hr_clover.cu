@@ -946,15 +946,15 @@ hr_status hr_clover_insertion_force(hr_ctx *ctx, hr_lattice lat, double c_sw, co
 
 hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, hr_clover_kind kind, double m0, double c_sw,
                                   const double *gauge, const void *gauge_packed, const void *clover, const void *X,
-                                  int with_det, double coeff, double *force, void *work, size_t work_bytes,
-                                  hr_stream stream)
+                                  const void *Y, int with_det, double coeff, double *force, void *work,
+                                  size_t work_bytes, hr_stream stream)
 {
     if (ctx && kind != HR_CLOVER_SW && kind != HR_CLOVER_EXP)
         return set_error(ctx, HR_ERR_INVALID_ARG, "bad clover kind");
     if (!ctx) return HR_ERR_INVALID_ARG;
     hr_status st = validate_lattice(ctx, lat, 1);
     if (st) return st;
-    st = check_buffers(ctx, {gauge_packed, clover, X, work}, {gauge, force});
+    st = check_buffers(ctx, {gauge_packed, clover, X, work}, {gauge, force}, {Y});
     if (st) return st;
     if (!(4.0 + m0 != 0.0) || !std::isfinite(c_sw) || !std::isfinite(coeff))
         return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 nonzero, c_sw and coeff finite");
@@ -969,10 +969,15 @@ hr_status hr_clover_fermion_force(hr_ctx *ctx, hr_lattice lat, hr_clover_kind ki
     char *b = a + 2 * half;          // full field (X | Z)
     char *t_odd = b + 2 * half;
     const void *ainv_odd = clover_half(clover, g, HR_FUND, kF64, true, 1);
-    // Y = Mhat X
-    st = apply_eo_op(ctx, g, m0, HR_FUND, kF64, HR_OP_SCHUR, gauge_packed, X, a, t_odd, nullptr, kFinNone, nullptr,
-                     nullptr, s, nullptr, clover);
-    if (st) return st;
+    // Y = Mhat X, or the given Y
+    if (Y) {
+        cudaError_t ce = cudaMemcpyAsync(a, Y, half, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "copy: %s", cudaGetErrorString(ce));
+    } else {
+        st = apply_eo_op(ctx, g, m0, HR_FUND, kF64, HR_OP_SCHUR, gauge_packed, X, a, t_odd, nullptr, kFinNone,
+                         nullptr, nullptr, s, nullptr, clover);
+        if (st) return st;
+    }
     // Z = A_oo^-1 H_oe X,  W = A_oo^-1 g5 H_oe g5 Y  (A commutes with g5)
     for (int k = 0; k < 2; ++k) {
         HopLaunch L{};

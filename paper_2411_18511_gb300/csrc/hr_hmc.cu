@@ -255,6 +255,7 @@ struct HmcWork {
     void *cg;         // CG workspace
     size_t cg_bytes;
     void *clover;     // clover fermions: the packed FP64 clover field of the current links
+    void *clover_h;   // with Hasenbusch: the clover field at the heavy mass
     void *cf;         // clover force workspace
     size_t cf_bytes;
 };
@@ -290,14 +291,17 @@ size_t layout_hmc(hr_lattice lat, const hr_hmc_params &prm, char *w, HmcWork *hw
         e2 = take(half);
     }
     void *cg = take(cgb);
-    void *clover = nullptr, *cf = nullptr;
+    void *clover = nullptr, *clover_h = nullptr, *cf = nullptr;
     size_t cfb = 0;
     if (prm.clover) {
         clover = take(hr_clover_packed_bytes(lat, HR_FUND, HR_F64));
+        if (prm.hasenbusch) clover_h = take(hr_clover_packed_bytes(lat, HR_FUND, HR_F64));
         cfb = hr_clover_force_workspace_bytes(lat);
         cf = take(cfb);
     }
-    if (hw) *hw = HmcWork{gauge, (double *)F, (double *)Fg, X, X2, eta2, e1, e2, a, b, t, cg, cgb, clover, cf, cfb};
+    if (hw)
+        *hw = HmcWork{gauge, (double *)F, (double *)Fg, X, X2, eta2, e1, e2, a, b, t, cg, cgb, clover, clover_h, cf,
+                      cfb};
     return off;
 }
 
@@ -322,14 +326,20 @@ struct Trajectory {
     // the mass of the solve with eta: the heavy one under Hasenbusch preconditioning
     double eta_mass() const { return prm.hasenbusch ? prm.m0_hasenbusch : prm.m0; }
 
+    // the clover field of a solve at mass m0 (the heavy one under Hasenbusch)
+    void *clover_of(double m0) const
+    {
+        return (prm.hasenbusch && m0 == prm.m0_hasenbusch && m0 != prm.m0) ? w.clover_h : w.clover;
+    }
+
     hr_status cg(double m0, const void *src, void *x)
     {
         hr_solver_opts o = prm.solver;
         o.n_rhs = 1;
         o.x0_is_guess = 0;
         hr_solve_info info{};
-        hr_status st = prm.clover ? hr_cg_solve_clover(ctx, lat, HR_FUND, &o, w.gauge, w.clover, src, x, &info, w.cg,
-                                                       w.cg_bytes, (hr_stream)s)
+        hr_status st = prm.clover ? hr_cg_solve_clover(ctx, lat, HR_FUND, &o, w.gauge, clover_of(m0), src, x, &info,
+                                                       w.cg, w.cg_bytes, (hr_stream)s)
                                   : hr_cg_solve(ctx, lat, m0, HR_FUND, &o, w.gauge, src, x, &info, w.cg, w.cg_bytes,
                                                 (hr_stream)s);
         cg_iters += info.iters;
@@ -344,11 +354,15 @@ struct Trajectory {
         if (!st && prm.clover)
             st = hr_clover_build(ctx, lat, HR_FUND, HR_F64, prm.clover_kind, prm.m0, prm.c_sw, q, w.clover,
                                  (hr_stream)s);
+        if (!st && prm.clover && prm.hasenbusch)
+            st = hr_clover_build(ctx, lat, HR_FUND, HR_F64, prm.clover_kind, prm.m0_hasenbusch, prm.c_sw, q,
+                                 w.clover_h, (hr_stream)s);
         if (!st) st = cg(eta_mass(), eta, w.X);
         if (!st && prm.hasenbusch) {
             // eta2 = Mhat_H^+ phi at the current links, then the ratio term's solve
             st = apply_eo_op(ctx, g, prm.m0_hasenbusch, HR_FUND, kF64, HR_OP_SCHUR_DAG, w.gauge, phi, w.eta2,
-                             w.t_odd, nullptr, kFinNone, nullptr, nullptr, s);
+                             w.t_odd, nullptr, kFinNone, nullptr, nullptr, s, nullptr,
+                             prm.clover ? w.clover_h : nullptr);
             if (!st) st = cg(prm.m0, w.eta2, w.X2);
         }
         if (st) return st;
@@ -451,10 +465,20 @@ struct Trajectory {
     {
         hr_status st = HR_OK;
         if (prm.fermions && prm.clover) {
+            auto cforce = [&](double m0, const void *clov, const void *X, const void *Y, int det, double coeff) {
+                return hr_clover_fermion_force(ctx, lat, prm.clover_kind, m0, prm.c_sw, q, w.gauge, clov, X, Y, det,
+                                               coeff, w.F, w.cf, w.cf_bytes, (hr_stream)s);
+            };
             st = solve();
-            if (!st)
-                st = hr_clover_fermion_force(ctx, lat, prm.clover_kind, prm.m0, prm.c_sw, q, w.gauge, w.clover, w.X, 1,
-                                             1.0, w.F, w.cf, w.cf_bytes, (hr_stream)s);
+            if (!prm.hasenbusch) {
+                if (!st) st = cforce(prm.m0, w.clover, w.X, nullptr, 1, 1.0);
+            } else {
+                // heavy term; ratio term's solve (and the light det A_oo); the variation of
+                // eta2 = Mhat_H^+ phi: 2 Re<phi, dMhat_H X2>, minus the force of -2 Re<Y, dMhat_H X>
+                if (!st) st = cforce(prm.m0_hasenbusch, w.clover_h, w.X, nullptr, 0, 1.0);
+                if (!st) st = cforce(prm.m0, w.clover, w.X2, nullptr, 1, 1.0);
+                if (!st) st = cforce(prm.m0_hasenbusch, w.clover_h, w.X2, phi, 0, -1.0);
+            }
         } else if (prm.fermions) {
             st = solve();
             if (!st) st = solve_force(eta_mass(), w.X);
@@ -634,10 +658,11 @@ hr_status hr_hmc_trajectory(hr_ctx *ctx, hr_lattice lat, const hr_hmc_params *pr
     if (prm->fermions && prm->hasenbusch && !(4.0 + prm->m0_hasenbusch != 0.0))
         return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0_hasenbusch must be nonzero");
     if (prm->hasenbusch && !prm->fermions) return set_error(ctx, HR_ERR_INVALID_ARG, "Hasenbusch needs fermions");
-    if (prm->clover && (!prm->fermions || prm->hasenbusch || !std::isfinite(prm->c_sw) ||
+    if (prm->clover && (!prm->fermions || !std::isfinite(prm->c_sw) ||
                         (prm->clover_kind != HR_CLOVER_SW && prm->clover_kind != HR_CLOVER_EXP)))
-        return set_error(ctx, prm->hasenbusch ? HR_ERR_UNSUPPORTED : HR_ERR_INVALID_ARG,
-                         "clover fermions: fermions on, a kind, a finite c_sw, without Hasenbusch");
+        return set_error(ctx, HR_ERR_INVALID_ARG, "clover fermions: fermions on, a kind, a finite c_sw");
+    if (prm->clover && prm->hasenbusch && prm->m0_hasenbusch == prm->m0)
+        return set_error(ctx, HR_ERR_INVALID_ARG, "Hasenbusch needs a heavy mass other than m0");
     if (prm->n_steps_gauge < 0 || prm->n_steps_gauge > 1000)
         return set_error(ctx, HR_ERR_INVALID_ARG, "n_steps_gauge must lie in [0, 1000]");
     if (prm->fermions && prm->hasenbusch) st = check_buffers(ctx, {eta, phi}, {gauge, mom}, {work});

@@ -71,21 +71,30 @@ class HMC:
         """Packed even eta = Mhat^+ xi for the links q (Hasenbusch: eta = Mhat_H^+ xi1
         and phi = Mhat_H (Mhat_H^+ Mhat_H)^-1 Mhat^+ xi2; returns (eta, phi))."""
         gauge = fields.pack_gauge(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, q)
+        m0, mh = self.prm.m0, self.prm.m0_hasenbusch
+        clov = clov_h = None
         if self.prm.clover:
-            clov = fields.build_clover(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, self.prm.clover_kind, self.prm.m0,
-                                       self.prm.c_sw, q)
-            return self._schur(gauge, self.prm.m0, self._xi(), True, clov)
+            def build(m):
+                return fields.build_clover(self.ctx, self.dims, hr.HR_FUND, hr.HR_F64, self.prm.clover_kind, m,
+                                           self.prm.c_sw, q)
+
+            clov = build(m0)
+            if self.prm.hasenbusch:
+                clov_h = build(mh)
         if not self.prm.hasenbusch:
-            return self._schur(gauge, self.prm.m0, self._xi(), True)
-        mh = self.prm.m0_hasenbusch
-        eta = self._schur(gauge, mh, self._xi(), True)
-        rhs = self._schur(gauge, self.prm.m0, self._xi(), True)
+            return self._schur(gauge, m0, self._xi(), True, clov)
+        eta = self._schur(gauge, mh, self._xi(), True, clov_h)
+        rhs = self._schur(gauge, m0, self._xi(), True, clov)
         opts = hr.hr_solver_opts.from_buffer_copy(self.prm.solver)
         opts.tol = min(opts.tol, 1e-12)
         y = fields.zeros_spinor(self.dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, device=self.device)
-        work = fields.empty_bytes(hr.hr_cg_workspace_bytes(self.dims, hr.HR_FUND, opts), self.device)
-        hr.hr_cg_solve(self.ctx, self.dims, mh, hr.HR_FUND, opts, gauge, rhs, y, work)
-        return eta, self._schur(gauge, mh, y, False)
+        if clov_h is not None:
+            work = fields.empty_bytes(hr.hr_cg_clover_workspace_bytes(self.dims, hr.HR_FUND, opts), self.device)
+            hr.hr_cg_solve_clover(self.ctx, self.dims, hr.HR_FUND, opts, gauge, clov_h, rhs, y, work)
+        else:
+            work = fields.empty_bytes(hr.hr_cg_workspace_bytes(self.dims, hr.HR_FUND, opts), self.device)
+            hr.hr_cg_solve(self.ctx, self.dims, mh, hr.HR_FUND, opts, gauge, rhs, y, work)
+        return eta, self._schur(gauge, mh, y, False, clov_h)
 
     def step(self, q: torch.Tensor):
         """One HMC update of the links q (device double[4][V][4], in place).

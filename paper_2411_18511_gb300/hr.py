@@ -172,7 +172,7 @@ def lib():
                 "hr_clover_build": ([P, LAT, I, I, I, D, D, P, P, P], I),
                 "hr_clover_force_workspace_bytes": ([LAT], S),
                 "hr_clover_insertion_force": ([P, LAT, D, P, P, D, P, P, S, P], I),
-                "hr_clover_fermion_force": ([P, LAT, I, D, D, P, P, P, P, I, D, P, P, S, P], I),
+                "hr_clover_fermion_force": ([P, LAT, I, D, D, P, P, P, P, P, I, D, P, P, S, P], I),
                 "hr_clover_logdet": ([P, LAT, I, P, I, ctypes.POINTER(ctypes.c_double), P], I),
                 "hr_clover_apply": ([P, LAT, I, I, I, I, I, P, P, P, P], I),
                 "hr_dirac_apply_clover": ([P, LAT, I, I, P, P, P, P, P], I),
@@ -432,14 +432,15 @@ def hr_clover_insertion_force(ctx: Context, dims, c_sw, gauge, lam, coeff, force
 
 
 def hr_clover_fermion_force(ctx: Context, dims, m0, c_sw, gauge, gauge_packed, clover, X, with_det, coeff, force,
-                            work, stream=None, kind=HR_CLOVER_SW):
+                            work, stream=None, kind=HR_CLOVER_SW, Y=None):
     V = _vol(dims)
     _need(gauge, 4 * V * 4 * 8, "gauge")
     _need(force, 4 * V * 3 * 8, "force")
     _need(X, hr_spinor_packed_bytes(dims, HR_FUND, HR_F64, HR_EVEN, 1), "X")
     return ctx.check(lib().hr_clover_fermion_force(ctx.handle, lattice(dims), int(kind), float(m0), float(c_sw),
                                                    _ptr(gauge),
-                                                   _ptr(gauge_packed), _ptr(clover), _ptr(X), int(bool(with_det)),
+                                                   _ptr(gauge_packed), _ptr(clover), _ptr(X), _ptr(Y),
+                                                   int(bool(with_det)),
                                                    float(coeff), _ptr(force), _ptr(work), _nbytes(work),
                                                    _stream(stream)))
 

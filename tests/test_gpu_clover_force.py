@@ -101,25 +101,25 @@ def test_argument_checks(ctx):
     L = hr.lib()
     small = fields.empty_bytes(need - 256)
     rc = L.hr_clover_fermion_force(ctx.handle, hr.lattice(lat), 0, 0.1, 1.0, hr._ptr(qd), hr._ptr(gauge),
-                                   hr._ptr(clov), hr._ptr(X), 1, 1.0, hr._ptr(F), hr._ptr(small), need - 256, None)
+                                   hr._ptr(clov), hr._ptr(X), None, 1, 1.0, hr._ptr(F), hr._ptr(small), need - 256, None)
     assert rc == hr.HR_ERR_WORKSPACE
     work = fields.empty_bytes(need)
     rc = L.hr_clover_fermion_force(ctx.handle, hr.lattice(lat), 7, 0.1, 1.0, hr._ptr(qd), hr._ptr(gauge),
-                                   hr._ptr(clov), hr._ptr(X), 1, 1.0, hr._ptr(F), hr._ptr(work), need, None)
+                                   hr._ptr(clov), hr._ptr(X), None, 1, 1.0, hr._ptr(F), hr._ptr(work), need, None)
     assert rc == hr.HR_ERR_INVALID_ARG
     big = fields.empty_bytes(hr.hr_spinor_packed_bytes(lat, 0, 0, 0, 1) + 64)
     rc = L.hr_clover_fermion_force(ctx.handle, hr.lattice(lat), 0, 0.1, 1.0, hr._ptr(qd), hr._ptr(gauge),
-                                   hr._ptr(clov), big.data_ptr() + 8, 1, 1.0, hr._ptr(F), hr._ptr(work), need, None)
+                                   hr._ptr(clov), big.data_ptr() + 8, None, 1, 1.0, hr._ptr(F), hr._ptr(work), need, None)
     assert rc == hr.HR_ERR_INVALID_ARG
     # a site block that is not positive definite: log det refuses it
     rough = fields.build_clover(ctx, lat, hr.HR_FUND, hr.HR_F64, hr.HR_CLOVER_SW, 0.1, 60.0, qd)
     with pytest.raises(hr.HrError, match="positive definite"):
         hr.hr_clover_logdet(ctx, lat, hr.HR_FUND, rough, hr.HR_ODD)
-    # clover fermions with Hasenbusch: not in the trajectory driver
+    # a clover kind the trajectory driver does not know
     prm = hr.hr_hmc_params_default(2.2, 0.1, True, 2, 0.2)
-    prm.clover, prm.c_sw, prm.hasenbusch, prm.m0_hasenbusch = 1, 1.0, 1, 0.5
+    prm.clover, prm.c_sw, prm.clover_kind = 1, 1.0, 5
     work_h = fields.empty_bytes(hr.hr_hmc_workspace_bytes(lat, prm))
     p = torch.zeros((4, V, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(hr.HrError) as err:
-        hr.hr_hmc_trajectory(ctx, lat, prm, qd.clone(), p, X, work_h, phi=X)
-    assert err.value.code == hr.HR_ERR_UNSUPPORTED
+        hr.hr_hmc_trajectory(ctx, lat, prm, qd.clone(), p, X, work_h)
+    assert err.value.code == hr.HR_ERR_INVALID_ARG

@@ -346,3 +346,41 @@ def test_clover_chain(ctx):
     pp.neg_()
     i2 = hr.hr_hmc_trajectory(ctx, lat, chain.prm, q, pp, eta, chain.work)
     assert (q - q0).abs().max().item() <= 1e-9 and abs(i1.dH + i2.dH) <= 1e-7
+
+
+@pytest.mark.parametrize("kind", [hr.HR_CLOVER_SW, hr.HR_CLOVER_EXP])
+def test_clover_hasenbusch_trajectory_matches_oracle(ctx, kind):
+    """Clover fermions with Hasenbusch's two pseudofermions (a heavy clover field
+    beside the light one), on two time scales, against the oracle."""
+    from oracle import clover as ocl
+
+    lat = hr.Lattice((4, 2, 2, 4), 1)
+    beta, m0, mh, csw = 2.2, 0.05, 0.5, 1.1
+    q = smeared(lat, 121)
+    p = np.random.default_rng(122).normal(size=(4, int(np.prod(lat)), 3))
+    prm = hr.hr_hmc_params_default(beta, m0, True, 2, 0.3, hr.HR_INTEGRATOR_OMELYAN)
+    prm.solver.tol = 1e-13
+    prm.n_steps_gauge = 2
+    prm.clover, prm.c_sw, prm.clover_kind = 1, csw, kind
+    prm.hasenbusch, prm.m0_hasenbusch = 1, mh
+    eta, eta_p = eta_field(ctx, lat, m0, 123)
+    phi, phi_p = eta_field(ctx, lat, m0, 124)
+    qg, pg, info = run_gpu(ctx, lat, q, p, prm, eta_p, phi_p)
+    okind = ocl.KIND_EXP if kind == hr.HR_CLOVER_EXP else ocl.KIND_SW
+    ferm = ocl.CloverHasenbusch(lat, m0, mh, csw, eta, phi, bc=1, kind=okind)
+    qo, po, io = ohmc.trajectory(lat, q, p, beta, 2, 0.3, hr.HR_INTEGRATOR_OMELYAN, ferm, n_steps_gauge=2)
+    assert np.abs(qg - qo).max() <= 1e-11
+    assert np.abs(pg - po).max() <= 1e-9
+    assert abs(info.dH - io["dH"]) <= 1e-9, (info.dH, io["dH"])
+    assert abs(info.fermion_action_end - io["end"]["fermion"]) <= 1e-9 * abs(io["end"]["fermion"])
+
+
+def test_clover_hasenbusch_chain(ctx):
+    lat = hr.Lattice((4, 4, 4, 4), 1)
+    q = dev(smeared(lat, 131))
+    chain = HMC(ctx, lat, beta=2.2, m0=0.05, fermions=True, n_steps=4, tau=0.5, seed=132, c_sw=1.0,
+                m0_hasenbusch=0.5, n_steps_gauge=2)
+    for _ in range(3):
+        acc, info = chain.step(q)
+        assert np.isfinite(info.dH) and abs(info.dH) < 2.0
+    assert chain.accepted >= 2
