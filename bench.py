@@ -611,7 +611,9 @@ def run_hmc(ctx, torch, hr, fields, synth):
                                              ("omelyan_f16_inner_hasenbusch", om, 12, hr.HR_F16, 0.2, 1),
                                              ("omelyan_f16_inner_2scales", om, 6, hr.HR_F16, None, 3),
                                              ("omelyan_f16_inner_hasenbusch_2scales", om, 6, hr.HR_F16, 0.2, 3),
-                                             ("omelyan_f16_inner_clover_2scales", om, 6, hr.HR_F16, None, 3)):
+                                             ("omelyan_f16_inner_clover_2scales", om, 6, hr.HR_F16, None, 3),
+                                             ("omelyan_f16_inner_clover_hasenbusch_2scales", om, 6, hr.HR_F16, 0.2,
+                                              3)):
         solver = hr.hr_solver_default_opts()
         solver.inner_prec = inner
         solver.reliable_delta = 0.01 if inner != hr.HR_F64 else 0.1
