@@ -103,6 +103,25 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks_fn(dist, device):
+    """x -> the maximum of x over the ranks of the default process group (the
+    slowest replica's time); the identity without one."""
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return max_over_ranks
+
+
+def replica_value(world: int, units_per_step: float, ms_per_step: float) -> float:
+    """Whole-job throughput of `world` replicas that each process units_per_step
+    per step, timed by the slowest rank: units per second."""
+    return world * units_per_step / (ms_per_step * 1e-3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -247,12 +266,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = max_over_ranks_fn(dist, "cuda")
 
     ctx = hr.Context(local)
     L4 = args.lattice
@@ -316,7 +330,7 @@ def run_ours(args):
     kernel = f"{kname}<fund,{pname}> x{block}"
     bytes_site = hop_bytes_per_site("fund", pname)
     bytes_step = 2 * Vh * bytes_site
-    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    value = replica_value(world, bytes_step, ms_step) / 1e9
     launch_ms = ms_step / 2.0  # the step is exactly two launches of the hop kernel
     achieved = Vh * bytes_site / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
