@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "hr_clover.cuh"
+#include "hr_clover_leaf.cuh"
 #include "hr_eigh.cuh"
 #include "hr_host.h"
 
@@ -562,12 +563,10 @@ hr_status hr_dirac_eo_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec pr
 // P_l^b = sum_{s,t} (s_l)_st Lam[(2b+t, .), (2b+s, .)] (colour 2x2),
 //   K_0l = P_l^1 - P_l^0,  K_23 = -(P_1^0 + P_1^1),  K_13 = P_2^0 + P_2^1,  K_12 = -(P_3^0 + P_3^1).
 // K field: double [V][6][2][2][2] (lexicographic site, planes 01 02 03 12 13 23).
-// The link derivative of f: each link occurs in 8 leaves of each of the 3
-// planes that contain its direction; for a leaf P = A V B whose factor V is
-// the link U (or U^+), dU = X U with X = i w.s/2, and
-//   tr[dP K] - tr[dP^+ K] = tr[X (U B K A + A^+ K B^+ U^+)]     (V = U)
-//                         = -tr[X (B K A U^+ + U A^+ K B^+)]    (V = U^+),
-// so the link's component a gains Re[(i/16) tr((i s_a/2) G)] = -Re tr(s_a G) / 32.
+// The link derivative of f: each link lies on two plaquettes of each of the
+// three planes that contain its direction, and each plaquette enters the
+// leaves of its four corners; hr_clover_leaf.cuh sums the four corner
+// insertions around one staple per plaquette.
 //
 // Two flavours of clover fermions through the even-odd pseudofermion (Mhat =
 // A_ee - H_eo A_oo^-1 H_oe / 4): with X = (Mhat^+ Mhat)^-1 eta, Y = Mhat X,
@@ -577,8 +576,6 @@ hr_status hr_dirac_eo_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec pr
 // and S_det = -2 sum_{odd} log det A adds Lam_det = -2 A^-1 (odd).
 
 namespace {
-
-__constant__ int kPlane[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 
 // (s_l)_st, l = 0, 1, 2 for s_1, s_2, s_3
 __device__ __forceinline__ zc pauli(int l, int s, int t)
@@ -768,30 +765,9 @@ __global__ void k_clover_k_from_fields(KFieldArgs A)
     store_k(A.K, x, P);
 }
 
-// leaves of Q_mn(x): factor j of leaf l is U_{mu or nu}(x + a mu + b nu), daggered or not
-struct LeafFactor {
-    int nu_dir; // 0: mu, 1: nu
-    int a, b;
-    int dag;
-};
-__constant__ LeafFactor kLeaf[4][4] = {
-    {{0, 0, 0, 0}, {1, 1, 0, 0}, {0, 0, 1, 1}, {1, 0, 0, 1}},
-    {{1, 0, 0, 0}, {0, -1, 1, 1}, {1, -1, 0, 1}, {0, -1, 0, 0}},
-    {{0, -1, 0, 1}, {1, -1, -1, 1}, {0, -1, -1, 0}, {1, 0, -1, 0}},
-    {{1, 0, -1, 1}, {0, 0, -1, 0}, {1, 1, -1, 0}, {0, 0, 0, 1}},
-};
-
-__device__ CM<2> ident2()
-{
-    CM<2> I;
-    I.m[0][0] = {1.0, 0.0};
-    I.m[0][1] = {0.0, 0.0};
-    I.m[1][0] = {0.0, 0.0};
-    I.m[1][1] = {1.0, 0.0};
-    return I;
-}
-
-// F[rho][z][a] += scale * d/dw_a Re sum_y tr[C Lam], one thread per link (rho, z)
+// F[rho][z][a] += scale * d/dw_a Re sum_y tr[C Lam], one thread per link (rho, z):
+// the two plaquettes of each of the three planes that hold rho, each with its
+// four corner insertions around one staple (hr_clover_leaf.cuh)
 __global__ void __launch_bounds__(128) k_clover_leaf_force(Geom g, const double *can, const double *K, double scale,
                                                            double *F)
 {
@@ -806,52 +782,12 @@ __global__ void __launch_bounds__(128) k_clover_leaf_force(Geom g, const double 
         x[k] = (int)(r % g.d[k]);
         r /= g.d[k];
     }
-    const CM<2> U = link_mat<2>(can, V, rho, z);
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int pl = 0; pl < 6; ++pl) {
-        const int mu = kPlane[pl][0], nu = kPlane[pl][1];
-        if (rho != mu && rho != nu) continue;
-        const int sel = rho == mu ? 0 : 1;
-        for (int l = 0; l < 4; ++l)
-            for (int k = 0; k < 4; ++k) {
-                const LeafFactor fk = kLeaf[l][k];
-                if (fk.nu_dir != sel) continue;
-                // the leaf's base y = z - a_k mu - b_k nu; factor j sits at y + a_j mu + b_j nu
-                CM<2> Am = ident2(), Bm = ident2();
-                for (int j = 0; j < 4; ++j) {
-                    if (j == k) continue;
-                    const LeafFactor fj = kLeaf[l][j];
-                    const long long sj = nb(g, x, mu, fj.a - fk.a, nu, fj.b - fk.b);
-                    const CM<2> Uj = link_mat<2>(can, V, fj.nu_dir ? nu : mu, sj);
-                    if (j < k) Am = cmul(Am, false, Uj, fj.dag != 0);
-                    else Bm = cmul(Bm, false, Uj, fj.dag != 0);
-                }
-                const long long y = nb(g, x, mu, -fk.a, nu, -fk.b);
-                CM<2> Km;
-                const double *kp = K + (y * 6 + pl) * 8;
-                for (int d = 0; d < 2; ++d)
-                    for (int c = 0; c < 2; ++c) Km.m[d][c] = {kp[(d * 2 + c) * 2], kp[(d * 2 + c) * 2 + 1]};
-                CM<2> G1, G2;
-                if (!fk.dag) {
-                    // U B K A + A^+ K B^+ U^+
-                    G1 = cmul(cmul(U, false, Bm, false), false, cmul(Km, false, Am, false), false);
-                    G2 = cmul(cmul(Am, true, Km, false), false, cmul(U, false, Bm, false), true);
-                } else {
-                    // -(B K A U^+ + U A^+ K B^+)
-                    G1 = cmul(cmul(Bm, false, Km, false), false, cmul(Am, false, U, true), false);
-                    G2 = cmul(cmul(U, false, Am, true), false, cmul(Km, false, Bm, true), false);
-                }
-                const double sgn = fk.dag ? -1.0 : 1.0;
-                const zc G00 = zadd(G1.m[0][0], G2.m[0][0]), G01 = zadd(G1.m[0][1], G2.m[0][1]);
-                const zc G10 = zadd(G1.m[1][0], G2.m[1][0]), G11 = zadd(G1.m[1][1], G2.m[1][1]);
-                // -Re tr(s_a G) / 32
-                acc[0] -= sgn * (G10.re + G01.re) / 32.0;
-                acc[1] -= sgn * (G10.im - G01.im) / 32.0;
-                acc[2] -= sgn * (G00.re - G11.re) / 32.0;
-            }
-    }
+    LeafLattice L;
+    for (int k = 0; k < 4; ++k) L.d[k] = g.d[k];
+    double out[3];
+    leaf_force_link(L, can, K, rho, x, out);
     double *o = F + ((long long)rho * V + z) * 3;
-    for (int a = 0; a < 3; ++a) o[a] += scale * acc[a];
+    for (int a = 0; a < 3; ++a) o[a] += scale * out[a];
 }
 
 // block sums of sum_{odd sites} log det A (both blocks, Cholesky), one partial per block
