@@ -180,7 +180,8 @@ def hop(dims, L, psi, parity: int = -1, out=None, bc=None, theta=None) -> np.nda
     th = _theta(dims, theta)
     psi = _c128(psi)
     out = np.zeros_like(psi) if out is None else out
-    _check(_load().or_hop(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), int(parity), _ptr(psi), _ptr(out)), "hop")
+    _check(_load().or_hop(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), int(parity), _ptr(psi), _ptr(out)),
+           "hop")
     return out
 
 
@@ -191,7 +192,8 @@ def hop_sites(dims, L, psi, sites, bc=None, theta=None) -> np.ndarray:
     psi = _c128(psi)
     s = np.ascontiguousarray(sites, dtype=np.int64)
     out = np.zeros((s.size, 4, _nc(L)), dtype=np.complex128)
-    _check(_load().or_hop_sites(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), _ptr(s), s.size, _ptr(psi), _ptr(out)),
+    _check(_load().or_hop_sites(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), _ptr(s), s.size, _ptr(psi),
+                                _ptr(out)),
            "hop_sites")
     return out
 
@@ -202,7 +204,8 @@ def dirac(dims, L, m0: float, psi, bc=None, theta=None) -> np.ndarray:
     th = _theta(dims, theta)
     psi = _c128(psi)
     out = np.zeros_like(psi)
-    _check(_load().or_dirac(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "dirac")
+    _check(_load().or_dirac(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)),
+           "dirac")
     return out
 
 
@@ -223,7 +226,8 @@ def normal(dims, L, m0: float, psi, bc=None, theta=None) -> np.ndarray:
     th = _theta(dims, theta)
     psi = _c128(psi)
     out = np.zeros_like(psi)
-    _check(_load().or_normal(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)), "normal")
+    _check(_load().or_normal(_ptr(d), _bc(dims, bc), _tp(th), _nc(L), _ptr(L), float(m0), _ptr(psi), _ptr(out)),
+           "normal")
     return out
 
 

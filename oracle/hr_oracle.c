@@ -262,7 +262,8 @@ static void hop_site(const int *d, int bc, const double *th, int nc, const cplx 
 
 /* out(x) = (H psi)(x) for every x of the given parity (-1: every site).
  * Sites of the other parity in out are left untouched. */
-int or_hop(const int *d, int bc, const double *th, int nc, const double *Lr, int par, const double *psir, double *outr)
+int or_hop(const int *d, int bc, const double *th, int nc, const double *Lr, int par, const double *psir,
+           double *outr)
 {
     init_tables();
     if (check_lat(d, bc, th) || (nc != 2 && nc != 3)) return -1;
@@ -295,7 +296,8 @@ int or_hop_sites(const int *d, int bc, const double *th, int nc, const double *L
 }
 
 /* full operator: out = (4+m0) psi - 1/2 H psi */
-int or_dirac(const int *d, int bc, const double *th, int nc, const double *Lr, double m0, const double *psir, double *outr)
+int or_dirac(const int *d, int bc, const double *th, int nc, const double *Lr, double m0, const double *psir,
+             double *outr)
 {
     int rc = or_hop(d, bc, th, nc, Lr, -1, psir, outr);
     if (rc) return rc;
@@ -348,7 +350,8 @@ int or_schur(const int *d, int bc, const double *th, int nc, const double *Lr, d
 }
 
 /* out = Mhat^+ Mhat psi (even sites) */
-int or_normal(const int *d, int bc, const double *th, int nc, const double *Lr, double m0, const double *psir, double *outr)
+int or_normal(const int *d, int bc, const double *th, int nc, const double *Lr, double m0, const double *psir,
+              double *outr)
 {
     long n = volume(d) * 4 * nc;
     double *tmp = calloc(2 * n, sizeof(double));
@@ -413,7 +416,8 @@ int or_cg(const int *d, int bc, const double *th, int nc, const double *Lr, doub
  * Across the boundary the hop x -> x+mu carries its factor f (wrap_phase, step
  * +1) and the hop x+mu -> x its factor fb (step -1): the two terms become
  * f Q1 and fb Q2 (for antiperiodic directions both are -1). */
-int or_force(const int *d, int bc, const double *th, const double *Lr, const double *ar, const double *br, double *F)
+int or_force(const int *d, int bc, const double *th, const double *Lr, const double *ar, const double *br,
+             double *F)
 {
     init_tables();
     if (check_lat(d, bc, th)) return -1;
