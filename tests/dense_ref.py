@@ -179,11 +179,11 @@ def clover_site_dense(dims, q, nc, m0, csw, exponential=False) -> np.ndarray:
     return A
 
 
-def dirac_clover_dense(dims, q, nc, A, bc=0) -> np.ndarray:
+def dirac_clover_dense(dims, q, nc, A, bc=0, theta=None) -> np.ndarray:
     """Dense D = A - H/2 with the site matrices A on the diagonal blocks."""
     V = int(np.prod(dims))
     n = V * 4 * nc
-    D = -0.5 * hopping_dense(dims, q, nc, bc)
+    D = -0.5 * hopping_dense(dims, q, nc, bc, theta)
     for x in range(V):
         s = slice(x * 4 * nc, (x + 1) * 4 * nc)
         D[s, s] += A[x]

@@ -16,7 +16,9 @@ its boundary factor:
 * an independent dense build (tests/dense_ref.py), gamma5-hermiticity of the
   Schur operator, CG and the even-odd solve against dense solves;
 * the link gradient and the force against central finite differences through
-  the dense build.
+  the dense build;
+* the clover operators and the clover fermion force on twisted lattices against
+  dense builds and finite differences of dense-matrix actions.
 """
 
 import numpy as np
@@ -261,3 +263,69 @@ def test_bad_theta_is_rejected():
         oracle.hop(dims, L, psi, theta=[0.1, np.nan, 0, 0])
     with pytest.raises(ValueError):
         oracle.hop(dims, L, psi, theta=[0.1, 0.2])
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_twisted_clover_operators_against_dense(kind):
+    """The clover oracle's operators on a twisted lattice (the site term is
+    blind to the twist: it sits in closed loops) against a dense build."""
+    from oracle import clover as ocl
+
+    dims = (2, 4, 2, 4)
+    m0, csw, bc, theta = 0.1, 1.2, 1, np.array([0.6, -0.9, 1.4, 0.3])
+    q = synth.haar_links(dims, 371)
+    L = oracle.expand_links(dims, 2, q)
+    A = ocl.site_term(dims, L, m0, csw, kind)
+    Ad = dr.clover_site_dense(dims, q, 2, m0, csw, exponential=bool(kind))
+    assert np.abs(A - Ad).max() < 1e-13
+    D = dr.dirac_clover_dense(dims, q, 2, Ad, bc, theta)
+    psi = synth.gaussian_spinor(dims, 2, 372)
+    assert rel(ocl.dirac(dims, L, A, psi, bc=bc, theta=theta).reshape(-1), D @ psi.reshape(-1)) < 1e-14
+    Dee, Deo, Doe, Doo, e, o = dr.eo_blocks(dims, 2, D)
+    M = Dee - Deo @ np.linalg.solve(Doo, Doe)
+    psi[oracle.parity_mask(dims) == 1] = 0
+    got = ocl.schur(dims, L, A, psi, bc=bc, theta=theta).reshape(-1)
+    assert rel(got[e], M @ psi.reshape(-1)[e]) < 1e-13
+
+
+def exp_update(q, mu, x, w, eps):
+    """U_mu(x) -> exp(i eps w.s/2) U_mu(x)."""
+    from oracle import hmc
+
+    out = q.copy()
+    out[mu, x] = hmc.link_update(q[mu, x][None], w[None], eps)[0]
+    return out
+
+
+def test_twisted_clover_force_matches_finite_differences():
+    """The clover fermion force (hops, site term, det A_oo) on a twisted lattice
+    against finite differences of dense-matrix actions."""
+    from oracle import clover as ocl
+
+    dims = (2, 2, 2, 4)
+    V = int(np.prod(dims))
+    m0, csw, bc, theta = 0.1, 1.3, 1, np.array([0.8, 0.0, -1.1, 0.5])
+    q, _, _ = synth.ape_smear_to_plaquette(synth.haar_links(dims, 381), dims, 0.6)
+    eta = synth.gaussian_spinor(dims, 2, 382)
+    odd = oracle.parity_mask(dims) == 1
+    eta[odd] = 0
+
+    def S(qq):
+        A = dr.clover_site_dense(dims, qq, 2, m0, csw)
+        D = dr.dirac_clover_dense(dims, qq, 2, A, bc, theta)
+        Dee, Deo, Doe, Doo, e, o = dr.eo_blocks(dims, 2, D)
+        M = Dee - Deo @ np.linalg.solve(Doo, Doe)
+        y = eta.reshape(-1)[e]
+        S_det = -2.0 * sum(np.linalg.slogdet(A[k])[1] for k in np.where(odd)[0])
+        return np.vdot(y, np.linalg.solve(M.conj().T @ M, y)).real + S_det
+
+    ferm = ocl.CloverFermions(dims, m0, csw, eta, bc=bc, tol=1e-14, theta=theta)
+    S0 = S(q)
+    assert abs(ferm.action(q) - S0) <= 1e-10 * abs(S0)
+    F = ferm.force(q)
+    eps = 1e-5
+    for mu, x in _boundary_samples(dims, theta, 10):
+        w = RNG.normal(size=3)
+        w /= np.linalg.norm(w)
+        fd = (S(exp_update(q, mu, x, w, eps)) - S(exp_update(q, mu, x, w, -eps))) / (2 * eps)
+        assert abs(fd - F[mu, x] @ w) <= 1e-6 * max(1.0, abs(fd)), (mu, x, fd, F[mu, x] @ w)
