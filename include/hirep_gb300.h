@@ -323,7 +323,7 @@ hr_status hr_solve_full_clover(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const hr
                                hr_system system, const void *gauge, const void *clover, const void *b, void *x,
                                hr_solve_info *info, void *work, size_t work_bytes, hr_stream stream);
 
-/* ---- the clover term in the HMC (fundamental links, SW form) ----
+/* ---- the clover term in the HMC (fundamental links; SW and exponential forms) ----
  * The paper measures the clover operator (Sec. 2.2) and names the HMC as its
  * consumer; these calls give the molecular-dynamics force and action of the
  * term.  With the site term, two flavours weigh det(D^+ D) = det(A_oo)^2
