@@ -100,6 +100,27 @@ def test_solver_defaults_and_workspace():
     assert hr.hr_cg_workspace_bytes(d, hr.HR_FUND, o) == 0
 
 
+def test_hmc_and_clover_force_workspaces():
+    """Host-side sizes (no device needed): each HMC option adds its buffers."""
+    d = (8, 8, 8, 8)
+    V = 8 ** 4
+    half = hr.hr_spinor_packed_bytes(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, 1)
+    assert hr.hr_clover_force_workspace_bytes(d) == V * 48 * 8 + 5 * half
+    assert hr.hr_clover_force_workspace_bytes((8, 8, 8, 7)) == 0
+    prm = hr.hr_hmc_params_default(2.2, 0.1, True, 4, 1.0)
+    base = hr.hr_hmc_workspace_bytes(d, prm)
+    assert base > 0
+    prm.n_steps_gauge = 3                     # a second force buffer
+    two = hr.hr_hmc_workspace_bytes(d, prm)
+    assert two - base == 12 * V * 8
+    prm.clover, prm.c_sw = 1, 1.0             # the clover field and the force workspace
+    clov = hr.hr_hmc_workspace_bytes(d, prm)
+    cfield = hr.hr_clover_packed_bytes(d, hr.HR_FUND, hr.HR_F64)
+    assert clov - two >= cfield + hr.hr_clover_force_workspace_bytes(d)
+    prm.hasenbusch, prm.m0_hasenbusch = 1, 0.5  # a heavy clover field and the ratio term's fields
+    assert hr.hr_hmc_workspace_bytes(d, prm) - clov >= cfield + 4 * half
+
+
 def test_null_context_is_rejected():
     L = hr.lib()
     assert L.hr_last_error(None) == b"null context"
