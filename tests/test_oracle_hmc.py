@@ -244,3 +244,31 @@ def test_nested_trajectory_reversible_and_second_order(integrator):
     dh = [abs(hmc.trajectory(dims, q, p, 2.2, n, 0.5, integrator, ferm, n_steps_gauge=2)[2]["dH"])
           for n in (8, 16, 32)]
     assert 3.8 < dh[0] / dh[1] < 4.2 and 3.8 < dh[1] / dh[2] < 4.2, dh
+
+
+def test_oracle_chain_creutz_equality():
+    """<exp(-dH)> = 1 over an equilibrium chain of the oracle's own HMC (Wilson
+    fermions, eta = Mhat^+ xi drawn with the oracle's Schur operator): the
+    trajectory's area preservation and reversibility and the heat baths'
+    normalisation together (deterministic seed; 4 standard errors)."""
+    dims = (2, 2, 2, 4)
+    V = int(np.prod(dims))
+    beta, m0 = 2.0, 0.2
+    rng = np.random.default_rng(91)
+    q = smeared(dims, 92)
+    even = oracle.parity_mask(dims) == 0
+    w = []
+    for it in range(240):
+        p = rng.normal(size=(4, V, 3))
+        xi = (rng.normal(size=(V, 4, 2)) + 1j * rng.normal(size=(V, 4, 2))) / np.sqrt(2.0)
+        xi[~even] = 0
+        eta = oracle.schur(dims, oracle.expand_links(dims, 2, q), m0, xi, dagger=True, bc=1)
+        ferm = hmc.Fermions(dims, m0, eta, bc=1)
+        q1, _, info = hmc.trajectory(dims, q, p, beta, 2, 1.0, hmc.OMELYAN, ferm)   # std(dH) about 0.2
+        if it >= 40:
+            w.append(np.exp(-info["dH"]))
+        if rng.uniform() < np.exp(-info["dH"]):
+            q = q1
+    w = np.array(w)
+    err = w.std(ddof=1) / np.sqrt(len(w))
+    assert abs(w.mean() - 1.0) <= 4 * err + 1e-3, (w.mean(), err)
