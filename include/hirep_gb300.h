@@ -76,7 +76,10 @@ typedef enum {
 } hr_rep;
 
 typedef enum {
-    HR_F64 = 0, /* FP64 storage (IEEE binary64)                                          */
+    HR_F64 = 0, /* FP64 class: each real packed as an unevaluated pair of floats (hi + lo,
+                   48 significant bits, about 3.6e-15 relative) and computed with error-free
+                   float transformations; the canonical buffers stay IEEE binary64.  Full
+                   precision for magnitudes 2^-102 (2e-31) .. 2^120 (1.3e36): see hr_ctx_status */
     HR_F32 = 1, /* FP32 storage and arithmetic                                            */
     HR_F16 = 2  /* binary16 storage (spinors scaled by a per-site FP32 max-abs), FP32 arithmetic */
 } hr_prec;
@@ -135,6 +138,21 @@ hr_status hr_ctx_create(hr_ctx **ctx, int device);
 hr_status hr_ctx_destroy(hr_ctx *ctx);
 /* Message of the last failed call on this context ("" if none). Never NULL. */
 const char *hr_last_error(const hr_ctx *ctx);
+
+/* The value-range status of the fields packed with this context since the
+ * last check.  The packed layouts hold reals in the float exponent range (the
+ * FP64 class as pairs of floats), so hr_gauge_pack and hr_spinor_pack flag,
+ * on the device and without stopping, every canonical value that is NaN or
+ * Inf or exceeds 2^120 = 1.3e36 in magnitude (beyond that an operator's sums
+ * could overflow).  This call synchronises the stream, clears the flags and
+ * returns HR_ERR_NUMERIC (a NaN or Inf was packed), HR_ERR_UNSUPPORTED (a value
+ * above 2^120) or HR_OK.  The solvers (hr_cg_solve, hr_cg_solve_clover,
+ * hr_solve_full, hr_cg_solve_batch, hr_hmc_trajectory) make the same check
+ * before they start and return the same codes.  Small magnitudes are not
+ * flagged: a pair keeps 48 bits down to 2^-102 (its low float stays normal)
+ * and loses them gradually below, which matters only relative to the field's
+ * largest component (the solvers check that, see hr_cg_solve). */
+hr_status hr_ctx_status(hr_ctx *ctx, hr_stream stream);
 /* Library version string. */
 const char *hr_version(void);
 
@@ -152,7 +170,8 @@ size_t hr_gauge_packed_bytes(hr_lattice lat, hr_rep rep, hr_prec prec);
  * right-hand sides (parity = HR_EVEN/HR_ODD), or both halves (HR_FULL). */
 size_t hr_spinor_packed_bytes(hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity parity, int n_rhs);
 
-/* canonical gauge (device, double[4][V][4]) -> packed (device).  For HR_ADJ_MAT
+/* canonical gauge (device, double[4][V][4]) -> packed (device); values out of
+ * range are flagged (hr_ctx_status).  For HR_ADJ_MAT
  * the 3x3 adjoint matrices are built on the GPU from the quaternions.  The
  * boundary sign of lat.bc is folded in: HR_FUND stores -q on the boundary
  * slice; HR_ADJ stores the representative of +-q whose q0 has its sign bit
@@ -163,7 +182,8 @@ hr_status hr_gauge_pack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec,
                         const double *canonical, void *packed, hr_stream stream);
 
 /* canonical spinor(s) (device, double[n_rhs][V][4][nc][2]) -> packed sites of
- * `parity` (HR_FULL: both halves).  n_rhs > 1 gives the multi-RHS layout. */
+ * `parity` (HR_FULL: both halves).  n_rhs > 1 gives the multi-RHS layout.
+ * NaN, Inf and magnitudes above 2^120 are flagged (hr_ctx_status). */
 hr_status hr_spinor_pack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, hr_parity parity,
                          int n_rhs, const double *canonical, void *packed, hr_stream stream);
 /* packed -> canonical; writes only the sites of `parity` (all for HR_FULL). */
@@ -225,7 +245,14 @@ size_t hr_cg_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *o
  * of `rep`; b, x: packed HR_F64 even spinors (n_rhs of them).  Low-precision
  * gauge copies for the mixed solver are made inside `work`.  Synchronises the
  * stream before returning (it reads the residuals); info may be NULL.
- * Returns HR_ERR_NOT_CONVERGED if maxiter is reached (x = last iterate). */
+ * Every right-hand side is rescaled inside `work` by the power of two that
+ * brings its largest component into [0.5, 1) (exact: the iterates are the
+ * same numbers in other units), so the solve does not depend on the scale of
+ * b; x is returned in the caller's units.  Returns HR_ERR_NOT_CONVERGED if
+ * maxiter is reached (x = last iterate); HR_ERR_UNSUPPORTED if a right-hand
+ * side's largest component is nonzero but below 2^-100 (its pairs have lost
+ * low bits already) or a value packed since the last check exceeded 2^120,
+ * HR_ERR_NUMERIC if one was NaN or Inf (hr_ctx_status). */
 hr_status hr_cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep,
                       const hr_solver_opts *opts, const void *gauge, const void *b, void *x,
                       hr_solve_info *info, void *work, size_t work_bytes, hr_stream stream);
@@ -487,16 +514,58 @@ hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, doub
 /* link derivatives                                                         */
 /* ---------------------------------------------------------------------- */
 
-/* force[mu][x][a] += beta * d Re<a_f, H b_f> / d w_a  for the variation
- * U_mu(x) -> exp(i w.s/2) U_mu(x) (HMC fermion force, fundamental links).
- * a_f, b_f: full packed FP64 fundamental spinors; force: device double[4][V][3]. */
+/* The even-odd preconditioned operator is "used mainly in the HMC" (Sec. 2.1),
+ * whose molecular dynamics needs the derivative of fermion bilinears with
+ * respect to the links.  The paper writes no formula; these are the textbook
+ * ones for the operator above.  Variation: U_mu(x) -> exp(i w.s/2) U_mu(x),
+ * F_a = d/dw_a (the su(2) force), or the four quaternion components q_k of
+ * U = sum_k q_k E_k (E_0 = 1, E_k = i s_k).  Outputs are accumulated (+=):
+ * force double[4][V][3], grad double[4][V][4] (device, lexicographic sites).
+ * Fundamental links only (HR_ERR_UNSUPPORTED otherwise); lat.bc and lat.theta
+ * apply as in the operators. */
+
+/* Work bytes of hr_fermion_force / hr_fermion_link_grad (five packed FP64
+ * spinor halves); 0 for an invalid lattice. */
+size_t hr_fermion_force_workspace_bytes(hr_lattice lat);
+
+/* force += coeff * d/dw Re<L, Mhat^+ Mhat X> at fixed even fields X and L
+ * (packed HR_F64 even spinors; L = NULL means L = X), gauge: packed HR_F64
+ * fundamental links, m0 the Wilson mass of Mhat.  For the pseudofermion
+ * action S = Re<eta, (Mhat^+ Mhat)^-1 eta> with X = (Mhat^+ Mhat)^-1 eta (the
+ * solution of hr_cg_solve), dS/dw = -d/dw Re<X, Mhat^+ Mhat X>: call with
+ * L = NULL, coeff = -1.  Internally, with c = 1/(4(4+m0)) and
+ * H_eo^+ = g5 H_oe g5, Re<Y, dMhat Z> = -c dRe<(Y, H_eo^+ Y), H (Z, H_oe Z)>:
+ * the call forms Mhat X (and Mhat L), the odd halves by hops, and applies
+ * the hop derivative of hr_force once (L = X) or twice.  Asynchronous;
+ * work: hr_fermion_force_workspace_bytes, 16-byte aligned. */
+hr_status hr_fermion_force(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const void *gauge, const void *X,
+                           const void *L, double coeff, double *force, void *work, size_t work_bytes,
+                           hr_stream stream);
+
+/* As hr_fermion_force, with the derivative taken with respect to the
+ * quaternion components: grad += coeff * d/dq Re<L, Mhat^+ Mhat X>.  The
+ * gradient of x = (Mhat^+ Mhat)^-1 eta against a cotangent g is
+ * -d/dq Re<lambda, Mhat^+ Mhat x> with lambda = (Mhat^+ Mhat)^-1 g: X = x,
+ * L = lambda, coeff = -1. */
+hr_status hr_fermion_link_grad(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const void *gauge,
+                               const void *X, const void *L, double coeff, double *grad, void *work,
+                               size_t work_bytes, hr_stream stream);
+
+/* The hop derivative itself (the building block of the calls above; Sec. 2.1
+ * defines the hopping term H whose links it varies):
+ * force[mu][x][a] += beta * d Re<a_f, H b_f> / d w_a.  The two terms of H that
+ * hold U_mu(x) are a(x)^+ (1-g_mu) U b(x+mu) and a(x+mu)^+ (1+g_mu) U^+ b(x);
+ * with M1 = sum_s b(x+mu)_s [((1-g_mu) a(x))_s]^+ and
+ * M2 = sum_s b(x)_s [((1+g_mu) a(x+mu))_s]^+, F_a = Re tr[(i s_a/2)(U M1 - M2 U^+)].
+ * a_f, b_f: full packed FP64 fundamental spinors; gauge: packed HR_F64
+ * fundamental links (the boundary signs ride on them). */
 hr_status hr_force(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *a_full,
                    const void *b_full, double beta, double *force, hr_stream stream);
 
-/* grad[mu][x][k] += beta * d Re<a_f, H b_f> / d q_k for the quaternion
- * components q_k of U_mu(x) (U = sum_k q_k E_k, E_0 = 1, E_k = i s_k), with
+/* The hop derivative with respect to the quaternion components (same terms as
+ * hr_force): grad[mu][x][k] += beta * (Re tr[E_k M1] + Re tr[E_k^+ M2]), with
  * the boundary sign of lat.bc on the links of the last slice of each
- * antiperiodic direction.  grad: device double[4][V][4]. */
+ * antiperiodic direction (the call takes no gauge field: H is linear in U). */
 hr_status hr_link_grad(hr_ctx *ctx, hr_lattice lat, const void *a_full, const void *b_full,
                        double beta, double *grad, hr_stream stream);
 
@@ -516,7 +585,10 @@ typedef struct {
                           instruction (fundamental: the two colours; adjoint FP64: re and
                           im); 11: as 10, operands staged by cp.async one direction ahead
                           (fundamental, adjoint FP64 with quaternion links); 12, 13: 10,
-                          11 for fundamental FP64 capped at 96 registers */
+                          11 for fundamental FP64 capped at 96 registers; 14: fundamental
+                          binary16 with the spin projection in half2 arithmetic (only the
+                          projected half spinor is widened to FP32, the neighbour's scale
+                          rides on the accumulating FMAs); 15: as 14, 64 registers */
     int block;         /* threads per block                                               */
     double best_ms;    /* time of one hop launch with the chosen shape (median of 4)      */
     double default_ms; /* the same for the shape in use before tuning                     */
@@ -550,6 +622,11 @@ hr_status hr_tune_lookup(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, 
  * Synchronises the stream. */
 hr_status hr_norm2(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *v, double *result,
                    hr_stream stream);
+/* *re + i *im (host) = <a, b> = sum conj(a) b over the packed FP64 fields of
+ * one parity (n_rhs = 1), accumulated in binary64 and summed in a fixed order
+ * (deterministic).  Synchronises the stream. */
+hr_status hr_dot(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *a, const void *b, double *re, double *im,
+                 hr_stream stream);
 /* y = a*x + y on packed FP64 fields of one parity. */
 hr_status hr_axpy(hr_ctx *ctx, hr_lattice lat, hr_rep rep, double a, const void *x, void *y,
                   hr_stream stream);

@@ -11,12 +11,11 @@ for y = A z with A linear, grad_z = A^+ grad_y.
   grad_q[mu, x, k] = -1/2 d Re<g, H psi> / d q_k (``hr_link_grad``).
 * :class:`EoSolve` -- x = (Mhat^+ Mhat)^-1 eta on even sites (eta and x are
   full-lattice tensors whose odd sites are zero).  backward: one extra solve
-  lambda = A^-1 grad_x (A is Hermitian), grad_eta = lambda, and with
-  c = 1/(4(4+m0)) and H_eo^+ = g5 H_oe g5,
-  grad_q = c [ dRe<(Mhat x, H_eo^+ Mhat x), H (lambda, H_oe lambda)>
-             + dRe<(Mhat lambda, H_eo^+ Mhat lambda), H (x, H_oe x)> ] / dq
-  (even components first, odd second).
-* :func:`fermion_force` -- the su(2) force of S = Re<eta, (Mhat^+ Mhat)^-1 eta>.
+  lambda = A^-1 grad_x (A is Hermitian), grad_eta = lambda, and
+  grad_q = -d Re<lambda, A x> / dq at fixed x, lambda (``hr_fermion_link_grad``).
+* :func:`fermion_force` -- the su(2) force of S = Re<eta, (Mhat^+ Mhat)^-1 eta>,
+  -d Re<x, A x> / dw at x = A^-1 eta (``hr_fermion_force``), and S = Re<eta, x>
+  (``hr_dot``).
 
 These are the differentiable solve and the fermion force of the HMC that
 consumes the even-odd preconditioned operator (arXiv:2411.18511, Sec. 2.1).
@@ -94,27 +93,6 @@ class _Lattice:
     def gamma5(self, p_half):
         hr.hr_gamma5(self.ctx, self.dims, hr.HR_FUND, p_half)
 
-    def schur(self, m0, src_even, dst_even):
-        work = fields.empty_bytes(hr.hr_dirac_workspace_bytes(self.dims, hr.HR_FUND, hr.HR_F64, hr.HR_OP_SCHUR),
-                                  self.dev)
-        hr.hr_dirac_eo(self.ctx, self.dims, m0, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, hr.HR_OP_SCHUR, 1,
-                       self.gauge, src_even, dst_even, work)
-
-    def h_oe_into(self, src_even, dst_odd, dagger_eo: bool = False):
-        """dst_o = H_oe src_e, or H_eo^+ src_e = g5 H_oe g5 src_e when dagger_eo."""
-        src = src_even
-        if dagger_eo:
-            src = src_even.clone()
-            self.gamma5(src)
-        hop = self.even()
-        # HR_OP_HOP computes -1/2 H_oe; dst = -2 * hop, dst starting from zero
-        hr.hr_dirac_eo(self.ctx, self.dims, 0.0, hr.HR_FUND, hr.HR_F64, hr.HR_ODD, hr.HR_OP_HOP, 1,
-                       self.gauge, src, hop)
-        dst_odd.zero_()
-        hr.hr_axpy(self.ctx, self.dims, hr.HR_FUND, -2.0, hop, dst_odd)
-        if dagger_eo:
-            self.gamma5(dst_odd)
-
     def solve(self, m0, b_even, tol, maxiter):
         opts = hr.hr_solver_default_opts()
         opts.tol = tol
@@ -126,14 +104,8 @@ class _Lattice:
             raise hr.HrError(rc, f"solve did not reach tol={tol}: residual {info.true_rel_residual:.3e}")
         return x, info
 
-    def force_pair(self, m0, v_even):
-        """Packed full fields a = (Mhat v, H_eo^+ Mhat v) and b = (v, H_oe v)."""
-        a, b = self.full(), self.full()
-        self.schur(m0, v_even, self.ev(a))
-        self.h_oe_into(self.ev(a), self.od(a), dagger_eo=True)
-        self.ev(b).copy_(v_even)
-        self.h_oe_into(v_even, self.od(b))
-        return a, b
+    def force_work(self):
+        return fields.empty_bytes(hr.hr_fermion_force_workspace_bytes(self.dims), self.dev)
 
 
 class DiracApply(torch.autograd.Function):
@@ -191,12 +163,9 @@ class EoSolve(torch.autograd.Function):
         grad_eta = lat.unpack_even(lam) if ctx.needs_input_grad[1] else None
         grad_q = None
         if ctx.needs_input_grad[0]:
-            c = 1.0 / (4.0 * (4.0 + ctx.m0))
             grad_q = torch.zeros_like(q)
-            ax, bx = lat.force_pair(ctx.m0, ctx.x)
-            al, bl = lat.force_pair(ctx.m0, lam)
-            hr.hr_link_grad(lat.ctx, ctx.dims, ax, bl, c, grad_q)  # (Mhat x, ..), (lambda, ..)
-            hr.hr_link_grad(lat.ctx, ctx.dims, al, bx, c, grad_q)  # (Mhat lambda, ..), (x, ..)
+            hr.hr_fermion_link_grad(lat.ctx, ctx.dims, ctx.m0, hr.HR_FUND, lat.gauge, ctx.x, lam, -1.0, grad_q,
+                                    lat.force_work())
         return grad_q, grad_eta, None, None, None, None
 
 
@@ -207,8 +176,7 @@ def fermion_force(q: torch.Tensor, eta: torch.Tensor, dims, m0, tol=1e-12):
     lat = _Lattice(dims, q)
     e = lat.even(eta)
     x, _ = lat.solve(m0, e, tol, 20000)
-    a, b = lat.force_pair(m0, x)
     F = torch.zeros((4, q.shape[1], 3), dtype=torch.float64, device=q.device)
-    hr.hr_force(lat.ctx, dims, lat.gauge, a, b, 2.0 / (4.0 * (4.0 + m0)), F)
-    S = torch.sum(eta.conj() * lat.unpack_even(x)).real
-    return F, S
+    hr.hr_fermion_force(lat.ctx, dims, m0, hr.HR_FUND, lat.gauge, x, None, -1.0, F, lat.force_work())
+    S = hr.hr_dot(lat.ctx, dims, hr.HR_FUND, e, x).real
+    return F, torch.tensor(S, dtype=torch.float64, device=q.device)

@@ -422,6 +422,8 @@ hr_status hr_cg_solve_batch(hr_ctx *ctx, int n_lat, const hr_lattice *lats, doub
     if (!work || work_bytes < P.bytes)
         return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", P.bytes, work_bytes);
     if (hr_status sw = check_buffers(ctx, {work})) return sw;
+    // values packed out of range since the last check (synchronises the stream)
+    if (hr_status sp = consume_pack_status(ctx, (cudaStream_t)stream)) return sp;
     if (infos) std::memset(infos, 0, sizeof(hr_solve_info) * n_lat);
     cudaStream_t s = (cudaStream_t)stream;
     char *w = (char *)work;

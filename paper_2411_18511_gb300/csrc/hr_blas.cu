@@ -11,6 +11,8 @@
 // Per-RHS scalars (alpha, beta, ...) are read from the context's device scalar
 // block, so a solver iteration needs no host round trip.  Reductions are FP64,
 // deterministic (warp shuffle, block, then last-block sum in block order).
+#include <vector>
+
 #include "hr_host.h"
 
 using namespace hr;
@@ -208,6 +210,108 @@ __global__ void __launch_bounds__(kBS) k_gamma5(Geom g, void *v)
     }
 }
 
+// per-RHS largest |component| (the hi parts of the double-float pairs) of a
+// packed FP64 field, folded into scal[S_BMAX][r] as float bits: non-negative
+// floats order like their bit patterns, so an unsigned atomicMax is a float max
+template <int NC>
+__global__ void __launch_bounds__(kBS) k_maxabs(Geom g, const void *v, double *scal)
+{
+    const int nv = g.vh << g.lrhs;
+    float m = 0.f;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<dd> a[4][NC];
+        load_spinor<NC, kF64>(v, g.nblk_s, j, a);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) m = fmaxf(m, fmaxf(fabsf(a[s][c].re.h), fabsf(a[s][c].im.h)));
+    }
+    // lanes of one RHS differ in their bits >= log2(nrhs)
+    for (int off = 16; off >= g.nrhs; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) < g.nrhs)
+        atomicMax(reinterpret_cast<unsigned *>(scal + S_BMAX * kMaxRhsSlots) + thread_rhs(g), __float_as_uint(m));
+}
+
+// scal[S_SCALE][r] = 2^-e with max = f 2^e, f in [0.5, 1); a zero field keeps 1.
+// A nonzero maximum below 2^-100 raises F_RANGE: the pairs have already lost
+// low bits (the low float of such a value is subnormal).
+__global__ void k_scale_setup(double *scal, int nrhs)
+{
+    const int r = threadIdx.x;
+    if (r >= nrhs) return;
+    const float m = __uint_as_float(reinterpret_cast<const unsigned *>(scal + S_BMAX * kMaxRhsSlots)[r]);
+    double f = 1.0;
+    if (m > 0.f) {
+        int e;
+        frexpf(m, &e);
+        f = ldexp(1.0, -e);
+        if (m < 0x1p-100f) scal[S_FLAGS * kMaxRhsSlots + F_RANGE] = 1.0;
+    }
+    scal[S_SCALE * kMaxRhsSlots + r] = f;
+}
+
+// dst = f_r src (inverse: src / f_r), f_r a power of two: exact on both parts of a pair
+template <int NC>
+__global__ void __launch_bounds__(kBS) k_scale(Geom g, const void *src, void *dst, const double *scal, int inverse)
+{
+    const int nv = g.vh << g.lrhs;
+    const int r = thread_rhs(g);
+    const double f = scal[S_SCALE * kMaxRhsSlots + r];
+    const float k = (float)(inverse ? 1.0 / f : f);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<dd> a[4][NC];
+        load_spinor<NC, kF64>(src, g.nblk_s, j, a);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                a[s][c].re = dd(a[s][c].re.h * k, a[s][c].re.l * k);
+                a[s][c].im = dd(a[s][c].im.h * k, a[s][c].im.l * k);
+            }
+        store_spinor<NC, kF64>(dst, g.nblk_s, j, a);
+    }
+}
+
+// <a, b> = sum conj(a) b over the packed FP64 fields of one parity, in FP64
+// (each pair widened to a double: a utility, not a solver kernel); one
+// (re, im) partial per block, summed on the host in block order
+constexpr int kDotBlocks = 1024;
+template <int NC>
+__global__ void __launch_bounds__(kBS) k_dot(Geom g, const void *a, const void *b, double *partial)
+{
+    const int nv = g.vh << g.lrhs;
+    double re = 0.0, im = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
+        cpx<dd> u[4][NC], v[4][NC];
+        load_spinor<NC, kF64>(a, g.nblk_s, j, u);
+        load_spinor<NC, kF64>(b, g.nblk_s, j, v);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const double ur = dd_to_double(u[s][c].re), ui = dd_to_double(u[s][c].im);
+                const double vr = dd_to_double(v[s][c].re), vi = dd_to_double(v[s][c].im);
+                re = fma(ur, vr, fma(ui, vi, re));
+                im = fma(ur, vi, fma(-ui, vr, im));
+            }
+    }
+    __shared__ double sh[2][kBS];
+    sh[0][threadIdx.x] = re;
+    sh[1][threadIdx.x] = im;
+    __syncthreads();
+    for (int w = kBS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sh[0][0];
+        partial[2 * blockIdx.x + 1] = sh[1][0];
+    }
+}
+
 inline int grid_cap(hr_ctx *ctx, const Geom &g)
 {
     long long nv = (long long)g.vh << g.lrhs;
@@ -321,6 +425,23 @@ hr_status blas_gamma5(hr_ctx *ctx, const Geom &g, int rep, void *v, cudaStream_t
     return check_launch(ctx, "gamma5");
 }
 
+hr_status blas_source_scale(hr_ctx *ctx, const Geom &g, int rep, const void *v, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    HR_DISPATCH_NC(rep, (k_maxabs<NC><<<grid, kBS, 0, s>>>(g, v, ctx->d_scal)));
+    hr_status st = check_launch(ctx, "max |component|");
+    if (st) return st;
+    k_scale_setup<<<1, 32, 0, s>>>(ctx->d_scal, g.nrhs);
+    return check_launch(ctx, "source scale");
+}
+
+hr_status blas_scale(hr_ctx *ctx, const Geom &g, int rep, const void *src, void *dst, int inverse, cudaStream_t s)
+{
+    int grid = grid_cap(ctx, g);
+    HR_DISPATCH_NC(rep, (k_scale<NC><<<grid, kBS, 0, s>>>(g, src, dst, ctx->d_scal, inverse)));
+    return check_launch(ctx, "scale");
+}
+
 hr_status blas_zero(hr_ctx *ctx, const Geom &g, int rep, int prec, void *v, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(v, 0, spinor_half_bytes(g, rep, prec), s);
@@ -357,6 +478,35 @@ hr_status hr_norm2(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *v, doubl
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "norm2 readback: %s", cudaGetErrorString(e));
     *result = ctx->h_scal[0];
+    return HR_OK;
+}
+
+hr_status hr_dot(hr_ctx *ctx, hr_lattice lat, hr_rep rep, const void *a, const void *b, double *re, double *im,
+                 hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
+    if (!re || !im) return set_error(ctx, HR_ERR_INVALID_ARG, "null result pointer");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    st = check_buffers(ctx, {a, b});
+    if (st) return st;
+    Geom g = make_geom(lat, 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    HR_DISPATCH_NC(rep, (k_dot<NC><<<kDotBlocks, kBS, 0, s>>>(g, a, b, ctx->d_partials)));
+    st = check_launch(ctx, "dot");
+    if (st) return st;
+    std::vector<double> h(2 * kDotBlocks);
+    cudaError_t e = cudaMemcpyAsync(h.data(), ctx->d_partials, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(ctx, HR_ERR_CUDA, "dot readback: %s", cudaGetErrorString(e));
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < kDotBlocks; ++k) {
+        sr += h[2 * k];
+        si += h[2 * k + 1];
+    }
+    *re = sr;
+    *im = si;
     return HR_OK;
 }
 

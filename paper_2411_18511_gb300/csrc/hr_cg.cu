@@ -121,8 +121,9 @@ struct Solver {
     const void *b;
     void *x;
     cudaStream_t s;
+    const void *b_user; // the caller's source; b is its scaled copy bs64 once start() ran
     // FP64 buffers
-    void *r64, *p64, *q64, *u64, *t64;
+    void *r64, *p64, *q64, *u64, *t64, *bs64;
     // low precision buffers
     void *gauge_lo, *r_lo, *p_lo, *q_lo, *u_lo, *t_lo, *x_lo;
     void *clov_lo; // FP32 copy of the clover field (mixed solvers)
@@ -140,6 +141,8 @@ struct Solver {
             off += (n + 255) & ~(size_t)255;
             return p;
         };
+        void *bs = take(h64);
+        if (sv) sv->bs64 = bs;
         if (o.inner_prec == HR_F64) {
             void *r = take(h64), *p = take(h64), *q = take(h64), *u = take(h64), *t = take(h64);
             if (sv) {
@@ -233,9 +236,36 @@ struct Solver {
                              mixed() ? r_lo : nullptr, s);
     }
 
+    // Rescale the source by a power of two per right-hand side (exact) so that
+    // its largest component lies in [0.5, 1): the vectors the recurrence
+    // iterates then stay far from both ends of the float exponent range that
+    // the double-float pairs keep, whatever the scale of the caller's b.  x
+    // is solved for in the same units (a guess is scaled along) and scaled
+    // back by finish().
+    hr_status scale_source()
+    {
+        hr_status st = blas_source_scale(ctx, g, rep, b_user, s);
+        if (st) return st;
+        st = read_scalars(ctx, S_FLAGS, 1, s);
+        if (st) return st;
+        if (ctx->h_scal[F_RANGE] != 0.0)
+            return set_error(ctx, HR_ERR_UNSUPPORTED,
+                             "the source's largest component is below 2^-100 = 7.9e-31: its FP64 pairs have lost low "
+                             "bits (scale b up)");
+        st = blas_scale(ctx, g, rep, b_user, bs64, 0, s);
+        if (!st && o.x0_is_guess) st = blas_scale(ctx, g, rep, x, x, 0, s);
+        b = bs64;
+        return st;
+    }
+
+    // x back in the caller's units
+    hr_status finish() { return blas_scale(ctx, g, rep, x, x, 1, s); }
+
     hr_status start()
     {
         hr_status st = init_scalars(ctx, g.nrhs, o.tol, o.reliable_delta, o.maxiter, s);
+        if (st) return st;
+        st = scale_source();
         if (st) return st;
         if (mixed()) {
             st = gauge_convert(ctx, make_geom_gauge(), rep, o.inner_prec, gauge, gauge_lo, s);
@@ -416,6 +446,10 @@ hr_status cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_
     if (!work || work_bytes < need)
         return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, work_bytes);
 
+    // values packed out of range since the last check (this synchronises the stream)
+    st = consume_pack_status(ctx, (cudaStream_t)stream);
+    if (st) return st;
+
     Solver sv{};
     sv.ctx = ctx;
     sv.g = make_geom(lat, opts->n_rhs);
@@ -424,6 +458,7 @@ hr_status cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_
     sv.o = *opts;
     sv.gauge = gauge;
     sv.clov64 = clover;
+    sv.b_user = b;
     sv.b = b;
     sv.x = x;
     sv.s = (cudaStream_t)stream;
@@ -547,6 +582,8 @@ hr_status cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_
         if (!st) st = sv.restart_direction();
         if (st) return st;
     }
+    st = sv.finish();
+    if (st) return st;
     e = cudaEventRecord(ctx->ev1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev1);
     float ms = 0.f;

@@ -120,7 +120,7 @@ __device__ __forceinline__ bool boundary_link(const Geom &g, int mu, const int (
 // of +-q with the sign bit of q0 clear, then set it on boundary links; the
 // fundamental stores -q on boundary links.
 template <int PREC>
-__global__ void k_gauge_pack_quat(Geom g, int canon, const double *__restrict__ can, void *packed)
+__global__ void k_gauge_pack_quat(Geom g, int canon, const double *__restrict__ can, void *packed, unsigned *status)
 {
     long long V = 2LL * g.vh;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,6 +136,8 @@ __global__ void k_gauge_pack_quat(Geom g, int canon, const double *__restrict__ 
     int p = (x0 + x1 + x2 + x3) & 1;
     int i = (int)(x >> 1);
     double a[4] = {can[t * 4 + 0], can[t * 4 + 1], can[t * 4 + 2], can[t * 4 + 3]};
+    const unsigned bad = pack_range_flags(a[0]) | pack_range_flags(a[1]) | pack_range_flags(a[2]) | pack_range_flags(a[3]);
+    if (bad) atomicOr(status, bad);
     const int xc[4] = {x0, x1, x2, x3};
     const bool neg = (canon && sign_bit(a[0])) != boundary_link(g, mu, xc);
     if (neg)
@@ -144,7 +146,7 @@ __global__ void k_gauge_pack_quat(Geom g, int canon, const double *__restrict__ 
 }
 
 template <int PREC>
-__global__ void k_gauge_pack_mat(Geom g, const double *__restrict__ can, void *packed)
+__global__ void k_gauge_pack_mat(Geom g, const double *__restrict__ can, void *packed, unsigned *status)
 {
     long long V = 2LL * g.vh;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -160,6 +162,8 @@ __global__ void k_gauge_pack_mat(Geom g, const double *__restrict__ can, void *p
     int p = (x0 + x1 + x2 + x3) & 1;
     int i = (int)(x >> 1);
     double a[4] = {can[t * 4 + 0], can[t * 4 + 1], can[t * 4 + 2], can[t * 4 + 3]};
+    const unsigned bad = pack_range_flags(a[0]) | pack_range_flags(a[1]) | pack_range_flags(a[2]) | pack_range_flags(a[3]);
+    if (bad) atomicOr(status, bad);
     if (sign_bit(a[0]))
         for (int k = 0; k < 4; ++k) a[k] = -a[k]; // R(q) = R(-q); quat_to_adj reads the sign bit
     double R[3][3];
@@ -174,7 +178,7 @@ __global__ void k_gauge_pack_mat(Geom g, const double *__restrict__ can, void *p
 // canonical double[nrhs][V][4][NC][2] -> packed virtual sites of parity p.
 // One thread per (rhs, even-odd site).
 template <int NC, int PREC>
-__global__ void k_spinor_pack(Geom g, int p, const double *__restrict__ can, void *packed)
+__global__ void k_spinor_pack(Geom g, int p, const double *__restrict__ can, void *packed, unsigned *status)
 {
     using T = double; // the canonical side is FP64; the layout code converts
     long long n = (long long)g.vh << g.lrhs;
@@ -186,10 +190,15 @@ __global__ void k_spinor_pack(Geom g, int p, const double *__restrict__ can, voi
     long long V = 2LL * g.vh;
     const double *src = can + ((long long)r * V + lex) * (8 * NC);
     cpx<T> s[4][NC];
+    unsigned bad = 0;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) s[a][c] = {(T)src[(a * NC + c) * 2], (T)src[(a * NC + c) * 2 + 1]};
+        for (int c = 0; c < NC; ++c) {
+            s[a][c] = {(T)src[(a * NC + c) * 2], (T)src[(a * NC + c) * 2 + 1]};
+            bad |= pack_range_flags(s[a][c].re) | pack_range_flags(s[a][c].im);
+        }
+    if (bad) atomicOr(status, bad);
     store_spinor<NC, PREC>(packed, g.nblk_s, (i << g.lrhs) + r, s);
 }
 
@@ -224,7 +233,7 @@ hr_status launch_spinor_pack(hr_ctx *ctx, const Geom &g, int p, const double *ca
     int bs = 256;
     int grid = (int)((n + bs - 1) / bs);
     if (unpack) k_spinor_unpack<NC, PREC><<<grid, bs, 0, s>>>(g, p, packed, (double *)can);
-    else k_spinor_pack<NC, PREC><<<grid, bs, 0, s>>>(g, p, can, packed);
+    else k_spinor_pack<NC, PREC><<<grid, bs, 0, s>>>(g, p, can, packed, ctx->d_counters + C_PACK);
     return check_launch(ctx, unpack ? "spinor unpack" : "spinor pack");
 }
 
@@ -299,6 +308,24 @@ __global__ void k_gauge_convert(Geom g, const void *src, void *dst)
 } // namespace
 
 namespace hr {
+hr_status consume_pack_status(hr_ctx *ctx, cudaStream_t s)
+{
+    unsigned flags = 0;
+    cudaError_t e = cudaMemcpyAsync(&flags, ctx->d_counters + C_PACK, sizeof flags, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && flags) e = cudaMemsetAsync(ctx->d_counters + C_PACK, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, HR_ERR_CUDA, "pack status readback: %s", cudaGetErrorString(e));
+    }
+    if (flags & kPackNonFinite) return set_error(ctx, HR_ERR_NUMERIC, "a packed field held a NaN or Inf");
+    if (flags & kPackAboveRange)
+        return set_error(ctx, HR_ERR_UNSUPPORTED,
+                         "a packed value exceeded 2^120 = 1.3e36 in magnitude (the pair-of-floats FP64 layout "
+                         "keeps the float exponent range): scale the field down");
+    return HR_OK;
+}
+
 hr_status gauge_convert(hr_ctx *ctx, const Geom &g, int rep, int pdst, const void *src, void *dst, cudaStream_t s)
 {
     long long n = 8LL * g.nblk_g * 32;
@@ -383,6 +410,12 @@ hr_status hr_ctx_destroy(hr_ctx *ctx)
     return HR_OK;
 }
 
+hr_status hr_ctx_status(hr_ctx *ctx, hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    return consume_pack_status(ctx, (cudaStream_t)stream);
+}
+
 const char *hr_last_error(const hr_ctx *ctx)
 {
     if (!ctx) return "null context";
@@ -419,15 +452,16 @@ hr_status hr_gauge_pack(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec, c
     long long n = 8LL * g.vh;
     int bs = 256;
     int grid = (int)((n + bs - 1) / bs);
+    unsigned *status = ctx->d_counters + C_PACK;
     if (rep == HR_ADJ_MAT) {
-        if (prec == kF64) k_gauge_pack_mat<kF64><<<grid, bs, 0, s>>>(g, canonical, packed);
-        else if (prec == kF32) k_gauge_pack_mat<kF32><<<grid, bs, 0, s>>>(g, canonical, packed);
-        else k_gauge_pack_mat<kF16><<<grid, bs, 0, s>>>(g, canonical, packed);
+        if (prec == kF64) k_gauge_pack_mat<kF64><<<grid, bs, 0, s>>>(g, canonical, packed, status);
+        else if (prec == kF32) k_gauge_pack_mat<kF32><<<grid, bs, 0, s>>>(g, canonical, packed, status);
+        else k_gauge_pack_mat<kF16><<<grid, bs, 0, s>>>(g, canonical, packed, status);
     } else {
         const int canon = rep == HR_ADJ ? 1 : 0;
-        if (prec == kF64) k_gauge_pack_quat<kF64><<<grid, bs, 0, s>>>(g, canon, canonical, packed);
-        else if (prec == kF32) k_gauge_pack_quat<kF32><<<grid, bs, 0, s>>>(g, canon, canonical, packed);
-        else k_gauge_pack_quat<kF16><<<grid, bs, 0, s>>>(g, canon, canonical, packed);
+        if (prec == kF64) k_gauge_pack_quat<kF64><<<grid, bs, 0, s>>>(g, canon, canonical, packed, status);
+        else if (prec == kF32) k_gauge_pack_quat<kF32><<<grid, bs, 0, s>>>(g, canon, canonical, packed, status);
+        else k_gauge_pack_quat<kF16><<<grid, bs, 0, s>>>(g, canon, canonical, packed, status);
     }
     return check_launch(ctx, "gauge pack");
 }

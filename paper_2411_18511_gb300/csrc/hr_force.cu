@@ -176,9 +176,98 @@ hr_status launch(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *af,
     return check_launch(ctx, mode ? "link grad" : "force");
 }
 
+// Link derivative of B(X, L) = Re<L, Mhat^+ Mhat X> at fixed even fields X, L
+// (Sec. 2.1: the even-odd operator in the HMC).  With Mhat = (4+m0) - c H_eo H_oe,
+// c = 1 / (4 (4+m0)), and H_eo^+ = g5 H_oe g5,
+//   dB = Re<Mhat L, dMhat X> + Re<Mhat X, dMhat L>,
+//   Re<Y, dMhat Z> = -c dRe<(Y, H_eo^+ Y), H (Z, H_oe Z)>,
+// so each of the two terms is one application of the hop derivative (mode 0:
+// su(2) force, 1: quaternion gradient) to full fields a = (Mhat Y, H_eo^+ Mhat Y)
+// and b = (Z, H_oe Z) assembled in the work buffer: L = X needs one (doubled).
+struct FermionWork {
+    char *a, *b, *t; // two full fields and an odd temporary
+    static size_t bytes(const Geom &g)
+    {
+        const size_t half = spinor_half_bytes(g, HR_FUND, kF64);
+        return 5 * half;
+    }
+};
+
+hr_status fermion_deriv(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const void *gauge, const void *X,
+                        const void *L, double coeff, double *out, int mode, void *work, size_t work_bytes,
+                        hr_stream stream)
+{
+    if (!ctx) return HR_ERR_INVALID_ARG;
+    if (!valid_rep(rep)) return set_error(ctx, HR_ERR_INVALID_ARG, "bad rep");
+    if (rep != HR_FUND)
+        return set_error(ctx, HR_ERR_UNSUPPORTED, "the fermion force is implemented for fundamental links only");
+    hr_status st = validate_lattice(ctx, lat, 1);
+    if (st) return st;
+    st = check_buffers(ctx, {gauge, X, work}, {out}, {L});
+    if (st) return st;
+    if (!(4.0 + m0 != 0.0) || !std::isfinite(m0)) return set_error(ctx, HR_ERR_INVALID_ARG, "4 + m0 must be nonzero");
+    if (!std::isfinite(coeff)) return set_error(ctx, HR_ERR_INVALID_ARG, "coeff is not finite");
+    const Geom g = make_geom(lat, 1);
+    const size_t half = spinor_half_bytes(g, HR_FUND, kF64);
+    const size_t need = FermionWork::bytes(g);
+    if (work_bytes < need)
+        return set_error(ctx, HR_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, work_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    FermionWork w{(char *)work, (char *)work + 2 * half, (char *)work + 4 * half};
+    const double c = 1.0 / (4.0 * (4.0 + m0));
+    // dst_odd = [g5] H_oe [g5] src_even
+    auto hop_oe = [&](const void *src, void *dst, int g5) {
+        HopLaunch H{};
+        H.p = 1;
+        H.gauge = gauge;
+        H.in = src;
+        H.out = dst;
+        H.beta = 1.0;
+        H.g5_in = g5;
+        H.g5_out = g5;
+        return launch_hop(ctx, g, HR_FUND, kF64, H, s);
+    };
+    // out += coeff * (-c) * k * dRe<(Mhat Y, H_eo^+ Mhat Y), H (Z, H_oe Z)>
+    auto term = [&](const void *Y, const void *Z, double k) {
+        hr_status t = apply_eo_op(ctx, g, m0, HR_FUND, kF64, HR_OP_SCHUR, gauge, Y, w.a, w.t, nullptr, kFinNone,
+                                  nullptr, nullptr, s);
+        if (!t) t = hop_oe(w.a, w.a + half, 1);
+        if (!t) {
+            cudaError_t e = cudaMemcpyAsync(w.b, Z, half, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) t = set_error(ctx, HR_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+        }
+        if (!t) t = hop_oe(Z, w.b + half, 0);
+        if (!t) t = launch(ctx, lat, gauge, w.a, w.b, -c * k * coeff, out, mode, stream);
+        return t;
+    };
+    if (!L || L == X) return term(X, X, 2.0);
+    st = term(L, X, 1.0);
+    if (!st) st = term(X, L, 1.0);
+    return st;
+}
+
 } // namespace
 
 extern "C" {
+
+size_t hr_fermion_force_workspace_bytes(hr_lattice lat)
+{
+    return 5 * hr_spinor_packed_bytes(lat, HR_FUND, HR_F64, HR_EVEN, 1);
+}
+
+hr_status hr_fermion_force(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const void *gauge, const void *X,
+                           const void *L, double coeff, double *force, void *work, size_t work_bytes,
+                           hr_stream stream)
+{
+    return fermion_deriv(ctx, lat, m0, rep, gauge, X, L, coeff, force, 0, work, work_bytes, stream);
+}
+
+hr_status hr_fermion_link_grad(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const void *gauge, const void *X,
+                               const void *L, double coeff, double *grad, void *work, size_t work_bytes,
+                               hr_stream stream)
+{
+    return fermion_deriv(ctx, lat, m0, rep, gauge, X, L, coeff, grad, 1, work, work_bytes, stream);
+}
 
 hr_status hr_force(hr_ctx *ctx, hr_lattice lat, const void *gauge, const void *a_full, const void *b_full,
                    double beta, double *force, hr_stream stream)

@@ -12,7 +12,7 @@
 //
 // This file holds the plain unrolled kernels (variants 0 and 7), the dispatch
 // over all variants (the other families are in hr_hop_staged.cu, hr_hop_loop.cu,
-// hr_hop_tile.cu and hr_hop_x2.cu; hr_hop_fam.h lists them; lattices with
+// hr_hop_tile.cu, hr_hop_x2.cu and hr_hop_half.cu; hr_hop_fam.h lists them; lattices with
 // twisted boundaries take the kernel of hr_hop_twist.cu), the operators built
 // from hops and their C ABI.  The autotuner (hr_tune.cu) picks variant and
 // block size per configuration.
@@ -151,6 +151,8 @@ hr_status dispatch(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs 
     case kVarPairedStaged:
     case kVarPairedR96:
     case kVarPairedStagedR96: done = launch_hop_paired(ctx, g, rep, prec, a, c, grid, s, st); break;
+    case kVarHalf:
+    case kVarHalfR64: done = launch_hop_half(ctx, g, rep, prec, a, c, grid, s, st); break;
     default: break;
     }
     // the plain kernels: variants 0 and 7, and any variant without a kernel here
@@ -234,6 +236,8 @@ bool hop_variant_available(int rep, int prec, int variant)
     if (variant == kVarPaired) return rep == HR_FUND || prec == HR_F64;
     if (variant == kVarPairedStaged) return rep == HR_FUND || (rep == HR_ADJ && prec == HR_F64);
     if (variant == kVarPairedR96 || variant == kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
+    // the half2-projection kernels: fundamental binary16 only
+    if (variant == kVarHalf || variant == kVarHalfR64) return rep == HR_FUND && prec == HR_F16;
     // the 96-register caps spill heavily with three colours: fundamental only
     if (variant == kVarSimpleR96) return rep == HR_FUND;
     if (variant == kVarTileR96) return rep == HR_FUND && prec != HR_F16;

@@ -1,0 +1,167 @@
+// hr_hop_half.cu -- the binary16 fundamental hop with the spin projection in
+// half2 arithmetic (variants 14 and 15).
+//
+// The FP16 hop moves 136 bytes per output site (the neighbour spinors as
+// binary16 with one FP32 scale per site, binary16 quaternion links), so at
+// the HBM copy rate it has about 800 instruction issues per site to spend,
+// and the FP32-arithmetic kernels spend more: they widen all 16 stored
+// halves of every neighbour to floats before projecting.  Here the
+// projection h_t = s_t + i^c s_pi of (1 -/+ g_mu) runs on the stored halves
+// themselves -- a packed word holds one part (re or im) of both colours, so a
+// half-spinor is four HADD2 -- and only the 8 projected halves are widened.
+// The neighbour's scale rides on the rebuild instead of the link: every
+// accumulation acc (+)= i^k sc r is one FMA with +-sc as its multiplier.
+//
+// Precision: the half2 addition rounds the projected components to binary16
+// (a relative 2^-11 of the neighbour site's largest component), the same
+// size as the storage rounding of the components it adds; the colour product
+// and the accumulation run in FP32.  The result agrees with the FP32-
+// arithmetic kernels to the storage precision, not bit for bit.
+//
+// Variant 14: registers as the compiler likes; 15: capped at 64 registers.
+#include "hr_hop_fam.h"
+#include "hr_hop_x2.cuh"
+
+using namespace hr;
+
+namespace {
+
+// h = s + i^C y on a packed (colour 0, colour 1) word pair (re, im)
+template <int C>
+__device__ __forceinline__ void h2_project(__half2 sre, __half2 sim, __half2 yre, __half2 yim, __half2 &hre,
+                                           __half2 &him)
+{
+    if constexpr (C == 0) {
+        hre = __hadd2(sre, yre);
+        him = __hadd2(sim, yim);
+    } else if constexpr (C == 1) {
+        hre = __hsub2(sre, yim);
+        him = __hadd2(sim, yre);
+    } else if constexpr (C == 2) {
+        hre = __hsub2(sre, yre);
+        him = __hsub2(sim, yim);
+    } else {
+        hre = __hadd2(sre, yim);
+        him = __hsub2(sim, yre);
+    }
+}
+
+// acc (+)= i^C sc z
+template <int C, bool FIRST>
+__device__ __forceinline__ void acc_scaled(cpx<float> &acc, const cpx<float> &z, float sc)
+{
+    if constexpr (FIRST) {
+        if constexpr (C == 0) acc = {sc * z.re, sc * z.im};
+        else if constexpr (C == 1) acc = {-sc * z.im, sc * z.re};
+        else if constexpr (C == 2) acc = {-sc * z.re, -sc * z.im};
+        else acc = {sc * z.im, -sc * z.re};
+    } else {
+        if constexpr (C == 0) acc = {__fmaf_rn(sc, z.re, acc.re), __fmaf_rn(sc, z.im, acc.im)};
+        else if constexpr (C == 1) acc = {__fmaf_rn(-sc, z.im, acc.re), __fmaf_rn(sc, z.re, acc.im)};
+        else if constexpr (C == 2) acc = {__fmaf_rn(-sc, z.re, acc.re), __fmaf_rn(-sc, z.im, acc.im)};
+        else acc = {__fmaf_rn(sc, z.im, acc.re), __fmaf_rn(-sc, z.re, acc.im)};
+    }
+}
+
+__device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<const __half2 *>(&u); }
+
+// One direction: acc (+)= (1 -/+ g_mu) U psi(neighbour) (FWD: U_mu(x), else
+// U_mu(x - mu)^+).  NEG: the input's upper spins are negated (g5 in); as in the
+// paired kernels the sign moves from the projection to the rebuild.
+template <int MU, bool FWD, bool FIRST, bool NEG>
+__device__ __forceinline__ void h16_term(const HopArgs &a, const float *nrm, int site_link, int link_par, int jn,
+                                         cpx<float> (&acc)[4][2])
+{
+    using D = X2Dir<MU, FWD>;
+    constexpr int F = NEG ? 2 : 0;
+    const uint4 *sp = (const uint4 *)a.in;
+    const uint4 w0 = __ldg(sp + vec_index(jn, 0, 2));
+    const uint4 w1 = __ldg(sp + vec_index(jn, 1, 2));
+    const float sc = __ldg(nrm + jn);
+    // spin t: word 2t = (c0.re, c1.re), word 2t+1 = (c0.im, c1.im)
+    const uint32_t u[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    __half2 h0re, h0im, h1re, h1im;
+    h2_project<(D::c0 + F) & 3>(as_h2(u[0]), as_h2(u[1]), as_h2(u[2 * D::pi0]), as_h2(u[2 * D::pi0 + 1]), h0re, h0im);
+    h2_project<(D::c1 + F) & 3>(as_h2(u[2]), as_h2(u[3]), as_h2(u[2 * D::pi1]), as_h2(u[2 * D::pi1 + 1]), h1re, h1im);
+    cpx<float> h[2][2];
+    {
+        const float2 r0 = __half22float2(h0re), i0 = __half22float2(h0im);
+        const float2 r1 = __half22float2(h1re), i1 = __half22float2(h1im);
+        h[0][0] = {r0.x, i0.x};
+        h[0][1] = {r0.y, i0.y};
+        h[1][0] = {r1.x, i1.x};
+        h[1][1] = {r1.y, i1.y};
+    }
+    float q[4];
+    load_quat<kF16>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+    cpx<float> r[2][2];
+    su2_mul<!FWD>(q, h[0], r[0]);
+    su2_mul<!FWD>(q, h[1], r[1]);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        acc_scaled<F, FIRST>(acc[0][c], r[0][c], sc);
+        acc_scaled<F, FIRST>(acc[1][c], r[1][c], sc);
+        acc_scaled<(D::d0 + F) & 3, FIRST>(acc[2][c], r[D::rho0][c], sc);
+        acc_scaled<(D::d1 + F) & 3, FIRST>(acc[3][c], r[D::rho1][c], sc);
+    }
+}
+
+template <int MU, bool FIRST, bool NEG>
+__device__ __forceinline__ void h16_dir(const HopArgs &a, const float *nrm, int i, int rr, const SiteNb &nb,
+                                        cpx<float> (&acc)[4][2])
+{
+    const int l = a.g.lrhs;
+    h16_term<MU, true, FIRST, NEG>(a, nrm, i, a.p, (nb.fwd[MU] << l) + rr, acc);
+    h16_term<MU, false, false, NEG>(a, nrm, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, acc);
+}
+
+template <int G5IN>
+__device__ __forceinline__ void h16_body(const HopArgs &a)
+{
+    constexpr bool NEG = G5IN != 0;
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const float *nrm = (const float *)((const char *)a.in + SpinorLayout<2, kF16>::data_bytes(g.nblk_s));
+    const float be = a.beta.h;
+    const float bu = a.g5_out ? -be : be;
+    const float al = a.alpha.h;
+    SqAcc<float> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        cpx<float> acc[4][2];
+        h16_dir<0, true, NEG>(a, nrm, i, rr, nb, acc);
+        h16_dir<1, false, NEG>(a, nrm, i, rr, nb, acc);
+        h16_dir<2, false, NEG>(a, nrm, i, rr, nb, acc);
+        h16_dir<3, false, NEG>(a, nrm, i, rr, nb, acc);
+        hop_epilogue<kF16>(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+template <int G5IN> __global__ void __launch_bounds__(256) k_hop_h16(HopArgs a) { h16_body<G5IN>(a); }
+template <int G5IN> __global__ void __maxnreg__(64) k_hop_h16_r64(HopArgs a) { h16_body<G5IN>(a); }
+
+} // namespace
+
+namespace hr {
+
+bool launch_hop_half(hr_ctx *ctx, const Geom &, int rep, int prec, const HopArgs &a, HopChoice c, int grid,
+                     cudaStream_t s, hr_status &st)
+{
+    if (rep != HR_FUND || prec != kF16) return false;
+    const bool g5 = a.g5_in != 0;
+    if (c.variant == kVarHalfR64) (g5 ? k_hop_h16_r64<1> : k_hop_h16_r64<0>)<<<grid, c.block, 0, s>>>(a);
+    else (g5 ? k_hop_h16<1> : k_hop_h16<0>)<<<grid, c.block, 0, s>>>(a);
+    st = check_launch(ctx, "binary16 hop kernel (half2 projection)");
+    return true;
+}
+
+} // namespace hr

@@ -28,7 +28,7 @@ struct HopChoice {
     int variant; // kernel variant, 0 .. kNumHopVariants-1 (hr_hop.cu)
     int block;   // threads per block
 };
-constexpr int kNumHopVariants = 14;
+constexpr int kNumHopVariants = 16;
 } // namespace hr
 
 struct hr_ctx {
@@ -90,7 +90,10 @@ inline int grid_for(long long n, int block, int cap)
 }
 
 // counters used by the reducing kernels (each reduction site has its own)
-enum Counter { C_HOP = 0, C_XR = 1, C_RES = 2, C_NORM = 3, C_DOT = 4, C_MISC = 5, C_BATCH = 16, C_STATUS = 63 };
+// (C_PACK: the pack status word, kPack* flags of the values packed since the
+// last check, read and cleared by consume_pack_status)
+enum Counter { C_HOP = 0, C_XR = 1, C_RES = 2, C_NORM = 3, C_DOT = 4, C_MISC = 5, C_BATCH = 16, C_PACK = 62,
+               C_STATUS = 63 };
 
 // clover site term in a hop epilogue (hr_clover.cuh): none, A(x) on the aux
 // term (out = alpha A aux + beta acc), or A(x) on the result (out = A (alpha aux + beta acc))
@@ -169,5 +172,15 @@ hr_status blas_axpy(hr_ctx *ctx, const Geom &g, int rep, double a, const void *x
 hr_status blas_gamma5(hr_ctx *ctx, const Geom &g, int rep, void *v, cudaStream_t s);
 hr_status blas_zero(hr_ctx *ctx, const Geom &g, int rep, int prec, void *v, cudaStream_t s);
 hr_status blas_copy(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *src, void *dst, cudaStream_t s);
+// per-RHS max |component| of a packed FP64 field -> scal[S_BMAX] (float bits; the slot must start at zero),
+// then scal[S_SCALE] = the power of two that maps it into [0.5, 1) (1 for a zero field) and the F_RANGE
+// flag when a nonzero maximum lies below 2^-100
+hr_status blas_source_scale(hr_ctx *ctx, const Geom &g, int rep, const void *v, cudaStream_t s);
+// dst = scal[S_SCALE] src per RHS (inverse: src / scale) on packed FP64 fields (dst may be src)
+hr_status blas_scale(hr_ctx *ctx, const Geom &g, int rep, const void *src, void *dst, int inverse, cudaStream_t s);
+
+// the pack status word (kPack* flags) since the last call, synchronising the
+// stream; cleared.  HR_ERR_NUMERIC / HR_ERR_UNSUPPORTED with a message if set.
+hr_status consume_pack_status(hr_ctx *ctx, cudaStream_t s);
 
 } // namespace hr

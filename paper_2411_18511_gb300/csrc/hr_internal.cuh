@@ -290,6 +290,22 @@ template <> struct SqAcc<dd> {
     __device__ double get() const { return dd_to_double(s); }
 };
 
+// ---------------------------------------------------------------- value range
+// The FP64 layouts hold each real as a pair of floats, so they keep the float
+// exponent range: a value v keeps its 48 significant bits while its low part
+// is a normal float (|v| >= 2^-102), and an operator's sums stay finite while
+// the inputs stay well below the float maximum 2^128.  The pack kernels accept
+// canonical values up to 2^120 in magnitude (room for the growth of a few
+// operator applications) and flag larger or non-finite ones in the context's
+// pack status word; the solvers rescale their source by a power of two, which
+// is exact, so that the vectors they iterate are of order one.
+constexpr unsigned kPackAboveRange = 2u, kPackNonFinite = 4u;
+__device__ __forceinline__ unsigned pack_range_flags(double v)
+{
+    if (!isfinite(v)) return kPackNonFinite;
+    return fabs(v) > 0x1p120 ? kPackAboveRange : 0u;
+}
+
 // ---------------------------------------------------------------- layouts
 
 template <int PREC> struct PrecTraits;
@@ -972,9 +988,12 @@ enum ScalSlot {
                    // [4] reliable updates, [5] device-loop passes, [6] device error (a
                    // bulk copy that did not land in time)
     S_DELTA2 = 11, // [0] reliable-update threshold delta^2, [1] tol^2, [2] maxiter (<= 0: none)
-    S_NSLOTS = 12
+    S_SCALE = 12,  // per-RHS power of two that brings the source's largest component into [0.5, 1)
+    S_BMAX = 13,   // per-RHS largest |component| of the source, as the bits of a float (32 unsigned)
+    S_NSLOTS = 14
 };
-constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4, F_BODY = 5, F_DEVERR = 6;
+constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4, F_BODY = 5, F_DEVERR = 6,
+              F_RANGE = 7;
 
 enum FinishMode {
     kFinNone = 0,

@@ -50,6 +50,7 @@ EXPORTED = [
     "hr_solve_full_clover_workspace_bytes", "hr_solve_full_clover", "hr_gauge_force", "hr_gauge_action",
     "hr_link_update", "hr_mom_update", "hr_kinetic_energy", "hr_hmc_workspace_bytes", "hr_hmc_trajectory",
     "hr_clover_force_workspace_bytes", "hr_clover_insertion_force", "hr_clover_fermion_force", "hr_clover_logdet",
+    "hr_ctx_status", "hr_dot", "hr_fermion_force_workspace_bytes", "hr_fermion_force", "hr_fermion_link_grad",
 ]
 
 
@@ -138,6 +139,7 @@ def lib():
                 "hr_ctx_create": ([ctypes.POINTER(P), I], I),
                 "hr_ctx_destroy": ([P], I),
                 "hr_last_error": ([P], ctypes.c_char_p),
+                "hr_ctx_status": ([P, P], I),
                 "hr_version": ([], ctypes.c_char_p),
                 "hr_kappa_to_m0": ([D], D),
                 "hr_m0_to_kappa": ([D], D),
@@ -155,6 +157,10 @@ def lib():
                                  ctypes.POINTER(hr_solve_info), P, S, P], I),
                 "hr_force": ([P, LAT, P, P, P, D, P, P], I),
                 "hr_link_grad": ([P, LAT, P, P, D, P, P], I),
+                "hr_fermion_force_workspace_bytes": ([LAT], S),
+                "hr_fermion_force": ([P, LAT, D, I, P, P, P, D, P, P, S, P], I),
+                "hr_fermion_link_grad": ([P, LAT, D, I, P, P, P, D, P, P, S, P], I),
+                "hr_dot": ([P, LAT, I, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P], I),
                 "hr_norm2": ([P, LAT, I, P, ctypes.POINTER(D), P], I),
                 "hr_axpy": ([P, LAT, I, D, P, P, P], I),
                 "hr_gamma5": ([P, LAT, I, P, P], I),
@@ -289,6 +295,13 @@ class Context:
 
 
 # ------------------------------------------------------------------ C entry points
+
+def hr_ctx_status(ctx: Context, stream=None):
+    """Range status of the fields packed since the last check (synchronises the
+    stream); raises :class:`HrError` (HR_ERR_NUMERIC / HR_ERR_UNSUPPORTED) if a
+    packed value was non-finite or above 2^120 in magnitude."""
+    ctx.check(lib().hr_ctx_status(ctx.handle, _stream(stream)))
+
 
 def hr_version() -> str:
     return lib().hr_version().decode()
@@ -601,6 +614,34 @@ def hr_link_grad(ctx: Context, dims, a_full, b_full, beta, grad, stream=None):
     _need(grad, 4 * _vol(dims) * 4 * 8, "grad")
     return ctx.check(lib().hr_link_grad(ctx.handle, lattice(dims), _ptr(a_full), _ptr(b_full),
                                         float(beta), _ptr(grad), _stream(stream)))
+
+
+def hr_fermion_force_workspace_bytes(dims) -> int:
+    return int(lib().hr_fermion_force_workspace_bytes(lattice(dims)))
+
+
+def hr_fermion_force(ctx: Context, dims, m0, rep, gauge, X, L, coeff, force, work, stream=None):
+    """force += coeff d/dw Re<L, Mhat^+ Mhat X> (L = None: L = X)."""
+    _need(force, 4 * _vol(dims) * 3 * 8, "force")
+    return ctx.check(lib().hr_fermion_force(ctx.handle, lattice(dims), float(m0), rep, _ptr(gauge), _ptr(X),
+                                            _ptr(L), float(coeff), _ptr(force), _ptr(work), _nbytes(work),
+                                            _stream(stream)))
+
+
+def hr_fermion_link_grad(ctx: Context, dims, m0, rep, gauge, X, L, coeff, grad, work, stream=None):
+    """grad += coeff d/dq Re<L, Mhat^+ Mhat X> (L = None: L = X)."""
+    _need(grad, 4 * _vol(dims) * 4 * 8, "grad")
+    return ctx.check(lib().hr_fermion_link_grad(ctx.handle, lattice(dims), float(m0), rep, _ptr(gauge), _ptr(X),
+                                                _ptr(L), float(coeff), _ptr(grad), _ptr(work), _nbytes(work),
+                                                _stream(stream)))
+
+
+def hr_dot(ctx: Context, dims, rep, a, b, stream=None) -> complex:
+    """<a, b> = sum conj(a) b over packed FP64 fields of one parity."""
+    re, im = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    ctx.check(lib().hr_dot(ctx.handle, lattice(dims), rep, _ptr(a), _ptr(b), ctypes.byref(re), ctypes.byref(im),
+                           _stream(stream)))
+    return complex(re.value, im.value)
 
 
 def hr_norm2(ctx: Context, dims, rep, v, stream=None) -> float:

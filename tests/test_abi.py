@@ -93,7 +93,8 @@ def test_solver_defaults_and_workspace():
     assert o.reliable_delta == 0.1 and o.n_rhs == 1 and o.x0_is_guess == 0
     d = (8, 8, 8, 8)
     w64 = hr.hr_cg_workspace_bytes(d, hr.HR_FUND, o)
-    assert w64 == 5 * hr.hr_spinor_packed_bytes(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, 1)
+    # r, p, q and two operator temporaries, and the rescaled copy of b
+    assert w64 == 6 * hr.hr_spinor_packed_bytes(d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, 1)
     o.inner_prec = hr.HR_F16
     assert hr.hr_cg_workspace_bytes(d, hr.HR_FUND, o) > 0
     o.n_rhs = 3
