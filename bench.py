@@ -61,25 +61,31 @@ HOP_VARIANT_NAMES = ["unrolled", "unrolled cp.async staged", "generic loop", "ge
                      "binary16, half2 projection", "binary16, half2 projection, 64 registers"]
 
 
-def roofline(pname, vh, bytes_site, launch_ms, achieved_gbs, peak_gbs, peak_kind, traffic, kernel):
-    """The dominant kernel's roofline.  FP32/FP16 hops are bound by HBM; the
-    double-float FP64 hop needs more FP32-pipe operations per site than the
-    FP32 pipes deliver in the time HBM needs for its bytes, so it is ALU bound."""
-    hbm = {"achieved": round(achieved_gbs, 2), "peak": peak_gbs, "unit": "GB/s",
-           "frac": round(achieved_gbs / peak_gbs, 4), "peak_kind": f"{peak_kind} HBM copy (burst)"}
-    base = {"traffic": traffic, "kernel": kernel, "bytes_per_launch": vh * bytes_site,
-            "avg_launch_ms": round(launch_ms, 5)}
-    if pname != "f64":
-        return {"bound": "hbm", **hbm, **base}
-    sites_per_s = vh / (launch_ms * 1e-3)
-    gops = sites_per_s * DF_OPS_PER_SITE_FUND / 1e9
-    alu_time_ms = vh * DF_OPS_PER_SITE_FUND / (FP32_PEAK_GOPS * 1e9) * 1e3
-    hbm_time_ms = vh * bytes_site / (peak_gbs * 1e9) * 1e3
-    return {"bound": "alu", "achieved": round(gops, 1), "peak": round(FP32_PEAK_GOPS, 1),
-            "unit": "Gop/s (FP32 pipe)", "frac": round(gops / FP32_PEAK_GOPS, 4),
-            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
-            "ops_per_site": DF_OPS_PER_SITE_FUND, "alu_bound_ms": round(alu_time_ms, 5),
-            "hbm_bound_ms": round(hbm_time_ms, 5), "hbm": hbm, **base}
+def roofline(pname, vh, bytes_site, launch_ms, achieved_gbs, peak_gbs, peak_kind, traffic, kernel, fma=None):
+    """The dominant kernel's roofline against HBM: compulsory bytes per launch
+    over the launch time, against the measured copy peak.  For the FP64 class
+    an "alu" view sits beside it: the double-float hop needs 4096 FP32-pipe
+    lane operations per site (the implementation's count, not the method's
+    624 flops), against the FP32 FMA rate measured on this GPU (fma: the
+    library's calibration, scalar and packed lane ops per second)."""
+    out = {"bound": "hbm", "achieved": round(achieved_gbs, 2), "peak": peak_gbs, "unit": "GB/s",
+           "frac": round(achieved_gbs / peak_gbs, 4), "peak_kind": f"{peak_kind} HBM copy (burst), of measured",
+           "traffic": traffic, "kernel": kernel, "bytes_per_launch": vh * bytes_site,
+           "avg_launch_ms": round(launch_ms, 5)}
+    if pname == "f64":
+        sites_per_s = vh / (launch_ms * 1e-3)
+        gops = sites_per_s * DF_OPS_PER_SITE_FUND / 1e9
+        alu = {"achieved": round(gops, 1), "unit": "Gop/s (FP32 lane ops)", "ops_per_site": DF_OPS_PER_SITE_FUND,
+               "ops_note": "the double-float implementation's FP32-pipe operations per site (the method: 624 flops)",
+               "nominal_peak": round(FP32_PEAK_GOPS, 1), "nominal_kind": "152 SMs x 128 FP32 lanes x 2.07 GHz",
+               "frac_of_nominal": round(gops / FP32_PEAK_GOPS, 4)}
+        if fma:
+            peak = max(fma) / 1e9
+            alu.update({"peak": round(peak, 1), "peak_kind": "measured FP32 FMA rate (hr_fp32_fma_rate, best of "
+                        "scalar / packed, operand-reuse best case)", "frac": round(gops / peak, 4),
+                        "measured_scalar": round(fma[0] / 1e9, 1), "measured_paired": round(fma[1] / 1e9, 1)})
+        out["alu"] = alu
+    return out
 
 
 def parse_args():
@@ -96,6 +102,9 @@ def parse_args():
                     help="L of the L^4 lattice (48 is the benchmark workload; smaller for profiling)")
     ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64",
                     help="hop precision of the timed step (f64 is the benchmark workload)")
+    ap.add_argument("--rep", choices=["fund", "adj", "adjmat"], default="fund",
+                    help="representation of the timed step (fund is the benchmark workload; adj: quaternion "
+                         "links, adjoint matrices rebuilt in registers; adjmat: stored 3x3 links)")
     return ap.parse_args()
 
 
@@ -152,7 +161,7 @@ def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_18511_gb300", "csrc")
     for f in ("hr_internal.cuh", "hr_clover.cuh", "hr_host.h", "hr_hop_dev.cuh", "hr_hop_fam.h", "hr_hop_x2.cuh",
-              "hr_hop.cu", "hr_hop_staged.cu", "hr_hop_loop.cu", "hr_hop_tile.cu", "hr_hop_x2.cu"):
+              "hr_hop.cu", "hr_hop_staged.cu", "hr_hop_loop.cu", "hr_hop_tile.cu", "hr_hop_x2.cu", "hr_hop_half.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -275,9 +284,11 @@ def run_ours(args):
     V = int(np.prod(dims))
     Vh = V // 2
     pname = args.prec
-    rep, prec = hr.HR_FUND, {"f64": hr.HR_F64, "f32": hr.HR_F32, "f16": hr.HR_F16}[pname]
+    rname = args.rep
+    rep = {"fund": hr.HR_FUND, "adj": hr.HR_ADJ, "adjmat": hr.HR_ADJ_MAT}[rname]
+    prec = {"f64": hr.HR_F64, "f32": hr.HR_F32, "f16": hr.HR_F16}[pname]
     q = synth.haar_links(dims, GAUGE_SEED)
-    psi = synth.gaussian_spinor(dims, 2, SPINOR_SEED)
+    psi = synth.gaussian_spinor(dims, 2, SPINOR_SEED) if rname == "fund" else synth.gaussian_spinor(dims, 3, 2004)
     gauge = fields.pack_gauge(ctx, dims, rep, prec, fields.gauge_to_device(q))
     src = fields.pack_spinor(ctx, dims, rep, prec, hr.HR_FULL, fields.spinor_to_device(psi))
     dst = fields.empty_spinor(dims, rep, prec, hr.HR_FULL)
@@ -324,12 +335,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms_step = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    fma = hr.hr_fp32_fma_rate(ctx) if pname == "f64" else None  # the FP32 pipe's measured rate (untimed)
+    hr.hr_ctx_status(ctx)  # every packed value was in range
     variant, block = hr.hr_tune_lookup(ctx, dims, rep, prec)
     kname = HOP_KERNELS[variant] if 0 <= variant < len(HOP_KERNELS) else str(variant)
     if pname != "f64" and kname in ("k_hop_x2", "k_hop_x2s"):
         kname = kname.replace("x2", "f2")  # the FP32-arithmetic paired kernels
-    kernel = f"{kname}<fund,{pname}> x{block}"
-    bytes_site = hop_bytes_per_site("fund", pname)
+    kernel = f"{kname}<{rname},{pname}> x{block}"
+    bytes_site = hop_bytes_per_site("fund" if rname == "fund" else "adj", pname)
+    if rname == "adjmat":  # stored 3x3 real links instead of quaternions
+        bytes_site += 8 * ({"f64": 72, "f32": 36, "f16": 18}[pname] - {"f64": 32, "f32": 16, "f16": 8}[pname])
     bytes_step = 2 * Vh * bytes_site
     value = replica_value(world, bytes_step, ms_step) / 1e9
     launch_ms = ms_step / 2.0  # the step is exactly two launches of the hop kernel
@@ -337,15 +352,16 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and rname == "fund":
         e2e = run_e2e(args, ctx, torch, hr, dims, rep, prec, psi, src, dst, step, stream,
                       max_over_ranks, world, bytes_step)
-    extras = {}
+    extras, sols = {}, None
     if not args.no_extras and rank == 0:
-        extras = run_extras(ctx, torch, hr, fields, synth, q, psi)
+        extras, sols = run_extras(ctx, torch, hr, fields, synth, q, psi)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(q, psi, dims)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and rname == "fund":
+        cpu = cpu_baseline(q, psi, dims, sols)
+        attach_oracle_checks(extras, cpu)
 
     gauge_mb = hr.hr_gauge_packed_bytes(dims, rep, prec) / 1e6
     result = {
@@ -362,21 +378,26 @@ def run_ours(args):
         "dtype": {"f64": "df64", "f32": "f32", "f16": "f16"}[pname],
         "data": "synthetic (Haar-random SU(2) links, Gaussian complex source, Philox seeds 1003/2003)",
         "config": {
-            "workload": f"even-odd Wilson-Dirac hop pair D_eo+D_oe, {L4}^4 SU(2) fundamental, {pname.upper()}",
-            "lattice": list(dims), "rep": "fund", "prec": pname,
+            "workload": (f"even-odd Wilson-Dirac hop pair D_eo+D_oe, {L4}^4 SU(2) "
+                         f"{ {'fund': 'fundamental', 'adj': 'adjoint', 'adjmat': 'adjoint (3x3 links)'}[rname]}, "
+                         f"{pname.upper()}"),
+            "lattice": list(dims), "rep": rname, "prec": pname,
             "arithmetic": ("double-float: each real an unevaluated pair of fp32 (hi + lo), TwoSum/"
                            "TwoProduct on the FP32 pipes, ~2^-48 relative" if pname == "f64" else pname),
             "launch": tuned,
             "bytes_per_site": bytes_site,
             "byte_convention": "compulsory (1 spinor in + 1 out + 8 quaternion links)",
-            "neighbour_counted_gbs": round(value * neighbour_bytes_per_site("fund", pname) / bytes_site, 2),
-            "gflops": round(value * HOP_FLOPS["fund"] / bytes_site, 1),
+            "neighbour_counted_gbs": round(value * (neighbour_bytes_per_site("fund" if rname == "fund" else "adj", pname)
+                                                    + bytes_site - hop_bytes_per_site(
+                                                        "fund" if rname == "fund" else "adj", pname)) / bytes_site, 2),
+            "gflops": round(value * HOP_FLOPS["fund" if rname == "fund" else "adj"] / bytes_site, 1),
             "pct_of_nominal_8000": round(100 * value / HBM_NOMINAL_GBS, 1),
             "l2": f"inputs larger than L2 (gauge {gauge_mb:.0f} MB + spinor half {half / 1e6:.0f} MB per launch)",
             "parallelism": f"replicas{world}",
         },
-        "roofline": roofline(pname, Vh, bytes_site, launch_ms, achieved, peak, peak_kind,
-                             profiled_traffic(f"hop_fund_{pname}_{L4}x{L4}x{L4}x{L4}.md", variant, block), kernel),
+        "roofline": roofline(pname if rname == "fund" else "", Vh, bytes_site, launch_ms, achieved, peak,
+                             peak_kind, profiled_traffic(f"hop_{rname}_{pname}_{L4}x{L4}x{L4}x{L4}.md", variant, block),
+                             kernel, fma),
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
@@ -548,6 +569,7 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
         hr.hr_autotune_hop(ctx, d32, hr.HR_FUND, prec, hr.HR_EVEN, 1, gp, src, dst, reps=10)
         del gp, src, dst
     xp = fields.zeros_spinor(d32, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
+    sols = {"cg_32": {"dims": d32, "q": q32, "b": b, "x": {}}}
     for name, inner, deltas in (("fp64", hr.HR_F64, (0.1,)), ("mixed_f32", hr.HR_F32, (0.1, 1e-2, 1e-3)),
                                 ("mixed_f16", hr.HR_F16, (0.1, 3e-2, 1e-2))):
         sweep = {}
@@ -569,6 +591,8 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
             sweep[str(delta)] = rec["seconds_median"]
             if rc == hr.HR_OK and (best is None or rec["seconds_median"] < best["seconds_median"]):
                 best = rec
+                sols["cg_32"]["x"][name] = fields.unpack_spinor(ctx, d32, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN,
+                                                                xp).cpu().numpy()
             del work
         cg[name] = dict(best or rec)
         if len(deltas) > 1:
@@ -586,12 +610,12 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     torch.cuda.empty_cache()
     out["diff_solve_16"] = run_diff_solve(torch, synth)
     torch.cuda.empty_cache()
-    out["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
+    out["multi_rhs_24"], sols["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
     torch.cuda.empty_cache()
     out["batch_12"] = run_batch(ctx, torch, hr, fields, synth)
     torch.cuda.empty_cache()
     out["hmc_16"] = run_hmc(ctx, torch, hr, fields, synth)
-    return out
+    return out, sols
 
 
 def run_hmc(ctx, torch, hr, fields, synth):
@@ -771,12 +795,11 @@ def run_diff_solve(torch, synth):
     solve; forward (one solve) and backward (one adjoint solve and the link
     gradient) wall times."""
     from paper_2411_18511_gb300 import autograd as ag
-    import oracle
     d = (16, 16, 16, 16)
     m0 = -0.2
     q, nsm, plaq = synth.ape_smear_to_plaquette(synth.haar_links(d, 1005), d, 0.6)
     eta = synth.gaussian_spinor(d, 2, 2005)
-    eta[oracle.parity_mask(d) == 1] = 0
+    eta[(np.indices(d).sum(axis=0).reshape(-1) & 1) == 1] = 0  # even source
     qt = torch.tensor(q, device="cuda")
     et = torch.tensor(eta, device="cuda")
     fwd, bwd = [], []
@@ -847,6 +870,7 @@ def run_multi_rhs(ctx, torch, hr, fields, synth):
     gauge = fields.pack_gauge(ctx, d, hr.HR_FUND, hr.HR_F64, fields.gauge_to_device(q))
     g32 = fields.pack_gauge(ctx, d, hr.HR_FUND, hr.HR_F32, fields.gauge_to_device(q))
     res = {"lattice": list(d), "m0": -0.2, "tol": 1e-10, "plaquette": round(plaq, 4), "inner": "f32"}
+    sols = {"dims": d, "q": q, "n": {}}
     t1 = None
     for n in (1, 4, 8, 16, 32):
         bs = synth.gaussian_spinor(d, 2, 2004, n_rhs=n)
@@ -873,6 +897,9 @@ def run_multi_rhs(ctx, torch, hr, fields, synth):
         t = statistics.median(times)
         if n == 1:
             t1 = t
+        if n in (1, 32):  # the solutions the oracle checks (cpu_baseline)
+            xs = fields.unpack_spinor(ctx, d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, xp, n).cpu().numpy()
+            sols["n"][n] = (bs if n > 1 else bs[0][None], xs if n > 1 else xs[None])
         # multi-RHS FP32 hop: each link load serves n spinors
         src = fields.pack_spinor(ctx, d, hr.HR_FUND, hr.HR_F32, hr.HR_ODD, dev)
         dst = fields.empty_spinor(d, hr.HR_FUND, hr.HR_F32, hr.HR_EVEN, n)
@@ -894,12 +921,17 @@ def run_multi_rhs(ctx, torch, hr, fields, synth):
                         "tuned_hop_shapes": tuned}
         del work, bp, src, dst, dev
         torch.cuda.empty_cache()
-    return res
+    return res, sols
 
 
-def cpu_baseline(q, psi, dims):
+def cpu_baseline(q, psi, dims, sols=None):
     """The FP64 oracle as it stands on the host cores: one hop pair over the
-    whole lattice (every site once), OpenMP over sites."""
+    whole lattice (every site once), OpenMP over sites; and, given the GPU
+    solutions of the extras (sols), the oracle's CG at 32^4 timed beside them
+    (the CPU baseline of the metric's CG half) with every GPU solution's true
+    residual recomputed by the oracle and its distance to the oracle's
+    solution, the same for the 24^4 multi-RHS solves (residual of every
+    right-hand side at N = 1 and 32, distance for the first and last)."""
     import oracle
     try:
         L = oracle.expand_links(dims, 2, q)
@@ -920,13 +952,76 @@ def cpu_baseline(q, psi, dims):
             oracle.set_num_threads(prev)
         gbs1 = len(sites) * hop_bytes_per_site("fund", "f64") / dt1 / 1e9
         del out, L
-        return {"value": round(gbs, 3), "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
-                "sample": f"one D_eo+D_oe application over all {V} sites of {dims[0]}^4 ({dt:.2f} s)",
-                "single_core": {"value": round(gbs1, 3), "unit": "GB/s", "cores": 1,
-                                "sample": f"{len(sites)} random sites, one hop each ({dt1:.2f} s)"},
-                "cpu": _cpu_model()}
+        res = {"value": round(gbs, 3), "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"one D_eo+D_oe application over all {V} sites of {dims[0]}^4 ({dt:.2f} s)",
+               "single_core": {"value": round(gbs1, 3), "unit": "GB/s", "cores": 1,
+                               "sample": f"{len(sites)} random sites, one hop each ({dt1:.2f} s)"},
+               "cpu": _cpu_model()}
     except Exception as exc:  # the baseline is informative only
         return {"value": None, "unit": "GB/s", "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
+    if sols:
+        try:
+            res["solver_checks"] = oracle_solver_checks(oracle, sols)
+        except Exception as exc:
+            res["solver_checks"] = {"failed": str(exc)}
+    return res
+
+
+def oracle_solver_checks(oracle, sols, m0=-0.2):
+    """The oracle's view of the GPU's CG solutions (see cpu_baseline)."""
+    out = {}
+    c = sols.get("cg_32")
+    if c:
+        d = c["dims"]
+        even = (np.indices(d).sum(axis=0).reshape(-1) & 1) == 0
+        b = c["b"].copy()
+        b[~even] = 0
+        L = oracle.expand_links(d, 2, c["q"])
+        t0 = time.perf_counter()
+        xo, it, tr, ok = oracle.cg(d, L, m0, b, tol=1e-10)
+        cg_s = time.perf_counter() - t0
+        rec = {"oracle_cg": {"seconds": round(cg_s, 2), "iters": it, "true_rel_residual": tr, "converged": ok,
+                             "cores": oracle.num_threads()}}
+        nb, nxo = np.linalg.norm(b), np.linalg.norm(xo[even])
+        for name, x in c["x"].items():
+            r = np.linalg.norm(b - oracle.normal(d, L, m0, x)) / nb
+            rec[name] = {"oracle_true_rel_residual": float(r),
+                         "rel_error_vs_oracle_x": float(np.linalg.norm((x - xo)[even]) / nxo)}
+        out["cg_32"] = rec
+        del L
+    m = sols.get("multi_rhs_24")
+    if m:
+        d = m["dims"]
+        even = (np.indices(d).sum(axis=0).reshape(-1) & 1) == 0
+        L = oracle.expand_links(d, 2, m["q"])
+        rec = {}
+        for n, (bs, xs) in m["n"].items():
+            worst = 0.0
+            errs = []
+            for r in range(n):
+                b = bs[r].copy()
+                b[~even] = 0
+                worst = max(worst, float(np.linalg.norm(b - oracle.normal(d, L, m0, xs[r])) / np.linalg.norm(b)))
+                if r in (0, n - 1) and (r == 0 or n > 1):
+                    xo, it, tr, ok = oracle.cg(d, L, m0, b, tol=1e-10)
+                    errs.append(float(np.linalg.norm((xs[r] - xo)[even]) / np.linalg.norm(xo[even])))
+            rec[f"n{n}"] = {"max_oracle_true_rel_residual": worst, "rel_error_vs_oracle_x": errs,
+                            "rhs_checked": n, "x_compared_for_rhs": sorted({0, n - 1})}
+        out["multi_rhs_24"] = rec
+    return out
+
+
+def attach_oracle_checks(extras, cpu):
+    """Each CG result of the extras states its error against the FP64 oracle."""
+    chk = (cpu or {}).get("solver_checks") or {}
+    for key in ("cg_32", "multi_rhs_24"):
+        if key not in extras or key not in chk:
+            continue
+        for name, v in chk[key].items():
+            if name in extras[key] and isinstance(extras[key][name], dict):
+                extras[key][name]["vs_oracle"] = v
+            else:
+                extras[key][name] = v
 
 
 def _cpu_model() -> str:

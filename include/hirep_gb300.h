@@ -634,6 +634,19 @@ hr_status hr_axpy(hr_ctx *ctx, hr_lattice lat, hr_rep rep, double a, const void 
 hr_status hr_gamma5(hr_ctx *ctx, hr_lattice lat, hr_rep rep, void *v, hr_stream stream);
 
 /* ---------------------------------------------------------------------- */
+/* calibration (a measurement service for benchmarks; no paper counterpart) */
+/* ---------------------------------------------------------------------- */
+
+/* The FP32 FMA pipe's delivered rate on the context's device, in lane
+ * operations per second (an FFMA counts 1, a packed f32x2 FMA 2): independent
+ * FMA chains with shared multiplier and addend (the operand-reuse best case),
+ * scalar into *scalar_lane_ops and packed into *paired_lane_ops, best of three
+ * timed launches of about half a millisecond.  The FP64-class kernels compute
+ * with pairs of floats on this pipe, so their ALU roofline is this rate.
+ * Synchronises the stream; uses the context's scratch. */
+hr_status hr_fp32_fma_rate(hr_ctx *ctx, double *scalar_lane_ops, double *paired_lane_ops, hr_stream stream);
+
+/* ---------------------------------------------------------------------- */
 /* allocation-free reduction (a library service; the paper has no           */
 /* counterpart)                                                             */
 /* ---------------------------------------------------------------------- */
@@ -648,13 +661,23 @@ hr_status hr_gamma5(hr_ctx *ctx, hr_lattice lat, hr_rep rep, void *v, hr_stream 
  * block partial sums and a completion counter) is a fixed 256 KiB device
  * array inside the library, which every GPU that loads the library keeps
  * until the process exits; it has room for up to 32 right-hand sides.
- * The first call on a device looks up that array's device address: make it
- * before any stream capture.  All calls share the array: calls that overlap
- * on the GPU (different streams or threads) race and return wrong sums, so
- * serialise them.  Errors (no message is recorded, there is no context):
- * n_rhs > 32 -> HR_ERR_WORKSPACE; n_rhs not a power of two, odd or oversized
- * extents -> HR_ERR_UNSUPPORTED; extent < 2, bad rep, null pointer ->
- * HR_ERR_INVALID_ARG; a failed launch -> HR_ERR_CUDA. */
+ * The first call on a device sets the array up: it looks up the array's
+ * device address, and under CUDA's default lazy module loading that is also
+ * when the driver loads this part of the library and places the array in
+ * device memory.  So make the first call before any stream capture and
+ * before the process reserves the rest of the device memory for itself (or
+ * run with CUDA_MODULE_LOADING=EAGER, which places it when the library is
+ * loaded); later calls take no device memory.  The kernel runs on the
+ * current device with that device's array: a stream of another device is
+ * refused.  All calls share the array: calls that overlap on the GPU
+ * (different streams or threads) race and return wrong sums, so serialise
+ * them.  After a cudaDeviceReset the next call looks the address up again
+ * only once a launch has failed: reload the library instead.  Errors (no
+ * message is recorded, there is no context): n_rhs > 32 -> HR_ERR_WORKSPACE;
+ * n_rhs not a power of two, odd or oversized extents -> HR_ERR_UNSUPPORTED;
+ * extent < 2, bc outside [0, 15], a non-finite theta, bad rep, null or
+ * misaligned pointer, a stream of another device -> HR_ERR_INVALID_ARG; a
+ * failed launch -> HR_ERR_CUDA. */
 hr_status hr_norm2_noalloc(hr_lattice lat, hr_rep rep, int n_rhs, const void *v, double *result,
                            hr_stream stream);
 

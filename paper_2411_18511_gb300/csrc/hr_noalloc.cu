@@ -10,6 +10,8 @@
 // block partial sums and its completion counter live in a fixed device array
 // declared at file scope, which every GPU that loads the library holds until
 // the process exits.
+#include <atomic>
+
 #include "hr_host.h"
 
 using namespace hr;
@@ -27,8 +29,12 @@ static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // Device address of the scratch, looked up once per device (host code may
 // not pass the symbol itself: in host code its name is only a stand-in).
+// Atomic entries: two host threads making their first call at the same time
+// both look the address up and store the same value.  A cudaDeviceReset on
+// the device invalidates the entry; a failed launch clears it, so the next
+// call looks the address up again.
 constexpr int kMaxDevices = 64;
-static NoAllocScratch *g_scratch_addr[kMaxDevices] = {nullptr};
+static std::atomic<NoAllocScratch *> g_scratch_addr[kMaxDevices];
 
 template <int NC>
 __global__ void __launch_bounds__(256) k_norm2_noalloc(Geom g, const void *v, NoAllocScratch *scr, double *result)
@@ -67,29 +73,38 @@ extern "C" hr_status hr_norm2_noalloc(hr_lattice lat, hr_rep rep, int n_rhs, con
     // the fixed scratch holds kMaxRhs partial sums per block: more RHS do not fit
     if (n_rhs > kMaxRhs) return HR_ERR_WORKSPACE;
     if (n_rhs < 1 || (n_rhs & (n_rhs - 1))) return HR_ERR_UNSUPPORTED;
-    if (validate_lattice(nullptr, lat, n_rhs) != HR_OK) {
-        for (int k = 0; k < 4; ++k)
-            if (lat.dims[k] < 2) return HR_ERR_INVALID_ARG;
-        return HR_ERR_UNSUPPORTED;
-    }
+    // the same codes as the context-based calls (a null ctx records no message)
+    if (hr_status st = validate_lattice(nullptr, lat, n_rhs)) return st;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return HR_ERR_CUDA;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the kernel runs on the current device, whose scratch it is given: a
+    // stream of another device is an argument error
+    if (s) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return HR_ERR_INVALID_ARG;
+        }
+        if (sdev != dev) return HR_ERR_INVALID_ARG;
+    }
     // set-up, once per device: the first call on a device must not be inside a
-    // stream capture (it queries the symbol address)
-    if (!g_scratch_addr[dev]) {
+    // stream capture (it queries the symbol address, which under lazy module
+    // loading also loads this file's module and places the array)
+    NoAllocScratch *scr = g_scratch_addr[dev].load();
+    if (!scr) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) {
             cudaGetLastError();
             return HR_ERR_CUDA;
         }
-        g_scratch_addr[dev] = (NoAllocScratch *)ptr;
+        scr = (NoAllocScratch *)ptr;
+        g_scratch_addr[dev].store(scr);
     }
-    NoAllocScratch *scr = g_scratch_addr[dev];
-    cudaStream_t s = (cudaStream_t)stream;
     Geom g = make_geom(lat, n_rhs);
     // the grid never exceeds the partial-sum slots of the scratch
     int sms = 0;
@@ -107,6 +122,9 @@ extern "C" hr_status hr_norm2_noalloc(hr_lattice lat, hr_rep rep, int n_rhs, con
     }
     if (rep_nc(rep) == 2) k_norm2_noalloc<2><<<grid, 256, 0, s>>>(g, v, scr, result);
     else k_norm2_noalloc<3><<<grid, 256, 0, s>>>(g, v, scr, result);
-    if (cudaGetLastError() != cudaSuccess) return HR_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) {
+        g_scratch_addr[dev].store(nullptr); // look the address up again next time
+        return HR_ERR_CUDA;
+    }
     return HR_OK;
 }

@@ -51,6 +51,7 @@ EXPORTED = [
     "hr_link_update", "hr_mom_update", "hr_kinetic_energy", "hr_hmc_workspace_bytes", "hr_hmc_trajectory",
     "hr_clover_force_workspace_bytes", "hr_clover_insertion_force", "hr_clover_fermion_force", "hr_clover_logdet",
     "hr_ctx_status", "hr_dot", "hr_fermion_force_workspace_bytes", "hr_fermion_force", "hr_fermion_link_grad",
+    "hr_fp32_fma_rate",
 ]
 
 
@@ -161,6 +162,7 @@ def lib():
                 "hr_fermion_force": ([P, LAT, D, I, P, P, P, D, P, P, S, P], I),
                 "hr_fermion_link_grad": ([P, LAT, D, I, P, P, P, D, P, P, S, P], I),
                 "hr_dot": ([P, LAT, I, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P], I),
+                "hr_fp32_fma_rate": ([P, ctypes.POINTER(D), ctypes.POINTER(D), P], I),
                 "hr_norm2": ([P, LAT, I, P, ctypes.POINTER(D), P], I),
                 "hr_axpy": ([P, LAT, I, D, P, P, P], I),
                 "hr_gamma5": ([P, LAT, I, P, P], I),
@@ -644,6 +646,13 @@ def hr_dot(ctx: Context, dims, rep, a, b, stream=None) -> complex:
     return complex(re.value, im.value)
 
 
+def hr_fp32_fma_rate(ctx: Context, stream=None):
+    """Measured FP32 FMA pipe rate (scalar, packed f32x2) in lane operations per second."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    ctx.check(lib().hr_fp32_fma_rate(ctx.handle, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return a.value, b.value
+
+
 def hr_norm2(ctx: Context, dims, rep, v, stream=None) -> float:
     out = ctypes.c_double(0.0)
     ctx.check(lib().hr_norm2(ctx.handle, lattice(dims), rep, _ptr(v), ctypes.byref(out),
@@ -669,8 +678,9 @@ def _vol(dims) -> int:
 
 def hr_norm2_noalloc(dims, rep, n_rhs, v, result, stream=None) -> int:
     """|v_r|^2 into the device tensor ``result`` without a context or any
-    allocation (for callers that may not allocate device memory). Returns the
-    status code; raises nothing."""
+    allocation (for callers that may not allocate device memory).  Returns the
+    library's status code; raises ValueError only when ``result`` is not a
+    contiguous CUDA tensor of at least n_rhs doubles."""
     _need(result, 8 * int(n_rhs), "result")
     return int(lib().hr_norm2_noalloc(lattice(dims), rep, int(n_rhs), _ptr(v), _ptr(result),
                                       _stream(stream)))
