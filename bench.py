@@ -608,6 +608,8 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     torch.cuda.empty_cache()
     out["twist_48"] = run_twist_48(ctx, torch, hr, fields, q48, psi48)
     torch.cuda.empty_cache()
+    out["dd_48"] = run_dd_48(ctx, torch, hr, fields, q48, psi48)
+    torch.cuda.empty_cache()
     out["diff_solve_16"] = run_diff_solve(torch, synth)
     torch.cuda.empty_cache()
     out["multi_rhs_24"], sols["multi_rhs_24"] = run_multi_rhs(ctx, torch, hr, fields, synth)
@@ -788,6 +790,47 @@ def run_twist_48(ctx, torch, hr, fields, q48, psi48, reps=30):
         out[k]["time_vs_untwisted"] = round(out[k]["ms"] / out["untwisted"]["ms"], 3)
     del qd, pd
     return out
+
+
+def run_dd_48(ctx, torch, hr, fields, q48, psi48, reps=20):
+    """48^4 fund FP64 split along time into 4 slabs of 12 x 48^3 on this one
+    GPU (the multi-GPU data flow, the exchange a device copy on a second
+    stream): one D_eo + D_oe application (per parity: face pack, exchange,
+    the 4 local hops, the boundary kernels) against the tuned whole-lattice
+    hop pair, 512 B per site.  The slabs run one after another on the one
+    GPU, so this is the decomposition's overhead, not a scaling figure."""
+    from paper_2411_18511_gb300 import dd
+    dims, n = DIMS, 4
+    Vh = int(np.prod(dims)) // 2
+    slabs = dd.TimeSlabs(dims, n)
+    op = dd.SlabHop(ctx, slabs, hr.HR_FUND, hr.HR_F64, q48)
+    src = {p: op.pack_input(psi48, 1 - p) for p in (hr.HR_EVEN, hr.HR_ODD)}
+    out = {p: [fields.empty_spinor(slabs.local(r), hr.HR_FUND, hr.HR_F64, p) for r in range(n)]
+           for p in (hr.HR_EVEN, hr.HR_ODD)}
+    # the local hops with the shape the tuner picks for a slab
+    loc = slabs.local(0)
+    g0, s0, d0 = op.gauge[0], src[hr.HR_EVEN][0], out[hr.HR_EVEN][0]
+    res = hr.hr_autotune_hop(ctx, loc, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, 1, g0, s0, d0, reps=10)
+
+    def step():
+        op.apply(hr.HR_EVEN, src[hr.HR_EVEN], out[hr.HR_EVEN])
+        op.apply(hr.HR_ODD, src[hr.HR_ODD], out[hr.HR_ODD])
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    face_mb = hr.hr_dd_face_bytes(loc, hr.HR_FUND, hr.HR_F64) / 1e6
+    return {"lattice": list(dims), "slabs": n, "slab": list(loc), "ms_per_hop_pair": round(ms, 4),
+            "gbs": round(2 * Vh * 512 / (ms * 1e-3) / 1e9, 1), "face_mb_each": round(face_mb, 2),
+            "faces_per_slab_per_hop": 2, "local_hop_launch": {"variant": res.variant, "block": res.block},
+            "note": "all slabs on one GPU, run in turn; multi-GPU runs untested here (one GPU per call)"}
 
 
 def run_diff_solve(torch, synth):

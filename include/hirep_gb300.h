@@ -634,6 +634,53 @@ hr_status hr_axpy(hr_ctx *ctx, hr_lattice lat, hr_rep rep, double a, const void 
 hr_status hr_gamma5(hr_ctx *ctx, hr_lattice lat, hr_rep rep, void *v, hr_stream stream);
 
 /* ---------------------------------------------------------------------- */
+/* domain decomposition along time (Sec. 2.1.1)                            */
+/* ---------------------------------------------------------------------- */
+
+/* The paper distributes the lattice over GPUs: each computes its inner sites
+ * while the boundary data travels, then its boundary sites (Sec. 2.1.1; the
+ * weak and strong scaling of Table 1).  Here the lattice (T, L1, L2, L3) is
+ * split along time into n slabs of T_loc = T / n slices (T_loc even), one per
+ * rank, each an ordinary local lattice (T_loc, L1, L2, L3) packed and hopped
+ * with the calls above.  A local hop (hr_dirac_eo, HR_OP_HOP) wraps time
+ * inside the slab; every term is right except the time hops of the two face
+ * slices.  Per hop, each rank
+ *   1. packs its faces of the input field (hr_dd_pack_faces),
+ *   2. sends to_lower to the rank below (it arrives there as from_upper) and
+ *      to_upper to the rank above (arriving as from_lower), periodic in the
+ *      rank index -- a device copy when two slabs share a GPU, NCCL send /
+ *      receive into the receiver's own buffer across GPUs,
+ *   3. runs the local hop meanwhile (the inner sites need nothing remote),
+ *   4. after the exchange, replaces the wrapped time terms of its face sites
+ *      by the received ones (hr_dd_hop_boundary).
+ * Boundary conditions: pack the local gauge field with lat.bc bit 0 only on
+ * the last slab (it holds the global time boundary) and the spatial bits on
+ * every slab; a twist in time is not supported (HR_ERR_UNSUPPORTED).  One
+ * right-hand side.  Face layout: 4 NC reals per face site (the two spins of
+ * a projected half spinor), V3/2 face sites (V3 = L1 L2 L3) numbered by their
+ * even-odd index within the slice; FP64 faces hold (hi, lo) float pairs. */
+
+/* Bytes of one face buffer for the local lattice `local` (0 if invalid). */
+size_t hr_dd_face_bytes(hr_lattice local, hr_rep rep, hr_prec prec);
+
+/* The two faces of the packed input field `in` (sites of in_parity of the
+ * local lattice): to_lower = P-_0 psi on the slice t = 0 and to_upper =
+ * U_0(x)^+ P+_0 psi(x) on t = T_loc - 1, with P-+_0 the projections of
+ * (1 -+ g_0).  gauge: the packed local gauge field of rep and prec. */
+hr_status hr_dd_pack_faces(hr_ctx *ctx, hr_lattice local, hr_rep rep, hr_prec prec, hr_parity in_parity,
+                           const void *gauge, const void *in, void *to_lower, void *to_upper, hr_stream stream);
+
+/* After out = -1/2 H_{p,1-p} in on the local lattice (hr_dirac_eo with
+ * HR_OP_HOP, out_parity p), give the face sites of out their time hops from
+ * the neighbouring slabs: out += -1/2 (1 - g_0) U_0(x) [from_upper - P-_0 psi
+ * (wrapped)] on t = T_loc - 1 and out += -1/2 (1 + g_0) [from_lower - U_0^+
+ * P+_0 psi (wrapped)] on t = 0.  from_upper / from_lower: the faces the rank
+ * above / below packed (its to_lower / to_upper) from its own input field. */
+hr_status hr_dd_hop_boundary(hr_ctx *ctx, hr_lattice local, hr_rep rep, hr_prec prec, hr_parity out_parity,
+                             const void *gauge, const void *in, const void *from_lower, const void *from_upper,
+                             void *out, hr_stream stream);
+
+/* ---------------------------------------------------------------------- */
 /* calibration (a measurement service for benchmarks; no paper counterpart) */
 /* ---------------------------------------------------------------------- */
 

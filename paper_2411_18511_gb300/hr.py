@@ -51,7 +51,7 @@ EXPORTED = [
     "hr_link_update", "hr_mom_update", "hr_kinetic_energy", "hr_hmc_workspace_bytes", "hr_hmc_trajectory",
     "hr_clover_force_workspace_bytes", "hr_clover_insertion_force", "hr_clover_fermion_force", "hr_clover_logdet",
     "hr_ctx_status", "hr_dot", "hr_fermion_force_workspace_bytes", "hr_fermion_force", "hr_fermion_link_grad",
-    "hr_fp32_fma_rate",
+    "hr_fp32_fma_rate", "hr_dd_face_bytes", "hr_dd_pack_faces", "hr_dd_hop_boundary",
 ]
 
 
@@ -163,6 +163,9 @@ def lib():
                 "hr_fermion_link_grad": ([P, LAT, D, I, P, P, P, D, P, P, S, P], I),
                 "hr_dot": ([P, LAT, I, P, P, ctypes.POINTER(D), ctypes.POINTER(D), P], I),
                 "hr_fp32_fma_rate": ([P, ctypes.POINTER(D), ctypes.POINTER(D), P], I),
+                "hr_dd_face_bytes": ([LAT, I, I], S),
+                "hr_dd_pack_faces": ([P, LAT, I, I, I, P, P, P, P, P], I),
+                "hr_dd_hop_boundary": ([P, LAT, I, I, I, P, P, P, P, P, P], I),
                 "hr_norm2": ([P, LAT, I, P, ctypes.POINTER(D), P], I),
                 "hr_axpy": ([P, LAT, I, D, P, P, P], I),
                 "hr_gamma5": ([P, LAT, I, P, P], I),
@@ -651,6 +654,22 @@ def hr_fp32_fma_rate(ctx: Context, stream=None):
     a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
     ctx.check(lib().hr_fp32_fma_rate(ctx.handle, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
     return a.value, b.value
+
+
+def hr_dd_face_bytes(local_dims, rep, prec) -> int:
+    return int(lib().hr_dd_face_bytes(lattice(local_dims), rep, prec))
+
+
+def hr_dd_pack_faces(ctx: Context, local_dims, rep, prec, in_parity, gauge, inp, to_lower, to_upper, stream=None):
+    return ctx.check(lib().hr_dd_pack_faces(ctx.handle, lattice(local_dims), rep, prec, in_parity, _ptr(gauge),
+                                            _ptr(inp), _ptr(to_lower), _ptr(to_upper), _stream(stream)))
+
+
+def hr_dd_hop_boundary(ctx: Context, local_dims, rep, prec, out_parity, gauge, inp, from_lower, from_upper, out,
+                       stream=None):
+    return ctx.check(lib().hr_dd_hop_boundary(ctx.handle, lattice(local_dims), rep, prec, out_parity, _ptr(gauge),
+                                              _ptr(inp), _ptr(from_lower), _ptr(from_upper), _ptr(out),
+                                              _stream(stream)))
 
 
 def hr_norm2(ctx: Context, dims, rep, v, stream=None) -> float:
