@@ -367,9 +367,11 @@ hr_status hr_ctx_create(hr_ctx **out, int device)
     ctx->device = device;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_partials, sizeof(double) * kMaxBlocks * kMaxRhs);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_partials, sizeof(double) * (kMaxBlocks + kRedMaxGroups) * kMaxRhs);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, sizeof(unsigned) * kNumCounters);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned) * kNumCounters);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_group_counters, sizeof(unsigned) * kNumCounters * kRedMaxGroups);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_group_counters, 0, sizeof(unsigned) * kNumCounters * kRedMaxGroups);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_scal, sizeof(double) * kScalDoubles);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_scal, 0, sizeof(double) * kScalDoubles);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_scal, sizeof(double) * kScalDoubles);
@@ -398,6 +400,7 @@ hr_status hr_ctx_destroy(hr_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->d_partials) cudaFree(ctx->d_partials);
     if (ctx->d_counters) cudaFree(ctx->d_counters);
+    if (ctx->d_group_counters) cudaFree(ctx->d_group_counters);
     if (ctx->d_scal) cudaFree(ctx->d_scal);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);

@@ -35,8 +35,9 @@ struct hr_ctx {
     int device = 0;
     int sm_count = 0;
     std::string err;
-    double *d_partials = nullptr;  // kMaxBlocks * kMaxRhs
+    double *d_partials = nullptr;  // kMaxBlocks * kMaxRhs, then kRedMaxGroups * kMaxRhs group sums
     unsigned *d_counters = nullptr;
+    unsigned *d_group_counters = nullptr; // kNumCounters * kRedMaxGroups (two-level reductions)
     double *d_scal = nullptr;      // kScalDoubles
     double *h_scal = nullptr;      // pinned mirror
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -78,8 +79,11 @@ inline RedSlot red_slot(hr_ctx *ctx, int counter)
     RedSlot s;
     s.partials = ctx->d_partials;
     s.counter = ctx->d_counters + counter;
+    s.group_counters = ctx->d_group_counters + (size_t)counter * kRedMaxGroups;
+    s.group_partials = ctx->d_partials + (size_t)kMaxBlocks * kMaxRhs;
     return s;
 }
+static_assert(kMaxBlocks <= kRedGroup * kRedMaxGroups, "two-level reductions cover every grid");
 
 inline int grid_for(long long n, int block, int cap)
 {

@@ -893,7 +893,15 @@ __device__ __forceinline__ void spin_accumulate(cpx<T> (&acc)[4][NC], const cpx<
 struct RedSlot {
     double *partials;  // >= gridDim.x * nrhs doubles
     unsigned *counter; // zero before the launch; reset by the last block
+    // two-level form (nullable): kRedGroup consecutive blocks form a group;
+    // the last block of a group to finish sums the group's partials into
+    // group_partials[group * nrhs + r] (counted in group_counters[group],
+    // zero before the launch, reset), and the last group summer adds the
+    // groups.  No block then sums more than kRedGroup blocks' partials.
+    unsigned *group_counters; // >= kRedMaxGroups
+    double *group_partials;   // >= kRedMaxGroups * nrhs doubles
 };
+constexpr int kRedGroup = 64, kRedMaxGroups = 64;
 
 __device__ __forceinline__ double warp_sum_strided(double v, int nrhs)
 {
@@ -957,14 +965,36 @@ __device__ inline bool grid_reduce(double v, int nrhs, RedSlot slot, double *sum
     __shared__ bool last;
     __threadfence();
     __syncthreads();
+    unsigned nparts = gridDim.x;
+    const double *parts = slot.partials;
+    if (slot.group_counters && gridDim.x > (unsigned)kRedGroup) {
+        // first level: the last block of this group sums the group's partials
+        const unsigned grp = blockIdx.x / kRedGroup;
+        const unsigned first = grp * kRedGroup;
+        const unsigned gsize = min((unsigned)kRedGroup, gridDim.x - first);
+        if (threadIdx.x == 0) {
+            unsigned t = atomicAdd(slot.group_counters + grp, 1u);
+            last = (t == gsize - 1);
+        }
+        __syncthreads();
+        if (!last) return false;
+        __threadfence();
+        sum_partials(slot.partials + (size_t)first * nrhs, gsize, nrhs, sums, smem);
+        if (threadIdx.x < nrhs) slot.group_partials[(size_t)grp * nrhs + threadIdx.x] = sums[threadIdx.x];
+        if (threadIdx.x == 0) slot.group_counters[grp] = 0u;
+        __threadfence();
+        __syncthreads();
+        nparts = (gridDim.x + kRedGroup - 1) / kRedGroup;
+        parts = slot.group_partials;
+    }
     if (threadIdx.x == 0) {
         unsigned t = atomicAdd(slot.counter, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == nparts - 1);
     }
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    sum_partials(slot.partials, gridDim.x, nrhs, sums, smem);
+    sum_partials(parts, nparts, nrhs, sums, smem);
     if (threadIdx.x == 0) *slot.counter = 0u;
     return true;
 }

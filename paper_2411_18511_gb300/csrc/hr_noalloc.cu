@@ -58,6 +58,8 @@ __global__ void __launch_bounds__(256) k_norm2_noalloc(Geom g, const void *v, No
     RedSlot slot;
     slot.partials = scr->partials;
     slot.counter = &scr->counter;
+    slot.group_counters = nullptr; // one level: the fixed scratch has no group slots
+    slot.group_partials = nullptr;
     if (grid_reduce(acc.get(), g.nrhs, slot, sums, smem)) {
         if (threadIdx.x < g.nrhs) result[threadIdx.x] = sums[threadIdx.x];
     }
