@@ -52,13 +52,17 @@ DF_OPS_PER_SITE_FUND = 8 * 384 + 7 * 128 + 32 + 96
 # kernel symbol of each hop variant (the tuner's index)
 HOP_KERNELS = ["k_hop", "k_hop_staged", "k_hop_loop", "k_hop_loop", "k_hop_sw", "k_hop_sw", "k_hop_pf",
                "k_hop_r96", "k_hop_tile", "k_hop_tile_r96", "k_hop_x2", "k_hop_x2s", "k_hop_x2_r96",
-               "k_hop_x2s_r96", "k_hop_h16", "k_hop_h16_r64"]
+               "k_hop_x2s_r96", "k_hop_h16", "k_hop_h16_r64", "k_hop_p2", "k_hop_p2_r96",
+               "k_hop_h16s", "k_hop_h16s_r64"]
 HOP_VARIANT_NAMES = ["unrolled", "unrolled cp.async staged", "generic loop", "generic loop staged",
                      "switched loop", "switched loop staged", "unrolled register prefetch",
                      "unrolled, 96 registers", "bulk-copy tiled", "bulk-copy tiled, 96 registers",
                      "paired f32x2", "paired f32x2, cp.async staged",
                      "paired f32x2, 96 registers", "paired f32x2, cp.async staged, 96 registers",
-                     "binary16, half2 projection", "binary16, half2 projection, 64 registers"]
+                     "binary16, half2 projection", "binary16, half2 projection, 64 registers",
+                     "two sites per thread (f32x2 lanes)", "two sites per thread (f32x2 lanes), 96 registers",
+                     "binary16, half2 projection, cp.async staged",
+                     "binary16, half2 projection, cp.async staged, 64 registers"]
 
 
 def roofline(pname, vh, bytes_site, launch_ms, achieved_gbs, peak_gbs, peak_kind, traffic, kernel, fma=None):

@@ -12,7 +12,7 @@
 //
 // This file holds the plain unrolled kernels (variants 0 and 7), the dispatch
 // over all variants (the other families are in hr_hop_staged.cu, hr_hop_loop.cu,
-// hr_hop_tile.cu, hr_hop_x2.cu and hr_hop_half.cu; hr_hop_fam.h lists them; lattices with
+// hr_hop_tile.cu, hr_hop_x2.cu, hr_hop_half.cu and hr_hop_p2.cu; hr_hop_fam.h lists them; lattices with
 // twisted boundaries take the kernel of hr_hop_twist.cu), the operators built
 // from hops and their C ABI.  The autotuner (hr_tune.cu) picks variant and
 // block size per configuration.
@@ -152,7 +152,11 @@ hr_status dispatch(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs 
     case kVarPairedR96:
     case kVarPairedStagedR96: done = launch_hop_paired(ctx, g, rep, prec, a, c, grid, s, st); break;
     case kVarHalf:
-    case kVarHalfR64: done = launch_hop_half(ctx, g, rep, prec, a, c, grid, s, st); break;
+    case kVarHalfR64:
+    case kVarHalfStaged:
+    case kVarHalfStagedR64: done = launch_hop_half(ctx, g, rep, prec, a, c, grid, s, st); break;
+    case kVarPairSites:
+    case kVarPairSitesR96: done = launch_hop_pair_sites(ctx, g, rep, prec, a, c, grid, s, st); break;
     default: break;
     }
     // the plain kernels: variants 0 and 7, and any variant without a kernel here
@@ -237,7 +241,10 @@ bool hop_variant_available(int rep, int prec, int variant)
     if (variant == kVarPairedStaged) return rep == HR_FUND || (rep == HR_ADJ && prec == HR_F64);
     if (variant == kVarPairedR96 || variant == kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
     // the half2-projection kernels: fundamental binary16 only
-    if (variant == kVarHalf || variant == kVarHalfR64) return rep == HR_FUND && prec == HR_F16;
+    if (variant == kVarHalf || variant == kVarHalfR64 || variant == kVarHalfStaged || variant == kVarHalfStagedR64)
+        return rep == HR_FUND && prec == HR_F16;
+    // two sites per thread: fundamental FP32 and binary16
+    if (variant == kVarPairSites || variant == kVarPairSitesR96) return rep == HR_FUND && prec != HR_F64;
     // the 96-register caps spill heavily with three colours: fundamental only
     if (variant == kVarSimpleR96) return rep == HR_FUND;
     if (variant == kVarTileR96) return rep == HR_FUND && prec != HR_F16;

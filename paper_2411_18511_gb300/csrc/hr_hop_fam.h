@@ -8,7 +8,9 @@
 //   hr_hop_x2.cu      10-13 fundamental FP64 on packed f32x2 FMAs (registers /
 //                     cp.async staged, compiler's registers / 96)
 //   hr_hop_half.cu    14, 15 fundamental binary16 with the projection in half2
-//                     (compiler's registers / 64)
+//                     (compiler's registers / 64); 18, 19 the same, cp.async staged
+//   hr_hop_p2.cu      16, 17 fundamental FP32 / binary16, two sites per thread in
+//                     the lanes of packed f32x2 FMAs (compiler's registers / 96)
 // All compute the same operator; the autotuner picks per configuration.
 #pragma once
 
@@ -33,9 +35,13 @@ enum HopVariant : int {
     kVarPairedR96 = 12,
     kVarPairedStagedR96 = 13,
     kVarHalf = 14,
-    kVarHalfR64 = 15
+    kVarHalfR64 = 15,
+    kVarPairSites = 16,
+    kVarPairSitesR96 = 17,
+    kVarHalfStaged = 18,
+    kVarHalfStagedR64 = 19
 };
-static_assert(kVarHalfR64 + 1 == kNumHopVariants, "variant list");
+static_assert(kVarHalfStagedR64 + 1 == kNumHopVariants, "variant list");
 
 // per-thread shared-memory slots of the cp.async staged variants (1, 3, 5, 11, 13)
 template <int REP, int PREC> struct Stage {
@@ -104,6 +110,8 @@ bool launch_hop_paired(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopA
                        cudaStream_t s, hr_status &st);
 bool launch_hop_half(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs &a, HopChoice c, int grid,
                      cudaStream_t s, hr_status &st);
+bool launch_hop_pair_sites(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs &a, HopChoice c, int grid,
+                           cudaStream_t s, hr_status &st);
 // the paired staged kernel with the clover epilogue (fundamental FP64)
 void launch_hop_clover_paired(hr_ctx *ctx, const HopArgs &a, int grid, int block, cudaStream_t s, hr_status &st);
 // the kernel of lattices with twisted boundaries (hr_hop_twist.cu): every

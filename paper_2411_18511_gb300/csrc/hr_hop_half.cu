@@ -1,5 +1,5 @@
 // hr_hop_half.cu -- the binary16 fundamental hop with the spin projection in
-// half2 arithmetic (variants 14 and 15).
+// half2 arithmetic (variants 14, 15, 18, 19).
 //
 // The FP16 hop moves 136 bytes per output site (the neighbour spinors as
 // binary16 with one FP32 scale per site, binary16 quaternion links), so at
@@ -18,33 +18,14 @@
 // and the accumulation run in FP32.  The result agrees with the FP32-
 // arithmetic kernels to the storage precision, not bit for bit.
 //
-// Variant 14: registers as the compiler likes; 15: capped at 64 registers.
+// Variant 14: registers as the compiler likes; 15: capped at 64 registers;
+// 18, 19: the same with the next direction's operands staged by cp.async.
 #include "hr_hop_fam.h"
 #include "hr_hop_x2.cuh"
 
 using namespace hr;
 
 namespace {
-
-// h = s + i^C y on a packed (colour 0, colour 1) word pair (re, im)
-template <int C>
-__device__ __forceinline__ void h2_project(__half2 sre, __half2 sim, __half2 yre, __half2 yim, __half2 &hre,
-                                           __half2 &him)
-{
-    if constexpr (C == 0) {
-        hre = __hadd2(sre, yre);
-        him = __hadd2(sim, yim);
-    } else if constexpr (C == 1) {
-        hre = __hsub2(sre, yim);
-        him = __hadd2(sim, yre);
-    } else if constexpr (C == 2) {
-        hre = __hsub2(sre, yre);
-        him = __hsub2(sim, yim);
-    } else {
-        hre = __hadd2(sre, yim);
-        him = __hsub2(sim, yre);
-    }
-}
 
 // acc (+)= i^C sc z
 template <int C, bool FIRST>
@@ -63,21 +44,17 @@ __device__ __forceinline__ void acc_scaled(cpx<float> &acc, const cpx<float> &z,
     }
 }
 
-__device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<const __half2 *>(&u); }
-
-// One direction: acc (+)= (1 -/+ g_mu) U psi(neighbour) (FWD: U_mu(x), else
-// U_mu(x - mu)^+).  NEG: the input's upper spins are negated (g5 in); as in the
-// paired kernels the sign moves from the projection to the rebuild.
+// One direction's arithmetic from the neighbour's two packed words w0, w1, its
+// scale sc and the link q (binary16, widened): acc (+)= (1 -/+ g_mu) U psi
+// (FWD: U_mu(x), else U_mu(x - mu)^+).  NEG: the input's upper spins are
+// negated (g5 in); as in the paired kernels the sign moves from the
+// projection to the rebuild.
 template <int MU, bool FWD, bool FIRST, bool NEG>
-__device__ __forceinline__ void h16_term(const HopArgs &a, const float *nrm, int site_link, int link_par, int jn,
-                                         cpx<float> (&acc)[4][2])
+__device__ __forceinline__ void h16_compute(const uint4 &w0, const uint4 &w1, float sc, const float (&q)[4],
+                                            cpx<float> (&acc)[4][2])
 {
     using D = X2Dir<MU, FWD>;
     constexpr int F = NEG ? 2 : 0;
-    const uint4 *sp = (const uint4 *)a.in;
-    const uint4 w0 = __ldg(sp + vec_index(jn, 0, 2));
-    const uint4 w1 = __ldg(sp + vec_index(jn, 1, 2));
-    const float sc = __ldg(nrm + jn);
     // spin t: word 2t = (c0.re, c1.re), word 2t+1 = (c0.im, c1.im)
     const uint32_t u[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
     __half2 h0re, h0im, h1re, h1im;
@@ -92,8 +69,6 @@ __device__ __forceinline__ void h16_term(const HopArgs &a, const float *nrm, int
         h[1][0] = {r1.x, i1.x};
         h[1][1] = {r1.y, i1.y};
     }
-    float q[4];
-    load_quat<kF16>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
     cpx<float> r[2][2];
     su2_mul<!FWD>(q, h[0], r[0]);
     su2_mul<!FWD>(q, h[1], r[1]);
@@ -104,6 +79,20 @@ __device__ __forceinline__ void h16_term(const HopArgs &a, const float *nrm, int
         acc_scaled<(D::d0 + F) & 3, FIRST>(acc[2][c], r[D::rho0][c], sc);
         acc_scaled<(D::d1 + F) & 3, FIRST>(acc[3][c], r[D::rho1][c], sc);
     }
+}
+
+// the neighbour and link loaded from global memory
+template <int MU, bool FWD, bool FIRST, bool NEG>
+__device__ __forceinline__ void h16_term(const HopArgs &a, const float *nrm, int site_link, int link_par, int jn,
+                                         cpx<float> (&acc)[4][2])
+{
+    const uint4 *sp = (const uint4 *)a.in;
+    const uint4 w0 = __ldg(sp + vec_index(jn, 0, 2));
+    const uint4 w1 = __ldg(sp + vec_index(jn, 1, 2));
+    const float sc = __ldg(nrm + jn);
+    float q[4];
+    load_quat<kF16>(a.gauge, a.g.nblk_g, link_par, MU, site_link, q);
+    h16_compute<MU, FWD, FIRST, NEG>(w0, w1, sc, q, acc);
 }
 
 template <int MU, bool FIRST, bool NEG>
@@ -146,8 +135,78 @@ __device__ __forceinline__ void h16_body(const HopArgs &a)
     }
 }
 
+// Staged form: direction K+1's two spinor words, link and scale are copied by
+// cp.async into this thread's shared-memory slots while direction K is
+// computed from the other buffer, so each warp keeps a direction's operands in
+// flight without holding them in registers.
+template <int K, bool NEG>
+__device__ __forceinline__ void h16_stage_step(const HopArgs &a, int i, int rr, const SiteNb &nb, uint4 *b0,
+                                               uint4 *b1, int bd, cpx<float> (&acc)[4][2])
+{
+    using S = Stage<kRepFund, kF16>;
+    static_assert(S::NV == 2 && S::NQ == 1 && S::NSLOT == 4, "two spinor words, the link, the scale");
+    uint4 *cur = (K & 1) ? b1 : b0;
+    uint4 *nxt = (K & 1) ? b0 : b1;
+    if constexpr (K < 7) {
+        stage_issue<K + 1, kRepFund, kF16>(a, i, rr, nb, nxt, bd);
+        cp_async_commit();
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
+    const uint4 w0 = cur[0], w1 = cur[bd];
+    const uint2 qw = *reinterpret_cast<const uint2 *>(cur + 2 * bd); // the link slot holds 8 bytes
+    const float sc = *reinterpret_cast<const float *>(cur + 3 * bd);  // the scale slot 4
+    const float2 q01 = __half22float2(as_h2(qw.x)), q23 = __half22float2(as_h2(qw.y));
+    const float q[4] = {q01.x, q01.y, q23.x, q23.y};
+    h16_compute<(K >> 1), (K & 1) == 0, K == 0, NEG>(w0, w1, sc, q, acc);
+}
+
+template <int G5IN>
+__device__ __forceinline__ void h16s_body(const HopArgs &a)
+{
+    using S = Stage<kRepFund, kF16>;
+    constexpr bool NEG = G5IN != 0;
+    extern __shared__ uint4 h16_stage_mem[];
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const int bd = blockDim.x;
+    uint4 *b0 = h16_stage_mem + threadIdx.x;
+    uint4 *b1 = h16_stage_mem + S::NSLOT * bd + threadIdx.x;
+    const float be = a.beta.h;
+    const float bu = a.g5_out ? -be : be;
+    const float al = a.alpha.h;
+    SqAcc<float> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        stage_issue<0, kRepFund, kF16>(a, i, rr, nb, b0, bd);
+        cp_async_commit();
+        cpx<float> acc[4][2];
+        h16_stage_step<0, NEG>(a, i, rr, nb, b0, b1, bd, acc);
+        h16_stage_step<1, NEG>(a, i, rr, nb, b0, b1, bd, acc);
+        h16_stage_step<2, NEG>(a, i, rr, nb, b0, b1, bd, acc);
+        h16_stage_step<3, NEG>(a, i, rr, nb, b0, b1, bd, acc);
+        h16_stage_step<4, NEG>(a, i, rr, nb, b0, b1, bd, acc);
+        h16_stage_step<5, NEG>(a, i, rr, nb, b0, b1, bd, acc);
+        h16_stage_step<6, NEG>(a, i, rr, nb, b0, b1, bd, acc);
+        h16_stage_step<7, NEG>(a, i, rr, nb, b0, b1, bd, acc);
+        hop_epilogue<kF16>(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
 template <int G5IN> __global__ void __launch_bounds__(256) k_hop_h16(HopArgs a) { h16_body<G5IN>(a); }
 template <int G5IN> __global__ void __maxnreg__(64) k_hop_h16_r64(HopArgs a) { h16_body<G5IN>(a); }
+template <int G5IN> __global__ void __launch_bounds__(256) k_hop_h16s(HopArgs a) { h16s_body<G5IN>(a); }
+template <int G5IN> __global__ void __maxnreg__(64) k_hop_h16s_r64(HopArgs a) { h16s_body<G5IN>(a); }
 
 } // namespace
 
@@ -158,8 +217,22 @@ bool launch_hop_half(hr_ctx *ctx, const Geom &, int rep, int prec, const HopArgs
 {
     if (rep != HR_FUND || prec != kF16) return false;
     const bool g5 = a.g5_in != 0;
-    if (c.variant == kVarHalfR64) (g5 ? k_hop_h16_r64<1> : k_hop_h16_r64<0>)<<<grid, c.block, 0, s>>>(a);
-    else (g5 ? k_hop_h16<1> : k_hop_h16<0>)<<<grid, c.block, 0, s>>>(a);
+    if (c.variant == kVarHalfStaged || c.variant == kVarHalfStagedR64) {
+        using S = Stage<kRepFund, kF16>;
+        static bool attr_set = false;
+        if (!attr_set) {
+            for (auto f : {k_hop_h16s<0>, k_hop_h16s<1>, k_hop_h16s_r64<0>, k_hop_h16s_r64<1>})
+                cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes(256));
+            attr_set = true;
+        }
+        const size_t sm = S::smem_bytes(c.block);
+        if (c.variant == kVarHalfStagedR64) (g5 ? k_hop_h16s_r64<1> : k_hop_h16s_r64<0>)<<<grid, c.block, sm, s>>>(a);
+        else (g5 ? k_hop_h16s<1> : k_hop_h16s<0>)<<<grid, c.block, sm, s>>>(a);
+    } else if (c.variant == kVarHalfR64) {
+        (g5 ? k_hop_h16_r64<1> : k_hop_h16_r64<0>)<<<grid, c.block, 0, s>>>(a);
+    } else {
+        (g5 ? k_hop_h16<1> : k_hop_h16<0>)<<<grid, c.block, 0, s>>>(a);
+    }
     st = check_launch(ctx, "binary16 hop kernel (half2 projection)");
     return true;
 }

@@ -245,4 +245,27 @@ __device__ __forceinline__ void x2_epilogue(const HopArgs &a, int j, const cdd2 
 }
 
 
+// ---------------------------------------------------------------- binary16 projection
+// h = s + i^C y on a packed (colour 0, colour 1) word pair (re, im)
+template <int C>
+__device__ __forceinline__ void h2_project(__half2 sre, __half2 sim, __half2 yre, __half2 yim, __half2 &hre,
+                                           __half2 &him)
+{
+    if constexpr (C == 0) {
+        hre = __hadd2(sre, yre);
+        him = __hadd2(sim, yim);
+    } else if constexpr (C == 1) {
+        hre = __hsub2(sre, yim);
+        him = __hadd2(sim, yre);
+    } else if constexpr (C == 2) {
+        hre = __hsub2(sre, yre);
+        him = __hsub2(sim, yim);
+    } else {
+        hre = __hadd2(sre, yim);
+        him = __hsub2(sim, yre);
+    }
+}
+
+__device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<const __half2 *>(&u); }
+
 } // namespace hr
