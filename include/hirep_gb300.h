@@ -585,14 +585,16 @@ typedef struct {
                           instruction (fundamental: the two colours; adjoint FP64: re and
                           im); 11: as 10, operands staged by cp.async one direction ahead
                           (fundamental, adjoint FP64 with quaternion links); 12, 13: 10,
-                          11 for fundamental FP64 capped at 96 registers; 14: fundamental
+                          11 for fundamental FP64 capped at 96 registers (12 for adjoint
+                          FP64: 10 with up to 168 registers); 14: fundamental
                           binary16 with the spin projection in half2 arithmetic (only the
                           projected half spinor is widened to FP32, the neighbour's scale
                           rides on the accumulating FMAs); 15: as 14, 64 registers; 16:
                           fundamental FP32 / binary16 with two sites per thread, one in
                           each lane of the packed f32x2 FMAs; 17: as 16, 96 registers;
                           18, 19: 14, 15 with the next direction's operands staged by
-                          cp.async in shared memory */
+                          cp.async in shared memory.  The FP64 results of 8-13 are
+                          bit-identical to those of 0. */
     int block;         /* threads per block                                               */
     double best_ms;    /* time of one hop launch with the chosen shape (median of 4)      */
     double default_ms; /* the same for the shape in use before tuning                     */

@@ -239,7 +239,9 @@ bool hop_variant_available(int rep, int prec, int variant)
     // FP64 ((re, im) lanes; staged for quaternion links only)
     if (variant == kVarPaired) return rep == HR_FUND || prec == HR_F64;
     if (variant == kVarPairedStaged) return rep == HR_FUND || (rep == HR_ADJ && prec == HR_F64);
-    if (variant == kVarPairedR96 || variant == kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
+    // 12 for the adjoint FP64 hop: the paired kernel with up to 168 registers
+    if (variant == kVarPairedR96) return prec == HR_F64;
+    if (variant == kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
     // the half2-projection kernels: fundamental binary16 only
     if (variant == kVarHalf || variant == kVarHalfR64 || variant == kVarHalfStaged || variant == kVarHalfStagedR64)
         return rep == HR_FUND && prec == HR_F16;

@@ -432,6 +432,66 @@ template <int C> __device__ __forceinline__ dd2 cx_pow_i(const K2 &k, const dd2 
     }
 }
 
+// the value sg c x of a product in its prod2 form, sg a lane pair of powers of
+// two (exact); nsg = -sg
+__device__ __forceinline__ dd2 prod2_scaled(const K2 &k, const prod2 &p, float2 nsg, float2 sg)
+{
+    return {__ffma2_rn(p.P, nsg, k.zero), __ffma2_rn(p.L, sg, k.zero)};
+}
+// r + sg c x lane by lane for a product in its prod2 form (sg a power of two
+// per lane, nsg = -sg): add2v on the exactly scaled product
+__device__ __forceinline__ dd2 acc_prod2v(const K2 &k, const dd2 &r, const prod2 &p, float2 nsg, float2 sg)
+{
+    const float2 s = __ffma2_rn(p.P, nsg, r.h);
+    const float2 w = __ffma2_rn(s, k.mone, r.h);
+    const float2 t = __ffma2_rn(w, k.one, s);
+    const float2 da = __ffma2_rn(t, k.mone, r.h);
+    const float2 db = __ffma2_rn(p.P, nsg, w);
+    const float2 e = __ffma2_rn(da, k.one, db);
+    const float2 lo = __ffma2_rn(p.L, sg, r.l);
+    return {s, __ffma2_rn(e, k.one, lo)};
+}
+__device__ __forceinline__ dd2 dup2(const dd &x) { return {make_float2(x.h, x.h), make_float2(x.l, x.l)}; }
+__device__ __forceinline__ dd lane_x(const dd2 &v) { return dd(v.h.x, v.l.x); }
+__device__ __forceinline__ dd lane_y(const dd2 &v) { return dd(v.h.y, v.l.y); }
+
+// R(q) from the packed quaternion (hi parts qh, lo parts ql) with the scalar
+// quat_to_adj's operations, two entries per f32x2 instruction where the
+// entries pair up: the squares (a0^2, a1^2), (a2^2, a3^2); (a0^2 - a2^2,
+// a1^2 + a3^2) for w; the diagonal pair (R11, R22); the products a1 (a2, a3)
+// and a0 (a3, a2), which give (R01, R02) and (R10, R20); (R12, R21).  Each
+// lane does the scalar operation on the same operands, so R is bit-identical
+// to the scalar rebuild's.
+__device__ __forceinline__ void quat_to_adj_x2(const K2 &k, const float4 &qh, const float4 &ql, dd (&R)[3][3])
+{
+    const bool neg = sign_bit(qh.x);
+    const float s2 = neg ? -2.f : 2.f;
+    const dd2 q01 = {make_float2(qh.x, qh.y), make_float2(ql.x, ql.y)};
+    const dd2 q23 = {make_float2(qh.z, qh.w), make_float2(ql.z, ql.w)};
+    const dd2 q32 = {make_float2(qh.w, qh.z), make_float2(ql.w, ql.z)};
+    const prod2 p01 = mul2(k, q01, make_float2(-qh.x, -qh.y), q01);
+    const prod2 p23 = mul2(k, q23, make_float2(-qh.z, -qh.w), q23);
+    const dd2 s01 = prod2_scaled(k, p01, k.mone, k.one), s23 = prod2_scaled(k, p23, k.mone, k.one);
+    const dd2 d = add2v(k, s01, s23, k.mp); // (a0^2 - a2^2, a1^2 + a3^2)
+    dd w = lane_x(d) - lane_y(d);
+    if (neg) w = -w;
+    R[0][0] = w + scale_pow2(lane_y(s01), s2);
+    const dd2 r12 = add2v(k, dup2(w), s23, make_float2(s2, s2));
+    R[1][1] = lane_x(r12);
+    R[2][2] = lane_y(r12);
+    const dd a0(qh.x, ql.x), a1(qh.y, ql.y), a2(qh.z, ql.z), a3(qh.w, ql.w);
+    const prod2 x = mul2(k, dup2(a1), make_float2(-a1.h, -a1.h), q23); // a1 (a2, a3)
+    const prod2 y = mul2(k, dup2(a0), make_float2(-a0.h, -a0.h), q32); // a0 (a3, a2)
+    const dd2 xs = prod2_scaled(k, x, make_float2(-s2, -s2), make_float2(s2, s2));
+    const dd2 u = acc_prod2v(k, xs, y, make_float2(-s2, s2), make_float2(s2, -s2));
+    const dd2 v = acc_prod2v(k, xs, y, make_float2(s2, -s2), make_float2(-s2, s2));
+    R[0][1] = lane_x(u); R[0][2] = lane_y(u);
+    R[1][0] = lane_x(v); R[2][0] = lane_y(v);
+    const dd m23 = scale_pow2(a2 * a3, s2), m01 = a0 * a1;
+    const dd2 t = add2v(k, dup2(m23), dup2(m01), make_float2(s2, -s2));
+    R[1][2] = lane_x(t); R[2][1] = lane_y(t);
+}
+
 // r_t,b = sum_c M_bc h_t,c for both half-spinor components t at one output
 // colour b, M = R (forward) or R^T (backward), in the scalar kernel's order
 template <bool FWD, int B>
@@ -496,12 +556,13 @@ __device__ __forceinline__ void x2a_compute(const K2 &k, const float4 (&w)[12], 
 }
 
 template <int REP>
-__device__ __forceinline__ void x2a_link(const HopArgs &a, int link_par, int mu, int site_link, dd (&R)[3][3])
+__device__ __forceinline__ void x2a_link(const HopArgs &a, const K2 &k, int link_par, int mu, int site_link,
+                                         dd (&R)[3][3])
 {
     if constexpr (REP == kRepAdj) {
-        dd q[4];
-        load_quat<kF64>(a.gauge, a.g.nblk_g, link_par, mu, site_link, q);
-        quat_to_adj(q, R);
+        const size_t slot = (size_t)(link_par * 4 + mu) * a.g.nblk_g + (site_link >> 5);
+        const float4 *q = (const float4 *)a.gauge + slot * 64 + (site_link & 31);
+        quat_to_adj_x2(k, __ldg(q), __ldg(q + 32), R);
     } else {
         load_mat<kF64>(a.gauge, a.g.nblk_g, link_par, mu, site_link, R);
     }
@@ -516,7 +577,7 @@ __device__ __forceinline__ void x2a_term(const HopArgs &a, const K2 &k, int site
 #pragma unroll
     for (int v = 0; v < 12; ++v) w[v] = __ldg(sp + vec_index(j_nb, v, 12));
     dd R[3][3];
-    x2a_link<REP>(a, link_par, MU, site_link, R);
+    x2a_link<REP>(a, k, link_par, MU, site_link, R);
     x2a_compute<MU, FWD, FIRST, NEG>(k, w, R, acc);
 }
 
@@ -586,9 +647,8 @@ __device__ __forceinline__ void x2a_stage_step(const HopArgs &a, const K2 &k, in
     for (int v = 0; v < 12; ++v) w[v] = *reinterpret_cast<const float4 *>(cur + v * bd);
     const float4 qh = *reinterpret_cast<const float4 *>(cur + 12 * bd);
     const float4 ql = *reinterpret_cast<const float4 *>(cur + 13 * bd);
-    const dd q[4] = {dd(qh.x, ql.x), dd(qh.y, ql.y), dd(qh.z, ql.z), dd(qh.w, ql.w)};
     dd R[3][3];
-    quat_to_adj(q, R);
+    quat_to_adj_x2(k, qh, ql, R);
     x2a_compute<(K >> 1), (K & 1) == 0, K == 0, NEG>(k, w, R, acc);
 }
 
@@ -636,6 +696,10 @@ __device__ __forceinline__ void x2as_body(const HopArgs &a)
 }
 
 template <int REP, int G5IN> __global__ void __maxnreg__(128) k_hop_x2a(HopArgs a) { x2a_body<REP, G5IN>(a); }
+// the same with up to 168 registers: no spills (the 128-register form spills
+// about 100 bytes a thread for the quaternion links), 12 warps an SM at
+// blocks of 64, 128 or 192 threads
+template <int REP, int G5IN> __global__ void __maxnreg__(168) k_hop_x2a_big(HopArgs a) { x2a_body<REP, G5IN>(a); }
 template <int G5IN> __global__ void __launch_bounds__(256) k_hop_x2as(HopArgs a) { x2as_body<G5IN>(a); }
 
 template <int REP, int PREC> struct Launch {
@@ -662,8 +726,14 @@ template <int REP, int PREC> struct Launch {
             return true;
         } else if constexpr (PREC == kF64) {
             // adjoint (quaternion or stored 3x3 links): (re, im) lanes
-            if (c.variant != kVarPaired && c.variant != kVarPairedStaged) return false;
+            if (c.variant != kVarPaired && c.variant != kVarPairedStaged && c.variant != kVarPairedR96) return false;
             const bool g5 = a.g5_in != 0;
+            if (c.variant == kVarPairedR96) {
+                // for the adjoint: the form with 168 registers
+                (g5 ? k_hop_x2a_big<REP, 1> : k_hop_x2a_big<REP, 0>)<<<grid, c.block, 0, s>>>(a);
+                st = check_launch(ctx, "paired adjoint hop kernel (168 registers)");
+                return true;
+            }
             if constexpr (REP == kRepAdj) {
                 if (c.variant == kVarPairedStaged) {
                     using S = Stage<kRepAdj, kF64>;

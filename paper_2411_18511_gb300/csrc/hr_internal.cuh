@@ -772,19 +772,34 @@ __device__ __forceinline__ bool sign_bit(const dd &x) { return sign_bit(x.h); }
 // negated when the sign bit of a0 is set: R(q) = R(-q), and the packed
 // adjoint links keep that bit clear except on an antiperiodic boundary slice,
 // where it carries the factor -1 of the boundary condition
+// exact multiplication by a power of two (+-2 here): both parts of a pair scale
+__device__ __forceinline__ float scale_pow2(float x, float s) { return x * s; }
+__device__ __forceinline__ double scale_pow2(double x, float s) { return x * s; }
+__device__ __forceinline__ dd scale_pow2(const dd &x, float s) { return dd(x.h * s, x.l * s); }
+
 template <class T> __device__ __forceinline__ void quat_to_adj(const T (&a)[4], T (&R)[3][3])
 {
-    // the sign s enters through the factors: every term of R has one of them
-    // (s w on the diagonal, 2 s a_k and 2 s a0 in the products), so no extra
-    // value stays live
+    // The sign s enters as -w and as the factor 2 s of every product term.
+    // Four squares give w = (a0^2 - a2^2) - (a1^2 + a3^2) and the diagonal
+    // s w + 2 s a_k^2; the off-diagonal entries come in pairs that share
+    // their two products (R_ab and R_ba hold 2 s a_a a_b + and - 2 s a0 a_c),
+    // so six products serve the six entries.  The doublings are exact.  The
+    // paired adjoint kernels build the same entries two at a time on f32x2
+    // lanes with these operations in this order (bit-identical results).
     const bool neg = sign_bit(a[0]);
-    const float two = neg ? -2.f : 2.f;
-    T w = a[0] * a[0] - (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+    const float s2 = neg ? -2.f : 2.f;
+    const T sq0 = a[0] * a[0], sq1 = a[1] * a[1], sq2 = a[2] * a[2], sq3 = a[3] * a[3];
+    T w = (sq0 - sq2) - (sq1 + sq3);
     if (neg) w = -w;
-    T b1 = two * a[1], b2 = two * a[2], b3 = two * a[3], c = two * a[0];
-    R[0][0] = w + b1 * a[1]; R[0][1] = b1 * a[2] + c * a[3]; R[0][2] = b1 * a[3] - c * a[2];
-    R[1][0] = b2 * a[1] - c * a[3]; R[1][1] = w + b2 * a[2]; R[1][2] = b2 * a[3] + c * a[1];
-    R[2][0] = b3 * a[1] + c * a[2]; R[2][1] = b3 * a[2] - c * a[1]; R[2][2] = w + b3 * a[3];
+    R[0][0] = w + scale_pow2(sq1, s2);
+    R[1][1] = w + scale_pow2(sq2, s2);
+    R[2][2] = w + scale_pow2(sq3, s2);
+    const T m12 = scale_pow2(a[1] * a[2], s2), m13 = scale_pow2(a[1] * a[3], s2);
+    const T m03 = scale_pow2(a[0] * a[3], s2), m02 = scale_pow2(a[0] * a[2], s2);
+    const T m23 = scale_pow2(a[2] * a[3], s2), m01 = scale_pow2(a[0] * a[1], s2);
+    R[0][1] = m12 + m03; R[0][2] = m13 - m02;
+    R[1][0] = m12 - m03; R[2][0] = m13 + m02;
+    R[1][2] = m23 + m01; R[2][1] = m23 - m01;
 }
 
 // ---------------------------------------------------------------- colour algebra

@@ -121,13 +121,15 @@ def _forced_context(tmp_path, monkeypatch, name, dims, reps, precs, n_rhs, varia
                                            (11, 192), (12, 64), (13, 128)])
 def test_variant_bitwise_equals_plain(tmp_path, monkeypatch, variant, block, n_rhs):
     """The bulk-copy tiled kernels (8, 9) take the near-direction neighbours
-    from shared memory, the paired kernels (10-13) run two colours per f32x2
-    instruction; in double-float all form every sum in the plain kernel's
-    order, so every operator (hop, Schur, normal: g5 inputs, aux terms, fused
-    norms) must agree bit for bit (FP32 paired: to rounding), on a lattice
-    whose tiles straddle rows, wraps and a ragged end."""
+    from shared memory, the paired kernels (10-13) run two colours (adjoint:
+    re and im) per f32x2 instruction and rebuild the adjoint links two entries
+    at a time; in double-float all form every sum
+    in the plain kernel's order, so every operator (hop, Schur, normal: g5
+    inputs, aux terms, fused norms) must agree bit for bit (FP32 paired: to
+    rounding), on a lattice whose tiles straddle rows, wraps and a ragged end,
+    for quaternion and stored-matrix adjoint links."""
     dims = (4, 6, 6, 10)  # h3 = 5, 360 sites per parity
-    reps, precs = (hr.HR_FUND, hr.HR_ADJ), (hr.HR_F64, hr.HR_F32)
+    reps, precs = (hr.HR_FUND, hr.HR_ADJ, hr.HR_ADJ_MAT), (hr.HR_F64, hr.HR_F32)
     base = _forced_context(tmp_path, monkeypatch, "plain", dims, reps, precs, n_rhs, 0, 128)
     tiled = _forced_context(tmp_path, monkeypatch, "tiled", dims, reps, precs, n_rhs, variant, block)
     for rep in reps:
