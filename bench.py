@@ -62,7 +62,8 @@ HOP_VARIANT_NAMES = ["unrolled", "unrolled cp.async staged", "generic loop", "ge
                      "binary16, half2 projection", "binary16, half2 projection, 64 registers",
                      "two sites per thread (f32x2 lanes)", "two sites per thread (f32x2 lanes), 96 registers",
                      "binary16, half2 projection, cp.async staged",
-                     "binary16, half2 projection, cp.async staged, 64 registers"]
+                     "binary16, half2 projection, cp.async staged, 64 registers",
+                     "2 right-hand sides per thread", "4 right-hand sides per thread"]
 
 
 def variant_name(rep, variant):
@@ -174,7 +175,7 @@ def kernel_source_hash() -> str:
     csrc = os.path.join(ROOT, "paper_2411_18511_gb300", "csrc")
     for f in ("hr_internal.cuh", "hr_clover.cuh", "hr_host.h", "hr_hop_dev.cuh", "hr_hop_fam.h", "hr_hop_x2.cuh",
               "hr_hop.cu", "hr_hop_staged.cu", "hr_hop_loop.cu", "hr_hop_tile.cu", "hr_hop_x2.cu", "hr_hop_half.cu",
-              "hr_hop_p2.cu"):
+              "hr_hop_p2.cu", "hr_hop_chunk.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -593,8 +593,11 @@ typedef struct {
                           fundamental FP32 / binary16 with two sites per thread, one in
                           each lane of the packed f32x2 FMAs; 17: as 16, 96 registers;
                           18, 19: 14, 15 with the next direction's operands staged by
-                          cp.async in shared memory.  The FP64 results of 8-13 are
-                          bit-identical to those of 0. */
+                          cp.async in shared memory; 20, 21: fundamental FP32 /
+                          binary16 with n_rhs >= 2 / 4, a chunk of 2 / 4 right-hand
+                          sides per thread sharing the site's neighbour indices and
+                          links.  The FP64 results of 8-13 are bit-identical to
+                          those of 0. */
     int block;         /* threads per block                                               */
     double best_ms;    /* time of one hop launch with the chosen shape (median of 4)      */
     double default_ms; /* the same for the shape in use before tuning                     */

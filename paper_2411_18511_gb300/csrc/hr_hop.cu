@@ -12,7 +12,8 @@
 //
 // This file holds the plain unrolled kernels (variants 0 and 7), the dispatch
 // over all variants (the other families are in hr_hop_staged.cu, hr_hop_loop.cu,
-// hr_hop_tile.cu, hr_hop_x2.cu, hr_hop_half.cu and hr_hop_p2.cu; hr_hop_fam.h lists them; lattices with
+// hr_hop_tile.cu, hr_hop_x2.cu, hr_hop_half.cu, hr_hop_p2.cu and hr_hop_chunk.cu;
+// hr_hop_fam.h lists them; lattices with
 // twisted boundaries take the kernel of hr_hop_twist.cu), the operators built
 // from hops and their C ABI.  The autotuner (hr_tune.cu) picks variant and
 // block size per configuration.
@@ -157,6 +158,8 @@ hr_status dispatch(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs 
     case kVarHalfStagedR64: done = launch_hop_half(ctx, g, rep, prec, a, c, grid, s, st); break;
     case kVarPairSites:
     case kVarPairSitesR96: done = launch_hop_pair_sites(ctx, g, rep, prec, a, c, grid, s, st); break;
+    case kVarRhsChunk2:
+    case kVarRhsChunk4: done = launch_hop_chunk(ctx, g, rep, prec, a, c, grid, s, st); break;
     default: break;
     }
     // the plain kernels: variants 0 and 7, and any variant without a kernel here
@@ -232,13 +235,15 @@ hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const H
     return dispatch(ctx, g, rep, prec, make_args(ctx, g, L), c, s);
 }
 
-bool hop_variant_available(int rep, int prec, int variant)
+bool hop_variant_available(int rep, int prec, int variant, int nrhs)
 {
-    (void)prec;
     // the paired kernels: fundamental (colour lanes) at every precision, adjoint
     // FP64 ((re, im) lanes; staged for quaternion links only)
     if (variant == kVarPaired) return rep == HR_FUND || prec == HR_F64;
     if (variant == kVarPairedStaged) return rep == HR_FUND || (rep == HR_ADJ && prec == HR_F64);
+    // 20, 21: chunks of 2 / 4 right-hand sides per thread
+    if (variant == kVarRhsChunk2) return rep == HR_FUND && prec != HR_F64 && nrhs >= 2;
+    if (variant == kVarRhsChunk4) return rep == HR_FUND && prec != HR_F64 && nrhs >= 4;
     // 12 for the adjoint FP64 hop: the paired kernel with up to 168 registers
     if (variant == kVarPairedR96) return prec == HR_F64;
     if (variant == kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;

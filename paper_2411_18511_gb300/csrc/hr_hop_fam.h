@@ -11,6 +11,8 @@
 //                     (compiler's registers / 64); 18, 19 the same, cp.async staged
 //   hr_hop_p2.cu      16, 17 fundamental FP32 / binary16, two sites per thread in
 //                     the lanes of packed f32x2 FMAs (compiler's registers / 96)
+//   hr_hop_chunk.cu   20, 21 fundamental FP32 / binary16, a chunk of 2 / 4
+//                     right-hand sides per thread sharing the site's links
 // All compute the same operator; the autotuner picks per configuration.
 #pragma once
 
@@ -39,9 +41,11 @@ enum HopVariant : int {
     kVarPairSites = 16,
     kVarPairSitesR96 = 17,
     kVarHalfStaged = 18,
-    kVarHalfStagedR64 = 19
+    kVarHalfStagedR64 = 19,
+    kVarRhsChunk2 = 20,
+    kVarRhsChunk4 = 21
 };
-static_assert(kVarHalfStagedR64 + 1 == kNumHopVariants, "variant list");
+static_assert(kVarRhsChunk4 + 1 == kNumHopVariants, "variant list");
 
 // per-thread shared-memory slots of the cp.async staged variants (1, 3, 5, 11, 13)
 template <int REP, int PREC> struct Stage {
@@ -112,6 +116,8 @@ bool launch_hop_half(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArg
                      cudaStream_t s, hr_status &st);
 bool launch_hop_pair_sites(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs &a, HopChoice c, int grid,
                            cudaStream_t s, hr_status &st);
+bool launch_hop_chunk(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs &a, HopChoice c, int grid,
+                      cudaStream_t s, hr_status &st);
 // the paired staged kernel with the clover epilogue (fundamental FP64)
 void launch_hop_clover_paired(hr_ctx *ctx, const HopArgs &a, int grid, int block, cudaStream_t s, hr_status &st);
 // the kernel of lattices with twisted boundaries (hr_hop_twist.cu): every

@@ -27,60 +27,6 @@ using namespace hr;
 
 namespace {
 
-// acc (+)= i^C sc z
-template <int C, bool FIRST>
-__device__ __forceinline__ void acc_scaled(cpx<float> &acc, const cpx<float> &z, float sc)
-{
-    if constexpr (FIRST) {
-        if constexpr (C == 0) acc = {sc * z.re, sc * z.im};
-        else if constexpr (C == 1) acc = {-sc * z.im, sc * z.re};
-        else if constexpr (C == 2) acc = {-sc * z.re, -sc * z.im};
-        else acc = {sc * z.im, -sc * z.re};
-    } else {
-        if constexpr (C == 0) acc = {__fmaf_rn(sc, z.re, acc.re), __fmaf_rn(sc, z.im, acc.im)};
-        else if constexpr (C == 1) acc = {__fmaf_rn(-sc, z.im, acc.re), __fmaf_rn(sc, z.re, acc.im)};
-        else if constexpr (C == 2) acc = {__fmaf_rn(-sc, z.re, acc.re), __fmaf_rn(-sc, z.im, acc.im)};
-        else acc = {__fmaf_rn(sc, z.im, acc.re), __fmaf_rn(-sc, z.re, acc.im)};
-    }
-}
-
-// One direction's arithmetic from the neighbour's two packed words w0, w1, its
-// scale sc and the link q (binary16, widened): acc (+)= (1 -/+ g_mu) U psi
-// (FWD: U_mu(x), else U_mu(x - mu)^+).  NEG: the input's upper spins are
-// negated (g5 in); as in the paired kernels the sign moves from the
-// projection to the rebuild.
-template <int MU, bool FWD, bool FIRST, bool NEG>
-__device__ __forceinline__ void h16_compute(const uint4 &w0, const uint4 &w1, float sc, const float (&q)[4],
-                                            cpx<float> (&acc)[4][2])
-{
-    using D = X2Dir<MU, FWD>;
-    constexpr int F = NEG ? 2 : 0;
-    // spin t: word 2t = (c0.re, c1.re), word 2t+1 = (c0.im, c1.im)
-    const uint32_t u[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-    __half2 h0re, h0im, h1re, h1im;
-    h2_project<(D::c0 + F) & 3>(as_h2(u[0]), as_h2(u[1]), as_h2(u[2 * D::pi0]), as_h2(u[2 * D::pi0 + 1]), h0re, h0im);
-    h2_project<(D::c1 + F) & 3>(as_h2(u[2]), as_h2(u[3]), as_h2(u[2 * D::pi1]), as_h2(u[2 * D::pi1 + 1]), h1re, h1im);
-    cpx<float> h[2][2];
-    {
-        const float2 r0 = __half22float2(h0re), i0 = __half22float2(h0im);
-        const float2 r1 = __half22float2(h1re), i1 = __half22float2(h1im);
-        h[0][0] = {r0.x, i0.x};
-        h[0][1] = {r0.y, i0.y};
-        h[1][0] = {r1.x, i1.x};
-        h[1][1] = {r1.y, i1.y};
-    }
-    cpx<float> r[2][2];
-    su2_mul<!FWD>(q, h[0], r[0]);
-    su2_mul<!FWD>(q, h[1], r[1]);
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        acc_scaled<F, FIRST>(acc[0][c], r[0][c], sc);
-        acc_scaled<F, FIRST>(acc[1][c], r[1][c], sc);
-        acc_scaled<(D::d0 + F) & 3, FIRST>(acc[2][c], r[D::rho0][c], sc);
-        acc_scaled<(D::d1 + F) & 3, FIRST>(acc[3][c], r[D::rho1][c], sc);
-    }
-}
-
 // the neighbour and link loaded from global memory
 template <int MU, bool FWD, bool FIRST, bool NEG>
 __device__ __forceinline__ void h16_term(const HopArgs &a, const float *nrm, int site_link, int link_par, int jn,

@@ -28,7 +28,7 @@ struct HopChoice {
     int variant; // kernel variant, 0 .. kNumHopVariants-1 (hr_hop.cu)
     int block;   // threads per block
 };
-constexpr int kNumHopVariants = 20;
+constexpr int kNumHopVariants = 22;
 } // namespace hr
 
 struct hr_ctx {
@@ -137,7 +137,7 @@ hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const H
                           cudaStream_t s);
 HopChoice hop_choice(hr_ctx *ctx, const Geom &g, int rep, int prec);
 std::string tune_key(const Geom &g, int rep, int prec);
-bool hop_variant_available(int rep, int prec, int variant);
+bool hop_variant_available(int rep, int prec, int variant, int nrhs);
 // autotuner cache file (hr_tune.cu)
 void tune_cache_load(hr_ctx *ctx);
 bool tune_cache_save(hr_ctx *ctx);

@@ -104,7 +104,7 @@ hr_status hr_autotune_hop(hr_ctx *ctx, hr_lattice lat, hr_rep rep, hr_prec prec,
     std::vector<HopChoice> cands;
     cands.push_back(def);
     for (int v = 0; v < kNumHopVariants; ++v) {
-        if (!hop_variant_available(rep, prec, v)) continue;
+        if (!hop_variant_available(rep, prec, v, g.nrhs)) continue;
         for (int b : blocks) {
             if (v == def.variant && b == def.block) continue;
             cands.push_back(HopChoice{v, b});
