@@ -582,7 +582,8 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
         del gp, src, dst
     xp = fields.zeros_spinor(d32, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
     sols = {"cg_32": {"dims": d32, "q": q32, "b": b, "x": {}}}
-    for name, inner, deltas in (("fp64", hr.HR_F64, (0.1,)), ("mixed_f32", hr.HR_F32, (0.1, 1e-2, 1e-3)),
+    for name, inner, deltas in (("fp64", hr.HR_F64, (0.1,)),
+                                ("mixed_f32", hr.HR_F32, (0.1, 1e-2, 1e-3, 1e-4, 1e-5)),
                                 ("mixed_f16", hr.HR_F16, (0.1, 3e-2, 1e-2))):
         sweep = {}
         best = None
@@ -925,7 +926,7 @@ def run_multi_rhs(ctx, torch, hr, fields, synth):
     gauge = fields.pack_gauge(ctx, d, hr.HR_FUND, hr.HR_F64, fields.gauge_to_device(q))
     g32 = fields.pack_gauge(ctx, d, hr.HR_FUND, hr.HR_F32, fields.gauge_to_device(q))
     res = {"lattice": list(d), "m0": -0.2, "tol": 1e-10, "plaquette": round(plaq, 4), "inner": "f32",
-           "reliable_delta": 1e-3}
+           "reliable_delta": 1e-5}
     sols = {"dims": d, "q": q, "n": {}}
     t1 = None
     for n in (1, 4, 8, 16, 32):
@@ -934,7 +935,7 @@ def run_multi_rhs(ctx, torch, hr, fields, synth):
         bp = fields.pack_spinor(ctx, d, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, dev)
         opts = hr.hr_solver_default_opts()
         opts.inner_prec = hr.HR_F32
-        opts.reliable_delta = 1e-3  # the FP32-inner setting that wins at 32^4 (cg_32): fewer FP64 updates
+        opts.reliable_delta = 1e-5  # the FP32-inner setting that wins at 32^4 (cg_32): fewer FP64 updates
         opts.n_rhs = n
         # the solver's hop shapes (FP32 inner, FP64 reliable updates) tuned for this N
         tuned = {}

@@ -174,6 +174,7 @@ def cg32(ctx):
 
 
 @pytest.mark.parametrize("inner,delta", [(hr.HR_F64, 0.1), (hr.HR_F32, 0.1), (hr.HR_F32, 1e-2), (hr.HR_F32, 1e-3),
+                                         (hr.HR_F32, 1e-4), (hr.HR_F32, 1e-5),
                                          (hr.HR_F16, 0.1), (hr.HR_F16, 3e-2), (hr.HR_F16, 1e-2)])
 def test_cg_32_matches_oracle(ctx, cg32, inner, delta):
     opts = hr.hr_solver_default_opts()
@@ -200,10 +201,12 @@ def test_cg_32_matches_oracle(ctx, cg32, inner, delta):
 
 # ---------------------------------------------------------------------- 24^4 x 32 RHS
 
-def test_cg_24_multi_rhs_32_matches_oracle(ctx):
+@pytest.mark.parametrize("delta", [0.1, 1e-5])
+def test_cg_24_multi_rhs_32_matches_oracle(ctx, delta):
     """The multi-RHS configuration: 24^4 smeared links (seed 1004), 32 Gaussian
     sources (seed 2004), FP32 inner / FP64 outer CG with the hop shapes tuned
-    for 32 right-hand sides, every right-hand side checked by the oracle."""
+    for 32 right-hand sides, at the default reliable_delta and at the
+    benchmark's, every right-hand side checked by the oracle."""
     n = 32
     q, _, plaq = synth.ape_smear_to_plaquette(synth.haar_links(D24, 1004), D24, 0.6)
     bs = synth.gaussian_spinor(D24, 2, 2004, n_rhs=n)
@@ -221,6 +224,7 @@ def test_cg_24_multi_rhs_32_matches_oracle(ctx):
     del dev
     opts = hr.hr_solver_default_opts()
     opts.inner_prec = hr.HR_F32
+    opts.reliable_delta = delta
     opts.n_rhs = n
     work = fields.empty_bytes(hr.hr_cg_workspace_bytes(D24, hr.HR_FUND, opts))
     xp = fields.zeros_spinor(D24, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, n)

@@ -75,7 +75,7 @@ CASES = [((4, 6, 6, 10), 2), ((2, 4, 6, 6), 4), ((4, 6, 6, 10), 4), ((4, 6, 2, 6
 
 
 @pytest.mark.parametrize("prec", [hr.HR_F32, hr.HR_F16])
-@pytest.mark.parametrize("variant,block", [(20, 64), (20, 256), (21, 128), (21, 32)])
+@pytest.mark.parametrize("variant,block", [(20, 64), (20, 256), (21, 128), (21, 192), (21, 32)])
 @pytest.mark.parametrize("dims,n_rhs", CASES, ids=[f"{d[0]}x{d[1]}x{d[2]}x{d[3]}_n{n}" for d, n in CASES])
 def test_rhs_chunk_every_operator(tmp_path, monkeypatch, dims, n_rhs, variant, block, prec):
     q = synth.haar_links(dims, 83)
@@ -153,4 +153,32 @@ def test_rhs_chunk_inner_cg(tmp_path, monkeypatch, inner, n_rhs, variant):
     for r in range(n_rhs):
         res = np.linalg.norm(bs[r] - oracle.normal(dims, L, -0.2, xs[r])) / np.linalg.norm(bs[r])
         assert res <= 1e-10, (r, res)
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [hr.HR_F32, hr.HR_F16])
+def test_autotune_with_several_rhs_includes_the_chunks(tmp_path, monkeypatch, prec):
+    """With 4 right-hand sides the tuner also times the chunk kernels; whatever
+    it picks, the tuned hop matches the oracle for every right-hand side."""
+    dims = (8, 8, 8, 8)
+    n_rhs = 4
+    monkeypatch.setenv("HR_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    c = hr.Context(0)
+    q = synth.haar_links(dims, 95)
+    psi = synth.gaussian_spinor(dims, 2, 96, n_rhs=n_rhs)
+    gauge = fields.pack_gauge(c, dims, hr.HR_FUND, prec, fields.gauge_to_device(q))
+    src = fields.pack_spinor(c, dims, hr.HR_FUND, prec, hr.HR_ODD, fields.spinor_to_device(psi))
+    dst = fields.empty_spinor(dims, hr.HR_FUND, prec, hr.HR_EVEN, n_rhs)
+    res = hr.hr_autotune_hop(c, dims, hr.HR_FUND, prec, hr.HR_EVEN, n_rhs, gauge, src, dst, reps=3)
+    one = hr.hr_autotune_hop(c, dims, hr.HR_FUND, prec, hr.HR_EVEN, 1, gauge, src, dst, reps=3)
+    # two more shapes (variants 20 and 21) at each of the four block sizes
+    assert res.candidates >= one.candidates + 8 - 1
+    assert hr.hr_tune_lookup(c, dims, hr.HR_FUND, prec, n_rhs) == (res.variant, res.block)
+    hr.hr_dirac_eo(c, dims, 0.0, hr.HR_FUND, prec, hr.HR_EVEN, hr.HR_OP_HOP, n_rhs, gauge, src, dst)
+    got = fields.unpack_spinor(c, dims, hr.HR_FUND, prec, hr.HR_EVEN, dst, n_rhs).cpu().numpy()
+    L = oracle.expand_links(dims, 2, q)
+    m = oracle.parity_mask(dims) == 0
+    for r in range(n_rhs):
+        want = -0.5 * oracle.hop(dims, L, psi[r], parity=0)
+        assert rel(got[r][m], want[m]) <= TOL[prec], r
     c.close()
