@@ -63,7 +63,9 @@ HOP_VARIANT_NAMES = ["unrolled", "unrolled cp.async staged", "generic loop", "ge
                      "two sites per thread (f32x2 lanes)", "two sites per thread (f32x2 lanes), 96 registers",
                      "binary16, half2 projection, cp.async staged",
                      "binary16, half2 projection, cp.async staged, 64 registers",
-                     "2 right-hand sides per thread", "4 right-hand sides per thread"]
+                     "2 right-hand sides per thread", "4 right-hand sides per thread",
+                     "binary16, half2 projection, register prefetch, 80 registers",
+                     "binary16, half2 projection, register prefetch two directions ahead, 96 registers"]
 
 
 def variant_name(rep, variant):

@@ -596,8 +596,10 @@ typedef struct {
                           cp.async in shared memory; 20, 21: fundamental FP32 /
                           binary16 with n_rhs >= 2 / 4, a chunk of 2 / 4 right-hand
                           sides per thread sharing the site's neighbour indices and
-                          links.  The FP64 results of 8-13 are bit-identical to
-                          those of 0. */
+                          links; 22, 23: 14 with the next one / two directions'
+                          operands loaded into registers ahead (80 / 96 registers).
+                          The FP64 results of 8-13 are bit-identical to those
+                          of 0. */
     int block;         /* threads per block                                               */
     double best_ms;    /* time of one hop launch with the chosen shape (median of 4)      */
     double default_ms; /* the same for the shape in use before tuning                     */

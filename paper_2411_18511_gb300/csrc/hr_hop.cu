@@ -155,7 +155,9 @@ hr_status dispatch(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopArgs 
     case kVarHalf:
     case kVarHalfR64:
     case kVarHalfStaged:
-    case kVarHalfStagedR64: done = launch_hop_half(ctx, g, rep, prec, a, c, grid, s, st); break;
+    case kVarHalfStagedR64:
+    case kVarHalfPrefetch:
+    case kVarHalfPrefetch2: done = launch_hop_half(ctx, g, rep, prec, a, c, grid, s, st); break;
     case kVarPairSites:
     case kVarPairSitesR96: done = launch_hop_pair_sites(ctx, g, rep, prec, a, c, grid, s, st); break;
     case kVarRhsChunk2:
@@ -248,7 +250,8 @@ bool hop_variant_available(int rep, int prec, int variant, int nrhs)
     if (variant == kVarPairedR96) return prec == HR_F64;
     if (variant == kVarPairedStagedR96) return rep == HR_FUND && prec == HR_F64;
     // the half2-projection kernels: fundamental binary16 only
-    if (variant == kVarHalf || variant == kVarHalfR64 || variant == kVarHalfStaged || variant == kVarHalfStagedR64)
+    if (variant == kVarHalf || variant == kVarHalfR64 || variant == kVarHalfStaged || variant == kVarHalfStagedR64 ||
+        variant == kVarHalfPrefetch || variant == kVarHalfPrefetch2)
         return rep == HR_FUND && prec == HR_F16;
     // two sites per thread: fundamental FP32 and binary16
     if (variant == kVarPairSites || variant == kVarPairSitesR96) return rep == HR_FUND && prec != HR_F64;

@@ -8,7 +8,8 @@
 //   hr_hop_x2.cu      10-13 fundamental FP64 on packed f32x2 FMAs (registers /
 //                     cp.async staged, compiler's registers / 96)
 //   hr_hop_half.cu    14, 15 fundamental binary16 with the projection in half2
-//                     (compiler's registers / 64); 18, 19 the same, cp.async staged
+//                     (compiler's registers / 64); 18, 19 the same, cp.async staged;
+//                     22, 23 with register prefetch one / two directions ahead
 //   hr_hop_p2.cu      16, 17 fundamental FP32 / binary16, two sites per thread in
 //                     the lanes of packed f32x2 FMAs (compiler's registers / 96)
 //   hr_hop_chunk.cu   20, 21 fundamental FP32 / binary16, a chunk of 2 / 4
@@ -43,9 +44,11 @@ enum HopVariant : int {
     kVarHalfStaged = 18,
     kVarHalfStagedR64 = 19,
     kVarRhsChunk2 = 20,
-    kVarRhsChunk4 = 21
+    kVarRhsChunk4 = 21,
+    kVarHalfPrefetch = 22,
+    kVarHalfPrefetch2 = 23
 };
-static_assert(kVarRhsChunk4 + 1 == kNumHopVariants, "variant list");
+static_assert(kVarHalfPrefetch2 + 1 == kNumHopVariants, "variant list");
 
 // per-thread shared-memory slots of the cp.async staged variants (1, 3, 5, 11, 13)
 template <int REP, int PREC> struct Stage {

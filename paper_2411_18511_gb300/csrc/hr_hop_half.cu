@@ -1,5 +1,5 @@
 // hr_hop_half.cu -- the binary16 fundamental hop with the spin projection in
-// half2 arithmetic (variants 14, 15, 18, 19).
+// half2 arithmetic (variants 14, 15, 18, 19, 22, 23).
 //
 // The FP16 hop moves 136 bytes per output site (the neighbour spinors as
 // binary16 with one FP32 scale per site, binary16 quaternion links), so at
@@ -19,7 +19,9 @@
 // arithmetic kernels to the storage precision, not bit for bit.
 //
 // Variant 14: registers as the compiler likes; 15: capped at 64 registers;
-// 18, 19: the same with the next direction's operands staged by cp.async.
+// 18, 19: the same with the next direction's operands staged by cp.async;
+// 22, 23: with the operands of the next direction (80 registers) or of the
+// next two (96 registers) loaded into registers ahead of the arithmetic.
 #include "hr_hop_fam.h"
 #include "hr_hop_x2.cuh"
 
@@ -72,6 +74,82 @@ __device__ __forceinline__ void h16_body(const HopArgs &a)
         h16_dir<1, false, NEG>(a, nrm, i, rr, nb, acc);
         h16_dir<2, false, NEG>(a, nrm, i, rr, nb, acc);
         h16_dir<3, false, NEG>(a, nrm, i, rr, nb, acc);
+        hop_epilogue<kF16>(a, j, acc, al, be, bu, red);
+    }
+    if (a.fin) {
+        __shared__ double smem[32 * 32];
+        __shared__ double sums[32];
+        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+    }
+}
+
+// Register-prefetch form: direction K+1's two spinor words, scale and link
+// are loaded into registers before direction K is computed, so each thread
+// keeps one direction's loads in flight behind its arithmetic.
+struct H16Ops {
+    uint4 w0, w1;
+    float sc;
+    uint2 q;
+};
+
+template <int K>
+__device__ __forceinline__ void h16_fetch(const HopArgs &a, const float *nrm, int i, int rr, const SiteNb &nb,
+                                          H16Ops &o)
+{
+    constexpr int MU = K >> 1;
+    constexpr bool FWD = (K & 1) == 0;
+    const int jn = ((FWD ? nb.fwd[MU] : nb.bwd[MU]) << a.g.lrhs) + rr;
+    const int sl = FWD ? i : nb.bwd[MU];
+    const int lp = FWD ? a.p : 1 - a.p;
+    const uint4 *sp = (const uint4 *)a.in;
+    o.w0 = __ldg(sp + vec_index(jn, 0, 2));
+    o.w1 = __ldg(sp + vec_index(jn, 1, 2));
+    o.sc = __ldg(nrm + jn);
+    o.q = __ldg((const uint2 *)quat_addr<kF16>(a.gauge, a.g.nblk_g, lp, MU, sl, 0));
+}
+
+// direction K from buf[K % (D + 1)] after queueing the loads of direction K + D
+template <int K, int D, bool NEG>
+__device__ __forceinline__ void h16p_step(const HopArgs &a, const float *nrm, int i, int rr, const SiteNb &nb,
+                                          H16Ops (&buf)[D + 1], cpx<float> (&acc)[4][2])
+{
+    if constexpr (K + D < 8) h16_fetch<K + D>(a, nrm, i, rr, nb, buf[(K + D) % (D + 1)]);
+    const H16Ops &cur = buf[K % (D + 1)];
+    const float2 q01 = __half22float2(as_h2(cur.q.x)), q23 = __half22float2(as_h2(cur.q.y));
+    const float q[4] = {q01.x, q01.y, q23.x, q23.y};
+    h16_compute<(K >> 1), (K & 1) == 0, K == 0, NEG>(cur.w0, cur.w1, cur.sc, q, acc);
+}
+
+// D: how many directions ahead the loads run (1 or 2)
+template <int D, int G5IN>
+__device__ __forceinline__ void h16p_body(const HopArgs &a)
+{
+    constexpr bool NEG = G5IN != 0;
+    if ((a.gate && *a.gate == 0.0) || (a.done && *a.done != 0.0)) return;
+    const Geom &g = a.g;
+    const int nv = g.vh << g.lrhs;
+    const int stride = gridDim.x * blockDim.x;
+    const float *nrm = (const float *)((const char *)a.in + SpinorLayout<2, kF16>::data_bytes(g.nblk_s));
+    const float be = a.beta.h;
+    const float bu = a.g5_out ? -be : be;
+    const float al = a.alpha.h;
+    SqAcc<float> red;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += stride) {
+        const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
+        SiteNb nb;
+        site_neighbours(g, i, a.p, nb);
+        H16Ops buf[D + 1];
+        h16_fetch<0>(a, nrm, i, rr, nb, buf[0]);
+        if constexpr (D > 1) h16_fetch<1>(a, nrm, i, rr, nb, buf[1]);
+        cpx<float> acc[4][2];
+        h16p_step<0, D, NEG>(a, nrm, i, rr, nb, buf, acc);
+        h16p_step<1, D, NEG>(a, nrm, i, rr, nb, buf, acc);
+        h16p_step<2, D, NEG>(a, nrm, i, rr, nb, buf, acc);
+        h16p_step<3, D, NEG>(a, nrm, i, rr, nb, buf, acc);
+        h16p_step<4, D, NEG>(a, nrm, i, rr, nb, buf, acc);
+        h16p_step<5, D, NEG>(a, nrm, i, rr, nb, buf, acc);
+        h16p_step<6, D, NEG>(a, nrm, i, rr, nb, buf, acc);
+        h16p_step<7, D, NEG>(a, nrm, i, rr, nb, buf, acc);
         hop_epilogue<kF16>(a, j, acc, al, be, bu, red);
     }
     if (a.fin) {
@@ -153,6 +231,8 @@ template <int G5IN> __global__ void __launch_bounds__(256) k_hop_h16(HopArgs a) 
 template <int G5IN> __global__ void __maxnreg__(64) k_hop_h16_r64(HopArgs a) { h16_body<G5IN>(a); }
 template <int G5IN> __global__ void __launch_bounds__(256) k_hop_h16s(HopArgs a) { h16s_body<G5IN>(a); }
 template <int G5IN> __global__ void __maxnreg__(64) k_hop_h16s_r64(HopArgs a) { h16s_body<G5IN>(a); }
+template <int G5IN> __global__ void __maxnreg__(80) k_hop_h16p_r80(HopArgs a) { h16p_body<1, G5IN>(a); }
+template <int G5IN> __global__ void __maxnreg__(96) k_hop_h16p2_r96(HopArgs a) { h16p_body<2, G5IN>(a); }
 
 } // namespace
 
@@ -176,6 +256,10 @@ bool launch_hop_half(hr_ctx *ctx, const Geom &, int rep, int prec, const HopArgs
         else (g5 ? k_hop_h16s<1> : k_hop_h16s<0>)<<<grid, c.block, sm, s>>>(a);
     } else if (c.variant == kVarHalfR64) {
         (g5 ? k_hop_h16_r64<1> : k_hop_h16_r64<0>)<<<grid, c.block, 0, s>>>(a);
+    } else if (c.variant == kVarHalfPrefetch) {
+        (g5 ? k_hop_h16p_r80<1> : k_hop_h16p_r80<0>)<<<grid, c.block, 0, s>>>(a);
+    } else if (c.variant == kVarHalfPrefetch2) {
+        (g5 ? k_hop_h16p2_r96<1> : k_hop_h16p2_r96<0>)<<<grid, c.block, 0, s>>>(a);
     } else {
         (g5 ? k_hop_h16<1> : k_hop_h16<0>)<<<grid, c.block, 0, s>>>(a);
     }

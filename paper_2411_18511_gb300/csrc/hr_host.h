@@ -28,7 +28,7 @@ struct HopChoice {
     int variant; // kernel variant, 0 .. kNumHopVariants-1 (hr_hop.cu)
     int block;   // threads per block
 };
-constexpr int kNumHopVariants = 22;
+constexpr int kNumHopVariants = 24;
 } // namespace hr
 
 struct hr_ctx {

@@ -1,7 +1,7 @@
 """The binary16 hop with the spin projection in half2 arithmetic (kernel
-variants 14, 15 and their cp.async-staged forms 18, 19), forced through the
-tuning cache, against the FP64 oracle and against the FP32-arithmetic
-binary16 kernel.
+variants 14, 15, their cp.async-staged forms 18, 19 and register-prefetch
+forms 22, 23), forced through the tuning cache, against the FP64 oracle and
+against the FP32-arithmetic binary16 kernel.
 
 Tolerances: the stored binary16 components carry a relative rounding of 2^-11
 of their site's largest component; the half2 projection adds one more such
@@ -70,7 +70,8 @@ def oracle_op(lat, L, psi, op, par):
 
 
 @pytest.mark.parametrize("n_rhs", [1, 4])
-@pytest.mark.parametrize("variant,block", [(14, 64), (14, 128), (15, 256), (18, 64), (18, 192), (19, 128)])
+@pytest.mark.parametrize("variant,block", [(14, 64), (14, 128), (15, 256), (18, 64), (18, 192), (19, 128),
+                                           (22, 64), (23, 128)])
 def test_half_variant_every_operator(tmp_path, monkeypatch, variant, block, n_rhs):
     q = synth.haar_links(DIMS, 61)
     psi = synth.gaussian_spinor(DIMS, 2, 62, n_rhs=n_rhs) if n_rhs > 1 else synth.gaussian_spinor(DIMS, 2, 62)
@@ -91,7 +92,7 @@ def test_half_variant_every_operator(tmp_path, monkeypatch, variant, block, n_rh
     half.close()
 
 
-@pytest.mark.parametrize("variant", [14, 15, 18, 19])
+@pytest.mark.parametrize("variant", [14, 15, 18, 19, 22, 23])
 def test_half_variant_antiperiodic(tmp_path, monkeypatch, variant):
     lat = hr.Lattice(DIMS, 15)
     c = forced(tmp_path, monkeypatch, "bc", lat, variant, 128)
@@ -110,7 +111,7 @@ def test_half_variant_antiperiodic(tmp_path, monkeypatch, variant):
     c.close()
 
 
-@pytest.mark.parametrize("variant", [14, 15, 18, 19])
+@pytest.mark.parametrize("variant", [14, 15, 18, 19, 22, 23])
 def test_half_variant_inner_cg(tmp_path, monkeypatch, variant):
     """FP16-inner mixed-precision CG with the half2 kernel as its inner hop."""
     dims = (8, 8, 8, 8)

@@ -52,7 +52,7 @@ def key(dims, rep, prec, n_rhs=1):
                                            (8, 64), (8, 128), (8, 256), (9, 64), (9, 128), (10, 64),
                                            (10, 256), (11, 64), (11, 256), (12, 128), (13, 128), (14, 64),
                                            (14, 256), (15, 128), (15, 256), (16, 64), (16, 256), (17, 128), (18, 64),
-                                           (18, 256), (19, 128)])
+                                           (18, 256), (19, 128), (22, 64), (23, 256)])
 def test_forced_shapes_from_cache_match_oracle(tmp_path, monkeypatch, variant, block):
     dims = (6, 4, 2, 6)  # 144 sites per parity: ragged last block of 32
     cache = tmp_path / "tune.json"
@@ -84,7 +84,7 @@ def test_autotune_chooses_and_persists(tmp_path, monkeypatch, rep, prec):
     src = fields.pack_spinor(c, dims, rep, prec, hr.HR_ODD, fields.spinor_to_device(psi))
     dst = fields.empty_spinor(dims, rep, prec, hr.HR_EVEN)
     res = hr.hr_autotune_hop(c, dims, rep, prec, hr.HR_EVEN, 1, gauge, src, dst, reps=5)
-    assert res.variant in range(22) and res.block in (64, 128, 192, 256)
+    assert res.variant in range(24) and res.block in (64, 128, 192, 256)
     # the winner is the best median of four timings of the fastest shapes
     assert res.candidates >= 4 and 0 < res.best_ms <= 1.1 * res.default_ms
     assert hr.hr_tune_lookup(c, dims, rep, prec) == (res.variant, res.block)
@@ -202,7 +202,7 @@ def _gauge_padding_bytes(dims, prec):
 
 @pytest.mark.parametrize("variant,block", [(0, 64), (1, 128), (2, 64), (4, 128), (6, 128), (7, 64), (8, 64),
                                            (10, 64), (11, 128), (14, 64), (15, 128), (16, 64), (17, 128), (18, 64),
-                                           (19, 128)])
+                                           (19, 128), (22, 64), (23, 128)])
 def test_padding_lanes_are_never_read(tmp_path, monkeypatch, variant, block):
     """NaN canaries in the padding lanes of the ragged last block (inputs and
     links) must not reach any output: every kernel variant reads only real
