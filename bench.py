@@ -773,7 +773,8 @@ def run_clover_48(ctx, torch, hr, fields, q48, psi48, reps=30):
 
 def run_twist_48(ctx, torch, hr, fields, q48, psi48, reps=30):
     """48^4 fund FP64 hop with twisted boundaries (theta in time only, and in
-    all four directions): the separate, untuned kernel that applies the phase,
+    all four directions): the twisted kernel (paired double-float, one launch
+    shape, the phase on the projected doublets of boundary-crossing hops),
     against the tuned untwisted hop on the same fields (512 B per site)."""
     dims = DIMS
     Vh = int(np.prod(dims)) // 2
