@@ -536,10 +536,14 @@ def time_hop(ctx, torch, hr, fields, dims, rep, prec, q, psi, steps=100, peak=No
     rname = "fund" if rep == hr.HR_FUND else "adj"
     pname = {hr.HR_F64: "f64", hr.HR_F32: "f32", hr.HR_F16: "f16"}[prec]
     b = hop_bytes_per_site(rname, pname)
+    nb = neighbour_bytes_per_site(rname, pname)
     if rep == hr.HR_ADJ_MAT:
-        b += 8 * ({"f64": 72, "f32": 36, "f16": 18}[pname] - {"f64": 32, "f32": 16, "f16": 8}[pname])
+        extra = 8 * ({"f64": 72, "f32": 36, "f16": 18}[pname] - {"f64": 32, "f32": 16, "f16": 8}[pname])
+        b += extra
+        nb += extra
     gbs = Vh * b / (ms * 1e-3) / 1e9
     out = {"ms": round(ms, 5), "gbs": round(gbs, 1), "bytes_per_site": b,
+           "gbs_neighbour_counted": round(Vh * nb / (ms * 1e-3) / 1e9, 1),
            "gflops": round(Vh * HOP_FLOPS[rname] / (ms * 1e-3) / 1e9, 1),
            "pct_of_nominal_8000": round(100 * gbs / HBM_NOMINAL_GBS, 1),
            "launch": {"variant": variant_name(rep, res.variant), "block": res.block}}
