@@ -590,7 +590,7 @@ def run_extras(ctx, torch, hr, fields, synth, q48, psi48):
     sols = {"cg_32": {"dims": d32, "q": q32, "b": b, "x": {}}}
     for name, inner, deltas in (("fp64", hr.HR_F64, (0.1,)),
                                 ("mixed_f32", hr.HR_F32, (0.1, 1e-2, 1e-3, 1e-4, 1e-5)),
-                                ("mixed_f16", hr.HR_F16, (0.1, 3e-2, 1e-2))):
+                                ("mixed_f16", hr.HR_F16, (0.1, 3e-2, 1e-2, 3e-3))):
         sweep = {}
         best = None
         for delta in deltas:

@@ -59,40 +59,6 @@ __global__ void __launch_bounds__(kBS) k_norm2(Geom g, const void *v, RedSlot re
     if (grid_reduce(acc.get(), g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
 }
 
-// x += alpha p ; r -= alpha q ; |r|^2 -> fin (kFinBeta / kFinBetaMixed)
-template <int NC, int PX, int PP, int PR, int PQ>
-__global__ void __launch_bounds__(kBS) k_xr(Geom g, void *x, const void *p, void *r, const void *q, RedSlot red,
-                                            double *scal, int fin)
-{
-    using T = typename Wider<RT<PX>, RT<PR>>::T;
-    if (sc(scal, S_FLAGS, F_DONE) != 0.0) return;
-    const int nv = g.vh << g.lrhs;
-    const T al = Real<T>::from_double(sc(scal, S_ALPHA, thread_rhs(g)));
-    SqAcc<T> acc;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
-        cpx<T> xv[4][NC], pv[4][NC], rv[4][NC], qv[4][NC];
-        load_spinor<NC, PX>(x, g.nblk_s, j, xv);
-        load_spinor<NC, PP>(p, g.nblk_s, j, pv);
-        load_spinor<NC, PR>(r, g.nblk_s, j, rv);
-        load_spinor<NC, PQ>(q, g.nblk_s, j, qv);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                xv[a][c].re += al * pv[a][c].re;
-                xv[a][c].im += al * pv[a][c].im;
-                rv[a][c].re -= al * qv[a][c].re;
-                rv[a][c].im -= al * qv[a][c].im;
-            }
-        store_spinor<NC, PX>(x, g.nblk_s, j, xv);
-        store_spinor<NC, PR>(r, g.nblk_s, j, rv);
-        acc_site<NC>(acc, rv);
-    }
-    __shared__ double smem[32 * 32];
-    __shared__ double sums[32];
-    if (grid_reduce(acc.get(), g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
-}
-
 // p = r + beta p
 template <int NC, int PP, int PR>
 __global__ void __launch_bounds__(kBS) k_p(Geom g, void *p, const void *r, const double *scal)
@@ -348,23 +314,6 @@ hr_status blas_norm2(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *
     RedSlot red = red_slot(ctx, C_NORM);
     HR_DISPATCH_NC(rep, HR_DISPATCH_P(prec, P, (k_norm2<NC, P><<<grid, kBS, 0, s>>>(g, v, red, ctx->d_scal, fin))));
     return check_launch(ctx, "norm2");
-}
-
-hr_status blas_xr(hr_ctx *ctx, const Geom &g, int rep, int px, int pp, int pr, int pq, void *x, const void *p, void *r,
-                  const void *q, cudaStream_t s)
-{
-    int grid = grid_cap(ctx, g);
-    RedSlot red = red_slot(ctx, C_XR);
-    if (px == kF64 && pp == kF64 && pr == kF64 && pq == kF64) {
-        HR_DISPATCH_NC(rep, (k_xr<NC, kF64, kF64, kF64, kF64><<<grid, kBS, 0, s>>>(g, x, p, r, q, red, ctx->d_scal, kFinBeta)));
-    } else if (px == kF32 && pp == kF32 && pr == kF32 && pq == kF32) {
-        HR_DISPATCH_NC(rep, (k_xr<NC, kF32, kF32, kF32, kF32><<<grid, kBS, 0, s>>>(g, x, p, r, q, red, ctx->d_scal, kFinBetaMixed)));
-    } else if (px == kF32 && pp == kF16 && pr == kF16 && pq == kF16) {
-        HR_DISPATCH_NC(rep, (k_xr<NC, kF32, kF16, kF16, kF16><<<grid, kBS, 0, s>>>(g, x, p, r, q, red, ctx->d_scal, kFinBetaMixed)));
-    } else {
-        return set_error(ctx, HR_ERR_UNSUPPORTED, "xr precision combination");
-    }
-    return check_launch(ctx, "xr update");
 }
 
 hr_status blas_p(hr_ctx *ctx, const Geom &g, int rep, int pp, int pr, void *p, const void *r, cudaStream_t s)

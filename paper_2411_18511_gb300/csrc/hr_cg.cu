@@ -182,24 +182,17 @@ struct Solver {
     hr_status part_a()
     {
         const double *done = flag_ptr(ctx, F_DONE);
-        hr_status st;
         if (!mixed()) {
             // q = A p with the x/r update and |r|^2 fused into the last hop
             const CgFuse fz{x, p64, r64, kFinBeta};
             return apply_eo_op(ctx, g, m0, rep, kF64, HR_OP_NORMAL, gauge, p64, q64, t64, u64, kFinAlpha, nullptr,
                                done, s, &fz, clov64);
         }
-        const int P = o.inner_prec;
-        if (P == kF32) {
-            // x_lo, p, r are all FP32: fused as above
-            const CgFuse fz{x_lo, p_lo, r_lo, kFinBetaMixed};
-            return apply_eo_op(ctx, g, m0, rep, P, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha,
-                               nullptr, done, s, &fz, clov_lo);
-        }
-        st = apply_eo_op(ctx, g, m0, rep, P, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha, nullptr,
-                         done, s, nullptr, clov_lo);
-        if (!st) st = blas_xr(ctx, g, rep, kF32, P, P, P, x_lo, p_lo, r_lo, q_lo, s);
-        return st;
+        // p, r in the inner precision, x_lo in FP32: fused as above (the
+        // last hop's epilogue updates x_lo and r from q in registers)
+        const CgFuse fz{x_lo, p_lo, r_lo, kFinBetaMixed};
+        return apply_eo_op(ctx, g, m0, rep, o.inner_prec, HR_OP_NORMAL, gauge_lo, p_lo, q_lo, t_lo, u_lo, kFinAlpha,
+                           nullptr, done, s, &fz, clov_lo);
     }
 
     // x += x_lo, r = b - A x in FP64, restart the low-precision residual;
@@ -555,14 +548,22 @@ hr_status cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_
                 break;
         }
         if (numeric) break;
-        if (sv.mixed()) {
-            // fold the pending low-precision increment into x
-            st = blas_accum(ctx, sv.g, rep, kF32, x, sv.x_lo, nullptr, s);
+        // A mixed solve normally stops inside a reliable update: the recurrence's
+        // convergence opens the gate, and only the FP64 residual it recomputes
+        // stops a right-hand side.  Its x_lo is then folded into x and S_OUT
+        // holds |b - A x|^2 for the x being returned, so the same residual is
+        // not computed twice.  Otherwise (maxiter, the FP64 solver) compute it.
+        const bool have_true = sv.mixed() && ctx->h_scal[F_TRUERES] != 0.0;
+        if (!have_true) {
+            if (sv.mixed()) {
+                // fold the pending low-precision increment into x
+                st = blas_accum(ctx, sv.g, rep, kF32, x, sv.x_lo, nullptr, s);
+                if (st) return st;
+            }
+            // true FP64 residual per RHS
+            st = sv.true_residual(kFinStore);
             if (st) return st;
         }
-        // true FP64 residual per RHS
-        st = sv.true_residual(kFinStore);
-        if (st) return st;
         st = read_scalars(ctx, 0, S_NSLOTS, s);
         if (st) return st;
         worst = 0.0;

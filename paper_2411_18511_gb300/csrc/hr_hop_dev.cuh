@@ -167,10 +167,13 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<
         if (a.clov_mode == kClovOut) clover_apply<CP>(a.clov, j >> a.g.lrhs, o);
     if (a.cg_r) {
         // the CG's x/r update on this site, with q = o in registers (the
-        // vector kernel's arithmetic, in the hop's precision)
+        // vector kernel's arithmetic, in the hop's precision); the binary16
+        // solver keeps its x increment in FP32, and r -= alpha q takes q
+        // before any rounding to binary16
+        constexpr int PX = PREC == kF16 ? kF32 : PREC;
         const T alr = Real<T>::from_double(a.scal[S_ALPHA * kMaxRhsSlots + (j & (a.g.nrhs - 1))]);
         cpx<T> xv[4][NC], pv[4][NC], rv[4][NC];
-        load_spinor<NC, PREC>(a.cg_x, a.g.nblk_s, j, xv);
+        load_spinor<NC, PX>(a.cg_x, a.g.nblk_s, j, xv);
         load_spinor<NC, PREC>(a.cg_p, a.g.nblk_s, j, pv);
         load_spinor<NC, PREC>(a.cg_r, a.g.nblk_s, j, rv);
 #pragma unroll
@@ -184,7 +187,7 @@ __device__ __forceinline__ void hop_epilogue(const HopArgs &a, int j, const cpx<
                 red.add(rv[s][c].re);
                 red.add(rv[s][c].im);
             }
-        store_spinor<NC, PREC>(a.cg_x, a.g.nblk_s, j, xv);
+        store_spinor<NC, PX>(a.cg_x, a.g.nblk_s, j, xv);
         store_spinor<NC, PREC>(a.cg_r, a.g.nblk_s, j, rv);
         return;
     }

@@ -125,7 +125,8 @@ struct HopLaunch {
     const void *clov;
     int clov_mode;
 };
-// a CG x/r update fused into the last hop of an operator (same precision)
+// a CG x/r update fused into the last hop of an operator (the operator's
+// precision; x in FP32 when the operator runs in binary16)
 struct CgFuse {
     void *x;
     const void *p;
@@ -160,8 +161,6 @@ hr_status clover_apply_half(hr_ctx *ctx, const Geom &g, int rep, int prec, const
 
 // ---- BLAS launches (hr_blas.cu) ----
 hr_status blas_norm2(hr_ctx *ctx, const Geom &g, int rep, int prec, const void *v, int fin, cudaStream_t s);
-hr_status blas_xr(hr_ctx *ctx, const Geom &g, int rep, int px, int pp, int pr, int pq, void *x, const void *p,
-                  void *r, const void *q, cudaStream_t s);
 hr_status blas_p(hr_ctx *ctx, const Geom &g, int rep, int pp, int pr, void *p, const void *r, cudaStream_t s);
 hr_status blas_convert(hr_ctx *ctx, const Geom &g, int rep, int psrc, int pdst, const void *src, void *dst,
                        const double *gate, cudaStream_t s);

@@ -1031,14 +1031,16 @@ enum ScalSlot {
     S_OUT = 9,     // generic reduction output
     S_FLAGS = 10,  // [0] all done, [1] reliable-update gate, [2] NaN/Inf seen, [3] iterations,
                    // [4] reliable updates, [5] device-loop passes, [6] device error (a
-                   // bulk copy that did not land in time)
+                   // bulk copy that did not land in time), [7] source out of range,
+                   // [8] S_OUT holds the true FP64 residuals of the current x (the
+                   // last scalar update was a reliable update's)
     S_DELTA2 = 11, // [0] reliable-update threshold delta^2, [1] tol^2, [2] maxiter (<= 0: none)
     S_SCALE = 12,  // per-RHS power of two that brings the source's largest component into [0.5, 1)
     S_BMAX = 13,   // per-RHS largest |component| of the source, as the bits of a float (32 unsigned)
     S_NSLOTS = 14
 };
 constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4, F_BODY = 5, F_DEVERR = 6,
-              F_RANGE = 7;
+              F_RANGE = 7, F_TRUERES = 8;
 
 enum FinishMode {
     kFinNone = 0,
@@ -1130,6 +1132,11 @@ __device__ inline void finish_reduction(int mode, const double *sums, int nrhs, 
         if (mode == kFinResidual) {
             sc(scal, S_FLAGS, F_GATE) = 0.0;
             sc(scal, S_FLAGS, F_NRELIABLE) += 1.0;
+            // x_lo was folded into x and S_OUT = |b - A x|^2: a loop that stops
+            // here needs no further true-residual computation
+            sc(scal, S_FLAGS, F_TRUERES) = 1.0;
+        } else if (mode == kFinBeta || mode == kFinBetaMixed || mode == kFinInit) {
+            sc(scal, S_FLAGS, F_TRUERES) = 0.0; // x (or x_lo) moved since
         }
     }
 }
