@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kBS) k_norm2(Geom g, const void *v, RedSlot re
     }
     __shared__ double smem[32 * 32];
     __shared__ double sums[32];
-    if (grid_reduce(acc.get(), g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
+    if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
 }
 
 // p = r + beta p
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kBS) k_residual(Geom g, const void *b, const v
     }
     __shared__ double smem[32 * 32];
     __shared__ double sums[32];
-    if (grid_reduce(acc.get(), g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
+    if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
 }
 
 // x_hi += x_lo ; x_lo = 0

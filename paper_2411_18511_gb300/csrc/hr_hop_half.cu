@@ -79,7 +79,7 @@ __device__ __forceinline__ void h16_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -155,7 +155,7 @@ __device__ __forceinline__ void h16p_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -223,7 +223,7 @@ __device__ __forceinline__ void h16s_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_hop_loop(HopArgs a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) k_hop_sw(HopArgs a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(128) k_hop_twist(HopArgs a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -240,7 +240,7 @@ __device__ __forceinline__ void x2t_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 

@@ -77,7 +77,7 @@ __device__ __forceinline__ void x2s_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -109,7 +109,7 @@ __device__ __forceinline__ void x2_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -305,7 +305,7 @@ __device__ __forceinline__ void f2_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -397,7 +397,7 @@ __device__ __forceinline__ void f2s_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -624,7 +624,7 @@ __device__ __forceinline__ void x2a_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 
@@ -691,7 +691,7 @@ __device__ __forceinline__ void x2as_body(const HopArgs &a)
     if (a.fin) {
         __shared__ double smem[32 * 32];
         __shared__ double sums[32];
-        if (grid_reduce(red.get(), g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
+        if (grid_reduce(red, g.nrhs, a.red, sums, smem)) finish_reduction(a.fin, sums, g.nrhs, a.scal);
     }
 }
 

@@ -965,20 +965,46 @@ __device__ inline void sum_partials(const double *partials, unsigned nparts, int
     __syncthreads();
 }
 
-template <int MAXW = 32>
-__device__ inline bool grid_reduce(double v, int nrhs, RedSlot slot, double *sums, double *smem /* >= 32*32 */)
+// The warp stage of a grid reduction in the accumulator's own arithmetic:
+// FP32 sums add as floats, double-float sums as pairs on the FP32 pipes (this
+// GPU's FP64 unit runs at a small fraction of the FP32 rate, and a reducing
+// hop would otherwise convert and shuffle a double on every thread); the
+// warp's total becomes a double once.  Lanes r < nrhs return right-hand side
+// r's total (the same butterfly order as warp_sum_strided: deterministic).
+__device__ __forceinline__ double warp_total(const SqAcc<float> &a, int nrhs)
+{
+    float v = a.s;
+    for (int off = 16; off >= nrhs; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return (double)v;
+}
+__device__ __forceinline__ double warp_total(const SqAcc<dd> &a, int nrhs)
+{
+    dd v = a.s;
+    for (int off = 16; off >= nrhs; off >>= 1)
+        v += dd(__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off));
+    return dd_to_double(v);
+}
+__device__ __forceinline__ double warp_total(const SqAcc<double> &a, int nrhs)
+{
+    return warp_sum_strided(a.s, nrhs);
+}
+
+// grid_reduce from per-warp totals (lanes r < nrhs hold right-hand side r's)
+__device__ inline bool grid_reduce_warped(double v, int nrhs, RedSlot slot, double *sums, double *smem)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    v = warp_sum_strided(v, nrhs);
     if (lane < nrhs) smem[warp * 32 + lane] = v;
     __syncthreads();
     if (threadIdx.x < nrhs) {
         double s = 0;
         for (int w = 0; w < nwarps; ++w) s += smem[w * 32 + threadIdx.x];
         slot.partials[(size_t)blockIdx.x * nrhs + threadIdx.x] = s;
+        // only the writers of the partials order them before the block's
+        // count: a fence on every thread would hold each block until its
+        // output stores had drained
+        __threadfence();
     }
     __shared__ bool last;
-    __threadfence();
     __syncthreads();
     unsigned nparts = gridDim.x;
     const double *parts = slot.partials;
@@ -995,9 +1021,11 @@ __device__ inline bool grid_reduce(double v, int nrhs, RedSlot slot, double *sum
         if (!last) return false;
         __threadfence();
         sum_partials(slot.partials + (size_t)first * nrhs, gsize, nrhs, sums, smem);
-        if (threadIdx.x < nrhs) slot.group_partials[(size_t)grp * nrhs + threadIdx.x] = sums[threadIdx.x];
+        if (threadIdx.x < nrhs) {
+            slot.group_partials[(size_t)grp * nrhs + threadIdx.x] = sums[threadIdx.x];
+            __threadfence();
+        }
         if (threadIdx.x == 0) slot.group_counters[grp] = 0u;
-        __threadfence();
         __syncthreads();
         nparts = (gridDim.x + kRedGroup - 1) / kRedGroup;
         parts = slot.group_partials;
@@ -1012,6 +1040,18 @@ __device__ inline bool grid_reduce(double v, int nrhs, RedSlot slot, double *sum
     sum_partials(parts, nparts, nrhs, sums, smem);
     if (threadIdx.x == 0) *slot.counter = 0u;
     return true;
+}
+
+// Deterministic grid reduction of a value per thread (see RedSlot)
+__device__ inline bool grid_reduce(double v, int nrhs, RedSlot slot, double *sums, double *smem /* >= 32*32 */)
+{
+    return grid_reduce_warped(warp_sum_strided(v, nrhs), nrhs, slot, sums, smem);
+}
+// ... and of a sum-of-squares accumulator per thread, warp stage in its own arithmetic
+template <class T>
+__device__ inline bool grid_reduce(const SqAcc<T> &acc, int nrhs, RedSlot slot, double *sums, double *smem)
+{
+    return grid_reduce_warped(warp_total(acc, nrhs), nrhs, slot, sums, smem);
 }
 
 // ---------------------------------------------------------------- solver scalars

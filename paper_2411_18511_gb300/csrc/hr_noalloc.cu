@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_norm2_noalloc(Geom g, const void *v, No
     slot.counter = &scr->counter;
     slot.group_counters = nullptr; // one level: the fixed scratch has no group slots
     slot.group_partials = nullptr;
-    if (grid_reduce(acc.get(), g.nrhs, slot, sums, smem)) {
+    if (grid_reduce(acc, g.nrhs, slot, sums, smem)) {
         if (threadIdx.x < g.nrhs) result[threadIdx.x] = sums[threadIdx.x];
     }
 }
