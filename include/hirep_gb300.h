@@ -243,7 +243,15 @@ size_t hr_cg_workspace_bytes(hr_lattice lat, hr_rep rep, const hr_solver_opts *o
 /* Solve Mhat^+ Mhat x = b on even sites by CG (Sec. 1 "inverters"; the
  * even-odd preconditioned operator of Sec. 2.1).  gauge: packed HR_F64 gauge
  * of `rep`; b, x: packed HR_F64 even spinors (n_rhs of them).  Low-precision
- * gauge copies for the mixed solver are made inside `work`.  Synchronises the
+ * gauge copies for the mixed solver are made inside `work`.  Mixed precision
+ * follows the reliable-update scheme: the inner recurrence runs in
+ * inner_prec, and whenever |r| falls by reliable_delta the residual is
+ * recomputed from the accumulated solution.  With HR_F16 inner, that
+ * recomputation is FP32 (r_ref - A x_mid, x_mid the correction since the
+ * last FP64 residual r_ref) until |r| has fallen by 1e-4 from r_ref, and FP64
+ * (r = b - A x) then and at convergence; HR_F32 inner always recomputes in
+ * FP64.  A right-hand side stops only on its FP64 residual, and
+ * info->n_reliable_updates counts the FP64 recomputations.  Synchronises the
  * stream before returning (it reads the residuals); info may be NULL.
  * Every right-hand side is rescaled inside `work` by the power of two that
  * brings its largest component into [0.5, 1) (exact: the iterates are the

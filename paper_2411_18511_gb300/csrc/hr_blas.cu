@@ -93,7 +93,9 @@ __global__ void __launch_bounds__(kBS) k_convert(Geom g, const void *src, void *
 }
 
 // r = b - ax (FP64 fields) ; |r|^2 -> fin ; optionally r_lo = r in precision PL
-template <int NC, int PL>
+// r = b - ax in FP64 (b FP64, ax FP64 or FP32; r nullable: not stored), |r|^2 -> fin,
+// and r_lo = r in the inner precision PL
+template <int NC, int PL, int PA>
 __global__ void __launch_bounds__(kBS) k_residual(Geom g, const void *b, const void *ax, void *r, RedSlot red,
                                                   double *scal, int fin, const double *gate, void *r_lo)
 {
@@ -104,12 +106,12 @@ __global__ void __launch_bounds__(kBS) k_residual(Geom g, const void *b, const v
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
         cpx<T> bv[4][NC], av[4][NC];
         load_spinor<NC, kF64>(b, g.nblk_s, j, bv);
-        load_spinor<NC, kF64>(ax, g.nblk_s, j, av);
+        load_spinor<NC, PA>(ax, g.nblk_s, j, av);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int c = 0; c < NC; ++c) bv[a][c] = csub(bv[a][c], av[a][c]);
-        store_spinor<NC, kF64>(r, g.nblk_s, j, bv);
+        if (r) store_spinor<NC, kF64>(r, g.nblk_s, j, bv);
         if (PL != kF64 && r_lo) store_spinor<NC, PL>(r_lo, g.nblk_s, j, bv);
         acc_site<NC>(acc, bv);
     }
@@ -118,16 +120,16 @@ __global__ void __launch_bounds__(kBS) k_residual(Geom g, const void *b, const v
     if (grid_reduce(acc, g.nrhs, red, sums, smem)) finish_reduction(fin, sums, g.nrhs, scal);
 }
 
-// x_hi += x_lo ; x_lo = 0
-template <int NC, int PL>
+// x_hi += x_lo ; x_lo = 0  (x_hi FP64 or FP32)
+template <int NC, int PH, int PL>
 __global__ void __launch_bounds__(kBS) k_accum(Geom g, void *xhi, void *xlo, const double *gate)
 {
-    using T = RT<kF64>;
+    using T = RT<PH>;
     if (gate && *gate == 0.0) return;
     const int nv = g.vh << g.lrhs;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += gridDim.x * blockDim.x) {
         cpx<T> h[4][NC], l[4][NC];
-        load_spinor<NC, kF64>(xhi, g.nblk_s, j, h);
+        load_spinor<NC, PH>(xhi, g.nblk_s, j, h);
         load_spinor<NC, PL>(xlo, g.nblk_s, j, l);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(kBS) k_accum(Geom g, void *xhi, void *xlo, con
                 h[a][c] = cadd(h[a][c], l[a][c]);
                 l[a][c] = {T(0.f), T(0.f)};
             }
-        store_spinor<NC, kF64>(xhi, g.nblk_s, j, h);
+        store_spinor<NC, PH>(xhi, g.nblk_s, j, h);
         store_spinor<NC, PL>(xlo, g.nblk_s, j, l);
     }
 }
@@ -339,21 +341,29 @@ hr_status blas_convert(hr_ctx *ctx, const Geom &g, int rep, int psrc, int pdst, 
 }
 
 hr_status blas_residual(hr_ctx *ctx, const Geom &g, int rep, const void *b, const void *ax, void *r, int fin,
-                        const double *gate, int plo, void *r_lo, cudaStream_t s)
+                        const double *gate, int plo, void *r_lo, cudaStream_t s, int pax)
 {
     int grid = grid_cap(ctx, g);
     RedSlot red = red_slot(ctx, C_RES);
     if (!r_lo) plo = kF64;
-    HR_DISPATCH_NC(rep, HR_DISPATCH_P(plo, P, (k_residual<NC, P><<<grid, kBS, 0, s>>>(g, b, ax, r, red, ctx->d_scal, fin, gate, r_lo))));
+    if (pax == kF64) {
+        HR_DISPATCH_NC(rep, HR_DISPATCH_P(plo, P, (k_residual<NC, P, kF64><<<grid, kBS, 0, s>>>(g, b, ax, r, red, ctx->d_scal, fin, gate, r_lo))));
+    } else if (pax == kF32 && plo == kF16) {
+        HR_DISPATCH_NC(rep, (k_residual<NC, kF16, kF32><<<grid, kBS, 0, s>>>(g, b, ax, r, red, ctx->d_scal, fin, gate, r_lo)));
+    } else {
+        return set_error(ctx, HR_ERR_UNSUPPORTED, "residual precision combination");
+    }
     return check_launch(ctx, "residual");
 }
 
 hr_status blas_accum(hr_ctx *ctx, const Geom &g, int rep, int plo, void *xhi, void *xlo, const double *gate,
-                     cudaStream_t s)
+                     cudaStream_t s, int phi)
 {
     int grid = grid_cap(ctx, g);
-    if (plo == kF32) {
-        HR_DISPATCH_NC(rep, (k_accum<NC, kF32><<<grid, kBS, 0, s>>>(g, xhi, xlo, gate)));
+    if (plo == kF32 && phi == kF64) {
+        HR_DISPATCH_NC(rep, (k_accum<NC, kF64, kF32><<<grid, kBS, 0, s>>>(g, xhi, xlo, gate)));
+    } else if (plo == kF32 && phi == kF32) {
+        HR_DISPATCH_NC(rep, (k_accum<NC, kF32, kF32><<<grid, kBS, 0, s>>>(g, xhi, xlo, gate)));
     } else {
         return set_error(ctx, HR_ERR_UNSUPPORTED, "accumulate precision");
     }

@@ -64,13 +64,20 @@ hr_status cuda_err(hr_ctx *ctx, cudaError_t e, const char *what)
     return set_error(ctx, HR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-hr_status init_scalars(hr_ctx *ctx, int nrhs, double tol, double delta, int maxiter, cudaStream_t s)
+// The binary16 solver's reliable updates use the FP32 tier while |r| stays above
+// kDeltaMid times the last FP64 residual: r_ref - A_32 x_mid carries an error of
+// about 1e-7 |r_ref| (FP32 links and arithmetic), 0.1 % of |r| at the switch.
+constexpr double kDeltaMid = 1e-4;
+
+hr_status init_scalars(hr_ctx *ctx, int nrhs, double tol, double delta, int maxiter, cudaStream_t s,
+                       double delta_mid = 0.0)
 {
     std::vector<double> h(kScalDoubles, 0.0);
     for (int r = 0; r < nrhs; ++r) h[S_ACTIVE * kMaxRhsSlots + r] = 1.0;
     h[S_DELTA2 * kMaxRhsSlots + 0] = delta * delta;
     h[S_DELTA2 * kMaxRhsSlots + 1] = tol * tol;
     h[S_DELTA2 * kMaxRhsSlots + 2] = maxiter;
+    h[S_DELTA2 * kMaxRhsSlots + 3] = delta_mid * delta_mid;
     std::memcpy(ctx->h_scal, h.data(), sizeof(double) * kScalDoubles);
     cudaError_t e = cudaMemcpyAsync(ctx->d_scal, ctx->h_scal, sizeof(double) * kScalDoubles, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -127,9 +134,14 @@ struct Solver {
     // low precision buffers
     void *gauge_lo, *r_lo, *p_lo, *q_lo, *u_lo, *t_lo, *x_lo;
     void *clov_lo; // FP32 copy of the clover field (mixed solvers)
+    // the FP32 tier of the binary16 solver's reliable updates: the FP32 gauge,
+    // the correction since the last FP64 residual, and the FP32 operator's vectors
+    void *gauge_mid, *x_mid, *q_mid, *t_mid, *u_mid;
     size_t h64, hlo, h32, glo;
 
     bool mixed() const { return o.inner_prec != HR_F64; }
+    // binary16 inner solves refresh their residual in FP32 between FP64 ones
+    bool two_tier() const { return o.inner_prec == HR_F16; }
 
     static size_t layout(const Geom &g, int rep, const hr_solver_opts &o, bool clover, Solver *sv, void *work)
     {
@@ -158,7 +170,13 @@ struct Solver {
             void *gl = take(glo), *rl = take(hlo), *pl = take(hlo), *ql = take(hlo), *ul = take(hlo), *tl = take(hlo);
             void *xl = take(h32);
             void *cl = clover ? take(4 * clover_half_bytes(g, rep, kF32)) : nullptr;
+            void *gm = nullptr, *xm = nullptr, *qm = nullptr, *tm = nullptr, *um = nullptr;
+            if (o.inner_prec == HR_F16) {
+                gm = take(gauge_bytes(g, rep, kF32));
+                xm = take(h32); qm = take(h32); tm = take(h32); um = take(h32);
+            }
             if (sv) {
+                sv->gauge_mid = gm; sv->x_mid = xm; sv->q_mid = qm; sv->t_mid = tm; sv->u_mid = um;
                 sv->clov_lo = cl;
                 sv->r64 = r; sv->q64 = q; sv->u64 = u; sv->t64 = t; sv->p64 = nullptr;
                 sv->gauge_lo = gl; sv->r_lo = rl; sv->p_lo = pl; sv->q_lo = ql; sv->u_lo = ul; sv->t_lo = tl;
@@ -197,8 +215,28 @@ struct Solver {
 
     // x += x_lo, r = b - A x in FP64, restart the low-precision residual;
     // every launch skips its work unless *gate != 0 (gate == nullptr: always run)
+    //
+    // Two tiers for the binary16 solver (the gate of the open tier set on the
+    // device by the recurrence's last reduction; gate is then unused):
+    //   FP32: x_mid += x_lo, r_lo = r_ref - A_32 x_mid, with r_ref the last FP64
+    //         residual (r64): accurate to FP32 relative to r_ref, which is all a
+    //         binary16 recurrence can use while |r| > delta_mid |r_ref|;
+    //   FP64: x += x_lo + x_mid, r = b - A x (the reference and the stop test).
     hr_status reliable_update(const double *gate)
     {
+        if (two_tier()) {
+            const double *g1 = flag_ptr(ctx, F_TIER1), *g2 = flag_ptr(ctx, F_TIER2);
+            hr_status st = blas_accum(ctx, g, rep, kF32, x_mid, x_lo, g1, s, kF32);
+            if (!st)
+                st = apply_eo_op(ctx, g, m0, rep, kF32, HR_OP_NORMAL, gauge_mid, x_mid, q_mid, t_mid, u_mid, kFinNone,
+                                 g1, nullptr, s, nullptr, clov_lo);
+            if (!st) st = blas_residual(ctx, g, rep, r64, q_mid, nullptr, kFinMid, g1, kF16, r_lo, s, kF32);
+            if (!st) st = blas_accum(ctx, g, rep, kF32, x, x_lo, g2, s);
+            if (!st) st = blas_accum(ctx, g, rep, kF32, x, x_mid, g2, s);
+            if (!st) st = apply64(x, q64, kFinNone, g2, nullptr);
+            if (!st) st = blas_residual(ctx, g, rep, b, q64, r64, kFinResidual, g2, o.inner_prec, r_lo, s);
+            return st;
+        }
         hr_status st = blas_accum(ctx, g, rep, kF32, x, x_lo, gate, s);
         if (!st) st = apply64(x, q64, kFinNone, gate, nullptr);
         if (!st) st = blas_residual(ctx, g, rep, b, q64, r64, kFinResidual, gate, o.inner_prec, r_lo, s);
@@ -256,13 +294,15 @@ struct Solver {
 
     hr_status start()
     {
-        hr_status st = init_scalars(ctx, g.nrhs, o.tol, o.reliable_delta, o.maxiter, s);
+        hr_status st = init_scalars(ctx, g.nrhs, o.tol, o.reliable_delta, o.maxiter, s, two_tier() ? kDeltaMid : 0.0);
         if (st) return st;
         st = scale_source();
         if (st) return st;
         if (mixed()) {
             st = gauge_convert(ctx, make_geom_gauge(), rep, o.inner_prec, gauge, gauge_lo, s);
             if (!st && clov64) st = clover_convert_f32(ctx, g, rep, clov64, clov_lo, s);
+            if (!st && two_tier()) st = gauge_convert(ctx, make_geom_gauge(), rep, kF32, gauge, gauge_mid, s);
+            if (!st && two_tier()) st = blas_zero(ctx, g, rep, kF32, x_mid, s);
             if (st) return st;
         }
         st = blas_norm2(ctx, g, rep, kF64, b, kFinBB, s);
@@ -556,8 +596,9 @@ hr_status cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_
         const bool have_true = sv.mixed() && ctx->h_scal[F_TRUERES] != 0.0;
         if (!have_true) {
             if (sv.mixed()) {
-                // fold the pending low-precision increment into x
+                // fold the pending low-precision increments into x
                 st = blas_accum(ctx, sv.g, rep, kF32, x, sv.x_lo, nullptr, s);
+                if (!st && sv.two_tier()) st = blas_accum(ctx, sv.g, rep, kF32, x, sv.x_mid, nullptr, s);
                 if (st) return st;
             }
             // true FP64 residual per RHS

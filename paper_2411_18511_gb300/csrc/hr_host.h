@@ -165,12 +165,14 @@ hr_status blas_p(hr_ctx *ctx, const Geom &g, int rep, int pp, int pr, void *p, c
 hr_status blas_convert(hr_ctx *ctx, const Geom &g, int rep, int psrc, int pdst, const void *src, void *dst,
                        const double *gate, cudaStream_t s);
 // r = b - ax (FP64) with |r|^2 -> fin; also writes r in precision plo to r_lo when given
+// r = b - ax (ax FP64, or FP32 with a binary16 r_lo; r nullable), |r|^2 -> fin, r_lo = r
 hr_status blas_residual(hr_ctx *ctx, const Geom &g, int rep, const void *b, const void *ax, void *r, int fin,
-                        const double *gate, int plo, void *r_lo, cudaStream_t s);
+                        const double *gate, int plo, void *r_lo, cudaStream_t s, int pax = kF64);
 // packed FP64 gauge -> packed gauge of precision pdst (same rep)
 hr_status gauge_convert(hr_ctx *ctx, const Geom &g, int rep, int pdst, const void *src, void *dst, cudaStream_t s);
+// x_hi (FP64, or FP32) += x_lo (FP32); x_lo = 0
 hr_status blas_accum(hr_ctx *ctx, const Geom &g, int rep, int plo, void *xhi, void *xlo, const double *gate,
-                     cudaStream_t s);
+                     cudaStream_t s, int phi = kF64);
 hr_status blas_axpy(hr_ctx *ctx, const Geom &g, int rep, double a, const void *x, void *y, cudaStream_t s);
 hr_status blas_gamma5(hr_ctx *ctx, const Geom &g, int rep, void *v, cudaStream_t s);
 hr_status blas_zero(hr_ctx *ctx, const Geom &g, int rep, int prec, void *v, cudaStream_t s);

@@ -1073,14 +1073,17 @@ enum ScalSlot {
                    // [4] reliable updates, [5] device-loop passes, [6] device error (a
                    // bulk copy that did not land in time), [7] source out of range,
                    // [8] S_OUT holds the true FP64 residuals of the current x (the
-                   // last scalar update was a reliable update's)
-    S_DELTA2 = 11, // [0] reliable-update threshold delta^2, [1] tol^2, [2] maxiter (<= 0: none)
+                   // last scalar update was a reliable update's), [9] / [10] the
+                   // open reliable update is of the FP32 / FP64 tier
+    S_DELTA2 = 11, // [0] reliable-update threshold delta^2, [1] tol^2, [2] maxiter (<= 0: none),
+                   // [3] FP32-tier threshold delta_mid^2 (0: every update is an FP64 one)
     S_SCALE = 12,  // per-RHS power of two that brings the source's largest component into [0.5, 1)
     S_BMAX = 13,   // per-RHS largest |component| of the source, as the bits of a float (32 unsigned)
-    S_NSLOTS = 14
+    S_RREF = 14,   // |r|^2 of the last FP64 residual (the FP32 tier's reference)
+    S_NSLOTS = 15
 };
 constexpr int F_DONE = 0, F_GATE = 1, F_NUMERIC = 2, F_ITERS = 3, F_NRELIABLE = 4, F_BODY = 5, F_DEVERR = 6,
-              F_RANGE = 7, F_TRUERES = 8;
+              F_RANGE = 7, F_TRUERES = 8, F_TIER1 = 9, F_TIER2 = 10;
 
 enum FinishMode {
     kFinNone = 0,
@@ -1090,7 +1093,8 @@ enum FinishMode {
     kFinBetaMixed = 4,  // as kFinBeta, but convergence and small residuals open the reliable-update gate
     kFinResidual = 5,   // true FP64 residual of a reliable update: restart bookkeeping, close the gate
     kFinInit = 6,       // |r0|^2: rr = rmax = rrold = sums, a RHS is active while rr > stop
-    kFinBB = 7          // |b|^2: bb = sums, stop = tol^2 bb (tol^2 in scal[S_DELTA2][1])
+    kFinBB = 7,         // |b|^2: bb = sums, stop = tol^2 bb (tol^2 in scal[S_DELTA2][1])
+    kFinMid = 8         // residual of an FP32-tier reliable update: restart bookkeeping (no stop), close the gate
 };
 
 __device__ __forceinline__ double &sc(double *scal, int slot, int r) { return scal[slot * kMaxRhsSlots + r]; }
@@ -1124,7 +1128,14 @@ __device__ inline void finish_reduction(int mode, const double *sums, int nrhs, 
                 } else {
                     double rmax = fmax(sc(scal, S_RMAX, r), v);
                     sc(scal, S_RMAX, r) = rmax;
-                    if (v <= sc(scal, S_STOP, r) || v < sc(scal, S_DELTA2, 0) * rmax) sc(scal, S_FLAGS, F_GATE) = 1.0;
+                    const bool conv = v <= sc(scal, S_STOP, r);
+                    if (conv || v < sc(scal, S_DELTA2, 0) * rmax) {
+                        sc(scal, S_FLAGS, F_GATE) = 1.0;
+                        // the FP64 tier when the FP32 tier is off, at convergence, or
+                        // once |r| fell by delta_mid since the last FP64 residual
+                        const double dm = sc(scal, S_DELTA2, 3);
+                        if (dm == 0.0 || conv || v < dm * sc(scal, S_RREF, r)) sc(scal, S_FLAGS, F_TIER2) = 1.0;
+                    }
                 }
             } else {
                 sc(scal, S_BETA, r) = 0.0;
@@ -1135,6 +1146,7 @@ __device__ inline void finish_reduction(int mode, const double *sums, int nrhs, 
             sc(scal, S_RR, r) = v;
             sc(scal, S_RMAX, r) = v;
             sc(scal, S_RROLD, r) = v;
+            sc(scal, S_RREF, r) = v;
             sc(scal, S_ACTIVE, r) = (v > sc(scal, S_STOP, r)) ? 1.0 : 0.0;
             break;
         case kFinBB:
@@ -1151,6 +1163,18 @@ __device__ inline void finish_reduction(int mode, const double *sums, int nrhs, 
                 sc(scal, S_BETA, r) = 0.0;
             }
             sc(scal, S_OUT, r) = v;
+            sc(scal, S_RREF, r) = v;
+            break;
+        case kFinMid:
+            // r = r_ref - A_32 dx is accurate to FP32 relative to r_ref only: it
+            // restarts the recurrence but stops no right-hand side
+            if (act) {
+                sc(scal, S_BETA, r) = v / sc(scal, S_RROLD, r);
+                sc(scal, S_RR, r) = v;
+                sc(scal, S_RMAX, r) = v;
+            } else {
+                sc(scal, S_BETA, r) = 0.0;
+            }
             break;
         default:
             break;
@@ -1171,13 +1195,22 @@ __device__ inline void finish_reduction(int mode, const double *sums, int nrhs, 
         sc(scal, S_FLAGS, F_DONE) = all_done ? 1.0 : 0.0;
         if (mode == kFinResidual) {
             sc(scal, S_FLAGS, F_GATE) = 0.0;
+            sc(scal, S_FLAGS, F_TIER1) = 0.0;
+            sc(scal, S_FLAGS, F_TIER2) = 0.0;
             sc(scal, S_FLAGS, F_NRELIABLE) += 1.0;
             // x_lo was folded into x and S_OUT = |b - A x|^2: a loop that stops
             // here needs no further true-residual computation
             sc(scal, S_FLAGS, F_TRUERES) = 1.0;
+        } else if (mode == kFinMid) {
+            sc(scal, S_FLAGS, F_GATE) = 0.0;
+            sc(scal, S_FLAGS, F_TIER1) = 0.0;
+            sc(scal, S_FLAGS, F_TRUERES) = 0.0;
         } else if (mode == kFinBeta || mode == kFinBetaMixed || mode == kFinInit) {
             sc(scal, S_FLAGS, F_TRUERES) = 0.0; // x (or x_lo) moved since
         }
+        // an open gate is of exactly one tier
+        if (mode == kFinBetaMixed && sc(scal, S_FLAGS, F_GATE) != 0.0)
+            sc(scal, S_FLAGS, F_TIER1) = sc(scal, S_FLAGS, F_TIER2) != 0.0 ? 0.0 : 1.0;
     }
 }
 
