@@ -125,6 +125,32 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, int i, int rr, const S
     hop_term<MU, false, REP, PREC>(a, nb.bwd[MU], 1 - a.p, (nb.bwd[MU] << l) + rr, g5_in_of<G5IN>(a), acc);
 }
 
+// The epilogue's own operands -- the aux vector, and the fused CG update's
+// x, p and r -- are read only after the eight directions, so their load
+// latency would add to every site of the reducing hops.  Requested into L1
+// when the site starts, they arrive behind the directions' work (a hint: no
+// effect on the results).
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+template <int NC, int PREC>
+__device__ __forceinline__ void prefetch_site(const void *base, int nblk_s, int j)
+{
+    constexpr int NV = SpinorLayout<NC, PREC>::NVEC;
+    const uint4 *v = (const uint4 *)base;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) prefetch_l1(v + vec_index(j, k, NV));
+    if constexpr (PREC == kF16) prefetch_l1((const float *)((const char *)base + SpinorLayout<NC, PREC>::data_bytes(nblk_s)) + j);
+}
+template <int NC, int PREC>
+__device__ __forceinline__ void epilogue_prefetch(const HopArgs &a, int j)
+{
+    if (a.aux) prefetch_site<NC, PREC>(a.aux, a.g.nblk_s, j);
+    if (a.cg_r) {
+        prefetch_site<NC, PREC == kF16 ? kF32 : PREC>(a.cg_x, a.g.nblk_s, j);
+        prefetch_site<NC, PREC>(a.cg_p, a.g.nblk_s, j);
+        prefetch_site<NC, PREC>(a.cg_r, a.g.nblk_s, j);
+    }
+}
+
 // out = alpha * aux + beta * g5^{g5_out} acc, stored; |out|^2 into red.
 // CLOV: the kernel instantiation that also applies the clover site term
 // (a.clov_mode); the others carry no trace of it.
@@ -212,6 +238,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &a, int j, T al, T be, T 
     const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
     SiteNb nb;
     site_neighbours(g, i, a.p, nb);
+    epilogue_prefetch<NC, PREC>(a, j);
     cpx<T> acc[4][NC]; // set by the first term
     hop_dir<0, REP, PREC, G5IN, true>(a, i, rr, nb, acc);
     hop_dir<1, REP, PREC, G5IN>(a, i, rr, nb, acc);

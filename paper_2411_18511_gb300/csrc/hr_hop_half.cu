@@ -138,6 +138,7 @@ __device__ __forceinline__ void h16p_body(const HopArgs &a)
         const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
         SiteNb nb;
         site_neighbours(g, i, a.p, nb);
+        epilogue_prefetch<2, kF16>(a, j);
         H16Ops buf[D + 1];
         h16_fetch<0>(a, nrm, i, rr, nb, buf[0]);
         if constexpr (D > 1) h16_fetch<1>(a, nrm, i, rr, nb, buf[1]);

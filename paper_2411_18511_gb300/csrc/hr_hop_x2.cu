@@ -99,6 +99,7 @@ __device__ __forceinline__ void x2_body(const HopArgs &a)
         const int i = j >> g.lrhs, rr = j & (g.nrhs - 1);
         SiteNb nb;
         site_neighbours(g, i, a.p, nb);
+        epilogue_prefetch<2, kF64>(a, j);
         cdd2 acc[4];
         x2_dir<0, true, NEG>(a, k, i, rr, nb, acc);
         x2_dir<1, false, NEG>(a, k, i, rr, nb, acc);
