@@ -38,9 +38,11 @@ def true_rel_residual(dims, L, m0, b, x):
     return np.linalg.norm(r) / np.linalg.norm(b)
 
 
-def run_solve(ctx, dims, rep, q, m0, b, inner, n_rhs=1, tol=1e-10, maxiter=20000, check_every=0):
+def run_solve(ctx, dims, rep, q, m0, b, inner, n_rhs=1, tol=1e-10, maxiter=20000, check_every=0, delta=None):
     opts = hr.hr_solver_default_opts()
     opts.check_every = check_every
+    if delta is not None:
+        opts.reliable_delta = delta
     opts.tol = tol
     opts.maxiter = maxiter
     opts.inner_prec = inner
@@ -87,6 +89,31 @@ def test_cg_multi_rhs_matches_single(ctx, smeared_8):
     L = oracle.expand_links(dims, 2, q)
     for r in range(n):
         assert true_rel_residual(dims, L, m0, bs[r], xs[r]) <= 1e-10
+
+
+@pytest.mark.parametrize("n_rhs", [1, 4])
+def test_cg_binary16_two_tier_updates(ctx, smeared_8, n_rhs):
+    """Binary16 inner solves refresh the residual in FP32 between FP64 ones.
+    With delta 1e-2 the recurrence asks for a reliable update at every 1e-2
+    of reduction; only those at 1e-4 of the last FP64 residual and at
+    convergence are FP64 (the ones n_reliable_updates counts): 3 for tol
+    1e-10 with one right-hand side, where the FP32-inner solve, whose updates
+    are all FP64, needs 5.  The oracle recomputes every true residual."""
+    dims, q = smeared_8
+    m0 = -0.2
+    b = synth.gaussian_spinor(dims, 2, 2005, n_rhs=n_rhs)
+    b[:, oracle.parity_mask(dims) == 1] = 0
+    rb = b if n_rhs > 1 else b[0]
+    rc16, i16, x16 = run_solve(ctx, dims, hr.HR_FUND, q, m0, rb, hr.HR_F16, n_rhs=n_rhs, delta=1e-2)
+    rc32, i32, x32 = run_solve(ctx, dims, hr.HR_FUND, q, m0, rb, hr.HR_F32, n_rhs=n_rhs, delta=1e-2)
+    assert rc16 == hr.HR_OK and rc32 == hr.HR_OK
+    L = oracle.expand_links(dims, 2, q)
+    xs16 = x16 if n_rhs > 1 else x16[None]
+    for r in range(n_rhs):
+        assert true_rel_residual(dims, L, m0, b[r], xs16[r]) <= 1e-10
+    assert i32.n_reliable_updates >= 4, i32.n_reliable_updates
+    assert i16.n_reliable_updates <= (3 if n_rhs == 1 else 4), i16.n_reliable_updates
+    assert i16.n_reliable_updates < i32.n_reliable_updates
 
 
 @pytest.mark.parametrize("inner", [hr.HR_F64, hr.HR_F32, hr.HR_F16])
