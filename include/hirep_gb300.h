@@ -611,7 +611,7 @@ typedef struct {
     int block;         /* threads per block                                               */
     double best_ms;    /* time of one hop launch with the chosen shape (median of 4)      */
     double default_ms; /* the same for the shape in use before tuning                     */
-    int candidates;    /* shapes timed                                                    */
+    int candidates;    /* shapes timed, both sweeps                                       */
 } hr_tune_result;
 
 /* Time every kernel variant and block size for the hop of this configuration
@@ -619,9 +619,15 @@ typedef struct {
  * out_parity) is overwritten with D_{p,1-p} in, `reps` timed launches per
  * shape; the four fastest are timed three more times, interleaved, and the
  * best median wins -- and use it for all later hop launches of the
- * configuration on this context (operators and solvers included).  If the
- * environment variable HR_AUTOTUNE_CACHE names a file, the choice is written
- * there as JSON and read back by later contexts.  Synchronises the stream.
+ * configuration on this context (operators and solvers included).  A second
+ * sweep, starting from that winner, times the reducing form the solvers
+ * launch (the epilogue also reads an aux vector and reduces |out|^2 over the
+ * grid; `out` serves as its aux) and keeps its own winner for those launches;
+ * *result reports the plain hop's choice.  If the environment variable
+ * HR_AUTOTUNE_CACHE names a file, both choices are written there as JSON (the
+ * reducing one under the key suffixed ":fin") and read back by later
+ * contexts; a plain key without its ":fin" entry serves both forms.
+ * Synchronises the stream.
  * A lattice with twisted boundaries (hr_lattice.theta) runs one kernel
  * whatever the shape: the call returns HR_OK at once, *result zeroed.
  * (The paper measures a hand-tuned kernel, Sec. 3; tuning per shape is this

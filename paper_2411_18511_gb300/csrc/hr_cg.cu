@@ -514,17 +514,22 @@ hr_status cg_solve(hr_ctx *ctx, hr_lattice lat, double m0, hr_rep rep, const hr_
     char keybuf[512];
     {
         HopChoice c64 = hop_choice(ctx, sv.g, rep, kF64), clo = hop_choice(ctx, sv.g, rep, opts->inner_prec);
+        // the reducing launches' shapes are baked in too
+        const HopChoice f64 = hop_choice_fin(ctx, sv.g, rep, kF64), flo = hop_choice_fin(ctx, sv.g, rep, opts->inner_prec),
+                        f32 = hop_choice_fin(ctx, sv.g, rep, kF32), c32 = hop_choice(ctx, sv.g, rep, kF32);
         unsigned long long m0bits;
         std::memcpy(&m0bits, &m0, sizeof m0bits);
         // the twist angles select the kernel and its phases
         unsigned long long tb[4];
         std::memcpy(tb, lat.theta, sizeof tb);
         snprintf(keybuf, sizeof keybuf,
-                 "cg:%d:%d:%d:%d:%d:%d:%d:%llx:%d:%d:%d:%p:%p:%p:%p:%p:%d.%d:%d.%d:%zu:%llx.%llx.%llx.%llx",
+                 "cg:%d:%d:%d:%d:%d:%d:%d:%llx:%d:%d:%d:%p:%p:%p:%p:%p:%d.%d:%d.%d:%d.%d:%d.%d:%d.%d:%d.%d:%zu:"
+                 "%llx.%llx.%llx.%llx",
                  lat.dims[0], lat.dims[1], lat.dims[2], lat.dims[3], sv.g.nrhs, rep, opts->inner_prec, m0bits,
                  device_loop ? -chunk : chunk,
                  opts->maxiter, (int)sizeof(void *), gauge, clover, b, x, work, c64.variant, c64.block, clo.variant,
-                 clo.block, work_bytes, tb[0], tb[1], tb[2], tb[3]);
+                 clo.block, f64.variant, f64.block, flo.variant, flo.block, c32.variant, c32.block, f32.variant,
+                 f32.block, work_bytes, tb[0], tb[1], tb[2], tb[3]);
     }
     cudaGraphExec_t exec = nullptr;
     auto cached = ctx->graphs.find(keybuf);

@@ -226,9 +226,19 @@ HopChoice hop_choice(hr_ctx *ctx, const Geom &g, int rep, int prec)
     return default_choice(rep, prec);
 }
 
+std::string tune_key_fin(const Geom &g, int rep, int prec) { return tune_key(g, rep, prec) + ":fin"; }
+
+HopChoice hop_choice_fin(hr_ctx *ctx, const Geom &g, int rep, int prec)
+{
+    auto it = ctx->tuned.find(tune_key_fin(g, rep, prec));
+    if (it != ctx->tuned.end()) return it->second;
+    return hop_choice(ctx, g, rep, prec);
+}
+
 hr_status launch_hop(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, cudaStream_t s)
 {
-    return dispatch(ctx, g, rep, prec, make_args(ctx, g, L), hop_choice(ctx, g, rep, prec), s);
+    const HopChoice c = L.fin != kFinNone ? hop_choice_fin(ctx, g, rep, prec) : hop_choice(ctx, g, rep, prec);
+    return dispatch(ctx, g, rep, prec, make_args(ctx, g, L), c, s);
 }
 
 hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const HopLaunch &L, HopChoice c,

@@ -138,6 +138,10 @@ hr_status launch_hop_with(hr_ctx *ctx, const Geom &g, int rep, int prec, const H
                           cudaStream_t s);
 HopChoice hop_choice(hr_ctx *ctx, const Geom &g, int rep, int prec);
 std::string tune_key(const Geom &g, int rep, int prec);
+// the shape of reducing launches (aux read and |out|^2 or a fused CG update):
+// their own tuned choice if there is one, else the plain one
+HopChoice hop_choice_fin(hr_ctx *ctx, const Geom &g, int rep, int prec);
+std::string tune_key_fin(const Geom &g, int rep, int prec);
 bool hop_variant_available(int rep, int prec, int variant, int nrhs);
 // autotuner cache file (hr_tune.cu)
 void tune_cache_load(hr_ctx *ctx);

@@ -90,11 +90,60 @@ def test_autotune_chooses_and_persists(tmp_path, monkeypatch, rep, prec):
     assert hr.hr_tune_lookup(c, dims, rep, prec) == (res.variant, res.block)
     saved = json.loads(cache.read_text())
     assert saved[key(dims, rep, prec)] == [res.variant, res.block]
+    # the reducing form (aux read, |out|^2 over the grid) keeps a choice of its own
+    fin = saved[key(dims, rep, prec) + ":fin"]
+    assert fin[0] in range(24) and fin[1] in (64, 128, 192, 256)
+    assert res.candidates >= 8
     assert hop_error(c, dims, rep, prec) <= TOL[prec]
     c.close()
     c2 = hr.Context(0)
     assert hr.hr_tune_lookup(c2, dims, rep, prec) == (res.variant, res.block)
     c2.close()
+
+
+@pytest.mark.parametrize("inner", [hr.HR_F64, hr.HR_F32, hr.HR_F16])
+def test_reducing_shape_from_cache_drives_the_solver(tmp_path, monkeypatch, inner):
+    """A ':fin' cache entry sets the shape of the reducing launches only (the
+    Schur operator's second hop and the CG's fused update), apart from the
+    plain hops' shape; the solve stays right: the oracle recomputes its true
+    residual, and x equals the one solved with the plain shape everywhere to
+    the solver's tolerance."""
+    dims = (6, 4, 8, 10)
+    m0 = -0.2
+    q, _, _ = synth.ape_smear_to_plaquette(synth.haar_links(dims, 1002), dims, 0.6)
+    b = synth.gaussian_spinor(dims, 2, 2006)
+    b[oracle.parity_mask(dims) == 1] = 0
+    red = {hr.HR_F64: [12, 192], hr.HR_F32: [7, 128], hr.HR_F16: [23, 128]}[inner]
+    xs = []
+    for with_fin in (False, True):
+        entries = {}
+        for p, sh in ((hr.HR_F64, [0, 64]), (inner, [0, 64])):
+            entries[key(dims, hr.HR_FUND, p)] = sh
+        if with_fin:
+            entries[key(dims, hr.HR_FUND, inner) + ":fin"] = red
+        cache = tmp_path / f"fin{int(with_fin)}.json"
+        cache.write_text(json.dumps(entries))
+        monkeypatch.setenv("HR_AUTOTUNE_CACHE", str(cache))
+        c = hr.Context(0)
+        opts = hr.hr_solver_default_opts()
+        opts.inner_prec = inner
+        opts.reliable_delta = 0.1 if inner == hr.HR_F64 else (1e-5 if inner == hr.HR_F32 else 3e-3)
+        gauge = fields.pack_gauge(c, dims, hr.HR_FUND, hr.HR_F64, fields.gauge_to_device(q))
+        bp = fields.pack_spinor(c, dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, fields.spinor_to_device(b))
+        xp = fields.zeros_spinor(dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN)
+        work = fields.empty_bytes(hr.hr_cg_workspace_bytes(dims, hr.HR_FUND, opts))
+        rc, info = hr.hr_cg_solve(c, dims, m0, hr.HR_FUND, opts, gauge, bp, xp, work)
+        assert rc == hr.HR_OK
+        assert hr.hr_tune_lookup(c, dims, hr.HR_FUND, inner) == (0, 64)
+        x = fields.unpack_spinor(c, dims, hr.HR_FUND, hr.HR_F64, hr.HR_EVEN, xp).cpu().numpy()
+        L = oracle.expand_links(dims, 2, q)
+        r = b - oracle.normal(dims, L, m0, x)
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+        xs.append(x)
+        c.close()
+    even = oracle.parity_mask(dims) == 0
+    # both stop at a true residual of 1e-10: x agrees to about cond(A) x 1e-10
+    assert np.linalg.norm((xs[0] - xs[1])[even]) / np.linalg.norm(xs[0][even]) < 1e-6
 
 
 def test_autotune_rejects_bad_arguments(ctx):
