@@ -143,6 +143,10 @@ __device__ __forceinline__ void prefetch_site(const void *base, int nblk_s, int 
 template <int NC, int PREC>
 __device__ __forceinline__ void epilogue_prefetch(const HopArgs &a, int j)
 {
+    // the solvers' hot path is the fundamental one; with three colours the
+    // four fields are 24 vectors a site, and the adjoint plain hop ran slower
+    // with the request code in it
+    if constexpr (NC != 2) return;
     if (a.aux) prefetch_site<NC, PREC>(a.aux, a.g.nblk_s, j);
     if (a.cg_r) {
         prefetch_site<NC, PREC == kF16 ? kF32 : PREC>(a.cg_x, a.g.nblk_s, j);
